@@ -1,0 +1,241 @@
+"""Seeded synthetic inputs for the time-evolution FE cases (mesh, materials, sources, regions).
+
+This module only *generates inputs*: node coordinates, tetrahedral connectivity, per-element material
+ids with their Lame parameters and density, the Dirichlet mask, Ricker point-source parameters and the
+node -> region map used by the regional predictor.  It contains none of the method's arithmetic (no
+element matrices, no time integration, no solver, no predictor); both the CUDA path and the CPU oracle
+consume what it returns.
+
+The workloads stand in for the paper's ground models (Section 3.1: layered ground, random impulse inputs at
+surface points, bottom fixed), which are not public: a unit-spaced hex grid split into six linear tets per
+hex (Kuhn/Freudenthal split along the (0,0,0)->(1,1,1) diagonal, the same in every hex, hence conforming),
+horizontally layered log-normal materials (soft over stiff, like sediment over bedrock), an optional
+low-velocity basin inclusion, and one Ricker-wavelet point force per case at a random interior node in a
+random direction.
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+import math
+
+import numpy as np
+
+# Six Kuhn tets of the unit hex: vertex chains 0 -> e_a -> e_a + e_b -> (1,1,1) for every permutation
+# (a, b, c) of the axes.  Corner index bits: bit0 = x, bit1 = y, bit2 = z.
+_KUHN = []
+for perm in itertools.permutations(range(3)):
+    c0 = 0
+    c1 = c0 | (1 << perm[0])
+    c2 = c1 | (1 << perm[1])
+    c3 = 7
+    # parity of the permutation decides orientation; odd permutations swap the last two vertices
+    inv = sum(1 for i in range(3) for j in range(i + 1, 3) if perm[i] > perm[j])
+    _KUHN.append((c0, c1, c3, c2) if inv % 2 else (c0, c1, c2, c3))
+KUHN_TETS = np.array(_KUHN, dtype=np.int64)  # [6][4] corner ids
+
+
+@dataclasses.dataclass
+class Mesh:
+    """A tet4 mesh with per-element materials and a per-DOF Dirichlet mask."""
+    xyz: np.ndarray          # [N][3] float64
+    conn: np.ndarray         # [E][4] int32, positively oriented
+    mat_id: np.ndarray       # [E] int32
+    lam_mu_rho: np.ndarray   # [n_mat][3] float64
+    fixed_dof: np.ndarray    # [3N] uint8 (1 = Dirichlet, value 0)
+    dims: tuple              # (Hx, Hy, Hz) hex counts
+    h: float                 # hex edge length
+
+    @property
+    def n_nodes(self) -> int:
+        return self.xyz.shape[0]
+
+    @property
+    def n_elems(self) -> int:
+        return self.conn.shape[0]
+
+
+@dataclasses.dataclass
+class Source:
+    """Ricker point force: amp * (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2) along `direction`."""
+    node: int
+    direction: np.ndarray    # [3] unit vector
+    f0: float
+    t0: float
+    amp: float = 1.0
+
+
+@dataclasses.dataclass
+class TimeParams:
+    dt: float = 0.01
+    beta: float = 0.25
+    gamma: float = 0.5
+    a0: float = 0.01         # Rayleigh mass-proportional damping
+    a1: float = 0.001        # Rayleigh stiffness-proportional damping
+
+
+def rng_for(config: int, mesh_id: int = 0, case_id: int = 0, stream: int = 0) -> np.random.Generator:
+    """Independent reproducible stream per (config, mesh, case, purpose)."""
+    return np.random.default_rng(np.random.SeedSequence([20380, config, mesh_id, case_id, stream]))
+
+
+def _morton3(ix, iy, iz, bits=21):
+    code = np.zeros(ix.shape, dtype=np.uint64)
+    for b in range(bits):
+        code |= ((ix >> b) & 1).astype(np.uint64) << np.uint64(3 * b)
+        code |= ((iy >> b) & 1).astype(np.uint64) << np.uint64(3 * b + 1)
+        code |= ((iz >> b) & 1).astype(np.uint64) << np.uint64(3 * b + 2)
+    return code
+
+
+def structured_grid(Hx: int, Hy: int, Hz: int, h: float):
+    """Node coordinates and Kuhn-split connectivity of an Hx x Hy x Hz hex grid.
+
+    Nodes are numbered in Morton (Z-curve) order of their integer grid position and elements hex by hex
+    in Morton order of the hex, the six tets of a hex consecutive -- the locality-preserving numbering a
+    mesher's reordering step would hand to an FE solver.
+    """
+    nx, ny, nz = Hx + 1, Hy + 1, Hz + 1
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    node_order = np.argsort(_morton3(i, j, k), kind="stable")
+    new_id = np.empty(node_order.size, dtype=np.int64)
+    new_id[node_order] = np.arange(node_order.size)
+    xyz = np.stack([i[node_order] * h, j[node_order] * h, k[node_order] * h], axis=1).astype(np.float64)
+    hk, hj, hi = np.meshgrid(np.arange(Hz), np.arange(Hy), np.arange(Hx), indexing="ij")
+    hi, hj, hk = hi.ravel(), hj.ravel(), hk.ravel()
+    hex_order = np.argsort(_morton3(hi, hj, hk), kind="stable")
+    base = (hi + nx * (hj + ny * hk))[hex_order].astype(np.int64)        # [H] lower corner (lexicographic)
+    corner_off = np.array([(c & 1) + nx * (((c >> 1) & 1) + ny * ((c >> 2) & 1)) for c in range(8)],
+                          dtype=np.int64)
+    conn_lex = base[:, None, None] + corner_off[KUHN_TETS][None, :, :]   # [H][6][4]
+    return xyz, new_id[conn_lex].reshape(-1, 4).astype(np.int32)
+
+
+def _element_centroid_z(xyz, conn):
+    return xyz[conn, 2].mean(axis=1)
+
+
+def layered_mesh(Hx, Hy, Hz, h, layer_tops, base_lame, rho=1.0, sigma=0.0, rng=None, basin=None) -> Mesh:
+    """Horizontally layered materials assigned by element centroid depth.
+
+    layer_tops: increasing z-coordinates of the layer interfaces from the bottom (len = n_layers - 1).
+    base_lame:  (lambda, mu) per layer, listed bottom -> top.
+    sigma:      log-normal scatter: each layer's (lambda, mu) times exp(sigma * xi), xi ~ N(0,1), one xi per
+                layer shared by lambda and mu (Poisson ratio kept).
+    basin:      optional (cx, cy, ax, ay, az, mu_factor): half-ellipsoid at the top surface whose elements
+                get mu scaled by mu_factor (one extra material per layer it cuts).
+    """
+    xyz, conn = structured_grid(Hx, Hy, Hz, h)
+    zc = _element_centroid_z(xyz, conn)
+    layer = np.searchsorted(np.asarray(layer_tops, dtype=np.float64), zc, side="right").astype(np.int32)
+    n_layers = len(base_lame)
+    lmr = []
+    for li in range(n_layers):
+        lam, mu = base_lame[li]
+        if sigma > 0.0:
+            s = math.exp(sigma * rng.standard_normal())
+            lam, mu = lam * s, mu * s
+        lmr.append((lam, mu, rho))
+    mat_id = layer.copy()
+    if basin is not None:
+        cx, cy, ax, ay, az, fac = basin
+        ztop = Hz * h
+        cen = xyz[conn].mean(axis=1)
+        inside = ((cen[:, 0] - cx) / ax) ** 2 + ((cen[:, 1] - cy) / ay) ** 2 + ((cen[:, 2] - ztop) / az) ** 2 < 1.0
+        for li in range(n_layers):
+            lam, mu, r = lmr[li]
+            lmr.append((lam, mu * fac, r))
+        mat_id = np.where(inside, layer + n_layers, layer).astype(np.int32)
+    fixed = np.zeros(xyz.shape[0] * 3, dtype=np.uint8)
+    bottom = np.nonzero(xyz[:, 2] == 0.0)[0]
+    fixed[3 * bottom] = 1
+    fixed[3 * bottom + 1] = 1
+    fixed[3 * bottom + 2] = 1
+    return Mesh(xyz=xyz, conn=conn, mat_id=mat_id, lam_mu_rho=np.asarray(lmr, dtype=np.float64),
+                fixed_dof=fixed, dims=(Hx, Hy, Hz), h=h)
+
+
+def interior_nodes(mesh: Mesh) -> np.ndarray:
+    """Nodes strictly inside the box (on no boundary face)."""
+    Hx, Hy, Hz = mesh.dims
+    q = np.rint(mesh.xyz / mesh.h).astype(np.int64)
+    m = ((q[:, 0] > 0) & (q[:, 0] < Hx) & (q[:, 1] > 0) & (q[:, 1] < Hy) & (q[:, 2] > 0) & (q[:, 2] < Hz))
+    return np.nonzero(m)[0]
+
+
+def random_source(mesh: Mesh, rng: np.random.Generator, f0=None, f0_range=(2.0, 8.0)) -> Source:
+    nodes = interior_nodes(mesh)
+    node = int(nodes[rng.integers(0, nodes.size)])
+    d = rng.standard_normal(3)
+    d = d / np.linalg.norm(d)
+    if f0 is None:
+        f0 = float(rng.uniform(*f0_range))
+    return Source(node=node, direction=d, f0=float(f0), t0=1.2 / float(f0), amp=1.0)
+
+
+def region_map(mesh: Mesh, region_nodes: int = 1024) -> np.ndarray:
+    """Node -> region id: free nodes in Morton order of their grid position, cut into runs of
+    `region_nodes`; nodes whose three DOFs are all fixed get -1 (they carry no unknowns)."""
+    q = np.rint(mesh.xyz / mesh.h).astype(np.int64)
+    code = _morton3(q[:, 0], q[:, 1], q[:, 2])
+    free_node = mesh.fixed_dof.reshape(-1, 3).min(axis=1) == 0
+    order = np.argsort(code, kind="stable")
+    order = order[free_node[order]]
+    reg = np.full(mesh.n_nodes, -1, dtype=np.int32)
+    reg[order] = (np.arange(order.size) // region_nodes).astype(np.int32)
+    return reg
+
+
+# --------------------------------------------------------------------------------------------------------
+# The benchmark workloads.  Sizes follow the five configurations the method is exercised on; every
+# random draw is seeded by (config, mesh, case).
+# --------------------------------------------------------------------------------------------------------
+
+def config1_mesh() -> Mesh:
+    """Unit box, 8^3 hexes, h = 1/8: two layers, (4,2) below z = 0.5 and (2,1) above, rho = 1."""
+    return layered_mesh(8, 8, 8, 1.0 / 8, layer_tops=[0.5], base_lame=[(4.0, 2.0), (2.0, 1.0)])
+
+
+def config1_sources(n_cases: int = 1):
+    m = config1_mesh()
+    return [random_source(m, rng_for(1, 0, c), f0=5.0) for c in range(n_cases)]
+
+
+def config2_mesh(Hx=64, Hy=64, Hz=32, mesh_id=0, h=1.0 / 64) -> Mesh:
+    """Three equal layers, base (8,4)/(4,2)/(2,1) bottom -> top, log-normal sigma = 0.3 per layer."""
+    zt = Hz * h
+    return layered_mesh(Hx, Hy, Hz, h, layer_tops=[zt / 3.0, 2.0 * zt / 3.0],
+                        base_lame=[(8.0, 4.0), (4.0, 2.0), (2.0, 1.0)], sigma=0.3,
+                        rng=rng_for(2, mesh_id, 0, 1))
+
+
+def config2_sources(mesh: Mesh, n_cases: int = 16, config: int = 2, first_case: int = 0):
+    return [random_source(mesh, rng_for(config, 0, first_case + c, 2)) for c in range(n_cases)]
+
+
+def config3_dims(n_meshes: int = 64):
+    rng = rng_for(3, 0, 0, 3)
+    return [(int(rng.integers(24, 65)), int(rng.integers(24, 65)), int(rng.integers(24, 49)))
+            for _ in range(n_meshes)]
+
+
+def config3_mesh(mesh_id: int, dims) -> Mesh:
+    Hx, Hy, Hz = dims
+    h = 1.0 / 64
+    zt = Hz * h
+    return layered_mesh(Hx, Hy, Hz, h, layer_tops=[zt / 3.0, 2.0 * zt / 3.0],
+                        base_lame=[(8.0, 4.0), (4.0, 2.0), (2.0, 1.0)], sigma=0.3,
+                        rng=rng_for(3, mesh_id, 0, 1))
+
+
+def config4_mesh(Hx=256, Hy=256, Hz=128, h=1.0 / 64) -> Mesh:
+    """Five seeded layers plus a half-ellipsoid low-velocity basin (mu x 0.3) at the surface."""
+    rng = rng_for(4, 0, 0, 1)
+    zt = Hz * h
+    tops = [zt * f for f in (0.2, 0.4, 0.6, 0.8)]
+    base = [(16.0, 8.0), (12.0, 6.0), (8.0, 4.0), (4.0, 2.0), (2.0, 1.0)]
+    Lx, Ly = Hx * h, Hy * h
+    basin = (rng.uniform(0.25 * Lx, 0.75 * Lx), rng.uniform(0.25 * Ly, 0.75 * Ly),
+             rng.uniform(0.5, 1.5), rng.uniform(0.5, 1.5), rng.uniform(0.3, 1.0), 0.3)
+    return layered_mesh(Hx, Hy, Hz, h, layer_tops=tops, base_lame=base, sigma=0.3, rng=rng, basin=basin)
