@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark: time-steps/s over all cases at certified relative residual 1e-8 (one JSON line).
+
+Workload (the medium configuration): a 64x64x32 hex box (h = 1/64) split into 786,432 linear tets
+(139,425 nodes, 418,275 DOF), three seeded log-normal layers, bottom fixed, 16 cases sharing the mesh
+(Ricker point sources at seeded interior nodes, f0 ~ U[2, 8]), Newmark dt = 0.01 with Rayleigh damping
+(0.01, 0.001).  The solver is the FP32-inner / FP64-refined block-Jacobi PCG with the EBE product, started
+from the data-driven predictor (s = 32 stored steps, regions of 1024 nodes).  A "step" advances all 16
+cases by one time step: predictor, right-hand side, certified solve, Newmark update.  The simulation is
+first run for --spinup steps (default 250: the paper times steps 250-500), then --warmup untimed steps,
+then --steps timed steps.
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (different case seeds) on its own
+GPU; value = all ranks' case-steps / the slowest rank's time ("replicas only": cases are independent).
+
+--impl reference times the FP64 CPU oracle (scipy CSR, Algorithm 1, the regional MGS predictor) on the
+host cores; each of its steps is one case-step of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-steps/s over all cases at rel. residual 1e-8; EBE matvec HBM GB/s vs peak"
+UNIT = "case-steps/s"
+FLOP_PER_ELEM_CASE = 190.0     # factorised tet4 apply + consistent mass + fused p^T A p (FMA = 2 flops)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--spinup", type=int, default=250)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--predictor", default="dd", choices=["dd", "ab4"])
+    ap.add_argument("--cases", type=int, default=16)
+    ap.add_argument("--dims", default="64,64,32")
+    ap.add_argument("--s-max", type=int, default=32)
+    ap.add_argument("--region-nodes", type=int, default=1024)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--comparator-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz", 2070.0)
+    return 6800.0, "fallback", 2070.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower() == "active":
+                        reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(args, rank):
+    from paper_2409_20380_gb300 import workload as wl
+    Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
+    mesh = wl.config2_mesh(Hx, Hy, Hz)
+    srcs = wl.config2_sources(mesh, args.cases, first_case=rank * args.cases)
+    return mesh, srcs, wl.TimeParams(), wl.region_map(mesh, args.region_nodes)
+
+
+def cpu_baseline(args, mesh, srcs, tp, regions, n_case_steps=8):
+    """The FP64 oracle, as it stands, on case 0 of the same workload from rest (bounded sample)."""
+    import numpy as np
+    import oracle
+    sysm, A = oracle.build_system(mesh, tp)
+    Binv = oracle.block_jacobi_inverse(A, sysm.free)
+    sim = oracle.CaseSimulator(sysm, A, Binv, srcs[0], predictor="dd" if args.predictor == "dd" else "ab4",
+                               s_max=args.s_max, region_of_node=regions)
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(n_case_steps):
+        its += sim.step().iters
+    dt = time.perf_counter() - t0
+    return {"value": n_case_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"case 0, steps 1-{n_case_steps} from rest of the same mesh/sources "
+                      f"(scipy CSR FP64 Algorithm 1 + regional MGS, {its} CG iterations, single thread)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    mesh, srcs, tp, regions = workload(args, 0)
+    import oracle
+    sysm, A = oracle.build_system(mesh, tp)
+    Binv = oracle.block_jacobi_inverse(A, sysm.free)
+    sim = oracle.CaseSimulator(sysm, A, Binv, srcs[0], predictor="dd" if args.predictor == "dd" else "ab4",
+                               s_max=args.s_max, region_of_node=regions)
+    for _ in range(args.warmup):
+        sim.step()
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        its += sim.step().iters
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    sample = (f"case 0 of the workload, steps {args.warmup + 1}-{args.warmup + args.steps} from rest, one "
+              f"case-step per benchmark step ({its} CG iterations)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args, mesh),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def config_dict(args, mesh):
+    return {"workload": f"medium: {args.dims.replace(',', 'x')} hex box split into {mesh.n_elems} tets "
+                        f"({mesh.n_nodes} nodes), {args.cases} cases on one mesh, "
+                        f"{'FP32-inner/FP64-refined' if args.precision == 'mixed' else 'FP64'} block-Jacobi "
+                        f"EBE-PCG to rel. residual 1e-8, "
+                        f"{'data-driven predictor s=%d' % args.s_max if args.predictor == 'dd' else 'AB4 predictor'}",
+            "mesh_hex": args.dims, "n_elems": mesh.n_elems, "n_nodes": mesh.n_nodes, "cases_per_gpu": args.cases,
+            "precision": args.precision, "predictor": args.predictor, "s_max": args.s_max,
+            "region_nodes": args.region_nodes, "tol": 1e-8, "spinup_steps": args.spinup,
+            "l2": "inputs larger than L2: each step streams the 16-case state and the snapshot ring (>1 GB)",
+            "parallelism": "replicas"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2409_20380_gb300 import build, fem
+    from paper_2409_20380_gb300 import workload as wl
+    build.build()
+    fem.lib()
+    mesh, srcs, tp, regions = workload(args, rank)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER if args.precision == "mixed" else fem.FEM_FP64,
+                                predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
+                                s_max=args.s_max, snapshot_fp32=1, tol=1e-8)
+    h = fem.fem_mesh_create(mesh, tp)
+    fem.fem_mesh_set_regions(h, regions)
+    bt = fem.fem_batch_create(opts)
+    nc = len(srcs)
+    for s in srcs:
+        fem.fem_case_add(bt, h, s)
+    fem.fem_step(bt, args.spinup, nc)
+    fem.fem_step(bt, args.warmup, nc)
+    # ---- timed region: device-resident, CUDA events on the batch stream ----
+    sampler = ClockSampler(local)
+    fem.fem_batch_profile(bt, 1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    st, iters, relres = fem.fem_step(bt, args.steps, nc)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    prof = fem.fem_batch_profile(bt, 0)
+    ms = ev0.elapsed_time(ev1)
+    t_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = t.item()
+    value = ws * nc * args.steps / (t_max / 1e3)
+    # ---- end to end through the public API: H2D loads, step, D2H displacements ----
+    N = mesh.n_nodes
+    step0 = fem.fem_batch_steps(bt)
+    ne = args.e2e_steps
+    loads = torch.empty((ne + 2, nc, 3), dtype=torch.float64).pin_memory()
+    for k in range(ne + 2):
+        tk = (step0 + 1 + k) * tp.dt
+        for c, s in enumerate(srcs):
+            loads[k, c] = torch.from_numpy(wl.ricker_load(s, tk))
+    u_host = torch.empty(nc * N * 3, dtype=torch.float64).pin_memory()
+    for k in range(2):
+        fem.fem_batch_set_loads(bt, loads[k])
+        fem.fem_step(bt, 1, nc)
+        fem.fem_batch_get_field(bt, fem.FEM_FIELD_U, u_host)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(2, ne + 2):
+        fem.fem_batch_set_loads(bt, loads[k])
+        fem.fem_step(bt, 1, nc)
+        fem.fem_batch_get_field(bt, fem.FEM_FIELD_U, u_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = t.item()
+    e2e = {"value": ws * nc * ne / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nc * 3 * 8,
+           "d2h_bytes_per_step": nc * N * 3 * 8, "steps": ne}
+    # ---- plain FP64 EBE-PCG with Adams-Bashforth on the same state (the comparator) ----
+    comparator = None
+    if not args.no_comparator and args.comparator_steps > 0:
+        cmp_opts = fem.fem_opts_default(precision=fem.FEM_FP64, predictor=fem.FEM_PRED_AB4, tol=1e-8)
+        bt2 = fem.fem_batch_create(cmp_opts)
+        for s in srcs:
+            fem.fem_case_add(bt2, h, s)
+        # same physics from rest is not the same state; run the comparator on the steps right after a
+        # short spin-up so its iteration counts are those of a developed wavefield
+        fem.fem_step(bt2, 30, nc)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st2, it2, rr2 = fem.fem_step(bt2, args.comparator_steps, nc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1)
+        comparator = {"value": nc * args.comparator_steps / (cms / 1e3), "unit": UNIT,
+                      "what": "plain FP64 EBE-PCG + Adams-Bashforth, same GPU, steps 31-%d" %
+                              (30 + args.comparator_steps),
+                      "cg_iters_per_case_step": float(it2.sum()) / (nc * args.comparator_steps)}
+        fem.fem_batch_destroy(bt2)
+    if rank != 0:
+        fem.fem_batch_destroy(bt)
+        fem.fem_mesh_destroy(h)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    # ---- roofline of the dominant kernel ----
+    hbm_peak, peak_kind, sm_max = peaks()
+    E = mesh.n_elems
+    rpad = 1 << (nc - 1).bit_length()
+    if prof["ebe32_launches"] > 0:
+        avg_ms = prof["ebe32_ms"] / prof["ebe32_launches"]
+        w_val = 4
+        kernel = "k_ebe (FP32, %d cases)" % rpad
+    else:
+        avg_ms = prof["ebe64_ms"] / max(prof["ebe64_launches"], 1)
+        w_val = 8
+        kernel = "k_ebe (FP64, %d cases)" % rpad
+    rec_b = 12 * w_val
+    bytes_launch = E * (16 + rec_b) + rpad * N * 3 * (w_val + w_val)
+    flops_launch = FLOP_PER_ELEM_CASE * E * rpad
+    gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
+    tfs = flops_launch / (avg_ms * 1e-3) / 1e12
+    # FP32 ALU peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x max clock; FP64: 152 x 4 flop
+    alu_peak = 152 * (128 if w_val == 4 else 4) * 2 * sm_max * 1e6 / 1e12
+    t_hbm = bytes_launch / (hbm_peak * 1e9)
+    t_alu = flops_launch / (alu_peak * 1e12)
+    if t_alu > t_hbm:
+        roof = {"bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfs / alu_peak,
+                "peak_kind": "derived from unit counts x max SM clock", "traffic": None}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "peak_kind": peak_kind, "traffic": None}
+    roof.update({"kernel": kernel, "avg_launch_ms": avg_ms, "launches": prof["ebe32_launches"] or prof["ebe64_launches"],
+                 "alg_bytes_per_launch": bytes_launch, "alg_flops_per_launch": flops_launch,
+                 "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak})
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(args, mesh, srcs, tp, regions)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": config_dict(args, mesh), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": prof["kernel_launches"], "clocks": clocks,
+        "cg_iters_per_case_step": float(iters.sum()) / (nc * args.steps),
+        "max_certified_relres": float(relres.max()), "status": int(st),
+        "phase_ms_per_step": {k: prof[k] / max(prof["steps"], 1) for k in
+                              ("predict_ms", "rhs_ms", "solve_ms", "update_ms")},
+        "kernel_ms_per_step": {"ebe32": prof["ebe32_ms"] / max(prof["steps"], 1),
+                               "ebe64": prof["ebe64_ms"] / max(prof["steps"], 1),
+                               "cg_vec": prof["cg_vec_ms"] / max(prof["steps"], 1)},
+        "fp64_plain_comparator": comparator,
+    }
+    print(json.dumps(out), flush=True)
+    fem.fem_batch_destroy(bt)
+    fem.fem_mesh_destroy(h)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * libfem -- matrix-free element-by-element (EBE) solver for many time-evolution linear-elastic FE cases,
+ * with the data-driven initial-guess predictor, for one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The operations follow Ichimura et al., "Heterogeneous computing in a strongly-connected CPU-GPU
+ * environment: fast multiple time-evolution equation-based modeling accelerated using data-driven
+ * approach" (arXiv 2409.20380):
+ *   - the target problem: many cases of A x^it = f^it solved sequentially in it (Section 2.1, Eq. 1);
+ *   - the Newmark-beta system A = 4M/dt^2 + 2C/dt + K with C = a0 M + a1 K and its right-hand side
+ *     (Section 3.1, Eq. GE:DIS), and the velocity/acceleration update (Section 3.1, Eq. timestep);
+ *   - the EBE matrix-vector product q = sum_e P_e^T A_e P_e p, for r cases at once (Section 3.2,
+ *     Eq. eqebefem and Eq. eqmebefem);
+ *   - the 3x3 block-Jacobi preconditioned CG (Algorithm 1);
+ *   - the Adams-Bashforth initial guess and the regional orthogonal-decomposition predictor (Section 3.2).
+ * Elements are linear 4-node tetrahedra (12x12 element matrices); the paper's own runs use 10-node tets.
+ *
+ * Conventions for every entry point:
+ *   - Return value: FEM_OK (0) or a negative fem_status; fem_last_error() gives a message (thread-local).
+ *     No call aborts, traps or prints.
+ *   - Host pointers (named *_host or documented as host) are read during the call and copied; the caller
+ *     keeps ownership.  Device pointers (*_dev) are caller-owned device memory of the current device; the
+ *     library never frees them.
+ *   - Work is ordered on the CUDA stream passed as `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  Calls that return per-case results to host memory synchronise that stream.
+ *   - Multi-case nodal vectors use the layout [node][3][n_rhs] (component-major within a node, case
+ *     fastest), i.e. value (node n, direction k, case c) is at index (n*3 + k)*n_rhs + c.  n_rhs must be
+ *     1, 2, 4, 8, 16 or 32.
+ *   - Dirichlet DOFs (fixed_dof = 1) hold zero in every solution; their entries of right-hand sides are
+ *     ignored and their entries of matrix-vector products are returned as zero.
+ */
+#ifndef FEM_H_
+#define FEM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fem_status;
+enum {
+  FEM_OK = 0,
+  FEM_ERR_ARG = -1,            /* invalid argument (null pointer, size, layout, unsupported option) */
+  FEM_ERR_OOM = -2,            /* device allocation failed */
+  FEM_ERR_CUDA = -3,           /* a CUDA runtime call or kernel launch failed */
+  FEM_ERR_NOT_CONVERGED = -4,  /* maxit reached before the certified tolerance */
+  FEM_ERR_BREAKDOWN = -5,      /* p^T A p <= 0 or a non-finite CG scalar */
+  FEM_ERR_NONFINITE = -6,      /* NaN/Inf in inputs or results */
+  FEM_ERR_TIMEOUT = -7,        /* a bounded device-side wait expired */
+  FEM_ERR_STATE = -8           /* call not valid in the object's current state */
+};
+
+/* Precision of the solve. */
+enum {
+  FEM_FP64 = 0,          /* every operation in FP64 (the plain method) */
+  FEM_FP32_INNER = 1     /* FP32 EBE + preconditioner inside an inner PCG; FP64 outer residual,
+                            dot-product accumulation and refinement update; certified in FP64 */
+};
+
+/* Initial-guess predictor used by fem_step. */
+enum {
+  FEM_PRED_AB4 = 0,      /* Adams-Bashforth 4 (Section 3.2) */
+  FEM_PRED_DD = 1        /* Adams-Bashforth 4 + regional data-driven correction (Section 3.2) */
+};
+
+/* What fem_case_get returns. */
+enum {
+  FEM_FIELD_U = 0,       /* displacement u^it */
+  FEM_FIELD_V = 1,       /* velocity v^it */
+  FEM_FIELD_A = 2,       /* acceleration a^it */
+  FEM_FIELD_DU = 3,      /* last solved increment du = u^it - u^{it-1} */
+  FEM_FIELD_B = 4,       /* last right-hand side b (Section 3.1, Eq. GE:DIS in increment form) */
+  FEM_FIELD_GUESS = 5    /* last initial guess of the increment handed to the solver */
+};
+
+typedef struct {
+  double dt;             /* time increment */
+  double beta;           /* Newmark beta; only 0.25 is supported */
+  double gamma;          /* Newmark gamma; only 0.5 is supported */
+  double a0, a1;         /* Rayleigh damping C = a0 M + a1 K */
+} fem_time_params;
+
+typedef struct {
+  int precision;         /* FEM_FP64 or FEM_FP32_INNER */
+  int predictor;         /* FEM_PRED_AB4 or FEM_PRED_DD */
+  double tol;            /* certified relative residual ||b - A x|| / ||b|| (Algorithm 1's epsilon) */
+  int maxit;             /* max CG iterations per solve (inner iterations summed in FEM_FP32_INNER) */
+  int s_max;             /* max stored snapshot pairs s of the data-driven predictor (<= 32) */
+  double inner_tol;      /* FEM_FP32_INNER: relative reduction asked of each inner solve */
+  double tau;            /* predictor column-drop threshold (relative orthogonalised norm) */
+  int snapshot_fp32;     /* 1: store predictor snapshots in FP32 (Gram accumulated in FP64) */
+  int check_every;       /* CG iterations between host-side convergence polls (>= 1) */
+  int reserved[6];
+} fem_opts;
+
+/* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-5, tau 1e-6,
+ * snapshot_fp32 1, check_every 8. */
+void fem_opts_default(fem_opts* o);
+
+typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */
+typedef struct fem_batch fem_batch;  /* opaque: per-case time-stepping state and predictor snapshots */
+
+/*
+ * Creates a mesh on the current device and precomputes, on the GPU, what the EBE operator needs
+ * (Section 3.2, Eq. eqebefem): per-element shape-function gradients and volume-weighted material
+ * coefficients, the node 3x3 diagonal blocks of A = (4/dt^2 + 2 a0/dt) M + (1 + 2 a1/dt) K and their
+ * inverses (Algorithm 1's block-Jacobi B^{-1}; only the free DOFs of a node enter its block).
+ *   xyz        [n_nodes][3] host, FP64 coordinates.
+ *   conn       [n_elems][4] host, node ids of each linear tet, positively oriented (det > 0).
+ *   mat_id     [n_elems] host, index into lam_mu_rho.
+ *   lam_mu_rho [n_mat][3] host, (lambda, mu, rho) per material.
+ *   fixed_dof  [3*n_nodes] host, 1 = Dirichlet (value 0), 0 = free.
+ *   tp         time parameters (beta = 1/4, gamma = 1/2 only).
+ * Errors: FEM_ERR_ARG for null pointers, ids out of range, non-positive volumes or unsupported Newmark
+ * parameters; FEM_ERR_OOM / FEM_ERR_CUDA.  Synchronises `stream`.
+ */
+fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
+                           const int32_t* mat_id, int n_mat, const double* lam_mu_rho,
+                           const uint8_t* fixed_dof, const fem_time_params* tp, void* stream,
+                           fem_mesh** out);
+fem_status fem_mesh_destroy(fem_mesh* m);
+
+/*
+ * Sets the predictor's regions (Section 3.2: the domain is divided into small regions, each predicted
+ * independently).  region_of_node [n_nodes] host: region id >= 0, or -1 for a node with no free DOF.
+ * The nodes of one region must form a contiguous node-id range (nodes with id -1 may sit inside it).
+ * Errors: FEM_ERR_ARG if ids are out of range or a region is not contiguous.
+ */
+fem_status fem_mesh_set_regions(fem_mesh* m, const int32_t* region_of_node);
+
+/*
+ * Matrix-free EBE product (Section 3.2, Eq. eqebefem / eqmebefem), for n_rhs cases at once:
+ *   q = sum_e P_e^T ((alpha_M M_e + alpha_K K_e) (P_e p)),  q = 0 on Dirichlet DOFs.
+ * With alpha_M = 4/dt^2 + 2 a0/dt and alpha_K = 1 + 2 a1/dt this is q = A p.
+ *   precision FEM_FP64: p_dev, q_dev are double*; FEM_FP32_INNER: float* (FP32 element records).
+ *   p_dev, q_dev [n_nodes][3][n_rhs] device; p must be zero on Dirichlet DOFs; q is overwritten.
+ *   ptq_dev      optional [n_rhs] device double*: receives p^T q per case, accumulated element by
+ *                element (p_e^T A_e p_e) with FP64 reduction; NULL to skip.
+ * Errors: FEM_ERR_ARG (null pointers, n_rhs), FEM_ERR_CUDA.
+ */
+fem_status fem_ebe_apply(fem_mesh* m, int precision, const void* p_dev, void* q_dev, int n_rhs,
+                         double alpha_M, double alpha_K, double* ptq_dev, void* stream);
+
+/*
+ * Solves A x = b for n_rhs cases (Algorithm 1: 3x3 block-Jacobi PCG with the EBE product), starting from
+ * the guess in x_dev.  With opts->precision = FEM_FP32_INNER the solve is an FP64 iterative refinement
+ * whose corrections come from an FP32 inner PCG.  Either way each case stops when its FP64 true residual
+ * ||b - A x|| / ||b|| < opts->tol (a recursive residual below tol is re-checked against the true one and
+ * the iteration continues if needed).  ||b|| = 0 gives x = 0 and 0 iterations.
+ *   b_dev, x_dev [n_nodes][3][n_rhs] device doubles; x is in: guess, out: solution (0 on Dirichlet DOFs).
+ *   iters_out    [n_rhs] host (nullable): CG iterations per case (inner iterations in FEM_FP32_INNER).
+ *   relres_out   [n_rhs] host (nullable): certified FP64 relative residual per case.
+ * Returns FEM_ERR_NOT_CONVERGED if some case hit maxit, FEM_ERR_BREAKDOWN on p^T A p <= 0.
+ * Scratch vectors are allocated by the library (cached in the mesh).  Synchronises `stream`.
+ */
+fem_status pcg_solve(fem_mesh* m, const double* b_dev, double* x_dev, int n_rhs, const fem_opts* opts,
+                     void* stream, int* iters_out, double* relres_out);
+
+/* Creates an empty batch of cases; all later work of the batch is ordered on `stream`. */
+fem_status fem_batch_create(const fem_opts* opts, void* stream, fem_batch** out);
+fem_status fem_batch_destroy(fem_batch* b);
+
+/*
+ * Adds a case on mesh `m` starting at rest, loaded by a Ricker-wavelet point force
+ *   f(t) = amp (1 - 2 pi^2 f0^2 (t - t0)^2) exp(-pi^2 f0^2 (t - t0)^2) * dir   at node src_node,
+ * evaluated at t = it * dt (the paper's runs use random impulses at surface points, Section 3.1).
+ * Cases on the same mesh are solved together as one multi-RHS system (Section 3.2, Eq. eqmebefem), in
+ * groups of at most 32.  Must be called before the first fem_step.  case_id receives the case index.
+ */
+fem_status fem_case_add(fem_batch* b, fem_mesh* m, int32_t src_node, const double dir[3], double f0,
+                        double t0, double amp, int* case_id);
+
+/*
+ * Advances every case by n_steps time steps.  One step of a case (Section 3.1 and Algorithm 3's
+ * per-case work on one device): Adams-Bashforth guess, data-driven correction (FEM_PRED_DD), Newmark
+ * right-hand side b = f - K u + C v + M (a + 4/dt v), certified solve of A du = b, then
+ * u += du, v = 2/dt du - v, a = 4/dt^2 du - 4/dt v_prev - a, and the snapshot push.
+ *   iters_out   optional host [n_cases] int: CG iterations of each case summed over the n_steps.
+ *   relres_out  optional host [n_cases] double: largest certified residual of each case over the steps.
+ * Returns the worst per-step status (FEM_ERR_NOT_CONVERGED, FEM_ERR_BREAKDOWN) or FEM_OK.
+ */
+fem_status fem_step(fem_batch* b, int n_steps, int* iters_out, double* relres_out);
+
+/*
+ * Refreshes the predictor of case `case_id` from its stored snapshots: recomputes the per-region Gram
+ * matrices of the stored corrections from scratch (Section 3.2: the orthogonal decomposition of the
+ * stored inputs X), replacing the incrementally updated ones.
+ */
+fem_status predictor_fit(fem_batch* b, int case_id);
+
+/*
+ * Writes the initial guess the predictor gives for the next step of case `case_id` (the increment
+ * u_bar^{it+1} - u^it: Adams-Bashforth plus, with FEM_PRED_DD, the regional correction) into
+ * x_guess_dev [n_nodes][3] device doubles.  Does not change the batch state.
+ */
+fem_status predictor_predict(fem_batch* b, int case_id, double* x_guess_dev);
+
+/* Copies field `what` (FEM_FIELD_*) of case `case_id`, [n_nodes][3] doubles, to `dst` (device memory if
+ * on_device != 0, else host memory; a host copy synchronises the batch stream). */
+fem_status fem_case_get(fem_batch* b, int case_id, int what, double* dst, int on_device);
+
+/*
+ * Replaces, for the next fem_step only, the Ricker point force of every case by the force vectors in
+ * loads [n_cases][3] (host, FP64; the load at each case's source node, i.e. the case's f^it of Section
+ * 2.1, Eq. 1).  The copy to the device is ordered on the batch stream.
+ */
+fem_status fem_batch_set_loads(fem_batch* b, const double* loads);
+
+/* Copies field `what` (FEM_FIELD_*) of every case to dst [n_cases][n_nodes][3] (device memory if
+ * on_device != 0, else host memory; a host copy synchronises the batch stream). */
+fem_status fem_batch_get_field(fem_batch* b, int what, double* dst, int on_device);
+
+/* Device-time profile of fem_step, measured with CUDA events on the batch stream. */
+typedef struct {
+  int steps;                         /* steps profiled */
+  long long kernel_launches;         /* kernels the library launched */
+  long long ebe32_launches;          /* FP32 EBE products (inner CG of FEM_FP32_INNER) */
+  double ebe32_ms;
+  long long ebe64_launches;          /* FP64 EBE products (FP64 CG, outer residuals, right-hand sides) */
+  double ebe64_ms;
+  long long cg_vec_launches;         /* CG direction + update kernels */
+  double cg_vec_ms;
+  double predict_ms, rhs_ms, solve_ms, update_ms;  /* phases of fem_step, summed over steps */
+} fem_profile;
+
+/* enable = 1: reset and start profiling; 0: stop; -1: leave as is.  out (nullable) receives the totals
+ * accumulated so far. */
+fem_status fem_batch_profile(fem_batch* b, int enable, fem_profile* out);
+
+/* Number of completed steps of the batch. */
+fem_status fem_batch_steps(const fem_batch* b, int* steps_out);
+
+/* Message of the last error on this thread ("" if none). */
+const char* fem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEM_H_ */

@@ -1,0 +1,962 @@
+// libfem C-ABI: host runtime around the kernels -- mesh setup, the PCG drivers (FP64 and FP32-inner /
+// FP64-refined), and the batched time stepping of many cases (Section 3.1 time loop with the predictor
+// of Section 3.2 and the solver of Algorithm 1; cases on one mesh form one multi-RHS system, Eq. eqmebefem).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fem_internal.cuh"
+
+using namespace fem;
+
+
+static thread_local std::string g_err;
+
+static fem_status fail(fem_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CU(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(FEM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CHK(call)                    \
+  do {                               \
+    fem_status st_ = (call);         \
+    if (st_ != FEM_OK) return st_;   \
+  } while (0)
+
+template <typename T>
+static fem_status dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(FEM_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  return FEM_OK;
+}
+
+template <typename T>
+static void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+static bool pow2_rhs(int r) { return r == 1 || r == 2 || r == 4 || r == 8 || r == 16 || r == 32; }
+
+static int next_pow2(int r) {
+  int p = 1;
+  while (p < r) p <<= 1;
+  return p;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Event-based device-time profiler (CUDA events on the working stream, resolved at sync points).
+// ------------------------------------------------------------------------------------------------------
+enum ProfClass { P_EBE32 = 0, P_EBE64, P_VEC, P_PREDICT, P_RHS, P_SOLVE, P_UPDATE, P_NCLASS };
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  struct Pair {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pair> pend;
+  double ms[P_NCLASS] = {};
+  long long n[P_NCLASS] = {};
+  long long launches = 0;
+  int steps = 0;
+  ~Prof() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+  void reset() {
+    for (int i = 0; i < P_NCLASS; ++i) {
+      ms[i] = 0.0;
+      n[i] = 0;
+    }
+    launches = 0;
+    steps = 0;
+  }
+  cudaEvent_t get() {
+    if (next == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[next++];
+  }
+  int begin(int cls, cudaStream_t s) {
+    if (!on) return -1;
+    Pair p{cls, get(), get()};
+    cudaEventRecord(p.a, s);
+    pend.push_back(p);
+    return (int)pend.size() - 1;
+  }
+  void end(int idx, cudaStream_t s) {
+    if (idx >= 0) cudaEventRecord(pend[idx].b, s);
+  }
+  void resolve() {  // call after the stream has been synchronised
+    for (auto& p : pend) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+        ms[p.cls] += t;
+        n[p.cls] += 1;
+      }
+    }
+    cudaGetLastError();
+    pend.clear();
+    next = 0;
+  }
+};
+
+// ------------------------------------------------------------------------------------------------------
+// PCG workspace (scratch vectors, per-case scalars, reduction buffers) for one mesh and case count.
+// ------------------------------------------------------------------------------------------------------
+struct Workspace {
+  int rpad = 0;
+  int64_t n = 0;  // N * 3 * rpad
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  float *r32 = nullptr, *x32 = nullptr, *rr32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  CgCase* sc = nullptr;
+  CgCase* outer = nullptr;
+  double* partial = nullptr;
+  unsigned* counter = nullptr;
+  double* out = nullptr;
+  int* n_active = nullptr;
+  int* h_active = nullptr;   // pinned
+  CgCase* h_sc = nullptr;    // pinned
+  Prof* prof = nullptr;      // not owned; null = not profiled
+  void count(int k = 1) {
+    if (prof && prof->on) prof->launches += k;
+  }
+  int pbeg(int cls, cudaStream_t s) { return prof ? prof->begin(cls, s) : -1; }
+  void pend(int idx, cudaStream_t s) {
+    if (prof) prof->end(idx, s);
+  }
+  void resolve() {
+    if (prof && prof->on) prof->resolve();
+  }
+  ~Workspace() {
+    dfree(r); dfree(z); dfree(p); dfree(q);
+    dfree(r32); dfree(x32); dfree(rr32); dfree(z32); dfree(p32); dfree(q32);
+    dfree(sc); dfree(outer); dfree(partial); dfree(counter); dfree(out); dfree(n_active);
+    if (h_active) cudaFreeHost(h_active);
+    if (h_sc) cudaFreeHost(h_sc);
+  }
+  Reducer red() const { return Reducer{partial, counter, out}; }
+};
+
+static fem_status ws_create(int64_t N, int rpad, Workspace** out) {
+  Workspace* w = new Workspace();
+  w->rpad = rpad;
+  w->n = N * 3 * rpad;
+  fem_status st = FEM_OK;
+  if (st == FEM_OK) st = dalloc(&w->r, w->n);
+  if (st == FEM_OK) st = dalloc(&w->z, w->n);
+  if (st == FEM_OK) st = dalloc(&w->p, w->n);
+  if (st == FEM_OK) st = dalloc(&w->q, w->n);
+  if (st == FEM_OK) st = dalloc(&w->r32, w->n);
+  if (st == FEM_OK) st = dalloc(&w->x32, w->n);
+  if (st == FEM_OK) st = dalloc(&w->rr32, w->n);
+  if (st == FEM_OK) st = dalloc(&w->z32, w->n);
+  if (st == FEM_OK) st = dalloc(&w->p32, w->n);
+  if (st == FEM_OK) st = dalloc(&w->q32, w->n);
+  if (st == FEM_OK) st = dalloc(&w->sc, kMaxRpad);
+  if (st == FEM_OK) st = dalloc(&w->outer, kMaxRpad);
+  if (st == FEM_OK) st = dalloc(&w->partial, (size_t)kMaxRedBlocks * 3 * kMaxRpad);
+  if (st == FEM_OK) st = dalloc(&w->counter, 1);
+  if (st == FEM_OK) st = dalloc(&w->out, 3 * kMaxRpad);
+  if (st == FEM_OK) st = dalloc(&w->n_active, 1);
+  if (st != FEM_OK) {
+    delete w;
+    return st;
+  }
+  if (cudaMallocHost((void**)&w->h_active, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost((void**)&w->h_sc, sizeof(CgCase) * kMaxRpad) != cudaSuccess) {
+    cudaGetLastError();
+    delete w;
+    return fail(FEM_ERR_OOM, "cudaMallocHost failed");
+  }
+  cudaMemset(w->counter, 0, sizeof(unsigned));
+  cudaMemset(w->p, 0, w->n * sizeof(double));
+  cudaMemset(w->p32, 0, w->n * sizeof(float));
+  cudaMemset(w->sc, 0, sizeof(CgCase) * kMaxRpad);
+  cudaMemset(w->outer, 0, sizeof(CgCase) * kMaxRpad);
+  *out = w;
+  return FEM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------------
+struct fem_mesh {
+  int64_t N = 0, E = 0;
+  fem_time_params tp{};
+  double cM = 0, cK = 0;
+  int device = 0;
+  double* xyz = nullptr;
+  int4* conn = nullptr;
+  int32_t* mat = nullptr;
+  double* lmr = nullptr;
+  double* rec64 = nullptr;
+  float* rec32 = nullptr;
+  double* D = nullptr;
+  double* binv64 = nullptr;
+  float* binv32 = nullptr;
+  uint8_t* fm = nullptr;
+  int n_regions = 0;
+  int32_t* reg_lo = nullptr;
+  int32_t* reg_hi = nullptr;
+  std::vector<Workspace*> ws;
+  MeshView view() const { return MeshView{N, E, conn, rec64, rec32, binv64, binv32, fm}; }
+  ~fem_mesh() {
+    dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(D);
+    dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi);
+    for (auto* w : ws) delete w;
+  }
+  fem_status workspace(int rpad, Workspace** out) {
+    for (auto* w : ws)
+      if (w->rpad == rpad) {
+        *out = w;
+        return FEM_OK;
+      }
+    Workspace* w = nullptr;
+    CHK(ws_create(N, rpad, &w));
+    ws.push_back(w);
+    *out = w;
+    return FEM_OK;
+  }
+};
+
+// ------------------------------------------------------------------------------------------------------
+// PCG drivers.
+// ------------------------------------------------------------------------------------------------------
+template <typename T>
+static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T* z, T* p, T* q, CgCase* sc,
+                           bool zero_guess, bool true_check, double tol, int maxit, const CgCase* gate,
+                           int check_every, cudaStream_t s) {
+  const MeshView mv = m->view();
+  const int rpad = w->rpad;
+  const Reducer red = w->red();
+  const int ebe_cls = sizeof(T) == 4 ? P_EBE32 : P_EBE64;
+  CU(launch_norm_b_gated<T>(mv, rpad, b, red, sc, gate, s));
+  w->count();
+  if (zero_guess) {
+    CU(cudaMemsetAsync(x, 0, sizeof(T) * (size_t)w->n, s));
+    CU(launch_resid<T>(mv, rpad, b, nullptr, x, r, z, 1, red, sc, w->n_active, tol, maxit, s));
+    w->count();
+  } else {
+    // the guess is zeroed on Dirichlet DOFs (and for b = 0) before its residual is formed
+    CU(launch_zero_b0_t<T>(mv, rpad, x, sc, s));
+    int pi = w->pbeg(ebe_cls, s);
+    CU(launch_ebe<T>(mv, rpad, x, nullptr, q, m->cM, m->cK, nullptr, nullptr, nullptr, s));
+    w->pend(pi, s);
+    CU(launch_resid<T>(mv, rpad, b, q, x, r, z, 1, red, sc, w->n_active, tol, maxit, s));
+    w->count(3);
+  }
+  if (check_every < 1) check_every = 1;
+  int issued = 0, rechecks = 0;
+  for (;;) {
+    for (int k = 0; k < check_every; ++k) {
+      int p0 = w->pbeg(P_VEC, s);
+      CU(launch_dir_gated<T>(mv, rpad, z, p, sc, w->n_active, s));
+      w->pend(p0, s);
+      int p1 = w->pbeg(ebe_cls, s);
+      CU(launch_ebe_gated<T>(mv, rpad, p, nullptr, q, m->cM, m->cK, &red, sc, nullptr, w->n_active, s));
+      w->pend(p1, s);
+      int p2 = w->pbeg(P_VEC, s);
+      CU(launch_update<T>(mv, rpad, p, q, x, r, z, red, sc, w->n_active, tol, maxit, s));
+      w->pend(p2, s);
+      w->count(3);
+    }
+    issued += check_every;
+    CU(cudaMemcpyAsync(w->h_active, w->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    w->resolve();
+    if (*w->h_active == 0) {
+      if (!true_check) break;
+      if (++rechecks > 32) break;
+      // Algorithm 1 stops on the recursive residual; confirm with the true one and resume if needed.
+      int pi = w->pbeg(ebe_cls, s);
+      CU(launch_ebe<T>(mv, rpad, x, nullptr, q, m->cM, m->cK, nullptr, nullptr, nullptr, s));
+      w->pend(pi, s);
+      CU(launch_resid<T>(mv, rpad, b, q, x, r, z, 0, red, sc, w->n_active, tol, maxit, s));
+      w->count(2);
+      CU(cudaMemcpyAsync(w->h_active, w->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      w->resolve();
+      if (*w->h_active == 0) break;
+    }
+    if (issued > maxit + 64 * check_every) break;
+  }
+  return FEM_OK;
+}
+
+// FP32-inner / FP64-outer iterative refinement:  r64 = b - A64 x;  A32 d = r64 (inner PCG);  x += d.
+static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double* x, const fem_opts& o,
+                              cudaStream_t s) {
+  const MeshView mv = m->view();
+  const int rpad = w->rpad;
+  const Reducer red = w->red();
+  CU(launch_norm_b_gated<double>(mv, rpad, b, red, w->outer, nullptr, s));
+  CU(launch_zero_b0_t<double>(mv, rpad, x, w->outer, s));
+  w->count(2);
+  const int kMaxOuter = 40;
+  for (int outer_it = 0; outer_it <= kMaxOuter; ++outer_it) {
+    int pi = w->pbeg(P_EBE64, s);
+    CU(launch_ebe<double>(mv, rpad, x, nullptr, w->q, m->cM, m->cK, nullptr, nullptr, nullptr, s));
+    w->pend(pi, s);
+    CU(launch_outer_resid(mv, rpad, b, w->q, w->r32, red, w->outer, w->n_active, o.tol, s));
+    w->count(2);
+    CU(cudaMemcpyAsync(w->h_active, w->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(w->h_sc, w->outer, sizeof(CgCase) * rpad, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (*w->h_active == 0) break;
+    int used = 0;
+    if (outer_it == kMaxOuter) used = o.maxit;   // refinement stalled: report the active cases
+    for (int c = 0; c < rpad; ++c) used = std::max(used, w->h_sc[c].iters);
+    if (used >= o.maxit) {
+      for (int c = 0; c < rpad; ++c) w->h_sc[c].status = w->h_sc[c].active ? FEM_ERR_NOT_CONVERGED : w->h_sc[c].status;
+      CU(cudaMemcpyAsync(w->outer, w->h_sc, sizeof(CgCase) * rpad, cudaMemcpyHostToDevice, s));
+      break;
+    }
+    CHK(pcg_core<float>(m, w, w->r32, w->x32, w->rr32, w->z32, w->p32, w->q32, w->sc, true, false, o.inner_tol,
+                        o.maxit - used, w->outer, o.check_every, s));
+    CU(launch_refine_counts(mv, rpad, x, w->x32, w->outer, w->sc, s));
+    w->count();
+  }
+  w->resolve();
+  return FEM_OK;
+}
+
+static fem_status solve_any(fem_mesh* m, Workspace* w, const double* b, double* x, const fem_opts& o,
+                            cudaStream_t s, CgCase** result_dev) {
+  if (o.precision == FEM_FP64) {
+    CHK(pcg_core<double>(m, w, b, x, w->r, w->z, w->p, w->q, w->sc, false, true, o.tol, o.maxit, nullptr,
+                         o.check_every, s));
+    *result_dev = w->sc;
+  } else {
+    CHK(solve_mixed(m, w, b, x, o, s));
+    *result_dev = w->outer;
+  }
+  return FEM_OK;
+}
+
+static fem_status check_opts(const fem_opts* o) {
+  if (!o) return fail(FEM_ERR_ARG, "opts is null");
+  if (o->precision != FEM_FP64 && o->precision != FEM_FP32_INNER) return fail(FEM_ERR_ARG, "unknown precision");
+  if (!(o->tol > 0.0) || o->maxit < 1) return fail(FEM_ERR_ARG, "tol must be > 0 and maxit >= 1");
+  if (o->precision == FEM_FP32_INNER && !(o->inner_tol > 0.0 && o->inner_tol < 1.0))
+    return fail(FEM_ERR_ARG, "inner_tol must be in (0, 1)");
+  if (o->predictor != FEM_PRED_AB4 && o->predictor != FEM_PRED_DD) return fail(FEM_ERR_ARG, "unknown predictor");
+  if (o->s_max < 1 || o->s_max > kMaxSlots - 1) return fail(FEM_ERR_ARG, "s_max must be in [1, 32]");
+  return FEM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Batch of cases.
+// ------------------------------------------------------------------------------------------------------
+struct Group {
+  fem_mesh* mesh = nullptr;
+  int rpad = 0;
+  std::vector<int> cases;
+  std::vector<RickerSrc> hsrc;
+  int64_t n = 0;
+  double *u = nullptr, *a = nullptr, *vh[4] = {nullptr, nullptr, nullptr, nullptr};
+  double *b = nullptr, *x = nullptr, *du_ab = nullptr, *m_in = nullptr, *k_in = nullptr, *guess = nullptr;
+  void* ring = nullptr;
+  int n_slots = 0;
+  int n_regions = 0;            // regions the Gram buffers were sized for
+  double* gram = nullptr;
+  double* wcoef = nullptr;
+  int* slot_lists = nullptr;    // device [2][kMaxSlots]
+  int* h_slots = nullptr;       // pinned [2][kMaxSlots]
+  RickerSrc* src = nullptr;
+  double* ext = nullptr;        // device [rpad][3]: external loads for the next step
+  bool use_ext = false;
+  Workspace* ws = nullptr;
+  int steps = 0;
+  std::vector<int> iters_acc;
+  std::vector<double> relres_max;
+  ~Group() {
+    dfree(u); dfree(a);
+    for (auto& v : vh) dfree(v);
+    dfree(b); dfree(x); dfree(du_ab); dfree(m_in); dfree(k_in); dfree(guess);
+    if (ring) cudaFree(ring);
+    dfree(gram); dfree(wcoef); dfree(slot_lists); dfree(src); dfree(ext);
+    if (h_slots) cudaFreeHost(h_slots);
+    delete ws;
+  }
+};
+
+struct fem_batch {
+  fem_opts opts{};
+  Prof prof;
+  cudaStream_t s = nullptr;
+  std::vector<Group*> groups;
+  std::vector<std::pair<int, int>> loc;   // case -> (group, lane)
+  bool started = false;
+  int steps = 0;
+  ~fem_batch() {
+    for (auto* g : groups) delete g;
+  }
+};
+
+static fem_status group_alloc(fem_batch* bt, Group* g) {
+  fem_mesh* m = g->mesh;
+  g->rpad = next_pow2((int)g->cases.size());
+  g->n = m->N * 3 * g->rpad;
+  const size_t n = (size_t)g->n;
+  CHK(dalloc(&g->u, n));
+  CHK(dalloc(&g->a, n));
+  for (auto& v : g->vh) CHK(dalloc(&v, n));
+  CHK(dalloc(&g->b, n));
+  CHK(dalloc(&g->x, n));
+  CHK(dalloc(&g->du_ab, n));
+  CHK(dalloc(&g->m_in, n));
+  CHK(dalloc(&g->k_in, n));
+  CHK(dalloc(&g->guess, n));
+  cudaStream_t s = bt->s;
+  CU(cudaMemsetAsync(g->u, 0, n * 8, s));
+  CU(cudaMemsetAsync(g->a, 0, n * 8, s));
+  for (auto& v : g->vh) CU(cudaMemsetAsync(v, 0, n * 8, s));
+  CU(cudaMemsetAsync(g->x, 0, n * 8, s));
+  CU(cudaMemsetAsync(g->guess, 0, n * 8, s));
+  CU(cudaMemsetAsync(g->b, 0, n * 8, s));
+  if (bt->opts.predictor == FEM_PRED_DD) {
+    g->n_slots = bt->opts.s_max + 1;
+    const size_t esz = bt->opts.snapshot_fp32 ? 4 : 8;
+    cudaError_t e = cudaMalloc(&g->ring, esz * n * g->n_slots);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g->ring = nullptr;
+      return fail(FEM_ERR_OOM, "snapshot ring allocation failed");
+    }
+    CU(cudaMemsetAsync(g->ring, 0, esz * n * g->n_slots, s));
+    g->n_regions = m->n_regions;
+    const int R = std::max(1, m->n_regions);
+    CHK(dalloc(&g->gram, (size_t)R * g->rpad * kMaxSlots * kMaxSlots));
+    CHK(dalloc(&g->wcoef, (size_t)R * g->rpad * kMaxSlots));
+    CU(cudaMemsetAsync(g->gram, 0, sizeof(double) * (size_t)R * g->rpad * kMaxSlots * kMaxSlots, s));
+  }
+  CHK(dalloc(&g->slot_lists, 2 * kMaxSlots));
+  if (cudaMallocHost((void**)&g->h_slots, sizeof(int) * 2 * kMaxSlots) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FEM_ERR_OOM, "cudaMallocHost failed");
+  }
+  g->hsrc.resize(g->rpad);
+  for (int l = (int)g->cases.size(); l < g->rpad; ++l) g->hsrc[l] = RickerSrc{-1, {0, 0, 0}, 1.0, 0.0, 0.0};
+  CHK(dalloc(&g->src, g->rpad));
+  CHK(dalloc(&g->ext, 3 * g->rpad));
+  CU(cudaMemsetAsync(g->ext, 0, sizeof(double) * 3 * g->rpad, s));
+  CU(cudaMemcpyAsync(g->src, g->hsrc.data(), sizeof(RickerSrc) * g->rpad, cudaMemcpyHostToDevice, s));
+  CHK(ws_create(m->N, g->rpad, &g->ws));
+  g->ws->prof = &bt->prof;
+  g->iters_acc.assign(g->rpad, 0);
+  g->relres_max.assign(g->rpad, 0.0);
+  return FEM_OK;
+}
+
+static PredView pred_view(const fem_batch* bt, const Group* g) {
+  PredView p;
+  p.n_regions = g->n_regions;
+  p.reg_lo = g->mesh->reg_lo;
+  p.reg_hi = g->mesh->reg_hi;
+  p.rpad = g->rpad;
+  p.n_slots = g->n_slots;
+  p.slot_stride = g->n;
+  p.ring = g->ring;
+  p.fp32 = bt->opts.snapshot_fp32;
+  p.gram = g->gram;
+  p.w = g->wcoef;
+  return p;
+}
+
+static int slot_of(const Group* g, int j) { return (j - 1) % g->n_slots; }  // correction e^j, j >= 1
+
+// Initial guess of the increment for step it = g->steps + 1 into `out`: AB4 (+ regional correction).
+static fem_status group_predict(fem_batch* bt, Group* g, double* out) {
+  const int it = g->steps + 1;
+  const double dt = g->mesh->tp.dt;
+  auto vslot = [&](int j) { return g->vh[((j % 4) + 4) % 4]; };
+  cudaStream_t s = bt->s;
+  CU(launch_ab4(g->n, dt, vslot(it - 4), vslot(it - 3), vslot(it - 2), vslot(it - 1), g->du_ab, s));
+  g->ws->count();
+  CU(cudaMemcpyAsync(out, g->du_ab, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+  if (bt->opts.predictor != FEM_PRED_DD || g->n_regions == 0) return FEM_OK;
+  if (g->mesh->n_regions != g->n_regions) return fail(FEM_ERR_STATE, "mesh regions changed after the batch started");
+  const int n_e = std::min(it - 1, g->n_slots);
+  const int n_pairs = std::min(bt->opts.s_max, n_e - 1);
+  if (n_pairs <= 0) return FEM_OK;
+  // X: e^{it-1-n_pairs} .. e^{it-2};  Y: e^{it-n_pairs} .. e^{it-1};  query: e^{it-1}
+  for (int a = 0; a < n_pairs; ++a) {
+    g->h_slots[a] = slot_of(g, it - 1 - n_pairs + a);
+    g->h_slots[kMaxSlots + a] = slot_of(g, it - n_pairs + a);
+  }
+  CU(cudaMemcpyAsync(g->slot_lists, g->h_slots, sizeof(int) * 2 * kMaxSlots, cudaMemcpyHostToDevice, s));
+  const PredView pv = pred_view(bt, g);
+  CU(launch_pred_solve(pv, g->slot_lists, n_pairs, slot_of(g, it - 1), bt->opts.tau, s));
+  CU(launch_pred_combine(pv, g->slot_lists + kMaxSlots, n_pairs, out, s));
+  g->ws->count(2);
+  // the pinned slot list is reused next step: order the host write after this step's copy
+  CU(cudaStreamSynchronize(s));
+  return FEM_OK;
+}
+
+static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
+  fem_mesh* m = g->mesh;
+  const MeshView mv = m->view();
+  cudaStream_t s = bt->s;
+  const int it = g->steps + 1;
+  const double dt = m->tp.dt;
+  auto vslot = [&](int j) { return g->vh[((j % 4) + 4) % 4]; };
+  Workspace* w = g->ws;
+  // 1. initial guess (Section 3.2)
+  int ph = w->pbeg(P_PREDICT, s);
+  CHK(group_predict(bt, g, g->guess));
+  w->pend(ph, s);
+  // 2. Newmark right-hand side (Section 3.1, Eq. GE:DIS, increment form)
+  ph = w->pbeg(P_RHS, s);
+  CU(launch_rhs_prep(g->n, dt, m->tp.a0, m->tp.a1, g->u, vslot(it - 1), g->a, g->m_in, g->k_in, s));
+  int pe = w->pbeg(P_EBE64, s);
+  CU(launch_ebe<double>(mv, g->rpad, g->m_in, g->k_in, g->b, 1.0, 1.0, nullptr, nullptr, nullptr, s));
+  w->pend(pe, s);
+  CU(launch_rhs_finish(mv, g->rpad, g->b, g->src, g->use_ext ? g->ext : nullptr, it * dt, s));
+  g->use_ext = false;
+  w->pend(ph, s);
+  w->count(3);
+  // 3. certified solve of A du = b from the guess (Algorithm 1)
+  ph = w->pbeg(P_SOLVE, s);
+  CU(cudaMemcpyAsync(g->x, g->guess, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+  CgCase* res = nullptr;
+  CHK(solve_any(m, g->ws, g->b, g->x, bt->opts, s, &res));
+  w->pend(ph, s);
+  CU(cudaMemcpyAsync(g->ws->h_sc, res, sizeof(CgCase) * g->rpad, cudaMemcpyDeviceToHost, s));
+  ph = w->pbeg(P_UPDATE, s);
+  // 4. Newmark update and snapshot push (Section 3.1, Eq. timestep)
+  void* e_push = nullptr;
+  const bool dd = bt->opts.predictor == FEM_PRED_DD && g->n_regions > 0;
+  if (dd) {
+    const size_t esz = bt->opts.snapshot_fp32 ? 4 : 8;
+    e_push = (char*)g->ring + esz * (size_t)g->n * slot_of(g, it);
+  }
+  CU(launch_newmark_update(g->n, dt, g->x, g->du_ab, g->u, vslot(it - 1), g->a, vslot(it), e_push,
+                           bt->opts.snapshot_fp32, s));
+  w->count();
+  if (dd) {
+    unsigned mask = 0;
+    const int n_e = std::min(it, g->n_slots);
+    for (int j = it - n_e + 1; j <= it; ++j) mask |= 1u << slot_of(g, j);
+    CU(launch_pred_dots(pred_view(bt, g), slot_of(g, it), mask, s));
+    w->count();
+  }
+  w->pend(ph, s);
+  CU(cudaStreamSynchronize(s));
+  w->resolve();
+  for (int l = 0; l < (int)g->cases.size(); ++l) {
+    const CgCase& c = g->ws->h_sc[l];
+    g->iters_acc[l] += c.iters;
+    g->relres_max[l] = std::max(g->relres_max[l], c.relres);
+    if (c.status != FEM_OK && (*worst == FEM_OK || c.status < *worst)) *worst = c.status;
+  }
+  g->steps = it;
+  return FEM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// C-ABI
+// ------------------------------------------------------------------------------------------------------
+extern "C" {
+
+const char* fem_last_error(void) { return g_err.c_str(); }
+
+void fem_opts_default(fem_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = FEM_FP64;
+  o->predictor = FEM_PRED_AB4;
+  o->tol = 1e-8;
+  o->maxit = 5000;
+  o->s_max = 32;
+  o->inner_tol = 1e-5;
+  o->tau = 1e-6;
+  o->snapshot_fp32 = 1;
+  o->check_every = 8;
+}
+
+fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
+                           const int32_t* mat_id, int n_mat, const double* lam_mu_rho, const uint8_t* fixed_dof,
+                           const fem_time_params* tp, void* stream, fem_mesh** out) {
+  g_err.clear();
+  if (!out) return fail(FEM_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!xyz || !conn || !mat_id || !lam_mu_rho || !fixed_dof || !tp) return fail(FEM_ERR_ARG, "null input pointer");
+  if (n_nodes < 4 || n_elems < 1 || n_mat < 1) return fail(FEM_ERR_ARG, "empty mesh");
+  if (n_nodes > INT32_MAX) return fail(FEM_ERR_ARG, "node ids must fit int32");
+  if (tp->beta != 0.25 || tp->gamma != 0.5) return fail(FEM_ERR_ARG, "only Newmark beta=1/4, gamma=1/2 is supported");
+  if (!(tp->dt > 0.0)) return fail(FEM_ERR_ARG, "dt must be > 0");
+  for (int i = 0; i < n_mat; ++i)
+    if (!(lam_mu_rho[3 * i + 1] > 0.0) || !(lam_mu_rho[3 * i + 2] > 0.0) ||
+        !(lam_mu_rho[3 * i] + 2.0 / 3.0 * lam_mu_rho[3 * i + 1] > 0.0))
+      return fail(FEM_ERR_ARG, "material parameters must give a positive-definite elasticity tensor");
+  cudaStream_t s = (cudaStream_t)stream;
+  fem_mesh* m = new fem_mesh();
+  cudaGetDevice(&m->device);
+  m->N = n_nodes;
+  m->E = n_elems;
+  m->tp = *tp;
+  m->cM = 4.0 / (tp->dt * tp->dt) + 2.0 * tp->a0 / tp->dt;
+  m->cK = 1.0 + 2.0 * tp->a1 / tp->dt;
+  std::vector<uint8_t> fm(n_nodes);
+  for (int64_t n = 0; n < n_nodes; ++n)
+    fm[n] = (uint8_t)((fixed_dof[3 * n] ? 0 : 1) | (fixed_dof[3 * n + 1] ? 0 : 2) | (fixed_dof[3 * n + 2] ? 0 : 4));
+  fem_status st = FEM_OK;
+  auto bail = [&](fem_status e) {
+    delete m;
+    return e;
+  };
+  if ((st = dalloc(&m->xyz, 3 * n_nodes)) != FEM_OK) return bail(st);
+  if ((st = dalloc(&m->conn, n_elems)) != FEM_OK) return bail(st);
+  if ((st = dalloc(&m->mat, n_elems)) != FEM_OK) return bail(st);
+  if ((st = dalloc(&m->lmr, 3 * n_mat)) != FEM_OK) return bail(st);
+  if ((st = dalloc(&m->rec64, kRec * n_elems)) != FEM_OK) return bail(st);
+  if ((st = dalloc(&m->rec32, kRec * n_elems)) != FEM_OK) return bail(st);
+  if ((st = dalloc(&m->D, 6 * n_nodes)) != FEM_OK) return bail(st);
+  if ((st = dalloc(&m->binv64, 6 * n_nodes)) != FEM_OK) return bail(st);
+  if ((st = dalloc(&m->binv32, 6 * n_nodes)) != FEM_OK) return bail(st);
+  if ((st = dalloc(&m->fm, n_nodes)) != FEM_OK) return bail(st);
+  int* d_err = nullptr;
+  if ((st = dalloc(&d_err, 1)) != FEM_OK) return bail(st);
+  cudaError_t e = cudaSuccess;
+  auto cu = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  cu(cudaMemcpyAsync(m->xyz, xyz, sizeof(double) * 3 * n_nodes, cudaMemcpyHostToDevice, s));
+  cu(cudaMemcpyAsync(m->conn, conn, sizeof(int4) * n_elems, cudaMemcpyHostToDevice, s));
+  cu(cudaMemcpyAsync(m->mat, mat_id, sizeof(int32_t) * n_elems, cudaMemcpyHostToDevice, s));
+  cu(cudaMemcpyAsync(m->lmr, lam_mu_rho, sizeof(double) * 3 * n_mat, cudaMemcpyHostToDevice, s));
+  cu(cudaMemcpyAsync(m->fm, fm.data(), n_nodes, cudaMemcpyHostToDevice, s));
+  cu(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  cu(cudaMemsetAsync(m->D, 0, sizeof(double) * 6 * n_nodes, s));
+  cu(launch_elem_setup(n_elems, n_nodes, m->xyz, m->conn, m->mat, n_mat, m->lmr, m->rec64, m->rec32, d_err, s));
+  cu(launch_diag_blocks(m->view(), m->cM, m->cK, m->D, s));
+  cu(launch_binv(n_nodes, m->D, m->fm, m->binv64, m->binv32, d_err, s));
+  int h_err = 0;
+  cu(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  cu(cudaStreamSynchronize(s));
+  cudaFree(d_err);
+  if (e != cudaSuccess) {
+    delete m;
+    return fail(FEM_ERR_CUDA, std::string("mesh setup: ") + cudaGetErrorString(e));
+  }
+  if (h_err & 1) return bail(fail(FEM_ERR_ARG, "connectivity or material id out of range"));
+  if (h_err & 2) return bail(fail(FEM_ERR_ARG, "element with non-positive volume (conn must be positively oriented)"));
+  if (h_err & 4) return bail(fail(FEM_ERR_ARG, "singular node diagonal block (node with no element?)"));
+  *out = m;
+  return FEM_OK;
+}
+
+fem_status fem_mesh_destroy(fem_mesh* m) {
+  if (!m) return fail(FEM_ERR_ARG, "mesh is null");
+  cudaDeviceSynchronize();
+  delete m;
+  return FEM_OK;
+}
+
+fem_status fem_mesh_set_regions(fem_mesh* m, const int32_t* region_of_node) {
+  g_err.clear();
+  if (!m || !region_of_node) return fail(FEM_ERR_ARG, "null argument");
+  int R = 0;
+  for (int64_t n = 0; n < m->N; ++n) {
+    if (region_of_node[n] < -1) return fail(FEM_ERR_ARG, "region id < -1");
+    R = std::max(R, region_of_node[n] + 1);
+  }
+  std::vector<int32_t> lo(R, INT32_MAX), hi(R, -1);
+  for (int64_t n = 0; n < m->N; ++n) {
+    const int r = region_of_node[n];
+    if (r < 0) continue;
+    lo[r] = std::min<int32_t>(lo[r], (int32_t)n);
+    hi[r] = std::max<int32_t>(hi[r], (int32_t)n + 1);
+  }
+  for (int r = 0; r < R; ++r) {
+    if (hi[r] < 0) return fail(FEM_ERR_ARG, "empty region id " + std::to_string(r));
+    for (int64_t n = lo[r]; n < hi[r]; ++n)
+      if (region_of_node[n] != r && region_of_node[n] != -1)
+        return fail(FEM_ERR_ARG, "region " + std::to_string(r) + " is not a contiguous node range");
+  }
+  dfree(m->reg_lo);
+  dfree(m->reg_hi);
+  m->n_regions = 0;
+  CHK(dalloc(&m->reg_lo, R));
+  CHK(dalloc(&m->reg_hi, R));
+  CU(cudaMemcpy(m->reg_lo, lo.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(m->reg_hi, hi.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice));
+  m->n_regions = R;
+  return FEM_OK;
+}
+
+fem_status fem_ebe_apply(fem_mesh* m, int precision, const void* p_dev, void* q_dev, int n_rhs, double alpha_M,
+                         double alpha_K, double* ptq_dev, void* stream) {
+  g_err.clear();
+  if (!m || !p_dev || !q_dev) return fail(FEM_ERR_ARG, "null argument");
+  if (!pow2_rhs(n_rhs)) return fail(FEM_ERR_ARG, "n_rhs must be 1, 2, 4, 8, 16 or 32");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = nullptr;
+  CHK(m->workspace(n_rhs, &w));
+  const Reducer red = w->red();
+  const MeshView mv = m->view();
+  if (precision == FEM_FP64) {
+    CU(launch_ebe<double>(mv, n_rhs, (const double*)p_dev, nullptr, (double*)q_dev, alpha_M, alpha_K,
+                          ptq_dev ? &red : nullptr, nullptr, ptq_dev, s));
+    CU(launch_mask<double>(m->N, n_rhs, m->fm, (double*)q_dev, s));
+  } else if (precision == FEM_FP32_INNER) {
+    CU(launch_ebe<float>(mv, n_rhs, (const float*)p_dev, nullptr, (float*)q_dev, alpha_M, alpha_K,
+                         ptq_dev ? &red : nullptr, nullptr, ptq_dev, s));
+    CU(launch_mask<float>(m->N, n_rhs, m->fm, (float*)q_dev, s));
+  } else {
+    return fail(FEM_ERR_ARG, "unknown precision");
+  }
+  return FEM_OK;
+}
+
+fem_status pcg_solve(fem_mesh* m, const double* b_dev, double* x_dev, int n_rhs, const fem_opts* opts, void* stream,
+                     int* iters_out, double* relres_out) {
+  g_err.clear();
+  if (!m || !b_dev || !x_dev) return fail(FEM_ERR_ARG, "null argument");
+  if (!pow2_rhs(n_rhs)) return fail(FEM_ERR_ARG, "n_rhs must be 1, 2, 4, 8, 16 or 32");
+  CHK(check_opts(opts));
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = nullptr;
+  CHK(m->workspace(n_rhs, &w));
+  CgCase* res = nullptr;
+  CHK(solve_any(m, w, b_dev, x_dev, *opts, s, &res));
+  CU(cudaMemcpyAsync(w->h_sc, res, sizeof(CgCase) * n_rhs, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  fem_status worst = FEM_OK;
+  for (int c = 0; c < n_rhs; ++c) {
+    if (iters_out) iters_out[c] = w->h_sc[c].iters;
+    if (relres_out) relres_out[c] = w->h_sc[c].relres;
+    const int st = w->h_sc[c].status;
+    if (st != FEM_OK && (worst == FEM_OK || st < worst)) worst = st;
+  }
+  if (worst != FEM_OK) return fail(worst, "pcg_solve: a case did not converge or broke down");
+  return FEM_OK;
+}
+
+fem_status fem_batch_create(const fem_opts* opts, void* stream, fem_batch** out) {
+  g_err.clear();
+  if (!out) return fail(FEM_ERR_ARG, "out is null");
+  *out = nullptr;
+  CHK(check_opts(opts));
+  fem_batch* b = new fem_batch();
+  b->opts = *opts;
+  if (b->opts.check_every < 1) b->opts.check_every = 1;
+  b->s = (cudaStream_t)stream;
+  *out = b;
+  return FEM_OK;
+}
+
+fem_status fem_batch_destroy(fem_batch* b) {
+  if (!b) return fail(FEM_ERR_ARG, "batch is null");
+  cudaStreamSynchronize(b->s);
+  delete b;
+  return FEM_OK;
+}
+
+fem_status fem_case_add(fem_batch* b, fem_mesh* m, int32_t src_node, const double dir[3], double f0, double t0,
+                        double amp, int* case_id) {
+  g_err.clear();
+  if (!b || !m || !dir) return fail(FEM_ERR_ARG, "null argument");
+  if (b->started) return fail(FEM_ERR_STATE, "cases must be added before the first fem_step");
+  if (src_node < 0 || src_node >= m->N) return fail(FEM_ERR_ARG, "source node out of range");
+  Group* g = nullptr;
+  for (auto* gg : b->groups)
+    if (gg->mesh == m && gg->cases.size() < (size_t)kMaxRpad) g = gg;
+  if (!g) {
+    g = new Group();
+    g->mesh = m;
+    b->groups.push_back(g);
+  }
+  const int id = (int)b->loc.size();
+  g->cases.push_back(id);
+  g->hsrc.push_back(RickerSrc{src_node, {dir[0], dir[1], dir[2]}, f0, t0, amp});
+  b->loc.push_back({(int)(std::find(b->groups.begin(), b->groups.end(), g) - b->groups.begin()),
+                    (int)g->cases.size() - 1});
+  if (case_id) *case_id = id;
+  return FEM_OK;
+}
+
+static fem_status batch_start(fem_batch* b) {
+  if (b->started) return FEM_OK;
+  if (b->loc.empty()) return fail(FEM_ERR_STATE, "batch has no cases");
+  for (auto* g : b->groups) CHK(group_alloc(b, g));
+  CU(cudaStreamSynchronize(b->s));
+  b->started = true;
+  return FEM_OK;
+}
+
+fem_status fem_step(fem_batch* b, int n_steps, int* iters_out, double* relres_out) {
+  g_err.clear();
+  if (!b) return fail(FEM_ERR_ARG, "batch is null");
+  if (n_steps < 0) return fail(FEM_ERR_ARG, "n_steps < 0");
+  CHK(batch_start(b));
+  for (auto* g : b->groups) {
+    std::fill(g->iters_acc.begin(), g->iters_acc.end(), 0);
+    std::fill(g->relres_max.begin(), g->relres_max.end(), 0.0);
+  }
+  fem_status worst = FEM_OK;
+  for (int k = 0; k < n_steps; ++k) {
+    for (auto* g : b->groups) CHK(group_step(b, g, &worst));
+    b->steps += 1;
+    if (b->prof.on) b->prof.steps += 1;
+  }
+  for (size_t c = 0; c < b->loc.size(); ++c) {
+    const Group* g = b->groups[b->loc[c].first];
+    const int l = b->loc[c].second;
+    if (iters_out) iters_out[c] = g->iters_acc[l];
+    if (relres_out) relres_out[c] = g->relres_max[l];
+  }
+  if (worst != FEM_OK) return fail(worst, "fem_step: a case did not converge or broke down");
+  return FEM_OK;
+}
+
+fem_status predictor_fit(fem_batch* b, int case_id) {
+  g_err.clear();
+  if (!b || case_id < 0 || case_id >= (int)b->loc.size()) return fail(FEM_ERR_ARG, "bad case id");
+  CHK(batch_start(b));
+  Group* g = b->groups[b->loc[case_id].first];
+  if (b->opts.predictor != FEM_PRED_DD || g->n_regions == 0) return FEM_OK;
+  const int it = g->steps;
+  const int n_e = std::min(it, g->n_slots);
+  unsigned mask = 0;
+  for (int j = it - n_e + 1; j <= it; ++j) mask |= 1u << slot_of(g, j);
+  for (int j = it - n_e + 1; j <= it; ++j) CU(launch_pred_dots(pred_view(b, g), slot_of(g, j), mask, b->s));
+  CU(cudaStreamSynchronize(b->s));
+  return FEM_OK;
+}
+
+fem_status predictor_predict(fem_batch* b, int case_id, double* x_guess_dev) {
+  g_err.clear();
+  if (!b || !x_guess_dev || case_id < 0 || case_id >= (int)b->loc.size()) return fail(FEM_ERR_ARG, "bad argument");
+  CHK(batch_start(b));
+  Group* g = b->groups[b->loc[case_id].first];
+  CHK(group_predict(b, g, g->ws->q));
+  CU(launch_extract_case(g->mesh->N, g->rpad, b->loc[case_id].second, g->ws->q, x_guess_dev, b->s));
+  CU(cudaStreamSynchronize(b->s));
+  return FEM_OK;
+}
+
+fem_status fem_case_get(fem_batch* b, int case_id, int what, double* dst, int on_device) {
+  g_err.clear();
+  if (!b || !dst || case_id < 0 || case_id >= (int)b->loc.size()) return fail(FEM_ERR_ARG, "bad argument");
+  CHK(batch_start(b));
+  Group* g = b->groups[b->loc[case_id].first];
+  const double* src = nullptr;
+  switch (what) {
+    case FEM_FIELD_U: src = g->u; break;
+    case FEM_FIELD_V: src = g->vh[((g->steps % 4) + 4) % 4]; break;
+    case FEM_FIELD_A: src = g->a; break;
+    case FEM_FIELD_DU: src = g->x; break;
+    case FEM_FIELD_B: src = g->b; break;
+    case FEM_FIELD_GUESS: src = g->guess; break;
+    default: return fail(FEM_ERR_ARG, "unknown field");
+  }
+  const int l = b->loc[case_id].second;
+  if (on_device) {
+    CU(launch_extract_case(g->mesh->N, g->rpad, l, src, dst, b->s));
+  } else {
+    double* tmp = g->ws->r;  // scratch, [N][3] fits
+    CU(launch_extract_case(g->mesh->N, g->rpad, l, src, tmp, b->s));
+    CU(cudaMemcpyAsync(dst, tmp, sizeof(double) * 3 * g->mesh->N, cudaMemcpyDeviceToHost, b->s));
+    CU(cudaStreamSynchronize(b->s));
+  }
+  return FEM_OK;
+}
+
+fem_status fem_batch_set_loads(fem_batch* b, const double* loads) {
+  g_err.clear();
+  if (!b || !loads) return fail(FEM_ERR_ARG, "null argument");
+  CHK(batch_start(b));
+  for (size_t c = 0; c < b->loc.size(); ++c) {
+    Group* g = b->groups[b->loc[c].first];
+    const int l = b->loc[c].second;
+    CU(cudaMemcpyAsync(g->ext + 3 * l, loads + 3 * c, 3 * sizeof(double), cudaMemcpyHostToDevice, b->s));
+    g->use_ext = true;
+  }
+  return FEM_OK;
+}
+
+fem_status fem_batch_get_field(fem_batch* b, int what, double* dst, int on_device) {
+  g_err.clear();
+  if (!b || !dst) return fail(FEM_ERR_ARG, "null argument");
+  CHK(batch_start(b));
+  for (auto* g : b->groups) {
+    const double* src = nullptr;
+    switch (what) {
+      case FEM_FIELD_U: src = g->u; break;
+      case FEM_FIELD_V: src = g->vh[((g->steps % 4) + 4) % 4]; break;
+      case FEM_FIELD_A: src = g->a; break;
+      case FEM_FIELD_DU: src = g->x; break;
+      case FEM_FIELD_B: src = g->b; break;
+      case FEM_FIELD_GUESS: src = g->guess; break;
+      default: return fail(FEM_ERR_ARG, "unknown field");
+    }
+    const int64_t n3 = g->mesh->N * 3;
+    double* tmp = g->ws->r;  // [rpad][N][3] scratch
+    CU(launch_extract_all(g->mesh->N, g->rpad, (int)g->cases.size(), src, tmp, b->s));
+    // cases of a group are contiguous in tmp; their ids may not be contiguous in dst
+    for (size_t l = 0; l < g->cases.size(); ++l) {
+      double* d = dst + (size_t)g->cases[l] * n3;
+      CU(cudaMemcpyAsync(d, tmp + l * n3, sizeof(double) * n3,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->s));
+    }
+  }
+  if (!on_device) CU(cudaStreamSynchronize(b->s));
+  return FEM_OK;
+}
+
+fem_status fem_batch_profile(fem_batch* b, int enable, fem_profile* out) {
+  g_err.clear();
+  if (!b) return fail(FEM_ERR_ARG, "batch is null");
+  CU(cudaStreamSynchronize(b->s));
+  b->prof.resolve();
+  if (enable == 1) {
+    b->prof.reset();
+    b->prof.on = true;
+  } else if (enable == 0) {
+    b->prof.on = false;
+  }
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    const Prof& p = b->prof;
+    out->steps = p.steps;
+    out->kernel_launches = p.launches;
+    out->ebe32_launches = p.n[P_EBE32];
+    out->ebe32_ms = p.ms[P_EBE32];
+    out->ebe64_launches = p.n[P_EBE64];
+    out->ebe64_ms = p.ms[P_EBE64];
+    out->cg_vec_launches = p.n[P_VEC];
+    out->cg_vec_ms = p.ms[P_VEC];
+    out->predict_ms = p.ms[P_PREDICT];
+    out->rhs_ms = p.ms[P_RHS];
+    out->solve_ms = p.ms[P_SOLVE];
+    out->update_ms = p.ms[P_UPDATE];
+  }
+  return FEM_OK;
+}
+
+fem_status fem_batch_steps(const fem_batch* b, int* steps_out) {
+  if (!b || !steps_out) return fail(FEM_ERR_ARG, "null argument");
+  *steps_out = b->steps;
+  return FEM_OK;
+}
+
+}  // extern "C"

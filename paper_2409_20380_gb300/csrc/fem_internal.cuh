@@ -1,0 +1,199 @@
+// Internal declarations shared by the libfem translation units (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fem.h"
+
+namespace fem {
+
+constexpr int kBlock = 256;              // threads per block of the streaming kernels
+constexpr int kMaxRpad = 32;             // max cases per multi-RHS group
+constexpr int kMaxSlots = 33;            // predictor ring: s_max + 1 <= 33
+constexpr int kMaxRedBlocks = 152 * 8;   // grid cap of reducing kernels (partials buffer rows)
+
+// Per-element record, 12 values: g1 (3), g2 (3), g3 (3) shape-function gradients of local nodes 1..3
+// (g0 = -g1-g2-g3), lambda*V, mu*V, rho*V/20.
+constexpr int kRec = 12;
+
+// Per-case CG scalars, device resident.
+struct CgCase {
+  double rho;      // (z, r) of the current residual
+  double pq;       // (p, A p)
+  double rr;       // (r, r)
+  double bb;       // (b, b)
+  double alpha;
+  double beta;
+  double relres;   // last certified / recursive relative residual
+  int active;      // 1 while the case iterates
+  int iters;
+  int status;      // FEM_OK or a negative fem_status
+  int phase;       // internal: 0 = before first direction
+};
+
+// Grid-wide deterministic per-case reduction: per-block partials + last-block final sum.
+struct Reducer {
+  double* partial;     // [kMaxRedBlocks][3 * kMaxRpad]
+  unsigned* counter;   // one counter, 0 between launches
+  double* out;         // [3 * kMaxRpad]
+};
+
+struct MeshView {
+  int64_t N, E;
+  const int4* conn;
+  const double* rec64;
+  const float* rec32;
+  const double* binv64;   // [N][6] xx yy zz xy xz yz
+  const float* binv32;
+  const uint8_t* freemask;  // [N] bit k = DOF k free
+};
+
+struct RickerSrc {          // per case of a group
+  int node;                 // -1: no source (padding lane)
+  double dir[3];
+  double f0, t0, amp;
+};
+
+// ---- launchers (stream-ordered; return cudaGetLastError()) ----
+int grid_for(int64_t items, int cap = kMaxRedBlocks);
+
+cudaError_t launch_elem_setup(int64_t E, int64_t N, const double* xyz, const int4* conn, const int32_t* mat,
+                              int n_mat, const double* lmr, double* rec64, float* rec32, int* err_flag,
+                              cudaStream_t s);
+cudaError_t launch_diag_blocks(const MeshView& m, double aM, double aK, double* D, cudaStream_t s);
+cudaError_t launch_binv(int64_t N, const double* D, const uint8_t* freemask, double* binv64, float* binv32,
+                        int* err_flag, cudaStream_t s);
+
+// q = (aM M + aK K) pm  (+ aK K pk - aK K pm when pk != nullptr: M acts on pm, K on pk).  q is zeroed
+// first; Dirichlet DOFs of q are NOT masked (consumers mask).  If red != nullptr the per-case p^T q
+// (element-wise p_e^T A_e p_e) is reduced into red->out[c] / ptq_out[c] and, if sc != nullptr, the CG
+// step length alpha = rho / p^T A p is set.  gate: skip when *gate == 0.
+template <typename T>
+cudaError_t launch_ebe(const MeshView& m, int rpad, const T* pm, const T* pk, T* q, double aM, double aK,
+                       const Reducer* red, CgCase* sc, double* ptq_out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_ebe_gated(const MeshView& m, int rpad, const T* pm, const T* pk, T* q, double aM, double aK,
+                             const Reducer* red, CgCase* sc, double* ptq_out, const int* gate, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mask(int64_t N, int rpad, const uint8_t* fm, T* v, cudaStream_t s);
+
+// CG vector kernels on [N][3][rpad] data of type T (scalars and reductions in FP64).
+template <typename T>
+cudaError_t launch_norm_b_gated(const MeshView& m, int rpad, const T* b, Reducer red, CgCase* sc,
+                                const CgCase* gate, cudaStream_t s);
+template <typename T>
+cudaError_t launch_resid(const MeshView& m, int rpad, const T* b, const T* q, T* x, T* r, T* z,
+                         int first, Reducer red, CgCase* sc, int* n_active, double tol, int maxit,
+                         cudaStream_t s);
+template <typename T>
+cudaError_t launch_dir_gated(const MeshView& m, int rpad, const T* z, T* p, const CgCase* sc, const int* n_active,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_update(const MeshView& m, int rpad, const T* p, const T* q, T* x, T* r, T* z,
+                          Reducer red, CgCase* sc, int* n_active, double tol, int maxit, cudaStream_t s);
+
+// Mixed precision helpers.
+cudaError_t launch_outer_resid(const MeshView& m, int rpad, const double* b, const double* q,
+                               float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
+                               cudaStream_t s);
+cudaError_t launch_refine_counts(const MeshView& m, int rpad, double* x, const float* d32, CgCase* outer,
+                                 const CgCase* inner, cudaStream_t s);
+// x = 0 on Dirichlet DOFs and for cases with ||b|| = 0.
+template <typename T>
+cudaError_t launch_zero_b0_t(const MeshView& m, int rpad, T* x, const CgCase* sc, cudaStream_t s);
+cudaError_t launch_extract_case(int64_t N, int rpad, int c, const double* src, double* dst, cudaStream_t s);
+
+// Time stepping (FP64 [N][3][rpad]).
+cudaError_t launch_rhs_prep(int64_t n, double dt, double a0, double a1, const double* u, const double* v,
+                            const double* a, double* m_in, double* k_in, cudaStream_t s);
+// ext (nullable, device [rpad][3]): loads replacing the Ricker forces for this step.
+cudaError_t launch_rhs_finish(const MeshView& m, int rpad, double* b, const RickerSrc* src, const double* ext,
+                              double t, cudaStream_t s);
+// dst[c][n*3 + k] = src[(n*3 + k)*rpad + c] for c < n_cases
+cudaError_t launch_extract_all(int64_t N, int rpad, int n_cases, const double* src, double* dst, cudaStream_t s);
+cudaError_t launch_ab4(int64_t n, double dt, const double* v4, const double* v3, const double* v2,
+                       const double* v1, double* du_ab, cudaStream_t s);
+cudaError_t launch_add(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
+cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const double* du_ab, double* u,
+                                  const double* v_prev, double* a, double* v_push, void* e_push, int e_fp32,
+                                  cudaStream_t s);
+
+// Predictor (regions are node ranges [reg_lo[R], reg_hi[R])).
+struct PredView {
+  int n_regions;
+  const int32_t* reg_lo;
+  const int32_t* reg_hi;
+  int rpad;
+  int n_slots;             // ring size (s_max + 1)
+  int64_t slot_stride;     // elements per slot = N * 3 * rpad
+  const void* ring;        // [n_slots][N][3][rpad] float or double
+  int fp32;
+  double* gram;            // [R][rpad][kMaxSlots][kMaxSlots]
+  double* w;               // [R][rpad][kMaxSlots] coefficients in X order
+};
+cudaError_t launch_pred_dots(const PredView& p, int slot_new, unsigned valid_mask, cudaStream_t s);
+cudaError_t launch_pred_solve(const PredView& p, const int* x_slots, int n_pairs, int slot_new, double tau,
+                              cudaStream_t s);
+cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out,
+                                cudaStream_t s);
+
+}  // namespace fem
+
+// ---- device helpers ----
+#ifdef __CUDACC__
+namespace fem {
+
+__device__ __forceinline__ bool dof_free(uint8_t fm, int k) { return (fm >> k) & 1; }
+
+// Per-case sums over the grid.  Threads hold vals[q] for case c = threadIdx.x % rpad (the grid stride of
+// every caller is a multiple of rpad).  Returns true in the last block to finish, after red.out[q*rpad+c]
+// holds the grid totals (summed in a fixed order: deterministic).
+template <int NQ>
+__device__ __forceinline__ bool block_reduce_last(double (&vals)[NQ], int rpad, const Reducer& red) {
+  __shared__ double sh[kBlock / 32][NQ][32];
+  __shared__ bool am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double v = vals[q];
+    for (int off = 16; off >= rpad; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane < rpad) sh[warp][q][lane] = v;
+  }
+  __syncthreads();
+  const int V = NQ * rpad;
+  if (threadIdx.x < V) {
+    const int q = threadIdx.x / rpad, c = threadIdx.x % rpad;
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sh[w][q][c];
+    red.partial[(size_t)blockIdx.x * V + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(red.counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double* flat = &sh[0][0][0];
+  const int S = blockDim.x / V;
+  if (threadIdx.x < S * V) {
+    const int v = threadIdx.x % V, sl = threadIdx.x / V;
+    double acc = 0.0;
+    for (int b = sl; b < (int)gridDim.x; b += S) acc += __ldcg(red.partial + (size_t)b * V + v);
+    flat[sl * V + v] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < V) {
+    double acc = 0.0;
+    for (int sl = 0; sl < S; ++sl) acc += flat[sl * V + threadIdx.x];
+    red.out[threadIdx.x] = acc;
+  }
+  if (threadIdx.x == 0) *red.counter = 0u;
+  __syncthreads();
+  return true;
+}
+
+}  // namespace fem
+#endif

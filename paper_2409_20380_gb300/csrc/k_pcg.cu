@@ -1,0 +1,340 @@
+// Vector kernels of Algorithm 1 (block-Jacobi PCG) on [N][3][rpad] data, fused so that each iteration
+// makes three passes: direction (p = z + beta p), EBE (q = A p with p^T q fused), and the update
+// (x += alpha p, r -= alpha q, z = B^{-1} r, (z, r), (r, r)).  Per-case scalars live on the device and
+// are advanced by the last block of each reducing kernel, so the host only polls the active count.
+#include "fem_internal.cuh"
+
+namespace fem {
+
+template <typename T> struct Acc { using type = double; };
+template <> struct Acc<float> { using type = float; };
+
+template <typename T> __device__ __forceinline__ const T* binv_of(const MeshView& m);
+template <> __device__ __forceinline__ const double* binv_of<double>(const MeshView& m) { return m.binv64; }
+template <> __device__ __forceinline__ const float* binv_of<float>(const MeshView& m) { return m.binv32; }
+
+static int log2i(int r) {
+  int s = 0;
+  while ((1 << s) < r) ++s;
+  return s;
+}
+
+__device__ __forceinline__ void count_active(const CgCase* sc, int rpad, int* n_active) {
+  if (threadIdx.x == 0 && n_active) {
+    int n = 0;
+    for (int c = 0; c < rpad; ++c) n += sc[c].active;
+    *n_active = n;
+  }
+}
+
+// bb = ||b||^2 over free DOFs; resets the case state.  gate (optional): a case whose gate is inactive is
+// treated as b = 0.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_norm_b(MeshView m, int rpad, int rshift, const T* __restrict__ b,
+                                                   Reducer red, CgCase* sc, const CgCase* gate) {
+  typename Acc<T>::type acc = 0;
+  const int64_t total = m.N << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const uint8_t f = m.freemask[n];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const T v = b[(n * 3 + k) * rpad + c];
+      if (dof_free(f, k)) acc += v * v;
+    }
+  }
+  double v[1] = {(double)acc};
+  if (block_reduce_last<1>(v, rpad, red)) {
+    if (threadIdx.x < rpad) {
+      const int c = threadIdx.x;
+      CgCase& s = sc[c];
+      s.bb = (gate && !gate[c].active) ? 0.0 : red.out[c];
+      s.rho = s.pq = s.rr = s.alpha = s.beta = s.relres = 0.0;
+      s.active = 0;
+      s.iters = 0;
+      s.status = isfinite(s.bb) ? FEM_OK : FEM_ERR_NONFINITE;
+      s.phase = 0;
+    }
+  }
+}
+
+// r = b - q (q may be null: zero), masked; first: x = 0 for cases with b = 0.  z = B^{-1} r.
+// Tail (first): start the iteration.  Tail (re-check): true-residual test of cases that stopped on the
+// recursive residual; they resume if the true residual is above tol.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_resid(MeshView m, int rpad, int rshift, const T* __restrict__ b,
+                                                  const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
+                                                  T* __restrict__ z, int first, Reducer red, CgCase* sc,
+                                                  int* n_active, double tol, int maxit) {
+  const T* __restrict__ bi = binv_of<T>(m);
+  typename Acc<T>::type zr = 0, rr = 0;
+  const int64_t total = m.N << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const uint8_t f = m.freemask[n];
+    const bool zero_b = first && (sc[c].bb == 0.0);
+    T rv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int64_t id = (n * 3 + k) * rpad + c;
+      T v = b[id] - (q ? q[id] : (T)0);
+      if (!dof_free(f, k) || zero_b) v = (T)0;
+      rv[k] = v;
+      r[id] = v;
+      if (zero_b || !dof_free(f, k)) x[id] = (T)0;
+    }
+    const T* B = bi + n * 6;
+    const T z0 = B[0] * rv[0] + B[3] * rv[1] + B[4] * rv[2];
+    const T z1 = B[3] * rv[0] + B[1] * rv[1] + B[5] * rv[2];
+    const T z2 = B[4] * rv[0] + B[5] * rv[1] + B[2] * rv[2];
+    z[(n * 3 + 0) * rpad + c] = z0;
+    z[(n * 3 + 1) * rpad + c] = z1;
+    z[(n * 3 + 2) * rpad + c] = z2;
+    zr += z0 * rv[0] + z1 * rv[1] + z2 * rv[2];
+    rr += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+  }
+  double v[2] = {(double)zr, (double)rr};
+  if (block_reduce_last<2>(v, rpad, red)) {
+    if (threadIdx.x < rpad) {
+      const int c = threadIdx.x;
+      CgCase& s = sc[c];
+      const double zrc = red.out[c], rrc = red.out[rpad + c];
+      const double thr = tol * tol * s.bb;
+      if (first) {
+        s.rho = zrc;
+        s.rr = rrc;
+        s.beta = 0.0;
+        s.phase = 0;
+        s.relres = s.bb > 0.0 ? sqrt(rrc / s.bb) : 0.0;
+        if (!isfinite(rrc) || !isfinite(zrc)) s.status = FEM_ERR_NONFINITE;
+        s.active = (s.status == FEM_OK && s.bb > 0.0 && rrc >= thr) ? 1 : 0;
+      } else if (s.status == FEM_OK && !s.active && s.bb > 0.0) {
+        s.rr = rrc;
+        s.relres = sqrt(rrc / s.bb);
+        if (rrc >= thr) {
+          if (s.iters >= maxit) {
+            s.status = FEM_ERR_NOT_CONVERGED;
+          } else {
+            s.beta = (s.phase && s.rho != 0.0) ? zrc / s.rho : 0.0;
+            s.rho = zrc;
+            s.active = 1;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    count_active(sc, rpad, n_active);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_dir(MeshView m, int rpad, int rshift, const T* __restrict__ z,
+                                                T* __restrict__ p, const CgCase* sc, const int* n_active) {
+  if (*n_active == 0) return;
+  const int64_t total = (m.N * 3) << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i & (rpad - 1));
+    const CgCase& s = sc[c];
+    if (!s.active) continue;
+    const T beta = (T)(s.phase ? s.beta : 0.0);
+    p[i] = z[i] + beta * p[i];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_update(MeshView m, int rpad, int rshift, const T* __restrict__ p,
+                                                   const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
+                                                   T* __restrict__ z, Reducer red, CgCase* sc, int* n_active,
+                                                   double tol, int maxit) {
+  if (*n_active == 0) return;
+  const T* __restrict__ bi = binv_of<T>(m);
+  typename Acc<T>::type zr = 0, rr = 0;
+  const int64_t total = m.N << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const uint8_t f = m.freemask[n];
+    const T alpha = (T)sc[c].alpha;
+    T rv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int64_t id = (n * 3 + k) * rpad + c;
+      T rk = r[id];
+      if (alpha != (T)0) {
+        x[id] += alpha * p[id];
+        if (dof_free(f, k)) rk -= alpha * q[id];
+        r[id] = rk;
+      }
+      rv[k] = rk;
+    }
+    const T* B = bi + n * 6;
+    const T z0 = B[0] * rv[0] + B[3] * rv[1] + B[4] * rv[2];
+    const T z1 = B[3] * rv[0] + B[1] * rv[1] + B[5] * rv[2];
+    const T z2 = B[4] * rv[0] + B[5] * rv[1] + B[2] * rv[2];
+    z[(n * 3 + 0) * rpad + c] = z0;
+    z[(n * 3 + 1) * rpad + c] = z1;
+    z[(n * 3 + 2) * rpad + c] = z2;
+    zr += z0 * rv[0] + z1 * rv[1] + z2 * rv[2];
+    rr += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+  }
+  double v[2] = {(double)zr, (double)rr};
+  if (block_reduce_last<2>(v, rpad, red)) {
+    if (threadIdx.x < rpad) {
+      const int c = threadIdx.x;
+      CgCase& s = sc[c];
+      if (s.active) {
+        const double zrc = red.out[c], rrc = red.out[rpad + c];
+        s.beta = zrc / s.rho;
+        s.rho = zrc;
+        s.rr = rrc;
+        s.iters += 1;
+        s.phase = 1;
+        s.relres = sqrt(rrc / s.bb);
+        if (!isfinite(zrc) || !isfinite(rrc)) {
+          s.status = FEM_ERR_NONFINITE;
+          s.active = 0;
+        } else if (rrc < tol * tol * s.bb) {
+          s.active = 0;
+        } else if (s.iters >= maxit) {
+          s.active = 0;
+          s.status = FEM_ERR_NOT_CONVERGED;
+        }
+      }
+    }
+    __syncthreads();
+    count_active(sc, rpad, n_active);
+  }
+}
+
+// ---- mixed precision: FP64 outer residual -> FP32 inner right-hand side; FP64 refinement update ----
+__global__ void __launch_bounds__(kBlock) k_outer_resid(MeshView m, int rpad, int rshift, const double* __restrict__ b,
+                                                        const double* __restrict__ q, float* __restrict__ r32,
+                                                        Reducer red, CgCase* outer, int* n_active, double tol) {
+  double rr = 0.0;
+  const int64_t total = m.N << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const uint8_t f = m.freemask[n];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int64_t id = (n * 3 + k) * rpad + c;
+      const double v = dof_free(f, k) ? b[id] - q[id] : 0.0;
+      r32[id] = (float)v;
+      rr += v * v;
+    }
+  }
+  double v[1] = {rr};
+  if (block_reduce_last<1>(v, rpad, red)) {
+    if (threadIdx.x < rpad) {
+      const int c = threadIdx.x;
+      CgCase& s = outer[c];
+      const double rrc = red.out[c];
+      s.rr = rrc;
+      s.relres = s.bb > 0.0 ? sqrt(rrc / s.bb) : 0.0;
+      if (!isfinite(rrc)) s.status = FEM_ERR_NONFINITE;
+      s.active = (s.status == FEM_OK && s.bb > 0.0 && rrc >= tol * tol * s.bb) ? 1 : 0;
+    }
+    __syncthreads();
+    count_active(outer, rpad, n_active);
+  }
+}
+
+// x += d (FP64 accumulation of the FP32 correction); block 0 adds the inner iteration counts.
+__global__ void k_refine(int64_t n_items, int rpad, double* __restrict__ x, const float* __restrict__ d,
+                         CgCase* outer, const CgCase* inner) {
+  if (blockIdx.x == 0 && threadIdx.x < rpad) {
+    outer[threadIdx.x].iters += inner[threadIdx.x].iters;
+    if (inner[threadIdx.x].status == FEM_ERR_BREAKDOWN || inner[threadIdx.x].status == FEM_ERR_NONFINITE)
+      outer[threadIdx.x].status = inner[threadIdx.x].status;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+
+// x = 0 on Dirichlet DOFs and for cases whose right-hand side is zero (||b|| = 0 gives x = 0).
+template <typename T>
+__global__ void k_zero_b0(MeshView m, int rpad, int rshift, T* __restrict__ x, const CgCase* __restrict__ sc) {
+  const int64_t total = m.N << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const uint8_t f = m.freemask[n];
+    const bool z = sc[c].bb == 0.0;
+    for (int k = 0; k < 3; ++k)
+      if (z || !dof_free(f, k)) x[(n * 3 + k) * rpad + c] = (T)0;
+  }
+}
+
+// ---- launchers ----
+template <typename T>
+cudaError_t launch_zero_b0_t(const MeshView& m, int rpad, T* x, const CgCase* sc, cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_zero_b0<T><<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, x, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_zero_b0_t<double>(const MeshView&, int, double*, const CgCase*, cudaStream_t);
+template cudaError_t launch_zero_b0_t<float>(const MeshView&, int, float*, const CgCase*, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_norm_b_gated(const MeshView& m, int rpad, const T* b, Reducer red, CgCase* sc,
+                                const CgCase* gate, cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_norm_b<T><<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, b, red, sc, gate);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_resid(const MeshView& m, int rpad, const T* b, const T* q, T* x, T* r, T* z, int first,
+                         Reducer red, CgCase* sc, int* n_active, double tol, int maxit, cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_resid<T><<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, b, q, x, r, z, first, red, sc, n_active, tol, maxit);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dir_gated(const MeshView& m, int rpad, const T* z, T* p, const CgCase* sc, const int* n_active,
+                             cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_dir<T><<<grid_for((m.N * 3) << rs), kBlock, 0, s>>>(m, rpad, rs, z, p, sc, n_active);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update(const MeshView& m, int rpad, const T* p, const T* q, T* x, T* r, T* z, Reducer red,
+                          CgCase* sc, int* n_active, double tol, int maxit, cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_update<T><<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, p, q, x, r, z, red, sc, n_active, tol, maxit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outer_resid(const MeshView& m, int rpad, const double* b, const double* q, float* r32,
+                               Reducer red, CgCase* outer, int* n_active, double tol, cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_outer_resid<<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, b, q, r32, red, outer, n_active, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_counts(const MeshView& m, int rpad, double* x, const float* d32, CgCase* outer,
+                                 const CgCase* inner, cudaStream_t s) {
+  const int64_t n = m.N * 3 * rpad;
+  k_refine<<<grid_for(n), kBlock, 0, s>>>(n, rpad, x, d32, outer, inner);
+  return cudaGetLastError();
+}
+
+#define INST(T)                                                                                                   \
+  template cudaError_t launch_norm_b_gated<T>(const MeshView&, int, const T*, Reducer, CgCase*, const CgCase*,    \
+                                              cudaStream_t);                                                      \
+  template cudaError_t launch_resid<T>(const MeshView&, int, const T*, const T*, T*, T*, T*, int, Reducer,        \
+                                       CgCase*, int*, double, int, cudaStream_t);                                 \
+  template cudaError_t launch_dir_gated<T>(const MeshView&, int, const T*, T*, const CgCase*, const int*,         \
+                                           cudaStream_t);                                                         \
+  template cudaError_t launch_update<T>(const MeshView&, int, const T*, const T*, T*, T*, T*, Reducer, CgCase*,   \
+                                        int*, double, int, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace fem

@@ -1,0 +1,306 @@
+// Time-stepping kernels (Section 3.1, Eq. GE:DIS and Eq. timestep, in increment form) and the
+// predictors of Section 3.2: Adams-Bashforth 4 and the regional data-driven correction.
+// All vectors are [N][3][rpad] FP64 unless stated.
+#include "fem_internal.cuh"
+
+namespace fem {
+
+static int log2i(int r) {
+  int s = 0;
+  while ((1 << s) < r) ++s;
+  return s;
+}
+
+// Inputs of the fused right-hand-side EBE:  b = f + M m_in + K k_in  with
+//   m_in = a + (4/dt + a0) v,  k_in = a1 v - u
+// which equals f - K u + C v + M (a + 4/dt v) for C = a0 M + a1 K.
+__global__ void k_rhs_prep(int64_t n, double c_mv, double a1, const double* __restrict__ u,
+                           const double* __restrict__ v, const double* __restrict__ a, double* __restrict__ m_in,
+                           double* __restrict__ k_in) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double vv = v[i];
+    m_in[i] = a[i] + c_mv * vv;
+    k_in[i] = a1 * vv - u[i];
+  }
+}
+
+// Adds the Ricker point forces at time t and zeroes Dirichlet DOFs.
+__global__ void k_rhs_finish(MeshView m, int rpad, int rshift, double* __restrict__ b, const RickerSrc* __restrict__ src,
+                             const double* __restrict__ ext, double t) {
+  const int64_t total = m.N << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const uint8_t f = m.freemask[n];
+    const RickerSrc s = src[c];
+    double fv[3] = {0.0, 0.0, 0.0};
+    if (s.node == n) {
+      if (ext) {
+        for (int k = 0; k < 3; ++k) fv[k] = ext[c * 3 + k];
+      } else {
+        const double arg = (M_PI * s.f0 * (t - s.t0)) * (M_PI * s.f0 * (t - s.t0));
+        const double w = s.amp * (1.0 - 2.0 * arg) * exp(-arg);
+        for (int k = 0; k < 3; ++k) fv[k] = w * s.dir[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int64_t id = (n * 3 + k) * rpad + c;
+      b[id] = dof_free(f, k) ? b[id] + fv[k] : 0.0;
+    }
+  }
+}
+
+// du_AB = dt/24 (-9 v^{it-4} + 37 v^{it-3} - 59 v^{it-2} + 55 v^{it-1})   (Section 3.2)
+__global__ void k_ab4(int64_t n, double h, const double* __restrict__ v4, const double* __restrict__ v3,
+                      const double* __restrict__ v2, const double* __restrict__ v1, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = h * (-9.0 * v4[i] + 37.0 * v3[i] - 59.0 * v2[i] + 55.0 * v1[i]);
+}
+
+__global__ void k_add(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = a[i] + b[i];
+}
+
+// u += du;  v^it = 2/dt du - v^{it-1};  a^it = 4/dt^2 du - 4/dt v^{it-1} - a^{it-1};
+// snapshot e^it = du - du_AB (= u^it - u_AB^it).   v_prev and v_push may not alias.
+template <typename E>
+__global__ void k_newmark(int64_t n, double dt, const double* __restrict__ du, const double* __restrict__ du_ab,
+                          double* __restrict__ u, const double* __restrict__ v_prev, double* __restrict__ a,
+                          double* __restrict__ v_push, E* __restrict__ e_push) {
+  const double c2 = 2.0 / dt, c4 = 4.0 / dt, c44 = 4.0 / (dt * dt);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = du[i];
+    const double vp = v_prev[i];
+    u[i] += d;
+    v_push[i] = c2 * d - vp;
+    a[i] = c44 * d - c4 * vp - a[i];
+    if (e_push) e_push[i] = (E)(d - du_ab[i]);
+  }
+}
+
+// ---- data-driven predictor ----
+// Ring slot j of a group holds a past correction e (same layout as the state vectors).  Per region R
+// (node range) and case c the Gram of stored corrections gram[R][c][i][j] = e_i . e_j is kept up to date
+// by computing, after each push, the dots of the newest slot with every valid slot.
+
+template <typename T> struct PredAcc;
+template <> struct PredAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct PredAcc<float> {   // compensated FP32 summation of FP32 products
+  float s = 0.f, comp = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float y = a * b - comp;
+    const float t = s + y;
+    comp = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)comp; }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_pred_dots(PredView p, int slot_new, unsigned valid_mask) {
+  const int R = blockIdx.x;
+  const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
+  const int rpad = p.rpad;
+  const T* ring = (const T*)p.ring;
+  const T* xn = ring + (int64_t)slot_new * p.slot_stride;
+  PredAcc<T> acc[kMaxSlots];
+  const int64_t base = lo * 3 * rpad, cnt = (hi - lo) * 3 * rpad;
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const T x = xn[base + i];
+#pragma unroll
+    for (int j = 0; j < kMaxSlots; ++j)
+      if ((valid_mask >> j) & 1u) acc[j].add(ring[(int64_t)j * p.slot_stride + base + i], x);
+  }
+  __shared__ double sh[kBlock / 32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < kMaxSlots; ++j) {
+    if (!((valid_mask >> j) & 1u)) continue;
+    double v = acc[j].get();
+    for (int off = 16; off >= rpad; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane < rpad) sh[warp][lane] = v;
+    __syncthreads();
+    if (threadIdx.x < rpad) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[w][threadIdx.x];
+      double* G = p.gram + ((int64_t)R * rpad + threadIdx.x) * kMaxSlots * kMaxSlots;
+      G[slot_new * kMaxSlots + j] = s;
+      G[j * kMaxSlots + slot_new] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Per (region, case): least-squares coefficients w of the query (newest slot) on the X slots, by a
+// pivot-free Cholesky of the Gram with the column-drop rule  pivot <= tau^2 G_jj  (the squared form of
+// the modified Gram-Schmidt test ||v_j|| <= tau ||x_j||), then forward/back substitution.
+__global__ void k_pred_solve(PredView p, const int* __restrict__ x_slots, int n, int slot_new, double tau) {
+  const int R = blockIdx.x / p.rpad, c = blockIdx.x % p.rpad;
+  const int lane = threadIdx.x;
+  __shared__ double L[kMaxSlots][kMaxSlots + 1];
+  __shared__ double rhs[kMaxSlots], y[kMaxSlots], diag0[kMaxSlots];
+  __shared__ int keep[kMaxSlots];
+  __shared__ int xs[kMaxSlots];
+  const double* G = p.gram + ((int64_t)R * p.rpad + c) * kMaxSlots * kMaxSlots;
+  if (lane < n) xs[lane] = x_slots[lane];
+  __syncwarp();
+  for (int i = lane; i < n * n; i += 32) {
+    const int a = i / n, b = i % n;
+    L[a][b] = G[xs[a] * kMaxSlots + xs[b]];
+  }
+  if (lane < n) {
+    rhs[lane] = G[xs[lane] * kMaxSlots + slot_new];
+    diag0[lane] = G[xs[lane] * kMaxSlots + xs[lane]];
+  }
+  __syncwarp();
+  for (int j = 0; j < n; ++j) {
+    if (lane == 0) {
+      double s = L[j][j];
+      for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+      const bool kp = diag0[j] > 0.0 && s > tau * tau * diag0[j] && isfinite(s);
+      keep[j] = kp;
+      L[j][j] = kp ? sqrt(s) : 0.0;
+    }
+    __syncwarp();
+    const bool kp = keep[j];
+    for (int i = j + 1 + lane; i < n; i += 32) {
+      double s = L[i][j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      L[i][j] = kp ? s / L[j][j] : 0.0;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    for (int i = 0; i < n; ++i) {
+      double s = rhs[i];
+      for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+      y[i] = keep[i] ? s / L[i][i] : 0.0;
+    }
+    double* w = p.w + ((int64_t)R * p.rpad + c) * kMaxSlots;
+    for (int i = n - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int k = i + 1; k < n; ++k) s -= L[k][i] * w[k];
+      w[i] = keep[i] ? s / L[i][i] : 0.0;
+    }
+    for (int i = n; i < kMaxSlots; ++i) w[i] = 0.0;
+  }
+}
+
+// y_out += sum_a w_a Y_a over region nodes (Y_a = ring slot y_slots[a]).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* __restrict__ y_slots, int n,
+                                                         double* __restrict__ y_out) {
+  const int R = blockIdx.x;
+  const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
+  const int rpad = p.rpad;
+  const T* ring = (const T*)p.ring;
+  const int c = threadIdx.x & (rpad - 1);
+  const double* w = p.w + ((int64_t)R * rpad + c) * kMaxSlots;
+  T wl[kMaxSlots];
+  int64_t off[kMaxSlots];
+#pragma unroll
+  for (int a = 0; a < kMaxSlots; ++a) {
+    wl[a] = a < n ? (T)w[a] : (T)0;
+    off[a] = a < n ? (int64_t)y_slots[a] * p.slot_stride : 0;
+  }
+  const int64_t base = lo * 3 * rpad, cnt = (hi - lo) * 3 * rpad;
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    T s = 0;
+#pragma unroll
+    for (int a = 0; a < kMaxSlots; ++a)
+      if (a < n) s += wl[a] * ring[off[a] + base + i];
+    y_out[base + i] += (double)s;
+  }
+}
+
+// dst[n*3 + k] = src[(n*3 + k)*rpad + c]
+__global__ void k_extract_case(int64_t n3, int rpad, int c, const double* __restrict__ src, double* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i * rpad + c];
+}
+
+__global__ void k_extract_all(int64_t n3, int rpad, int n_cases, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+  const int64_t total = n3 * n_cases;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / n3, j = i - c * n3;
+    dst[i] = src[j * rpad + c];
+  }
+}
+
+// ---- launchers ----
+cudaError_t launch_extract_all(int64_t N, int rpad, int n_cases, const double* src, double* dst, cudaStream_t s) {
+  k_extract_all<<<grid_for(N * 3 * n_cases, 152 * 16), kBlock, 0, s>>>(N * 3, rpad, n_cases, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extract_case(int64_t N, int rpad, int c, const double* src, double* dst, cudaStream_t s) {
+  k_extract_case<<<grid_for(N * 3), kBlock, 0, s>>>(N * 3, rpad, c, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_prep(int64_t n, double dt, double a0, double a1, const double* u, const double* v,
+                            const double* a, double* m_in, double* k_in, cudaStream_t s) {
+  k_rhs_prep<<<grid_for(n), kBlock, 0, s>>>(n, 4.0 / dt + a0, a1, u, v, a, m_in, k_in);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_finish(const MeshView& m, int rpad, double* b, const RickerSrc* src, const double* ext,
+                              double t, cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_rhs_finish<<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, b, src, ext, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ab4(int64_t n, double dt, const double* v4, const double* v3, const double* v2, const double* v1,
+                       double* du_ab, cudaStream_t s) {
+  k_ab4<<<grid_for(n), kBlock, 0, s>>>(n, dt / 24.0, v4, v3, v2, v1, du_ab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
+  k_add<<<grid_for(n), kBlock, 0, s>>>(n, a, b, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const double* du_ab, double* u,
+                                  const double* v_prev, double* a, double* v_push, void* e_push, int e_fp32,
+                                  cudaStream_t s) {
+  if (e_fp32)
+    k_newmark<float><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (float*)e_push);
+  else
+    k_newmark<double><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (double*)e_push);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pred_dots(const PredView& p, int slot_new, unsigned valid_mask, cudaStream_t s) {
+  if (p.n_regions == 0) return cudaSuccess;
+  if (p.fp32)
+    k_pred_dots<float><<<p.n_regions, kBlock, 0, s>>>(p, slot_new, valid_mask);
+  else
+    k_pred_dots<double><<<p.n_regions, kBlock, 0, s>>>(p, slot_new, valid_mask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pred_solve(const PredView& p, const int* x_slots, int n_pairs, int slot_new, double tau,
+                              cudaStream_t s) {
+  if (p.n_regions == 0 || n_pairs <= 0) return cudaSuccess;
+  k_pred_solve<<<p.n_regions * p.rpad, 32, 0, s>>>(p, x_slots, n_pairs, slot_new, tau);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out, cudaStream_t s) {
+  if (p.n_regions == 0 || n_pairs <= 0) return cudaSuccess;
+  if (p.fp32)
+    k_pred_combine<float><<<p.n_regions, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out);
+  else
+    k_pred_combine<double><<<p.n_regions, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out);
+  return cudaGetLastError();
+}
+
+}  // namespace fem

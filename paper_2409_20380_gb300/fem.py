@@ -1,0 +1,262 @@
+"""Python binding of libfem (include/fem.h): argument marshalling only.
+
+Every function keeps the C-ABI name and forwards to the compiled library; tensors are CUDA tensors whose
+data pointers are passed as device pointers, and the current torch stream is passed as the CUDA stream.
+There is no fallback: if libfem.so is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfem.so")
+
+FEM_OK = 0
+FEM_ERR_ARG, FEM_ERR_OOM, FEM_ERR_CUDA = -1, -2, -3
+FEM_ERR_NOT_CONVERGED, FEM_ERR_BREAKDOWN, FEM_ERR_NONFINITE, FEM_ERR_TIMEOUT, FEM_ERR_STATE = -4, -5, -6, -7, -8
+FEM_FP64, FEM_FP32_INNER = 0, 1
+FEM_PRED_AB4, FEM_PRED_DD = 0, 1
+FEM_FIELD_U, FEM_FIELD_V, FEM_FIELD_A, FEM_FIELD_DU, FEM_FIELD_B, FEM_FIELD_GUESS = range(6)
+
+# every symbol include/fem.h declares
+EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_set_regions", "fem_ebe_apply",
+           "pcg_solve", "fem_batch_create", "fem_batch_destroy", "fem_case_add", "fem_step", "predictor_fit",
+           "predictor_predict", "fem_case_get", "fem_batch_set_loads", "fem_batch_get_field", "fem_batch_profile",
+           "fem_batch_steps", "fem_last_error")
+
+
+class FemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libfem status {status}: {msg}")
+        self.status = status
+
+
+class fem_time_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("a0", ctypes.c_double), ("a1", ctypes.c_double)]
+
+
+class fem_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("predictor", ctypes.c_int), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("s_max", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("tau", ctypes.c_double), ("snapshot_fp32", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class fem_profile(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("kernel_launches", ctypes.c_longlong),
+                ("ebe32_launches", ctypes.c_longlong), ("ebe32_ms", ctypes.c_double),
+                ("ebe64_launches", ctypes.c_longlong), ("ebe64_ms", ctypes.c_double),
+                ("cg_vec_launches", ctypes.c_longlong), ("cg_vec_ms", ctypes.c_double),
+                ("predict_ms", ctypes.c_double), ("rhs_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("update_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Loads libfem.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2409_20380_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    sig = {
+        "fem_opts_default": (None, [ctypes.POINTER(fem_opts)]),
+        "fem_mesh_create": (I, [I64, P, I64, P, P, I, P, P, ctypes.POINTER(fem_time_params), P, ctypes.POINTER(P)]),
+        "fem_mesh_destroy": (I, [P]),
+        "fem_mesh_set_regions": (I, [P, P]),
+        "fem_ebe_apply": (I, [P, I, P, P, I, D, D, P, P]),
+        "pcg_solve": (I, [P, P, P, I, ctypes.POINTER(fem_opts), P, P, P]),
+        "fem_batch_create": (I, [ctypes.POINTER(fem_opts), P, ctypes.POINTER(P)]),
+        "fem_batch_destroy": (I, [P]),
+        "fem_case_add": (I, [P, P, ctypes.c_int32, P, D, D, D, ctypes.POINTER(I)]),
+        "fem_step": (I, [P, I, P, P]),
+        "predictor_fit": (I, [P, I]),
+        "predictor_predict": (I, [P, I, P]),
+        "fem_case_get": (I, [P, I, I, P, I]),
+        "fem_batch_set_loads": (I, [P, P]),
+        "fem_batch_get_field": (I, [P, I, P, I]),
+        "fem_batch_profile": (I, [P, I, ctypes.POINTER(fem_profile)]),
+        "fem_batch_steps": (I, [P, ctypes.POINTER(I)]),
+        "fem_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != FEM_OK:
+        raise FemError(st, lib().fem_last_error().decode())
+    return st
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    import torch
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    if dtype is not None:
+        assert t.dtype == dtype, f"expected {dtype}, got {t.dtype}"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def fem_opts_default(**overrides) -> fem_opts:
+    o = fem_opts()
+    lib().fem_opts_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def fem_mesh_create(mesh, tp, stream=None):
+    """mesh: workload.Mesh (host arrays); tp: workload.TimeParams.  Returns an opaque handle."""
+    xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    conn = np.ascontiguousarray(mesh.conn, dtype=np.int32)
+    mat = np.ascontiguousarray(mesh.mat_id, dtype=np.int32)
+    lmr = np.ascontiguousarray(mesh.lam_mu_rho, dtype=np.float64)
+    fixed = np.ascontiguousarray(mesh.fixed_dof, dtype=np.uint8)
+    t = fem_time_params(tp.dt, tp.beta, tp.gamma, tp.a0, tp.a1)
+    h = ctypes.c_void_p()
+    _check(lib().fem_mesh_create(xyz.shape[0], _np_ptr(xyz), conn.shape[0], _np_ptr(conn), _np_ptr(mat),
+                                 lmr.shape[0], _np_ptr(lmr), _np_ptr(fixed), ctypes.byref(t), _stream(stream),
+                                 ctypes.byref(h)))
+    return h
+
+
+def fem_mesh_destroy(h):
+    _check(lib().fem_mesh_destroy(h))
+
+
+def fem_mesh_set_regions(h, region_of_node):
+    reg = np.ascontiguousarray(region_of_node, dtype=np.int32)
+    _check(lib().fem_mesh_set_regions(h, _np_ptr(reg)))
+
+
+def fem_ebe_apply(h, p, q, n_rhs, alpha_M, alpha_K, ptq=None, precision=None, stream=None):
+    import torch
+    if precision is None:
+        precision = FEM_FP64 if p.dtype == torch.float64 else FEM_FP32_INNER
+    dt = torch.float64 if precision == FEM_FP64 else torch.float32
+    _check(lib().fem_ebe_apply(h, precision, _ptr(p, dt), _ptr(q, dt), n_rhs, float(alpha_M), float(alpha_K),
+                               _ptr(ptq, torch.float64), _stream(stream)))
+
+
+def pcg_solve(h, b, x, n_rhs, opts, stream=None, raise_on_error=True):
+    """Returns (status, iters [n_rhs], relres [n_rhs])."""
+    import torch
+    iters = np.zeros(n_rhs, dtype=np.int32)
+    relres = np.zeros(n_rhs, dtype=np.float64)
+    st = lib().pcg_solve(h, _ptr(b, torch.float64), _ptr(x, torch.float64), n_rhs, ctypes.byref(opts),
+                         _stream(stream), _np_ptr(iters), _np_ptr(relres))
+    if raise_on_error and st not in (FEM_OK,):
+        _check(st)
+    return st, iters, relres
+
+
+def fem_batch_create(opts, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().fem_batch_create(ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def fem_batch_destroy(h):
+    _check(lib().fem_batch_destroy(h))
+
+
+def fem_case_add(batch, mesh_h, src):
+    """src: workload.Source.  Returns the case id."""
+    d = np.ascontiguousarray(src.direction, dtype=np.float64)
+    cid = ctypes.c_int()
+    _check(lib().fem_case_add(batch, mesh_h, int(src.node), _np_ptr(d), float(src.f0), float(src.t0),
+                              float(src.amp), ctypes.byref(cid)))
+    return cid.value
+
+
+def fem_step(batch, n_steps, n_cases, raise_on_error=True):
+    """Returns (status, iters [n_cases] summed over the steps, max relres [n_cases])."""
+    iters = np.zeros(n_cases, dtype=np.int32)
+    relres = np.zeros(n_cases, dtype=np.float64)
+    st = lib().fem_step(batch, n_steps, _np_ptr(iters), _np_ptr(relres))
+    if raise_on_error:
+        _check(st)
+    return st, iters, relres
+
+
+def predictor_fit(batch, case_id):
+    _check(lib().predictor_fit(batch, case_id))
+
+
+def predictor_predict(batch, case_id, x_guess):
+    import torch
+    _check(lib().predictor_predict(batch, case_id, _ptr(x_guess, torch.float64)))
+
+
+def fem_case_get(batch, case_id, what, n_nodes, out=None):
+    """Returns field `what` of a case as a host numpy array [n_nodes*3] (or fills the CUDA tensor `out`)."""
+    import torch
+    if out is not None:
+        _check(lib().fem_case_get(batch, case_id, what, _ptr(out, torch.float64), 1))
+        return out
+    a = np.zeros(3 * n_nodes, dtype=np.float64)
+    _check(lib().fem_case_get(batch, case_id, what, _np_ptr(a), 0))
+    return a
+
+
+def fem_batch_set_loads(batch, loads):
+    """loads: host array [n_cases][3] (numpy; pinned torch CPU tensors are passed by pointer too)."""
+    if hasattr(loads, "data_ptr"):
+        ptr = ctypes.c_void_p(loads.data_ptr())
+    else:
+        loads = np.ascontiguousarray(loads, dtype=np.float64)
+        ptr = _np_ptr(loads)
+    _check(lib().fem_batch_set_loads(batch, ptr))
+
+
+def fem_batch_get_field(batch, what, out):
+    """out: host numpy array or CUDA/CPU torch tensor [n_cases*n_nodes*3] (float64), filled in place."""
+    if hasattr(out, "data_ptr"):
+        _check(lib().fem_batch_get_field(batch, what, ctypes.c_void_p(out.data_ptr()), 1 if out.is_cuda else 0))
+    else:
+        assert out.dtype == np.float64 and out.flags.c_contiguous
+        _check(lib().fem_batch_get_field(batch, what, _np_ptr(out), 0))
+    return out
+
+
+def fem_batch_profile(batch, enable=-1):
+    p = fem_profile()
+    _check(lib().fem_batch_profile(batch, enable, ctypes.byref(p)))
+    return p.as_dict()
+
+
+def fem_batch_steps(batch):
+    s = ctypes.c_int()
+    _check(lib().fem_batch_steps(batch, ctypes.byref(s)))
+    return s.value
+
+
+def fem_last_error():
+    return lib().fem_last_error().decode()

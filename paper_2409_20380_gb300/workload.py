@@ -239,3 +239,9 @@ def config4_mesh(Hx=256, Hy=256, Hz=128, h=1.0 / 64) -> Mesh:
     basin = (rng.uniform(0.25 * Lx, 0.75 * Lx), rng.uniform(0.25 * Ly, 0.75 * Ly),
              rng.uniform(0.5, 1.5), rng.uniform(0.5, 1.5), rng.uniform(0.3, 1.0), 0.3)
     return layered_mesh(Hx, Hy, Hz, h, layer_tops=tops, base_lame=base, sigma=0.3, rng=rng, basin=basin)
+
+
+def ricker_load(src: Source, t: float) -> np.ndarray:
+    """Point-force vector [3] that source `src` applies at time t (a case's load input at its node)."""
+    arg = (math.pi * src.f0 * (t - src.t0)) ** 2
+    return src.amp * (1.0 - 2.0 * arg) * math.exp(-arg) * np.asarray(src.direction, dtype=np.float64)

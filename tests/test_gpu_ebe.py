@@ -1,0 +1,117 @@
+"""EBE product on the GPU (Section 3.2, Eq. eqebefem / eqmebefem) against the oracle's assembled CSR
+matrices, element by element of the output, for 1..32 interleaved cases, FP64 and FP32 element data.
+
+Tolerances: FP64 results differ from the CSR product only by summation order (relative 1e-13 of the
+vector norm); FP32 element records and arithmetic give ~1e-7 relative per entry, bounded here by 2e-6."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_20380_gb300 import build, fem
+from paper_2409_20380_gb300 import workload as wl
+from helpers import from_cases, random_free_vectors, small_mesh, to_cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    build.build()
+    fem.lib()
+    assert torch.cuda.is_available()
+    return torch
+
+
+CASES = [((7, 5, 4), 1, 0.0), ((7, 5, 4), 4, 0.2), ((9, 6, 5), 16, 0.1), ((3, 2, 2), 32, 0.0), ((12, 9, 7), 8, 0.15)]
+
+
+@pytest.mark.parametrize("dims,r,perturb", CASES)
+@pytest.mark.parametrize("coef", ["A", "M", "K"])
+def test_ebe_fp64_matches_csr(torch_dev, dims, r, perturb, coef):
+    torch = torch_dev
+    m = small_mesh(*dims, perturb=perturb)
+    tp = wl.TimeParams()
+    sysm, _ = oracle.build_system(m, tp)
+    cM = 4.0 / tp.dt ** 2 + 2.0 * tp.a0 / tp.dt
+    cK = 1.0 + 2.0 * tp.a1 / tp.dt
+    aM, aK, ref_mat = {"A": (cM, cK, sysm.A_full), "M": (1.0, 0.0, sysm.M), "K": (0.0, 1.0, sysm.K)}[coef]
+    h = fem.fem_mesh_create(m, tp)
+    try:
+        ps = random_free_vectors(m, r, seed=r)
+        p = torch.tensor(from_cases(ps, m.n_nodes, r), device="cuda")
+        q = torch.full_like(p, 7.0)                      # stale contents must be overwritten
+        ptq = torch.zeros(r, dtype=torch.float64, device="cuda")
+        fem.fem_ebe_apply(h, p, q, r, aM, aK, ptq)
+        torch.cuda.synchronize()
+        qs = to_cases(q.cpu().numpy(), m.n_nodes, r)
+        fixed = m.fixed_dof == 1
+        for c in range(r):
+            ref = ref_mat @ ps[c]
+            ref[fixed] = 0.0
+            assert np.all(qs[c][fixed] == 0.0)
+            err = np.abs(qs[c] - ref).max() / np.abs(ref).max()
+            assert err < 1e-13, (c, err)
+            d_ref = ps[c] @ (ref_mat @ ps[c])
+            assert abs(ptq[c].item() - d_ref) <= 1e-13 * abs(d_ref)
+    finally:
+        fem.fem_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("dims,r,perturb", CASES[:3])
+def test_ebe_fp32_matches_csr(torch_dev, dims, r, perturb):
+    torch = torch_dev
+    m = small_mesh(*dims, perturb=perturb)
+    tp = wl.TimeParams()
+    sysm, _ = oracle.build_system(m, tp)
+    cM = 4.0 / tp.dt ** 2 + 2.0 * tp.a0 / tp.dt
+    cK = 1.0 + 2.0 * tp.a1 / tp.dt
+    h = fem.fem_mesh_create(m, tp)
+    try:
+        ps = random_free_vectors(m, r, seed=3 * r)
+        p = torch.tensor(from_cases(ps, m.n_nodes, r), device="cuda", dtype=torch.float32)
+        q = torch.empty_like(p)
+        ptq = torch.zeros(r, dtype=torch.float64, device="cuda")
+        fem.fem_ebe_apply(h, p, q, r, cM, cK, ptq)
+        torch.cuda.synchronize()
+        qs = to_cases(q.cpu().double().numpy(), m.n_nodes, r)
+        p32 = [x.astype(np.float32).astype(np.float64) for x in ps]
+        for c in range(r):
+            ref = sysm.A_full @ p32[c]
+            ref[m.fixed_dof == 1] = 0.0
+            err = np.abs(qs[c] - ref).max() / np.abs(ref).max()
+            assert err < 2e-6, (c, err)
+            d_ref = p32[c] @ (sysm.A_full @ p32[c])
+            assert abs(ptq[c].item() - d_ref) <= 2e-6 * abs(d_ref)
+    finally:
+        fem.fem_mesh_destroy(h)
+
+
+def test_ebe_edge_cases(torch_dev):
+    torch = torch_dev
+    m = small_mesh(2, 2, 1)
+    tp = wl.TimeParams()
+    h = fem.fem_mesh_create(m, tp)
+    try:
+        p = torch.zeros(m.n_nodes * 3 * 4, dtype=torch.float64, device="cuda")
+        q = torch.ones_like(p)
+        fem.fem_ebe_apply(h, p, q, 4, 1.0, 1.0)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(q).item() == 0
+        with pytest.raises(fem.FemError) as ei:
+            fem.fem_ebe_apply(h, p, q, 3, 1.0, 1.0)
+        assert ei.value.status == fem.FEM_ERR_ARG
+    finally:
+        fem.fem_mesh_destroy(h)
+    # invalid meshes are rejected with an argument error
+    bad = small_mesh(2, 2, 1)
+    bad.conn = bad.conn.copy()
+    bad.conn[0, [2, 3]] = bad.conn[0, [3, 2]]              # negative orientation
+    with pytest.raises(fem.FemError) as ei:
+        fem.fem_mesh_create(bad, tp)
+    assert ei.value.status == fem.FEM_ERR_ARG
+    bad2 = small_mesh(2, 2, 1)
+    bad2.conn = bad2.conn.copy()
+    bad2.conn[5, 1] = bad2.n_nodes                        # node id out of range
+    with pytest.raises(fem.FemError):
+        fem.fem_mesh_create(bad2, tp)
