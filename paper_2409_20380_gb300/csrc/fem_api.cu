@@ -552,9 +552,9 @@ static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
                            bt->opts.snapshot_fp32, s));
   w->count();
   if (dd) {
-    unsigned mask = 0;
+    uint64_t mask = 0;
     const int n_e = std::min(it, g->n_slots);
-    for (int j = it - n_e + 1; j <= it; ++j) mask |= 1u << slot_of(g, j);
+    for (int j = it - n_e + 1; j <= it; ++j) mask |= 1ull << slot_of(g, j);
     CU(launch_pred_dots(pred_view(bt, g), slot_of(g, it), mask, s));
     w->count();
   }
@@ -836,8 +836,8 @@ fem_status predictor_fit(fem_batch* b, int case_id) {
   if (b->opts.predictor != FEM_PRED_DD || g->n_regions == 0) return FEM_OK;
   const int it = g->steps;
   const int n_e = std::min(it, g->n_slots);
-  unsigned mask = 0;
-  for (int j = it - n_e + 1; j <= it; ++j) mask |= 1u << slot_of(g, j);
+  uint64_t mask = 0;
+  for (int j = it - n_e + 1; j <= it; ++j) mask |= 1ull << slot_of(g, j);
   for (int j = it - n_e + 1; j <= it; ++j) CU(launch_pred_dots(pred_view(b, g), slot_of(g, j), mask, b->s));
   CU(cudaStreamSynchronize(b->s));
   return FEM_OK;

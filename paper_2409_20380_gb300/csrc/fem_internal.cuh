@@ -134,7 +134,8 @@ struct PredView {
   double* gram;            // [R][rpad][kMaxSlots][kMaxSlots]
   double* w;               // [R][rpad][kMaxSlots] coefficients in X order
 };
-cudaError_t launch_pred_dots(const PredView& p, int slot_new, unsigned valid_mask, cudaStream_t s);
+// valid_mask bit j = ring slot j holds a stored correction (64-bit: up to kMaxSlots = 33 slots).
+cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mask, cudaStream_t s);
 cudaError_t launch_pred_solve(const PredView& p, const int* x_slots, int n_pairs, int slot_new, double tau,
                               cudaStream_t s);
 cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out,

@@ -103,7 +103,7 @@ template <> struct PredAcc<float> {   // compensated FP32 summation of FP32 prod
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_pred_dots(PredView p, int slot_new, unsigned valid_mask) {
+__global__ void __launch_bounds__(kBlock) k_pred_dots(PredView p, int slot_new, uint64_t valid_mask) {
   const int R = blockIdx.x;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
   const int rpad = p.rpad;
@@ -115,12 +115,12 @@ __global__ void __launch_bounds__(kBlock) k_pred_dots(PredView p, int slot_new, 
     const T x = xn[base + i];
 #pragma unroll
     for (int j = 0; j < kMaxSlots; ++j)
-      if ((valid_mask >> j) & 1u) acc[j].add(ring[(int64_t)j * p.slot_stride + base + i], x);
+      if ((valid_mask >> j) & 1ull) acc[j].add(ring[(int64_t)j * p.slot_stride + base + i], x);
   }
   __shared__ double sh[kBlock / 32][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j < kMaxSlots; ++j) {
-    if (!((valid_mask >> j) & 1u)) continue;
+    if (!((valid_mask >> j) & 1ull)) continue;
     double v = acc[j].get();
     for (int off = 16; off >= rpad; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (lane < rpad) sh[warp][lane] = v;
@@ -278,7 +278,7 @@ cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_pred_dots(const PredView& p, int slot_new, unsigned valid_mask, cudaStream_t s) {
+cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mask, cudaStream_t s) {
   if (p.n_regions == 0) return cudaSuccess;
   if (p.fp32)
     k_pred_dots<float><<<p.n_regions, kBlock, 0, s>>>(p, slot_new, valid_mask);
