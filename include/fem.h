@@ -142,6 +142,24 @@ fem_status fem_ebe_apply(fem_mesh* m, int precision, const void* p_dev, void* q_
                          double alpha_M, double alpha_K, double* ptq_dev, void* stream);
 
 /*
+ * Allocation-free variant of fem_ebe_apply (the paper has no counterpart: this is a library service).
+ * Same arguments, results and errors as fem_ebe_apply, but it never allocates device memory (no
+ * cudaMalloc/cudaFree, no allocating library routine).  It is meant for callers that cannot allocate:
+ * code whose device memory is owned by another allocator under a fixed budget, and latency-critical loops
+ * that cannot take the device-wide synchronisation cudaMalloc/cudaFree may cause.  The scratch of the
+ * p^T q reduction is one fixed device array of 311,808 bytes inside the library (per-block partial sums
+ * for up to 32 cases), present on every GPU that loads the library until the process exits.
+ *   - n_rhs above 32 is rejected with FEM_ERR_ARG; the mesh's device must be the current device.
+ *   - The first call with ptq_dev != NULL on a device looks up the array's device address (a one-time
+ *     set-up per device); make that first call before any stream capture.
+ *   - Every call uses the same array: calls whose kernels overlap on the GPU (e.g. on two streams without
+ *     ordering between them) race and give wrong p^T q values.  Order such calls on one stream.
+ *   - q is overwritten and the reduction counter is cleared by each call; nothing else needs zeroing.
+ */
+fem_status fem_ebe_apply_noalloc(fem_mesh* m, int precision, const void* p_dev, void* q_dev, int n_rhs,
+                                 double alpha_M, double alpha_K, double* ptq_dev, void* stream);
+
+/*
  * Solves A x = b for n_rhs cases (Algorithm 1: 3x3 block-Jacobi PCG with the EBE product), starting from
  * the guess in x_dev.  With opts->precision = FEM_FP32_INNER the solve is an FP64 iterative refinement
  * whose corrections come from an FP32 inner PCG.  Either way each case stops when its FP64 true residual

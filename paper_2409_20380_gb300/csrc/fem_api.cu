@@ -571,6 +571,14 @@ static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
   return FEM_OK;
 }
 
+namespace fem {
+fem_status set_error(fem_status s, const std::string& msg) { return fail(s, msg); }
+void mesh_view_of(const fem_mesh* m, MeshView* view, int* device) {
+  *view = m->view();
+  *device = m->device;
+}
+}  // namespace fem
+
 // ------------------------------------------------------------------------------------------------------
 // C-ABI
 // ------------------------------------------------------------------------------------------------------

@@ -57,6 +57,11 @@ struct RickerSrc {          // per case of a group
   double f0, t0, amp;
 };
 
+// Accessors for translation units other than the C-ABI one: record the thread's error message and
+// return `s`; the device view and device id of a mesh.
+fem_status set_error(fem_status s, const std::string& msg);
+void mesh_view_of(const fem_mesh* m, MeshView* view, int* device);
+
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
 int grid_for(int64_t items, int cap = kMaxRedBlocks);
 

@@ -23,6 +23,7 @@ FEM_FIELD_U, FEM_FIELD_V, FEM_FIELD_A, FEM_FIELD_DU, FEM_FIELD_B, FEM_FIELD_GUES
 
 # every symbol include/fem.h declares
 EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_set_regions", "fem_ebe_apply",
+           "fem_ebe_apply_noalloc",
            "pcg_solve", "fem_batch_create", "fem_batch_destroy", "fem_case_add", "fem_step", "predictor_fit",
            "predictor_predict", "fem_case_get", "fem_batch_set_loads", "fem_batch_get_field", "fem_batch_profile",
            "fem_batch_steps", "fem_last_error")
@@ -76,6 +77,7 @@ def lib():
         "fem_mesh_destroy": (I, [P]),
         "fem_mesh_set_regions": (I, [P, P]),
         "fem_ebe_apply": (I, [P, I, P, P, I, D, D, P, P]),
+        "fem_ebe_apply_noalloc": (I, [P, I, P, P, I, D, D, P, P]),
         "pcg_solve": (I, [P, P, P, I, ctypes.POINTER(fem_opts), P, P, P]),
         "fem_batch_create": (I, [ctypes.POINTER(fem_opts), P, ctypes.POINTER(P)]),
         "fem_batch_destroy": (I, [P]),
@@ -163,6 +165,16 @@ def fem_ebe_apply(h, p, q, n_rhs, alpha_M, alpha_K, ptq=None, precision=None, st
     dt = torch.float64 if precision == FEM_FP64 else torch.float32
     _check(lib().fem_ebe_apply(h, precision, _ptr(p, dt), _ptr(q, dt), n_rhs, float(alpha_M), float(alpha_K),
                                _ptr(ptq, torch.float64), _stream(stream)))
+
+
+def fem_ebe_apply_noalloc(h, p, q, n_rhs, alpha_M, alpha_K, ptq=None, precision=None, stream=None):
+    """Like fem_ebe_apply, but the library allocates no device memory (fixed internal scratch)."""
+    import torch
+    if precision is None:
+        precision = FEM_FP64 if p.dtype == torch.float64 else FEM_FP32_INNER
+    dt = torch.float64 if precision == FEM_FP64 else torch.float32
+    _check(lib().fem_ebe_apply_noalloc(h, precision, _ptr(p, dt), _ptr(q, dt), n_rhs, float(alpha_M),
+                                       float(alpha_K), _ptr(ptq, torch.float64), _stream(stream)))
 
 
 def pcg_solve(h, b, x, n_rhs, opts, stream=None, raise_on_error=True):
