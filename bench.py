@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--comparator-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--kernel", default=None, choices=["ebe"],
+                    help="time one kernel alone (EBE product) instead of the full step")
+    ap.add_argument("--kernel-precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--variant", type=int, default=0, help="EBE variant: 0 auto, 1 generic, 2 tiled hex")
+    ap.add_argument("--hex-per-tile", type=int, default=0)
     return ap.parse_args()
 
 
@@ -358,8 +363,56 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_kernel(args):
+    """Times the EBE product alone (CUDA events, inputs resident) on the --dims mesh with --cases cases."""
+    import numpy as np
+    import torch
+    from paper_2409_20380_gb300 import build, fem
+    from paper_2409_20380_gb300 import workload as wl
+    build.build()
+    fem.lib()
+    torch.cuda.set_device(0)
+    Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
+    mesh = wl.config2_mesh(Hx, Hy, Hz)
+    tp = wl.TimeParams()
+    h = fem.fem_mesh_create(mesh, tp)
+    fem.fem_mesh_tune(h, args.variant, args.hex_per_tile)
+    r = args.cases
+    dt = torch.float32 if args.kernel_precision == "fp32" else torch.float64
+    g = torch.Generator(device="cuda").manual_seed(0)
+    p = torch.randn(mesh.n_nodes * 3 * r, device="cuda", dtype=dt, generator=g)
+    p.view(mesh.n_nodes, 3, r)[torch.from_numpy(mesh.fixed_dof.reshape(-1, 3).astype(bool)).cuda()] = 0
+    q = torch.empty_like(p)
+    ptq = torch.zeros(r, dtype=torch.float64, device="cuda")
+    cM = 4.0 / tp.dt ** 2 + 2.0 * tp.a0 / tp.dt
+    cK = 1.0 + 2.0 * tp.a1 / tp.dt
+    for _ in range(args.warmup):
+        fem.fem_ebe_apply(h, p, q, r, cM, cK, ptq)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fem.fem_ebe_apply(h, p, q, r, cM, cK, ptq)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    w = 4 if args.kernel_precision == "fp32" else 8
+    E, N = mesh.n_elems, mesh.n_nodes
+    bytes_launch = E * (16 + 12 * w) + r * N * 3 * 2 * w
+    info = fem.fem_mesh_info(h)
+    print(json.dumps({"kernel": "ebe", "precision": args.kernel_precision, "dims": args.dims, "cases": r,
+                      "variant": args.variant, "hex_per_tile": args.hex_per_tile, "mesh_info": info,
+                      "ms_per_launch": ms, "alg_gbs": bytes_launch / (ms * 1e-3) / 1e9,
+                      "alg_tflops": FLOP_PER_ELEM_CASE * E * r / (ms * 1e-3) / 1e12,
+                      "note": "includes the q zero-fill and the Dirichlet mask pass of fem_ebe_apply"}), flush=True)
+    fem.fem_mesh_destroy(h)
+
+
 def main():
     args = parse()
+    if args.kernel == "ebe":
+        run_kernel(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

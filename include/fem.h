@@ -90,11 +90,14 @@ typedef struct {
   double tau;            /* predictor column-drop threshold (relative orthogonalised norm) */
   int snapshot_fp32;     /* 1: store predictor snapshots in FP32 (Gram accumulated in FP64) */
   int check_every;       /* CG iterations between host-side convergence polls (>= 1) */
-  int reserved[6];
+  int refresh_every;     /* FEM_FP32_INNER steps: every this many steps the products K u, M v, K v, M a and
+                            A v^{it-3..it} that fem_step keeps by recurrence are recomputed directly
+                            (0 = 200) */
+  int reserved[5];
 } fem_opts;
 
 /* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-5, tau 1e-6,
- * snapshot_fp32 1, check_every 8. */
+ * snapshot_fp32 1, check_every 8, refresh_every 200. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */
@@ -119,6 +122,19 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
                            const uint8_t* fixed_dof, const fem_time_params* tp, void* stream,
                            fem_mesh** out);
 fem_status fem_mesh_destroy(fem_mesh* m);
+
+/*
+ * Selects the EBE product implementation of a mesh (library tuning knob; the paper's EBE is one product,
+ * Section 3.2, Eq. eqebefem).  ebe_variant: 0 = automatic, 1 = generic element kernel, 2 = tiled hex-patch
+ * kernel (available when the elements come in groups of six tets splitting a hexahedron with the Kuhn
+ * topology, which fem_mesh_create detects).  hex_per_tile: 0 = automatic (largest tile whose shared-memory
+ * accumulator fits), or 64/128/256/512 hexes per tile.  Errors: FEM_ERR_ARG for other values or variant 2
+ * on a mesh without hex patches.
+ */
+fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile);
+
+/* Reports whether the mesh has hex patches and its current EBE variant and tile size (nullable outputs). */
+fem_status fem_mesh_info(const fem_mesh* m, int* has_hex_patches, int* ebe_variant, int* hex_per_tile);
 
 /*
  * Sets the predictor's regions (Section 3.2: the domain is divided into small regions, each predicted
@@ -244,6 +260,18 @@ typedef struct {
 /* enable = 1: reset and start profiling; 0: stop; -1: leave as is.  out (nullable) receives the totals
  * accumulated so far. */
 fem_status fem_batch_profile(fem_batch* b, int enable, fem_profile* out);
+
+/* Statistics of the last completed step of one case. */
+typedef struct {
+  int steps;             /* completed steps of the case */
+  int iters;             /* CG iterations of the last step (inner iterations summed in FEM_FP32_INNER) */
+  int outer;             /* FP64 residual evaluations of the last step (FEM_FP32_INNER; 0 in FEM_FP64) */
+  int status;            /* fem_status of the last step's solve */
+  double init_relres;    /* ||b - A guess|| / ||b|| of the last step's initial guess (predictor quality) */
+  double relres;         /* certified ||b - A du|| / ||b|| of the last step */
+} fem_case_stats_t;
+
+fem_status fem_case_stats(fem_batch* b, int case_id, fem_case_stats_t* out);
 
 /* Number of completed steps of the batch. */
 fem_status fem_batch_steps(const fem_batch* b, int* steps_out);

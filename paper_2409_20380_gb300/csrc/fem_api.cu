@@ -65,11 +65,12 @@ enum ProfClass { P_EBE32 = 0, P_EBE64, P_VEC, P_PREDICT, P_RHS, P_SOLVE, P_UPDAT
 
 struct Prof {
   bool on = false;
-  std::vector<cudaEvent_t> pool;
-  size_t next = 0;
+  std::vector<cudaEvent_t> all, free_ev;
   struct Pair {
     int cls;
     cudaEvent_t a, b;
+    bool closed;
+    bool done;
   };
   std::vector<Pair> pend;
   double ms[P_NCLASS] = {};
@@ -77,7 +78,7 @@ struct Prof {
   long long launches = 0;
   int steps = 0;
   ~Prof() {
-    for (auto e : pool) cudaEventDestroy(e);
+    for (auto e : all) cudaEventDestroy(e);
   }
   void reset() {
     for (int i = 0; i < P_NCLASS; ++i) {
@@ -88,34 +89,52 @@ struct Prof {
     steps = 0;
   }
   cudaEvent_t get() {
-    if (next == pool.size()) {
+    if (free_ev.empty()) {
       cudaEvent_t e;
       cudaEventCreate(&e);
-      pool.push_back(e);
+      all.push_back(e);
+      return e;
     }
-    return pool[next++];
+    cudaEvent_t e = free_ev.back();
+    free_ev.pop_back();
+    return e;
   }
   int begin(int cls, cudaStream_t s) {
     if (!on) return -1;
-    Pair p{cls, get(), get()};
+    Pair p{cls, get(), get(), false, false};
     cudaEventRecord(p.a, s);
     pend.push_back(p);
     return (int)pend.size() - 1;
   }
   void end(int idx, cudaStream_t s) {
-    if (idx >= 0) cudaEventRecord(pend[idx].b, s);
+    if (idx < 0 || idx >= (int)pend.size()) return;
+    cudaEventRecord(pend[idx].b, s);
+    pend[idx].closed = true;
   }
-  void resolve() {  // call after the stream has been synchronised
+  // Accumulates closed pairs (the stream has been synchronised); slots are recycled once none is open.
+  void resolve() {
+    bool any_open = false;
     for (auto& p : pend) {
+      if (p.done) continue;
+      if (!p.closed) {
+        any_open = true;
+        continue;
+      }
       float t = 0.f;
       if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
         ms[p.cls] += t;
         n[p.cls] += 1;
       }
+      p.done = true;
     }
     cudaGetLastError();
-    pend.clear();
-    next = 0;
+    if (!any_open) {
+      for (auto& p : pend) {
+        free_ev.push_back(p.a);
+        free_ev.push_back(p.b);
+      }
+      pend.clear();
+    }
   }
 };
 
@@ -216,11 +235,33 @@ struct fem_mesh {
   int32_t* reg_lo = nullptr;
   int32_t* reg_hi = nullptr;
   std::vector<Workspace*> ws;
+  // tiled hex-patch EBE (present when the elements come in Kuhn hex patches)
+  bool hex = false;
+  static constexpr int kNTile = 4;
+  HexTiles tiles[kNTile];          // hex_per_tile 64, 128, 256, 512
+  std::vector<void*> tile_bufs;
+  int ebe_variant = 0;             // 0 auto, 1 generic element kernel, 2 tiled hex kernel
+  int hex_per_tile = 0;            // 0 auto
   MeshView view() const { return MeshView{N, E, conn, rec64, rec32, binv64, binv32, fm}; }
   ~fem_mesh() {
     dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(D);
     dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi);
     for (auto* w : ws) delete w;
+    for (void* b : tile_bufs) cudaFree(b);
+  }
+  // Tiling for a product on T with rpad cases: the largest tile whose accumulator fits the budget.
+  const HexTiles* pick_tiles(size_t elem_bytes, int rpad) const {
+    if (!hex || ebe_variant == 1) return nullptr;
+    const size_t budget = elem_bytes == 4 ? 100 * 1024 : 200 * 1024;
+    const HexTiles* best = nullptr;
+    for (int i = 0; i < kNTile; ++i) {
+      const HexTiles& t = tiles[i];
+      if (t.n_tiles == 0) continue;
+      if (hex_per_tile && t.hex_per_tile != hex_per_tile) continue;
+      const size_t need = (size_t)t.nloc_max * (3 * rpad * elem_bytes + 4);
+      if (need <= budget || (hex_per_tile && need <= 220 * 1024)) best = &t;
+    }
+    return best;
   }
   fem_status workspace(int rpad, Workspace** out) {
     for (auto* w : ws)
@@ -235,6 +276,16 @@ struct fem_mesh {
     return FEM_OK;
   }
 };
+
+// EBE product q = (aM M + aK K) p on the mesh: the tiled hex kernel when the mesh has hex patches and a
+// tiling fits, else the generic element kernel (q masked on Dirichlet DOFs by the consumers).
+template <typename T>
+static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, double aM, double aK,
+                               const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s) {
+  if (const HexTiles* t = m->pick_tiles(sizeof(T), rpad))
+    return launch_ebe_hex<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
+  return launch_ebe_gated<T>(m->view(), rpad, p, nullptr, q, aM, aK, red, sc, ptq, gate, s);
+}
 
 // ------------------------------------------------------------------------------------------------------
 // PCG drivers.
@@ -257,7 +308,7 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
     // the guess is zeroed on Dirichlet DOFs (and for b = 0) before its residual is formed
     CU(launch_zero_b0_t<T>(mv, rpad, x, sc, s));
     int pi = w->pbeg(ebe_cls, s);
-    CU(launch_ebe<T>(mv, rpad, x, nullptr, q, m->cM, m->cK, nullptr, nullptr, nullptr, s));
+    CU(ebe_product<T>(m, rpad, x, q, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
     w->pend(pi, s);
     CU(launch_resid<T>(mv, rpad, b, q, x, r, z, 1, red, sc, w->n_active, tol, maxit, s));
     w->count(3);
@@ -270,7 +321,7 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
       CU(launch_dir_gated<T>(mv, rpad, z, p, sc, w->n_active, s));
       w->pend(p0, s);
       int p1 = w->pbeg(ebe_cls, s);
-      CU(launch_ebe_gated<T>(mv, rpad, p, nullptr, q, m->cM, m->cK, &red, sc, nullptr, w->n_active, s));
+      CU(ebe_product<T>(m, rpad, p, q, m->cM, m->cK, &red, sc, nullptr, w->n_active, s));
       w->pend(p1, s);
       int p2 = w->pbeg(P_VEC, s);
       CU(launch_update<T>(mv, rpad, p, q, x, r, z, red, sc, w->n_active, tol, maxit, s));
@@ -286,7 +337,7 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
       if (++rechecks > 32) break;
       // Algorithm 1 stops on the recursive residual; confirm with the true one and resume if needed.
       int pi = w->pbeg(ebe_cls, s);
-      CU(launch_ebe<T>(mv, rpad, x, nullptr, q, m->cM, m->cK, nullptr, nullptr, nullptr, s));
+      CU(ebe_product<T>(m, rpad, x, q, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
       w->pend(pi, s);
       CU(launch_resid<T>(mv, rpad, b, q, x, r, z, 0, red, sc, w->n_active, tol, maxit, s));
       w->count(2);
@@ -312,7 +363,7 @@ static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double
   const int kMaxOuter = 40;
   for (int outer_it = 0; outer_it <= kMaxOuter; ++outer_it) {
     int pi = w->pbeg(P_EBE64, s);
-    CU(launch_ebe<double>(mv, rpad, x, nullptr, w->q, m->cM, m->cK, nullptr, nullptr, nullptr, s));
+    CU(ebe_product<double>(m, rpad, x, w->q, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
     w->pend(pi, s);
     CU(launch_outer_resid(mv, rpad, b, w->q, w->r32, red, w->outer, w->n_active, o.tol, s));
     w->count(2);
@@ -381,17 +432,23 @@ struct Group {
   int* h_slots = nullptr;       // pinned [2][kMaxSlots]
   RickerSrc* src = nullptr;
   double* ext = nullptr;        // device [rpad][3]: external loads for the next step
+  // FP32-inner steps: products kept by recurrences (K u, M v, K v, M a, ring of A v) and split products
+  double *Ku = nullptr, *Mv = nullptr, *Kv = nullptr, *Ma = nullptr, *Av[4] = {nullptr, nullptr, nullptr, nullptr};
+  double *qM = nullptr, *qK = nullptr;
   bool use_ext = false;
   Workspace* ws = nullptr;
   int steps = 0;
   std::vector<int> iters_acc;
   std::vector<double> relres_max;
+  std::vector<CgCase> last;     // per-lane solve statistics of the last step
   ~Group() {
     dfree(u); dfree(a);
     for (auto& v : vh) dfree(v);
     dfree(b); dfree(x); dfree(du_ab); dfree(m_in); dfree(k_in); dfree(guess);
     if (ring) cudaFree(ring);
     dfree(gram); dfree(wcoef); dfree(slot_lists); dfree(src); dfree(ext);
+    dfree(Ku); dfree(Mv); dfree(Kv); dfree(Ma); dfree(qM); dfree(qK);
+    for (auto& v : Av) dfree(v);
     if (h_slots) cudaFreeHost(h_slots);
     delete ws;
   }
@@ -431,6 +488,12 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
   CU(cudaMemsetAsync(g->x, 0, n * 8, s));
   CU(cudaMemsetAsync(g->guess, 0, n * 8, s));
   CU(cudaMemsetAsync(g->b, 0, n * 8, s));
+  if (bt->opts.precision == FEM_FP32_INNER) {
+    for (double** v : {&g->Ku, &g->Mv, &g->Kv, &g->Ma, &g->Av[0], &g->Av[1], &g->Av[2], &g->Av[3], &g->qM, &g->qK}) {
+      CHK(dalloc(v, n));
+      CU(cudaMemsetAsync(*v, 0, n * 8, s));
+    }
+  }
   if (bt->opts.predictor == FEM_PRED_DD) {
     g->n_slots = bt->opts.s_max + 1;
     const size_t esz = bt->opts.snapshot_fp32 ? 4 : 8;
@@ -462,6 +525,7 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
   g->ws->prof = &bt->prof;
   g->iters_acc.assign(g->rpad, 0);
   g->relres_max.assign(g->rpad, 0.0);
+  g->last.assign(g->rpad, CgCase{});
   return FEM_OK;
 }
 
@@ -483,7 +547,8 @@ static PredView pred_view(const fem_batch* bt, const Group* g) {
 static int slot_of(const Group* g, int j) { return (j - 1) % g->n_slots; }  // correction e^j, j >= 1
 
 // Initial guess of the increment for step it = g->steps + 1 into `out`: AB4 (+ regional correction).
-static fem_status group_predict(fem_batch* bt, Group* g, double* out) {
+static fem_status group_predict(fem_batch* bt, Group* g, double* out, bool* corrected = nullptr) {
+  if (corrected) *corrected = false;
   const int it = g->steps + 1;
   const double dt = g->mesh->tp.dt;
   auto vslot = [&](int j) { return g->vh[((j % 4) + 4) % 4]; };
@@ -506,12 +571,142 @@ static fem_status group_predict(fem_batch* bt, Group* g, double* out) {
   CU(launch_pred_solve(pv, g->slot_lists, n_pairs, slot_of(g, it - 1), bt->opts.tau, s));
   CU(launch_pred_combine(pv, g->slot_lists + kMaxSlots, n_pairs, out, s));
   g->ws->count(2);
+  if (corrected) *corrected = true;
   // the pinned slot list is reused next step: order the host write after this step's copy
   CU(cudaStreamSynchronize(s));
   return FEM_OK;
 }
 
+// Direct recomputation of the recurrence products from the state (bounds their rounding drift).
+static fem_status group_refresh(fem_batch* bt, Group* g) {
+  fem_mesh* m = g->mesh;
+  const MeshView mv = m->view();
+  cudaStream_t s = bt->s;
+  const int it = g->steps;      // state after step it
+  CU(launch_ebe_split(mv, g->rpad, g->u, g->qM, g->qK, s));
+  CU(cudaMemcpyAsync(g->Ku, g->qK, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+  CU(launch_ebe_split(mv, g->rpad, g->a, g->Ma, g->qK, s));
+  for (int j = it - 3; j <= it; ++j) {
+    const int sl = ((j % 4) + 4) % 4;
+    CU(launch_ebe_split(mv, g->rpad, g->vh[sl], g->qM, g->qK, s));
+    CU(launch_axpby(g->n, m->cM, g->qM, m->cK, g->qK, g->Av[sl], s));
+    if (j == it) {
+      CU(cudaMemcpyAsync(g->Mv, g->qM, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+      CU(cudaMemcpyAsync(g->Kv, g->qK, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  g->ws->count(12);
+  return FEM_OK;
+}
+
+// One step with the FP32-inner solver: right-hand side and the residual of the guess from the product
+// recurrences (no FP64 product), inner FP32 PCG, and one FP64 certification product per refinement pass,
+// whose split products M du, K du advance the recurrences.
+static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
+  fem_mesh* m = g->mesh;
+  const MeshView mv = m->view();
+  cudaStream_t s = bt->s;
+  const int it = g->steps + 1;
+  const double dt = m->tp.dt;
+  const fem_opts& o = bt->opts;
+  Workspace* w = g->ws;
+  const Reducer red = w->red();
+  auto vslot = [&](int j) { return g->vh[((j % 4) + 4) % 4]; };
+  auto aslot = [&](int j) { return g->Av[((j % 4) + 4) % 4]; };
+  const int every = o.refresh_every > 0 ? o.refresh_every : 200;
+  if (it > 1 && (it - 1) % every == 0) CHK(group_refresh(bt, g));
+  // 1. initial guess (Section 3.2)
+  int ph = w->pbeg(P_PREDICT, s);
+  bool corrected = false;
+  CHK(group_predict(bt, g, g->guess, &corrected));
+  w->pend(ph, s);
+  // 2. right-hand side (Section 3.1, Eq. GE:DIS) from the recurrences
+  ph = w->pbeg(P_RHS, s);
+  CU(launch_rhs_incr(mv, g->rpad, dt, m->tp.a0, m->tp.a1, g->Ma, g->Mv, g->Kv, g->Ku, g->b, g->src,
+                     g->use_ext ? g->ext : nullptr, it * dt, s));
+  g->use_ext = false;
+  w->pend(ph, s);
+  w->count();
+  // 3. residual of the guess: exact FP64 for the Adams-Bashforth part, FP32 product for the correction
+  ph = w->pbeg(P_SOLVE, s);
+  const float* qy = nullptr;
+  if (corrected) {
+    CU(launch_corr_f32(g->n, g->guess, g->du_ab, w->z32, s));
+    int pe = w->pbeg(P_EBE32, s);
+    CU(ebe_product<float>(m, g->rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
+    w->pend(pe, s);
+    qy = w->q32;
+    w->count(2);
+  }
+  CU(launch_r0(mv, g->rpad, dt, g->b, aslot(it - 4), aslot(it - 3), aslot(it - 2), aslot(it - 1), qy, w->r32, red,
+               w->outer, w->n_active, o.tol, s));
+  CU(cudaMemcpyAsync(g->x, g->guess, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+  w->count();
+  // 4. refinement passes: inner FP32 PCG (cases whose residual is above tol) + FP64 certification
+  const int kMaxPass = 40;
+  for (int pass = 0; pass < kMaxPass; ++pass) {
+    CU(cudaMemcpyAsync(w->h_active, w->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(w->h_sc, w->outer, sizeof(CgCase) * g->rpad, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    w->resolve();
+    int used = 0;
+    for (int c = 0; c < g->rpad; ++c) used = std::max(used, w->h_sc[c].iters);
+    if (*w->h_active > 0) {
+      if (used >= o.maxit || pass == kMaxPass - 1) {
+        for (int c = 0; c < g->rpad; ++c)
+          if (w->h_sc[c].active) w->h_sc[c].status = FEM_ERR_NOT_CONVERGED, w->h_sc[c].active = 0;
+        CU(cudaMemcpyAsync(w->outer, w->h_sc, sizeof(CgCase) * g->rpad, cudaMemcpyHostToDevice, s));
+      } else {
+        CHK(pcg_core<float>(m, w, w->r32, w->x32, w->rr32, w->z32, w->p32, w->q32, w->sc, true, false, o.inner_tol,
+                            o.maxit - used, w->outer, o.check_every, s));
+        CU(launch_refine_counts(mv, g->rpad, g->x, w->x32, w->outer, w->sc, s));
+        w->count();
+      }
+    } else if (pass > 0) {
+      break;
+    }
+    int pe = w->pbeg(P_EBE64, s);
+    CU(launch_ebe_split(mv, g->rpad, g->x, g->qM, g->qK, s));
+    w->pend(pe, s);
+    CU(launch_cert(mv, g->rpad, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol, s));
+    w->count(2);
+  }
+  w->pend(ph, s);
+  CU(cudaMemcpyAsync(w->h_sc, w->outer, sizeof(CgCase) * g->rpad, cudaMemcpyDeviceToHost, s));
+  // 5. Newmark update, product recurrences, snapshot push (Section 3.1, Eq. timestep)
+  ph = w->pbeg(P_UPDATE, s);
+  void* e_push = nullptr;
+  const bool dd = o.predictor == FEM_PRED_DD && g->n_regions > 0;
+  if (dd) {
+    const size_t esz = o.snapshot_fp32 ? 4 : 8;
+    e_push = (char*)g->ring + esz * (size_t)g->n * slot_of(g, it);
+  }
+  CU(launch_newmark_incr(g->n, dt, m->cM, m->cK, g->x, g->du_ab, g->qM, g->qK, g->u, vslot(it - 1), g->a, vslot(it),
+                         g->Ku, g->Mv, g->Kv, g->Ma, aslot(it), e_push, o.snapshot_fp32, s));
+  w->count();
+  if (dd) {
+    uint64_t mask = 0;
+    const int n_e = std::min(it, g->n_slots);
+    for (int j = it - n_e + 1; j <= it; ++j) mask |= 1ull << slot_of(g, j);
+    CU(launch_pred_dots(pred_view(bt, g), slot_of(g, it), mask, s));
+    w->count();
+  }
+  w->pend(ph, s);
+  CU(cudaStreamSynchronize(s));
+  w->resolve();
+  for (int l = 0; l < g->rpad; ++l) g->last[l] = w->h_sc[l];
+  for (int l = 0; l < (int)g->cases.size(); ++l) {
+    const CgCase& c = w->h_sc[l];
+    g->iters_acc[l] += c.iters;
+    g->relres_max[l] = std::max(g->relres_max[l], c.relres);
+    if (c.status != FEM_OK && (*worst == FEM_OK || c.status < *worst)) *worst = c.status;
+  }
+  g->steps = it;
+  return FEM_OK;
+}
+
 static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
+  if (bt->opts.precision == FEM_FP32_INNER) return group_step_mixed(bt, g, worst);
   fem_mesh* m = g->mesh;
   const MeshView mv = m->view();
   cudaStream_t s = bt->s;
@@ -561,6 +756,7 @@ static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
   w->pend(ph, s);
   CU(cudaStreamSynchronize(s));
   w->resolve();
+  for (int l = 0; l < g->rpad; ++l) g->last[l] = g->ws->h_sc[l];
   for (int l = 0; l < (int)g->cases.size(); ++l) {
     const CgCase& c = g->ws->h_sc[l];
     g->iters_acc[l] += c.iters;
@@ -598,6 +794,7 @@ void fem_opts_default(fem_opts* o) {
   o->tau = 1e-6;
   o->snapshot_fp32 = 1;
   o->check_every = 8;
+  o->refresh_every = 200;
 }
 
 fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
@@ -668,6 +865,36 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
   if (h_err & 1) return bail(fail(FEM_ERR_ARG, "connectivity or material id out of range"));
   if (h_err & 2) return bail(fail(FEM_ERR_ARG, "element with non-positive volume (conn must be positively oriented)"));
   if (h_err & 4) return bail(fail(FEM_ERR_ARG, "singular node diagonal block (node with no element?)"));
+  if (detect_hex_patches(conn, n_elems)) {
+    const int sizes[fem_mesh::kNTile] = {64, 128, 256, 512};
+    bool ok = true;
+    for (int i = 0; i < fem_mesh::kNTile && ok; ++i) {
+      HexTilesHost th;
+      if (!build_hex_tiles(conn, n_elems, n_nodes, sizes[i], &th)) continue;
+      int *d_hoff = nullptr, *d_noff = nullptr, *d_nodes = nullptr;
+      uint4* d_loc = nullptr;
+      ok = dalloc(&d_hoff, th.tile_hex_off.size()) == FEM_OK && dalloc(&d_noff, th.tile_node_off.size()) == FEM_OK &&
+           dalloc(&d_nodes, th.tile_nodes.size()) == FEM_OK && dalloc(&d_loc, (size_t)th.n_hex) == FEM_OK;
+      for (void* b : {(void*)d_hoff, (void*)d_noff, (void*)d_nodes, (void*)d_loc})
+        if (b) m->tile_bufs.push_back(b);
+      if (!ok) break;
+      cudaError_t ce = cudaMemcpy(d_hoff, th.tile_hex_off.data(), sizeof(int) * th.tile_hex_off.size(), cudaMemcpyHostToDevice);
+      if (ce == cudaSuccess) ce = cudaMemcpy(d_noff, th.tile_node_off.data(), sizeof(int) * th.tile_node_off.size(), cudaMemcpyHostToDevice);
+      if (ce == cudaSuccess) ce = cudaMemcpy(d_nodes, th.tile_nodes.data(), sizeof(int) * th.tile_nodes.size(), cudaMemcpyHostToDevice);
+      if (ce == cudaSuccess) ce = cudaMemcpy(d_loc, th.hex_local.data(), sizeof(uint16_t) * th.hex_local.size(), cudaMemcpyHostToDevice);
+      if (ce != cudaSuccess) return bail(fail(FEM_ERR_CUDA, std::string("tile upload: ") + cudaGetErrorString(ce)));
+      HexTiles& t = m->tiles[i];
+      t.n_tiles = th.n_tiles;
+      t.nloc_max = th.nloc_max;
+      t.hex_per_tile = th.hex_per_tile;
+      t.tile_hex_off = d_hoff;
+      t.tile_node_off = d_noff;
+      t.tile_nodes = d_nodes;
+      t.hex_local = d_loc;
+    }
+    if (!ok) return bail(fail(FEM_ERR_OOM, "tile allocation failed"));
+    m->hex = true;
+  }
   *out = m;
   return FEM_OK;
 }
@@ -676,6 +903,26 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
   cudaDeviceSynchronize();
   delete m;
+  return FEM_OK;
+}
+
+fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile) {
+  g_err.clear();
+  if (!m) return fail(FEM_ERR_ARG, "mesh is null");
+  if (ebe_variant < 0 || ebe_variant > 2) return fail(FEM_ERR_ARG, "ebe_variant must be 0, 1 or 2");
+  if (ebe_variant == 2 && !m->hex) return fail(FEM_ERR_ARG, "the mesh has no hex patches: tiled kernel unavailable");
+  if (hex_per_tile != 0 && hex_per_tile != 64 && hex_per_tile != 128 && hex_per_tile != 256 && hex_per_tile != 512)
+    return fail(FEM_ERR_ARG, "hex_per_tile must be 0, 64, 128, 256 or 512");
+  m->ebe_variant = ebe_variant;
+  m->hex_per_tile = hex_per_tile;
+  return FEM_OK;
+}
+
+fem_status fem_mesh_info(const fem_mesh* m, int* has_hex_patches, int* ebe_variant, int* hex_per_tile) {
+  if (!m) return fail(FEM_ERR_ARG, "mesh is null");
+  if (has_hex_patches) *has_hex_patches = m->hex ? 1 : 0;
+  if (ebe_variant) *ebe_variant = m->ebe_variant;
+  if (hex_per_tile) *hex_per_tile = m->hex_per_tile;
   return FEM_OK;
 }
 
@@ -722,12 +969,12 @@ fem_status fem_ebe_apply(fem_mesh* m, int precision, const void* p_dev, void* q_
   const Reducer red = w->red();
   const MeshView mv = m->view();
   if (precision == FEM_FP64) {
-    CU(launch_ebe<double>(mv, n_rhs, (const double*)p_dev, nullptr, (double*)q_dev, alpha_M, alpha_K,
-                          ptq_dev ? &red : nullptr, nullptr, ptq_dev, s));
+    CU(ebe_product<double>(m, n_rhs, (const double*)p_dev, (double*)q_dev, alpha_M, alpha_K,
+                           ptq_dev ? &red : nullptr, nullptr, ptq_dev, nullptr, s));
     CU(launch_mask<double>(m->N, n_rhs, m->fm, (double*)q_dev, s));
   } else if (precision == FEM_FP32_INNER) {
-    CU(launch_ebe<float>(mv, n_rhs, (const float*)p_dev, nullptr, (float*)q_dev, alpha_M, alpha_K,
-                         ptq_dev ? &red : nullptr, nullptr, ptq_dev, s));
+    CU(ebe_product<float>(m, n_rhs, (const float*)p_dev, (float*)q_dev, alpha_M, alpha_K,
+                          ptq_dev ? &red : nullptr, nullptr, ptq_dev, nullptr, s));
     CU(launch_mask<float>(m->N, n_rhs, m->fm, (float*)q_dev, s));
   } else {
     return fail(FEM_ERR_ARG, "unknown precision");
@@ -958,6 +1205,22 @@ fem_status fem_batch_profile(fem_batch* b, int enable, fem_profile* out) {
     out->solve_ms = p.ms[P_SOLVE];
     out->update_ms = p.ms[P_UPDATE];
   }
+  return FEM_OK;
+}
+
+fem_status fem_case_stats(fem_batch* b, int case_id, fem_case_stats_t* out) {
+  g_err.clear();
+  if (!b || !out || case_id < 0 || case_id >= (int)b->loc.size()) return fail(FEM_ERR_ARG, "bad argument");
+  std::memset(out, 0, sizeof(*out));
+  if (!b->started) return FEM_OK;
+  const Group* g = b->groups[b->loc[case_id].first];
+  const CgCase& c = g->last[b->loc[case_id].second];
+  out->steps = g->steps;
+  out->iters = c.iters;
+  out->outer = b->opts.precision == FEM_FP64 ? 0 : c.outer;
+  out->status = c.status;
+  out->init_relres = c.relres0;
+  out->relres = c.relres;
   return FEM_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fem.h"
 
@@ -19,6 +20,31 @@ constexpr int kMaxRedBlocks = 152 * 8;   // grid cap of reducing kernels (partia
 // (g0 = -g1-g2-g3), lambda*V, mu*V, rho*V/20.
 constexpr int kRec = 12;
 
+// Hex-patch topology: slots of the four corners of each of the six tets of a hex, slots numbered by first
+// appearance (the Kuhn split along the (0,0,0)-(1,1,1) diagonal gives exactly this table).
+constexpr int kHexTet[6][4] = {{0, 1, 2, 3}, {0, 1, 3, 4}, {0, 5, 3, 2}, {0, 5, 6, 3}, {0, 7, 4, 3}, {0, 7, 3, 6}};
+
+// Tiling of a hex-patch mesh (host copy).  tile_nodes carries bit 31 set for nodes other tiles touch too.
+struct HexTilesHost {
+  int hex_per_tile = 0;
+  int64_t n_hex = 0;
+  int n_tiles = 0;
+  int nloc_max = 0;
+  std::vector<int> tile_hex_off, tile_node_off, tile_nodes;
+  std::vector<uint16_t> hex_local;   // [n_hex][8] tile-local corner index
+};
+struct HexTiles {                    // device view
+  int n_tiles = 0;
+  int nloc_max = 0;
+  int hex_per_tile = 0;
+  const int* tile_hex_off = nullptr;
+  const int* tile_node_off = nullptr;
+  const int* tile_nodes = nullptr;
+  const uint4* hex_local = nullptr;  // 8 x uint16 per hex
+};
+bool detect_hex_patches(const int32_t* conn, int64_t E);
+bool build_hex_tiles(const int32_t* conn, int64_t E, int64_t N, int hex_per_tile, HexTilesHost* out);
+
 // Per-case CG scalars, device resident.
 struct CgCase {
   double rho;      // (z, r) of the current residual
@@ -32,6 +58,9 @@ struct CgCase {
   int iters;
   int status;      // FEM_OK or a negative fem_status
   int phase;       // internal: 0 = before first direction
+  double relres0;  // relative residual of the initial guess
+  int outer;       // FP64 residual evaluations (refinement passes) of the solve
+  int pad_;
 };
 
 // Grid-wide deterministic per-case reduction: per-block partials + last-block final sum.
@@ -84,6 +113,10 @@ cudaError_t launch_ebe_gated(const MeshView& m, int rpad, const T* pm, const T* 
                              const Reducer* red, CgCase* sc, double* ptq_out, const int* gate, cudaStream_t s);
 template <typename T>
 cudaError_t launch_mask(int64_t N, int rpad, const uint8_t* fm, T* v, cudaStream_t s);
+// Tiled hex-patch EBE: q = (aM M + aK K) p with Dirichlet DOFs of q zeroed; same reduction/tail options.
+template <typename T>
+cudaError_t launch_ebe_hex(const HexTiles& ht, const MeshView& m, int rpad, const T* p, T* q, double aM, double aK,
+                           const Reducer* red, CgCase* sc, double* ptq_out, const int* gate, cudaStream_t s);
 
 // CG vector kernels on [N][3][rpad] data of type T (scalars and reductions in FP64).
 template <typename T>
@@ -125,6 +158,26 @@ cudaError_t launch_add(int64_t n, const double* a, const double* b, double* out,
 cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const double* du_ab, double* u,
                                   const double* v_prev, double* a, double* v_push, void* e_push, int e_fp32,
                                   cudaStream_t s);
+
+// FP32-inner steps with products kept by recurrences (see k_step.cu).
+cudaError_t launch_rhs_incr(const MeshView& m, int rpad, double dt, double a0, double a1, const double* Ma,
+                            const double* Mv, const double* Kv, const double* Ku, double* b, const RickerSrc* src,
+                            const double* ext, double t, cudaStream_t s);
+cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab, float* y32, cudaStream_t s);
+cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
+                      const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
+                      int* n_active, double tol, cudaStream_t s);
+cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const double* b, const double* qM,
+                        const double* qK, float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
+                        cudaStream_t s);
+cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, const double* du, const double* du_ab,
+                                const double* qM, const double* qK, double* u, const double* v_prev, double* a,
+                                double* v_push, double* Ku, double* Mv, double* Kv, double* Ma, double* Av_push,
+                                void* e_push, int e_fp32, cudaStream_t s);
+cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, const double* y, double* out,
+                         cudaStream_t s);
+// Split FP64 product: qM = M p and qK = K p in one pass (generic element kernel).
+cudaError_t launch_ebe_split(const MeshView& m, int rpad, const double* p, double* qM, double* qK, cudaStream_t s);
 
 // Predictor (regions are node ranges [reg_lo[R], reg_hi[R])).
 struct PredView {

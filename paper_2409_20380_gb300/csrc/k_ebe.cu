@@ -14,6 +14,36 @@ template <typename T> __device__ __forceinline__ const T* rec_of(const MeshView&
 template <> __device__ __forceinline__ const double* rec_of<double>(const MeshView& m) { return m.rec64; }
 template <> __device__ __forceinline__ const float* rec_of<float>(const MeshView& m) { return m.rec32; }
 
+// Last block of a product with the fused p^T q: publish it and set the CG step length alpha.
+__device__ __forceinline__ void ebe_tail(const Reducer& red, CgCase* sc, double* ptq_out, int rpad) {
+  if (threadIdx.x < rpad) {
+    const int c = threadIdx.x;
+    const double pq = red.out[c];
+    if (ptq_out) ptq_out[c] = pq;
+    if (sc) {
+      CgCase& s = sc[c];
+      s.pq = pq;
+      if (s.active) {
+        if (!(pq > 0.0) || !isfinite(pq)) {
+          s.active = 0;
+          s.status = FEM_ERR_BREAKDOWN;
+          s.alpha = 0.0;
+        } else {
+          s.alpha = s.rho / pq;
+        }
+      } else {
+        s.alpha = 0.0;
+      }
+    }
+  }
+}
+
+static int log2i(int r) {
+  int s = 0;
+  while ((1 << s) < r) ++s;
+  return s;
+}
+
 template <typename T, bool TWO, bool DOT>
 __global__ void __launch_bounds__(kBlock) k_ebe_atomic(MeshView m, int rpad, int rshift, const T* __restrict__ pm,
                                                        const T* __restrict__ pk, T* __restrict__ q, T aM, T aK,
@@ -81,35 +111,8 @@ __global__ void __launch_bounds__(kBlock) k_ebe_atomic(MeshView m, int rpad, int
   }
   if (DOT) {
     double v[1] = {(double)dot};
-    if (block_reduce_last<1>(v, rpad, red)) {
-      if (threadIdx.x < rpad) {
-        const int c = threadIdx.x;
-        const double pq = red.out[c];
-        if (ptq_out) ptq_out[c] = pq;
-        if (sc) {
-          CgCase& s = sc[c];
-          s.pq = pq;
-          if (s.active) {
-            if (!(pq > 0.0) || !isfinite(pq)) {
-              s.active = 0;
-              s.status = FEM_ERR_BREAKDOWN;
-              s.alpha = 0.0;
-            } else {
-              s.alpha = s.rho / pq;
-            }
-          } else {
-            s.alpha = 0.0;
-          }
-        }
-      }
-    }
+    if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
   }
-}
-
-static int log2i(int r) {
-  int s = 0;
-  while ((1 << s) < r) ++s;
-  return s;
 }
 
 template <typename T>
@@ -167,5 +170,240 @@ cudaError_t launch_mask(int64_t N, int rpad, const uint8_t* fm, T* v, cudaStream
 }
 template cudaError_t launch_mask<double>(int64_t, int, const uint8_t*, double*, cudaStream_t);
 template cudaError_t launch_mask<float>(int64_t, int, const uint8_t*, float*, cudaStream_t);
+
+
+// ------------------------------------------------------------------------------------------------------
+// Tiled hex-patch EBE.  One thread per (hex, case): the hex's eight corner values of its case are gathered
+// once, its six tets are applied with register accumulation into the eight corners (the tet corner slots
+// are compile-time constants, kHexTet), and the 24 corner sums are added into a shared-memory accumulator
+// of the tile's nodes.  The flush stores nodes only this tile touches and adds (global red) the others;
+// q must be zero beforehand for those.  Dirichlet DOFs of q are written as zero.
+// ------------------------------------------------------------------------------------------------------
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  __device__ __forceinline__ static void load12(const float* __restrict__ src, float (&r)[12]) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    const float4 a = __ldg(s4), b = __ldg(s4 + 1), c = __ldg(s4 + 2);
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+    r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+    r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
+  }
+};
+template <> struct Vec4<double> {
+  __device__ __forceinline__ static void load12(const double* __restrict__ src, double (&r)[12]) {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const double2 v = __ldg(s2 + i);
+      r[2 * i] = v.x;
+      r[2 * i + 1] = v.y;
+    }
+  }
+};
+
+template <typename T, int A0, int A1, int A2, int A3>
+__device__ __forceinline__ void tet_acc(const T* __restrict__ re, T aM, T aK, const T (&P)[8][3], T (&Q)[8][3]) {
+  T r[12];
+  Vec4<T>::load12(re, r);
+  const T lam = aK * r[9], mu = aK * r[10], ms = aM * r[11];
+  T G[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T d1 = P[A1][i] - P[A0][i], d2 = P[A2][i] - P[A0][i], d3 = P[A3][i] - P[A0][i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) G[i][j] = d1 * r[j] + d2 * r[3 + j] + d3 * r[6 + j];
+  }
+  const T tr = G[0][0] + G[1][1] + G[2][2];
+  const T mu2 = mu + mu;
+  T S[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) S[i][i] = lam * tr + mu2 * G[i][i];
+  S[0][1] = S[1][0] = mu * (G[0][1] + G[1][0]);
+  S[0][2] = S[2][0] = mu * (G[0][2] + G[2][0]);
+  S[1][2] = S[2][1] = mu * (G[1][2] + G[2][1]);
+  T F[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[b][i] = S[i][0] * r[3 * b] + S[i][1] * r[3 * b + 1] + S[i][2] * r[3 * b + 2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T sum = P[A0][k] + P[A1][k] + P[A2][k] + P[A3][k];
+    Q[A0][k] += ms * (P[A0][k] + sum) - (F[0][k] + F[1][k] + F[2][k]);
+    Q[A1][k] += ms * (P[A1][k] + sum) + F[0][k];
+    Q[A2][k] += ms * (P[A2][k] + sum) + F[1][k];
+    Q[A3][k] += ms * (P[A3][k] + sum) + F[2][k];
+  }
+}
+
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex(HexTiles ht, MeshView m, int rpad, int rshift,
+                                                    const T* __restrict__ p, T* __restrict__ q, T aM, T aK,
+                                                    Reducer red, CgCase* sc, double* ptq_out, const int* gate) {
+  if (gate && *gate == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* qs = reinterpret_cast<T*>(smem_raw);
+  int* snode = reinterpret_cast<int*>(smem_raw + sizeof(T) * (size_t)ht.nloc_max * 3 * rpad);
+  const T* __restrict__ rec = rec_of<T>(m);
+  double dot = 0.0;
+  const int per_node = 3 * rpad;
+  for (int tile = blockIdx.x; tile < ht.n_tiles; tile += gridDim.x) {
+    const int n0 = ht.tile_node_off[tile], nl = ht.tile_node_off[tile + 1] - n0;
+    const int h0 = ht.tile_hex_off[tile], nh = ht.tile_hex_off[tile + 1] - h0;
+    for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) qs[i] = (T)0;
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) snode[i] = ht.tile_nodes[n0 + i];
+    __syncthreads();
+    T tdot = 0;
+    const int items = nh << rshift;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int hl = it >> rshift, c = it & (rpad - 1);
+      const int64_t hx = h0 + hl;
+      const uint4 lw = __ldg(ht.hex_local + hx);
+      int ls[8] = {(int)(lw.x & 0xffff), (int)(lw.x >> 16), (int)(lw.y & 0xffff), (int)(lw.y >> 16),
+                   (int)(lw.z & 0xffff), (int)(lw.z >> 16), (int)(lw.w & 0xffff), (int)(lw.w >> 16)};
+      T P[8][3], Q[8][3];
+#pragma unroll
+      for (int sl = 0; sl < 8; ++sl) {
+        const int64_t g = snode[ls[sl]] & 0x7fffffff;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          P[sl][k] = p[(g * 3 + k) * rpad + c];
+          Q[sl][k] = (T)0;
+        }
+      }
+      const T* re = rec + hx * 6 * kRec;
+      tet_acc<T, kHexTet[0][0], kHexTet[0][1], kHexTet[0][2], kHexTet[0][3]>(re + 0 * kRec, aM, aK, P, Q);
+      tet_acc<T, kHexTet[1][0], kHexTet[1][1], kHexTet[1][2], kHexTet[1][3]>(re + 1 * kRec, aM, aK, P, Q);
+      tet_acc<T, kHexTet[2][0], kHexTet[2][1], kHexTet[2][2], kHexTet[2][3]>(re + 2 * kRec, aM, aK, P, Q);
+      tet_acc<T, kHexTet[3][0], kHexTet[3][1], kHexTet[3][2], kHexTet[3][3]>(re + 3 * kRec, aM, aK, P, Q);
+      tet_acc<T, kHexTet[4][0], kHexTet[4][1], kHexTet[4][2], kHexTet[4][3]>(re + 4 * kRec, aM, aK, P, Q);
+      tet_acc<T, kHexTet[5][0], kHexTet[5][1], kHexTet[5][2], kHexTet[5][3]>(re + 5 * kRec, aM, aK, P, Q);
+#pragma unroll
+      for (int sl = 0; sl < 8; ++sl)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (DOT) tdot += P[sl][k] * Q[sl][k];
+          atomicAdd(qs + ls[sl] * per_node + k * rpad + c, Q[sl][k]);
+        }
+    }
+    dot += (double)tdot;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) {
+      const int l = i / per_node, rem = i - l * per_node;
+      const int k = rem >> rshift;
+      const int raw = snode[l];
+      const int64_t g = raw & 0x7fffffff;
+      const bool fixed = !dof_free(m.freemask[g], k);
+      T* dst = q + g * per_node + rem;
+      if (raw < 0) {
+        if (!fixed) atomicAdd(dst, qs[i]);
+      } else {
+        *dst = fixed ? (T)0 : qs[i];
+      }
+    }
+    __syncthreads();
+  }
+  if (DOT) {
+    double v[1] = {dot};
+    if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
+  }
+}
+
+template <typename T>
+cudaError_t launch_ebe_hex(const HexTiles& ht, const MeshView& m, int rpad, const T* p, T* q, double aM, double aK,
+                           const Reducer* red, CgCase* sc, double* ptq_out, const int* gate, cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(q, 0, sizeof(T) * (size_t)m.N * 3 * rpad, s);
+  if (err != cudaSuccess) return err;
+  const int rs = log2i(rpad);
+  const size_t smem = sizeof(T) * (size_t)ht.nloc_max * 3 * rpad + sizeof(int) * (size_t)ht.nloc_max;
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 1;
+  if (red) {
+    err = cudaFuncSetAttribute(k_ebe_hex<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe_hex<T, true>, kBlock, smem);
+  } else {
+    err = cudaFuncSetAttribute(k_ebe_hex<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe_hex<T, false>, kBlock, smem);
+  }
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  int grid = nsm * per_sm;
+  if (grid > ht.n_tiles) grid = ht.n_tiles;
+  if (grid > kMaxRedBlocks) grid = kMaxRedBlocks;
+  Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
+  if (red)
+    k_ebe_hex<T, true><<<grid, kBlock, smem, s>>>(ht, m, rpad, rs, p, q, (T)aM, (T)aK, rd, sc, ptq_out, gate);
+  else
+    k_ebe_hex<T, false><<<grid, kBlock, smem, s>>>(ht, m, rpad, rs, p, q, (T)aM, (T)aK, rd, nullptr, nullptr, gate);
+  return cudaGetLastError();
+}
+template cudaError_t launch_ebe_hex<double>(const HexTiles&, const MeshView&, int, const double*, double*, double,
+                                            double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
+template cudaError_t launch_ebe_hex<float>(const HexTiles&, const MeshView&, int, const float*, float*, double,
+                                           double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
+
+// Split FP64 product for the certification pass: qM = M p and qK = K p in one pass over the elements (the
+// increment's two products feed the recurrences of the right-hand side).  Generic element kernel.
+__global__ void __launch_bounds__(kBlock) k_ebe_split(MeshView m, int rpad, int rshift, const double* __restrict__ p,
+                                                      double* __restrict__ qM, double* __restrict__ qK) {
+  const int64_t total = m.E << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const int4 cn = __ldg(m.conn + e);
+    const int64_t nd[4] = {cn.x, cn.y, cn.z, cn.w};
+    double r[12];
+    Vec4<double>::load12(m.rec64 + e * kRec, r);
+    double P[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) P[a][k] = p[(nd[a] * 3 + k) * rpad + c];
+    double G[3][3];
+#pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2) {
+      const double d1 = P[1][i2] - P[0][i2], d2 = P[2][i2] - P[0][i2], d3 = P[3][i2] - P[0][i2];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) G[i2][j] = d1 * r[j] + d2 * r[3 + j] + d3 * r[6 + j];
+    }
+    const double lam = r[9], mu = r[10], ms = r[11];
+    const double tr = G[0][0] + G[1][1] + G[2][2];
+    double S[3][3];
+#pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2) S[i2][i2] = lam * tr + 2.0 * mu * G[i2][i2];
+    S[0][1] = S[1][0] = mu * (G[0][1] + G[1][0]);
+    S[0][2] = S[2][0] = mu * (G[0][2] + G[2][0]);
+    S[1][2] = S[2][1] = mu * (G[1][2] + G[2][1]);
+    double F[4][3];
+#pragma unroll
+    for (int b = 1; b < 4; ++b)
+#pragma unroll
+      for (int i2 = 0; i2 < 3; ++i2)
+        F[b][i2] = S[i2][0] * r[(b - 1) * 3] + S[i2][1] * r[(b - 1) * 3 + 1] + S[i2][2] * r[(b - 1) * 3 + 2];
+#pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2) F[0][i2] = -(F[1][i2] + F[2][i2] + F[3][i2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double sum = P[0][k] + P[1][k] + P[2][k] + P[3][k];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        atomicAdd(qK + (nd[a] * 3 + k) * rpad + c, F[a][k]);
+        atomicAdd(qM + (nd[a] * 3 + k) * rpad + c, ms * (P[a][k] + sum));
+      }
+    }
+  }
+}
+
+cudaError_t launch_ebe_split(const MeshView& m, int rpad, const double* p, double* qM, double* qK, cudaStream_t s) {
+  const size_t bytes = sizeof(double) * (size_t)m.N * 3 * rpad;
+  cudaError_t err = cudaMemsetAsync(qM, 0, bytes, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(qK, 0, bytes, s);
+  if (err != cudaSuccess) return err;
+  const int rs = log2i(rpad);
+  k_ebe_split<<<grid_for(m.E << rs), kBlock, 0, s>>>(m, rpad, rs, p, qM, qK);
+  return cudaGetLastError();
+}
 
 }  // namespace fem

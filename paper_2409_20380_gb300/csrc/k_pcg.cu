@@ -50,9 +50,10 @@ __global__ void __launch_bounds__(kBlock) k_norm_b(MeshView m, int rpad, int rsh
       const int c = threadIdx.x;
       CgCase& s = sc[c];
       s.bb = (gate && !gate[c].active) ? 0.0 : red.out[c];
-      s.rho = s.pq = s.rr = s.alpha = s.beta = s.relres = 0.0;
+      s.rho = s.pq = s.rr = s.alpha = s.beta = s.relres = s.relres0 = 0.0;
       s.active = 0;
       s.iters = 0;
+      s.outer = 0;
       s.status = isfinite(s.bb) ? FEM_OK : FEM_ERR_NONFINITE;
       s.phase = 0;
     }
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(kBlock) k_resid(MeshView m, int rpad, int rshi
         s.beta = 0.0;
         s.phase = 0;
         s.relres = s.bb > 0.0 ? sqrt(rrc / s.bb) : 0.0;
+        s.relres0 = s.relres;
         if (!isfinite(rrc) || !isfinite(zrc)) s.status = FEM_ERR_NONFINITE;
         s.active = (s.status == FEM_OK && s.bb > 0.0 && rrc >= thr) ? 1 : 0;
       } else if (s.status == FEM_OK && !s.active && s.bb > 0.0) {
@@ -234,6 +236,8 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(MeshView m, int rpad, in
       const double rrc = red.out[c];
       s.rr = rrc;
       s.relres = s.bb > 0.0 ? sqrt(rrc / s.bb) : 0.0;
+      if (s.outer == 0) s.relres0 = s.relres;
+      s.outer += 1;
       if (!isfinite(rrc)) s.status = FEM_ERR_NONFINITE;
       s.active = (s.status == FEM_OK && s.bb > 0.0 && rrc >= tol * tol * s.bb) ? 1 : 0;
     }

@@ -233,7 +233,184 @@ __global__ void k_extract_all(int64_t n3, int rpad, int n_cases, const double* _
   }
 }
 
+// ---- products kept by linear recurrences (FP32-inner steps) ----
+// With Ku, Mv, Kv, Ma maintained exactly (FP64) from the split products M du, K du of each certified
+// increment, the Newmark right-hand side needs no EBE pass:
+//   b = f + M a + (4/dt + a0) M v + a1 K v - K u.
+__global__ void k_rhs_incr(MeshView m, int rpad, int rshift, double c_mv, double a1, const double* __restrict__ Ma,
+                           const double* __restrict__ Mv, const double* __restrict__ Kv,
+                           const double* __restrict__ Ku, double* __restrict__ b, const RickerSrc* __restrict__ src,
+                           const double* __restrict__ ext, double t) {
+  const int64_t total = m.N << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const uint8_t f = m.freemask[n];
+    const RickerSrc s = src[c];
+    double fv[3] = {0.0, 0.0, 0.0};
+    if (s.node == n) {
+      if (ext) {
+        for (int k = 0; k < 3; ++k) fv[k] = ext[c * 3 + k];
+      } else {
+        const double arg = (M_PI * s.f0 * (t - s.t0)) * (M_PI * s.f0 * (t - s.t0));
+        const double w = s.amp * (1.0 - 2.0 * arg) * exp(-arg);
+        for (int k = 0; k < 3; ++k) fv[k] = w * s.dir[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int64_t id = (n * 3 + k) * rpad + c;
+      b[id] = dof_free(f, k) ? fv[k] + Ma[id] + c_mv * Mv[id] + a1 * Kv[id] - Ku[id] : 0.0;
+    }
+  }
+}
+
+// y32 = float(guess - du_ab): the data-driven part of the guess, for its FP32 product.
+__global__ void k_corr_f32(int64_t n, const double* __restrict__ guess, const double* __restrict__ du_ab,
+                           float* __restrict__ y32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y32[i] = (float)(guess[i] - du_ab[i]);
+}
+
+// Residual of the guess without an FP64 product:  r0 = b - A du_AB - A y  with
+// A du_AB = dt/24 (-9 Av^{it-4} + 37 Av^{it-3} - 59 Av^{it-2} + 55 Av^{it-1}) exact (FP64 recurrences)
+// and A y from the FP32 product of the small data-driven correction (qy, nullable).  Writes r32 and
+// starts the outer (FP64) iteration state.
+__global__ void __launch_bounds__(kBlock) k_r0(MeshView m, int rpad, int rshift, double h, const double* __restrict__ b,
+                                               const double* __restrict__ Av4, const double* __restrict__ Av3,
+                                               const double* __restrict__ Av2, const double* __restrict__ Av1,
+                                               const float* __restrict__ qy, float* __restrict__ r32, Reducer red,
+                                               CgCase* outer, int* n_active, double tol) {
+  double bb = 0.0, rr = 0.0;
+  const int64_t total = m.N << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const uint8_t f = m.freemask[n];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int64_t id = (n * 3 + k) * rpad + c;
+      double v = 0.0;
+      const double bv = b[id];
+      if (dof_free(f, k)) {
+        v = bv - h * (-9.0 * Av4[id] + 37.0 * Av3[id] - 59.0 * Av2[id] + 55.0 * Av1[id]);
+        if (qy) v -= (double)qy[id];
+      }
+      r32[id] = (float)v;
+      bb += bv * bv;
+      rr += v * v;
+    }
+  }
+  double vals[2] = {bb, rr};
+  if (block_reduce_last<2>(vals, rpad, red)) {
+    if (threadIdx.x < rpad) {
+      const int c = threadIdx.x;
+      CgCase& s = outer[c];
+      const double bbc = red.out[c], rrc = red.out[rpad + c];
+      s.rho = s.pq = s.alpha = s.beta = 0.0;
+      s.iters = 0;
+      s.outer = 0;
+      s.phase = 0;
+      s.bb = bbc;
+      s.rr = rrc;
+      s.relres = bbc > 0.0 ? sqrt(rrc / bbc) : 0.0;
+      s.relres0 = s.relres;
+      s.status = (isfinite(bbc) && isfinite(rrc)) ? FEM_OK : FEM_ERR_NONFINITE;
+      // estimate only: the certificate is the FP64 residual computed after the solve
+      s.active = (s.status == FEM_OK && bbc > 0.0 && rrc >= tol * tol * bbc) ? 1 : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int na = 0;
+      for (int c = 0; c < rpad; ++c) na += outer[c].active;
+      *n_active = na;
+    }
+  }
+}
+
+// Certified FP64 residual from the split products:  r = b - (cM qM + cK qK);  r32 = float(r) for the next
+// inner solve; cases at or above tol stay active.
+__global__ void __launch_bounds__(kBlock) k_cert(MeshView m, int rpad, int rshift, double cM, double cK,
+                                                 const double* __restrict__ b, const double* __restrict__ qM,
+                                                 const double* __restrict__ qK, float* __restrict__ r32, Reducer red,
+                                                 CgCase* outer, int* n_active, double tol) {
+  double rr = 0.0;
+  const int64_t total = m.N << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const uint8_t f = m.freemask[n];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int64_t id = (n * 3 + k) * rpad + c;
+      const double v = dof_free(f, k) ? b[id] - (cM * qM[id] + cK * qK[id]) : 0.0;
+      r32[id] = (float)v;
+      rr += v * v;
+    }
+  }
+  double vals[1] = {rr};
+  if (block_reduce_last<1>(vals, rpad, red)) {
+    if (threadIdx.x < rpad) {
+      const int c = threadIdx.x;
+      CgCase& s = outer[c];
+      const double rrc = red.out[c];
+      s.rr = rrc;
+      s.relres = s.bb > 0.0 ? sqrt(rrc / s.bb) : 0.0;
+      s.outer += 1;
+      if (!isfinite(rrc)) s.status = FEM_ERR_NONFINITE;
+      s.active = (s.status == FEM_OK && s.bb > 0.0 && rrc >= tol * tol * s.bb) ? 1 : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int na = 0;
+      for (int c = 0; c < rpad; ++c) na += outer[c].active;
+      *n_active = na;
+    }
+  }
+}
+
+// Newmark update with the product recurrences (du, its products qM = M du, qK = K du):
+//   u += du;  v' = 2/dt du - v;  a' = 4/dt^2 du - 4/dt v - a;
+//   Ku += qK;  Mv' = 2/dt qM - Mv;  Kv' = 2/dt qK - Kv;  Ma' = 4/dt^2 qM - 4/dt Mv - Ma;
+//   Av' = cM Mv' + cK Kv' (pushed to the 4-deep ring);  e = du - du_AB (snapshot).
+template <typename E>
+__global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, const double* __restrict__ du,
+                               const double* __restrict__ du_ab, const double* __restrict__ qM,
+                               const double* __restrict__ qK, double* __restrict__ u, const double* __restrict__ v_prev,
+                               double* __restrict__ a, double* __restrict__ v_push, double* __restrict__ Ku,
+                               double* __restrict__ Mv, double* __restrict__ Kv, double* __restrict__ Ma,
+                               double* __restrict__ Av_push, E* __restrict__ e_push) {
+  const double c2 = 2.0 / dt, c4 = 4.0 / dt, c44 = 4.0 / (dt * dt);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = du[i], vp = v_prev[i], m_ = qM[i], k_ = qK[i];
+    u[i] += d;
+    v_push[i] = c2 * d - vp;
+    a[i] = c44 * d - c4 * vp - a[i];
+    Ku[i] += k_;
+    const double mv = Mv[i], kv = Kv[i];
+    const double mv2 = c2 * m_ - mv, kv2 = c2 * k_ - kv;
+    Ma[i] = c44 * m_ - c4 * mv - Ma[i];
+    Mv[i] = mv2;
+    Kv[i] = kv2;
+    Av_push[i] = cM * mv2 + cK * kv2;
+    if (e_push) e_push[i] = (E)(d - du_ab[i]);
+  }
+}
+
+// out = alpha x + beta y
+__global__ void k_axpby(int64_t n, double alpha, const double* __restrict__ x, double beta,
+                        const double* __restrict__ y, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = alpha * x[i] + beta * y[i];
+}
+
 // ---- launchers ----
+cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, const double* y, double* out,
+                         cudaStream_t s) {
+  k_axpby<<<grid_for(n), kBlock, 0, s>>>(n, alpha, x, beta, y, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_extract_all(int64_t N, int rpad, int n_cases, const double* src, double* dst, cudaStream_t s) {
   k_extract_all<<<grid_for(N * 3 * n_cases, 152 * 16), kBlock, 0, s>>>(N * 3, rpad, n_cases, src, dst);
   return cudaGetLastError();
@@ -275,6 +452,49 @@ cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const 
     k_newmark<float><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (float*)e_push);
   else
     k_newmark<double><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (double*)e_push);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_incr(const MeshView& m, int rpad, double dt, double a0, double a1, const double* Ma,
+                            const double* Mv, const double* Kv, const double* Ku, double* b, const RickerSrc* src,
+                            const double* ext, double t, cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_rhs_incr<<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, 4.0 / dt + a0, a1, Ma, Mv, Kv, Ku, b, src, ext, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab, float* y32, cudaStream_t s) {
+  k_corr_f32<<<grid_for(n), kBlock, 0, s>>>(n, guess, du_ab, y32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
+                      const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
+                      int* n_active, double tol, cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_r0<<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer,
+                                                n_active, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const double* b, const double* qM,
+                        const double* qK, float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
+                        cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_cert<<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, cM, cK, b, qM, qK, r32, red, outer, n_active, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, const double* du, const double* du_ab,
+                                const double* qM, const double* qK, double* u, const double* v_prev, double* a,
+                                double* v_push, double* Ku, double* Mv, double* Kv, double* Ma, double* Av_push,
+                                void* e_push, int e_fp32, cudaStream_t s) {
+  if (e_fp32)
+    k_newmark_incr<float><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
+                                                         Mv, Kv, Ma, Av_push, (float*)e_push);
+  else
+    k_newmark_incr<double><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
+                                                          Mv, Kv, Ma, Av_push, (double*)e_push);
   return cudaGetLastError();
 }
 

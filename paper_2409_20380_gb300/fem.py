@@ -22,11 +22,12 @@ FEM_PRED_AB4, FEM_PRED_DD = 0, 1
 FEM_FIELD_U, FEM_FIELD_V, FEM_FIELD_A, FEM_FIELD_DU, FEM_FIELD_B, FEM_FIELD_GUESS = range(6)
 
 # every symbol include/fem.h declares
-EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_set_regions", "fem_ebe_apply",
+EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_tune", "fem_mesh_info",
+           "fem_mesh_set_regions", "fem_ebe_apply",
            "fem_ebe_apply_noalloc",
            "pcg_solve", "fem_batch_create", "fem_batch_destroy", "fem_case_add", "fem_step", "predictor_fit",
            "predictor_predict", "fem_case_get", "fem_batch_set_loads", "fem_batch_get_field", "fem_batch_profile",
-           "fem_batch_steps", "fem_last_error")
+           "fem_case_stats", "fem_batch_steps", "fem_last_error")
 
 
 class FemError(RuntimeError):
@@ -44,7 +45,7 @@ class fem_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("predictor", ctypes.c_int), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("s_max", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("tau", ctypes.c_double), ("snapshot_fp32", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("refresh_every", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class fem_profile(ctypes.Structure):
@@ -57,6 +58,11 @@ class fem_profile(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fem_case_stats_t(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("iters", ctypes.c_int), ("outer", ctypes.c_int), ("status", ctypes.c_int),
+                ("init_relres", ctypes.c_double), ("relres", ctypes.c_double)]
 
 
 _lib = None
@@ -75,6 +81,8 @@ def lib():
         "fem_opts_default": (None, [ctypes.POINTER(fem_opts)]),
         "fem_mesh_create": (I, [I64, P, I64, P, P, I, P, P, ctypes.POINTER(fem_time_params), P, ctypes.POINTER(P)]),
         "fem_mesh_destroy": (I, [P]),
+        "fem_mesh_tune": (I, [P, I, I]),
+        "fem_mesh_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "fem_mesh_set_regions": (I, [P, P]),
         "fem_ebe_apply": (I, [P, I, P, P, I, D, D, P, P]),
         "fem_ebe_apply_noalloc": (I, [P, I, P, P, I, D, D, P, P]),
@@ -89,6 +97,7 @@ def lib():
         "fem_batch_set_loads": (I, [P, P]),
         "fem_batch_get_field": (I, [P, I, P, I]),
         "fem_batch_profile": (I, [P, I, ctypes.POINTER(fem_profile)]),
+        "fem_case_stats": (I, [P, I, ctypes.POINTER(fem_case_stats_t)]),
         "fem_batch_steps": (I, [P, ctypes.POINTER(I)]),
         "fem_last_error": (ctypes.c_char_p, []),
     }
@@ -151,6 +160,16 @@ def fem_mesh_create(mesh, tp, stream=None):
 
 def fem_mesh_destroy(h):
     _check(lib().fem_mesh_destroy(h))
+
+
+def fem_mesh_tune(h, ebe_variant=0, hex_per_tile=0):
+    _check(lib().fem_mesh_tune(h, ebe_variant, hex_per_tile))
+
+
+def fem_mesh_info(h):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().fem_mesh_info(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"has_hex_patches": a.value, "ebe_variant": b.value, "hex_per_tile": c.value}
 
 
 def fem_mesh_set_regions(h, region_of_node):
@@ -262,6 +281,12 @@ def fem_batch_profile(batch, enable=-1):
     p = fem_profile()
     _check(lib().fem_batch_profile(batch, enable, ctypes.byref(p)))
     return p.as_dict()
+
+
+def fem_case_stats(batch, case_id):
+    st = fem_case_stats_t()
+    _check(lib().fem_case_stats(batch, case_id, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in st._fields_}
 
 
 def fem_batch_steps(batch):

@@ -24,11 +24,15 @@ def torch_dev():
 
 
 CASES = [((7, 5, 4), 1, 0.0), ((7, 5, 4), 4, 0.2), ((9, 6, 5), 16, 0.1), ((3, 2, 2), 32, 0.0), ((12, 9, 7), 8, 0.15)]
+# (ebe_variant, hex_per_tile): generic element kernel; tiled hex kernel with automatic and small tiles
+# (140..756 hexes over 64-hex tiles: several tiles and a ragged last one)
+VARIANTS = [(1, 0), (2, 0), (2, 64)]
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("dims,r,perturb", CASES)
 @pytest.mark.parametrize("coef", ["A", "M", "K"])
-def test_ebe_fp64_matches_csr(torch_dev, dims, r, perturb, coef):
+def test_ebe_fp64_matches_csr(torch_dev, dims, r, perturb, coef, variant):
     torch = torch_dev
     m = small_mesh(*dims, perturb=perturb)
     tp = wl.TimeParams()
@@ -38,6 +42,8 @@ def test_ebe_fp64_matches_csr(torch_dev, dims, r, perturb, coef):
     aM, aK, ref_mat = {"A": (cM, cK, sysm.A_full), "M": (1.0, 0.0, sysm.M), "K": (0.0, 1.0, sysm.K)}[coef]
     h = fem.fem_mesh_create(m, tp)
     try:
+        assert fem.fem_mesh_info(h)["has_hex_patches"] == 1
+        fem.fem_mesh_tune(h, *variant)
         ps = random_free_vectors(m, r, seed=r)
         p = torch.tensor(from_cases(ps, m.n_nodes, r), device="cuda")
         q = torch.full_like(p, 7.0)                      # stale contents must be overwritten
@@ -58,8 +64,9 @@ def test_ebe_fp64_matches_csr(torch_dev, dims, r, perturb, coef):
         fem.fem_mesh_destroy(h)
 
 
-@pytest.mark.parametrize("dims,r,perturb", CASES[:3])
-def test_ebe_fp32_matches_csr(torch_dev, dims, r, perturb):
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("dims,r,perturb", CASES)
+def test_ebe_fp32_matches_csr(torch_dev, dims, r, perturb, variant):
     torch = torch_dev
     m = small_mesh(*dims, perturb=perturb)
     tp = wl.TimeParams()
@@ -68,6 +75,7 @@ def test_ebe_fp32_matches_csr(torch_dev, dims, r, perturb):
     cK = 1.0 + 2.0 * tp.a1 / tp.dt
     h = fem.fem_mesh_create(m, tp)
     try:
+        fem.fem_mesh_tune(h, *variant)
         ps = random_free_vectors(m, r, seed=3 * r)
         p = torch.tensor(from_cases(ps, m.n_nodes, r), device="cuda", dtype=torch.float32)
         q = torch.empty_like(p)
@@ -115,3 +123,31 @@ def test_ebe_edge_cases(torch_dev):
     bad2.conn[5, 1] = bad2.n_nodes                        # node id out of range
     with pytest.raises(fem.FemError):
         fem.fem_mesh_create(bad2, tp)
+
+
+def test_ebe_mesh_without_hex_patches(torch_dev):
+    """Elements in shuffled order do not form hex patches: the generic kernel serves, with the same result."""
+    torch = torch_dev
+    m = small_mesh(6, 5, 4, perturb=0.1)
+    perm = np.random.default_rng(0).permutation(m.n_elems)
+    m.conn = np.ascontiguousarray(m.conn[perm])
+    m.mat_id = np.ascontiguousarray(m.mat_id[perm])
+    tp = wl.TimeParams()
+    sysm, _ = oracle.build_system(m, tp)
+    h = fem.fem_mesh_create(m, tp)
+    try:
+        assert fem.fem_mesh_info(h)["has_hex_patches"] == 0
+        with pytest.raises(fem.FemError):
+            fem.fem_mesh_tune(h, 2, 0)
+        ps = random_free_vectors(m, 4, seed=1)
+        p = torch.tensor(from_cases(ps, m.n_nodes, 4), device="cuda")
+        q = torch.empty_like(p)
+        fem.fem_ebe_apply(h, p, q, 4, 1.0, 1.0)
+        torch.cuda.synchronize()
+        qs = to_cases(q.cpu().numpy(), m.n_nodes, 4)
+        for c in range(4):
+            ref = (sysm.M + sysm.K) @ ps[c]
+            ref[m.fixed_dof == 1] = 0.0
+            assert np.abs(qs[c] - ref).max() <= 1e-13 * np.abs(ref).max()
+    finally:
+        fem.fem_mesh_destroy(h)

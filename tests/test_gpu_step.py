@@ -129,13 +129,23 @@ def test_step_multicase_dd_fp64_snapshots(torch_dev):
     assert it_dd.sum() < it_ab.sum(), (it_dd, it_ab)
 
 
-def test_step_mixed_precision_dd(torch_dev):
+@pytest.mark.parametrize("refresh", [200, 7])
+def test_step_mixed_precision_dd(torch_dev, refresh):
+    """FP32-inner steps keep K u, M v, K v, M a and A v by recurrences: b must still match the oracle's b
+    recomputed from the state (1e-12), with or without periodic direct refreshes of those products."""
     mesh = small_mesh(8, 7, 6)
     tp = wl.TimeParams()
     srcs = [wl.random_source(mesh, wl.rng_for(92, 0, c), f0=4.0) for c in range(3)]   # padded to 4 lanes
     opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=8,
-                                snapshot_fp32=1)
-    _run_and_check(mesh, tp, srcs, opts, 30, region_nodes=64, check_pred=False)
+                                snapshot_fp32=1, refresh_every=refresh)
+    _run_and_check(mesh, tp, srcs, opts, 40, region_nodes=64, check_pred=False)
+
+
+def test_step_mixed_precision_ab4_cfg1(torch_dev):
+    mesh = wl.config1_mesh()
+    tp = wl.TimeParams()
+    opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER)
+    _run_and_check(mesh, tp, wl.config1_sources(1), opts, 100)
 
 
 def test_step_matches_independent_oracle_run(torch_dev):
