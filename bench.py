@@ -3,7 +3,7 @@
 
 Workload (the medium configuration): a 64x64x32 hex box (h = 1/64) split into 786,432 linear tets
 (139,425 nodes, 418,275 DOF), three seeded log-normal layers, bottom fixed, 16 cases sharing the mesh
-(Ricker point sources at seeded interior nodes, f0 ~ U[2, 8]), Newmark dt = 0.01 with Rayleigh damping
+(Ricker point sources at seeded interior nodes, f0 ~ U[2, 8]), Newmark dt = 0.004 with Rayleigh damping
 (0.01, 0.001).  The solver is the FP32-inner / FP64-refined block-Jacobi PCG with the EBE product, started
 from the data-driven predictor (s = 32 stored steps, regions of 1024 nodes).  A "step" advances all 16
 cases by one time step: predictor, right-hand side, certified solve, Newmark update.  The simulation is
@@ -131,7 +131,7 @@ def workload(args, rank):
     Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
     mesh = wl.config2_mesh(Hx, Hy, Hz)
     srcs = wl.config2_sources(mesh, args.cases, first_case=rank * args.cases)
-    return mesh, srcs, wl.TimeParams(), wl.region_map(mesh, args.region_nodes)
+    return mesh, srcs, wl.config2_time_params(), wl.region_map(mesh, args.region_nodes)
 
 
 def cpu_baseline(args, mesh, srcs, tp, regions, n_case_steps=8):
@@ -220,7 +220,7 @@ def run_ours(args):
 
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER if args.precision == "mixed" else fem.FEM_FP64,
                                 predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
-                                s_max=args.s_max, snapshot_fp32=1, tol=1e-8)
+                                s_max=args.s_max, snapshot_fp32=0, tol=1e-8)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
     bt = fem.fem_batch_create(opts)
@@ -374,7 +374,7 @@ def run_kernel(args):
     torch.cuda.set_device(0)
     Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
     mesh = wl.config2_mesh(Hx, Hy, Hz)
-    tp = wl.TimeParams()
+    tp = wl.config2_time_params()
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_tune(h, args.variant, args.hex_per_tile)
     r = args.cases

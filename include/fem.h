@@ -86,9 +86,12 @@ typedef struct {
   double tol;            /* certified relative residual ||b - A x|| / ||b|| (Algorithm 1's epsilon) */
   int maxit;             /* max CG iterations per solve (inner iterations summed in FEM_FP32_INNER) */
   int s_max;             /* max stored snapshot pairs s of the data-driven predictor (<= 32) */
-  double inner_tol;      /* FEM_FP32_INNER: relative reduction asked of each inner solve */
+  double inner_tol;      /* FEM_FP32_INNER: finest relative reduction asked of one inner FP32 solve; each
+                            inner solve asks for just enough to reach tol (a tenth of tol / residual),
+                            but not less than this */
   double tau;            /* predictor column-drop threshold (relative orthogonalised norm) */
-  int snapshot_fp32;     /* 1: store predictor snapshots in FP32 (Gram accumulated in FP64) */
+  int snapshot_fp32;     /* 1: store predictor snapshots in FP32 (halves their memory; the prediction
+                            loses the small orthogonal components FP32 rounds away); 0: FP64 */
   int check_every;       /* CG iterations between host-side convergence polls (>= 1) */
   int refresh_every;     /* FEM_FP32_INNER steps: every this many steps the products K u, M v, K v, M a and
                             A v^{it-3..it} that fem_step keeps by recurrence are recomputed directly
@@ -96,8 +99,8 @@ typedef struct {
   int reserved[5];
 } fem_opts;
 
-/* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-5, tau 1e-6,
- * snapshot_fp32 1, check_every 8, refresh_every 200. */
+/* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-6, tau 1e-6,
+ * snapshot_fp32 0, check_every 8, refresh_every 200. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */

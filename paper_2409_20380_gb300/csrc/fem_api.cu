@@ -298,7 +298,7 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
   const int rpad = w->rpad;
   const Reducer red = w->red();
   const int ebe_cls = sizeof(T) == 4 ? P_EBE32 : P_EBE64;
-  CU(launch_norm_b_gated<T>(mv, rpad, b, red, sc, gate, s));
+  CU(launch_norm_b_gated<T>(mv, rpad, b, red, sc, gate, tol, s));
   w->count();
   if (zero_guess) {
     CU(cudaMemsetAsync(x, 0, sizeof(T) * (size_t)w->n, s));
@@ -357,7 +357,7 @@ static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double
   const MeshView mv = m->view();
   const int rpad = w->rpad;
   const Reducer red = w->red();
-  CU(launch_norm_b_gated<double>(mv, rpad, b, red, w->outer, nullptr, s));
+  CU(launch_norm_b_gated<double>(mv, rpad, b, red, w->outer, nullptr, o.tol, s));
   CU(launch_zero_b0_t<double>(mv, rpad, x, w->outer, s));
   w->count(2);
   const int kMaxOuter = 40;
@@ -365,7 +365,7 @@ static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double
     int pi = w->pbeg(P_EBE64, s);
     CU(ebe_product<double>(m, rpad, x, w->q, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
     w->pend(pi, s);
-    CU(launch_outer_resid(mv, rpad, b, w->q, w->r32, red, w->outer, w->n_active, o.tol, s));
+    CU(launch_outer_resid(mv, rpad, b, w->q, w->r32, red, w->outer, w->n_active, o.tol, o.inner_tol, s));
     w->count(2);
     CU(cudaMemcpyAsync(w->h_active, w->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(w->h_sc, w->outer, sizeof(CgCase) * rpad, cudaMemcpyDeviceToHost, s));
@@ -428,6 +428,8 @@ struct Group {
   int n_regions = 0;            // regions the Gram buffers were sized for
   double* gram = nullptr;
   double* wcoef = nullptr;
+  double* dpart = nullptr;
+  int n_chunks = 1;
   int* slot_lists = nullptr;    // device [2][kMaxSlots]
   int* h_slots = nullptr;       // pinned [2][kMaxSlots]
   RickerSrc* src = nullptr;
@@ -446,7 +448,7 @@ struct Group {
     for (auto& v : vh) dfree(v);
     dfree(b); dfree(x); dfree(du_ab); dfree(m_in); dfree(k_in); dfree(guess);
     if (ring) cudaFree(ring);
-    dfree(gram); dfree(wcoef); dfree(slot_lists); dfree(src); dfree(ext);
+    dfree(gram); dfree(wcoef); dfree(dpart); dfree(slot_lists); dfree(src); dfree(ext);
     dfree(Ku); dfree(Mv); dfree(Kv); dfree(Ma); dfree(qM); dfree(qK);
     for (auto& v : Av) dfree(v);
     if (h_slots) cudaFreeHost(h_slots);
@@ -508,6 +510,9 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
     const int R = std::max(1, m->n_regions);
     CHK(dalloc(&g->gram, (size_t)R * g->rpad * kMaxSlots * kMaxSlots));
     CHK(dalloc(&g->wcoef, (size_t)R * g->rpad * kMaxSlots));
+    // enough blocks for the dot/combine kernels to fill the GPU: about 4 per SM over all regions
+    g->n_chunks = std::max(1, std::min(64, (4 * 152 + R - 1) / R));
+    CHK(dalloc(&g->dpart, (size_t)R * g->n_chunks * kMaxSlots * g->rpad));
     CU(cudaMemsetAsync(g->gram, 0, sizeof(double) * (size_t)R * g->rpad * kMaxSlots * kMaxSlots, s));
   }
   CHK(dalloc(&g->slot_lists, 2 * kMaxSlots));
@@ -541,6 +546,8 @@ static PredView pred_view(const fem_batch* bt, const Group* g) {
   p.fp32 = bt->opts.snapshot_fp32;
   p.gram = g->gram;
   p.w = g->wcoef;
+  p.n_chunks = g->n_chunks;
+  p.dpart = g->dpart;
   return p;
 }
 
@@ -639,7 +646,7 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     w->count(2);
   }
   CU(launch_r0(mv, g->rpad, dt, g->b, aslot(it - 4), aslot(it - 3), aslot(it - 2), aslot(it - 1), qy, w->r32, red,
-               w->outer, w->n_active, o.tol, s));
+               w->outer, w->n_active, o.tol, o.inner_tol, s));
   CU(cudaMemcpyAsync(g->x, g->guess, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
   w->count();
   // 4. refinement passes: inner FP32 PCG (cases whose residual is above tol) + FP64 certification
@@ -668,7 +675,8 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     int pe = w->pbeg(P_EBE64, s);
     CU(launch_ebe_split(mv, g->rpad, g->x, g->qM, g->qK, s));
     w->pend(pe, s);
-    CU(launch_cert(mv, g->rpad, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol, s));
+    CU(launch_cert(mv, g->rpad, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
+                   o.inner_tol, s));
     w->count(2);
   }
   w->pend(ph, s);
@@ -790,9 +798,9 @@ void fem_opts_default(fem_opts* o) {
   o->tol = 1e-8;
   o->maxit = 5000;
   o->s_max = 32;
-  o->inner_tol = 1e-5;
+  o->inner_tol = 1e-6;
   o->tau = 1e-6;
-  o->snapshot_fp32 = 1;
+  o->snapshot_fp32 = 0;
   o->check_every = 8;
   o->refresh_every = 200;
 }

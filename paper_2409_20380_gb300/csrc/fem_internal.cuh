@@ -11,7 +11,9 @@
 
 namespace fem {
 
-constexpr int kBlock = 256;              // threads per block of the streaming kernels
+constexpr int kBlock = 256;              // threads per block of the element kernels
+constexpr int kVecBlock = 512;           // threads per block of the reducing vector kernels
+constexpr int kVecGrid = 152 * 3;        // their grid cap: few blocks keep the final reduction short
 constexpr int kMaxRpad = 32;             // max cases per multi-RHS group
 constexpr int kMaxSlots = 33;            // predictor ring: s_max + 1 <= 33
 constexpr int kMaxRedBlocks = 152 * 8;   // grid cap of reducing kernels (partials buffer rows)
@@ -61,6 +63,8 @@ struct CgCase {
   double relres0;  // relative residual of the initial guess
   int outer;       // FP64 residual evaluations (refinement passes) of the solve
   int pad_;
+  double tol2;     // squared relative tolerance of this case's (inner) solve; set when the solve starts
+  double inner_tol;  // outer state: relative reduction the next inner solve is asked for
 };
 
 // Grid-wide deterministic per-case reduction: per-block partials + last-block final sum.
@@ -119,9 +123,11 @@ cudaError_t launch_ebe_hex(const HexTiles& ht, const MeshView& m, int rpad, cons
                            const Reducer* red, CgCase* sc, double* ptq_out, const int* gate, cudaStream_t s);
 
 // CG vector kernels on [N][3][rpad] data of type T (scalars and reductions in FP64).
+// Starts a solve: bb = ||b||^2, state reset; the case's tolerance is gate[c].inner_tol when given (> 0),
+// else tol.
 template <typename T>
 cudaError_t launch_norm_b_gated(const MeshView& m, int rpad, const T* b, Reducer red, CgCase* sc,
-                                const CgCase* gate, cudaStream_t s);
+                                const CgCase* gate, double tol, cudaStream_t s);
 template <typename T>
 cudaError_t launch_resid(const MeshView& m, int rpad, const T* b, const T* q, T* x, T* r, T* z,
                          int first, Reducer red, CgCase* sc, int* n_active, double tol, int maxit,
@@ -136,7 +142,7 @@ cudaError_t launch_update(const MeshView& m, int rpad, const T* p, const T* q, T
 // Mixed precision helpers.
 cudaError_t launch_outer_resid(const MeshView& m, int rpad, const double* b, const double* q,
                                float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
-                               cudaStream_t s);
+                               double inner_max, cudaStream_t s);
 cudaError_t launch_refine_counts(const MeshView& m, int rpad, double* x, const float* d32, CgCase* outer,
                                  const CgCase* inner, cudaStream_t s);
 // x = 0 on Dirichlet DOFs and for cases with ||b|| = 0.
@@ -166,10 +172,10 @@ cudaError_t launch_rhs_incr(const MeshView& m, int rpad, double dt, double a0, d
 cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab, float* y32, cudaStream_t s);
 cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
                       const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
-                      int* n_active, double tol, cudaStream_t s);
+                      int* n_active, double tol, double inner_max, cudaStream_t s);
 cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const double* b, const double* qM,
                         const double* qK, float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
-                        cudaStream_t s);
+                        double inner_max, cudaStream_t s);
 cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, const double* du, const double* du_ab,
                                 const double* qM, const double* qK, double* u, const double* v_prev, double* a,
                                 double* v_push, double* Ku, double* Mv, double* Kv, double* Ma, double* Av_push,
@@ -191,6 +197,8 @@ struct PredView {
   int fp32;
   double* gram;            // [R][rpad][kMaxSlots][kMaxSlots]
   double* w;               // [R][rpad][kMaxSlots] coefficients in X order
+  int n_chunks;            // node-range chunks per region (blocks per region of the dot/combine kernels)
+  double* dpart;           // [R][n_chunks][kMaxSlots][rpad] partial dots
 };
 // valid_mask bit j = ring slot j holds a stored correction (64-bit: up to kMaxSlots = 33 slots).
 cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mask, cudaStream_t s);
@@ -207,12 +215,22 @@ namespace fem {
 
 __device__ __forceinline__ bool dof_free(uint8_t fm, int k) { return (fm >> k) & 1; }
 
+// Relative reduction asked of the next inner FP32 solve: just enough for one refinement pass to reach the
+// FP64 tolerance (a tenth of tol / current relative residual), but no finer than `floor` (what FP32 can
+// deliver) and at least a halving.
+__device__ __forceinline__ double inner_target(double tol, double relres, double floor) {
+  double t = relres > 0.0 ? 0.1 * tol / relres : floor;
+  if (t > 0.5) t = 0.5;
+  if (t < floor) t = floor;
+  return t;
+}
+
 // Per-case sums over the grid.  Threads hold vals[q] for case c = threadIdx.x % rpad (the grid stride of
 // every caller is a multiple of rpad).  Returns true in the last block to finish, after red.out[q*rpad+c]
 // holds the grid totals (summed in a fixed order: deterministic).
 template <int NQ>
 __device__ __forceinline__ bool block_reduce_last(double (&vals)[NQ], int rpad, const Reducer& red) {
-  __shared__ double sh[kBlock / 32][NQ][32];
+  __shared__ double sh[kVecBlock / 32][NQ][32];
   __shared__ bool am_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -236,12 +254,22 @@ __device__ __forceinline__ bool block_reduce_last(double (&vals)[NQ], int rpad, 
   if (!am_last) return false;
   __threadfence();
   double* flat = &sh[0][0][0];
-  const int S = blockDim.x / V;
+  int S = blockDim.x / V;
+  if (S * V > (kVecBlock / 32) * NQ * 32) S = (kVecBlock / 32) * NQ * 32 / V;
   if (threadIdx.x < S * V) {
     const int v = threadIdx.x % V, sl = threadIdx.x / V;
-    double acc = 0.0;
-    for (int b = sl; b < (int)gridDim.x; b += S) acc += __ldcg(red.partial + (size_t)b * V + v);
-    flat[sl * V + v] = acc;
+    // four independent chains so the L2 loads overlap; fixed assignment keeps the sum deterministic
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = sl;
+    const int nb = (int)gridDim.x;
+    for (; b + 3 * S < nb; b += 4 * S) {
+      a0 += __ldcg(red.partial + (size_t)b * V + v);
+      a1 += __ldcg(red.partial + (size_t)(b + S) * V + v);
+      a2 += __ldcg(red.partial + (size_t)(b + 2 * S) * V + v);
+      a3 += __ldcg(red.partial + (size_t)(b + 3 * S) * V + v);
+    }
+    for (; b < nb; b += S) a0 += __ldcg(red.partial + (size_t)b * V + v);
+    flat[sl * V + v] = (a0 + a1) + (a2 + a3);
   }
   __syncthreads();
   if (threadIdx.x < V) {

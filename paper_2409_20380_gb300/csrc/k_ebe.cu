@@ -121,7 +121,7 @@ cudaError_t launch_ebe_gated(const MeshView& m, int rpad, const T* pm, const T* 
   cudaError_t err = cudaMemsetAsync(q, 0, sizeof(T) * (size_t)m.N * 3 * rpad, s);
   if (err != cudaSuccess) return err;
   const int rs = log2i(rpad);
-  const int grid = grid_for(m.E << rs);
+  const int grid = grid_for(m.E << rs, red ? kVecGrid : kMaxRedBlocks);
   Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
   if (pk) {
     k_ebe_atomic<T, true, false><<<grid, kBlock, 0, s>>>(m, rpad, rs, pm, pk, q, (T)aM, (T)aK, rd, nullptr, nullptr, gate);

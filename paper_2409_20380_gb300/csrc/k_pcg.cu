@@ -13,6 +13,13 @@ template <typename T> __device__ __forceinline__ const T* binv_of(const MeshView
 template <> __device__ __forceinline__ const double* binv_of<double>(const MeshView& m) { return m.binv64; }
 template <> __device__ __forceinline__ const float* binv_of<float>(const MeshView& m) { return m.binv32; }
 
+static int vec_grid(int64_t items) {
+  int64_t g = (items + kVecBlock - 1) / kVecBlock;
+  if (g < 1) g = 1;
+  if (g > kVecGrid) g = kVecGrid;
+  return (int)g;
+}
+
 static int log2i(int r) {
   int s = 0;
   while ((1 << s) < r) ++s;
@@ -30,8 +37,8 @@ __device__ __forceinline__ void count_active(const CgCase* sc, int rpad, int* n_
 // bb = ||b||^2 over free DOFs; resets the case state.  gate (optional): a case whose gate is inactive is
 // treated as b = 0.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_norm_b(MeshView m, int rpad, int rshift, const T* __restrict__ b,
-                                                   Reducer red, CgCase* sc, const CgCase* gate) {
+__global__ void __launch_bounds__(kVecBlock, 3) k_norm_b(MeshView m, int rpad, int rshift, const T* __restrict__ b,
+                                                   Reducer red, CgCase* sc, const CgCase* gate, double tol) {
   typename Acc<T>::type acc = 0;
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -54,6 +61,8 @@ __global__ void __launch_bounds__(kBlock) k_norm_b(MeshView m, int rpad, int rsh
       s.active = 0;
       s.iters = 0;
       s.outer = 0;
+      const double t = (gate && gate[c].inner_tol > 0.0) ? gate[c].inner_tol : tol;
+      s.tol2 = t * t;
       s.status = isfinite(s.bb) ? FEM_OK : FEM_ERR_NONFINITE;
       s.phase = 0;
     }
@@ -64,18 +73,19 @@ __global__ void __launch_bounds__(kBlock) k_norm_b(MeshView m, int rpad, int rsh
 // Tail (first): start the iteration.  Tail (re-check): true-residual test of cases that stopped on the
 // recursive residual; they resume if the true residual is above tol.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_resid(MeshView m, int rpad, int rshift, const T* __restrict__ b,
+__global__ void __launch_bounds__(kVecBlock, 3) k_resid(MeshView m, int rpad, int rshift, const T* __restrict__ b,
                                                   const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
                                                   T* __restrict__ z, int first, Reducer red, CgCase* sc,
                                                   int* n_active, double tol, int maxit) {
   const T* __restrict__ bi = binv_of<T>(m);
   typename Acc<T>::type zr = 0, rr = 0;
   const int64_t total = m.N << rshift;
+  const bool zero_case = sc[(blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & (rpad - 1)].bb == 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = i >> rshift;
     const int c = (int)(i & (rpad - 1));
     const uint8_t f = m.freemask[n];
-    const bool zero_b = first && (sc[c].bb == 0.0);
+    const bool zero_b = first && zero_case;
     T rv[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -102,7 +112,7 @@ __global__ void __launch_bounds__(kBlock) k_resid(MeshView m, int rpad, int rshi
       const int c = threadIdx.x;
       CgCase& s = sc[c];
       const double zrc = red.out[c], rrc = red.out[rpad + c];
-      const double thr = tol * tol * s.bb;
+      const double thr = s.tol2 * s.bb;
       if (first) {
         s.rho = zrc;
         s.rr = rrc;
@@ -136,17 +146,17 @@ __global__ void __launch_bounds__(kBlock) k_dir(MeshView m, int rpad, int rshift
                                                 T* __restrict__ p, const CgCase* sc, const int* n_active) {
   if (*n_active == 0) return;
   const int64_t total = (m.N * 3) << rshift;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i & (rpad - 1));
-    const CgCase& s = sc[c];
-    if (!s.active) continue;
-    const T beta = (T)(s.phase ? s.beta : 0.0);
+  // the grid stride is a multiple of rpad: every thread serves one case
+  const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & (rpad - 1));
+  const CgCase s = sc[c];
+  if (!s.active) return;
+  const T beta = (T)(s.phase ? s.beta : 0.0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
-  }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_update(MeshView m, int rpad, int rshift, const T* __restrict__ p,
+__global__ void __launch_bounds__(kVecBlock, 3) k_update(MeshView m, int rpad, int rshift, const T* __restrict__ p,
                                                    const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
                                                    T* __restrict__ z, Reducer red, CgCase* sc, int* n_active,
                                                    double tol, int maxit) {
@@ -154,11 +164,11 @@ __global__ void __launch_bounds__(kBlock) k_update(MeshView m, int rpad, int rsh
   const T* __restrict__ bi = binv_of<T>(m);
   typename Acc<T>::type zr = 0, rr = 0;
   const int64_t total = m.N << rshift;
+  const T alpha = (T)sc[(blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & (rpad - 1)].alpha;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = i >> rshift;
     const int c = (int)(i & (rpad - 1));
     const uint8_t f = m.freemask[n];
-    const T alpha = (T)sc[c].alpha;
     T rv[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -197,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) k_update(MeshView m, int rpad, int rsh
         if (!isfinite(zrc) || !isfinite(rrc)) {
           s.status = FEM_ERR_NONFINITE;
           s.active = 0;
-        } else if (rrc < tol * tol * s.bb) {
+        } else if (rrc < s.tol2 * s.bb) {
           s.active = 0;
         } else if (s.iters >= maxit) {
           s.active = 0;
@@ -211,9 +221,10 @@ __global__ void __launch_bounds__(kBlock) k_update(MeshView m, int rpad, int rsh
 }
 
 // ---- mixed precision: FP64 outer residual -> FP32 inner right-hand side; FP64 refinement update ----
-__global__ void __launch_bounds__(kBlock) k_outer_resid(MeshView m, int rpad, int rshift, const double* __restrict__ b,
+__global__ void __launch_bounds__(kVecBlock, 3) k_outer_resid(MeshView m, int rpad, int rshift, const double* __restrict__ b,
                                                         const double* __restrict__ q, float* __restrict__ r32,
-                                                        Reducer red, CgCase* outer, int* n_active, double tol) {
+                                                        Reducer red, CgCase* outer, int* n_active, double tol,
+                                                        double inner_max) {
   double rr = 0.0;
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -240,6 +251,7 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(MeshView m, int rpad, in
       s.outer += 1;
       if (!isfinite(rrc)) s.status = FEM_ERR_NONFINITE;
       s.active = (s.status == FEM_OK && s.bb > 0.0 && rrc >= tol * tol * s.bb) ? 1 : 0;
+      s.inner_tol = inner_target(tol, s.relres, inner_max);
     }
     __syncthreads();
     count_active(outer, rpad, n_active);
@@ -284,9 +296,9 @@ template cudaError_t launch_zero_b0_t<float>(const MeshView&, int, float*, const
 
 template <typename T>
 cudaError_t launch_norm_b_gated(const MeshView& m, int rpad, const T* b, Reducer red, CgCase* sc,
-                                const CgCase* gate, cudaStream_t s) {
+                                const CgCase* gate, double tol, cudaStream_t s) {
   const int rs = log2i(rpad);
-  k_norm_b<T><<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, b, red, sc, gate);
+  k_norm_b<T><<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, b, red, sc, gate, tol);
   return cudaGetLastError();
 }
 
@@ -294,7 +306,7 @@ template <typename T>
 cudaError_t launch_resid(const MeshView& m, int rpad, const T* b, const T* q, T* x, T* r, T* z, int first,
                          Reducer red, CgCase* sc, int* n_active, double tol, int maxit, cudaStream_t s) {
   const int rs = log2i(rpad);
-  k_resid<T><<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, b, q, x, r, z, first, red, sc, n_active, tol, maxit);
+  k_resid<T><<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, b, q, x, r, z, first, red, sc, n_active, tol, maxit);
   return cudaGetLastError();
 }
 
@@ -310,14 +322,15 @@ template <typename T>
 cudaError_t launch_update(const MeshView& m, int rpad, const T* p, const T* q, T* x, T* r, T* z, Reducer red,
                           CgCase* sc, int* n_active, double tol, int maxit, cudaStream_t s) {
   const int rs = log2i(rpad);
-  k_update<T><<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, p, q, x, r, z, red, sc, n_active, tol, maxit);
+  k_update<T><<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, p, q, x, r, z, red, sc, n_active, tol, maxit);
   return cudaGetLastError();
 }
 
 cudaError_t launch_outer_resid(const MeshView& m, int rpad, const double* b, const double* q, float* r32,
-                               Reducer red, CgCase* outer, int* n_active, double tol, cudaStream_t s) {
+                               Reducer red, CgCase* outer, int* n_active, double tol, double inner_max,
+                               cudaStream_t s) {
   const int rs = log2i(rpad);
-  k_outer_resid<<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, b, q, r32, red, outer, n_active, tol);
+  k_outer_resid<<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, b, q, r32, red, outer, n_active, tol, inner_max);
   return cudaGetLastError();
 }
 
@@ -330,7 +343,7 @@ cudaError_t launch_refine_counts(const MeshView& m, int rpad, double* x, const f
 
 #define INST(T)                                                                                                   \
   template cudaError_t launch_norm_b_gated<T>(const MeshView&, int, const T*, Reducer, CgCase*, const CgCase*,    \
-                                              cudaStream_t);                                                      \
+                                              double, cudaStream_t);                                              \
   template cudaError_t launch_resid<T>(const MeshView&, int, const T*, const T*, T*, T*, T*, int, Reducer,        \
                                        CgCase*, int*, double, int, cudaStream_t);                                 \
   template cudaError_t launch_dir_gated<T>(const MeshView&, int, const T*, T*, const CgCase*, const int*,         \

@@ -5,6 +5,13 @@
 
 namespace fem {
 
+static int vec_grid(int64_t items) {
+  int64_t g = (items + kVecBlock - 1) / kVecBlock;
+  if (g < 1) g = 1;
+  if (g > kVecGrid) g = kVecGrid;
+  return (int)g;
+}
+
 static int log2i(int r) {
   int s = 0;
   while ((1 << s) < r) ++s;
@@ -102,15 +109,19 @@ template <> struct PredAcc<float> {   // compensated FP32 summation of FP32 prod
   __device__ __forceinline__ double get() const { return (double)s - (double)comp; }
 };
 
+// Region R is split into p.n_chunks node ranges; block (R, k) accumulates, for each valid slot j, the
+// partial dot of slot j with the newest slot over its range, per case: dpart[R][k][j][c].
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_pred_dots(PredView p, int slot_new, uint64_t valid_mask) {
-  const int R = blockIdx.x;
+  const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
+  const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
+  const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
   const int rpad = p.rpad;
   const T* ring = (const T*)p.ring;
   const T* xn = ring + (int64_t)slot_new * p.slot_stride;
   PredAcc<T> acc[kMaxSlots];
-  const int64_t base = lo * 3 * rpad, cnt = (hi - lo) * 3 * rpad;
+  const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
   for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     const T x = xn[base + i];
 #pragma unroll
@@ -119,6 +130,7 @@ __global__ void __launch_bounds__(kBlock) k_pred_dots(PredView p, int slot_new, 
   }
   __shared__ double sh[kBlock / 32][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* out = p.dpart + ((int64_t)R * p.n_chunks + k) * kMaxSlots * rpad;
   for (int j = 0; j < kMaxSlots; ++j) {
     if (!((valid_mask >> j) & 1ull)) continue;
     double v = acc[j].get();
@@ -128,11 +140,23 @@ __global__ void __launch_bounds__(kBlock) k_pred_dots(PredView p, int slot_new, 
     if (threadIdx.x < rpad) {
       double s = 0.0;
       for (int w = 0; w < nw; ++w) s += sh[w][threadIdx.x];
-      double* G = p.gram + ((int64_t)R * rpad + threadIdx.x) * kMaxSlots * kMaxSlots;
-      G[slot_new * kMaxSlots + j] = s;
-      G[j * kMaxSlots + slot_new] = s;
+      out[j * rpad + threadIdx.x] = s;
     }
     __syncthreads();
+  }
+}
+
+// Sums the chunk partials in chunk order and writes row/column slot_new of each (region, case) Gram.
+__global__ void k_pred_dots_finish(PredView p, int slot_new, uint64_t valid_mask) {
+  const int R = blockIdx.x;
+  for (int t = threadIdx.x; t < kMaxSlots * p.rpad; t += blockDim.x) {
+    const int j = t / p.rpad, c = t % p.rpad;
+    if (!((valid_mask >> j) & 1ull)) continue;
+    double s = 0.0;
+    for (int k = 0; k < p.n_chunks; ++k) s += p.dpart[(((int64_t)R * p.n_chunks + k) * kMaxSlots + j) * p.rpad + c];
+    double* G = p.gram + ((int64_t)R * p.rpad + c) * kMaxSlots * kMaxSlots;
+    G[slot_new * kMaxSlots + j] = s;
+    G[j * kMaxSlots + slot_new] = s;
   }
 }
 
@@ -195,8 +219,10 @@ __global__ void k_pred_solve(PredView p, const int* __restrict__ x_slots, int n,
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* __restrict__ y_slots, int n,
                                                          double* __restrict__ y_out) {
-  const int R = blockIdx.x;
+  const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
+  const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
+  const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
   const int rpad = p.rpad;
   const T* ring = (const T*)p.ring;
   const int c = threadIdx.x & (rpad - 1);
@@ -208,7 +234,7 @@ __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* 
     wl[a] = a < n ? (T)w[a] : (T)0;
     off[a] = a < n ? (int64_t)y_slots[a] * p.slot_stride : 0;
   }
-  const int64_t base = lo * 3 * rpad, cnt = (hi - lo) * 3 * rpad;
+  const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
   for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     T s = 0;
 #pragma unroll
@@ -276,11 +302,11 @@ __global__ void k_corr_f32(int64_t n, const double* __restrict__ guess, const do
 // A du_AB = dt/24 (-9 Av^{it-4} + 37 Av^{it-3} - 59 Av^{it-2} + 55 Av^{it-1}) exact (FP64 recurrences)
 // and A y from the FP32 product of the small data-driven correction (qy, nullable).  Writes r32 and
 // starts the outer (FP64) iteration state.
-__global__ void __launch_bounds__(kBlock) k_r0(MeshView m, int rpad, int rshift, double h, const double* __restrict__ b,
+__global__ void __launch_bounds__(kVecBlock, 3) k_r0(MeshView m, int rpad, int rshift, double h, const double* __restrict__ b,
                                                const double* __restrict__ Av4, const double* __restrict__ Av3,
                                                const double* __restrict__ Av2, const double* __restrict__ Av1,
                                                const float* __restrict__ qy, float* __restrict__ r32, Reducer red,
-                                               CgCase* outer, int* n_active, double tol) {
+                                               CgCase* outer, int* n_active, double tol, double inner_max) {
   double bb = 0.0, rr = 0.0;
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -318,6 +344,7 @@ __global__ void __launch_bounds__(kBlock) k_r0(MeshView m, int rpad, int rshift,
       s.status = (isfinite(bbc) && isfinite(rrc)) ? FEM_OK : FEM_ERR_NONFINITE;
       // estimate only: the certificate is the FP64 residual computed after the solve
       s.active = (s.status == FEM_OK && bbc > 0.0 && rrc >= tol * tol * bbc) ? 1 : 0;
+      s.inner_tol = inner_target(tol, s.relres, inner_max);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -330,10 +357,10 @@ __global__ void __launch_bounds__(kBlock) k_r0(MeshView m, int rpad, int rshift,
 
 // Certified FP64 residual from the split products:  r = b - (cM qM + cK qK);  r32 = float(r) for the next
 // inner solve; cases at or above tol stay active.
-__global__ void __launch_bounds__(kBlock) k_cert(MeshView m, int rpad, int rshift, double cM, double cK,
+__global__ void __launch_bounds__(kVecBlock, 3) k_cert(MeshView m, int rpad, int rshift, double cM, double cK,
                                                  const double* __restrict__ b, const double* __restrict__ qM,
                                                  const double* __restrict__ qK, float* __restrict__ r32, Reducer red,
-                                                 CgCase* outer, int* n_active, double tol) {
+                                                 CgCase* outer, int* n_active, double tol, double inner_max) {
   double rr = 0.0;
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -359,6 +386,7 @@ __global__ void __launch_bounds__(kBlock) k_cert(MeshView m, int rpad, int rshif
       s.outer += 1;
       if (!isfinite(rrc)) s.status = FEM_ERR_NONFINITE;
       s.active = (s.status == FEM_OK && s.bb > 0.0 && rrc >= tol * tol * s.bb) ? 1 : 0;
+      s.inner_tol = inner_target(tol, s.relres, inner_max);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -470,18 +498,19 @@ cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab,
 
 cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
                       const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
-                      int* n_active, double tol, cudaStream_t s) {
+                      int* n_active, double tol, double inner_max, cudaStream_t s) {
   const int rs = log2i(rpad);
-  k_r0<<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer,
-                                                n_active, tol);
+  k_r0<<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer,
+                                                n_active, tol, inner_max);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const double* b, const double* qM,
                         const double* qK, float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
-                        cudaStream_t s) {
+                        double inner_max, cudaStream_t s) {
   const int rs = log2i(rpad);
-  k_cert<<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, cM, cK, b, qM, qK, r32, red, outer, n_active, tol);
+  k_cert<<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, cM, cK, b, qM, qK, r32, red, outer, n_active, tol,
+                                                inner_max);
   return cudaGetLastError();
 }
 
@@ -500,10 +529,14 @@ cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, cons
 
 cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mask, cudaStream_t s) {
   if (p.n_regions == 0) return cudaSuccess;
+  const int grid = p.n_regions * p.n_chunks;
   if (p.fp32)
-    k_pred_dots<float><<<p.n_regions, kBlock, 0, s>>>(p, slot_new, valid_mask);
+    k_pred_dots<float><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask);
   else
-    k_pred_dots<double><<<p.n_regions, kBlock, 0, s>>>(p, slot_new, valid_mask);
+    k_pred_dots<double><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_pred_dots_finish<<<p.n_regions, 256, 0, s>>>(p, slot_new, valid_mask);
   return cudaGetLastError();
 }
 
@@ -516,10 +549,11 @@ cudaError_t launch_pred_solve(const PredView& p, const int* x_slots, int n_pairs
 
 cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out, cudaStream_t s) {
   if (p.n_regions == 0 || n_pairs <= 0) return cudaSuccess;
+  const int grid = p.n_regions * p.n_chunks;
   if (p.fp32)
-    k_pred_combine<float><<<p.n_regions, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out);
+    k_pred_combine<float><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out);
   else
-    k_pred_combine<double><<<p.n_regions, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out);
+    k_pred_combine<double><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out);
   return cudaGetLastError();
 }
 

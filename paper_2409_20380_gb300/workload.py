@@ -210,6 +210,13 @@ def config2_mesh(Hx=64, Hy=64, Hz=32, mesh_id=0, h=1.0 / 64) -> Mesh:
                         rng=rng_for(2, mesh_id, 0, 1))
 
 
+def config2_time_params() -> TimeParams:
+    """dt = 0.004 for the h = 1/64 meshes: S-wave Courant number c_s dt / h = 0.36-0.7 and 12-30 steps per
+    period over the sources' band, the regime of the paper's runs (dt = 0.005 with 2.5 m elements), where the
+    Adams-Bashforth initial error is O(1e-3).  Damping as in the unit-box configuration."""
+    return TimeParams(dt=0.004, a0=0.01, a1=0.001)
+
+
 def config2_sources(mesh: Mesh, n_cases: int = 16, config: int = 2, first_case: int = 0):
     return [random_source(mesh, rng_for(config, 0, first_case + c, 2)) for c in range(n_cases)]
 
