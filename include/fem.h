@@ -96,11 +96,14 @@ typedef struct {
   int refresh_every;     /* FEM_FP32_INNER steps: every this many steps the products K u, M v, K v, M a and
                             A v^{it-3..it} that fem_step keeps by recurrence are recomputed directly
                             (0 = 200) */
-  int reserved[5];
+  int cert_df;           /* FEM_FP32_INNER steps: 1 = the certification product runs in double-float
+                            arithmetic (FP32 pairs, 48-bit significand; the certified residual is exact to
+                            ~1e-12 of ||b||), 0 = native FP64 */
+  int reserved[4];
 } fem_opts;
 
 /* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-6, tau 1e-6,
- * snapshot_fp32 0, check_every 8, refresh_every 200. */
+ * snapshot_fp32 0, check_every 8, refresh_every 200, cert_df 0. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */

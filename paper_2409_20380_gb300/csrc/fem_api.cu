@@ -227,6 +227,7 @@ struct fem_mesh {
   double* lmr = nullptr;
   double* rec64 = nullptr;
   float* rec32 = nullptr;
+  float* rec_df = nullptr;         // [E][12][2] (hi, lo) split of rec64 for double-float products
   double* D = nullptr;
   double* binv64 = nullptr;
   float* binv32 = nullptr;
@@ -244,7 +245,7 @@ struct fem_mesh {
   int hex_per_tile = 0;            // 0 auto
   MeshView view() const { return MeshView{N, E, conn, rec64, rec32, binv64, binv32, fm}; }
   ~fem_mesh() {
-    dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(D);
+    dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(rec_df); dfree(D);
     dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi);
     for (auto* w : ws) delete w;
     for (void* b : tile_bufs) cudaFree(b);
@@ -673,7 +674,10 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
       break;
     }
     int pe = w->pbeg(P_EBE64, s);
-    CU(launch_ebe_split(mv, g->rpad, g->x, g->qM, g->qK, s));
+    if (o.cert_df)
+      CU(launch_ebe_split_df(mv, m->rec_df, g->rpad, g->x, g->qM, g->qK, s));
+    else
+      CU(launch_ebe_split(mv, g->rpad, g->x, g->qM, g->qK, s));
     w->pend(pe, s);
     CU(launch_cert(mv, g->rpad, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
                    o.inner_tol, s));
@@ -803,6 +807,7 @@ void fem_opts_default(fem_opts* o) {
   o->snapshot_fp32 = 0;
   o->check_every = 8;
   o->refresh_every = 200;
+  o->cert_df = 0;
 }
 
 fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
@@ -842,6 +847,7 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
   if ((st = dalloc(&m->lmr, 3 * n_mat)) != FEM_OK) return bail(st);
   if ((st = dalloc(&m->rec64, kRec * n_elems)) != FEM_OK) return bail(st);
   if ((st = dalloc(&m->rec32, kRec * n_elems)) != FEM_OK) return bail(st);
+  if ((st = dalloc(&m->rec_df, 2 * kRec * n_elems)) != FEM_OK) return bail(st);
   if ((st = dalloc(&m->D, 6 * n_nodes)) != FEM_OK) return bail(st);
   if ((st = dalloc(&m->binv64, 6 * n_nodes)) != FEM_OK) return bail(st);
   if ((st = dalloc(&m->binv32, 6 * n_nodes)) != FEM_OK) return bail(st);
@@ -861,6 +867,7 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
   cu(cudaMemsetAsync(m->D, 0, sizeof(double) * 6 * n_nodes, s));
   cu(launch_elem_setup(n_elems, n_nodes, m->xyz, m->conn, m->mat, n_mat, m->lmr, m->rec64, m->rec32, d_err, s));
   cu(launch_diag_blocks(m->view(), m->cM, m->cK, m->D, s));
+  cu(launch_split_records(n_elems, m->rec64, m->rec_df, s));
   cu(launch_binv(n_nodes, m->D, m->fm, m->binv64, m->binv32, d_err, s));
   int h_err = 0;
   cu(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));

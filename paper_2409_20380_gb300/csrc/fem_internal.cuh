@@ -184,6 +184,10 @@ cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, 
                          cudaStream_t s);
 // Split FP64 product: qM = M p and qK = K p in one pass (generic element kernel).
 cudaError_t launch_ebe_split(const MeshView& m, int rpad, const double* p, double* qM, double* qK, cudaStream_t s);
+// The same product in double-float arithmetic from (hi, lo) FP32 records rec_df [E][12][2].
+cudaError_t launch_ebe_split_df(const MeshView& m, const float* rec_df, int rpad, const double* p, double* qM,
+                                double* qK, cudaStream_t s);
+cudaError_t launch_split_records(int64_t E, const double* rec64, float* rec_df, cudaStream_t s);
 
 // Predictor (regions are node ranges [reg_lo[R], reg_hi[R])).
 struct PredView {

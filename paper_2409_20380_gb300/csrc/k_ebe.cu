@@ -406,4 +406,126 @@ cudaError_t launch_ebe_split(const MeshView& m, int rpad, const double* p, doubl
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------------------
+// Split product in double-float arithmetic (value = hi + lo, two FP32 numbers; 48-bit significand).
+// GB300 issues FP32 at 64x its FP64 rate, so the certification product (q = M p and K p, needed to ~1e-12
+// of ||b||) runs as error-free FP32 transforms instead of FP64 instructions.  Records are split once into
+// (hi, lo) pairs; p is split on load; element contributions are converted back to FP64 and scattered with
+// FP64 atomics.  __fadd_rn/__fmul_rn keep the transforms from being contracted into FMAs.
+// ------------------------------------------------------------------------------------------------------
+struct dfl {
+  float hi, lo;
+};
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dfl df_fast(float a, float b) {   // requires |a| >= |b| (or a == 0)
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const dfl s = df_two_sum(a.hi, b.hi);
+  const float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return df_fast(s.hi, e);
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast(p, e);
+}
+__device__ __forceinline__ dfl df_from(double x) {
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+
+__global__ void __launch_bounds__(kBlock) k_ebe_split_df(MeshView m, const float* __restrict__ rec_df, int rpad,
+                                                         int rshift, const double* __restrict__ p,
+                                                         double* __restrict__ qM, double* __restrict__ qK) {
+  const int64_t total = m.E << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const int4 cn = __ldg(m.conn + e);
+    const int64_t nd[4] = {cn.x, cn.y, cn.z, cn.w};
+    const float* re = rec_df + e * 24;
+    dfl g[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) g[j] = {__ldg(re + 2 * j), __ldg(re + 2 * j + 1)};
+    dfl P[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) P[a][k] = df_from(p[(nd[a] * 3 + k) * rpad + c]);
+    dfl G[3][3];
+#pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2) {
+      const dfl d1 = df_sub(P[1][i2], P[0][i2]), d2 = df_sub(P[2][i2], P[0][i2]), d3 = df_sub(P[3][i2], P[0][i2]);
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        G[i2][j] = df_add(df_add(df_mul(d1, g[j]), df_mul(d2, g[3 + j])), df_mul(d3, g[6 + j]));
+    }
+    const dfl lam = g[9], mu = g[10], ms = g[11];
+    const dfl tr = df_add(df_add(G[0][0], G[1][1]), G[2][2]);
+    const dfl ltr = df_mul(lam, tr);
+    const dfl mu2 = df_add(mu, mu);
+    dfl S[3][3];
+#pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2) S[i2][i2] = df_add(ltr, df_mul(mu2, G[i2][i2]));
+    S[0][1] = S[1][0] = df_mul(mu, df_add(G[0][1], G[1][0]));
+    S[0][2] = S[2][0] = df_mul(mu, df_add(G[0][2], G[2][0]));
+    S[1][2] = S[2][1] = df_mul(mu, df_add(G[1][2], G[2][1]));
+    dfl F[4][3];
+#pragma unroll
+    for (int b = 1; b < 4; ++b)
+#pragma unroll
+      for (int i2 = 0; i2 < 3; ++i2)
+        F[b][i2] = df_add(df_add(df_mul(S[i2][0], g[(b - 1) * 3]), df_mul(S[i2][1], g[(b - 1) * 3 + 1])),
+                          df_mul(S[i2][2], g[(b - 1) * 3 + 2]));
+#pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2) F[0][i2] = df_neg(df_add(df_add(F[1][i2], F[2][i2]), F[3][i2]));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const dfl sum = df_add(df_add(P[0][k], P[1][k]), df_add(P[2][k], P[3][k]));
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        atomicAdd(qK + (nd[a] * 3 + k) * rpad + c, df_to(F[a][k]));
+        atomicAdd(qM + (nd[a] * 3 + k) * rpad + c, df_to(df_mul(ms, df_add(P[a][k], sum))));
+      }
+    }
+  }
+}
+
+__global__ void k_split_records(int64_t n, const double* __restrict__ rec64, float* __restrict__ rec_df) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = rec64[i];
+    const float hi = (float)x;
+    rec_df[2 * i] = hi;
+    rec_df[2 * i + 1] = (float)(x - (double)hi);
+  }
+}
+
+cudaError_t launch_split_records(int64_t E, const double* rec64, float* rec_df, cudaStream_t s) {
+  k_split_records<<<grid_for(E * kRec, 152 * 16), kBlock, 0, s>>>(E * kRec, rec64, rec_df);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ebe_split_df(const MeshView& m, const float* rec_df, int rpad, const double* p, double* qM,
+                                double* qK, cudaStream_t s) {
+  const size_t bytes = sizeof(double) * (size_t)m.N * 3 * rpad;
+  cudaError_t err = cudaMemsetAsync(qM, 0, bytes, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(qK, 0, bytes, s);
+  if (err != cudaSuccess) return err;
+  const int rs = log2i(rpad);
+  k_ebe_split_df<<<grid_for(m.E << rs), kBlock, 0, s>>>(m, rec_df, rpad, rs, p, qM, qK);
+  return cudaGetLastError();
+}
+
 }  // namespace fem

@@ -162,60 +162,67 @@ __global__ void k_pred_dots_finish(PredView p, int slot_new, uint64_t valid_mask
 
 // Per (region, case): least-squares coefficients w of the query (newest slot) on the X slots, by a
 // pivot-free Cholesky of the Gram with the column-drop rule  pivot <= tau^2 G_jj  (the squared form of
-// the modified Gram-Schmidt test ||v_j|| <= tau ||x_j||), then forward/back substitution.
+// the modified Gram-Schmidt test ||v_j|| <= tau ||x_j||), then forward/back substitution.  One warp: lane i
+// owns row i; rows padded to an odd length of doubles to spread shared-memory banks.
 __global__ void k_pred_solve(PredView p, const int* __restrict__ x_slots, int n, int slot_new, double tau) {
   const int R = blockIdx.x / p.rpad, c = blockIdx.x % p.rpad;
   const int lane = threadIdx.x;
-  __shared__ double L[kMaxSlots][kMaxSlots + 1];
-  __shared__ double rhs[kMaxSlots], y[kMaxSlots], diag0[kMaxSlots];
-  __shared__ int keep[kMaxSlots];
-  __shared__ int xs[kMaxSlots];
+  constexpr int LD = kMaxSlots;                 // 33 doubles per row
+  __shared__ double L[kMaxSlots * LD];
+  __shared__ double dg[kMaxSlots];
   const double* G = p.gram + ((int64_t)R * p.rpad + c) * kMaxSlots * kMaxSlots;
-  if (lane < n) xs[lane] = x_slots[lane];
-  __syncwarp();
-  for (int i = lane; i < n * n; i += 32) {
-    const int a = i / n, b = i % n;
-    L[a][b] = G[xs[a] * kMaxSlots + xs[b]];
+  const int xi = lane < n ? x_slots[lane] : 0;
+  for (int i = 0; i < n; ++i) {
+    const int xs_i = __shfl_sync(0xffffffffu, xi, i);
+    if (lane < n) L[i * LD + lane] = G[xs_i * kMaxSlots + xi];
   }
-  if (lane < n) {
-    rhs[lane] = G[xs[lane] * kMaxSlots + slot_new];
-    diag0[lane] = G[xs[lane] * kMaxSlots + xs[lane]];
-  }
+  double rhs = lane < n ? G[xi * kMaxSlots + slot_new] : 0.0;
+  const double d0 = lane < n ? G[xi * kMaxSlots + xi] : 0.0;
   __syncwarp();
+  // right-looking Cholesky: column j, then lanes i > j update their rows
   for (int j = 0; j < n; ++j) {
-    if (lane == 0) {
-      double s = L[j][j];
-      for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-      const bool kp = diag0[j] > 0.0 && s > tau * tau * diag0[j] && isfinite(s);
-      keep[j] = kp;
-      L[j][j] = kp ? sqrt(s) : 0.0;
+    const double djj = L[j * LD + j];
+    const double d0j = __shfl_sync(0xffffffffu, d0, j);
+    const bool keep = d0j > 0.0 && djj > tau * tau * d0j && isfinite(djj);
+    const double piv = keep ? sqrt(djj) : 0.0;
+    __syncwarp();
+    double lij = 0.0;
+    if (lane > j && lane < n) {
+      lij = keep ? L[lane * LD + j] / piv : 0.0;
+      L[lane * LD + j] = lij;
+    }
+    if (lane == j) {
+      L[j * LD + j] = piv;
+      dg[j] = keep ? 1.0 : 0.0;
     }
     __syncwarp();
-    const bool kp = keep[j];
-    for (int i = j + 1 + lane; i < n; i += 32) {
-      double s = L[i][j];
-      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-      L[i][j] = kp ? s / L[j][j] : 0.0;
-    }
+    if (lane > j && lane < n && keep)
+      for (int k2 = j + 1; k2 <= lane; ++k2) L[lane * LD + k2] -= lij * L[k2 * LD + j];
     __syncwarp();
   }
-  if (lane == 0) {
-    for (int i = 0; i < n; ++i) {
-      double s = rhs[i];
-      for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-      y[i] = keep[i] ? s / L[i][i] : 0.0;
-    }
-    double* w = p.w + ((int64_t)R * p.rpad + c) * kMaxSlots;
-    for (int i = n - 1; i >= 0; --i) {
-      double s = y[i];
-      for (int k = i + 1; k < n; ++k) s -= L[k][i] * w[k];
-      w[i] = keep[i] ? s / L[i][i] : 0.0;
-    }
-    for (int i = n; i < kMaxSlots; ++i) w[i] = 0.0;
+  // forward substitution L y = rhs (column sweep), dropped columns give 0
+  double y = rhs;
+  for (int j = 0; j < n; ++j) {
+    const double yj_raw = __shfl_sync(0xffffffffu, y, j);
+    const bool keep = dg[j] != 0.0;
+    const double yj = keep ? yj_raw / L[j * LD + j] : 0.0;
+    if (lane == j) y = yj;
+    if (lane > j && lane < n) y -= L[lane * LD + j] * yj;
   }
+  // back substitution L^T w = y (row sweep from the bottom)
+  double w = y;
+  for (int j = n - 1; j >= 0; --j) {
+    const double wj_raw = __shfl_sync(0xffffffffu, w, j);
+    const bool keep = dg[j] != 0.0;
+    const double wj = keep ? wj_raw / L[j * LD + j] : 0.0;
+    if (lane == j) w = wj;
+    if (lane < j) w -= L[j * LD + lane] * wj;
+  }
+  double* wo = p.w + ((int64_t)R * p.rpad + c) * kMaxSlots;
+  wo[lane] = lane < n ? w : 0.0;
+  if (lane == 0) wo[32] = 0.0;
 }
 
-// y_out += sum_a w_a Y_a over region nodes (Y_a = ring slot y_slots[a]).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* __restrict__ y_slots, int n,
                                                          double* __restrict__ y_out) {
@@ -225,22 +232,29 @@ __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* 
   const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
   const int rpad = p.rpad;
   const T* ring = (const T*)p.ring;
-  const int c = threadIdx.x & (rpad - 1);
-  const double* w = p.w + ((int64_t)R * rpad + c) * kMaxSlots;
-  T wl[kMaxSlots];
-  int64_t off[kMaxSlots];
-#pragma unroll
-  for (int a = 0; a < kMaxSlots; ++a) {
-    wl[a] = a < n ? (T)w[a] : (T)0;
-    off[a] = a < n ? (int64_t)y_slots[a] * p.slot_stride : 0;
+  // coefficients [a][case] and slot offsets in shared memory (registers stay free for the loads)
+  __shared__ T sw[kMaxSlots * kMaxRpad];
+  __shared__ int64_t soff[kMaxSlots];
+  for (int t = threadIdx.x; t < n * rpad; t += blockDim.x) {
+    const int a = t / rpad, c = t % rpad;
+    sw[t] = (T)p.w[((int64_t)R * rpad + c) * kMaxSlots + a];
   }
+  for (int a = threadIdx.x; a < n; a += blockDim.x) soff[a] = (int64_t)y_slots[a] * p.slot_stride;
+  __syncthreads();
+  const int c = threadIdx.x & (rpad - 1);
   const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
   for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-    T s = 0;
-#pragma unroll
-    for (int a = 0; a < kMaxSlots; ++a)
-      if (a < n) s += wl[a] * ring[off[a] + base + i];
-    y_out[base + i] += (double)s;
+    const int64_t gi = base + i;
+    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    int a = 0;
+    for (; a + 3 < n; a += 4) {
+      s0 += sw[a * rpad + c] * ring[soff[a] + gi];
+      s1 += sw[(a + 1) * rpad + c] * ring[soff[a + 1] + gi];
+      s2 += sw[(a + 2) * rpad + c] * ring[soff[a + 2] + gi];
+      s3 += sw[(a + 3) * rpad + c] * ring[soff[a + 3] + gi];
+    }
+    for (; a < n; ++a) s0 += sw[a * rpad + c] * ring[soff[a] + gi];
+    y_out[gi] += (double)((s0 + s1) + (s2 + s3));
   }
 }
 

@@ -25,7 +25,7 @@ def torch_dev():
     return torch
 
 
-def _run_and_check(mesh, tp, sources, opts, n_steps, region_nodes=None, check_pred=True):
+def _run_and_check(mesh, tp, sources, opts, n_steps, region_nodes=None, check_pred=True, b_tol=1e-12):
     sysm, A = oracle.build_system(mesh, tp)
     N = mesh.n_nodes
     h = fem.fem_mesh_create(mesh, tp)
@@ -58,7 +58,7 @@ def _run_and_check(mesh, tp, sources, opts, n_steps, region_nodes=None, check_pr
                 b_ref = oracle.newmark_rhs(sysm, f, S["u"], S["v"], S["a"])
                 b_ref[mesh.fixed_dof == 1] = 0.0
                 nb = np.linalg.norm(b_ref)
-                assert np.linalg.norm(b - b_ref) <= 1e-12 * nb, (it, c)
+                assert np.linalg.norm(b - b_ref) <= b_tol * nb, (it, c, np.linalg.norm(b - b_ref) / nb)
                 cert = np.linalg.norm(b_ref[sysm.free] - A @ du[sysm.free]) / nb
                 assert cert < opts.tol, (it, c, cert)
                 assert abs(relres[c] - cert) <= 1e-3 * opts.tol + 1e-6 * cert
@@ -129,23 +129,34 @@ def test_step_multicase_dd_fp64_snapshots(torch_dev):
     assert it_dd.sum() < it_ab.sum(), (it_dd, it_ab)
 
 
-@pytest.mark.parametrize("refresh", [200, 7])
-def test_step_mixed_precision_dd(torch_dev, refresh):
+@pytest.mark.parametrize("refresh,cert_df", [(200, 0), (7, 0), (200, 1), (7, 1)])
+def test_step_mixed_precision_dd(torch_dev, refresh, cert_df):
     """FP32-inner steps keep K u, M v, K v, M a and A v by recurrences: b must still match the oracle's b
-    recomputed from the state (1e-12), with or without periodic direct refreshes of those products."""
+    recomputed from the state, with or without periodic direct refreshes of those products.  With native
+    FP64 certification products the bound is FP64 rounding (1e-12); with double-float products (2^-47
+    relative error per operation, accumulated over 40 recurrence steps) it is 1e-11."""
     mesh = small_mesh(8, 7, 6)
     tp = wl.TimeParams()
     srcs = [wl.random_source(mesh, wl.rng_for(92, 0, c), f0=4.0) for c in range(3)]   # padded to 4 lanes
     opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=8,
-                                snapshot_fp32=1, refresh_every=refresh)
-    _run_and_check(mesh, tp, srcs, opts, 40, region_nodes=64, check_pred=False)
+                                snapshot_fp32=1, refresh_every=refresh, cert_df=cert_df)
+    _run_and_check(mesh, tp, srcs, opts, 40, region_nodes=64, check_pred=False, b_tol=1e-11 if cert_df else 1e-12)
 
 
 def test_step_mixed_precision_ab4_cfg1(torch_dev):
     mesh = wl.config1_mesh()
     tp = wl.TimeParams()
-    opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER)
+    opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, cert_df=0)
     _run_and_check(mesh, tp, wl.config1_sources(1), opts, 100)
+
+
+def test_step_mixed_precision_dd_medium_dt(torch_dev):
+    """The medium workload's time step (dt = 0.004) with FP64 snapshots and double-float certification."""
+    mesh = small_mesh(10, 8, 6, h=1.0 / 64)
+    tp = wl.config2_time_params()
+    srcs = [wl.random_source(mesh, wl.rng_for(93, 0, c)) for c in range(4)]
+    opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=16, cert_df=1)
+    _run_and_check(mesh, tp, srcs, opts, 60, region_nodes=64, check_pred=False, b_tol=1e-11)
 
 
 def test_step_matches_independent_oracle_run(torch_dev):
