@@ -99,11 +99,14 @@ typedef struct {
   int cert_df;           /* FEM_FP32_INNER steps: 1 = the certification product runs in double-float
                             arithmetic (FP32 pairs, 48-bit significand; the certified residual is exact to
                             ~1e-12 of ||b||), 0 = native FP64 */
-  int reserved[4];
+  int fuse_meshes;       /* 1 = solve all cases of the batch as one fused system (each case on its own mesh
+                            copy; meshes of different sizes; one set of launches for all; at most 128 cases;
+                            FEM_FP32_INNER only); 0 = one multi-RHS system per mesh */
+  int reserved[3];
 } fem_opts;
 
 /* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-6, tau 1e-6,
- * snapshot_fp32 0, check_every 8, refresh_every 200, cert_df 0. */
+ * snapshot_fp32 0, check_every 8, refresh_every 200, cert_df 0, fuse_meshes 0. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */
@@ -246,8 +249,9 @@ fem_status fem_case_get(fem_batch* b, int case_id, int what, double* dst, int on
  */
 fem_status fem_batch_set_loads(fem_batch* b, const double* loads);
 
-/* Copies field `what` (FEM_FIELD_*) of every case to dst [n_cases][n_nodes][3] (device memory if
- * on_device != 0, else host memory; a host copy synchronises the batch stream). */
+/* Copies field `what` (FEM_FIELD_*) of every case to dst: the cases' [n_nodes][3] fields one after the
+ * other in case order (n_nodes of each case's mesh; [n_cases][n_nodes][3] when all share one mesh).
+ * Device memory if on_device != 0, else host memory (a host copy synchronises the batch stream). */
 fem_status fem_batch_get_field(fem_batch* b, int what, double* dst, int on_device);
 
 /* Device-time profile of fem_step, measured with CUDA events on the batch stream. */

@@ -190,18 +190,18 @@ static fem_status ws_create(int64_t N, int rpad, Workspace** out) {
   if (st == FEM_OK) st = dalloc(&w->z32, w->n);
   if (st == FEM_OK) st = dalloc(&w->p32, w->n);
   if (st == FEM_OK) st = dalloc(&w->q32, w->n);
-  if (st == FEM_OK) st = dalloc(&w->sc, kMaxRpad);
-  if (st == FEM_OK) st = dalloc(&w->outer, kMaxRpad);
-  if (st == FEM_OK) st = dalloc(&w->partial, (size_t)kMaxRedBlocks * 3 * kMaxRpad);
+  if (st == FEM_OK) st = dalloc(&w->sc, kMaxCases);
+  if (st == FEM_OK) st = dalloc(&w->outer, kMaxCases);
+  if (st == FEM_OK) st = dalloc(&w->partial, (size_t)kMaxRedBlocks * 3 * kMaxCases);
   if (st == FEM_OK) st = dalloc(&w->counter, 1);
-  if (st == FEM_OK) st = dalloc(&w->out, 3 * kMaxRpad);
+  if (st == FEM_OK) st = dalloc(&w->out, 3 * kMaxCases);
   if (st == FEM_OK) st = dalloc(&w->n_active, 1);
   if (st != FEM_OK) {
     delete w;
     return st;
   }
   if (cudaMallocHost((void**)&w->h_active, sizeof(int)) != cudaSuccess ||
-      cudaMallocHost((void**)&w->h_sc, sizeof(CgCase) * kMaxRpad) != cudaSuccess) {
+      cudaMallocHost((void**)&w->h_sc, sizeof(CgCase) * kMaxCases) != cudaSuccess) {
     cudaGetLastError();
     delete w;
     return fail(FEM_ERR_OOM, "cudaMallocHost failed");
@@ -209,8 +209,8 @@ static fem_status ws_create(int64_t N, int rpad, Workspace** out) {
   cudaMemset(w->counter, 0, sizeof(unsigned));
   cudaMemset(w->p, 0, w->n * sizeof(double));
   cudaMemset(w->p32, 0, w->n * sizeof(float));
-  cudaMemset(w->sc, 0, sizeof(CgCase) * kMaxRpad);
-  cudaMemset(w->outer, 0, sizeof(CgCase) * kMaxRpad);
+  cudaMemset(w->sc, 0, sizeof(CgCase) * kMaxCases);
+  cudaMemset(w->outer, 0, sizeof(CgCase) * kMaxCases);
   *out = w;
   return FEM_OK;
 }
@@ -243,10 +243,17 @@ struct fem_mesh {
   std::vector<void*> tile_bufs;
   int ebe_variant = 0;             // 0 auto, 1 generic element kernel, 2 tiled hex kernel
   int hex_per_tile = 0;            // 0 auto
-  MeshView view() const { return MeshView{N, E, conn, rec64, rec32, binv64, binv32, fm}; }
+  // host copies of the inputs (used to fuse meshes into one system) and the region map
+  std::vector<double> h_xyz, h_lmr;
+  std::vector<int32_t> h_conn, h_mat, h_region;
+  std::vector<uint8_t> h_fixed;
+  // fused meshes: case of each node
+  uint8_t* seg = nullptr;
+  int nseg = 0;
+  MeshView view() const { return MeshView{N, E, conn, rec64, rec32, binv64, binv32, fm, seg, nseg}; }
   ~fem_mesh() {
     dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(rec_df); dfree(D);
-    dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi);
+    dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi); dfree(seg);
     for (auto* w : ws) delete w;
     for (void* b : tile_bufs) cudaFree(b);
   }
@@ -299,13 +306,23 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
   const int rpad = w->rpad;
   const Reducer red = w->red();
   const int ebe_cls = sizeof(T) == 4 ? P_EBE32 : P_EBE64;
-  CU(launch_norm_b_gated<T>(mv, rpad, b, red, sc, gate, tol, s));
+  const bool sg = mv.seg != nullptr;
+  if (sg) {
+    CU(launch_norm_b_seg<T>(mv, b, red, sc, gate, tol, s));
+  } else {
+    CU(launch_norm_b_gated<T>(mv, rpad, b, red, sc, gate, tol, s));
+  }
   w->count();
   if (zero_guess) {
     CU(cudaMemsetAsync(x, 0, sizeof(T) * (size_t)w->n, s));
-    CU(launch_resid<T>(mv, rpad, b, nullptr, x, r, z, 1, red, sc, w->n_active, tol, maxit, s));
+    if (sg) {
+      CU(launch_resid_seg<T>(mv, b, nullptr, x, r, z, red, sc, w->n_active, s));
+    } else {
+      CU(launch_resid<T>(mv, rpad, b, nullptr, x, r, z, 1, red, sc, w->n_active, tol, maxit, s));
+    }
     w->count();
   } else {
+    if (sg) return fail(FEM_ERR_ARG, "fused groups solve from a zero inner guess only");
     // the guess is zeroed on Dirichlet DOFs (and for b = 0) before its residual is formed
     CU(launch_zero_b0_t<T>(mv, rpad, x, sc, s));
     int pi = w->pbeg(ebe_cls, s);
@@ -319,13 +336,21 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
   for (;;) {
     for (int k = 0; k < check_every; ++k) {
       int p0 = w->pbeg(P_VEC, s);
-      CU(launch_dir_gated<T>(mv, rpad, z, p, sc, w->n_active, s));
+      if (sg) {
+        CU(launch_dir_seg<T>(mv, z, p, sc, w->n_active, s));
+      } else {
+        CU(launch_dir_gated<T>(mv, rpad, z, p, sc, w->n_active, s));
+      }
       w->pend(p0, s);
       int p1 = w->pbeg(ebe_cls, s);
       CU(ebe_product<T>(m, rpad, p, q, m->cM, m->cK, &red, sc, nullptr, w->n_active, s));
       w->pend(p1, s);
       int p2 = w->pbeg(P_VEC, s);
-      CU(launch_update<T>(mv, rpad, p, q, x, r, z, red, sc, w->n_active, tol, maxit, s));
+      if (sg) {
+        CU(launch_update_seg<T>(mv, p, q, x, r, z, red, sc, w->n_active, maxit, s));
+      } else {
+        CU(launch_update<T>(mv, rpad, p, q, x, r, z, red, sc, w->n_active, tol, maxit, s));
+      }
       w->pend(p2, s);
       w->count(3);
     }
@@ -382,7 +407,7 @@ static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double
     }
     CHK(pcg_core<float>(m, w, w->r32, w->x32, w->rr32, w->z32, w->p32, w->q32, w->sc, true, false, o.inner_tol,
                         o.maxit - used, w->outer, o.check_every, s));
-    CU(launch_refine_counts(mv, rpad, x, w->x32, w->outer, w->sc, s));
+    CU(launch_refine_counts(mv, rpad, rpad, x, w->x32, w->outer, w->sc, s));
     w->count();
   }
   w->resolve();
@@ -418,6 +443,9 @@ static fem_status check_opts(const fem_opts* o) {
 // ------------------------------------------------------------------------------------------------------
 struct Group {
   fem_mesh* mesh = nullptr;
+  fem_mesh* owned_mesh = nullptr;   // fused groups: the virtual mesh (owned)
+  std::vector<int64_t> node_off;    // fused groups: first node of each case's mesh, and the total
+  int ncase = 0;                    // per-case arrays: rpad (multi-RHS group) or number of meshes (fused)
   int rpad = 0;
   std::vector<int> cases;
   std::vector<RickerSrc> hsrc;
@@ -434,7 +462,7 @@ struct Group {
   int* slot_lists = nullptr;    // device [2][kMaxSlots]
   int* h_slots = nullptr;       // pinned [2][kMaxSlots]
   RickerSrc* src = nullptr;
-  double* ext = nullptr;        // device [rpad][3]: external loads for the next step
+  double* ext = nullptr;        // device [ncase][3]: external loads for the next step
   // FP32-inner steps: products kept by recurrences (K u, M v, K v, M a, ring of A v) and split products
   double *Ku = nullptr, *Mv = nullptr, *Kv = nullptr, *Ma = nullptr, *Av[4] = {nullptr, nullptr, nullptr, nullptr};
   double *qM = nullptr, *qK = nullptr;
@@ -454,6 +482,7 @@ struct Group {
     for (auto& v : Av) dfree(v);
     if (h_slots) cudaFreeHost(h_slots);
     delete ws;
+    delete owned_mesh;
   }
 };
 
@@ -472,7 +501,8 @@ struct fem_batch {
 
 static fem_status group_alloc(fem_batch* bt, Group* g) {
   fem_mesh* m = g->mesh;
-  g->rpad = next_pow2((int)g->cases.size());
+  g->rpad = g->owned_mesh ? 1 : next_pow2((int)g->cases.size());
+  g->ncase = g->owned_mesh ? (int)g->cases.size() : g->rpad;
   g->n = m->N * 3 * g->rpad;
   const size_t n = (size_t)g->n;
   CHK(dalloc(&g->u, n));
@@ -521,17 +551,18 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
     cudaGetLastError();
     return fail(FEM_ERR_OOM, "cudaMallocHost failed");
   }
-  g->hsrc.resize(g->rpad);
-  for (int l = (int)g->cases.size(); l < g->rpad; ++l) g->hsrc[l] = RickerSrc{-1, {0, 0, 0}, 1.0, 0.0, 0.0};
-  CHK(dalloc(&g->src, g->rpad));
-  CHK(dalloc(&g->ext, 3 * g->rpad));
-  CU(cudaMemsetAsync(g->ext, 0, sizeof(double) * 3 * g->rpad, s));
-  CU(cudaMemcpyAsync(g->src, g->hsrc.data(), sizeof(RickerSrc) * g->rpad, cudaMemcpyHostToDevice, s));
+  // one source and one external load per case: per column (multi-RHS group) or per mesh copy (fused)
+  g->hsrc.resize(g->ncase);
+  for (int l = (int)g->cases.size(); l < g->ncase; ++l) g->hsrc[l] = RickerSrc{-1, {0, 0, 0}, 1.0, 0.0, 0.0};
+  CHK(dalloc(&g->src, g->ncase));
+  CHK(dalloc(&g->ext, 3 * g->ncase));
+  CU(cudaMemsetAsync(g->ext, 0, sizeof(double) * 3 * g->ncase, s));
+  CU(cudaMemcpyAsync(g->src, g->hsrc.data(), sizeof(RickerSrc) * g->ncase, cudaMemcpyHostToDevice, s));
   CHK(ws_create(m->N, g->rpad, &g->ws));
   g->ws->prof = &bt->prof;
-  g->iters_acc.assign(g->rpad, 0);
-  g->relres_max.assign(g->rpad, 0.0);
-  g->last.assign(g->rpad, CgCase{});
+  g->iters_acc.assign(g->ncase, 0);
+  g->relres_max.assign(g->ncase, 0.0);
+  g->last.assign(g->ncase, CgCase{});
   return FEM_OK;
 }
 
@@ -646,28 +677,33 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     qy = w->q32;
     w->count(2);
   }
-  CU(launch_r0(mv, g->rpad, dt, g->b, aslot(it - 4), aslot(it - 3), aslot(it - 2), aslot(it - 1), qy, w->r32, red,
-               w->outer, w->n_active, o.tol, o.inner_tol, s));
+  if (mv.seg) {
+    CU(launch_r0_seg(mv, dt, g->b, aslot(it - 4), aslot(it - 3), aslot(it - 2), aslot(it - 1), qy, w->r32, red,
+                     w->outer, w->n_active, o.tol, o.inner_tol, s));
+  } else {
+    CU(launch_r0(mv, g->rpad, dt, g->b, aslot(it - 4), aslot(it - 3), aslot(it - 2), aslot(it - 1), qy, w->r32, red,
+                 w->outer, w->n_active, o.tol, o.inner_tol, s));
+  }
   CU(cudaMemcpyAsync(g->x, g->guess, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
   w->count();
   // 4. refinement passes: inner FP32 PCG (cases whose residual is above tol) + FP64 certification
   const int kMaxPass = 40;
   for (int pass = 0; pass < kMaxPass; ++pass) {
     CU(cudaMemcpyAsync(w->h_active, w->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(w->h_sc, w->outer, sizeof(CgCase) * g->rpad, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(w->h_sc, w->outer, sizeof(CgCase) * g->ncase, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     w->resolve();
     int used = 0;
-    for (int c = 0; c < g->rpad; ++c) used = std::max(used, w->h_sc[c].iters);
+    for (int c = 0; c < g->ncase; ++c) used = std::max(used, w->h_sc[c].iters);
     if (*w->h_active > 0) {
       if (used >= o.maxit || pass == kMaxPass - 1) {
-        for (int c = 0; c < g->rpad; ++c)
+        for (int c = 0; c < g->ncase; ++c)
           if (w->h_sc[c].active) w->h_sc[c].status = FEM_ERR_NOT_CONVERGED, w->h_sc[c].active = 0;
-        CU(cudaMemcpyAsync(w->outer, w->h_sc, sizeof(CgCase) * g->rpad, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(w->outer, w->h_sc, sizeof(CgCase) * g->ncase, cudaMemcpyHostToDevice, s));
       } else {
         CHK(pcg_core<float>(m, w, w->r32, w->x32, w->rr32, w->z32, w->p32, w->q32, w->sc, true, false, o.inner_tol,
                             o.maxit - used, w->outer, o.check_every, s));
-        CU(launch_refine_counts(mv, g->rpad, g->x, w->x32, w->outer, w->sc, s));
+        CU(launch_refine_counts(mv, g->rpad, g->ncase, g->x, w->x32, w->outer, w->sc, s));
         w->count();
       }
     } else if (pass > 0) {
@@ -679,12 +715,17 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     else
       CU(launch_ebe_split(mv, g->rpad, g->x, g->qM, g->qK, s));
     w->pend(pe, s);
-    CU(launch_cert(mv, g->rpad, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
-                   o.inner_tol, s));
+    if (mv.seg) {
+      CU(launch_cert_seg(mv, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
+                         o.inner_tol, s));
+    } else {
+      CU(launch_cert(mv, g->rpad, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
+                     o.inner_tol, s));
+    }
     w->count(2);
   }
   w->pend(ph, s);
-  CU(cudaMemcpyAsync(w->h_sc, w->outer, sizeof(CgCase) * g->rpad, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(w->h_sc, w->outer, sizeof(CgCase) * g->ncase, cudaMemcpyDeviceToHost, s));
   // 5. Newmark update, product recurrences, snapshot push (Section 3.1, Eq. timestep)
   ph = w->pbeg(P_UPDATE, s);
   void* e_push = nullptr;
@@ -706,7 +747,7 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   w->pend(ph, s);
   CU(cudaStreamSynchronize(s));
   w->resolve();
-  for (int l = 0; l < g->rpad; ++l) g->last[l] = w->h_sc[l];
+  for (int l = 0; l < g->ncase; ++l) g->last[l] = w->h_sc[l];
   for (int l = 0; l < (int)g->cases.size(); ++l) {
     const CgCase& c = w->h_sc[l];
     g->iters_acc[l] += c.iters;
@@ -719,6 +760,7 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
 
 static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
   if (bt->opts.precision == FEM_FP32_INNER) return group_step_mixed(bt, g, worst);
+  if (g->owned_mesh) return fail(FEM_ERR_ARG, "fused meshes need the FP32-inner solver");
   fem_mesh* m = g->mesh;
   const MeshView mv = m->view();
   cudaStream_t s = bt->s;
@@ -808,6 +850,7 @@ void fem_opts_default(fem_opts* o) {
   o->check_every = 8;
   o->refresh_every = 200;
   o->cert_df = 0;
+  o->fuse_meshes = 0;
 }
 
 fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
@@ -828,6 +871,11 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
   cudaStream_t s = (cudaStream_t)stream;
   fem_mesh* m = new fem_mesh();
   cudaGetDevice(&m->device);
+  m->h_xyz.assign(xyz, xyz + 3 * n_nodes);
+  m->h_conn.assign(conn, conn + 4 * n_elems);
+  m->h_mat.assign(mat_id, mat_id + n_elems);
+  m->h_lmr.assign(lam_mu_rho, lam_mu_rho + 3 * n_mat);
+  m->h_fixed.assign(fixed_dof, fixed_dof + 3 * n_nodes);
   m->N = n_nodes;
   m->E = n_elems;
   m->tp = *tp;
@@ -965,6 +1013,7 @@ fem_status fem_mesh_set_regions(fem_mesh* m, const int32_t* region_of_node) {
   dfree(m->reg_lo);
   dfree(m->reg_hi);
   m->n_regions = 0;
+  m->h_region.assign(region_of_node, region_of_node + m->N);
   CHK(dalloc(&m->reg_lo, R));
   CHK(dalloc(&m->reg_hi, R));
   CU(cudaMemcpy(m->reg_lo, lo.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice));
@@ -1064,9 +1113,99 @@ fem_status fem_case_add(fem_batch* b, fem_mesh* m, int32_t src_node, const doubl
   return FEM_OK;
 }
 
+// Fuses every case of the batch into one system: each case gets its own copy of its mesh, all copies are
+// concatenated into one virtual mesh (node, element, material and region numbering shifted), and the
+// node -> case map makes the solver's scalars per case.  One set of launches then serves all cases.
+static fem_status fuse_cases(fem_batch* b) {
+  const int nc = (int)b->loc.size();
+  if (nc > kMaxCases || nc > 255) return fail(FEM_ERR_ARG, "fuse_meshes supports at most 128 cases");
+  std::vector<fem_mesh*> mesh_of(nc);
+  std::vector<RickerSrc> src_of(nc);
+  for (int c = 0; c < nc; ++c) {
+    Group* g = b->groups[b->loc[c].first];
+    mesh_of[c] = g->mesh;
+    src_of[c] = g->hsrc[b->loc[c].second];
+  }
+  const fem_time_params tp = mesh_of[0]->tp;
+  bool all_regions = true;
+  int64_t N = 0, E = 0, nmat = 0;
+  for (int c = 0; c < nc; ++c) {
+    const fem_mesh* m = mesh_of[c];
+    if (m->tp.dt != tp.dt || m->tp.a0 != tp.a0 || m->tp.a1 != tp.a1)
+      return fail(FEM_ERR_ARG, "fused meshes must share dt and damping");
+    N += m->N;
+    E += m->E;
+    nmat += (int64_t)m->h_lmr.size() / 3;
+    all_regions = all_regions && m->n_regions > 0;
+  }
+  std::vector<double> xyz, lmr;
+  std::vector<int32_t> conn, mat, region;
+  std::vector<uint8_t> fixed, seg;
+  xyz.reserve(3 * N); conn.reserve(4 * E); mat.reserve(E); fixed.reserve(3 * N); seg.reserve(N);
+  if (all_regions) region.reserve(N);
+  std::vector<int64_t> node_off(nc + 1, 0);
+  int32_t mat_off = 0, reg_off = 0;
+  for (int c = 0; c < nc; ++c) {
+    const fem_mesh* m = mesh_of[c];
+    const int32_t noff = (int32_t)node_off[c];
+    node_off[c + 1] = node_off[c] + m->N;
+    xyz.insert(xyz.end(), m->h_xyz.begin(), m->h_xyz.end());
+    for (int32_t v : m->h_conn) conn.push_back(v + noff);
+    for (int32_t v : m->h_mat) mat.push_back(v + mat_off);
+    lmr.insert(lmr.end(), m->h_lmr.begin(), m->h_lmr.end());
+    fixed.insert(fixed.end(), m->h_fixed.begin(), m->h_fixed.end());
+    seg.insert(seg.end(), (size_t)m->N, (uint8_t)c);
+    if (all_regions) {
+      int32_t rmax = -1;
+      for (int32_t v : m->h_region) {
+        region.push_back(v < 0 ? -1 : v + reg_off);
+        rmax = std::max(rmax, v);
+      }
+      reg_off += rmax + 1;
+    }
+    mat_off += (int32_t)(m->h_lmr.size() / 3);
+  }
+  fem_mesh* vm = nullptr;
+  CHK(fem_mesh_create(N, xyz.data(), E, conn.data(), mat.data(), (int)nmat, lmr.data(), fixed.data(), &tp, b->s, &vm));
+  if (dalloc(&vm->seg, (size_t)N) != FEM_OK) {
+    delete vm;
+    return fail(FEM_ERR_OOM, "fused case map allocation failed");
+  }
+  vm->nseg = nc;
+  cudaError_t e = cudaMemcpy(vm->seg, seg.data(), (size_t)N, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    delete vm;
+    return fail(FEM_ERR_CUDA, std::string("fused case map upload: ") + cudaGetErrorString(e));
+  }
+  if (all_regions) {
+    fem_status st = fem_mesh_set_regions(vm, region.data());
+    if (st != FEM_OK) {
+      delete vm;
+      return st;
+    }
+  }
+  Group* fg = new Group();
+  fg->mesh = fg->owned_mesh = vm;
+  fg->node_off = node_off;
+  for (int c = 0; c < nc; ++c) {
+    fg->cases.push_back(c);
+    RickerSrc r = src_of[c];
+    if (r.node >= 0) r.node += (int)node_off[c];
+    fg->hsrc.push_back(r);
+  }
+  for (auto* g : b->groups) delete g;
+  b->groups.assign(1, fg);
+  for (int c = 0; c < nc; ++c) b->loc[c] = {0, c};
+  return FEM_OK;
+}
+
 static fem_status batch_start(fem_batch* b) {
   if (b->started) return FEM_OK;
   if (b->loc.empty()) return fail(FEM_ERR_STATE, "batch has no cases");
+  if (b->opts.fuse_meshes) {
+    if (b->opts.precision != FEM_FP32_INNER) return fail(FEM_ERR_ARG, "fuse_meshes needs the FP32-inner solver");
+    CHK(fuse_cases(b));
+  }
   for (auto* g : b->groups) CHK(group_alloc(b, g));
   CU(cudaStreamSynchronize(b->s));
   b->started = true;
@@ -1119,7 +1258,13 @@ fem_status predictor_predict(fem_batch* b, int case_id, double* x_guess_dev) {
   CHK(batch_start(b));
   Group* g = b->groups[b->loc[case_id].first];
   CHK(group_predict(b, g, g->ws->q));
-  CU(launch_extract_case(g->mesh->N, g->rpad, b->loc[case_id].second, g->ws->q, x_guess_dev, b->s));
+  const int l = b->loc[case_id].second;
+  if (g->owned_mesh) {
+    const int64_t n0 = g->node_off[l], n3 = 3 * (g->node_off[l + 1] - n0);
+    CU(cudaMemcpyAsync(x_guess_dev, g->ws->q + 3 * n0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, b->s));
+  } else {
+    CU(launch_extract_case(g->mesh->N, g->rpad, l, g->ws->q, x_guess_dev, b->s));
+  }
   CU(cudaStreamSynchronize(b->s));
   return FEM_OK;
 }
@@ -1140,6 +1285,13 @@ fem_status fem_case_get(fem_batch* b, int case_id, int what, double* dst, int on
     default: return fail(FEM_ERR_ARG, "unknown field");
   }
   const int l = b->loc[case_id].second;
+  if (g->owned_mesh) {   // fused: the case's own node range of the virtual mesh
+    const int64_t n0 = g->node_off[l], n3 = 3 * (g->node_off[l + 1] - n0);
+    CU(cudaMemcpyAsync(dst, src + 3 * n0, sizeof(double) * n3, on_device ? cudaMemcpyDeviceToDevice
+                                                                         : cudaMemcpyDeviceToHost, b->s));
+    if (!on_device) CU(cudaStreamSynchronize(b->s));
+    return FEM_OK;
+  }
   if (on_device) {
     CU(launch_extract_case(g->mesh->N, g->rpad, l, src, dst, b->s));
   } else {
@@ -1155,6 +1307,12 @@ fem_status fem_batch_set_loads(fem_batch* b, const double* loads) {
   g_err.clear();
   if (!b || !loads) return fail(FEM_ERR_ARG, "null argument");
   CHK(batch_start(b));
+  if (b->groups.size() == 1) {  // one group holds the cases in id order: one copy
+    Group* g = b->groups[0];
+    CU(cudaMemcpyAsync(g->ext, loads, 3 * sizeof(double) * b->loc.size(), cudaMemcpyHostToDevice, b->s));
+    g->use_ext = true;
+    return FEM_OK;
+  }
   for (size_t c = 0; c < b->loc.size(); ++c) {
     Group* g = b->groups[b->loc[c].first];
     const int l = b->loc[c].second;
@@ -1168,6 +1326,14 @@ fem_status fem_batch_get_field(fem_batch* b, int what, double* dst, int on_devic
   g_err.clear();
   if (!b || !dst) return fail(FEM_ERR_ARG, "null argument");
   CHK(batch_start(b));
+  // case c's field starts after the fields of cases 0..c-1 (each [n_nodes of its mesh][3])
+  std::vector<int64_t> case_off(b->loc.size() + 1, 0);
+  for (size_t c = 0; c < b->loc.size(); ++c) {
+    const Group* g = b->groups[b->loc[c].first];
+    const int l = b->loc[c].second;
+    const int64_t nn = g->owned_mesh ? g->node_off[l + 1] - g->node_off[l] : g->mesh->N;
+    case_off[c + 1] = case_off[c] + 3 * nn;
+  }
   for (auto* g : b->groups) {
     const double* src = nullptr;
     switch (what) {
@@ -1179,15 +1345,19 @@ fem_status fem_batch_get_field(fem_batch* b, int what, double* dst, int on_devic
       case FEM_FIELD_GUESS: src = g->guess; break;
       default: return fail(FEM_ERR_ARG, "unknown field");
     }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (g->owned_mesh) {
+      for (size_t l = 0; l < g->cases.size(); ++l) {
+        const int64_t n0 = g->node_off[l], n3 = 3 * (g->node_off[l + 1] - n0);
+        CU(cudaMemcpyAsync(dst + case_off[g->cases[l]], src + 3 * n0, sizeof(double) * n3, kind, b->s));
+      }
+      continue;
+    }
     const int64_t n3 = g->mesh->N * 3;
     double* tmp = g->ws->r;  // [rpad][N][3] scratch
     CU(launch_extract_all(g->mesh->N, g->rpad, (int)g->cases.size(), src, tmp, b->s));
-    // cases of a group are contiguous in tmp; their ids may not be contiguous in dst
-    for (size_t l = 0; l < g->cases.size(); ++l) {
-      double* d = dst + (size_t)g->cases[l] * n3;
-      CU(cudaMemcpyAsync(d, tmp + l * n3, sizeof(double) * n3,
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->s));
-    }
+    for (size_t l = 0; l < g->cases.size(); ++l)
+      CU(cudaMemcpyAsync(dst + case_off[g->cases[l]], tmp + l * n3, sizeof(double) * n3, kind, b->s));
   }
   if (!on_device) CU(cudaStreamSynchronize(b->s));
   return FEM_OK;

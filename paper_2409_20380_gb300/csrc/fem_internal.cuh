@@ -14,7 +14,8 @@ namespace fem {
 constexpr int kBlock = 256;              // threads per block of the element kernels
 constexpr int kVecBlock = 512;           // threads per block of the reducing vector kernels
 constexpr int kVecGrid = 152 * 3;        // their grid cap: few blocks keep the final reduction short
-constexpr int kMaxRpad = 32;             // max cases per multi-RHS group
+constexpr int kMaxRpad = 32;             // max cases per multi-RHS group (lanes of a node)
+constexpr int kMaxCases = 128;           // max cases of a group (fused groups: one case per mesh)
 constexpr int kMaxSlots = 33;            // predictor ring: s_max + 1 <= 33
 constexpr int kMaxRedBlocks = 152 * 8;   // grid cap of reducing kernels (partials buffer rows)
 
@@ -69,9 +70,9 @@ struct CgCase {
 
 // Grid-wide deterministic per-case reduction: per-block partials + last-block final sum.
 struct Reducer {
-  double* partial;     // [kMaxRedBlocks][3 * kMaxRpad]
+  double* partial;     // [kMaxRedBlocks][3 * kMaxCases]
   unsigned* counter;   // one counter, 0 between launches
-  double* out;         // [3 * kMaxRpad]
+  double* out;         // [3 * kMaxCases]
 };
 
 struct MeshView {
@@ -82,6 +83,10 @@ struct MeshView {
   const double* binv64;   // [N][6] xx yy zz xy xz yz
   const float* binv32;
   const uint8_t* freemask;  // [N] bit k = DOF k free
+  // Fused groups (several meshes concatenated, one case each): seg[n] is the case of node n, nseg the
+  // number of cases.  seg == nullptr: the case of an entry is its lane (index % rpad).
+  const uint8_t* seg = nullptr;
+  int nseg = 0;
 };
 
 struct RickerSrc {          // per case of a group
@@ -143,8 +148,27 @@ cudaError_t launch_update(const MeshView& m, int rpad, const T* p, const T* q, T
 cudaError_t launch_outer_resid(const MeshView& m, int rpad, const double* b, const double* q,
                                float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
                                double inner_max, cudaStream_t s);
-cudaError_t launch_refine_counts(const MeshView& m, int rpad, double* x, const float* d32, CgCase* outer,
+cudaError_t launch_refine_counts(const MeshView& m, int rpad, int ncase, double* x, const float* d32, CgCase* outer,
                                  const CgCase* inner, cudaStream_t s);
+
+// Fused groups (k_seg.cu): segmented forms of the CG and refinement kernels (rpad = 1, case = m.seg[node]).
+template <typename T>
+cudaError_t launch_norm_b_seg(const MeshView& m, const T* b, Reducer red, CgCase* sc, const CgCase* gate, double tol,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_resid_seg(const MeshView& m, const T* b, const T* q, T* x, T* r, T* z, Reducer red, CgCase* sc,
+                             int* n_active, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dir_seg(const MeshView& m, const T* z, T* p, const CgCase* sc, const int* n_active, cudaStream_t s);
+template <typename T>
+cudaError_t launch_update_seg(const MeshView& m, const T* p, const T* q, T* x, T* r, T* z, Reducer red, CgCase* sc,
+                              int* n_active, int maxit, cudaStream_t s);
+cudaError_t launch_r0_seg(const MeshView& m, double dt, const double* b, const double* Av4, const double* Av3,
+                          const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red,
+                          CgCase* outer, int* n_active, double tol, double inner_floor, cudaStream_t s);
+cudaError_t launch_cert_seg(const MeshView& m, double cM, double cK, const double* b, const double* qM, const double* qK,
+                            float* r32, Reducer red, CgCase* outer, int* n_active, double tol, double inner_floor,
+                            cudaStream_t s);
 // x = 0 on Dirichlet DOFs and for cases with ||b|| = 0.
 template <typename T>
 cudaError_t launch_zero_b0_t(const MeshView& m, int rpad, T* x, const CgCase* sc, cudaStream_t s);
@@ -227,6 +251,60 @@ __device__ __forceinline__ double inner_target(double tol, double relres, double
   if (t > 0.5) t = 0.5;
   if (t < floor) t = floor;
   return t;
+}
+
+// Number of cases the per-case arrays of a launch cover.
+__host__ __device__ __forceinline__ int n_cases(const MeshView& m, int rpad) { return m.seg ? m.nseg : rpad; }
+
+// Segmented accumulation for fused groups: per-case sums in shared memory acc[q * ncase + c].  Every lane
+// of the warp must call it (invalid items pass value 0 and any case); a warp whose lanes all hold the same
+// case reduces by shuffles and adds once.
+template <int NQ>
+__device__ __forceinline__ void seg_add(double* acc, int ncase, int c, const double (&v)[NQ]) {
+  const int c0 = __shfl_sync(0xffffffffu, c, 0);
+  if (__all_sync(0xffffffffu, c == c0)) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double x = v[q];
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      if ((threadIdx.x & 31) == 0) atomicAdd(acc + q * ncase + c0, x);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (v[q] != 0.0) atomicAdd(acc + q * ncase + c, v[q]);
+  }
+}
+
+// Grid-wide per-case sums of the shared accumulators acc[NQ * ncase] (all threads call it after the loop);
+// returns true in the last block with red.out[q * ncase + c] holding the totals (fixed summation order
+// over blocks).
+template <int NQ>
+__device__ __forceinline__ bool block_reduce_last_seg(double* acc, int ncase, const Reducer& red) {
+  __shared__ bool am_last;
+  const int V = NQ * ncase;
+  __syncthreads();
+  for (int t = threadIdx.x; t < V; t += blockDim.x) red.partial[(size_t)blockIdx.x * V + t] = acc[t];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(red.counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  for (int t = threadIdx.x; t < V; t += blockDim.x) {
+    double a0 = 0.0, a1 = 0.0;
+    int b = 0;
+    const int nb = (int)gridDim.x;
+    for (; b + 1 < nb; b += 2) {
+      a0 += __ldcg(red.partial + (size_t)b * V + t);
+      a1 += __ldcg(red.partial + (size_t)(b + 1) * V + t);
+    }
+    if (b < nb) a0 += __ldcg(red.partial + (size_t)b * V + t);
+    red.out[t] = a0 + a1;
+  }
+  if (threadIdx.x == 0) *red.counter = 0u;
+  __syncthreads();
+  return true;
 }
 
 // Per-case sums over the grid.  Threads hold vals[q] for case c = threadIdx.x % rpad (the grid stride of

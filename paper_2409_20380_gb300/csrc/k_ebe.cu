@@ -38,6 +38,29 @@ __device__ __forceinline__ void ebe_tail(const Reducer& red, CgCase* sc, double*
   }
 }
 
+// Same for fused groups: cases 0..nc-1, totals in red.out[c].
+__device__ __forceinline__ void ebe_tail_seg(const Reducer& red, CgCase* sc, double* ptq_out, int nc) {
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    const double pq = red.out[c];
+    if (ptq_out) ptq_out[c] = pq;
+    if (sc) {
+      CgCase& s = sc[c];
+      s.pq = pq;
+      if (s.active) {
+        if (!(pq > 0.0) || !isfinite(pq)) {
+          s.active = 0;
+          s.status = FEM_ERR_BREAKDOWN;
+          s.alpha = 0.0;
+        } else {
+          s.alpha = s.rho / pq;
+        }
+      } else {
+        s.alpha = 0.0;
+      }
+    }
+  }
+}
+
 static int log2i(int r) {
   int s = 0;
   while ((1 << s) < r) ++s;
@@ -236,7 +259,7 @@ __device__ __forceinline__ void tet_acc(const T* __restrict__ re, T aM, T aK, co
   }
 }
 
-template <typename T, bool DOT>
+template <typename T, bool DOT, bool SEG>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex(HexTiles ht, MeshView m, int rpad, int rshift,
                                                     const T* __restrict__ p, T* __restrict__ q, T aM, T aK,
                                                     Reducer red, CgCase* sc, double* ptq_out, const int* gate) {
@@ -244,6 +267,14 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex(HexT
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* qs = reinterpret_cast<T*>(smem_raw);
   int* snode = reinterpret_cast<int*>(smem_raw + sizeof(T) * (size_t)ht.nloc_max * 3 * rpad);
+  // fused groups: per-case p^T q accumulators after the node list (8-byte aligned)
+  double* sacc = reinterpret_cast<double*>(smem_raw + ((sizeof(T) * (size_t)ht.nloc_max * 3 * rpad +
+                                                        sizeof(int) * (size_t)ht.nloc_max + 7) & ~(size_t)7));
+  constexpr bool seg = DOT && SEG;
+  if (seg) {
+    for (int t = threadIdx.x; t < m.nseg; t += blockDim.x) sacc[t] = 0.0;
+    __syncthreads();
+  }
   const T* __restrict__ rec = rec_of<T>(m);
   double dot = 0.0;
   const int per_node = 3 * rpad;
@@ -255,7 +286,13 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex(HexT
     __syncthreads();
     T tdot = 0;
     const int items = nh << rshift;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int rounds_end = seg ? ((items + blockDim.x - 1) / blockDim.x) * blockDim.x : items;
+    for (int it = threadIdx.x; it < rounds_end; it += blockDim.x) {
+      if (it >= items) {   // idle lane of the last round (fused groups aggregate per warp)
+        double z1[1] = {0.0};
+        seg_add<1>(sacc, m.nseg, 0, z1);
+        continue;
+      }
       const int hl = it >> rshift, c = it & (rpad - 1);
       const int64_t hx = h0 + hl;
       const uint4 lw = __ldg(ht.hex_local + hx);
@@ -278,13 +315,20 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex(HexT
       tet_acc<T, kHexTet[3][0], kHexTet[3][1], kHexTet[3][2], kHexTet[3][3]>(re + 3 * kRec, aM, aK, P, Q);
       tet_acc<T, kHexTet[4][0], kHexTet[4][1], kHexTet[4][2], kHexTet[4][3]>(re + 4 * kRec, aM, aK, P, Q);
       tet_acc<T, kHexTet[5][0], kHexTet[5][1], kHexTet[5][2], kHexTet[5][3]>(re + 5 * kRec, aM, aK, P, Q);
+      T hdot = 0;
 #pragma unroll
       for (int sl = 0; sl < 8; ++sl)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          if (DOT) tdot += P[sl][k] * Q[sl][k];
+          if (DOT) hdot += P[sl][k] * Q[sl][k];
           atomicAdd(qs + ls[sl] * per_node + k * rpad + c, Q[sl][k]);
         }
+      if (seg) {
+        double v1[1] = {(double)hdot};
+        seg_add<1>(sacc, m.nseg, m.seg[snode[ls[0]] & 0x7fffffff], v1);
+      } else {
+        tdot += hdot;
+      }
     }
     dot += (double)tdot;
     __syncthreads();
@@ -304,8 +348,12 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex(HexT
     __syncthreads();
   }
   if (DOT) {
-    double v[1] = {dot};
-    if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
+    if (seg) {
+      if (block_reduce_last_seg<1>(sacc, m.nseg, red)) ebe_tail_seg(red, sc, ptq_out, m.nseg);
+    } else {
+      double v[1] = {dot};
+      if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
+    }
   }
 }
 
@@ -315,28 +363,23 @@ cudaError_t launch_ebe_hex(const HexTiles& ht, const MeshView& m, int rpad, cons
   cudaError_t err = cudaMemsetAsync(q, 0, sizeof(T) * (size_t)m.N * 3 * rpad, s);
   if (err != cudaSuccess) return err;
   const int rs = log2i(rpad);
-  const size_t smem = sizeof(T) * (size_t)ht.nloc_max * 3 * rpad + sizeof(int) * (size_t)ht.nloc_max;
+  const size_t smem = ((sizeof(T) * (size_t)ht.nloc_max * 3 * rpad + sizeof(int) * (size_t)ht.nloc_max + 7) & ~(size_t)7) +
+                      (m.seg ? sizeof(double) * (size_t)m.nseg : 0);
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 1;
-  if (red) {
-    err = cudaFuncSetAttribute(k_ebe_hex<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe_hex<T, true>, kBlock, smem);
-  } else {
-    err = cudaFuncSetAttribute(k_ebe_hex<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe_hex<T, false>, kBlock, smem);
-  }
+  auto kfn = red ? (m.seg ? k_ebe_hex<T, true, true> : k_ebe_hex<T, true, false>) : k_ebe_hex<T, false, false>;
+  err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBlock, smem);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) per_sm = 1;
   int grid = nsm * per_sm;
   if (grid > ht.n_tiles) grid = ht.n_tiles;
   if (grid > kMaxRedBlocks) grid = kMaxRedBlocks;
   Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
-  if (red)
-    k_ebe_hex<T, true><<<grid, kBlock, smem, s>>>(ht, m, rpad, rs, p, q, (T)aM, (T)aK, rd, sc, ptq_out, gate);
-  else
-    k_ebe_hex<T, false><<<grid, kBlock, smem, s>>>(ht, m, rpad, rs, p, q, (T)aM, (T)aK, rd, nullptr, nullptr, gate);
+  kfn<<<grid, kBlock, smem, s>>>(ht, m, rpad, rs, p, q, (T)aM, (T)aK, rd, red ? sc : nullptr, red ? ptq_out : nullptr,
+                                 gate);
   return cudaGetLastError();
 }
 template cudaError_t launch_ebe_hex<double>(const HexTiles&, const MeshView&, int, const double*, double*, double,

@@ -259,9 +259,9 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_outer_resid(MeshView m, int rp
 }
 
 // x += d (FP64 accumulation of the FP32 correction); block 0 adds the inner iteration counts.
-__global__ void k_refine(int64_t n_items, int rpad, double* __restrict__ x, const float* __restrict__ d,
+__global__ void k_refine(int64_t n_items, int ncase, double* __restrict__ x, const float* __restrict__ d,
                          CgCase* outer, const CgCase* inner) {
-  if (blockIdx.x == 0 && threadIdx.x < rpad) {
+  if (blockIdx.x == 0 && threadIdx.x < ncase) {
     outer[threadIdx.x].iters += inner[threadIdx.x].iters;
     if (inner[threadIdx.x].status == FEM_ERR_BREAKDOWN || inner[threadIdx.x].status == FEM_ERR_NONFINITE)
       outer[threadIdx.x].status = inner[threadIdx.x].status;
@@ -334,10 +334,10 @@ cudaError_t launch_outer_resid(const MeshView& m, int rpad, const double* b, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_refine_counts(const MeshView& m, int rpad, double* x, const float* d32, CgCase* outer,
+cudaError_t launch_refine_counts(const MeshView& m, int rpad, int ncase, double* x, const float* d32, CgCase* outer,
                                  const CgCase* inner, cudaStream_t s) {
   const int64_t n = m.N * 3 * rpad;
-  k_refine<<<grid_for(n), kBlock, 0, s>>>(n, rpad, x, d32, outer, inner);
+  k_refine<<<grid_for(n), kBlock, 0, s>>>(n, ncase, x, d32, outer, inner);
   return cudaGetLastError();
 }
 

@@ -285,12 +285,13 @@ __global__ void k_rhs_incr(MeshView m, int rpad, int rshift, double c_mv, double
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = i >> rshift;
     const int c = (int)(i & (rpad - 1));
+    const int cs = m.seg ? m.seg[n] : c;            // case of this entry (fused groups: the node's mesh)
     const uint8_t f = m.freemask[n];
-    const RickerSrc s = src[c];
+    const RickerSrc s = src[cs];
     double fv[3] = {0.0, 0.0, 0.0};
     if (s.node == n) {
       if (ext) {
-        for (int k = 0; k < 3; ++k) fv[k] = ext[c * 3 + k];
+        for (int k = 0; k < 3; ++k) fv[k] = ext[cs * 3 + k];
       } else {
         const double arg = (M_PI * s.f0 * (t - s.t0)) * (M_PI * s.f0 * (t - s.t0));
         const double w = s.amp * (1.0 - 2.0 * arg) * exp(-arg);

@@ -45,7 +45,8 @@ class fem_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("predictor", ctypes.c_int), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("s_max", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("tau", ctypes.c_double), ("snapshot_fp32", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("refresh_every", ctypes.c_int), ("cert_df", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("refresh_every", ctypes.c_int), ("cert_df", ctypes.c_int), ("fuse_meshes", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class fem_profile(ctypes.Structure):

@@ -1,0 +1,88 @@
+"""Fused groups: cases on meshes of different sizes solved as one system (one launch per kernel for all
+cases, Algorithm 1's scalars per case).  Every case's every step is certified against the oracle's CSR
+matrix of that case's own mesh, and the fused history matches the unfused (one system per mesh) history
+within the solver tolerance (both certified at 1e-9 here; kappa of these systems < 1e2)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_20380_gb300 import build, fem
+from paper_2409_20380_gb300 import workload as wl
+from helpers import small_mesh
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [(6, 5, 4), (9, 6, 5), (5, 7, 3), (8, 8, 6)]
+
+
+@pytest.fixture(scope="module")
+def setup():
+    build.build()
+    fem.lib()
+    tp = wl.config2_time_params()
+    meshes = [small_mesh(*d, h=1.0 / 64, seed_mesh=20 + i) for i, d in enumerate(DIMS)]
+    srcs = [wl.random_source(m, wl.rng_for(94, i, 0)) for i, m in enumerate(meshes)]
+    return tp, meshes, srcs
+
+
+def _run(tp, meshes, srcs, fuse, n_steps, certify):
+    opts = fem.fem_opts_default(tol=1e-9, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=8,
+                                fuse_meshes=fuse)
+    hs = []
+    for m in meshes:
+        h = fem.fem_mesh_create(m, tp)
+        fem.fem_mesh_set_regions(h, wl.region_map(m, 48))
+        hs.append(h)
+    bt = fem.fem_batch_create(opts)
+    systems = [oracle.build_system(m, tp) for m in meshes] if certify else None
+    try:
+        for h, s in zip(hs, srcs):
+            fem.fem_case_add(bt, h, s)
+        prev = [(np.zeros(3 * m.n_nodes),) * 3 for m in meshes]
+        for it in range(1, n_steps + 1):
+            st, iters, relres = fem.fem_step(bt, 1, len(meshes))
+            for c, m in enumerate(meshes):
+                N = m.n_nodes
+                cur = tuple(fem.fem_case_get(bt, c, f, N) for f in (fem.FEM_FIELD_U, fem.FEM_FIELD_V, fem.FEM_FIELD_A))
+                if certify:
+                    sysm, A = systems[c]
+                    du = fem.fem_case_get(bt, c, fem.FEM_FIELD_DU, N)
+                    b_gpu = fem.fem_case_get(bt, c, fem.FEM_FIELD_B, N)
+                    f = oracle.point_force(3 * N, srcs[c], it * tp.dt)
+                    b = oracle.newmark_rhs(sysm, f, *prev[c])
+                    b[m.fixed_dof == 1] = 0.0
+                    nb = np.linalg.norm(b)
+                    assert np.linalg.norm(b_gpu - b) <= 1e-12 * nb, (it, c)
+                    cert = np.linalg.norm(b[sysm.free] - A @ du[sysm.free]) / nb
+                    assert cert < 1e-9, (it, c, cert)
+                    assert abs(relres[c] - cert) <= 1e-12 + 1e-6 * cert
+                prev[c] = cur
+        out = np.concatenate([p[0] for p in prev])
+        field = np.zeros(sum(3 * m.n_nodes for m in meshes))
+        fem.fem_batch_get_field(bt, fem.FEM_FIELD_U, field)
+        assert np.array_equal(field, out)
+        return out
+    finally:
+        fem.fem_batch_destroy(bt)
+        for h in hs:
+            fem.fem_mesh_destroy(h)
+
+
+def test_fused_uneven_meshes(setup):
+    tp, meshes, srcs = setup
+    u_f = _run(tp, meshes, srcs, 1, 30, certify=True)
+    u_u = _run(tp, meshes, srcs, 0, 30, certify=False)
+    assert np.linalg.norm(u_f - u_u) <= 1e-6 * np.linalg.norm(u_u)
+
+
+def test_fused_rejects_fp64(setup):
+    tp, meshes, srcs = setup
+    h = fem.fem_mesh_create(meshes[0], tp)
+    bt = fem.fem_batch_create(fem.fem_opts_default(fuse_meshes=1))
+    try:
+        fem.fem_case_add(bt, h, srcs[0])
+        with pytest.raises(fem.FemError):
+            fem.fem_step(bt, 1, 1)
+    finally:
+        fem.fem_batch_destroy(bt)
+        fem.fem_mesh_destroy(h)
