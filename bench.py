@@ -34,12 +34,15 @@ if ROOT not in sys.path:
 METRIC = "time-steps/s over all cases at rel. residual 1e-8; EBE matvec HBM GB/s vs peak"
 UNIT = "case-steps/s"
 FLOP_PER_ELEM_CASE = 190.0     # factorised tet4 apply + consistent mass + fused p^T A p (FMA = 2 flops)
+# FP64 split product (M p and K p separately): 157 flops (FMA = 2) in 115 FP64 instructions per element and case
+FLOP_PER_ELEM_CASE_SPLIT = 157.0
+DP_INSTR_PER_ELEM_CASE_SPLIT = 115.0
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=150)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--spinup", type=int, default=250)
@@ -126,6 +129,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def ncu_traffic(kernel_tag, sources):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one kernel, from the committed
+    ncu summary profiles/<kernel_tag>.md, or None when that summary is missing or the kernel's source files
+    changed since it was taken (the summary records their sha256)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", kernel_tag + ".md")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for f in sources:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    traffic, digest = None, None
+    for line in open(path):
+        if line.startswith("traffic_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1])
+        elif line.startswith("source_sha256:"):
+            digest = line.split(":", 1)[1].strip()
+    return traffic if digest == h.hexdigest() else None
+
+
+EBE_SOURCES = ["paper_2409_20380_gb300/csrc/k_ebe.cu", "paper_2409_20380_gb300/csrc/fem_internal.cuh"]
+
+
 def workload(args, rank):
     from paper_2409_20380_gb300 import workload as wl
     Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
@@ -134,7 +160,7 @@ def workload(args, rank):
     return mesh, srcs, wl.config2_time_params(), wl.region_map(mesh, args.region_nodes)
 
 
-def cpu_baseline(args, mesh, srcs, tp, regions, n_case_steps=8):
+def cpu_baseline(args, mesh, srcs, tp, regions, n_case_steps=40):
     """The FP64 oracle, as it stands, on case 0 of the same workload from rest (bounded sample)."""
     import numpy as np
     import oracle
@@ -236,10 +262,12 @@ def run_ours(args):
     sampler.start()
     barrier()
     torch.cuda.synchronize()
+    torch.cuda.profiler.start()        # ncu --profile-from-start off captures the timed region only
     ev0.record(stream)
     st, iters, relres = fem.fem_step(bt, args.steps, nc)
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     barrier()
     clocks = sampler.stop()
     prof = fem.fem_batch_profile(bt, 0)
@@ -308,36 +336,58 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
-    # ---- roofline of the dominant kernel ----
+    # ---- roofline of the dominant kernel (largest measured time per step) ----
     hbm_peak, peak_kind, sm_max = peaks()
     E = mesh.n_elems
     rpad = 1 << (nc - 1).bit_length()
+    bytes32 = E * (16 + 12 * 4) + rpad * N * 3 * (4 + 4)
+    bytes64 = E * (16 + 12 * 8) + rpad * N * 3 * (8 + 8 + 8)      # p read, M p and K p written
+    inner = None
     if prof["ebe32_launches"] > 0:
-        avg_ms = prof["ebe32_ms"] / prof["ebe32_launches"]
-        w_val = 4
-        kernel = "k_ebe (FP32, %d cases)" % rpad
+        avg32 = prof["ebe32_ms"] / prof["ebe32_launches"]
+        fl = FLOP_PER_ELEM_CASE * E * rpad
+        gbs = bytes32 / (avg32 * 1e-3) / 1e9
+        alu32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32: 152 SMs x 128 lanes x FMA x max clock
+        inner = {"kernel": "k_ebe_hex<float> (FP32 EBE product A p, %d cases)" % rpad, "avg_launch_ms": avg32,
+                 "launches": prof["ebe32_launches"], "alg_bytes_per_launch": bytes32, "alg_flops_per_launch": fl,
+                 "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak, "hbm_peak_kind": peak_kind,
+                 "tflops": fl / (avg32 * 1e-3) / 1e12, "alu_peak_tflops": alu32,
+                 "alu_frac": fl / (avg32 * 1e-3) / 1e12 / alu32,
+                 "traffic": ncu_traffic("ebe_hex_f32_medium16", EBE_SOURCES)}
+    if prof["ebe64_launches"] > 0 and prof["ebe64_ms"] >= prof["ebe32_ms"]:
+        avg = prof["ebe64_ms"] / prof["ebe64_launches"]
+        fl = FLOP_PER_ELEM_CASE_SPLIT * E * rpad
+        alu64 = 152 * 2 * 2 * sm_max * 1e6 / 1e12      # FP64: 152 SMs x 2 DFMA/clk x 2 flops x max clock
+        achieved = fl / (avg * 1e-3) / 1e12
+        gbs = bytes64 / (avg * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu64, "unit": "TFLOP/s", "frac": achieved / alu64,
+                "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock",
+                "traffic": ncu_traffic("ebe_split_f64_medium16", EBE_SOURCES),
+                "kernel": "k_ebe_split (FP64 certification product M p, K p, %d cases)" % rpad,
+                "avg_launch_ms": avg, "launches": prof["ebe64_launches"], "alg_bytes_per_launch": bytes64,
+                "alg_flops_per_launch": fl,
+                "fp64_issue_frac": DP_INSTR_PER_ELEM_CASE_SPLIT * E * rpad / (avg * 1e-3) / (152 * 2 * sm_max * 1e6),
+                "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak}
+    elif inner is not None:
+        t_hbm = bytes32 / (hbm_peak * 1e9)
+        t_alu = inner["alg_flops_per_launch"] / (inner["alu_peak_tflops"] * 1e12)
+        if t_alu > t_hbm:
+            roof = {"bound": "alu", "achieved": inner["tflops"], "peak": inner["alu_peak_tflops"], "unit": "TFLOP/s",
+                    "frac": inner["alu_frac"], "peak_kind": "derived from unit counts x max SM clock"}
+        else:
+            roof = {"bound": "hbm", "achieved": inner["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": inner["hbm_frac"], "peak_kind": peak_kind}
+        roof.update({k: inner[k] for k in ("kernel", "avg_launch_ms", "launches", "alg_bytes_per_launch",
+                                           "alg_flops_per_launch", "hbm_gbs", "hbm_frac", "hbm_peak", "traffic")})
+        inner = None
     else:
-        avg_ms = prof["ebe64_ms"] / max(prof["ebe64_launches"], 1)
-        w_val = 8
-        kernel = "k_ebe (FP64, %d cases)" % rpad
-    rec_b = 12 * w_val
-    bytes_launch = E * (16 + rec_b) + rpad * N * 3 * (w_val + w_val)
-    flops_launch = FLOP_PER_ELEM_CASE * E * rpad
-    gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
-    tfs = flops_launch / (avg_ms * 1e-3) / 1e12
-    # FP32 ALU peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x max clock; FP64: 152 x 4 flop
-    alu_peak = 152 * (128 if w_val == 4 else 4) * 2 * sm_max * 1e6 / 1e12
-    t_hbm = bytes_launch / (hbm_peak * 1e9)
-    t_alu = flops_launch / (alu_peak * 1e12)
-    if t_alu > t_hbm:
-        roof = {"bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfs / alu_peak,
-                "peak_kind": "derived from unit counts x max SM clock", "traffic": None}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                "peak_kind": peak_kind, "traffic": None}
-    roof.update({"kernel": kernel, "avg_launch_ms": avg_ms, "launches": prof["ebe32_launches"] or prof["ebe64_launches"],
-                 "alg_bytes_per_launch": bytes_launch, "alg_flops_per_launch": flops_launch,
-                 "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak})
+        avg = prof["ebe64_ms"] / max(prof["ebe64_launches"], 1)
+        fl = FLOP_PER_ELEM_CASE * E * rpad
+        alu64 = 152 * 2 * 2 * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": fl / (avg * 1e-3) / 1e12, "peak": alu64, "unit": "TFLOP/s",
+                "frac": fl / (avg * 1e-3) / 1e12 / alu64, "peak_kind": "derived: FP64 unit counts x max SM clock",
+                "traffic": None, "kernel": "k_ebe_hex<double> (FP64 EBE product, %d cases)" % rpad,
+                "avg_launch_ms": avg, "launches": prof["ebe64_launches"]}
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(args, mesh, srcs, tp, regions)
@@ -345,7 +395,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": config_dict(args, mesh), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "config": config_dict(args, mesh), "roofline": roof, "roofline_inner_ebe": inner, "cpu_baseline": cpu,
+        "e2e": e2e,
         "gpu_launches": prof["kernel_launches"], "clocks": clocks,
         "cg_iters_per_case_step": float(iters.sum()) / (nc * args.steps),
         "max_certified_relres": float(relres.max()), "status": int(st),
@@ -354,6 +405,10 @@ def run_ours(args):
         "kernel_ms_per_step": {"ebe32": prof["ebe32_ms"] / max(prof["steps"], 1),
                                "ebe64": prof["ebe64_ms"] / max(prof["steps"], 1),
                                "cg_vec": prof["cg_vec_ms"] / max(prof["steps"], 1)},
+        "kernel_launches_per_step": {"ebe32": prof["ebe32_launches"] / max(prof["steps"], 1),
+                                     "ebe64": prof["ebe64_launches"] / max(prof["steps"], 1),
+                                     "cg_vec": prof["cg_vec_launches"] / max(prof["steps"], 1),
+                                     "all": prof["kernel_launches"] / max(prof["steps"], 1)},
         "fp64_plain_comparator": comparator,
     }
     print(json.dumps(out), flush=True)
