@@ -384,8 +384,10 @@ class CaseSimulator:
         free = self.sysm.free
         u_ab = adams_bashforth4(self.u, self.v_hist, dt)
         du_ab = (u_ab - self.u)[free]
+        self.last_W, self.last_npairs = None, 0
         if self.predictor == "dd" and self.region_of_dof is not None:
-            y, _ = regional_predict(self.E_hist, self.region_of_dof, self.n_regions, self.s_max, self.tau)
+            y, W = regional_predict(self.E_hist, self.region_of_dof, self.n_regions, self.s_max, self.tau)
+            self.last_W, self.last_npairs = W, max(0, min(self.s_max, len(self.E_hist) - 1))
             if y is not None:
                 return du_ab + y, du_ab
         return du_ab, du_ab

@@ -252,3 +252,30 @@ def ricker_load(src: Source, t: float) -> np.ndarray:
     """Point-force vector [3] that source `src` applies at time t (a case's load input at its node)."""
     arg = (math.pi * src.f0 * (t - src.t0)) ** 2
     return src.amp * (1.0 - 2.0 * arg) * math.exp(-arg) * np.asarray(src.direction, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------------------------------------
+# Learned proposal: initial network weights (seeded draws only; the network itself lives elsewhere).
+# --------------------------------------------------------------------------------------------------------
+
+MLP_LAYERS = (64, 256, 256, 32)
+
+
+def mlp_init_weights(seed: int = 0) -> np.ndarray:
+    """He-uniform draws for the 64-256-256-32 network, flat in the order W1 [256][64], b1 [256],
+    W2 [256][256], b2 [256], W3 [32][256], b3 [32]: W ~ U(-sqrt(6 / fan_in), +sqrt(6 / fan_in)), b = 0."""
+    rng = np.random.default_rng(np.random.SeedSequence([20380, 5, 0, seed, 9]))
+    parts = []
+    for i in range(3):
+        fan_in, fan_out = MLP_LAYERS[i], MLP_LAYERS[i + 1]
+        lim = math.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts)
+
+
+def config5_sources(mesh: Mesh, n_train: int = 200, n_eval: int = 32):
+    """Training and held-out sources on the medium mesh; the two seed ranges are disjoint."""
+    train = [random_source(mesh, rng_for(5, 0, c, 2)) for c in range(n_train)]
+    held = [random_source(mesh, rng_for(5, 0, 100000 + c, 2)) for c in range(n_eval)]
+    return train, held
