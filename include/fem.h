@@ -286,6 +286,58 @@ fem_status fem_case_stats(fem_batch* b, int case_id, fem_case_stats_t* out);
 /* Number of completed steps of the batch. */
 fem_status fem_batch_steps(const fem_batch* b, int* steps_out);
 
+/* ---------------------------------------------------------------------------------------------------
+ * Learned proposal: the learned form of the data-driven predictor (Section 3.2).  For every region R and
+ * case, the predictor's coefficients c_R on the stored outputs Y_R (y_R = Y_R c_R) are corrected by a
+ * network:  c_R + net(x_R),  x_R = [(source - centroid_R) / L, (f0 - 5) / 3, c_R in age order (newest pair
+ * first), zeros] (64 inputs; L = largest edge of the mesh's bounding box).  The network is 64 -> 256 ->
+ * 256 -> 32 with GELU (erf form) after the first two layers, BF16 weights and activations, FP32
+ * accumulation on the tensor cores.  It is trained to the best coefficients in the same basis,
+ * t_R = argmin ||Y_R c - e_R^it|| - c_R, from samples the time step itself collects.  In a step, a case
+ * takes the proposal only if its initial residual is smaller than the plain guess's (PCG to the same
+ * certified tolerance follows either way).
+ *
+ * Parameters: FP32 vector of FEM_MLP_N_PARAMS values in the order W1 [256][64], b1 [256], W2 [256][256],
+ * b2 [256], W3 [32][256], b3 [32]; layer l computes z = W_l a + b_l.  Gradients use the same layout.
+ * --------------------------------------------------------------------------------------------------- */
+#define FEM_MLP_N_PARAMS 90656
+#define FEM_MLP_IN 64
+#define FEM_MLP_OUT 32
+typedef struct fem_mlp fem_mlp;
+
+/* Creates a network from host parameters (copied) on the current device; Adam moments start at zero.
+ * `stream` orders the network's own calls (forward, gradient, training). */
+fem_status fem_mlp_create(const float* params, void* stream, fem_mlp** out);
+fem_status fem_mlp_destroy(fem_mlp* net);
+/* Current FP32 master parameters -> host [FEM_MLP_N_PARAMS] (synchronises the network's stream). */
+fem_status fem_mlp_get_params(fem_mlp* net, float* params);
+/* out_dev [B][32] = net(x_dev [B][64]) (device buffers, FP32; inputs rounded to BF16 inside). */
+fem_status fem_mlp_forward(fem_mlp* net, const float* x_dev, int64_t B, float* out_dev);
+/* Mean squared error of net(x) against t over the B x 32 outputs and its gradient (grad_dev
+ * [FEM_MLP_N_PARAMS] device FP32, may be NULL); the loss goes to *loss_out (host).  Synchronises. */
+fem_status fem_mlp_loss_grad(fem_mlp* net, const float* x_dev, const float* t_dev, int64_t B, float* grad_dev,
+                             double* loss_out);
+/* n_updates Adam steps (lr, beta = 0.9 / 0.999, eps = 1e-8, bias-corrected) on minibatches of `batch` rows
+ * of (x_dev [n_samples][64], t_dev [n_samples][32]); order_dev [n_updates][batch] (device int32) lists the
+ * sample rows of each minibatch (the caller draws the shuffling).  loss_out: host [n_updates] losses before
+ * each update, or NULL.  A row index outside [0, n_samples) returns FEM_ERR_ARG (that row counts as zero). */
+fem_status fem_mlp_train(fem_mlp* net, const float* x_dev, const float* t_dev, int64_t n_samples,
+                         const int32_t* order_dev, int n_updates, int batch, double lr, double* loss_out);
+
+/* Uses `net` (NULL: none) for the learned proposal in the batch's next steps.  Needs FEM_FP32_INNER, the
+ * data-driven predictor, regions and groups of one mesh (no fuse_meshes).  The caller keeps ownership and
+ * must not train the network while the batch steps. */
+fem_status fem_batch_set_mlp(fem_batch* b, fem_mlp* net);
+/* Starts collecting training samples into caller-owned device buffers x_dev [capacity][64] and t_dev
+ * [capacity][32] (NULL x_dev stops).  Every following step that made a data-driven prediction appends
+ * n_regions x n_cases rows (region-major, then case) while they fit.  Same requirements as
+ * fem_batch_set_mlp. */
+fem_status fem_batch_collect(fem_batch* b, float* x_dev, float* t_dev, int64_t capacity);
+/* Rows collected so far; *full = 1 if a step's rows no longer fit. */
+fem_status fem_batch_collected(fem_batch* b, int64_t* rows, int* full);
+/* Case-steps in which the learned proposal was taken / rejected (initial residual not smaller). */
+fem_status fem_batch_proposal_counts(fem_batch* b, long long* taken, long long* rejected);
+
 /* Message of the last error on this thread ("" if none). */
 const char* fem_last_error(void);
 

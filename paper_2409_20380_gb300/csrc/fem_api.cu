@@ -233,6 +233,8 @@ struct fem_mesh {
   float* binv32 = nullptr;
   uint8_t* fm = nullptr;
   int n_regions = 0;
+  float* reg_cent = nullptr;        // [R][3] centroid of each region's nodes (learned-proposal features)
+  float inv_extent = 1.0f;          // 1 / largest edge of the bounding box
   int32_t* reg_lo = nullptr;
   int32_t* reg_hi = nullptr;
   std::vector<Workspace*> ws;
@@ -253,7 +255,7 @@ struct fem_mesh {
   MeshView view() const { return MeshView{N, E, conn, rec64, rec32, binv64, binv32, fm, seg, nseg}; }
   ~fem_mesh() {
     dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(rec_df); dfree(D);
-    dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi); dfree(seg);
+    dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi); dfree(seg); dfree(reg_cent);
     for (auto* w : ws) delete w;
     for (void* b : tile_bufs) cudaFree(b);
   }
@@ -467,6 +469,17 @@ struct Group {
   double *Ku = nullptr, *Mv = nullptr, *Kv = nullptr, *Ma = nullptr, *Av[4] = {nullptr, nullptr, nullptr, nullptr};
   double *qM = nullptr, *qK = nullptr;
   bool use_ext = false;
+  // learned proposal and training-sample collection (allocated on first use)
+  float* F = nullptr;             // features [Mpad][64] of this step's prediction, row R * rpad + c
+  double* dw = nullptr;           // proposal's coefficient correction [R][rpad][kMaxSlots]
+  double* wbest = nullptr;        // best coefficients of the solved correction [R][rpad][kMaxSlots]
+  double* ydelta = nullptr;       // Y dw [n]
+  int* choose = nullptr;          // [rpad] 1 = the case takes the proposal this step
+  long long* counts = nullptr;    // [2] steps where cases took / rejected the proposal
+  float4* case_src = nullptr;     // [rpad] source position and (f0 - 5) / 3
+  int last_npairs = 0;            // pairs used by this step's prediction
+  bool featured = false;          // F holds this step's features
+  bool proposed = false;          // ydelta holds this step's proposal
   Workspace* ws = nullptr;
   int steps = 0;
   std::vector<int> iters_acc;
@@ -480,6 +493,7 @@ struct Group {
     dfree(gram); dfree(wcoef); dfree(dpart); dfree(slot_lists); dfree(src); dfree(ext);
     dfree(Ku); dfree(Mv); dfree(Kv); dfree(Ma); dfree(qM); dfree(qK);
     for (auto& v : Av) dfree(v);
+    dfree(F); dfree(dw); dfree(wbest); dfree(ydelta); dfree(choose); dfree(counts); dfree(case_src);
     if (h_slots) cudaFreeHost(h_slots);
     delete ws;
     delete owned_mesh;
@@ -494,6 +508,11 @@ struct fem_batch {
   std::vector<std::pair<int, int>> loc;   // case -> (group, lane)
   bool started = false;
   int steps = 0;
+  fem_mlp* mlp = nullptr;              // learned proposal (caller-owned), or none
+  float* col_x = nullptr;              // caller-owned sample buffers [capacity][64] / [capacity][32]
+  float* col_t = nullptr;
+  int64_t col_cap = 0, col_n = 0;
+  bool col_full = false;
   ~fem_batch() {
     for (auto* g : groups) delete g;
   }
@@ -585,9 +604,39 @@ static PredView pred_view(const fem_batch* bt, const Group* g) {
 
 static int slot_of(const Group* g, int j) { return (j - 1) % g->n_slots; }  // correction e^j, j >= 1
 
+// Buffers of the learned proposal and of sample collection (first use).
+static fem_status group_learn_alloc(fem_batch* bt, Group* g) {
+  if (g->F) return FEM_OK;
+  if (g->owned_mesh) return fail(FEM_ERR_ARG, "the learned proposal and sample collection need groups of one mesh");
+  const int64_t rows = (int64_t)std::max(1, g->n_regions) * g->rpad;
+  const int64_t mpad = ((rows + 63) / 64) * 64;
+  CHK(dalloc(&g->F, (size_t)(mpad * 64)));
+  CHK(dalloc(&g->dw, (size_t)(rows * kMaxSlots)));
+  CHK(dalloc(&g->wbest, (size_t)(rows * kMaxSlots)));
+  CHK(dalloc(&g->ydelta, (size_t)g->n));
+  CHK(dalloc(&g->choose, (size_t)g->rpad));
+  CHK(dalloc(&g->counts, 2));
+  CHK(dalloc(&g->case_src, (size_t)g->rpad));
+  std::vector<float4> cs(g->rpad, make_float4(0.f, 0.f, 0.f, 0.f));
+  const std::vector<double>& xyz = g->mesh->h_xyz;
+  for (int l = 0; l < (int)g->cases.size(); ++l) {
+    const RickerSrc& r = g->hsrc[l];
+    if (r.node < 0) continue;
+    cs[l] = make_float4((float)xyz[3 * (size_t)r.node], (float)xyz[3 * (size_t)r.node + 1],
+                        (float)xyz[3 * (size_t)r.node + 2], (float)((r.f0 - 5.0) / 3.0));
+  }
+  cudaStream_t s = bt->s;
+  CU(cudaMemcpyAsync(g->case_src, cs.data(), sizeof(float4) * g->rpad, cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(g->counts, 0, 2 * sizeof(long long), s));
+  CU(cudaStreamSynchronize(s));
+  return FEM_OK;
+}
+
 // Initial guess of the increment for step it = g->steps + 1 into `out`: AB4 (+ regional correction).
-static fem_status group_predict(fem_batch* bt, Group* g, double* out, bool* corrected = nullptr) {
+// learn: this is the time step's own prediction (features, learned proposal).
+static fem_status group_predict(fem_batch* bt, Group* g, double* out, bool* corrected = nullptr, bool learn = false) {
   if (corrected) *corrected = false;
+  if (learn) g->featured = g->proposed = false, g->last_npairs = 0;
   const int it = g->steps + 1;
   const double dt = g->mesh->tp.dt;
   auto vslot = [&](int j) { return g->vh[((j % 4) + 4) % 4]; };
@@ -608,7 +657,23 @@ static fem_status group_predict(fem_batch* bt, Group* g, double* out, bool* corr
   CU(cudaMemcpyAsync(g->slot_lists, g->h_slots, sizeof(int) * 2 * kMaxSlots, cudaMemcpyHostToDevice, s));
   const PredView pv = pred_view(bt, g);
   CU(launch_pred_solve(pv, g->slot_lists, n_pairs, slot_of(g, it - 1), bt->opts.tau, s));
-  CU(launch_pred_combine(pv, g->slot_lists + kMaxSlots, n_pairs, out, s));
+  if (learn && (bt->mlp || bt->col_x)) {
+    CHK(group_learn_alloc(bt, g));
+    CU(mlp_features(pv, n_pairs, g->case_src, g->mesh->reg_cent, g->mesh->inv_extent, g->F, s));
+    g->featured = true;
+    g->last_npairs = n_pairs;
+    g->ws->count();
+  }
+  if (learn && bt->mlp) {
+    // learned proposal: coefficients c + net(features); its difference to the plain guess, Y dw, is kept
+    CU(mlp_propose(bt->mlp, g->F, (int64_t)g->n_regions * g->rpad, n_pairs, g->dw, s));
+    CU(cudaMemsetAsync(g->ydelta, 0, sizeof(double) * g->n, s));
+    CU(launch_pred_combine2(pv, g->slot_lists + kMaxSlots, n_pairs, out, g->dw, g->ydelta, s));
+    g->proposed = true;
+    g->ws->count(6);
+  } else {
+    CU(launch_pred_combine(pv, g->slot_lists + kMaxSlots, n_pairs, out, s));
+  }
   g->ws->count(2);
   if (corrected) *corrected = true;
   // the pinned slot list is reused next step: order the host write after this step's copy
@@ -657,7 +722,7 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   // 1. initial guess (Section 3.2)
   int ph = w->pbeg(P_PREDICT, s);
   bool corrected = false;
-  CHK(group_predict(bt, g, g->guess, &corrected));
+  CHK(group_predict(bt, g, g->guess, &corrected, true));
   w->pend(ph, s);
   // 2. right-hand side (Section 3.1, Eq. GE:DIS) from the recurrences
   ph = w->pbeg(P_RHS, s);
@@ -683,6 +748,17 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   } else {
     CU(launch_r0(mv, g->rpad, dt, g->b, aslot(it - 4), aslot(it - 3), aslot(it - 2), aslot(it - 1), qy, w->r32, red,
                  w->outer, w->n_active, o.tol, o.inner_tol, s));
+  }
+  if (g->proposed) {
+    // learned proposal: r0' = r0 - A32 (Y dw); a case takes it where its initial residual is smaller
+    CU(mlp_to_f32(g->n, g->ydelta, w->z32, s));
+    int pe = w->pbeg(P_EBE32, s);
+    CU(ebe_product<float>(m, g->rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
+    w->pend(pe, s);
+    CU(mlp_choose(mv, g->rpad, w->r32, w->q32, red, w->outer, w->n_active, o.tol, o.inner_tol, g->ncase, g->choose,
+                  g->counts, s));
+    CU(mlp_apply(g->n, g->rpad, g->choose, w->r32, w->q32, g->guess, g->ydelta, s));
+    w->count(4);
   }
   CU(cudaMemcpyAsync(g->x, g->guess, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
   w->count();
@@ -743,6 +819,21 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     for (int j = it - n_e + 1; j <= it; ++j) mask |= 1ull << slot_of(g, j);
     CU(launch_pred_dots(pred_view(bt, g), slot_of(g, it), mask, s));
     w->count();
+    // training samples: features of this step's prediction, targets from the solved correction e^it
+    if (bt->col_x && g->featured && g->last_npairs > 0) {
+      const int64_t rows = (int64_t)g->n_regions * g->ncase;
+      if (bt->col_n + rows <= bt->col_cap) {
+        PredView pt = pred_view(bt, g);
+        pt.w = g->wbest;
+        CU(launch_pred_solve(pt, g->slot_lists + kMaxSlots, g->last_npairs, slot_of(g, it), o.tau, s));
+        CU(mlp_collect(g->n_regions, g->rpad, g->ncase, g->last_npairs, g->F, g->wbest, g->wcoef, bt->col_n,
+                       bt->col_x, bt->col_t, s));
+        bt->col_n += rows;
+        w->count(2);
+      } else {
+        bt->col_full = true;
+      }
+    }
   }
   w->pend(ph, s);
   CU(cudaStreamSynchronize(s));
@@ -1012,12 +1103,33 @@ fem_status fem_mesh_set_regions(fem_mesh* m, const int32_t* region_of_node) {
   }
   dfree(m->reg_lo);
   dfree(m->reg_hi);
+  dfree(m->reg_cent);
   m->n_regions = 0;
   m->h_region.assign(region_of_node, region_of_node + m->N);
+  // region centroids and the domain extent (inputs of the learned proposal)
+  std::vector<double> cs(3 * (size_t)R, 0.0), cnt(R, 0.0);
+  double bmin[3] = {INFINITY, INFINITY, INFINITY}, bmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t n = 0; n < m->N; ++n) {
+    for (int k = 0; k < 3; ++k) {
+      bmin[k] = std::min(bmin[k], m->h_xyz[3 * n + k]);
+      bmax[k] = std::max(bmax[k], m->h_xyz[3 * n + k]);
+    }
+    const int r = region_of_node[n];
+    if (r < 0) continue;
+    for (int k = 0; k < 3; ++k) cs[3 * (size_t)r + k] += m->h_xyz[3 * n + k];
+    cnt[r] += 1.0;
+  }
+  std::vector<float> cf(3 * (size_t)R);
+  for (int r = 0; r < R; ++r)
+    for (int k = 0; k < 3; ++k) cf[3 * (size_t)r + k] = (float)(cs[3 * (size_t)r + k] / cnt[r]);
+  const double ext = std::max(bmax[0] - bmin[0], std::max(bmax[1] - bmin[1], bmax[2] - bmin[2]));
+  m->inv_extent = ext > 0.0 ? (float)(1.0 / ext) : 1.0f;
   CHK(dalloc(&m->reg_lo, R));
   CHK(dalloc(&m->reg_hi, R));
+  CHK(dalloc(&m->reg_cent, 3 * (int64_t)R));
   CU(cudaMemcpy(m->reg_lo, lo.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(m->reg_hi, hi.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(m->reg_cent, cf.data(), sizeof(float) * 3 * R, cudaMemcpyHostToDevice));
   m->n_regions = R;
   return FEM_OK;
 }
@@ -1319,6 +1431,69 @@ fem_status fem_batch_set_loads(fem_batch* b, const double* loads) {
     CU(cudaMemcpyAsync(g->ext + 3 * l, loads + 3 * c, 3 * sizeof(double), cudaMemcpyHostToDevice, b->s));
     g->use_ext = true;
   }
+  return FEM_OK;
+}
+
+static fem_status learn_ok(const fem_batch* b) {
+  if (b->opts.precision != FEM_FP32_INNER) return fail(FEM_ERR_ARG, "the learned proposal needs FEM_FP32_INNER");
+  if (b->opts.predictor != FEM_PRED_DD) return fail(FEM_ERR_ARG, "the learned proposal needs the data-driven predictor");
+  if (b->opts.fuse_meshes) return fail(FEM_ERR_ARG, "the learned proposal needs groups of one mesh (no fuse_meshes)");
+  return FEM_OK;
+}
+
+fem_status fem_batch_set_mlp(fem_batch* b, fem_mlp* net) {
+  g_err.clear();
+  if (!b) return fail(FEM_ERR_ARG, "batch is null");
+  if (net) {
+    CHK(learn_ok(b));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (mlp_device(net) != dev) return fail(FEM_ERR_ARG, "the network lives on another device");
+  }
+  b->mlp = net;
+  return FEM_OK;
+}
+
+fem_status fem_batch_collect(fem_batch* b, float* x_dev, float* t_dev, int64_t capacity) {
+  g_err.clear();
+  if (!b) return fail(FEM_ERR_ARG, "batch is null");
+  if (!x_dev) {
+    b->col_x = b->col_t = nullptr;
+    b->col_cap = 0;
+    return FEM_OK;
+  }
+  if (!t_dev || capacity <= 0) return fail(FEM_ERR_ARG, "t_dev is null or capacity <= 0");
+  CHK(learn_ok(b));
+  b->col_x = x_dev;
+  b->col_t = t_dev;
+  b->col_cap = capacity;
+  b->col_n = 0;
+  b->col_full = false;
+  return FEM_OK;
+}
+
+fem_status fem_batch_collected(fem_batch* b, int64_t* rows, int* full) {
+  g_err.clear();
+  if (!b) return fail(FEM_ERR_ARG, "batch is null");
+  if (rows) *rows = b->col_n;
+  if (full) *full = b->col_full ? 1 : 0;
+  return FEM_OK;
+}
+
+fem_status fem_batch_proposal_counts(fem_batch* b, long long* taken, long long* rejected) {
+  g_err.clear();
+  if (!b) return fail(FEM_ERR_ARG, "batch is null");
+  long long t = 0, r = 0;
+  for (auto* g : b->groups) {
+    if (!g->counts) continue;
+    long long h[2] = {0, 0};
+    CU(cudaMemcpyAsync(h, g->counts, sizeof(h), cudaMemcpyDeviceToHost, b->s));
+    CU(cudaStreamSynchronize(b->s));
+    t += h[0];
+    r += h[1];
+  }
+  if (taken) *taken = t;
+  if (rejected) *rejected = r;
   return FEM_OK;
 }
 

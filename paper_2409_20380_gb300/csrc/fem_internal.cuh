@@ -234,6 +234,23 @@ cudaError_t launch_pred_solve(const PredView& p, const int* x_slots, int n_pairs
                               cudaStream_t s);
 cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out,
                                 cudaStream_t s);
+// y_out += Y w (as launch_pred_combine) and, in the same pass over the ring, y2 = Y w2.
+cudaError_t launch_pred_combine2(const PredView& p, const int* y_slots, int n_pairs, double* y_out,
+                                 const double* w2, double* y2, cudaStream_t s);
+
+// Learned proposal (k_mlp.cu).  Rows of the network's batch are (region R, case c) -> R * rpad + c.
+cudaError_t mlp_features(const PredView& p, int n_pairs, const float4* case_src, const float* centroid,
+                         float inv_extent, float* F, cudaStream_t s);
+cudaError_t mlp_propose(fem_mlp* net, const float* F, int64_t rows, int n_pairs, double* dw, cudaStream_t s);
+cudaError_t mlp_to_f32(int64_t n, const double* x, float* y, cudaStream_t s);
+cudaError_t mlp_choose(const MeshView& m, int rpad, const float* r32, const float* qd, Reducer red, CgCase* outer,
+                       int* n_active, double tol, double inner_max, int ncase, int* choose, long long* counts,
+                       cudaStream_t s);
+cudaError_t mlp_apply(int64_t n, int rpad, const int* choose, float* r32, const float* qd, double* guess,
+                      const double* dy, cudaStream_t s);
+cudaError_t mlp_collect(int n_regions, int rpad, int ncase, int n_pairs, const float* F, const double* w_best,
+                        const double* w_pred, int64_t row0, float* x_out, float* t_out, cudaStream_t s);
+int mlp_device(const fem_mlp* n);
 
 }  // namespace fem
 

@@ -258,6 +258,52 @@ __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* 
   }
 }
 
+// Two combinations in one pass over the ring: y_out += Y w (the data-driven guess) and y2 = Y w2 (the
+// learned proposal's correction of it).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_pred_combine2(PredView p, const int* __restrict__ y_slots, int n,
+                                                          double* __restrict__ y_out, const double* __restrict__ w2,
+                                                          double* __restrict__ y2) {
+  const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
+  const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
+  const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
+  const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
+  const int rpad = p.rpad;
+  const T* ring = (const T*)p.ring;
+  __shared__ T sw[kMaxSlots * kMaxRpad];
+  __shared__ T sw2[kMaxSlots * kMaxRpad];
+  __shared__ int64_t soff[kMaxSlots];
+  for (int t = threadIdx.x; t < n * rpad; t += blockDim.x) {
+    const int a = t / rpad, c = t % rpad;
+    const int64_t o = ((int64_t)R * rpad + c) * kMaxSlots + a;
+    sw[t] = (T)p.w[o];
+    sw2[t] = (T)w2[o];
+  }
+  for (int a = threadIdx.x; a < n; a += blockDim.x) soff[a] = (int64_t)y_slots[a] * p.slot_stride;
+  __syncthreads();
+  const int c = threadIdx.x & (rpad - 1);
+  const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const int64_t gi = base + i;
+    T s0 = 0, s1 = 0, t0 = 0, t1 = 0;
+    int a = 0;
+    for (; a + 1 < n; a += 2) {
+      const T y0 = ring[soff[a] + gi], y1 = ring[soff[a + 1] + gi];
+      s0 += sw[a * rpad + c] * y0;
+      t0 += sw2[a * rpad + c] * y0;
+      s1 += sw[(a + 1) * rpad + c] * y1;
+      t1 += sw2[(a + 1) * rpad + c] * y1;
+    }
+    if (a < n) {
+      const T y0 = ring[soff[a] + gi];
+      s0 += sw[a * rpad + c] * y0;
+      t0 += sw2[a * rpad + c] * y0;
+    }
+    y_out[gi] += (double)(s0 + s1);
+    y2[gi] = (double)(t0 + t1);
+  }
+}
+
 // dst[n*3 + k] = src[(n*3 + k)*rpad + c]
 __global__ void k_extract_case(int64_t n3, int rpad, int c, const double* __restrict__ src, double* __restrict__ dst) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
@@ -569,6 +615,17 @@ cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pai
     k_pred_combine<float><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out);
   else
     k_pred_combine<double><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pred_combine2(const PredView& p, const int* y_slots, int n_pairs, double* y_out, const double* w2,
+                                 double* y2, cudaStream_t s) {
+  if (p.n_regions == 0 || n_pairs <= 0) return cudaSuccess;
+  const int grid = p.n_regions * p.n_chunks;
+  if (p.fp32)
+    k_pred_combine2<float><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, w2, y2);
+  else
+    k_pred_combine2<double><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, w2, y2);
   return cudaGetLastError();
 }
 

@@ -27,7 +27,10 @@ EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_
            "fem_ebe_apply_noalloc",
            "pcg_solve", "fem_batch_create", "fem_batch_destroy", "fem_case_add", "fem_step", "predictor_fit",
            "predictor_predict", "fem_case_get", "fem_batch_set_loads", "fem_batch_get_field", "fem_batch_profile",
-           "fem_case_stats", "fem_batch_steps", "fem_last_error")
+           "fem_case_stats", "fem_batch_steps", "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_get_params",
+           "fem_mlp_forward", "fem_mlp_loss_grad", "fem_mlp_train", "fem_batch_set_mlp", "fem_batch_collect",
+           "fem_batch_collected", "fem_batch_proposal_counts", "fem_last_error")
+FEM_MLP_N_PARAMS, FEM_MLP_IN, FEM_MLP_OUT = 90656, 64, 32
 
 
 class FemError(RuntimeError):
@@ -100,6 +103,16 @@ def lib():
         "fem_batch_profile": (I, [P, I, ctypes.POINTER(fem_profile)]),
         "fem_case_stats": (I, [P, I, ctypes.POINTER(fem_case_stats_t)]),
         "fem_batch_steps": (I, [P, ctypes.POINTER(I)]),
+        "fem_mlp_create": (I, [P, P, ctypes.POINTER(P)]),
+        "fem_mlp_destroy": (I, [P]),
+        "fem_mlp_get_params": (I, [P, P]),
+        "fem_mlp_forward": (I, [P, P, I64, P]),
+        "fem_mlp_loss_grad": (I, [P, P, P, I64, P, ctypes.POINTER(D)]),
+        "fem_mlp_train": (I, [P, P, P, I64, P, I, I, D, P]),
+        "fem_batch_set_mlp": (I, [P, P]),
+        "fem_batch_collect": (I, [P, P, P, I64]),
+        "fem_batch_collected": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I)]),
+        "fem_batch_proposal_counts": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
         "fem_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -294,6 +307,79 @@ def fem_batch_steps(batch):
     s = ctypes.c_int()
     _check(lib().fem_batch_steps(batch, ctypes.byref(s)))
     return s.value
+
+
+def fem_mlp_create(params, stream=None):
+    """params: FP32 array [90656] (host, copied)."""
+    import numpy as np
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    assert a.shape == (FEM_MLP_N_PARAMS,)
+    h = ctypes.c_void_p()
+    _check(lib().fem_mlp_create(_np_ptr(a), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def fem_mlp_destroy(h):
+    _check(lib().fem_mlp_destroy(h))
+
+
+def fem_mlp_get_params(h):
+    import numpy as np
+    out = np.empty(FEM_MLP_N_PARAMS, dtype=np.float32)
+    _check(lib().fem_mlp_get_params(h, _np_ptr(out)))
+    return out
+
+
+def fem_mlp_forward(h, x, out):
+    import torch
+    assert x.shape[-1] == FEM_MLP_IN and out.shape[-1] == FEM_MLP_OUT and x.shape[0] == out.shape[0]
+    _check(lib().fem_mlp_forward(h, _ptr(x, torch.float32), x.shape[0], _ptr(out, torch.float32)))
+
+
+def fem_mlp_loss_grad(h, x, t, grad=None):
+    import torch
+    loss = ctypes.c_double()
+    _check(lib().fem_mlp_loss_grad(h, _ptr(x, torch.float32), _ptr(t, torch.float32), x.shape[0],
+                                   _ptr(grad, torch.float32), ctypes.byref(loss)))
+    return loss.value
+
+
+def fem_mlp_train(h, x, t, order, lr=1e-3, with_loss=True):
+    """order: int32 CUDA tensor [n_updates][batch] of sample rows.  Returns the losses (numpy) or None."""
+    import numpy as np
+    import torch
+    n_up, batch = order.shape
+    losses = np.zeros(n_up) if with_loss else None
+    _check(lib().fem_mlp_train(h, _ptr(x, torch.float32), _ptr(t, torch.float32), x.shape[0],
+                               _ptr(order, torch.int32), n_up, batch, lr,
+                               _np_ptr(losses) if with_loss else None))
+    return losses
+
+
+def fem_batch_set_mlp(batch, net):
+    _check(lib().fem_batch_set_mlp(batch, net))
+
+
+def fem_batch_collect(batch, x, t):
+    """Collect training samples into CUDA tensors x [cap][64], t [cap][32] (x = None stops)."""
+    import torch
+    if x is None:
+        _check(lib().fem_batch_collect(batch, None, None, 0))
+        return
+    assert x.shape[1] == FEM_MLP_IN and t.shape[1] == FEM_MLP_OUT and x.shape[0] == t.shape[0]
+    _check(lib().fem_batch_collect(batch, _ptr(x, torch.float32), _ptr(t, torch.float32), x.shape[0]))
+
+
+def fem_batch_collected(batch):
+    rows, full = ctypes.c_int64(), ctypes.c_int()
+    _check(lib().fem_batch_collected(batch, ctypes.byref(rows), ctypes.byref(full)))
+    return rows.value, bool(full.value)
+
+
+def fem_batch_proposal_counts(batch):
+    t, r = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib().fem_batch_proposal_counts(batch, ctypes.byref(t), ctypes.byref(r)))
+    return t.value, r.value
 
 
 def fem_last_error():
