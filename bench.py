@@ -61,6 +61,17 @@ def parse():
     ap.add_argument("--kernel-precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=0, help="EBE variant: 0 auto, 1 generic, 2 tiled hex")
     ap.add_argument("--hex-per-tile", type=int, default=0)
+    ap.add_argument("--uneven", action="store_true",
+                    help="batched uneven meshes: --meshes cases on meshes of different sizes fused into one system")
+    ap.add_argument("--meshes", type=int, default=64)
+    ap.add_argument("--no-fuse", action="store_true", help="(--uneven) step one group per mesh instead")
+    ap.add_argument("--learned", action="store_true",
+                    help="learned-proposal measurement: collect, train, evaluate on held-out cases")
+    ap.add_argument("--train-cases", type=int, default=200)
+    ap.add_argument("--eval-cases", type=int, default=32)
+    ap.add_argument("--case-steps", type=int, default=500, help="steps per case (learned-proposal mode)")
+    ap.add_argument("--updates", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -463,8 +474,177 @@ def run_kernel(args):
     fem.fem_mesh_destroy(h)
 
 
+def run_learned(args):
+    """Learned proposal on the medium mesh: samples from --train-cases cases x --case-steps steps, Adam on
+    the GPU, then --eval-cases held-out cases with and without the network (same certified tolerance)."""
+    import numpy as np
+    import torch
+    from paper_2409_20380_gb300 import build, fem
+    from paper_2409_20380_gb300 import workload as wl
+    build.build()
+    fem.lib()
+    torch.cuda.set_device(0)
+    Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
+    mesh = wl.config2_mesh(Hx, Hy, Hz)
+    tp = wl.config2_time_params()
+    regions = wl.region_map(mesh, args.region_nodes)
+    R = int(regions.max()) + 1
+    train_src, held_src = wl.config5_sources(mesh, args.train_cases, args.eval_cases)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    h = fem.fem_mesh_create(mesh, tp)
+    fem.fem_mesh_set_regions(h, regions)
+    K = args.case_steps
+    opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
+                                tol=1e-8, snapshot_fp32=0)
+
+    def run(srcs, net=None, xs=None, ts=None, window=(250, 500)):
+        """Cases in batches of --cases; returns (rows collected, case-steps/s over the window, iterations,
+        log initial residuals over the window)."""
+        rows, t_win, cs_win, its, logs = 0, 0.0, 0, 0, []
+        for g0 in range(0, len(srcs), args.cases):
+            grp = srcs[g0:g0 + args.cases]
+            bt = fem.fem_batch_create(opts)
+            for s_ in grp:
+                fem.fem_case_add(bt, h, s_)
+            if net is not None:
+                fem.fem_batch_set_mlp(bt, net)
+            if xs is not None:
+                fem.fem_batch_collect(bt, xs[rows:], ts[rows:])
+            nc = len(grp)
+            w0, w1 = min(window[0], K), min(window[1], K)
+            fem.fem_step(bt, w0, nc)
+            for k in range(w0, w1):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st, it, rr = fem.fem_step(bt, 1, nc)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t_win += e0.elapsed_time(e1) / 1e3
+                cs_win += nc
+                its += int(it.sum())
+                for c in range(nc):
+                    logs.append(math.log(max(fem.fem_case_stats(bt, c)["init_relres"], 1e-30)))
+            if K > w1:
+                fem.fem_step(bt, K - w1, nc)
+            if xs is not None:
+                rows += fem.fem_batch_collected(bt)[0]
+            fem.fem_batch_destroy(bt)
+        return rows, (cs_win / t_win if t_win > 0 else None), its, logs
+
+    cap = len(train_src) * K * R
+    xs = torch.empty((cap, 64), device="cuda")
+    ts = torch.empty((cap, 32), device="cuda")
+    t0 = time.perf_counter()
+    rows, _, _, _ = run(train_src, xs=xs, ts=ts, window=(K, K))
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    net = fem.fem_mlp_create(wl.mlp_init_weights(0).astype(np.float32))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    order = torch.randint(0, rows, (args.updates, args.batch), device="cuda", generator=g, dtype=torch.int32)
+    t0 = time.perf_counter()
+    losses = fem.fem_mlp_train(net, xs[:rows], ts[:rows], order, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    train_var = float((ts[:rows] ** 2).mean())
+    del xs, ts
+    hcap = len(held_src) * K * R
+    hx = torch.empty((hcap, 64), device="cuda")
+    ht = torch.empty((hcap, 32), device="cuda")
+    hrows, v_dd, it_dd, log_dd = run(held_src, xs=hx, ts=ht)
+    held_loss, n_l = 0.0, 0
+    for a in range(0, hrows, 65536):
+        b = min(hrows, a + 65536)
+        held_loss += fem.fem_mlp_loss_grad(net, hx[a:b], ht[a:b]) * (b - a)
+        n_l += b - a
+    held_loss /= max(n_l, 1)
+    held_var = float((ht[:hrows] ** 2).mean())
+    del hx, ht
+    _, v_ml, it_ml, log_ml = run(held_src, net=net)
+    print(json.dumps({
+        "metric": "learned proposal: held-out time-steps/s and CG iterations at rel. residual 1e-8",
+        "unit": UNIT, "value": v_ml, "plain_dd_value": v_dd,
+        "config": {"workload": f"medium {args.dims.replace(',', 'x')} mesh, {len(train_src)} training + "
+                               f"{len(held_src)} held-out cases x {K} steps, window steps 251-{min(500, K)}, "
+                               f"s={args.s_max}, regions of {args.region_nodes} nodes ({R})",
+                   "updates": args.updates, "batch": args.batch},
+        "samples": rows, "sample_gen_s": t_gen, "train_s": t_train,
+        "train_loss_first": float(losses[0]), "train_loss_last": float(np.mean(losses[-50:])),
+        "train_target_mean_sq": train_var, "heldout_loss": held_loss, "heldout_target_mean_sq": held_var,
+        "heldout_r2": 1.0 - held_loss / held_var if held_var > 0 else None,
+        "cg_iters_per_case_step": {"plain_dd": it_dd / max(len(log_dd), 1), "learned": it_ml / max(len(log_ml), 1)},
+        "geo_mean_init_relres": {"plain_dd": math.exp(np.mean(log_dd)), "learned": math.exp(np.mean(log_ml))},
+    }), flush=True)
+    fem.fem_mlp_destroy(net)
+    fem.fem_mesh_destroy(h)
+
+
+def run_uneven(args):
+    """Batched uneven cases: --meshes meshes with hex dims Hx, Hy ~ U{24..64}, Hz ~ U{24..48} (h = 1/64,
+    three seeded layers), one point source each, FP32-inner / FP64-certified PCG with the data-driven
+    predictor; all cases fused into one system (one launch sequence per step) unless --no-fuse."""
+    import numpy as np
+    import torch
+    from paper_2409_20380_gb300 import build, fem
+    from paper_2409_20380_gb300 import workload as wl
+    build.build()
+    fem.lib()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    tp = wl.config2_time_params()
+    dims = wl.config3_dims(args.meshes)
+    handles, n_el, n_nd = [], 0, 0
+    opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
+                                tol=1e-8, snapshot_fp32=0, fuse_meshes=0 if args.no_fuse else 1)
+    bt = fem.fem_batch_create(opts)
+    for i, d in enumerate(dims):
+        m = wl.config3_mesh(i, d)
+        h = fem.fem_mesh_create(m, tp)
+        fem.fem_mesh_set_regions(h, wl.region_map(m, args.region_nodes))
+        fem.fem_case_add(bt, h, wl.random_source(m, wl.rng_for(3, i, 0, 2)))
+        handles.append(h)
+        n_el += m.n_elems
+        n_nd += m.n_nodes
+    nc = len(dims)
+    fem.fem_step(bt, args.spinup, nc)
+    fem.fem_step(bt, args.warmup, nc)
+    sampler = ClockSampler(0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.start()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    st, iters, relres = fem.fem_step(bt, args.steps, nc)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    print(json.dumps({
+        "metric": "batched uneven cases: time-steps/s over all cases at rel. residual 1e-8", "unit": UNIT,
+        "value": nc * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps, "steps": args.steps,
+        "warmup": args.warmup, "spinup_steps": args.spinup, "n_gpus": 1, "higher_is_better": True,
+        "config": {"workload": f"{nc} meshes, hex dims U{{24..64}}^2 x U{{24..48}}, h = 1/64, {n_el} tets and "
+                               f"{n_nd} nodes in total, one case each, "
+                               f"{'fused into one system' if not args.no_fuse else 'one group per mesh'}, "
+                               f"FP32-inner/FP64-refined PCG, data-driven predictor s={args.s_max}",
+                   "fused": not args.no_fuse, "dims": dims},
+        "cg_iters_per_case_step": float(iters.sum()) / (nc * args.steps),
+        "max_certified_relres": float(relres.max()), "status": int(st), "clocks": clocks,
+    }), flush=True)
+    fem.fem_batch_destroy(bt)
+    for h in handles:
+        fem.fem_mesh_destroy(h)
+
+
 def main():
     args = parse()
+    if args.uneven:
+        run_uneven(args)
+        return
+    if args.learned:
+        run_learned(args)
+        return
     if args.kernel == "ebe":
         run_kernel(args)
         return

@@ -142,6 +142,17 @@ fem_status fem_mesh_destroy(fem_mesh* m);
  */
 fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile);
 
+/*
+ * Autotuner: times each EBE implementation that applies to the mesh on the inner solve's product
+ * (q = A p with the fused p^T A p, n_rhs cases; FEM_FP32_INNER = FP32 product, FEM_FP64 = FP64 product):
+ * the generic element kernel and the tiled hex kernel with 64/128/256/512 hexes per tile where its
+ * shared-memory accumulator fits.  The fastest is kept for that precision and n_rhs and used whenever
+ * fem_mesh_tune is left at automatic (0, 0).  Outputs (nullable): the chosen variant and tile size, and its
+ * time per product in ms.  Runs on `stream` and synchronises it; allocates two temporary vectors.
+ */
+fem_status fem_mesh_autotune(fem_mesh* m, int precision, int n_rhs, void* stream, int* ebe_variant_out,
+                             int* hex_per_tile_out, double* ms_out);
+
 /* Reports whether the mesh has hex patches and its current EBE variant and tile size (nullable outputs). */
 fem_status fem_mesh_info(const fem_mesh* m, int* has_hex_patches, int* ebe_variant, int* hex_per_tile);
 

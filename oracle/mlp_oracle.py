@@ -18,11 +18,15 @@ Readings (the paper states the data-driven predictor, and the network form is se
   L1  network 64 -> 256 -> 256 -> 32, GELU (erf form) after the first two layers, linear output.  The 36
       used inputs are zero-padded to 64.
   L2  inputs x[0:3] = (source position - region centroid) / L, with L the largest edge of the domain's
-      bounding box; x[3] = (f0 - 5) / 3; x[4:36] = c_R in age order (entry k belongs to the pair whose
-      output is e^{it-1-k}); missing pairs are 0.
+      bounding box; x[3] = (f0 - 5) / 3; x[4:36] = asinh(c_R) in age order (entry k belongs to the pair whose
+      output is e^{it-1-k}); missing pairs are 0.  asinh keeps the inputs bounded where nearly collinear
+      snapshots give least-squares coefficients of 1e6 and more.
   L3  the network predicts the correction c*_R - c_R (residual form), so an untrained (zero-output) network
       reproduces the data-driven predictor.
-  L4  targets c*_R use the same column-drop rule as the predictor (R9), applied to the columns of Y_R.
+  L4  targets c*_R use the same column-drop rule as the predictor (R9), applied to the columns of Y_R.  A
+      sample whose correction c*_R - c_R has a non-finite entry or one above TARGET_CLIP in magnitude gets the
+      target 0 (no correction): such coefficient jumps come from nearly collinear columns, where
+      coefficient space says little about the prediction Y_R c.
   L5  loss = mean over samples and the 32 outputs of the squared error; Adam with bias correction
       (lr 1e-3, beta = 0.9 / 0.999, eps = 1e-8).
 """
@@ -39,6 +43,7 @@ LAYERS = (64, 256, 256, 32)
 N_COEF = 32
 N_USED = 4 + N_COEF
 F0_CENTER, F0_SCALE = 5.0, 3.0
+TARGET_CLIP = 100.0
 
 
 # ---------------------------------------------------------------------------------------------------------
@@ -165,8 +170,18 @@ def features(src_pos, centroid, extent, f0, coef_slot_order):
     x[3] = (f0 - F0_CENTER) / F0_SCALE
     n = len(coef_slot_order)
     for a in range(n):
-        x[4 + (n - 1 - a)] = coef_slot_order[a]
+        c = coef_slot_order[a]
+        x[4 + (n - 1 - a)] = math.asinh(c) if math.isfinite(c) else 0.0
     return x
+
+
+def target(best_slot_order, pred_slot_order):
+    """Regression target in age order: c* - c, or zero when that correction is not finite or exceeds
+    TARGET_CLIP in magnitude (L4)."""
+    d = np.asarray(best_slot_order, dtype=np.float64) - np.asarray(pred_slot_order, dtype=np.float64)
+    if d.size and (not np.all(np.isfinite(d)) or np.abs(d).max() > TARGET_CLIP):
+        d = np.zeros_like(d)
+    return to_age_order(d)
 
 
 def best_coefficients(Y, e, tau=1e-6):
@@ -207,5 +222,5 @@ def step_samples(sim, src_pos, centroids, extent, f0, tau=1e-6):
         if n > 0:
             idx = np.nonzero(sim.region_of_dof == R)[0]
             cs = best_coefficients(Y[idx], e[idx], tau)
-            T[R] = to_age_order(cs - c)
+            T[R] = target(cs, c)
     return X, T

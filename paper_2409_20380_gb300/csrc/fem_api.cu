@@ -245,6 +245,10 @@ struct fem_mesh {
   std::vector<void*> tile_bufs;
   int ebe_variant = 0;             // 0 auto, 1 generic element kernel, 2 tiled hex kernel
   int hex_per_tile = 0;            // 0 auto
+  // autotuned choice per (FP32 / FP64 product, log2 of the case count); variant 0 = not tuned
+  struct Tuned {
+    int variant = 0, hpt = 0;
+  } tuned[2][6];
   // host copies of the inputs (used to fuse meshes into one system) and the region map
   std::vector<double> h_xyz, h_lmr;
   std::vector<int32_t> h_conn, h_mat, h_region;
@@ -260,16 +264,24 @@ struct fem_mesh {
     for (void* b : tile_bufs) cudaFree(b);
   }
   // Tiling for a product on T with rpad cases: the largest tile whose accumulator fits the budget.
+  // An explicit fem_mesh_tune setting wins; else the autotuned choice for this precision and case count.
   const HexTiles* pick_tiles(size_t elem_bytes, int rpad) const {
-    if (!hex || ebe_variant == 1) return nullptr;
+    int variant = ebe_variant, hpt = hex_per_tile;
+    if (variant == 0 && hpt == 0) {
+      int lg = 0;
+      while ((1 << lg) < rpad && lg < 5) ++lg;
+      const Tuned& t = tuned[elem_bytes == 4 ? 0 : 1][lg];
+      if (t.variant) variant = t.variant, hpt = t.hpt;
+    }
+    if (!hex || variant == 1) return nullptr;
     const size_t budget = elem_bytes == 4 ? 100 * 1024 : 200 * 1024;
     const HexTiles* best = nullptr;
     for (int i = 0; i < kNTile; ++i) {
       const HexTiles& t = tiles[i];
       if (t.n_tiles == 0) continue;
-      if (hex_per_tile && t.hex_per_tile != hex_per_tile) continue;
+      if (hpt && t.hex_per_tile != hpt) continue;
       const size_t need = (size_t)t.nloc_max * (3 * rpad * elem_bytes + 4);
-      if (need <= budget || (hex_per_tile && need <= 220 * 1024)) best = &t;
+      if (need <= budget || (hpt && need <= 220 * 1024)) best = &t;
     }
     return best;
   }
@@ -923,6 +935,70 @@ void mesh_view_of(const fem_mesh* m, MeshView* view, int* device) {
 // ------------------------------------------------------------------------------------------------------
 // C-ABI
 // ------------------------------------------------------------------------------------------------------
+// Times every EBE implementation that applies to the mesh (generic element kernel; tiled hex kernel with
+// 64/128/256/512 hexes per tile when its accumulator fits shared memory) on the product the inner solve
+// uses (A p with the fused p^T A p), and keeps the fastest for this precision and case count.
+template <typename T>
+static fem_status autotune_t(fem_mesh* m, int rpad, cudaStream_t s, int* v_out, int* h_out, double* ms_out) {
+  Workspace* w = nullptr;
+  CHK(m->workspace(rpad, &w));
+  const Reducer red = w->red();
+  const size_t n = (size_t)m->N * 3 * rpad;
+  T *p = nullptr, *q = nullptr;
+  double* ptq = nullptr;
+  CHK(dalloc(&p, n));
+  CHK(dalloc(&q, n));
+  CHK(dalloc(&ptq, (size_t)rpad));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fem_status st = FEM_OK;
+  const int sv = m->ebe_variant, sh = m->hex_per_tile;
+  int lg = 0;
+  while ((1 << lg) < rpad) ++lg;
+  std::vector<std::pair<int, int>> cand = {{1, 0}};
+  if (m->hex)
+    for (int hpt : {64, 128, 256, 512}) cand.push_back({2, hpt});
+  double best = 1e30;
+  int bv = 1, bh = 0;
+  cudaError_t e = cudaMemsetAsync(p, 0, n * sizeof(T), s);
+  for (auto [v, hpt] : cand) {
+    if (e != cudaSuccess) break;
+    m->ebe_variant = v, m->hex_per_tile = hpt;
+    if (v == 2) {
+      const HexTiles* t = m->pick_tiles(sizeof(T), rpad);
+      if (!t || t->hex_per_tile != hpt) continue;   // this tiling does not fit
+    }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+      e = ebe_product<T>(m, rpad, p, q, m->cM, m->cK, &red, w->sc, ptq, nullptr, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    const int reps = 5;
+    for (int k = 0; k < reps && e == cudaSuccess; ++k)
+      e = ebe_product<T>(m, rpad, p, q, m->cM, m->cK, &red, w->sc, ptq, nullptr, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && ms / reps < best) best = ms / reps, bv = v, bh = hpt;
+  }
+  m->ebe_variant = sv, m->hex_per_tile = sh;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    st = fail(FEM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  } else {
+    m->tuned[sizeof(T) == 4 ? 0 : 1][lg] = {bv, bh};
+    if (v_out) *v_out = bv;
+    if (h_out) *h_out = bh;
+    if (ms_out) *ms_out = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dfree(p);
+  dfree(q);
+  dfree(ptq);
+  return st;
+}
+
 extern "C" {
 
 const char* fem_last_error(void) { return g_err.c_str(); }
@@ -1070,6 +1146,17 @@ fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile) {
   m->ebe_variant = ebe_variant;
   m->hex_per_tile = hex_per_tile;
   return FEM_OK;
+}
+
+fem_status fem_mesh_autotune(fem_mesh* m, int precision, int n_rhs, void* stream, int* ebe_variant_out,
+                             int* hex_per_tile_out, double* ms_out) {
+  g_err.clear();
+  if (!m) return fail(FEM_ERR_ARG, "mesh is null");
+  if (!pow2_rhs(n_rhs)) return fail(FEM_ERR_ARG, "n_rhs must be 1, 2, 4, 8, 16 or 32");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == FEM_FP64) return autotune_t<double>(m, n_rhs, s, ebe_variant_out, hex_per_tile_out, ms_out);
+  if (precision == FEM_FP32_INNER) return autotune_t<float>(m, n_rhs, s, ebe_variant_out, hex_per_tile_out, ms_out);
+  return fail(FEM_ERR_ARG, "unknown precision");
 }
 
 fem_status fem_mesh_info(const fem_mesh* m, int* has_hex_patches, int* ebe_variant, int* hex_per_tile) {

@@ -407,8 +407,8 @@ cudaError_t adam(fem_mlp* n, double lr, cudaStream_t s) {
 // Kernels of the time step.
 // ------------------------------------------------------------------------------------------------------
 
-// Input features of row R * rpad + c: (source - centroid_R) / L, (f0 - 5) / 3, the predictor's coefficients
-// in age order (newest pair first), zeros.  Pad rows up to Mpad are zero.
+// Input features of row R * rpad + c: (source - centroid_R) / L, (f0 - 5) / 3, asinh of the predictor's
+// coefficients in age order (newest pair first), zeros.  Pad rows up to Mpad are zero.
 __global__ void k_features(PredView p, int n_pairs, const float4* __restrict__ case_src,
                            const float* __restrict__ centroid, float inv_extent, int64_t Mpad, float* __restrict__ F) {
   const int64_t rows = (int64_t)p.n_regions * p.rpad;
@@ -427,7 +427,8 @@ __global__ void k_features(PredView p, int n_pairs, const float4* __restrict__ c
         v = case_src[c].w;
       } else if (j < 4 + n_pairs) {
         const int a = n_pairs - 1 - (j - 4);
-        v = (float)p.w[row * kMaxSlots + a];
+        const double c = p.w[row * kMaxSlots + a];
+        v = isfinite(c) ? (float)asinh(c) : 0.0f;     // bounded input for nearly collinear snapshots
       }
     }
     F[i] = v;
@@ -505,27 +506,37 @@ __global__ void k_apply(int64_t n, int rpad, const int* __restrict__ choose, flo
 }
 
 // Training samples of one step: features F (computed at prediction time) and targets c* - c in age
-// order, for the real cases; rows are appended at row0 in (region, case) order.
+// order, for the real cases; rows are appended at row0 in (region, case) order.  A target with a
+// non-finite entry or one above kTargetClip in magnitude is written as zero (no correction).
+constexpr double kTargetClip = 100.0;
+
 __global__ void k_collect(int n_regions, int rpad, int ncase, int n_pairs, const float* __restrict__ F,
                           const double* __restrict__ w_best, const double* __restrict__ w_pred, int64_t row0,
                           float* __restrict__ x_out, float* __restrict__ t_out) {
   const int64_t rows = (int64_t)n_regions * ncase;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * (kL0 + kL3);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * (kL0 + 1);
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = i / (kL0 + kL3);
-    const int j = (int)(i % (kL0 + kL3));
+    const int64_t row = i / (kL0 + 1);
+    const int j = (int)(i % (kL0 + 1));
     const int R = (int)(row / ncase), c = (int)(row % ncase);
     const int64_t src = (int64_t)R * rpad + c;
     if (j < kL0) {
       x_out[(row0 + row) * kL0 + j] = F[src * kL0 + j];
     } else {
-      const int k = j - kL0;
-      float v = 0.0f;
-      if (k < n_pairs) {
-        const int a = n_pairs - 1 - k;
-        v = (float)(w_best[src * kMaxSlots + a] - w_pred[src * kMaxSlots + a]);
+      float t[kL3];
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < kL3; ++k) {
+        double d = 0.0;
+        if (k < n_pairs) {
+          const int a = n_pairs - 1 - k;
+          d = w_best[src * kMaxSlots + a] - w_pred[src * kMaxSlots + a];
+        }
+        ok = ok && isfinite(d) && fabs(d) <= kTargetClip;
+        t[k] = (float)d;
       }
-      t_out[(row0 + row) * kL3 + k] = v;
+#pragma unroll
+      for (int k = 0; k < kL3; ++k) t_out[(row0 + row) * kL3 + k] = ok ? t[k] : 0.0f;
     }
   }
 }
@@ -579,7 +590,7 @@ cudaError_t mlp_apply(int64_t n, int rpad, const int* choose, float* r32, const 
 cudaError_t mlp_collect(int n_regions, int rpad, int ncase, int n_pairs, const float* F, const double* w_best,
                         const double* w_pred, int64_t row0, float* x_out, float* t_out, cudaStream_t s) {
   const int64_t rows = (int64_t)n_regions * ncase;
-  k_collect<<<grid_of(rows * (kL0 + kL3)), 256, 0, s>>>(n_regions, rpad, ncase, n_pairs, F, w_best, w_pred, row0,
+  k_collect<<<grid_of(rows * (kL0 + 1)), 256, 0, s>>>(n_regions, rpad, ncase, n_pairs, F, w_best, w_pred, row0,
                                                         x_out, t_out);
   return cudaGetLastError();
 }

@@ -22,7 +22,8 @@ FEM_PRED_AB4, FEM_PRED_DD = 0, 1
 FEM_FIELD_U, FEM_FIELD_V, FEM_FIELD_A, FEM_FIELD_DU, FEM_FIELD_B, FEM_FIELD_GUESS = range(6)
 
 # every symbol include/fem.h declares
-EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_tune", "fem_mesh_info",
+EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_tune", "fem_mesh_autotune",
+           "fem_mesh_info",
            "fem_mesh_set_regions", "fem_ebe_apply",
            "fem_ebe_apply_noalloc",
            "pcg_solve", "fem_batch_create", "fem_batch_destroy", "fem_case_add", "fem_step", "predictor_fit",
@@ -86,6 +87,7 @@ def lib():
         "fem_mesh_create": (I, [I64, P, I64, P, P, I, P, P, ctypes.POINTER(fem_time_params), P, ctypes.POINTER(P)]),
         "fem_mesh_destroy": (I, [P]),
         "fem_mesh_tune": (I, [P, I, I]),
+        "fem_mesh_autotune": (I, [P, I, I, P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
         "fem_mesh_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "fem_mesh_set_regions": (I, [P, P]),
         "fem_ebe_apply": (I, [P, I, P, P, I, D, D, P, P]),
@@ -178,6 +180,14 @@ def fem_mesh_destroy(h):
 
 def fem_mesh_tune(h, ebe_variant=0, hex_per_tile=0):
     _check(lib().fem_mesh_tune(h, ebe_variant, hex_per_tile))
+
+
+def fem_mesh_autotune(h, precision, n_rhs, stream=None):
+    """Returns (ebe_variant, hex_per_tile, ms per product) of the fastest EBE implementation, now in use."""
+    v, t, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().fem_mesh_autotune(h, precision, n_rhs, _stream(stream), ctypes.byref(v), ctypes.byref(t),
+                                   ctypes.byref(ms)))
+    return v.value, t.value, ms.value
 
 
 def fem_mesh_info(h):

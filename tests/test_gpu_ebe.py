@@ -151,3 +151,35 @@ def test_ebe_mesh_without_hex_patches(torch_dev):
             assert np.abs(qs[c] - ref).max() <= 1e-13 * np.abs(ref).max()
     finally:
         fem.fem_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("r", [1, 8, 32])
+def test_autotuned_product_matches_csr(torch_dev, precision, r):
+    """The autotuner picks one of the implementations, and the product it selects keeps parity."""
+    torch = torch_dev
+    m = small_mesh(12, 9, 7, perturb=0.1)
+    tp = wl.TimeParams()
+    sysm, _ = oracle.build_system(m, tp)
+    cM = 4.0 / tp.dt ** 2 + 2.0 * tp.a0 / tp.dt
+    cK = 1.0 + 2.0 * tp.a1 / tp.dt
+    h = fem.fem_mesh_create(m, tp)
+    try:
+        prec = fem.FEM_FP32_INNER if precision == "fp32" else fem.FEM_FP64
+        v, hpt, ms = fem.fem_mesh_autotune(h, prec, r)
+        assert (v, hpt) in [(1, 0), (2, 64), (2, 128), (2, 256), (2, 512)] and ms > 0
+        dt = torch.float32 if precision == "fp32" else torch.float64
+        ps = random_free_vectors(m, r, seed=5 + r)
+        p = torch.tensor(from_cases(ps, m.n_nodes, r), device="cuda", dtype=dt)
+        q = torch.empty_like(p)
+        fem.fem_ebe_apply(h, p, q, r, cM, cK)
+        torch.cuda.synchronize()
+        qs = to_cases(q.cpu().double().numpy(), m.n_nodes, r)
+        pr = [x.astype(np.float32).astype(np.float64) for x in ps] if precision == "fp32" else ps
+        tol = 2e-6 if precision == "fp32" else 1e-13
+        for c in range(r):
+            ref = sysm.A_full @ pr[c]
+            ref[m.fixed_dof == 1] = 0.0
+            assert np.abs(qs[c] - ref).max() / np.abs(ref).max() < tol
+    finally:
+        fem.fem_mesh_destroy(h)

@@ -119,7 +119,16 @@ def test_age_order_and_features():
     assert np.array_equal(mo.from_age_order(a, 3), c)
     x = mo.features([0.5, 0.25, 0.125], [0.25, 0.25, 0.25], 2.0, 8.0, c)
     assert np.allclose(x[:4], [0.125, 0.0, -0.0625, 1.0])
-    assert list(x[4:8]) == [3.0, 2.0, 1.0, 0.0] and np.all(x[36:] == 0)
+    # asinh(t) = log(t + sqrt(t^2 + 1))
+    assert np.allclose(x[4:8], [math.log(3 + math.sqrt(10)), math.log(2 + math.sqrt(5)), math.log(1 + math.sqrt(2)), 0])
+    assert np.all(x[36:] == 0)
+    assert abs(mo.features([0, 0, 0], [0, 0, 0], 1.0, 5.0, [1e300])[4] - 691.4686750787736) < 1e-9
+
+
+def test_target_clip():
+    assert list(mo.target([1.0, 5.0], [0.5, 1.0])[:3]) == [4.0, 0.5, 0.0]
+    assert np.all(mo.target([1.0, 500.0], [0.0, 0.0]) == 0.0)
+    assert np.all(mo.target([np.inf, 1.0], [0.0, 0.0]) == 0.0)
 
 
 def test_step_samples_small_case():
@@ -144,7 +153,7 @@ def test_step_samples_small_case():
     e = sim.E_hist[-1]
     for r in range(R):
         idx = np.nonzero(sim.region_of_dof == r)[0]
-        c = mo.from_age_order(X[r, 4:36], n)
+        c = mo.from_age_order(np.sinh(X[r, 4:36]), n)
         cs = c + mo.from_age_order(T[r], n)
         assert np.linalg.norm(Y[idx] @ cs - e[idx]) <= np.linalg.norm(Y[idx] @ c - e[idx]) * (1 + 1e-9) + 1e-300
         assert np.allclose(X[r, :3], (m.xyz[src.node] - cents[r]) / L)
