@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--comparator-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="eager launches instead of the captured step graph")
+    ap.add_argument("--profile-steps", type=int, default=40,
+                    help="steps after the timed region timed per kernel class with CUDA events (eager)")
     ap.add_argument("--kernel", default=None, choices=["ebe"],
                     help="time one kernel alone (EBE product) instead of the full step")
     ap.add_argument("--kernel-precision", default="fp32", choices=["fp32", "fp64"])
@@ -257,7 +260,8 @@ def run_ours(args):
 
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER if args.precision == "mixed" else fem.FEM_FP64,
                                 predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
-                                s_max=args.s_max, snapshot_fp32=0, tol=1e-8)
+                                s_max=args.s_max, snapshot_fp32=0, tol=1e-8,
+                                use_graph=0 if args.no_graph else 1)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
     bt = fem.fem_batch_create(opts)
@@ -268,7 +272,7 @@ def run_ours(args):
     fem.fem_step(bt, args.warmup, nc)
     # ---- timed region: device-resident, CUDA events on the batch stream ----
     sampler = ClockSampler(local)
-    fem.fem_batch_profile(bt, 1)
+    fem.fem_batch_profile(bt, 2)        # count launches only: the step graph stays a graph
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler.start()
     barrier()
@@ -281,8 +285,13 @@ def run_ours(args):
     torch.cuda.profiler.stop()
     barrier()
     clocks = sampler.stop()
-    prof = fem.fem_batch_profile(bt, 0)
+    launches = fem.fem_batch_profile(bt, 0)["kernel_launches"]
     ms = ev0.elapsed_time(ev1)
+    # per-kernel-class device times: CUDA events around each launch over the next --profile-steps steps
+    # (eager launches of the same kernels; events cannot sit inside the graph's conditional loops)
+    fem.fem_batch_profile(bt, 1)
+    fem.fem_step(bt, max(1, args.profile_steps), nc)
+    prof = fem.fem_batch_profile(bt, 0)
     t_max = ms
     if ws > 1:
         t = torch.tensor([ms], device="cuda")
@@ -408,7 +417,10 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": config_dict(args, mesh), "roofline": roof, "roofline_inner_ebe": inner, "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": prof["kernel_launches"], "clocks": clocks,
+        "gpu_launches": launches, "clocks": clocks,
+        "step_graph": not args.no_graph,
+        "kernel_timing": f"CUDA events around each launch over the {prof['steps']} steps after the timed region "
+                         f"(eager launches of the same kernels)",
         "cg_iters_per_case_step": float(iters.sum()) / (nc * args.steps),
         "max_certified_relres": float(relres.max()), "status": int(st),
         "phase_ms_per_step": {k: prof[k] / max(prof["steps"], 1) for k in
@@ -597,7 +609,8 @@ def run_uneven(args):
     dims = wl.config3_dims(args.meshes)
     handles, n_el, n_nd = [], 0, 0
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
-                                tol=1e-8, snapshot_fp32=0, fuse_meshes=0 if args.no_fuse else 1)
+                                tol=1e-8, snapshot_fp32=0, fuse_meshes=0 if args.no_fuse else 1,
+                                use_graph=0 if args.no_graph else 1)
     bt = fem.fem_batch_create(opts)
     for i, d in enumerate(dims):
         m = wl.config3_mesh(i, d)

@@ -102,11 +102,16 @@ typedef struct {
   int fuse_meshes;       /* 1 = solve all cases of the batch as one fused system (each case on its own mesh
                             copy; meshes of different sizes; one set of launches for all; at most 128 cases;
                             FEM_FP32_INNER only); 0 = one multi-RHS system per mesh */
-  int reserved[3];
+  int use_graph;         /* FEM_FP32_INNER steps: 1 = each group's step is captured once as a CUDA graph
+                            (device-side step counter, conditional loops for the refinement passes and the
+                            inner PCG) and replayed with no host synchronisation between steps; statistics
+                            are read once per fem_step call.  Steps with profiling on, a learned proposal or
+                            sample collection run eagerly.  0 = eager launches with host-side control */
+  int reserved[2];
 } fem_opts;
 
 /* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-6, tau 1e-6,
- * snapshot_fp32 0, check_every 8, refresh_every 200, cert_df 0, fuse_meshes 0. */
+ * snapshot_fp32 0, check_every 8, refresh_every 200, cert_df 0, fuse_meshes 0, use_graph 1. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */
@@ -278,8 +283,9 @@ typedef struct {
   double predict_ms, rhs_ms, solve_ms, update_ms;  /* phases of fem_step, summed over steps */
 } fem_profile;
 
-/* enable = 1: reset and start profiling; 0: stop; -1: leave as is.  out (nullable) receives the totals
- * accumulated so far. */
+/* enable = 1: reset and start profiling (launch counts and per-class device times from CUDA events around
+ * each launch; steps run eagerly); 2: reset and count launches and steps only (graph steps stay graphs);
+ * 0: stop; -1: leave as is.  out (nullable) receives the totals accumulated so far. */
 fem_status fem_batch_profile(fem_batch* b, int enable, fem_profile* out);
 
 /* Statistics of the last completed step of one case. */

@@ -64,7 +64,8 @@ static int next_pow2(int r) {
 enum ProfClass { P_EBE32 = 0, P_EBE64, P_VEC, P_PREDICT, P_RHS, P_SOLVE, P_UPDATE, P_NCLASS };
 
 struct Prof {
-  bool on = false;
+  bool on = false;       // counting launches and steps
+  bool events = false;   // and timing kernel classes with events (forces eager steps)
   std::vector<cudaEvent_t> all, free_ev;
   struct Pair {
     int cls;
@@ -100,7 +101,7 @@ struct Prof {
     return e;
   }
   int begin(int cls, cudaStream_t s) {
-    if (!on) return -1;
+    if (!on || !events) return -1;
     Pair p{cls, get(), get(), false, false};
     cudaEventRecord(p.a, s);
     pend.push_back(p);
@@ -492,6 +493,18 @@ struct Group {
   int last_npairs = 0;            // pairs used by this step's prediction
   bool featured = false;          // F holds this step's features
   bool proposed = false;          // ydelta holds this step's proposal
+  // graph steps: the whole FP32-inner step captured once as a CUDA graph with device-side control
+  StepCtl* ctl = nullptr;         // device step record
+  int* acc_iters = nullptr;       // [ncase] inner iterations summed since the statistics were last read
+  double* acc_relres = nullptr;   // [ncase] worst certified relres since then
+  int* acc_status = nullptr;      // [ncase] worst status since then
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t gs[4] = {nullptr, nullptr, nullptr, nullptr};   // capture streams (top level and bodies)
+  int* h_pin = nullptr;           // pinned: [0] = 1 (use_ext flag), [1] = step counter to upload
+  int ctl_it = -1;                // step counter the device record holds (-1: unknown, upload first)
+  bool graph_failed = false;      // capture or instantiation failed: eager steps from now on
+  int graph_steps = 0;            // graph steps whose statistics are not read yet
   Workspace* ws = nullptr;
   int steps = 0;
   std::vector<int> iters_acc;
@@ -506,6 +519,12 @@ struct Group {
     dfree(Ku); dfree(Mv); dfree(Kv); dfree(Ma); dfree(qM); dfree(qK);
     for (auto& v : Av) dfree(v);
     dfree(F); dfree(dw); dfree(wbest); dfree(ydelta); dfree(choose); dfree(counts); dfree(case_src);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto& st : gs)
+      if (st) cudaStreamDestroy(st);
+    dfree(ctl); dfree(acc_iters); dfree(acc_relres); dfree(acc_status);
+    if (h_pin) cudaFreeHost(h_pin);
     if (h_slots) cudaFreeHost(h_slots);
     delete ws;
     delete owned_mesh;
@@ -861,7 +880,294 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   return FEM_OK;
 }
 
+// ------------------------------------------------------------------------------------------------------
+// Graph steps.  The FP32-inner step of a group is captured once into a CUDA graph: its kernels read the
+// step from a device record (StepCtl) and its loops (refinement passes, inner PCG) are conditional WHILE
+// / IF nodes whose conditions the device sets, so a step is one graph launch with no host round trip.
+// The periodic direct refresh of the recurrences runs between graph launches.
+// ------------------------------------------------------------------------------------------------------
+static const int kMaxPass = 40;
+
+static cudaError_t cond_node(cudaStream_t s, cudaGraphConditionalNodeType type, unsigned dflt, unsigned flags,
+                             cudaGraphConditionalHandle* h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  e = cudaGraphConditionalHandleCreate(h, graph, dflt, flags);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = *h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, graph, deps, nullptr, nd, &p);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaSuccess;
+}
+
+#define GE(x)                                  \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return e_;          \
+  } while (0)
+
+// Issues the launches of one step on the capture streams (nothing here synchronises).
+static cudaError_t capture_step(fem_batch* bt, Group* g) {
+  fem_mesh* m = g->mesh;
+  const MeshView mv = m->view();
+  Workspace* w = g->ws;
+  const Reducer red = w->red();
+  const fem_opts& o = bt->opts;
+  const double dt = m->tp.dt;
+  const int rpad = g->rpad;
+  const bool sg = mv.seg != nullptr;
+  const bool dd = o.predictor == FEM_PRED_DD && g->n_regions > 0;
+  const PredView pv = pred_view(bt, g);
+  const Ring4 V{{g->vh[0], g->vh[1], g->vh[2], g->vh[3]}};
+  const Ring4 AV{{g->Av[0], g->Av[1], g->Av[2], g->Av[3]}};
+  StepCtl* ctl = g->ctl;
+  const int ce = std::max(1, o.check_every);
+  cudaStream_t s = g->gs[0], s2 = g->gs[1], s3 = g->gs[2], s4 = g->gs[3];
+  const long long n_fixed = 6 + (dd ? 6 : 0), n_pass = 4, n_if = 4, n_inner = 3LL * ce + 1;
+  // 1. step record, initial guess
+  GE(launch_step_begin(ctl, dd ? g->n_slots : 0, o.s_max, dt, dd ? 1 : 0, n_fixed, s));
+  GE(launch_ab4_ring(g->n, dt, V, ctl, g->du_ab, s));
+  GE(cudaMemcpyAsync(g->guess, g->du_ab, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+  if (dd) {
+    GE(launch_pred_solve(pv, nullptr, 0, 0, o.tau, s, ctl));
+    GE(launch_pred_combine(pv, nullptr, 0, g->guess, s, ctl));
+  }
+  // 2. right-hand side from the recurrences
+  GE(launch_rhs_incr(mv, rpad, dt, m->tp.a0, m->tp.a1, g->Ma, g->Mv, g->Kv, g->Ku, g->b, g->src, g->ext, 0.0, s, ctl));
+  // 3. residual of the guess
+  const float* qy = nullptr;
+  if (dd) {
+    GE(launch_corr_f32(g->n, g->guess, g->du_ab, w->z32, s));
+    GE(ebe_product<float>(m, rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
+    qy = w->q32;
+  }
+  if (sg) {
+    GE(launch_r0_seg(mv, dt, g->b, nullptr, nullptr, nullptr, nullptr, qy, w->r32, red, w->outer, w->n_active, o.tol,
+                     o.inner_tol, s, AV, ctl));
+  } else {
+    GE(launch_r0(mv, rpad, dt, g->b, nullptr, nullptr, nullptr, nullptr, qy, w->r32, red, w->outer, w->n_active, o.tol,
+                 o.inner_tol, s, AV, ctl));
+  }
+  GE(cudaMemcpyAsync(g->x, g->guess, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+  // 4. refinement passes: WHILE (pass 0, then while a case is above tol)
+  cudaGraphConditionalHandle h_pass, h_if, h_in;
+  cudaGraph_t b_pass, b_if, b_in, tmp;
+  GE(cond_node(s, cudaGraphCondTypeWhile, 1, cudaGraphCondAssignDefault, &h_pass, &b_pass));
+  GE(cudaStreamBeginCaptureToGraph(s2, b_pass, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  {
+    // IF any case is active: inner FP32 PCG on the residual, then x += d
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t gb = nullptr;
+    GE(cudaStreamGetCaptureInfo(s2, &cs, nullptr, &gb, nullptr, nullptr, nullptr));
+    GE(cudaGraphConditionalHandleCreate(&h_if, gb, 0, 0));
+    GE(launch_pass_begin(w->outer, g->ncase, w->n_active, o.maxit, kMaxPass, ctl, h_if, n_if, s2));
+    cudaGraphNodeParams pif{};
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    GE(cudaStreamGetCaptureInfo(s2, &cs, nullptr, &gb, &deps, nullptr, &nd));
+    pif.type = cudaGraphNodeTypeConditional;
+    pif.conditional.handle = h_if;
+    pif.conditional.type = cudaGraphCondTypeIf;
+    pif.conditional.size = 1;
+    cudaGraphNode_t nif;
+    GE(cudaGraphAddNode(&nif, gb, deps, nullptr, nd, &pif));
+    GE(cudaStreamUpdateCaptureDependencies(s2, &nif, nullptr, 1, cudaStreamSetCaptureDependencies));
+    b_if = pif.conditional.phGraph_out[0];
+    GE(cudaStreamBeginCaptureToGraph(s3, b_if, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    {
+      if (sg) {
+        GE(launch_norm_b_seg<float>(mv, w->r32, red, w->sc, w->outer, o.inner_tol, s3));
+      } else {
+        GE(launch_norm_b_gated<float>(mv, rpad, w->r32, red, w->sc, w->outer, o.inner_tol, s3));
+      }
+      GE(cudaMemsetAsync(w->x32, 0, sizeof(float) * (size_t)w->n, s3));
+      if (sg) {
+        GE(launch_resid_seg<float>(mv, w->r32, nullptr, w->x32, w->rr32, w->z32, red, w->sc, w->n_active, s3));
+      } else {
+        GE(launch_resid<float>(mv, rpad, w->r32, nullptr, w->x32, w->rr32, w->z32, 1, red, w->sc, w->n_active,
+                               o.inner_tol, o.maxit, s3));
+      }
+      cudaGraph_t gi = nullptr;
+      GE(cudaStreamGetCaptureInfo(s3, &cs, nullptr, &gi, nullptr, nullptr, nullptr));
+      GE(cudaGraphConditionalHandleCreate(&h_in, gi, 0, 0));
+      GE(launch_inner_start(w->n_active, ctl, h_in, s3));
+      cudaGraphNodeParams pin{};
+      GE(cudaStreamGetCaptureInfo(s3, &cs, nullptr, &gi, &deps, nullptr, &nd));
+      pin.type = cudaGraphNodeTypeConditional;
+      pin.conditional.handle = h_in;
+      pin.conditional.type = cudaGraphCondTypeWhile;
+      pin.conditional.size = 1;
+      cudaGraphNode_t nin;
+      GE(cudaGraphAddNode(&nin, gi, deps, nullptr, nd, &pin));
+      GE(cudaStreamUpdateCaptureDependencies(s3, &nin, nullptr, 1, cudaStreamSetCaptureDependencies));
+      b_in = pin.conditional.phGraph_out[0];
+      GE(cudaStreamBeginCaptureToGraph(s4, b_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      for (int k = 0; k < ce; ++k) {
+        if (sg) {
+          GE(launch_dir_seg<float>(mv, w->z32, w->p32, w->sc, w->n_active, s4));
+        } else {
+          GE(launch_dir_gated<float>(mv, rpad, w->z32, w->p32, w->sc, w->n_active, s4));
+        }
+        GE(ebe_product<float>(m, rpad, w->p32, w->q32, m->cM, m->cK, &red, w->sc, nullptr, w->n_active, s4));
+        if (sg) {
+          GE(launch_update_seg<float>(mv, w->p32, w->q32, w->x32, w->rr32, w->z32, red, w->sc, w->n_active, o.maxit,
+                                      s4));
+        } else {
+          GE(launch_update<float>(mv, rpad, w->p32, w->q32, w->x32, w->rr32, w->z32, red, w->sc, w->n_active,
+                                  o.inner_tol, o.maxit, s4));
+        }
+      }
+      GE(launch_inner_cond(w->n_active, ctl, h_in, ce, o.maxit + 64 * ce, n_inner, s4));
+      GE(cudaStreamEndCapture(s4, &tmp));
+      GE(launch_refine_counts(mv, rpad, g->ncase, g->x, w->x32, w->outer, w->sc, s3));
+    }
+    GE(cudaStreamEndCapture(s3, &tmp));
+    // FP64 certification: split products of the increment, true residual, per-case stop test
+    if (o.cert_df) {
+      GE(launch_ebe_split_df(mv, m->rec_df, rpad, g->x, g->qM, g->qK, s2));
+    } else {
+      GE(launch_ebe_split(mv, rpad, g->x, g->qM, g->qK, s2));
+    }
+    if (sg) {
+      GE(launch_cert_seg(mv, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol, o.inner_tol,
+                         s2));
+    } else {
+      GE(launch_cert(mv, rpad, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
+                     o.inner_tol, s2));
+    }
+    GE(launch_pass_end(w->n_active, ctl, h_pass, kMaxPass, n_pass, s2));
+  }
+  GE(cudaStreamEndCapture(s2, &tmp));
+  // 5. Newmark update, recurrences, snapshot push, Gram row of the new snapshot, statistics
+  GE(launch_newmark_incr(g->n, dt, m->cM, m->cK, g->x, g->du_ab, g->qM, g->qK, g->u, nullptr, g->a, nullptr, g->Ku,
+                         g->Mv, g->Kv, g->Ma, nullptr, nullptr, o.snapshot_fp32, s, V, AV, dd ? g->ring : nullptr,
+                         g->n, ctl));
+  if (dd) GE(launch_pred_dots(pv, 0, 0, s, ctl));
+  GE(launch_step_end(w->outer, g->ncase, g->acc_iters, g->acc_relres, g->acc_status, ctl, s));
+  return cudaSuccess;
+}
+#undef GE
+
+static fem_status group_graph_build(fem_batch* bt, Group* g) {
+  if (!g->ctl) {
+    CHK(dalloc(&g->ctl, 1));
+    CHK(dalloc(&g->acc_iters, (size_t)g->ncase));
+    CHK(dalloc(&g->acc_relres, (size_t)g->ncase));
+    CHK(dalloc(&g->acc_status, (size_t)g->ncase));
+    if (cudaMallocHost((void**)&g->h_pin, 2 * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FEM_ERR_OOM, "cudaMallocHost failed");
+    }
+    g->h_pin[0] = 1;
+    CU(cudaMemsetAsync(g->ctl, 0, sizeof(StepCtl), bt->s));
+    CU(cudaMemsetAsync(g->acc_iters, 0, sizeof(int) * g->ncase, bt->s));
+    CU(cudaMemsetAsync(g->acc_relres, 0, sizeof(double) * g->ncase, bt->s));
+    CU(cudaMemsetAsync(g->acc_status, 0, sizeof(int) * g->ncase, bt->s));
+    for (auto& st : g->gs) CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CU(cudaStreamSynchronize(bt->s));
+  }
+  Prof* saved = g->ws->prof;
+  g->ws->prof = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(g->gs[0], cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) e = capture_step(bt, g);
+  // end every capture still open (an error leaves inner ones open), keep the top-level graph
+  for (int k = 3; k >= 1; --k) {
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(g->gs[k], &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t t = nullptr;
+      cudaStreamEndCapture(g->gs[k], &t);
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(g->gs[0], &graph);
+  if (e == cudaSuccess) e = e2;
+  g->ws->prof = saved;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->gexec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    g->gexec = nullptr;
+    g->graph_failed = true;
+    return fail(FEM_ERR_CUDA, std::string("step graph capture: ") + cudaGetErrorString(e));
+  }
+  g->graph = graph;
+  return FEM_OK;
+}
+
+// One graph step: host-side refresh when due, the step counter uploaded if eager steps ran meanwhile,
+// external loads flagged, one graph launch.
+static fem_status group_step_graph(fem_batch* bt, Group* g) {
+  const int it = g->steps + 1;
+  const int every = bt->opts.refresh_every > 0 ? bt->opts.refresh_every : 200;
+  if (it > 1 && (it - 1) % every == 0) CHK(group_refresh(bt, g));
+  cudaStream_t s = bt->s;
+  if (g->ctl_it != g->steps) {
+    CU(cudaStreamSynchronize(s));           // h_pin[1] may still be read by an earlier upload
+    g->h_pin[1] = g->steps;
+    CU(cudaMemcpyAsync(&g->ctl->it, &g->h_pin[1], sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  if (g->use_ext) CU(cudaMemcpyAsync(&g->ctl->use_ext, &g->h_pin[0], sizeof(int), cudaMemcpyHostToDevice, s));
+  g->use_ext = false;
+  CU(cudaGraphLaunch(g->gexec, s));
+  g->steps = it;
+  g->ctl_it = it;
+  g->graph_steps += 1;
+  return FEM_OK;
+}
+
+// After graph steps: per-case statistics (accumulated on the device) and the last step's solver state.
+static fem_status group_graph_stats(fem_batch* bt, Group* g, fem_status* worst) {
+  if (g->graph_steps == 0) return FEM_OK;
+  cudaStream_t s = bt->s;
+  std::vector<int> it_acc(g->ncase), st_acc(g->ncase);
+  std::vector<double> rr_acc(g->ncase);
+  long long launches = 0;
+  CU(cudaMemcpyAsync(it_acc.data(), g->acc_iters, sizeof(int) * g->ncase, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(rr_acc.data(), g->acc_relres, sizeof(double) * g->ncase, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(st_acc.data(), g->acc_status, sizeof(int) * g->ncase, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(&launches, &g->ctl->launches, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(g->ws->h_sc, g->ws->outer, sizeof(CgCase) * g->ncase, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  CU(cudaMemsetAsync(g->acc_iters, 0, sizeof(int) * g->ncase, s));
+  CU(cudaMemsetAsync(g->acc_relres, 0, sizeof(double) * g->ncase, s));
+  CU(cudaMemsetAsync(g->acc_status, 0, sizeof(int) * g->ncase, s));
+  CU(cudaMemsetAsync(&g->ctl->launches, 0, sizeof(long long), s));
+  for (int l = 0; l < g->ncase; ++l) g->last[l] = g->ws->h_sc[l];
+  for (int l = 0; l < (int)g->cases.size(); ++l) {
+    g->iters_acc[l] += it_acc[l];
+    g->relres_max[l] = std::max(g->relres_max[l], rr_acc[l]);
+    if (st_acc[l] != FEM_OK && (*worst == FEM_OK || st_acc[l] < *worst)) *worst = st_acc[l];
+  }
+  if (bt->prof.on) bt->prof.launches += launches;
+  g->graph_steps = 0;
+  return FEM_OK;
+}
+
+static bool graph_eligible(const fem_batch* bt, const Group* g) {
+  return bt->opts.use_graph && bt->opts.precision == FEM_FP32_INNER && !bt->mlp && !bt->col_x &&
+         !(bt->prof.on && bt->prof.events);
+}
+
 static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
+  if (graph_eligible(bt, g)) {
+    if (!g->gexec) CHK(group_graph_build(bt, g));     // use_graph was asked for: a failed capture is an error
+    return group_step_graph(bt, g);
+  }
+  if (g->graph_steps) CHK(group_graph_stats(bt, g, worst));
+  g->ctl_it = -1;
   if (bt->opts.precision == FEM_FP32_INNER) return group_step_mixed(bt, g, worst);
   if (g->owned_mesh) return fail(FEM_ERR_ARG, "fused meshes need the FP32-inner solver");
   fem_mesh* m = g->mesh;
@@ -1018,6 +1324,7 @@ void fem_opts_default(fem_opts* o) {
   o->refresh_every = 200;
   o->cert_df = 0;
   o->fuse_meshes = 0;
+  o->use_graph = 1;
 }
 
 fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
@@ -1426,6 +1733,7 @@ fem_status fem_step(fem_batch* b, int n_steps, int* iters_out, double* relres_ou
     b->steps += 1;
     if (b->prof.on) b->prof.steps += 1;
   }
+  for (auto* g : b->groups) CHK(group_graph_stats(b, g, &worst));
   for (size_t c = 0; c < b->loc.size(); ++c) {
     const Group* g = b->groups[b->loc[c].first];
     const int l = b->loc[c].second;
@@ -1630,11 +1938,13 @@ fem_status fem_batch_profile(fem_batch* b, int enable, fem_profile* out) {
   if (!b) return fail(FEM_ERR_ARG, "batch is null");
   CU(cudaStreamSynchronize(b->s));
   b->prof.resolve();
-  if (enable == 1) {
+  if (enable == 1 || enable == 2) {
     b->prof.reset();
     b->prof.on = true;
+    b->prof.events = enable == 1;
   } else if (enable == 0) {
     b->prof.on = false;
+    b->prof.events = false;
   }
   if (out) {
     std::memset(out, 0, sizeof(*out));

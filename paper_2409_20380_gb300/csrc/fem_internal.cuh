@@ -68,6 +68,28 @@ struct CgCase {
   double inner_tol;  // outer state: relative reduction the next inner solve is asked for
 };
 
+// Step-dependent values of a time step in device memory, so that one captured graph serves every step
+// (the graph's kernels read the step from here instead of from launch arguments).  Written by the
+// step-begin kernel; ring slot of correction e^j is (j - 1) mod n_slots.
+struct StepCtl {
+  int it;                        // step being computed (1-based)
+  int n_pairs;                   // data-driven predictor pairs of this step (0: no correction)
+  int slot_query;                // ring slot of e^{it-1}
+  int slot_new;                  // ring slot of e^{it}
+  unsigned long long mask;       // ring slots valid once e^it is pushed
+  double t;                      // it * dt
+  int use_ext;                   // external loads replace the point sources this step (set by the host)
+  int pass;                      // refinement passes done in this step
+  int issued;                    // inner iterations issued in this solve
+  int pad_;
+  long long launches;            // kernels the graph has run (for the launch count)
+  int xs[33], ys[33];            // X and Y slot lists of the predictor
+};
+// The four buffers of a 4-deep history ring (vector of step j in p[j mod 4]).
+struct Ring4 {
+  double* p[4];
+};
+
 // Grid-wide deterministic per-case reduction: per-block partials + last-block final sum.
 struct Reducer {
   double* partial;     // [kMaxRedBlocks][3 * kMaxCases]
@@ -165,7 +187,8 @@ cudaError_t launch_update_seg(const MeshView& m, const T* p, const T* q, T* x, T
                               int* n_active, int maxit, cudaStream_t s);
 cudaError_t launch_r0_seg(const MeshView& m, double dt, const double* b, const double* Av4, const double* Av3,
                           const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red,
-                          CgCase* outer, int* n_active, double tol, double inner_floor, cudaStream_t s);
+                          CgCase* outer, int* n_active, double tol, double inner_floor, cudaStream_t s,
+                          Ring4 avr = Ring4{}, const StepCtl* ctl = nullptr);
 cudaError_t launch_cert_seg(const MeshView& m, double cM, double cK, const double* b, const double* qM, const double* qK,
                             float* r32, Reducer red, CgCase* outer, int* n_active, double tol, double inner_floor,
                             cudaStream_t s);
@@ -184,6 +207,8 @@ cudaError_t launch_rhs_finish(const MeshView& m, int rpad, double* b, const Rick
 cudaError_t launch_extract_all(int64_t N, int rpad, int n_cases, const double* src, double* dst, cudaStream_t s);
 cudaError_t launch_ab4(int64_t n, double dt, const double* v4, const double* v3, const double* v2,
                        const double* v1, double* du_ab, cudaStream_t s);
+// The same from the velocity ring with the step read from ctl (v^j in v.p[j mod 4]).
+cudaError_t launch_ab4_ring(int64_t n, double dt, Ring4 v, const StepCtl* ctl, double* du_ab, cudaStream_t s);
 cudaError_t launch_add(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
 cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const double* du_ab, double* u,
                                   const double* v_prev, double* a, double* v_push, void* e_push, int e_fp32,
@@ -192,18 +217,22 @@ cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const 
 // FP32-inner steps with products kept by recurrences (see k_step.cu).
 cudaError_t launch_rhs_incr(const MeshView& m, int rpad, double dt, double a0, double a1, const double* Ma,
                             const double* Mv, const double* Kv, const double* Ku, double* b, const RickerSrc* src,
-                            const double* ext, double t, cudaStream_t s);
+                            const double* ext, double t, cudaStream_t s, const StepCtl* ctl = nullptr);
 cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab, float* y32, cudaStream_t s);
 cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
                       const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
-                      int* n_active, double tol, double inner_max, cudaStream_t s);
+                      int* n_active, double tol, double inner_max, cudaStream_t s, Ring4 avr = Ring4{},
+                      const StepCtl* ctl = nullptr);
 cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const double* b, const double* qM,
                         const double* qK, float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
                         double inner_max, cudaStream_t s);
+// With ctl: v_prev, v_push, Av_push and the snapshot slot come from the rings (vr, avr, ring of slots of
+// slot_stride elements) at the step read from ctl.
 cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, const double* du, const double* du_ab,
                                 const double* qM, const double* qK, double* u, const double* v_prev, double* a,
                                 double* v_push, double* Ku, double* Mv, double* Kv, double* Ma, double* Av_push,
-                                void* e_push, int e_fp32, cudaStream_t s);
+                                void* e_push, int e_fp32, cudaStream_t s, Ring4 vr = Ring4{}, Ring4 avr = Ring4{},
+                                void* ring = nullptr, int64_t slot_stride = 0, const StepCtl* ctl = nullptr);
 cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, const double* y, double* out,
                          cudaStream_t s);
 // Split FP64 product: qM = M p and qK = K p in one pass (generic element kernel).
@@ -229,11 +258,28 @@ struct PredView {
   double* dpart;           // [R][n_chunks][kMaxSlots][rpad] partial dots
 };
 // valid_mask bit j = ring slot j holds a stored correction (64-bit: up to kMaxSlots = 33 slots).
-cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mask, cudaStream_t s);
+// With ctl (graph steps) the slot lists, pair count, query/new slot and mask are read from ctl and the
+// kernels are launched whatever the pair count (0 pairs: no correction).
+cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mask, cudaStream_t s,
+                             const StepCtl* ctl = nullptr);
 cudaError_t launch_pred_solve(const PredView& p, const int* x_slots, int n_pairs, int slot_new, double tau,
-                              cudaStream_t s);
+                              cudaStream_t s, const StepCtl* ctl = nullptr);
 cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out,
-                                cudaStream_t s);
+                                cudaStream_t s, const StepCtl* ctl = nullptr);
+
+// Graph steps (k_graph.cu): device-side step control and the conditions of the graph's loops.
+cudaError_t launch_step_begin(StepCtl* ctl, int n_slots, int s_max, double dt, int dd, long long n_fixed,
+                              cudaStream_t s);
+cudaError_t launch_set_cond(cudaGraphConditionalHandle h, unsigned value, cudaStream_t s);
+cudaError_t launch_pass_begin(CgCase* outer, int ncase, int* n_active, int maxit, int max_pass, StepCtl* ctl,
+                              cudaGraphConditionalHandle h_if, long long n_if, cudaStream_t s);
+cudaError_t launch_inner_start(const int* n_active, StepCtl* ctl, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_inner_cond(const int* n_active, StepCtl* ctl, cudaGraphConditionalHandle h, int chunk, int limit,
+                              long long n_body, cudaStream_t s);
+cudaError_t launch_pass_end(const int* n_active, StepCtl* ctl, cudaGraphConditionalHandle h, int max_pass,
+                            long long n_body, cudaStream_t s);
+cudaError_t launch_step_end(const CgCase* outer, int ncase, int* acc_iters, double* acc_relres, int* acc_status,
+                            StepCtl* ctl, cudaStream_t s);
 // y_out += Y w (as launch_pred_combine) and, in the same pass over the ring, y2 = Y w2.
 cudaError_t launch_pred_combine2(const PredView& p, const int* y_slots, int n_pairs, double* y_out,
                                  const double* w2, double* y2, cudaStream_t s);

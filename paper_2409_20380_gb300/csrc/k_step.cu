@@ -65,6 +65,16 @@ __global__ void k_ab4(int64_t n, double h, const double* __restrict__ v4, const 
     out[i] = h * (-9.0 * v4[i] + 37.0 * v3[i] - 59.0 * v2[i] + 55.0 * v1[i]);
 }
 
+__global__ void k_ab4_ring(int64_t n, double h, Ring4 v, const StepCtl* __restrict__ ctl, double* __restrict__ out) {
+  const int it = ctl->it;   // v^{it-4} .. v^{it-1} sit in slots it, it+1, it+2, it+3 (mod 4)
+  const double* __restrict__ v4 = v.p[it & 3];
+  const double* __restrict__ v3 = v.p[(it + 1) & 3];
+  const double* __restrict__ v2 = v.p[(it + 2) & 3];
+  const double* __restrict__ v1 = v.p[(it + 3) & 3];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = h * (-9.0 * v4[i] + 37.0 * v3[i] - 59.0 * v2[i] + 55.0 * v1[i]);
+}
+
 __global__ void k_add(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     o[i] = a[i] + b[i];
@@ -112,7 +122,9 @@ template <> struct PredAcc<float> {   // compensated FP32 summation of FP32 prod
 // Region R is split into p.n_chunks node ranges; block (R, k) accumulates, for each valid slot j, the
 // partial dot of slot j with the newest slot over its range, per case: dpart[R][k][j][c].
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_pred_dots(PredView p, int slot_new, uint64_t valid_mask) {
+__global__ void __launch_bounds__(kBlock) k_pred_dots(PredView p, int slot_new, uint64_t valid_mask,
+                                                      const StepCtl* ctl) {
+  if (ctl) slot_new = ctl->slot_new, valid_mask = ctl->mask;
   const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
   const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
@@ -147,7 +159,8 @@ __global__ void __launch_bounds__(kBlock) k_pred_dots(PredView p, int slot_new, 
 }
 
 // Sums the chunk partials in chunk order and writes row/column slot_new of each (region, case) Gram.
-__global__ void k_pred_dots_finish(PredView p, int slot_new, uint64_t valid_mask) {
+__global__ void k_pred_dots_finish(PredView p, int slot_new, uint64_t valid_mask, const StepCtl* ctl) {
+  if (ctl) slot_new = ctl->slot_new, valid_mask = ctl->mask;
   const int R = blockIdx.x;
   for (int t = threadIdx.x; t < kMaxSlots * p.rpad; t += blockDim.x) {
     const int j = t / p.rpad, c = t % p.rpad;
@@ -164,7 +177,9 @@ __global__ void k_pred_dots_finish(PredView p, int slot_new, uint64_t valid_mask
 // pivot-free Cholesky of the Gram with the column-drop rule  pivot <= tau^2 G_jj  (the squared form of
 // the modified Gram-Schmidt test ||v_j|| <= tau ||x_j||), then forward/back substitution.  One warp: lane i
 // owns row i; rows padded to an odd length of doubles to spread shared-memory banks.
-__global__ void k_pred_solve(PredView p, const int* __restrict__ x_slots, int n, int slot_new, double tau) {
+__global__ void k_pred_solve(PredView p, const int* __restrict__ x_slots, int n, int slot_new, double tau,
+                             const StepCtl* ctl) {
+  if (ctl) x_slots = ctl->xs, n = ctl->n_pairs, slot_new = ctl->slot_query;
   const int R = blockIdx.x / p.rpad, c = blockIdx.x % p.rpad;
   const int lane = threadIdx.x;
   constexpr int LD = kMaxSlots;                 // 33 doubles per row
@@ -225,7 +240,8 @@ __global__ void k_pred_solve(PredView p, const int* __restrict__ x_slots, int n,
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* __restrict__ y_slots, int n,
-                                                         double* __restrict__ y_out) {
+                                                         double* __restrict__ y_out, const StepCtl* ctl) {
+  if (ctl) y_slots = ctl->ys, n = ctl->n_pairs;
   const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
   const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
@@ -326,7 +342,11 @@ __global__ void k_extract_all(int64_t n3, int rpad, int n_cases, const double* _
 __global__ void k_rhs_incr(MeshView m, int rpad, int rshift, double c_mv, double a1, const double* __restrict__ Ma,
                            const double* __restrict__ Mv, const double* __restrict__ Kv,
                            const double* __restrict__ Ku, double* __restrict__ b, const RickerSrc* __restrict__ src,
-                           const double* __restrict__ ext, double t) {
+                           const double* __restrict__ ext, double t, const StepCtl* ctl) {
+  if (ctl) {
+    t = ctl->t;
+    if (!ctl->use_ext) ext = nullptr;
+  }
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = i >> rshift;
@@ -367,7 +387,12 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_r0(MeshView m, int rpad, int r
                                                const double* __restrict__ Av4, const double* __restrict__ Av3,
                                                const double* __restrict__ Av2, const double* __restrict__ Av1,
                                                const float* __restrict__ qy, float* __restrict__ r32, Reducer red,
-                                               CgCase* outer, int* n_active, double tol, double inner_max) {
+                                               CgCase* outer, int* n_active, double tol, double inner_max,
+                                               Ring4 avr, const StepCtl* ctl) {
+  if (ctl) {   // A v^{it-4} .. A v^{it-1} in ring slots it .. it+3 (mod 4)
+    const int it = ctl->it;
+    Av4 = avr.p[it & 3], Av3 = avr.p[(it + 1) & 3], Av2 = avr.p[(it + 2) & 3], Av1 = avr.p[(it + 3) & 3];
+  }
   double bb = 0.0, rr = 0.0;
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -468,7 +493,15 @@ __global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, const
                                const double* __restrict__ qK, double* __restrict__ u, const double* __restrict__ v_prev,
                                double* __restrict__ a, double* __restrict__ v_push, double* __restrict__ Ku,
                                double* __restrict__ Mv, double* __restrict__ Kv, double* __restrict__ Ma,
-                               double* __restrict__ Av_push, E* __restrict__ e_push) {
+                               double* __restrict__ Av_push, E* __restrict__ e_push, Ring4 vr, Ring4 avr,
+                               E* __restrict__ ring, int64_t slot_stride, const StepCtl* ctl) {
+  if (ctl) {
+    const int it = ctl->it;
+    v_prev = vr.p[(it + 3) & 3];
+    v_push = vr.p[it & 3];
+    Av_push = avr.p[it & 3];
+    e_push = ring ? ring + (int64_t)ctl->slot_new * slot_stride : nullptr;
+  }
   const double c2 = 2.0 / dt, c4 = 4.0 / dt, c44 = 4.0 / (dt * dt);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double d = du[i], vp = v_prev[i], m_ = qM[i], k_ = qK[i];
@@ -529,6 +562,11 @@ cudaError_t launch_ab4(int64_t n, double dt, const double* v4, const double* v3,
   return cudaGetLastError();
 }
 
+cudaError_t launch_ab4_ring(int64_t n, double dt, Ring4 v, const StepCtl* ctl, double* du_ab, cudaStream_t s) {
+  k_ab4_ring<<<grid_for(n), kBlock, 0, s>>>(n, dt / 24.0, v, ctl, du_ab);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_add(int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
   k_add<<<grid_for(n), kBlock, 0, s>>>(n, a, b, out);
   return cudaGetLastError();
@@ -546,9 +584,10 @@ cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const 
 
 cudaError_t launch_rhs_incr(const MeshView& m, int rpad, double dt, double a0, double a1, const double* Ma,
                             const double* Mv, const double* Kv, const double* Ku, double* b, const RickerSrc* src,
-                            const double* ext, double t, cudaStream_t s) {
+                            const double* ext, double t, cudaStream_t s, const StepCtl* ctl) {
   const int rs = log2i(rpad);
-  k_rhs_incr<<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, 4.0 / dt + a0, a1, Ma, Mv, Kv, Ku, b, src, ext, t);
+  k_rhs_incr<<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, 4.0 / dt + a0, a1, Ma, Mv, Kv, Ku, b, src, ext, t,
+                                                   ctl);
   return cudaGetLastError();
 }
 
@@ -559,10 +598,10 @@ cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab,
 
 cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
                       const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
-                      int* n_active, double tol, double inner_max, cudaStream_t s) {
+                      int* n_active, double tol, double inner_max, cudaStream_t s, Ring4 avr, const StepCtl* ctl) {
   const int rs = log2i(rpad);
   k_r0<<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer,
-                                                n_active, tol, inner_max);
+                                                n_active, tol, inner_max, avr, ctl);
   return cudaGetLastError();
 }
 
@@ -578,43 +617,48 @@ cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const
 cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, const double* du, const double* du_ab,
                                 const double* qM, const double* qK, double* u, const double* v_prev, double* a,
                                 double* v_push, double* Ku, double* Mv, double* Kv, double* Ma, double* Av_push,
-                                void* e_push, int e_fp32, cudaStream_t s) {
+                                void* e_push, int e_fp32, cudaStream_t s, Ring4 vr, Ring4 avr, void* ring,
+                                int64_t slot_stride, const StepCtl* ctl) {
   if (e_fp32)
     k_newmark_incr<float><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
-                                                         Mv, Kv, Ma, Av_push, (float*)e_push);
+                                                         Mv, Kv, Ma, Av_push, (float*)e_push, vr, avr, (float*)ring,
+                                                         slot_stride, ctl);
   else
     k_newmark_incr<double><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
-                                                          Mv, Kv, Ma, Av_push, (double*)e_push);
+                                                          Mv, Kv, Ma, Av_push, (double*)e_push, vr, avr, (double*)ring,
+                                                          slot_stride, ctl);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mask, cudaStream_t s) {
+cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mask, cudaStream_t s,
+                             const StepCtl* ctl) {
   if (p.n_regions == 0) return cudaSuccess;
   const int grid = p.n_regions * p.n_chunks;
   if (p.fp32)
-    k_pred_dots<float><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask);
+    k_pred_dots<float><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask, ctl);
   else
-    k_pred_dots<double><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask);
+    k_pred_dots<double><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask, ctl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_pred_dots_finish<<<p.n_regions, 256, 0, s>>>(p, slot_new, valid_mask);
+  k_pred_dots_finish<<<p.n_regions, 256, 0, s>>>(p, slot_new, valid_mask, ctl);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pred_solve(const PredView& p, const int* x_slots, int n_pairs, int slot_new, double tau,
-                              cudaStream_t s) {
-  if (p.n_regions == 0 || n_pairs <= 0) return cudaSuccess;
-  k_pred_solve<<<p.n_regions * p.rpad, 32, 0, s>>>(p, x_slots, n_pairs, slot_new, tau);
+                              cudaStream_t s, const StepCtl* ctl) {
+  if (p.n_regions == 0 || (!ctl && n_pairs <= 0)) return cudaSuccess;
+  k_pred_solve<<<p.n_regions * p.rpad, 32, 0, s>>>(p, x_slots, n_pairs, slot_new, tau, ctl);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out, cudaStream_t s) {
-  if (p.n_regions == 0 || n_pairs <= 0) return cudaSuccess;
+cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out, cudaStream_t s,
+                                const StepCtl* ctl) {
+  if (p.n_regions == 0 || (!ctl && n_pairs <= 0)) return cudaSuccess;
   const int grid = p.n_regions * p.n_chunks;
   if (p.fp32)
-    k_pred_combine<float><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out);
+    k_pred_combine<float><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
   else
-    k_pred_combine<double><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out);
+    k_pred_combine<double><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
   return cudaGetLastError();
 }
 

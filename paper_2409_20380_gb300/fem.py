@@ -50,7 +50,7 @@ class fem_opts(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("s_max", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("tau", ctypes.c_double), ("snapshot_fp32", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("refresh_every", ctypes.c_int), ("cert_df", ctypes.c_int), ("fuse_meshes", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class fem_profile(ctypes.Structure):
