@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of the captured step graph")
+    ap.add_argument("--cert", type=int, default=3,
+                    help="certification product: 0 EBE FP64, 1 EBE double-float, 2 assembled FP64, "
+                         "3 assembled double-float")
     ap.add_argument("--profile-steps", type=int, default=40,
                     help="steps after the timed region timed per kernel class with CUDA events (eager)")
     ap.add_argument("--kernel", default=None, choices=["ebe"],
@@ -230,7 +233,7 @@ def config_dict(args, mesh):
                         f"EBE-PCG to rel. residual 1e-8, "
                         f"{'data-driven predictor s=%d' % args.s_max if args.predictor == 'dd' else 'AB4 predictor'}",
             "mesh_hex": args.dims, "n_elems": mesh.n_elems, "n_nodes": mesh.n_nodes, "cases_per_gpu": args.cases,
-            "precision": args.precision, "predictor": args.predictor, "s_max": args.s_max,
+            "precision": args.precision, "predictor": args.predictor, "s_max": args.s_max, "cert_product": args.cert,
             "region_nodes": args.region_nodes, "tol": 1e-8, "spinup_steps": args.spinup,
             "l2": "inputs larger than L2: each step streams the 16-case state and the snapshot ring (>1 GB)",
             "parallelism": "replicas"}
@@ -260,7 +263,7 @@ def run_ours(args):
 
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER if args.precision == "mixed" else fem.FEM_FP64,
                                 predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
-                                s_max=args.s_max, snapshot_fp32=0, tol=1e-8,
+                                s_max=args.s_max, snapshot_fp32=0, tol=1e-8, cert_df=args.cert,
                                 use_graph=0 if args.no_graph else 1)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
@@ -356,58 +359,63 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
-    # ---- roofline of the dominant kernel (largest measured time per step) ----
+    # ---- rooflines: the FP32 EBE product of the inner solve and the certification product; the one with
+    # the larger measured time per step is the dominant kernel ----
     hbm_peak, peak_kind, sm_max = peaks()
     E = mesh.n_elems
     rpad = 1 << (nc - 1).bit_length()
-    bytes32 = E * (16 + 12 * 4) + rpad * N * 3 * (4 + 4)
-    bytes64 = E * (16 + 12 * 8) + rpad * N * 3 * (8 + 8 + 8)      # p read, M p and K p written
+    alu32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # FP32: 152 SMs x 128 lanes x FMA x max clock
+    alu64 = 152 * 2 * 2 * sm_max * 1e6 / 1e12        # FP64: 152 SMs x 2 DFMA/clk x 2 flops x max clock
     inner = None
     if prof["ebe32_launches"] > 0:
         avg32 = prof["ebe32_ms"] / prof["ebe32_launches"]
+        bytes32 = E * (16 + 12 * 4) + rpad * N * 3 * (4 + 4)
         fl = FLOP_PER_ELEM_CASE * E * rpad
         gbs = bytes32 / (avg32 * 1e-3) / 1e9
-        alu32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32: 152 SMs x 128 lanes x FMA x max clock
-        inner = {"kernel": "k_ebe_hex<float> (FP32 EBE product A p, %d cases)" % rpad, "avg_launch_ms": avg32,
-                 "launches": prof["ebe32_launches"], "alg_bytes_per_launch": bytes32, "alg_flops_per_launch": fl,
-                 "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak, "hbm_peak_kind": peak_kind,
-                 "tflops": fl / (avg32 * 1e-3) / 1e12, "alu_peak_tflops": alu32,
-                 "alu_frac": fl / (avg32 * 1e-3) / 1e12 / alu32,
-                 "traffic": ncu_traffic("ebe_hex_f32_medium16", EBE_SOURCES)}
-    if prof["ebe64_launches"] > 0 and prof["ebe64_ms"] >= prof["ebe32_ms"]:
+        inner = {"bound": "alu", "achieved": fl / (avg32 * 1e-3) / 1e12, "peak": alu32, "unit": "TFLOP/s",
+                 "frac": fl / (avg32 * 1e-3) / 1e12 / alu32,
+                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock",
+                 "traffic": ncu_traffic("ebe_hex_f32_medium16", EBE_SOURCES),
+                 "kernel": "k_ebe_hex<float> (FP32 EBE product A p of the inner PCG, %d cases)" % rpad,
+                 "avg_launch_ms": avg32, "launches": prof["ebe32_launches"], "alg_bytes_per_launch": bytes32,
+                 "alg_flops_per_launch": fl, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak,
+                 "hbm_peak_kind": peak_kind, "ms_per_step": prof["ebe32_ms"] / max(prof["steps"], 1)}
+    cert = None
+    if prof["ebe64_launches"] > 0:
         avg = prof["ebe64_ms"] / prof["ebe64_launches"]
-        fl = FLOP_PER_ELEM_CASE_SPLIT * E * rpad
-        alu64 = 152 * 2 * 2 * sm_max * 1e6 / 1e12      # FP64: 152 SMs x 2 DFMA/clk x 2 flops x max clock
-        achieved = fl / (avg * 1e-3) / 1e12
-        gbs = bytes64 / (avg * 1e-3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu64, "unit": "TFLOP/s", "frac": achieved / alu64,
-                "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock",
-                "traffic": ncu_traffic("ebe_split_f64_medium16", EBE_SOURCES),
-                "kernel": "k_ebe_split (FP64 certification product M p, K p, %d cases)" % rpad,
-                "avg_launch_ms": avg, "launches": prof["ebe64_launches"], "alg_bytes_per_launch": bytes64,
-                "alg_flops_per_launch": fl,
-                "fp64_issue_frac": DP_INSTR_PER_ELEM_CASE_SPLIT * E * rpad / (avg * 1e-3) / (152 * 2 * sm_max * 1e6),
-                "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak}
-    elif inner is not None:
-        t_hbm = bytes32 / (hbm_peak * 1e9)
-        t_alu = inner["alg_flops_per_launch"] / (inner["alu_peak_tflops"] * 1e12)
-        if t_alu > t_hbm:
-            roof = {"bound": "alu", "achieved": inner["tflops"], "peak": inner["alu_peak_tflops"], "unit": "TFLOP/s",
-                    "frac": inner["alu_frac"], "peak_kind": "derived from unit counts x max SM clock"}
+        if args.cert in (2, 3):
+            import numpy as np
+            c4 = mesh.conn.astype(np.int64)
+            keys = np.unique((c4[:, :, None] * mesh.n_nodes + c4[:, None, :]).ravel())
+            nnz = int(keys.size)
+            bytes_c = nnz * (4 + 80) + N * 4 + rpad * N * 3 * (8 + 8 + 8 + (16 if args.cert == 3 else 0))
+            if args.cert == 3:     # per block and case: 12 double-float FMAs of 14 FP32 flops each
+                fl = 12 * 14 * nnz * rpad
+                roof = {"bound": "alu", "peak": alu32, "peak_kind": "derived: FP32 lanes x max SM clock"}
+                kname = "k_bcsr_split_df (certification product M p, K p: assembled 3x3 blocks, double-float)"
+            else:
+                fl = 12 * 2 * nnz * rpad
+                roof = {"bound": "alu", "peak": alu64, "peak_kind": "derived: 152 SMs x 2 DFMA/clk x max SM clock"}
+                kname = "k_bcsr_split_f64 (certification product M p, K p: assembled 3x3 blocks, FP64)"
+            roof.update({"nnz_blocks": nnz})
         else:
-            roof = {"bound": "hbm", "achieved": inner["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": inner["hbm_frac"], "peak_kind": peak_kind}
-        roof.update({k: inner[k] for k in ("kernel", "avg_launch_ms", "launches", "alg_bytes_per_launch",
-                                           "alg_flops_per_launch", "hbm_gbs", "hbm_frac", "hbm_peak", "traffic")})
-        inner = None
+            fl = FLOP_PER_ELEM_CASE_SPLIT * E * rpad
+            bytes_c = E * (16 + 12 * 8) + rpad * N * 3 * (8 + 8 + 8)
+            roof = {"bound": "alu", "peak": alu64, "peak_kind": "derived: 152 SMs x 2 DFMA/clk x max SM clock"}
+            kname = "k_ebe_split%s (certification product M p, K p, element by element)" % ("_df" if args.cert == 1 else "")
+        achieved = fl / (avg * 1e-3) / 1e12
+        gbs = bytes_c / (avg * 1e-3) / 1e9
+        roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"],
+                     "traffic": ncu_traffic("ebe_split_f64_medium16", EBE_SOURCES) if args.cert == 0 else None,
+                     "kernel": kname + ", %d cases" % rpad, "avg_launch_ms": avg, "launches": prof["ebe64_launches"],
+                     "alg_bytes_per_launch": bytes_c, "alg_flops_per_launch": fl, "hbm_gbs": gbs,
+                     "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak,
+                     "ms_per_step": prof["ebe64_ms"] / max(prof["steps"], 1)})
+        cert = roof
+    if inner is not None and (cert is None or inner["ms_per_step"] >= cert["ms_per_step"]):
+        roof, other = inner, cert
     else:
-        avg = prof["ebe64_ms"] / max(prof["ebe64_launches"], 1)
-        fl = FLOP_PER_ELEM_CASE * E * rpad
-        alu64 = 152 * 2 * 2 * sm_max * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": fl / (avg * 1e-3) / 1e12, "peak": alu64, "unit": "TFLOP/s",
-                "frac": fl / (avg * 1e-3) / 1e12 / alu64, "peak_kind": "derived: FP64 unit counts x max SM clock",
-                "traffic": None, "kernel": "k_ebe_hex<double> (FP64 EBE product, %d cases)" % rpad,
-                "avg_launch_ms": avg, "launches": prof["ebe64_launches"]}
+        roof, other = cert, inner
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(args, mesh, srcs, tp, regions)
@@ -415,7 +423,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": config_dict(args, mesh), "roofline": roof, "roofline_inner_ebe": inner, "cpu_baseline": cpu,
+        "config": config_dict(args, mesh), "roofline": roof, "roofline_second": other, "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches, "clocks": clocks,
         "step_graph": not args.no_graph,
@@ -508,7 +516,7 @@ def run_learned(args):
     fem.fem_mesh_set_regions(h, regions)
     K = args.case_steps
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
-                                tol=1e-8, snapshot_fp32=0)
+                                tol=1e-8, snapshot_fp32=0, cert_df=args.cert)
 
     def run(srcs, net=None, xs=None, ts=None, window=(250, 500)):
         """Cases in batches of --cases; returns (rows collected, case-steps/s over the window, iterations,
@@ -609,7 +617,7 @@ def run_uneven(args):
     dims = wl.config3_dims(args.meshes)
     handles, n_el, n_nd = [], 0, 0
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
-                                tol=1e-8, snapshot_fp32=0, fuse_meshes=0 if args.no_fuse else 1,
+                                tol=1e-8, snapshot_fp32=0, fuse_meshes=0 if args.no_fuse else 1, cert_df=args.cert,
                                 use_graph=0 if args.no_graph else 1)
     bt = fem.fem_batch_create(opts)
     for i, d in enumerate(dims):

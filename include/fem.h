@@ -96,9 +96,10 @@ typedef struct {
   int refresh_every;     /* FEM_FP32_INNER steps: every this many steps the products K u, M v, K v, M a and
                             A v^{it-3..it} that fem_step keeps by recurrence are recomputed directly
                             (0 = 200) */
-  int cert_df;           /* FEM_FP32_INNER steps: 1 = the certification product runs in double-float
-                            arithmetic (FP32 pairs, 48-bit significand; the certified residual is exact to
-                            ~1e-12 of ||b||), 0 = native FP64 */
+  int cert_df;           /* FEM_FP32_INNER steps: form of the FP64-accurate certification product (the split
+                            products M du, K du; see fem_mesh_split_product): 0 = element-by-element FP64,
+                            1 = element-by-element double-float (FP32 pairs, 48-bit significand),
+                            2 = assembled 3x3 blocks FP64, 3 = assembled 3x3 blocks double-float */
   int fuse_meshes;       /* 1 = solve all cases of the batch as one fused system (each case on its own mesh
                             copy; meshes of different sizes; one set of launches for all; at most 128 cases;
                             FEM_FP32_INNER only); 0 = one multi-RHS system per mesh */
@@ -111,7 +112,7 @@ typedef struct {
 } fem_opts;
 
 /* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-6, tau 1e-6,
- * snapshot_fp32 0, check_every 8, refresh_every 200, cert_df 0, fuse_meshes 0, use_graph 1. */
+ * snapshot_fp32 0, check_every 8, refresh_every 200, cert_df 3, fuse_meshes 0, use_graph 1. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */
@@ -157,6 +158,21 @@ fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile);
  */
 fem_status fem_mesh_autotune(fem_mesh* m, int precision, int n_rhs, void* stream, int* ebe_variant_out,
                              int* hex_per_tile_out, double* ms_out);
+
+/*
+ * Split product qM = M p and qK = K p (Section 3.1: the mass and stiffness of Eq. GE:DIS, tet4 elements),
+ * n_rhs cases in the [node][3][n_rhs] layout, FP64 in and out, Dirichlet rows zero.  This is the product
+ * the FP32-inner solver certifies with and advances its recurrences by (b - cM qM - cK qK).  mode:
+ *   0 = element by element in FP64 (the matrix-free form of Eq. eqebefem);
+ *   1 = element by element in double-float arithmetic (records and inputs as FP32 pairs);
+ *   2 = assembled operators in FP64: K as 3x3 blocks and M as scalars on the node pattern, assembled on the
+ *       device from the same FP64 element records (built on first use and kept with the mesh);
+ *   3 = the assembled operators in double-float arithmetic.
+ * Modes 0 and 2 round like FP64; 1 and 3 to about 1e-14 of the largest term.  Modes 2/3 need
+ * ~84 bytes x 15 x n_nodes of device memory for the operators.  Mode 3 allocates a temporary input copy.
+ */
+fem_status fem_mesh_split_product(fem_mesh* m, int mode, const double* p_dev, double* qM_dev, double* qK_dev,
+                                  int n_rhs, void* stream);
 
 /* Reports whether the mesh has hex patches and its current EBE variant and tile size (nullable outputs). */
 fem_status fem_mesh_info(const fem_mesh* m, int* has_hex_patches, int* ebe_variant, int* hex_per_tile);

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fem_internal.cuh"
@@ -229,6 +230,14 @@ struct fem_mesh {
   double* rec64 = nullptr;
   float* rec32 = nullptr;
   float* rec_df = nullptr;         // [E][12][2] (hi, lo) split of rec64 for double-float products
+  // assembled operators of the certification product (built on first use)
+  int32_t* row_ptr = nullptr;       // [N + 1] node pattern (a node's neighbours through elements, itself included)
+  int32_t* col = nullptr;           // [nnz]
+  int64_t nnz = 0;
+  double* Kb = nullptr;             // [nnz][3][3] stiffness blocks
+  double* Mb = nullptr;             // [nnz] consistent-mass entries
+  float2* Kd = nullptr;             // (hi, lo) pairs of Kb
+  float2* Md = nullptr;             // (hi, lo) pairs of Mb
   double* D = nullptr;
   double* binv64 = nullptr;
   float* binv32 = nullptr;
@@ -257,9 +266,89 @@ struct fem_mesh {
   // fused meshes: case of each node
   uint8_t* seg = nullptr;
   int nseg = 0;
+  // Node pattern (host, threads over node ranges) and GPU assembly of the certification operators.
+  fem_status ensure_bcsr(cudaStream_t s) {
+    if (row_ptr) return FEM_OK;
+    const int64_t n_nodes = N;
+    std::vector<int64_t> inc_ptr(n_nodes + 1, 0);
+    for (int32_t v : h_conn) inc_ptr[v + 1] += 1;
+    for (int64_t n = 0; n < n_nodes; ++n) inc_ptr[n + 1] += inc_ptr[n];
+    std::vector<int32_t> inc(h_conn.size());
+    {
+      std::vector<int64_t> pos(inc_ptr.begin(), inc_ptr.end() - 1);
+      for (size_t i = 0; i < h_conn.size(); ++i) inc[pos[h_conn[i]]++] = (int32_t)(i / 4);
+    }
+    const int nt = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+    std::vector<int32_t> cnt(n_nodes);
+    auto neighbours = [&](int64_t n, std::vector<int32_t>& buf) {
+      buf.clear();
+      for (int64_t k = inc_ptr[n]; k < inc_ptr[n + 1]; ++k)
+        for (int a = 0; a < 4; ++a) buf.push_back(h_conn[4 * (size_t)inc[k] + a]);
+      std::sort(buf.begin(), buf.end());
+      buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+      if (buf.empty()) buf.push_back((int32_t)n);     // isolated node: diagonal slot only
+    };
+    auto par = [&](auto body) {
+      std::vector<std::thread> th;
+      for (int t = 0; t < nt; ++t)
+        th.emplace_back([&, t]() {
+          std::vector<int32_t> buf;
+          for (int64_t n = n_nodes * t / nt; n < n_nodes * (t + 1) / nt; ++n) body(n, buf);
+        });
+      for (auto& x : th) x.join();
+    };
+    par([&](int64_t n, std::vector<int32_t>& buf) {
+      neighbours(n, buf);
+      cnt[n] = (int32_t)buf.size();
+    });
+    std::vector<int32_t> rp(n_nodes + 1, 0);
+    int64_t total = 0;
+    for (int64_t n = 0; n < n_nodes; ++n) {
+      rp[n] = (int32_t)total;
+      total += cnt[n];
+      if (total > INT32_MAX) return fail(FEM_ERR_ARG, "assembled pattern exceeds 2^31 entries");
+    }
+    rp[n_nodes] = (int32_t)total;
+    std::vector<int32_t> cl(total);
+    par([&](int64_t n, std::vector<int32_t>& buf) {
+      neighbours(n, buf);
+      std::copy(buf.begin(), buf.end(), cl.begin() + rp[n]);
+    });
+    int* missing = nullptr;
+    fem_status st = FEM_OK;
+    if (st == FEM_OK) st = dalloc(&row_ptr, (size_t)n_nodes + 1);
+    if (st == FEM_OK) st = dalloc(&col, (size_t)total);
+    if (st == FEM_OK) st = dalloc(&Kb, 9 * (size_t)total);
+    if (st == FEM_OK) st = dalloc(&Mb, (size_t)total);
+    if (st == FEM_OK) st = dalloc(&Kd, 9 * (size_t)total);
+    if (st == FEM_OK) st = dalloc(&Md, (size_t)total);
+    if (st == FEM_OK) st = dalloc(&missing, 1);
+    if (st != FEM_OK) {
+      dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(Kd); dfree(Md); dfree(missing);
+      return st;
+    }
+    nnz = total;
+    int h_missing = 0;
+    cudaError_t e = cudaMemcpyAsync(row_ptr, rp.data(), sizeof(int32_t) * (n_nodes + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(col, cl.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_bcsr_assemble(view(), row_ptr, col, nnz, Kb, Mb, Kd, Md, missing, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_missing, missing, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(missing);
+    if (e != cudaSuccess || h_missing) {
+      cudaGetLastError();
+      dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(Kd); dfree(Md);
+      row_ptr = nullptr;
+      nnz = 0;
+      return fail(e != cudaSuccess ? FEM_ERR_CUDA : FEM_ERR_ARG,
+                  e != cudaSuccess ? std::string("assembly: ") + cudaGetErrorString(e) : "assembly: missing pattern slot");
+    }
+    return FEM_OK;
+  }
   MeshView view() const { return MeshView{N, E, conn, rec64, rec32, binv64, binv32, fm, seg, nseg}; }
   ~fem_mesh() {
     dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(rec_df); dfree(D);
+    dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(Kd); dfree(Md);
     dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi); dfree(seg); dfree(reg_cent);
     for (auto* w : ws) delete w;
     for (void* b : tile_bufs) cudaFree(b);
@@ -450,6 +539,7 @@ static fem_status check_opts(const fem_opts* o) {
     return fail(FEM_ERR_ARG, "inner_tol must be in (0, 1)");
   if (o->predictor != FEM_PRED_AB4 && o->predictor != FEM_PRED_DD) return fail(FEM_ERR_ARG, "unknown predictor");
   if (o->s_max < 1 || o->s_max > kMaxSlots - 1) return fail(FEM_ERR_ARG, "s_max must be in [1, 32]");
+  if (o->cert_df < 0 || o->cert_df > 3) return fail(FEM_ERR_ARG, "cert_df must be 0, 1, 2 or 3");
   return FEM_OK;
 }
 
@@ -481,6 +571,7 @@ struct Group {
   // FP32-inner steps: products kept by recurrences (K u, M v, K v, M a, ring of A v) and split products
   double *Ku = nullptr, *Mv = nullptr, *Kv = nullptr, *Ma = nullptr, *Av[4] = {nullptr, nullptr, nullptr, nullptr};
   double *qM = nullptr, *qK = nullptr;
+  float2* xdf = nullptr;          // (hi, lo) split of the product input for the double-float assembled product
   bool use_ext = false;
   // learned proposal and training-sample collection (allocated on first use)
   float* F = nullptr;             // features [Mpad][64] of this step's prediction, row R * rpad + c
@@ -516,7 +607,7 @@ struct Group {
     dfree(b); dfree(x); dfree(du_ab); dfree(m_in); dfree(k_in); dfree(guess);
     if (ring) cudaFree(ring);
     dfree(gram); dfree(wcoef); dfree(dpart); dfree(slot_lists); dfree(src); dfree(ext);
-    dfree(Ku); dfree(Mv); dfree(Kv); dfree(Ma); dfree(qM); dfree(qK);
+    dfree(Ku); dfree(Mv); dfree(Kv); dfree(Ma); dfree(qM); dfree(qK); dfree(xdf);
     for (auto& v : Av) dfree(v);
     dfree(F); dfree(dw); dfree(wbest); dfree(ydelta); dfree(choose); dfree(counts); dfree(case_src);
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -576,6 +667,8 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
       CHK(dalloc(v, n));
       CU(cudaMemsetAsync(*v, 0, n * 8, s));
     }
+    if (bt->opts.cert_df >= 2) CHK(m->ensure_bcsr(s));
+    if (bt->opts.cert_df == 3) CHK(dalloc(&g->xdf, n));
   }
   if (bt->opts.predictor == FEM_PRED_DD) {
     g->n_slots = bt->opts.s_max + 1;
@@ -712,18 +805,31 @@ static fem_status group_predict(fem_batch* bt, Group* g, double* out, bool* corr
   return FEM_OK;
 }
 
+// The certification product qM = M p, qK = K p in the form opts.cert_df selects: 0 element-by-element FP64,
+// 1 element-by-element double-float, 2 assembled blocks FP64, 3 assembled blocks double-float.
+static cudaError_t split_product(const fem_mesh* m, int mode, int rpad, const double* p, float2* p_df, double* qM,
+                                 double* qK, cudaStream_t s) {
+  const MeshView mv = m->view();
+  if (mode == 1) return launch_ebe_split_df(mv, m->rec_df, rpad, p, qM, qK, s);
+  if (mode == 2 || mode == 3)
+    return launch_bcsr_split(mv, rpad, m->row_ptr, m->col, m->Kb, m->Mb, m->Kd, m->Md, p, mode == 3 ? p_df : nullptr,
+                             qM, qK, s);
+  return launch_ebe_split(mv, rpad, p, qM, qK, s);
+}
+
 // Direct recomputation of the recurrence products from the state (bounds their rounding drift).
 static fem_status group_refresh(fem_batch* bt, Group* g) {
   fem_mesh* m = g->mesh;
   const MeshView mv = m->view();
   cudaStream_t s = bt->s;
   const int it = g->steps;      // state after step it
-  CU(launch_ebe_split(mv, g->rpad, g->u, g->qM, g->qK, s));
+  const int cm = bt->opts.cert_df;
+  CU(split_product(m, cm, g->rpad, g->u, g->xdf, g->qM, g->qK, s));
   CU(cudaMemcpyAsync(g->Ku, g->qK, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
-  CU(launch_ebe_split(mv, g->rpad, g->a, g->Ma, g->qK, s));
+  CU(split_product(m, cm, g->rpad, g->a, g->xdf, g->Ma, g->qK, s));
   for (int j = it - 3; j <= it; ++j) {
     const int sl = ((j % 4) + 4) % 4;
-    CU(launch_ebe_split(mv, g->rpad, g->vh[sl], g->qM, g->qK, s));
+    CU(split_product(m, cm, g->rpad, g->vh[sl], g->xdf, g->qM, g->qK, s));
     CU(launch_axpby(g->n, m->cM, g->qM, m->cK, g->qK, g->Av[sl], s));
     if (j == it) {
       CU(cudaMemcpyAsync(g->Mv, g->qM, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
@@ -817,10 +923,7 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
       break;
     }
     int pe = w->pbeg(P_EBE64, s);
-    if (o.cert_df)
-      CU(launch_ebe_split_df(mv, m->rec_df, g->rpad, g->x, g->qM, g->qK, s));
-    else
-      CU(launch_ebe_split(mv, g->rpad, g->x, g->qM, g->qK, s));
+    CU(split_product(m, o.cert_df, g->rpad, g->x, g->xdf, g->qM, g->qK, s));
     w->pend(pe, s);
     if (mv.seg) {
       CU(launch_cert_seg(mv, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
@@ -1036,11 +1139,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
     }
     GE(cudaStreamEndCapture(s3, &tmp));
     // FP64 certification: split products of the increment, true residual, per-case stop test
-    if (o.cert_df) {
-      GE(launch_ebe_split_df(mv, m->rec_df, rpad, g->x, g->qM, g->qK, s2));
-    } else {
-      GE(launch_ebe_split(mv, rpad, g->x, g->qM, g->qK, s2));
-    }
+    GE(split_product(m, o.cert_df, rpad, g->x, g->xdf, g->qM, g->qK, s2));
     if (sg) {
       GE(launch_cert_seg(mv, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol, o.inner_tol,
                          s2));
@@ -1322,7 +1421,7 @@ void fem_opts_default(fem_opts* o) {
   o->snapshot_fp32 = 0;
   o->check_every = 8;
   o->refresh_every = 200;
-  o->cert_df = 0;
+  o->cert_df = 3;
   o->fuse_meshes = 0;
   o->use_graph = 1;
 }
@@ -1464,6 +1563,32 @@ fem_status fem_mesh_autotune(fem_mesh* m, int precision, int n_rhs, void* stream
   if (precision == FEM_FP64) return autotune_t<double>(m, n_rhs, s, ebe_variant_out, hex_per_tile_out, ms_out);
   if (precision == FEM_FP32_INNER) return autotune_t<float>(m, n_rhs, s, ebe_variant_out, hex_per_tile_out, ms_out);
   return fail(FEM_ERR_ARG, "unknown precision");
+}
+
+fem_status fem_mesh_split_product(fem_mesh* m, int mode, const double* p_dev, double* qM_dev, double* qK_dev,
+                                  int n_rhs, void* stream) {
+  g_err.clear();
+  if (!m || !p_dev || !qM_dev || !qK_dev) return fail(FEM_ERR_ARG, "null argument");
+  if (!pow2_rhs(n_rhs)) return fail(FEM_ERR_ARG, "n_rhs must be 1, 2, 4, 8, 16 or 32");
+  if (mode < 0 || mode > 3) return fail(FEM_ERR_ARG, "mode must be 0, 1, 2 or 3");
+  cudaStream_t s = (cudaStream_t)stream;
+  float2* pdf = nullptr;
+  if (mode >= 2) CHK(m->ensure_bcsr(s));
+  if (mode == 3) CHK(dalloc(&pdf, (size_t)m->N * 3 * n_rhs));
+  cudaError_t e = split_product(m, mode, n_rhs, p_dev, pdf, qM_dev, qK_dev, s);
+  if (e == cudaSuccess && mode < 2) {   // the element forms leave Dirichlet rows to their consumers
+    e = launch_mask<double>(m->N, n_rhs, m->fm, qM_dev, s);
+    if (e == cudaSuccess) e = launch_mask<double>(m->N, n_rhs, m->fm, qK_dev, s);
+  }
+  if (pdf) {
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(pdf);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FEM_ERR_CUDA, std::string("fem_mesh_split_product: ") + cudaGetErrorString(e));
+  }
+  return FEM_OK;
 }
 
 fem_status fem_mesh_info(const fem_mesh* m, int* has_hex_patches, int* ebe_variant, int* hex_per_tile) {

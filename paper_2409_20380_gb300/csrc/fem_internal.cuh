@@ -267,6 +267,17 @@ cudaError_t launch_pred_solve(const PredView& p, const int* x_slots, int n_pairs
 cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out,
                                 cudaStream_t s, const StepCtl* ctl = nullptr);
 
+// Assembled operators for the certification product (k_bcsr.cu): K as 3x3 blocks and M as scalars on the
+// node pattern row_ptr/col.  assemble also writes the (hi, lo) FP32-pair copies Kd, Md; *missing = 1 if
+// an element pair had no slot in the pattern.
+cudaError_t launch_bcsr_assemble(const MeshView& m, const int32_t* row_ptr, const int32_t* col, int64_t nnz,
+                                 double* Kb, double* Mb, float2* Kd, float2* Md, int* missing, cudaStream_t s);
+// qM = M p, qK = K p (r cases, Dirichlet rows zero).  p_df != null: double-float arithmetic (p split into
+// p_df first); else native FP64.
+cudaError_t launch_bcsr_split(const MeshView& m, int rpad, const int32_t* row_ptr, const int32_t* col,
+                              const double* Kb, const double* Mb, const float2* Kd, const float2* Md, const double* p,
+                              float2* p_df, double* qM, double* qK, cudaStream_t s);
+
 // Graph steps (k_graph.cu): device-side step control and the conditions of the graph's loops.
 cudaError_t launch_step_begin(StepCtl* ctl, int n_slots, int s_max, double dt, int dd, long long n_fixed,
                               cudaStream_t s);

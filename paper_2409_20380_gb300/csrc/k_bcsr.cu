@@ -1,0 +1,204 @@
+// Assembled operators for the FP64 certification product: the stiffness K as a 3x3-block CSR matrix and
+// the consistent mass M as a scalar CSR matrix on the same node pattern, assembled on the GPU from the
+// FP64 element records (the factorised form K_ab = V [lambda g_a g_b^T + mu (g_a . g_b) I + mu g_b g_a^T],
+// M_ab = rho V / 20 (1 + delta_ab) I of the element apply).  Applied to r cases at once, one block row
+// serves all r right-hand sides, so a product issues ~4x fewer FP64 operations than recomputing the element
+// operators; the double-float variant (values and inputs as FP32 pairs, error-free transforms) runs the
+// arithmetic on the FP32 pipe instead of GB300's narrow FP64 pipe.
+#include "fem_internal.cuh"
+
+namespace fem {
+
+namespace {
+
+__device__ __forceinline__ int find_col(const int32_t* __restrict__ col, int lo, int hi, int c) {
+  for (int j = lo; j < hi; ++j)
+    if (col[j] == c) return j;
+  return -1;
+}
+
+// One thread per element: its 16 node-pair blocks added to the assembled matrices.
+__global__ void k_bcsr_assemble(MeshView m, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                double* __restrict__ Kb, double* __restrict__ Mb, int* __restrict__ missing) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m.E; e += (int64_t)gridDim.x * blockDim.x) {
+    const int4 cn = m.conn[e];
+    const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
+    const double* r = m.rec64 + e * kRec;
+    double g[4][3];
+    for (int k = 0; k < 3; ++k) {
+      g[1][k] = r[k];
+      g[2][k] = r[3 + k];
+      g[3][k] = r[6 + k];
+      g[0][k] = -(g[1][k] + g[2][k] + g[3][k]);
+    }
+    const double lam = r[9], mu = r[10], ms = r[11];
+    for (int a = 0; a < 4; ++a) {
+      const int lo = row_ptr[nd[a]], hi = row_ptr[nd[a] + 1];
+      for (int b = 0; b < 4; ++b) {
+        const int j = find_col(col, lo, hi, nd[b]);
+        if (j < 0) {
+          atomicExch(missing, 1);
+          continue;
+        }
+        const double gab = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+        for (int i = 0; i < 3; ++i)
+          for (int k = 0; k < 3; ++k) {
+            const double v = lam * g[a][i] * g[b][k] + mu * g[b][i] * g[a][k] + (i == k ? mu * gab : 0.0);
+            atomicAdd(Kb + (int64_t)j * 9 + i * 3 + k, v);
+          }
+        atomicAdd(Mb + j, a == b ? 2.0 * ms : ms);
+      }
+    }
+  }
+}
+
+// FP64 values -> (hi, lo) FP32 pairs with hi + lo = v to 2^-48 relative.
+__global__ void k_to_df(int64_t n, const double* __restrict__ v, float2* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = v[i];
+    const float hi = (float)x;
+    out[i] = make_float2(hi, (float)(x - (double)hi));
+  }
+}
+
+// acc (sh + sl) += (ah + al)(bh + bl): the product's rounding error by FMA, the sum's by two-sum; the low
+// word is renormalised only at the end (its own FP32 rounding is ~2^-24 of a quantity ~2^-24 smaller).
+__device__ __forceinline__ void df_fma_acc(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// qM = M p, qK = K p for r cases, one thread per (node row, case); rows of Dirichlet DOFs are zero.
+__global__ void __launch_bounds__(256) k_bcsr_split_df(int64_t N, int rpad, int rshift, const int32_t* __restrict__ row_ptr,
+                                                       const int32_t* __restrict__ col, const float2* __restrict__ Kd,
+                                                       const float2* __restrict__ Md, const uint8_t* __restrict__ fm,
+                                                       const float2* __restrict__ p, double* __restrict__ qM,
+                                                       double* __restrict__ qK) {
+  const int64_t total = N << rshift;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = t >> rshift;
+    const int c = (int)(t & (rpad - 1));
+    float kh[3] = {0.f, 0.f, 0.f}, kl[3] = {0.f, 0.f, 0.f}, mh[3] = {0.f, 0.f, 0.f}, ml[3] = {0.f, 0.f, 0.f};
+    const int lo = __ldg(row_ptr + n), hi = __ldg(row_ptr + n + 1);
+    for (int j = lo; j < hi; ++j) {
+      const int64_t cn = __ldg(col + j);
+      float2 pv[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pv[k] = __ldg(p + (cn * 3 + k) * rpad + c);
+      const float2 mv = __ldg(Md + j);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        df_fma_acc(mh[i], ml[i], mv.x, mv.y, pv[i].x, pv[i].y);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float2 a = __ldg(Kd + (int64_t)j * 9 + i * 3 + k);
+          df_fma_acc(kh[i], kl[i], a.x, a.y, pv[k].x, pv[k].y);
+        }
+      }
+    }
+    const uint8_t f = fm[n];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int64_t id = (n * 3 + i) * rpad + c;
+      const bool fr = dof_free(f, i);
+      qM[id] = fr ? (double)mh[i] + (double)ml[i] : 0.0;
+      qK[id] = fr ? (double)kh[i] + (double)kl[i] : 0.0;
+    }
+  }
+}
+
+// The same product in native FP64.
+__global__ void __launch_bounds__(256) k_bcsr_split_f64(int64_t N, int rpad, int rshift,
+                                                        const int32_t* __restrict__ row_ptr,
+                                                        const int32_t* __restrict__ col, const double* __restrict__ Kb,
+                                                        const double* __restrict__ Mb, const uint8_t* __restrict__ fm,
+                                                        const double* __restrict__ p, double* __restrict__ qM,
+                                                        double* __restrict__ qK) {
+  const int64_t total = N << rshift;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = t >> rshift;
+    const int c = (int)(t & (rpad - 1));
+    double ka[3] = {0.0, 0.0, 0.0}, ma[3] = {0.0, 0.0, 0.0};
+    const int lo = __ldg(row_ptr + n), hi = __ldg(row_ptr + n + 1);
+    for (int j = lo; j < hi; ++j) {
+      const int64_t cn = __ldg(col + j);
+      double pv[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pv[k] = __ldg(p + (cn * 3 + k) * rpad + c);
+      const double mv = __ldg(Mb + j);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        ma[i] = fma(mv, pv[i], ma[i]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ka[i] = fma(__ldg(Kb + (int64_t)j * 9 + i * 3 + k), pv[k], ka[i]);
+      }
+    }
+    const uint8_t f = fm[n];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int64_t id = (n * 3 + i) * rpad + c;
+      const bool fr = dof_free(f, i);
+      qM[id] = fr ? ma[i] : 0.0;
+      qK[id] = fr ? ka[i] : 0.0;
+    }
+  }
+}
+
+int lg2(int r) {
+  int s = 0;
+  while ((1 << s) < r) ++s;
+  return s;
+}
+
+int grid_of(int64_t items) {
+  int64_t g = (items + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t launch_bcsr_assemble(const MeshView& m, const int32_t* row_ptr, const int32_t* col, int64_t nnz,
+                                 double* Kb, double* Mb, float2* Kd, float2* Md, int* missing, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(Kb, 0, sizeof(double) * 9 * (size_t)nnz, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Mb, 0, sizeof(double) * (size_t)nnz, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(missing, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k_bcsr_assemble<<<grid_of(m.E), 256, 0, s>>>(m, row_ptr, col, Kb, Mb, missing);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_to_df<<<grid_of(9 * nnz), 256, 0, s>>>(9 * nnz, Kb, Kd);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_to_df<<<grid_of(nnz), 256, 0, s>>>(nnz, Mb, Md);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_df(int64_t n, const double* v, float2* out, cudaStream_t s) {
+  k_to_df<<<grid_of(n), 256, 0, s>>>(n, v, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bcsr_split(const MeshView& m, int rpad, const int32_t* row_ptr, const int32_t* col,
+                              const double* Kb, const double* Mb, const float2* Kd, const float2* Md, const double* p,
+                              float2* p_df, double* qM, double* qK, cudaStream_t s) {
+  const int rs = lg2(rpad);
+  const int64_t items = m.N << rs;
+  if (p_df) {   // double-float: inputs split once per value, then the product on the FP32 pipe
+    cudaError_t e = launch_to_df(m.N * 3 * rpad, p, p_df, s);
+    if (e != cudaSuccess) return e;
+    k_bcsr_split_df<<<grid_of(items), 256, 0, s>>>(m.N, rpad, rs, row_ptr, col, Kd, Md, m.freemask, p_df, qM, qK);
+  } else {
+    k_bcsr_split_f64<<<grid_of(items), 256, 0, s>>>(m.N, rpad, rs, row_ptr, col, Kb, Mb, m.freemask, p, qM, qK);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fem

@@ -23,7 +23,7 @@ FEM_FIELD_U, FEM_FIELD_V, FEM_FIELD_A, FEM_FIELD_DU, FEM_FIELD_B, FEM_FIELD_GUES
 
 # every symbol include/fem.h declares
 EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_tune", "fem_mesh_autotune",
-           "fem_mesh_info",
+           "fem_mesh_info", "fem_mesh_split_product",
            "fem_mesh_set_regions", "fem_ebe_apply",
            "fem_ebe_apply_noalloc",
            "pcg_solve", "fem_batch_create", "fem_batch_destroy", "fem_case_add", "fem_step", "predictor_fit",
@@ -87,6 +87,7 @@ def lib():
         "fem_mesh_create": (I, [I64, P, I64, P, P, I, P, P, ctypes.POINTER(fem_time_params), P, ctypes.POINTER(P)]),
         "fem_mesh_destroy": (I, [P]),
         "fem_mesh_tune": (I, [P, I, I]),
+        "fem_mesh_split_product": (I, [P, I, P, P, P, I, P]),
         "fem_mesh_autotune": (I, [P, I, I, P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
         "fem_mesh_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "fem_mesh_set_regions": (I, [P, P]),
@@ -188,6 +189,13 @@ def fem_mesh_autotune(h, precision, n_rhs, stream=None):
     _check(lib().fem_mesh_autotune(h, precision, n_rhs, _stream(stream), ctypes.byref(v), ctypes.byref(t),
                                    ctypes.byref(ms)))
     return v.value, t.value, ms.value
+
+
+def fem_mesh_split_product(h, mode, p, qM, qK, n_rhs, stream=None):
+    """qM = M p, qK = K p (FP64 CUDA tensors, [node][3][n_rhs]); mode 0..3 as in include/fem.h."""
+    import torch
+    _check(lib().fem_mesh_split_product(h, mode, _ptr(p, torch.float64), _ptr(qM, torch.float64),
+                                        _ptr(qK, torch.float64), n_rhs, _stream(stream)))
 
 
 def fem_mesh_info(h):

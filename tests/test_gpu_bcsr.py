@@ -1,0 +1,69 @@
+"""Split certification products M p and K p on the GPU against the oracle's assembled CSR matrices (Section
+3.1, tet4 consistent mass and stiffness), for the four forms: element by element or assembled 3x3 blocks,
+each in FP64 or in double-float arithmetic.  FP64 forms match to 1e-13 of the largest entry (summation
+order only); double-float forms to 1e-12 (48-bit significands)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_20380_gb300 import build, fem
+from paper_2409_20380_gb300 import workload as wl
+from helpers import from_cases, random_free_vectors, small_mesh, to_cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    build.build()
+    fem.lib()
+    return torch
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("dims,r,perturb,shuffle", [((7, 5, 4), 1, 0.0, False), ((9, 6, 5), 16, 0.15, False),
+                                                    ((3, 2, 2), 32, 0.0, False), ((6, 5, 4), 4, 0.1, True)])
+def test_split_product_matches_csr(torch_dev, mode, dims, r, perturb, shuffle):
+    torch = torch_dev
+    m = small_mesh(*dims, perturb=perturb)
+    if shuffle:      # elements in random order: no hex patches, pattern from arbitrary connectivity
+        perm = np.random.default_rng(0).permutation(m.n_elems)
+        m.conn = np.ascontiguousarray(m.conn[perm])
+        m.mat_id = np.ascontiguousarray(m.mat_id[perm])
+    tp = wl.TimeParams()
+    sysm, _ = oracle.build_system(m, tp)
+    h = fem.fem_mesh_create(m, tp)
+    try:
+        ps = random_free_vectors(m, r, seed=7 + r)
+        p = torch.tensor(from_cases(ps, m.n_nodes, r), device="cuda")
+        qM = torch.full_like(p, 3.0)
+        qK = torch.full_like(p, 3.0)
+        fem.fem_mesh_split_product(h, mode, p, qM, qK, r)
+        torch.cuda.synchronize()
+        gM = to_cases(qM.cpu().numpy(), m.n_nodes, r)
+        gK = to_cases(qK.cpu().numpy(), m.n_nodes, r)
+        tol = 1e-13 if mode in (0, 2) else 1e-12
+        fixed = m.fixed_dof == 1
+        for c in range(r):
+            for got, mat in ((gM[c], sysm.M), (gK[c], sysm.K)):
+                ref = mat @ ps[c]
+                ref[fixed] = 0.0
+                assert np.all(got[fixed] == 0.0)
+                err = np.abs(got - ref).max() / np.abs(ref).max()
+                assert err < tol, (mode, c, err)
+    finally:
+        fem.fem_mesh_destroy(h)
+
+
+def test_split_product_rejects_bad_mode(torch_dev):
+    torch = torch_dev
+    m = small_mesh(2, 2, 1)
+    h = fem.fem_mesh_create(m, wl.TimeParams())
+    try:
+        p = torch.zeros(m.n_nodes * 3, dtype=torch.float64, device="cuda")
+        with pytest.raises(fem.FemError) as ei:
+            fem.fem_mesh_split_product(h, 4, p, p.clone(), p.clone(), 1)
+        assert ei.value.status == fem.FEM_ERR_ARG
+    finally:
+        fem.fem_mesh_destroy(h)

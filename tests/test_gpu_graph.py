@@ -80,7 +80,7 @@ def _same(a, b):
         assert s1["relres"] < 1e-8 and s2["relres"] < 1e-8
 
 
-@pytest.mark.parametrize("refresh_every,cert_df", [(0, 0), (9, 0), (9, 1)])
+@pytest.mark.parametrize("refresh_every,cert_df", [(0, 0), (9, 0), (9, 1), (9, 3)])
 def test_graph_step_equals_eager_multi_rhs(torch_dev, refresh_every, cert_df):
     m = small_mesh(8, 6, 5, h=1.0 / 64)
     srcs = [wl.random_source(m, wl.rng_for(93, 0, c, 2)) for c in range(3)]
@@ -109,6 +109,6 @@ def test_graph_step_equals_eager_external_loads(torch_dev):
 def test_graph_step_equals_eager_fused_meshes(torch_dev):
     meshes = [small_mesh(*d, h=1.0 / 64) for d in [(6, 5, 4), (9, 6, 5), (5, 7, 3)]]
     srcs = [wl.random_source(m, wl.rng_for(96, k, 0, 2)) for k, m in enumerate(meshes)]
-    eager = _run(meshes, srcs, 30, 0, fuse_meshes=1)
-    graph = _run(meshes, srcs, 30, 1, fuse_meshes=1)
+    eager = _run(meshes, srcs, 30, 0, fuse_meshes=1, cert_df=3)
+    graph = _run(meshes, srcs, 30, 1, fuse_meshes=1, cert_df=3)
     _same(eager, graph)

@@ -129,18 +129,20 @@ def test_step_multicase_dd_fp64_snapshots(torch_dev):
     assert it_dd.sum() < it_ab.sum(), (it_dd, it_ab)
 
 
-@pytest.mark.parametrize("refresh,cert_df", [(200, 0), (7, 0), (200, 1), (7, 1)])
+@pytest.mark.parametrize("refresh,cert_df", [(200, 0), (7, 0), (200, 1), (7, 1), (200, 2), (200, 3), (7, 3)])
 def test_step_mixed_precision_dd(torch_dev, refresh, cert_df):
     """FP32-inner steps keep K u, M v, K v, M a and A v by recurrences: b must still match the oracle's b
     recomputed from the state, with or without periodic direct refreshes of those products.  With native
-    FP64 certification products the bound is FP64 rounding (1e-12); with double-float products (2^-47
-    relative error per operation, accumulated over 40 recurrence steps) it is 1e-11."""
+    FP64 certification products (element by element or assembled) the bound is FP64 rounding (1e-12); with
+    double-float products (2^-47 relative error per operation, accumulated over 40 recurrence steps) it is
+    1e-11."""
     mesh = small_mesh(8, 7, 6)
     tp = wl.TimeParams()
     srcs = [wl.random_source(mesh, wl.rng_for(92, 0, c), f0=4.0) for c in range(3)]   # padded to 4 lanes
     opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=8,
                                 snapshot_fp32=1, refresh_every=refresh, cert_df=cert_df)
-    _run_and_check(mesh, tp, srcs, opts, 40, region_nodes=64, check_pred=False, b_tol=1e-11 if cert_df else 1e-12)
+    _run_and_check(mesh, tp, srcs, opts, 40, region_nodes=64, check_pred=False,
+                   b_tol=1e-11 if cert_df in (1, 3) else 1e-12)
 
 
 def test_step_mixed_precision_ab4_cfg1(torch_dev):
@@ -151,11 +153,12 @@ def test_step_mixed_precision_ab4_cfg1(torch_dev):
 
 
 def test_step_mixed_precision_dd_medium_dt(torch_dev):
-    """The medium workload's time step (dt = 0.004) with FP64 snapshots and double-float certification."""
+    """The medium workload's time step (dt = 0.004) with FP64 snapshots and the double-float assembled
+    certification product."""
     mesh = small_mesh(10, 8, 6, h=1.0 / 64)
     tp = wl.config2_time_params()
     srcs = [wl.random_source(mesh, wl.rng_for(93, 0, c)) for c in range(4)]
-    opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=16, cert_df=1)
+    opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=16, cert_df=3)
     _run_and_check(mesh, tp, srcs, opts, 60, region_nodes=64, check_pred=False, b_tol=1e-11)
 
 
