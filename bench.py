@@ -263,7 +263,7 @@ def run_ours(args):
 
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER if args.precision == "mixed" else fem.FEM_FP64,
                                 predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
-                                s_max=args.s_max, snapshot_fp32=0, tol=1e-8, cert_df=args.cert,
+                                s_max=args.s_max, snapshot_format=2, tol=1e-8, cert_df=args.cert,
                                 use_graph=0 if args.no_graph else 1)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
@@ -516,7 +516,7 @@ def run_learned(args):
     fem.fem_mesh_set_regions(h, regions)
     K = args.case_steps
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
-                                tol=1e-8, snapshot_fp32=0, cert_df=args.cert)
+                                tol=1e-8, snapshot_format=2, cert_df=args.cert)
 
     def run(srcs, net=None, xs=None, ts=None, window=(250, 500)):
         """Cases in batches of --cases; returns (rows collected, case-steps/s over the window, iterations,
@@ -617,7 +617,7 @@ def run_uneven(args):
     dims = wl.config3_dims(args.meshes)
     handles, n_el, n_nd = [], 0, 0
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
-                                tol=1e-8, snapshot_fp32=0, fuse_meshes=0 if args.no_fuse else 1, cert_df=args.cert,
+                                tol=1e-8, snapshot_format=2, fuse_meshes=0 if args.no_fuse else 1, cert_df=args.cert,
                                 use_graph=0 if args.no_graph else 1)
     bt = fem.fem_batch_create(opts)
     for i, d in enumerate(dims):

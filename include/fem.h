@@ -90,8 +90,9 @@ typedef struct {
                             inner solve asks for just enough to reach tol (a tenth of tol / residual),
                             but not less than this */
   double tau;            /* predictor column-drop threshold (relative orthogonalised norm) */
-  int snapshot_fp32;     /* 1: store predictor snapshots in FP32 (halves their memory; the prediction
-                            loses the small orthogonal components FP32 rounds away); 0: FP64 */
+  int snapshot_format;   /* predictor snapshot storage: 0 = FP64; 1 = FP32 (half the memory; the prediction
+                            loses the small orthogonal components FP32 rounds away); 2 = double-float pairs
+                            (hi, lo FP32: FP64 size, 48-bit significand, arithmetic on the FP32 pipe) */
   int check_every;       /* CG iterations between host-side convergence polls (>= 1) */
   int refresh_every;     /* FEM_FP32_INNER steps: every this many steps the products K u, M v, K v, M a and
                             A v^{it-3..it} that fem_step keeps by recurrence are recomputed directly
@@ -112,7 +113,7 @@ typedef struct {
 } fem_opts;
 
 /* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-6, tau 1e-6,
- * snapshot_fp32 0, check_every 8, refresh_every 200, cert_df 3, fuse_meshes 0, use_graph 1. */
+ * snapshot_format 2, check_every 8, refresh_every 200, cert_df 3, fuse_meshes 0, use_graph 1. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */

@@ -540,6 +540,7 @@ static fem_status check_opts(const fem_opts* o) {
   if (o->predictor != FEM_PRED_AB4 && o->predictor != FEM_PRED_DD) return fail(FEM_ERR_ARG, "unknown predictor");
   if (o->s_max < 1 || o->s_max > kMaxSlots - 1) return fail(FEM_ERR_ARG, "s_max must be in [1, 32]");
   if (o->cert_df < 0 || o->cert_df > 3) return fail(FEM_ERR_ARG, "cert_df must be 0, 1, 2 or 3");
+  if (o->snapshot_format < 0 || o->snapshot_format > 2) return fail(FEM_ERR_ARG, "snapshot_format must be 0, 1 or 2");
   return FEM_OK;
 }
 
@@ -672,7 +673,7 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
   }
   if (bt->opts.predictor == FEM_PRED_DD) {
     g->n_slots = bt->opts.s_max + 1;
-    const size_t esz = bt->opts.snapshot_fp32 ? 4 : 8;
+    const size_t esz = bt->opts.snapshot_format == 1 ? 4 : 8;
     cudaError_t e = cudaMalloc(&g->ring, esz * n * g->n_slots);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -684,8 +685,8 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
     const int R = std::max(1, m->n_regions);
     CHK(dalloc(&g->gram, (size_t)R * g->rpad * kMaxSlots * kMaxSlots));
     CHK(dalloc(&g->wcoef, (size_t)R * g->rpad * kMaxSlots));
-    // enough blocks for the dot/combine kernels to fill the GPU: about 4 per SM over all regions
-    g->n_chunks = std::max(1, std::min(64, (4 * 152 + R - 1) / R));
+    // enough blocks for the dot/combine kernels to fill the GPU: about 8 per SM over all regions
+    g->n_chunks = std::max(1, std::min(64, (8 * 152 + R - 1) / R));
     CHK(dalloc(&g->dpart, (size_t)R * g->n_chunks * kMaxSlots * g->rpad));
     CU(cudaMemsetAsync(g->gram, 0, sizeof(double) * (size_t)R * g->rpad * kMaxSlots * kMaxSlots, s));
   }
@@ -718,7 +719,7 @@ static PredView pred_view(const fem_batch* bt, const Group* g) {
   p.n_slots = g->n_slots;
   p.slot_stride = g->n;
   p.ring = g->ring;
-  p.fp32 = bt->opts.snapshot_fp32;
+  p.fmt = bt->opts.snapshot_format;
   p.gram = g->gram;
   p.w = g->wcoef;
   p.n_chunks = g->n_chunks;
@@ -941,11 +942,11 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   void* e_push = nullptr;
   const bool dd = o.predictor == FEM_PRED_DD && g->n_regions > 0;
   if (dd) {
-    const size_t esz = o.snapshot_fp32 ? 4 : 8;
+    const size_t esz = o.snapshot_format == 1 ? 4 : 8;
     e_push = (char*)g->ring + esz * (size_t)g->n * slot_of(g, it);
   }
   CU(launch_newmark_incr(g->n, dt, m->cM, m->cK, g->x, g->du_ab, g->qM, g->qK, g->u, vslot(it - 1), g->a, vslot(it),
-                         g->Ku, g->Mv, g->Kv, g->Ma, aslot(it), e_push, o.snapshot_fp32, s));
+                         g->Ku, g->Mv, g->Kv, g->Ma, aslot(it), e_push, o.snapshot_format, s));
   w->count();
   if (dd) {
     uint64_t mask = 0;
@@ -1152,7 +1153,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   GE(cudaStreamEndCapture(s2, &tmp));
   // 5. Newmark update, recurrences, snapshot push, Gram row of the new snapshot, statistics
   GE(launch_newmark_incr(g->n, dt, m->cM, m->cK, g->x, g->du_ab, g->qM, g->qK, g->u, nullptr, g->a, nullptr, g->Ku,
-                         g->Mv, g->Kv, g->Ma, nullptr, nullptr, o.snapshot_fp32, s, V, AV, dd ? g->ring : nullptr,
+                         g->Mv, g->Kv, g->Ma, nullptr, nullptr, o.snapshot_format, s, V, AV, dd ? g->ring : nullptr,
                          g->n, ctl));
   if (dd) GE(launch_pred_dots(pv, 0, 0, s, ctl));
   GE(launch_step_end(w->outer, g->ncase, g->acc_iters, g->acc_relres, g->acc_status, ctl, s));
@@ -1302,11 +1303,11 @@ static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
   void* e_push = nullptr;
   const bool dd = bt->opts.predictor == FEM_PRED_DD && g->n_regions > 0;
   if (dd) {
-    const size_t esz = bt->opts.snapshot_fp32 ? 4 : 8;
+    const size_t esz = bt->opts.snapshot_format == 1 ? 4 : 8;
     e_push = (char*)g->ring + esz * (size_t)g->n * slot_of(g, it);
   }
   CU(launch_newmark_update(g->n, dt, g->x, g->du_ab, g->u, vslot(it - 1), g->a, vslot(it), e_push,
-                           bt->opts.snapshot_fp32, s));
+                           bt->opts.snapshot_format, s));
   w->count();
   if (dd) {
     uint64_t mask = 0;
@@ -1418,7 +1419,7 @@ void fem_opts_default(fem_opts* o) {
   o->s_max = 32;
   o->inner_tol = 1e-6;
   o->tau = 1e-6;
-  o->snapshot_fp32 = 0;
+  o->snapshot_format = 2;
   o->check_every = 8;
   o->refresh_every = 200;
   o->cert_df = 3;

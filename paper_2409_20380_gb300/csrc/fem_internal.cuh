@@ -211,7 +211,7 @@ cudaError_t launch_ab4(int64_t n, double dt, const double* v4, const double* v3,
 cudaError_t launch_ab4_ring(int64_t n, double dt, Ring4 v, const StepCtl* ctl, double* du_ab, cudaStream_t s);
 cudaError_t launch_add(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
 cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const double* du_ab, double* u,
-                                  const double* v_prev, double* a, double* v_push, void* e_push, int e_fp32,
+                                  const double* v_prev, double* a, double* v_push, void* e_push, int e_fmt,
                                   cudaStream_t s);
 
 // FP32-inner steps with products kept by recurrences (see k_step.cu).
@@ -231,7 +231,7 @@ cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const
 cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, const double* du, const double* du_ab,
                                 const double* qM, const double* qK, double* u, const double* v_prev, double* a,
                                 double* v_push, double* Ku, double* Mv, double* Kv, double* Ma, double* Av_push,
-                                void* e_push, int e_fp32, cudaStream_t s, Ring4 vr = Ring4{}, Ring4 avr = Ring4{},
+                                void* e_push, int e_fmt, cudaStream_t s, Ring4 vr = Ring4{}, Ring4 avr = Ring4{},
                                 void* ring = nullptr, int64_t slot_stride = 0, const StepCtl* ctl = nullptr);
 cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, const double* y, double* out,
                          cudaStream_t s);
@@ -250,8 +250,8 @@ struct PredView {
   int rpad;
   int n_slots;             // ring size (s_max + 1)
   int64_t slot_stride;     // elements per slot = N * 3 * rpad
-  const void* ring;        // [n_slots][N][3][rpad] float or double
-  int fp32;
+  const void* ring;        // [n_slots][N][3][rpad] of FP64, FP32 or (hi, lo) FP32 pairs
+  int fmt;                 // snapshot storage: 0 FP64, 1 FP32, 2 double-float pairs
   double* gram;            // [R][rpad][kMaxSlots][kMaxSlots]
   double* w;               // [R][rpad][kMaxSlots] coefficients in X order
   int n_chunks;            // node-range chunks per region (blocks per region of the dot/combine kernels)

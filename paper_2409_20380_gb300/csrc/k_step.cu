@@ -5,6 +5,16 @@
 
 namespace fem {
 
+// Snapshot storage: FP64, FP32, or double-float pairs (hi, lo FP32 with hi + lo = e to 2^-48 relative; the
+// same 8 bytes as FP64, read and combined on the FP32 pipe).
+__device__ __forceinline__ void store_snap(double* p, double v) { *p = v; }
+__device__ __forceinline__ void store_snap(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void store_snap(float2* p, double v) {
+  const float hi = (float)v;
+  *p = make_float2(hi, (float)(v - (double)hi));
+}
+
+
 static int vec_grid(int64_t items) {
   int64_t g = (items + kVecBlock - 1) / kVecBlock;
   if (g < 1) g = 1;
@@ -93,7 +103,7 @@ __global__ void k_newmark(int64_t n, double dt, const double* __restrict__ du, c
     u[i] += d;
     v_push[i] = c2 * d - vp;
     a[i] = c44 * d - c4 * vp - a[i];
-    if (e_push) e_push[i] = (E)(d - du_ab[i]);
+    if (e_push) store_snap(e_push + i, d - du_ab[i]);
   }
 }
 
@@ -108,6 +118,21 @@ template <> struct PredAcc<double> {
   __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
   __device__ __forceinline__ double get() const { return s; }
 };
+template <> struct PredAcc<float2> {  // double-float: exact products by FMA, exact hi sums by two-sum
+  float s = 0.f, l = 0.f;
+  __device__ __forceinline__ void add(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float t = __fadd_rn(s, p);
+    const float bb = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    s = t;
+    l = __fadd_rn(l, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double get() const { return (double)s + (double)l; }
+};
 template <> struct PredAcc<float> {   // compensated FP32 summation of FP32 products
   float s = 0.f, comp = 0.f;
   __device__ __forceinline__ void add(float a, float b) {
@@ -119,42 +144,75 @@ template <> struct PredAcc<float> {   // compensated FP32 summation of FP32 prod
   __device__ __forceinline__ double get() const { return (double)s - (double)comp; }
 };
 
-// Region R is split into p.n_chunks node ranges; block (R, k) accumulates, for each valid slot j, the
-// partial dot of slot j with the newest slot over its range, per case: dpart[R][k][j][c].
+// Partial sums carried through the block reduction: FP64 for FP64 / FP32 snapshots, (hi, lo) FP32 pairs for
+// double-float snapshots (no FP64 conversion until one value per slot and case remains).
+template <typename T> struct RedVal {
+  double v;
+  __device__ __forceinline__ static RedVal from(const PredAcc<T>& a) { return RedVal{a.get()}; }
+  __device__ __forceinline__ void add(const RedVal& o) { v += o.v; }
+  __device__ __forceinline__ RedVal shfl_xor(int off) const { return RedVal{__shfl_xor_sync(0xffffffffu, v, off)}; }
+  __device__ __forceinline__ double get() const { return v; }
+};
+template <> struct RedVal<float2> {
+  float h, l;
+  __device__ __forceinline__ static RedVal from(const PredAcc<float2>& a) { return RedVal{a.s, a.l}; }
+  __device__ __forceinline__ void add(const RedVal& o) {   // two-sum of the high words, low words added
+    const float t = __fadd_rn(h, o.h);
+    const float bb = __fsub_rn(t, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bb)), __fsub_rn(o.h, bb));
+    h = t;
+    l = __fadd_rn(__fadd_rn(l, o.l), err);
+  }
+  __device__ __forceinline__ RedVal shfl_xor(int off) const {
+    return RedVal{__shfl_xor_sync(0xffffffffu, h, off), __shfl_xor_sync(0xffffffffu, l, off)};
+  }
+  __device__ __forceinline__ double get() const { return (double)h + (double)l; }
+};
+
+// Region R is split into p.n_chunks node ranges; block (R, k, g) accumulates, for each valid slot j of its
+// group g of kDotGrp slots, the partial dot of slot j with the newest slot over its range, per case:
+// dpart[R][k][j][c].  Slot groups keep the accumulators in registers at a useful occupancy.
+constexpr int kDotGrp = 11;
+constexpr int kDotGroups = (kMaxSlots + kDotGrp - 1) / kDotGrp;
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_pred_dots(PredView p, int slot_new, uint64_t valid_mask,
-                                                      const StepCtl* ctl) {
+__global__ void __launch_bounds__(kBlock, 3) k_pred_dots(PredView p, int slot_new, uint64_t valid_mask,
+                                                         const StepCtl* ctl) {
   if (ctl) slot_new = ctl->slot_new, valid_mask = ctl->mask;
   const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
+  const int j0 = blockIdx.y * kDotGrp;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
   const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
   const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
   const int rpad = p.rpad;
   const T* ring = (const T*)p.ring;
   const T* xn = ring + (int64_t)slot_new * p.slot_stride;
-  PredAcc<T> acc[kMaxSlots];
+  PredAcc<T> acc[kDotGrp];
   const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
   for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     const T x = xn[base + i];
 #pragma unroll
-    for (int j = 0; j < kMaxSlots; ++j)
-      if ((valid_mask >> j) & 1ull) acc[j].add(ring[(int64_t)j * p.slot_stride + base + i], x);
+    for (int jj = 0; jj < kDotGrp; ++jj) {
+      const int j = j0 + jj;
+      if (j < kMaxSlots && ((valid_mask >> j) & 1ull)) acc[jj].add(ring[(int64_t)j * p.slot_stride + base + i], x);
+    }
   }
-  __shared__ double sh[kBlock / 32][32];
+  __shared__ RedVal<T> sh[kBlock / 32][kDotGrp][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* out = p.dpart + ((int64_t)R * p.n_chunks + k) * kMaxSlots * rpad;
-  for (int j = 0; j < kMaxSlots; ++j) {
-    if (!((valid_mask >> j) & 1ull)) continue;
-    double v = acc[j].get();
-    for (int off = 16; off >= rpad; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane < rpad) sh[warp][lane] = v;
-    __syncthreads();
-    if (threadIdx.x < rpad) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += sh[w][threadIdx.x];
-      out[j * rpad + threadIdx.x] = s;
+#pragma unroll
+  for (int jj = 0; jj < kDotGrp; ++jj) {
+    RedVal<T> v = RedVal<T>::from(acc[jj]);
+    for (int off = 16; off >= rpad; off >>= 1) v.add(v.shfl_xor(off));
+    if (lane < rpad) sh[warp][jj][lane] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kDotGrp * rpad; t += blockDim.x) {
+    const int jj = t / rpad, c = t % rpad, j = j0 + jj;
+    if (j < kMaxSlots && ((valid_mask >> j) & 1ull)) {
+      RedVal<T> sum = sh[0][jj][c];
+      for (int w = 1; w < nw; ++w) sum.add(sh[w][jj][c]);
+      out[j * rpad + c] = sum.get();
     }
-    __syncthreads();
   }
 }
 
@@ -238,22 +296,70 @@ __global__ void k_pred_solve(PredView p, const int* __restrict__ x_slots, int n,
   if (lane == 0) wo[32] = 0.0;
 }
 
+// Accumulation of w * y for the combination kernels: FP64, FP32, or double-float (coefficients split into
+// (hi, lo) pairs; products exact by FMA, hi sums exact by two-sum) for double-float snapshots.
+template <typename T> struct CombAcc;
+template <> struct CombAcc<double> {
+  typedef double W;
+  double s = 0.0;
+  __device__ __forceinline__ static W wconv(double w) { return w; }
+  __device__ __forceinline__ void add(W w, double y) { s = fma(w, y, s); }
+  __device__ __forceinline__ void merge(const CombAcc& o) { s += o.s; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct CombAcc<float> {
+  typedef float W;
+  float s = 0.f;
+  __device__ __forceinline__ static W wconv(double w) { return (float)w; }
+  __device__ __forceinline__ void add(W w, float y) { s = fmaf(w, y, s); }
+  __device__ __forceinline__ void merge(const CombAcc& o) { s += o.s; }
+  __device__ __forceinline__ double get() const { return (double)s; }
+};
+template <> struct CombAcc<float2> {
+  typedef float2 W;
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ static W wconv(double w) {
+    const float hi = (float)w;
+    return make_float2(hi, (float)(w - (double)hi));
+  }
+  __device__ __forceinline__ void add(W w, float2 y) {
+    const float p = __fmul_rn(w.x, y.x);
+    float e = __fmaf_rn(w.x, y.x, -p);
+    e = __fmaf_rn(w.x, y.y, e);
+    e = __fmaf_rn(w.y, y.x, e);
+    const float t = __fadd_rn(h, p);
+    const float bb = __fsub_rn(t, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    h = t;
+    l = __fadd_rn(l, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ void merge(const CombAcc& o) {
+    const float t = __fadd_rn(h, o.h);
+    const float bb = __fsub_rn(t, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bb)), __fsub_rn(o.h, bb));
+    h = t;
+    l = __fadd_rn(__fadd_rn(l, o.l), err);
+  }
+  __device__ __forceinline__ double get() const { return (double)h + (double)l; }
+};
+
+// y_out += Y w over the region's node range: the coefficients [a][case] and slot offsets in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* __restrict__ y_slots, int n,
                                                          double* __restrict__ y_out, const StepCtl* ctl) {
   if (ctl) y_slots = ctl->ys, n = ctl->n_pairs;
+  typedef typename CombAcc<T>::W W;
   const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
   const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
   const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
   const int rpad = p.rpad;
   const T* ring = (const T*)p.ring;
-  // coefficients [a][case] and slot offsets in shared memory (registers stay free for the loads)
-  __shared__ T sw[kMaxSlots * kMaxRpad];
+  __shared__ W sw[kMaxSlots * kMaxRpad];
   __shared__ int64_t soff[kMaxSlots];
   for (int t = threadIdx.x; t < n * rpad; t += blockDim.x) {
     const int a = t / rpad, c = t % rpad;
-    sw[t] = (T)p.w[((int64_t)R * rpad + c) * kMaxSlots + a];
+    sw[t] = CombAcc<T>::wconv(p.w[((int64_t)R * rpad + c) * kMaxSlots + a]);
   }
   for (int a = threadIdx.x; a < n; a += blockDim.x) soff[a] = (int64_t)y_slots[a] * p.slot_stride;
   __syncthreads();
@@ -261,16 +367,20 @@ __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* 
   const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
   for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     const int64_t gi = base + i;
-    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    int a = 0;
-    for (; a + 3 < n; a += 4) {
-      s0 += sw[a * rpad + c] * ring[soff[a] + gi];
-      s1 += sw[(a + 1) * rpad + c] * ring[soff[a + 1] + gi];
-      s2 += sw[(a + 2) * rpad + c] * ring[soff[a + 2] + gi];
-      s3 += sw[(a + 3) * rpad + c] * ring[soff[a + 3] + gi];
+    CombAcc<T> s0, s1;
+    // eight loads in flight per thread before their products are formed
+    for (int a0 = 0; a0 < n; a0 += 8) {
+      T y[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) y[u] = a0 + u < n ? ring[soff[a0 + u] + gi] : T{};
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        if (a0 + u < n) s0.add(sw[(a0 + u) * rpad + c], y[u]);
+        if (a0 + u + 1 < n) s1.add(sw[(a0 + u + 1) * rpad + c], y[u + 1]);
+      }
     }
-    for (; a < n; ++a) s0 += sw[a * rpad + c] * ring[soff[a] + gi];
-    y_out[gi] += (double)((s0 + s1) + (s2 + s3));
+    s0.merge(s1);
+    y_out[gi] += s0.get();
   }
 }
 
@@ -280,20 +390,21 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_pred_combine2(PredView p, const int* __restrict__ y_slots, int n,
                                                           double* __restrict__ y_out, const double* __restrict__ w2,
                                                           double* __restrict__ y2) {
+  typedef typename CombAcc<T>::W W;
   const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
   const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
   const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
   const int rpad = p.rpad;
   const T* ring = (const T*)p.ring;
-  __shared__ T sw[kMaxSlots * kMaxRpad];
-  __shared__ T sw2[kMaxSlots * kMaxRpad];
+  __shared__ W sw[kMaxSlots * kMaxRpad];
+  __shared__ W sw2[kMaxSlots * kMaxRpad];
   __shared__ int64_t soff[kMaxSlots];
   for (int t = threadIdx.x; t < n * rpad; t += blockDim.x) {
     const int a = t / rpad, c = t % rpad;
     const int64_t o = ((int64_t)R * rpad + c) * kMaxSlots + a;
-    sw[t] = (T)p.w[o];
-    sw2[t] = (T)w2[o];
+    sw[t] = CombAcc<T>::wconv(p.w[o]);
+    sw2[t] = CombAcc<T>::wconv(w2[o]);
   }
   for (int a = threadIdx.x; a < n; a += blockDim.x) soff[a] = (int64_t)y_slots[a] * p.slot_stride;
   __syncthreads();
@@ -301,22 +412,14 @@ __global__ void __launch_bounds__(kBlock) k_pred_combine2(PredView p, const int*
   const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
   for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     const int64_t gi = base + i;
-    T s0 = 0, s1 = 0, t0 = 0, t1 = 0;
-    int a = 0;
-    for (; a + 1 < n; a += 2) {
-      const T y0 = ring[soff[a] + gi], y1 = ring[soff[a + 1] + gi];
-      s0 += sw[a * rpad + c] * y0;
-      t0 += sw2[a * rpad + c] * y0;
-      s1 += sw[(a + 1) * rpad + c] * y1;
-      t1 += sw2[(a + 1) * rpad + c] * y1;
+    CombAcc<T> s0, t0;
+    for (int a = 0; a < n; ++a) {
+      const T y = ring[soff[a] + gi];
+      s0.add(sw[a * rpad + c], y);
+      t0.add(sw2[a * rpad + c], y);
     }
-    if (a < n) {
-      const T y0 = ring[soff[a] + gi];
-      s0 += sw[a * rpad + c] * y0;
-      t0 += sw2[a * rpad + c] * y0;
-    }
-    y_out[gi] += (double)(s0 + s1);
-    y2[gi] = (double)(t0 + t1);
+    y_out[gi] += s0.get();
+    y2[gi] = t0.get();
   }
 }
 
@@ -515,7 +618,7 @@ __global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, const
     Mv[i] = mv2;
     Kv[i] = kv2;
     Av_push[i] = cM * mv2 + cK * kv2;
-    if (e_push) e_push[i] = (E)(d - du_ab[i]);
+    if (e_push) store_snap(e_push + i, d - du_ab[i]);
   }
 }
 
@@ -573,10 +676,12 @@ cudaError_t launch_add(int64_t n, const double* a, const double* b, double* out,
 }
 
 cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const double* du_ab, double* u,
-                                  const double* v_prev, double* a, double* v_push, void* e_push, int e_fp32,
+                                  const double* v_prev, double* a, double* v_push, void* e_push, int e_fmt,
                                   cudaStream_t s) {
-  if (e_fp32)
+  if (e_fmt == 1)
     k_newmark<float><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (float*)e_push);
+  else if (e_fmt == 2)
+    k_newmark<float2><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (float2*)e_push);
   else
     k_newmark<double><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (double*)e_push);
   return cudaGetLastError();
@@ -617,12 +722,16 @@ cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const
 cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, const double* du, const double* du_ab,
                                 const double* qM, const double* qK, double* u, const double* v_prev, double* a,
                                 double* v_push, double* Ku, double* Mv, double* Kv, double* Ma, double* Av_push,
-                                void* e_push, int e_fp32, cudaStream_t s, Ring4 vr, Ring4 avr, void* ring,
+                                void* e_push, int e_fmt, cudaStream_t s, Ring4 vr, Ring4 avr, void* ring,
                                 int64_t slot_stride, const StepCtl* ctl) {
-  if (e_fp32)
+  if (e_fmt == 1)
     k_newmark_incr<float><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
                                                          Mv, Kv, Ma, Av_push, (float*)e_push, vr, avr, (float*)ring,
                                                          slot_stride, ctl);
+  else if (e_fmt == 2)
+    k_newmark_incr<float2><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
+                                                          Mv, Kv, Ma, Av_push, (float2*)e_push, vr, avr, (float2*)ring,
+                                                          slot_stride, ctl);
   else
     k_newmark_incr<double><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
                                                           Mv, Kv, Ma, Av_push, (double*)e_push, vr, avr, (double*)ring,
@@ -633,9 +742,11 @@ cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, cons
 cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mask, cudaStream_t s,
                              const StepCtl* ctl) {
   if (p.n_regions == 0) return cudaSuccess;
-  const int grid = p.n_regions * p.n_chunks;
-  if (p.fp32)
+  const dim3 grid(p.n_regions * p.n_chunks, kDotGroups);
+  if (p.fmt == 1)
     k_pred_dots<float><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask, ctl);
+  else if (p.fmt == 2)
+    k_pred_dots<float2><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask, ctl);
   else
     k_pred_dots<double><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask, ctl);
   cudaError_t e = cudaGetLastError();
@@ -655,8 +766,10 @@ cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pai
                                 const StepCtl* ctl) {
   if (p.n_regions == 0 || (!ctl && n_pairs <= 0)) return cudaSuccess;
   const int grid = p.n_regions * p.n_chunks;
-  if (p.fp32)
+  if (p.fmt == 1)
     k_pred_combine<float><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
+  else if (p.fmt == 2)
+    k_pred_combine<float2><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
   else
     k_pred_combine<double><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
   return cudaGetLastError();
@@ -666,8 +779,10 @@ cudaError_t launch_pred_combine2(const PredView& p, const int* y_slots, int n_pa
                                  double* y2, cudaStream_t s) {
   if (p.n_regions == 0 || n_pairs <= 0) return cudaSuccess;
   const int grid = p.n_regions * p.n_chunks;
-  if (p.fp32)
+  if (p.fmt == 1)
     k_pred_combine2<float><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, w2, y2);
+  else if (p.fmt == 2)
+    k_pred_combine2<float2><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, w2, y2);
   else
     k_pred_combine2<double><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, w2, y2);
   return cudaGetLastError();

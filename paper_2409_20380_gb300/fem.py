@@ -48,7 +48,7 @@ class fem_time_params(ctypes.Structure):
 class fem_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("predictor", ctypes.c_int), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("s_max", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("tau", ctypes.c_double), ("snapshot_fp32", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("tau", ctypes.c_double), ("snapshot_format", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("refresh_every", ctypes.c_int), ("cert_df", ctypes.c_int), ("fuse_meshes", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 

@@ -124,7 +124,7 @@ def test_step_multicase_dd_fp64_snapshots(torch_dev):
     srcs = [wl.random_source(mesh, wl.rng_for(91, 0, c), f0=6.0) for c in range(4)]
     opts_ab = fem.fem_opts_default(tol=1e-8, predictor=fem.FEM_PRED_AB4)
     it_ab, _ = _run_and_check(mesh, tp, srcs, opts_ab, 40)
-    opts_dd = fem.fem_opts_default(tol=1e-8, predictor=fem.FEM_PRED_DD, s_max=8, snapshot_fp32=0)
+    opts_dd = fem.fem_opts_default(tol=1e-8, predictor=fem.FEM_PRED_DD, s_max=8, snapshot_format=2)
     it_dd, worst = _run_and_check(mesh, tp, srcs, opts_dd, 40, region_nodes=64)
     assert it_dd.sum() < it_ab.sum(), (it_dd, it_ab)
 
@@ -140,7 +140,7 @@ def test_step_mixed_precision_dd(torch_dev, refresh, cert_df):
     tp = wl.TimeParams()
     srcs = [wl.random_source(mesh, wl.rng_for(92, 0, c), f0=4.0) for c in range(3)]   # padded to 4 lanes
     opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=8,
-                                snapshot_fp32=1, refresh_every=refresh, cert_df=cert_df)
+                                snapshot_format=1, refresh_every=refresh, cert_df=cert_df)
     _run_and_check(mesh, tp, srcs, opts, 40, region_nodes=64, check_pred=False,
                    b_tol=1e-11 if cert_df in (1, 3) else 1e-12)
 
