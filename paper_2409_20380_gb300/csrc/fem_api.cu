@@ -354,26 +354,44 @@ struct fem_mesh {
     for (void* b : tile_bufs) cudaFree(b);
   }
   // Tiling for a product on T with rpad cases: the largest tile whose accumulator fits the budget.
-  // An explicit fem_mesh_tune setting wins; else the autotuned choice for this precision and case count.
-  const HexTiles* pick_tiles(size_t elem_bytes, int rpad) const {
-    int variant = ebe_variant, hpt = hex_per_tile;
-    if (variant == 0 && hpt == 0) {
+  // EBE implementation of a product on elements of elem_bytes with rpad cases: an explicit fem_mesh_tune
+  // setting wins, else the autotuned choice for this precision and case count, else the tiled hex kernel
+  // when the mesh has hex patches.
+  void resolve(size_t elem_bytes, int rpad, int* variant, int* hpt) const {
+    *variant = ebe_variant, *hpt = hex_per_tile;
+    if (*variant == 0 && *hpt == 0) {
       int lg = 0;
       while ((1 << lg) < rpad && lg < 5) ++lg;
       const Tuned& t = tuned[elem_bytes == 4 ? 0 : 1][lg];
-      if (t.variant) variant = t.variant, hpt = t.hpt;
+      if (t.variant) *variant = t.variant, *hpt = t.hpt;
     }
+    if (*variant == 0) *variant = hex ? 2 : 1;
+    if (!hex) *variant = 1;
+  }
+  // Tiling for the resolved variant: the largest tile whose shared memory fits (or the requested size).
+  const HexTiles* tiles_for(size_t elem_bytes, int rpad, int variant, int hpt) const {
     if (!hex || variant == 1) return nullptr;
-    const size_t budget = elem_bytes == 4 ? 100 * 1024 : 200 * 1024;
     const HexTiles* best = nullptr;
     for (int i = 0; i < kNTile; ++i) {
       const HexTiles& t = tiles[i];
       if (t.n_tiles == 0) continue;
       if (hpt && t.hex_per_tile != hpt) continue;
-      const size_t need = (size_t)t.nloc_max * (3 * rpad * elem_bytes + 4);
+      size_t need, budget;
+      if (variant == 3) {
+        need = elem_bytes == 4 ? ebe_hex_staged_smem<float>(t, view(), rpad) : ebe_hex_staged_smem<double>(t, view(), rpad);
+        budget = 110 * 1024;
+      } else {
+        need = (size_t)t.nloc_max * (3 * rpad * elem_bytes + 4);
+        budget = elem_bytes == 4 ? 100 * 1024 : 200 * 1024;
+      }
       if (need <= budget || (hpt && need <= 220 * 1024)) best = &t;
     }
     return best;
+  }
+  const HexTiles* pick_tiles(size_t elem_bytes, int rpad) const {
+    int v, h;
+    resolve(elem_bytes, rpad, &v, &h);
+    return v == 2 ? tiles_for(elem_bytes, rpad, 2, h) : nullptr;
   }
   fem_status workspace(int rpad, Workspace** out) {
     for (auto* w : ws)
@@ -394,8 +412,12 @@ struct fem_mesh {
 template <typename T>
 static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, double aM, double aK,
                                const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s) {
-  if (const HexTiles* t = m->pick_tiles(sizeof(T), rpad))
+  int v, h;
+  m->resolve(sizeof(T), rpad, &v, &h);
+  if (const HexTiles* t = m->tiles_for(sizeof(T), rpad, v, h)) {
+    if (v == 3) return launch_ebe_hex_staged<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
     return launch_ebe_hex<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
+  }
   return launch_ebe_gated<T>(m->view(), rpad, p, nullptr, q, aM, aK, red, sc, ptq, gate, s);
 }
 
@@ -1363,16 +1385,18 @@ static fem_status autotune_t(fem_mesh* m, int rpad, cudaStream_t s, int* v_out, 
   int lg = 0;
   while ((1 << lg) < rpad) ++lg;
   std::vector<std::pair<int, int>> cand = {{1, 0}};
-  if (m->hex)
+  if (m->hex) {
     for (int hpt : {64, 128, 256, 512}) cand.push_back({2, hpt});
+    for (int hpt : {64, 128, 256}) cand.push_back({3, hpt});
+  }
   double best = 1e30;
   int bv = 1, bh = 0;
   cudaError_t e = cudaMemsetAsync(p, 0, n * sizeof(T), s);
   for (auto [v, hpt] : cand) {
     if (e != cudaSuccess) break;
     m->ebe_variant = v, m->hex_per_tile = hpt;
-    if (v == 2) {
-      const HexTiles* t = m->pick_tiles(sizeof(T), rpad);
+    if (v >= 2) {
+      const HexTiles* t = m->tiles_for(sizeof(T), rpad, v, hpt);
       if (!t || t->hex_per_tile != hpt) continue;   // this tiling does not fit
     }
     for (int k = 0; k < 2 && e == cudaSuccess; ++k)
@@ -1546,8 +1570,8 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
 fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile) {
   g_err.clear();
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
-  if (ebe_variant < 0 || ebe_variant > 2) return fail(FEM_ERR_ARG, "ebe_variant must be 0, 1 or 2");
-  if (ebe_variant == 2 && !m->hex) return fail(FEM_ERR_ARG, "the mesh has no hex patches: tiled kernel unavailable");
+  if (ebe_variant < 0 || ebe_variant > 3) return fail(FEM_ERR_ARG, "ebe_variant must be 0, 1, 2 or 3");
+  if (ebe_variant >= 2 && !m->hex) return fail(FEM_ERR_ARG, "the mesh has no hex patches: tiled kernel unavailable");
   if (hex_per_tile != 0 && hex_per_tile != 64 && hex_per_tile != 128 && hex_per_tile != 256 && hex_per_tile != 512)
     return fail(FEM_ERR_ARG, "hex_per_tile must be 0, 64, 128, 256 or 512");
   m->ebe_variant = ebe_variant;

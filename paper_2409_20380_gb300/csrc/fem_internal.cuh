@@ -236,6 +236,13 @@ cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, cons
 cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, const double* y, double* out,
                          cudaStream_t s);
 // Split FP64 product: qM = M p and qK = K p in one pass (generic element kernel).
+// Staged variant of the tiled hex kernel (tile values and records copied to shared memory first).
+template <typename T>
+cudaError_t launch_ebe_hex_staged(const HexTiles& ht, const MeshView& m, int rpad, const T* p, T* q, double aM,
+                                  double aK, const Reducer* red, CgCase* sc, double* ptq_out, const int* gate,
+                                  cudaStream_t s);
+template <typename T>
+size_t ebe_hex_staged_smem(const HexTiles& ht, const MeshView& m, int rpad);
 cudaError_t launch_ebe_split(const MeshView& m, int rpad, const double* p, double* qM, double* qK, cudaStream_t s);
 // The same product in double-float arithmetic from (hi, lo) FP32 records rec_df [E][12][2].
 cudaError_t launch_ebe_split_df(const MeshView& m, const float* rec_df, int rpad, const double* p, double* qM,

@@ -387,6 +387,233 @@ template cudaError_t launch_ebe_hex<double>(const HexTiles&, const MeshView&, in
 template cudaError_t launch_ebe_hex<float>(const HexTiles&, const MeshView&, int, const float*, float*, double,
                                            double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
 
+// ------------------------------------------------------------------------------------------------------
+// Staged tiled hex-patch EBE: as k_ebe_hex, but each tile first copies its nodes' values of p and its
+// hexes' element records into shared memory with coalesced loads, so the per-hex work reads only shared
+// memory (no global-load latency inside the element arithmetic).  The flush divides by the constant 3
+// (a tile node holds 3 x rpad values, rpad a power of two).
+// ------------------------------------------------------------------------------------------------------
+template <typename T> struct SVec4;
+template <> struct SVec4<float> {
+  __device__ __forceinline__ static void load12(const float* src, float (&r)[12]) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    const float4 a = s4[0], b = s4[1], c = s4[2];
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+    r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+    r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
+  }
+};
+template <> struct SVec4<double> {
+  __device__ __forceinline__ static void load12(const double* src, double (&r)[12]) {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const double2 v = s2[i];
+      r[2 * i] = v.x;
+      r[2 * i + 1] = v.y;
+    }
+  }
+};
+
+template <typename T, int A0, int A1, int A2, int A3>
+__device__ __forceinline__ void tet_acc_s(const T* re, T aM, T aK, const T (&P)[8][3], T (&Q)[8][3]) {
+  T r[12];
+  SVec4<T>::load12(re, r);
+  const T lam = aK * r[9], mu = aK * r[10], ms = aM * r[11];
+  T G[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T d1 = P[A1][i] - P[A0][i], d2 = P[A2][i] - P[A0][i], d3 = P[A3][i] - P[A0][i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) G[i][j] = d1 * r[j] + d2 * r[3 + j] + d3 * r[6 + j];
+  }
+  const T tr = G[0][0] + G[1][1] + G[2][2];
+  const T mu2 = mu + mu;
+  T S[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) S[i][i] = lam * tr + mu2 * G[i][i];
+  S[0][1] = S[1][0] = mu * (G[0][1] + G[1][0]);
+  S[0][2] = S[2][0] = mu * (G[0][2] + G[2][0]);
+  S[1][2] = S[2][1] = mu * (G[1][2] + G[2][1]);
+  T F[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[b][i] = S[i][0] * r[3 * b] + S[i][1] * r[3 * b + 1] + S[i][2] * r[3 * b + 2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T sum = P[A0][k] + P[A1][k] + P[A2][k] + P[A3][k];
+    Q[A0][k] += ms * (P[A0][k] + sum) - (F[0][k] + F[1][k] + F[2][k]);
+    Q[A1][k] += ms * (P[A1][k] + sum) + F[0][k];
+    Q[A2][k] += ms * (P[A2][k] + sum) + F[1][k];
+    Q[A3][k] += ms * (P[A3][k] + sum) + F[2][k];
+  }
+}
+
+// Shared-memory layout of a staged tile (byte offsets, each section 16-byte aligned).
+struct StagedLayout {
+  size_t qs, ps, node, rec, acc, total;
+};
+template <typename T>
+__host__ __device__ inline StagedLayout staged_layout(int nloc_max, int rpad, int hex_per_tile, int nseg) {
+  auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  StagedLayout L;
+  const size_t vals = (size_t)nloc_max * 3 * rpad * sizeof(T);
+  L.qs = 0;
+  L.ps = up(vals);
+  L.node = L.ps + up(vals);
+  L.rec = L.node + up(sizeof(int) * (size_t)nloc_max);
+  L.acc = L.rec + up(sizeof(T) * (size_t)hex_per_tile * 6 * kRec);
+  L.total = L.acc + sizeof(double) * (size_t)nseg;
+  return L;
+}
+
+template <typename T, bool DOT, bool SEG>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_staged(
+    HexTiles ht, MeshView m, int rpad, int rshift, const T* __restrict__ p, T* __restrict__ q, T aM, T aK, Reducer red,
+    CgCase* sc, double* ptq_out, const int* gate) {
+  if (gate && *gate == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const StagedLayout L = staged_layout<T>(ht.nloc_max, rpad, ht.hex_per_tile, SEG ? m.nseg : 0);
+  T* qs = reinterpret_cast<T*>(smem_raw + L.qs);
+  T* ps = reinterpret_cast<T*>(smem_raw + L.ps);
+  int* snode = reinterpret_cast<int*>(smem_raw + L.node);
+  T* srec = reinterpret_cast<T*>(smem_raw + L.rec);
+  double* sacc = reinterpret_cast<double*>(smem_raw + L.acc);
+  constexpr bool seg = DOT && SEG;
+  if (seg) {
+    for (int t = threadIdx.x; t < m.nseg; t += blockDim.x) sacc[t] = 0.0;
+    __syncthreads();
+  }
+  const T* __restrict__ rec = rec_of<T>(m);
+  double dot = 0.0;
+  const int per_node = 3 * rpad;
+  for (int tile = blockIdx.x; tile < ht.n_tiles; tile += gridDim.x) {
+    const int n0 = ht.tile_node_off[tile], nl = ht.tile_node_off[tile + 1] - n0;
+    const int h0 = ht.tile_hex_off[tile], nh = ht.tile_hex_off[tile + 1] - h0;
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) snode[i] = ht.tile_nodes[n0 + i];
+    {  // element records of the tile: contiguous, copied as 16-byte vectors
+      const int nvec = nh * 6 * kRec * (int)sizeof(T) / 16;
+      const uint4* src = reinterpret_cast<const uint4*>(rec + (int64_t)h0 * 6 * kRec);
+      uint4* dst = reinterpret_cast<uint4*>(srec);
+      for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) {
+      const int l = (i >> rshift) / 3, rem = i - l * per_node;
+      ps[i] = p[(int64_t)(snode[l] & 0x7fffffff) * per_node + rem];
+      qs[i] = (T)0;
+    }
+    __syncthreads();
+    T tdot = 0;
+    const int items = nh << rshift;
+    const int rounds_end = seg ? ((items + blockDim.x - 1) / blockDim.x) * blockDim.x : items;
+    for (int it = threadIdx.x; it < rounds_end; it += blockDim.x) {
+      if (it >= items) {
+        double z1[1] = {0.0};
+        seg_add<1>(sacc, m.nseg, 0, z1);
+        continue;
+      }
+      const int hl = it >> rshift, c = it & (rpad - 1);
+      const uint4 lw = __ldg(ht.hex_local + h0 + hl);
+      int ls[8] = {(int)(lw.x & 0xffff), (int)(lw.x >> 16), (int)(lw.y & 0xffff), (int)(lw.y >> 16),
+                   (int)(lw.z & 0xffff), (int)(lw.z >> 16), (int)(lw.w & 0xffff), (int)(lw.w >> 16)};
+      T P[8][3], Q[8][3];
+#pragma unroll
+      for (int sl = 0; sl < 8; ++sl)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          P[sl][k] = ps[ls[sl] * per_node + (k << rshift) + c];
+          Q[sl][k] = (T)0;
+        }
+      const T* re = srec + hl * 6 * kRec;
+      tet_acc_s<T, kHexTet[0][0], kHexTet[0][1], kHexTet[0][2], kHexTet[0][3]>(re + 0 * kRec, aM, aK, P, Q);
+      tet_acc_s<T, kHexTet[1][0], kHexTet[1][1], kHexTet[1][2], kHexTet[1][3]>(re + 1 * kRec, aM, aK, P, Q);
+      tet_acc_s<T, kHexTet[2][0], kHexTet[2][1], kHexTet[2][2], kHexTet[2][3]>(re + 2 * kRec, aM, aK, P, Q);
+      tet_acc_s<T, kHexTet[3][0], kHexTet[3][1], kHexTet[3][2], kHexTet[3][3]>(re + 3 * kRec, aM, aK, P, Q);
+      tet_acc_s<T, kHexTet[4][0], kHexTet[4][1], kHexTet[4][2], kHexTet[4][3]>(re + 4 * kRec, aM, aK, P, Q);
+      tet_acc_s<T, kHexTet[5][0], kHexTet[5][1], kHexTet[5][2], kHexTet[5][3]>(re + 5 * kRec, aM, aK, P, Q);
+      T hdot = 0;
+#pragma unroll
+      for (int sl = 0; sl < 8; ++sl)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (DOT) hdot += P[sl][k] * Q[sl][k];
+          atomicAdd(qs + ls[sl] * per_node + (k << rshift) + c, Q[sl][k]);
+        }
+      if (seg) {
+        double v1[1] = {(double)hdot};
+        seg_add<1>(sacc, m.nseg, m.seg[snode[ls[0]] & 0x7fffffff], v1);
+      } else {
+        tdot += hdot;
+      }
+    }
+    dot += (double)tdot;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) {
+      const int l = (i >> rshift) / 3, rem = i - l * per_node;
+      const int k = rem >> rshift;
+      const int raw = snode[l];
+      const int64_t g = raw & 0x7fffffff;
+      const bool fixed = !dof_free(m.freemask[g], k);
+      T* dst = q + g * per_node + rem;
+      if (raw < 0) {
+        if (!fixed) atomicAdd(dst, qs[i]);
+      } else {
+        *dst = fixed ? (T)0 : qs[i];
+      }
+    }
+    __syncthreads();
+  }
+  if (DOT) {
+    if (seg) {
+      if (block_reduce_last_seg<1>(sacc, m.nseg, red)) ebe_tail_seg(red, sc, ptq_out, m.nseg);
+    } else {
+      double v[1] = {dot};
+      if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
+    }
+  }
+}
+
+template <typename T>
+size_t ebe_hex_staged_smem(const HexTiles& ht, const MeshView& m, int rpad) {
+  return staged_layout<T>(ht.nloc_max, rpad, ht.hex_per_tile, m.seg ? m.nseg : 0).total;
+}
+template size_t ebe_hex_staged_smem<float>(const HexTiles&, const MeshView&, int);
+template size_t ebe_hex_staged_smem<double>(const HexTiles&, const MeshView&, int);
+
+template <typename T>
+cudaError_t launch_ebe_hex_staged(const HexTiles& ht, const MeshView& m, int rpad, const T* p, T* q, double aM,
+                                  double aK, const Reducer* red, CgCase* sc, double* ptq_out, const int* gate,
+                                  cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(q, 0, sizeof(T) * (size_t)m.N * 3 * rpad, s);
+  if (err != cudaSuccess) return err;
+  const int rs = log2i(rpad);
+  const size_t smem = ebe_hex_staged_smem<T>(ht, m, rpad);
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 1;
+  auto kfn = red ? (m.seg ? k_ebe_hex_staged<T, true, true> : k_ebe_hex_staged<T, true, false>)
+                 : k_ebe_hex_staged<T, false, false>;
+  err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBlock, smem);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  int grid = nsm * per_sm;
+  if (grid > ht.n_tiles) grid = ht.n_tiles;
+  if (grid > kMaxRedBlocks) grid = kMaxRedBlocks;
+  Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
+  kfn<<<grid, kBlock, smem, s>>>(ht, m, rpad, rs, p, q, (T)aM, (T)aK, rd, red ? sc : nullptr, red ? ptq_out : nullptr,
+                                 gate);
+  return cudaGetLastError();
+}
+template cudaError_t launch_ebe_hex_staged<double>(const HexTiles&, const MeshView&, int, const double*, double*,
+                                                   double, double, const Reducer*, CgCase*, double*, const int*,
+                                                   cudaStream_t);
+template cudaError_t launch_ebe_hex_staged<float>(const HexTiles&, const MeshView&, int, const float*, float*, double,
+                                                  double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
+
 // Split FP64 product for the certification pass: qM = M p and qK = K p in one pass over the elements (the
 // increment's two products feed the recurrences of the right-hand side).  Generic element kernel.
 __global__ void __launch_bounds__(kBlock) k_ebe_split(MeshView m, int rpad, int rshift, const double* __restrict__ p,
