@@ -355,8 +355,8 @@ struct fem_mesh {
   }
   // Tiling for a product on T with rpad cases: the largest tile whose accumulator fits the budget.
   // EBE implementation of a product on elements of elem_bytes with rpad cases: an explicit fem_mesh_tune
-  // setting wins, else the autotuned choice for this precision and case count, else the tiled hex kernel
-  // when the mesh has hex patches.
+  // setting wins, else the autotuned choice for this precision and case count, else the staged tiled hex
+  // kernel when the mesh has hex patches.
   void resolve(size_t elem_bytes, int rpad, int* variant, int* hpt) const {
     *variant = ebe_variant, *hpt = hex_per_tile;
     if (*variant == 0 && *hpt == 0) {
@@ -365,7 +365,7 @@ struct fem_mesh {
       const Tuned& t = tuned[elem_bytes == 4 ? 0 : 1][lg];
       if (t.variant) *variant = t.variant, *hpt = t.hpt;
     }
-    if (*variant == 0) *variant = hex ? 2 : 1;
+    if (*variant == 0) *variant = hex ? 3 : 1;       // staged tiles where they apply (else tiled, else generic)
     if (!hex) *variant = 1;
   }
   // Tiling for the resolved variant: the largest tile whose shared memory fits (or the requested size).
@@ -388,11 +388,6 @@ struct fem_mesh {
     }
     return best;
   }
-  const HexTiles* pick_tiles(size_t elem_bytes, int rpad) const {
-    int v, h;
-    resolve(elem_bytes, rpad, &v, &h);
-    return v == 2 ? tiles_for(elem_bytes, rpad, 2, h) : nullptr;
-  }
   fem_status workspace(int rpad, Workspace** out) {
     for (auto* w : ws)
       if (w->rpad == rpad) {
@@ -414,10 +409,13 @@ static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, do
                                const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s) {
   int v, h;
   m->resolve(sizeof(T), rpad, &v, &h);
-  if (const HexTiles* t = m->tiles_for(sizeof(T), rpad, v, h)) {
-    if (v == 3) return launch_ebe_hex_staged<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
-    return launch_ebe_hex<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
+  if (v == 3) {   // staged copies need 16-byte rows (3 x rpad values) and a 16-byte aligned input
+    const HexTiles* t = (reinterpret_cast<uintptr_t>(p) & 15) == 0 ? m->tiles_for(sizeof(T), rpad, 3, h) : nullptr;
+    if (t) return launch_ebe_hex_staged<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
+    v = 2, h = 0;
   }
+  if (const HexTiles* t = m->tiles_for(sizeof(T), rpad, v, h))
+    return launch_ebe_hex<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
   return launch_ebe_gated<T>(m->view(), rpad, p, nullptr, q, aM, aK, red, sc, ptq, gate, s);
 }
 
@@ -1884,6 +1882,11 @@ fem_status fem_step(fem_batch* b, int n_steps, int* iters_out, double* relres_ou
     if (b->prof.on) b->prof.steps += 1;
   }
   for (auto* g : b->groups) CHK(group_graph_stats(b, g, &worst));
+  {
+    int tmo = 0;   // a staged EBE kernel whose bounded wait for its copies gave up: results not valid
+    CU(ebe_tma_timeout(&tmo));
+    if (tmo) return fail(FEM_ERR_TIMEOUT, "fem_step: an EBE kernel's wait for its tile copies timed out");
+  }
   for (size_t c = 0; c < b->loc.size(); ++c) {
     const Group* g = b->groups[b->loc[c].first];
     const int l = b->loc[c].second;

@@ -236,13 +236,16 @@ cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, cons
 cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, const double* y, double* out,
                          cudaStream_t s);
 // Split FP64 product: qM = M p and qK = K p in one pass (generic element kernel).
-// Staged variant of the tiled hex kernel (tile values and records copied to shared memory first).
+// Staged variant of the tiled hex kernel: each tile's node values and element records are brought into
+// shared memory by bulk asynchronous (TMA) copies, double-buffered against the previous tile's compute.
 template <typename T>
 cudaError_t launch_ebe_hex_staged(const HexTiles& ht, const MeshView& m, int rpad, const T* p, T* q, double aM,
                                   double aK, const Reducer* red, CgCase* sc, double* ptq_out, const int* gate,
                                   cudaStream_t s);
 template <typename T>
-size_t ebe_hex_staged_smem(const HexTiles& ht, const MeshView& m, int rpad);
+size_t ebe_hex_staged_smem(const HexTiles& ht, const MeshView& m, int rpad);   // ~0 when not applicable
+// Reads and clears the flag a staged kernel sets when a bounded wait for its copies gave up.
+cudaError_t ebe_tma_timeout(int* flag);
 cudaError_t launch_ebe_split(const MeshView& m, int rpad, const double* p, double* qM, double* qK, cudaStream_t s);
 // The same product in double-float arithmetic from (hi, lo) FP32 records rec_df [E][12][2].
 cudaError_t launch_ebe_split_df(const MeshView& m, const float* rec_df, int rpad, const double* p, double* qM,

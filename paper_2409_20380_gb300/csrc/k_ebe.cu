@@ -387,12 +387,6 @@ template cudaError_t launch_ebe_hex<double>(const HexTiles&, const MeshView&, in
 template cudaError_t launch_ebe_hex<float>(const HexTiles&, const MeshView&, int, const float*, float*, double,
                                            double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
 
-// ------------------------------------------------------------------------------------------------------
-// Staged tiled hex-patch EBE: as k_ebe_hex, but each tile first copies its nodes' values of p and its
-// hexes' element records into shared memory with coalesced loads, so the per-hex work reads only shared
-// memory (no global-load latency inside the element arithmetic).  The flush divides by the constant 3
-// (a tile node holds 3 x rpad values, rpad a power of two).
-// ------------------------------------------------------------------------------------------------------
 template <typename T> struct SVec4;
 template <> struct SVec4<float> {
   __device__ __forceinline__ static void load12(const float* src, float (&r)[12]) {
@@ -450,22 +444,68 @@ __device__ __forceinline__ void tet_acc_s(const T* re, T aM, T aK, const T (&P)[
   }
 }
 
-// Shared-memory layout of a staged tile (byte offsets, each section 16-byte aligned).
+// ------------------------------------------------------------------------------------------------------
+// TMA-staged tiled hex kernel.  Tile t's element records (one contiguous block) and its nodes' values of
+// p (3 x rpad contiguous values per node) are brought into shared memory by bulk asynchronous copies
+// (cp.async.bulk, completion counted in bytes on an mbarrier), double-buffered: while tile t is computed,
+// the copies of tile t+1 are in flight.  The per-hex arithmetic then reads only shared memory.  Waits are
+// bounded; a wait that gives up sets g_tma_timeout (the results are then not valid and the caller reports
+// FEM_ERR_TIMEOUT).  Needs 3 x rpad x sizeof(T) to be a multiple of 16 bytes (rpad >= 4 for FP32).
+// ------------------------------------------------------------------------------------------------------
+__device__ int g_tma_timeout = 0;
+
 struct StagedLayout {
-  size_t qs, ps, node, rec, acc, total;
+  size_t bar, qs, ps0, ps1, rec0, rec1, node0, node1, acc, total;
 };
 template <typename T>
 __host__ __device__ inline StagedLayout staged_layout(int nloc_max, int rpad, int hex_per_tile, int nseg) {
-  auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  auto up = [](size_t x) { return (x + 127) & ~(size_t)127; };
   StagedLayout L;
-  const size_t vals = (size_t)nloc_max * 3 * rpad * sizeof(T);
-  L.qs = 0;
-  L.ps = up(vals);
-  L.node = L.ps + up(vals);
-  L.rec = L.node + up(sizeof(int) * (size_t)nloc_max);
-  L.acc = L.rec + up(sizeof(T) * (size_t)hex_per_tile * 6 * kRec);
+  const size_t vals = up((size_t)nloc_max * 3 * rpad * sizeof(T));
+  const size_t recs = up(sizeof(T) * (size_t)hex_per_tile * 6 * kRec);
+  const size_t nodes = up(sizeof(int) * (size_t)nloc_max);
+  L.bar = 0;
+  L.qs = 128;
+  L.ps0 = L.qs + vals;
+  L.ps1 = L.ps0 + vals;
+  L.rec0 = L.ps1 + vals;
+  L.rec1 = L.rec0 + recs;
+  L.node0 = L.rec1 + recs;
+  L.node1 = L.node0 + nodes;
+  L.acc = L.node1 + nodes;
   L.total = L.acc + sizeof(double) * (size_t)nseg;
   return L;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
+__device__ __forceinline__ uint64_t gmem_u64(const void* ptr) {
+  uint64_t g;
+  asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(ptr));
+  return g;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(gmem_u64(src)), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// Bounded wait for phase `parity` of the barrier; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < (1 << 20); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
 }
 
 template <typename T, bool DOT, bool SEG>
@@ -473,38 +513,88 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
     HexTiles ht, MeshView m, int rpad, int rshift, const T* __restrict__ p, T* __restrict__ q, T aM, T aK, Reducer red,
     CgCase* sc, double* ptq_out, const int* gate) {
   if (gate && *gate == 0) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const StagedLayout L = staged_layout<T>(ht.nloc_max, rpad, ht.hex_per_tile, SEG ? m.nseg : 0);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L.bar);
   T* qs = reinterpret_cast<T*>(smem_raw + L.qs);
-  T* ps = reinterpret_cast<T*>(smem_raw + L.ps);
-  int* snode = reinterpret_cast<int*>(smem_raw + L.node);
-  T* srec = reinterpret_cast<T*>(smem_raw + L.rec);
+  // buffer b of each double-buffered section (selected arithmetically: no local-memory pointer arrays)
+  auto psb = [&](int b) { return reinterpret_cast<T*>(smem_raw + (b ? L.ps1 : L.ps0)); };
+  auto srb = [&](int b) { return reinterpret_cast<T*>(smem_raw + (b ? L.rec1 : L.rec0)); };
+  auto snb = [&](int b) { return reinterpret_cast<int*>(smem_raw + (b ? L.node1 : L.node0)); };
   double* sacc = reinterpret_cast<double*>(smem_raw + L.acc);
   constexpr bool seg = DOT && SEG;
-  if (seg) {
-    for (int t = threadIdx.x; t < m.nseg; t += blockDim.x) sacc[t] = 0.0;
-    __syncthreads();
-  }
-  const T* __restrict__ rec = rec_of<T>(m);
-  double dot = 0.0;
   const int per_node = 3 * rpad;
-  for (int tile = blockIdx.x; tile < ht.n_tiles; tile += gridDim.x) {
-    const int n0 = ht.tile_node_off[tile], nl = ht.tile_node_off[tile + 1] - n0;
-    const int h0 = ht.tile_hex_off[tile], nh = ht.tile_hex_off[tile + 1] - h0;
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) snode[i] = ht.tile_nodes[n0 + i];
-    {  // element records of the tile: contiguous, copied as 16-byte vectors
-      const int nvec = nh * 6 * kRec * (int)sizeof(T) / 16;
-      const uint4* src = reinterpret_cast<const uint4*>(rec + (int64_t)h0 * 6 * kRec);
-      uint4* dst = reinterpret_cast<uint4*>(srec);
-      for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = __ldg(src + i);
+  const uint32_t node_bytes = (uint32_t)(per_node * sizeof(T));
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&mbar[0]), 1);
+    mbar_init(smem_u32(&mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (seg)
+    for (int t = threadIdx.x; t < m.nseg; t += blockDim.x) sacc[t] = 0.0;
+  __syncthreads();
+  const T* __restrict__ rec = rec_of<T>(m);
+  // node ids of a tile (each thread owns tile nodes threadIdx.x and threadIdx.x + kBlock)
+  auto load_nodes = [&](int t, int (&nd)[2]) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int l = threadIdx.x + j * kBlock;
+      nd[j] = 0;
+      if (t < ht.n_tiles) {
+        const int n0 = ht.tile_node_off[t];
+        if (l < ht.tile_node_off[t + 1] - n0) nd[j] = ht.tile_nodes[n0 + l];
+      }
+    }
+  };
+  // bulk copies of tile t into buffer b (the buffer's previous readers have passed a block barrier)
+  auto issue = [&](int t, int b, const int (&nd)[2]) {
+    const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
+    const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
+    const uint32_t bar = smem_u32(mbar + b);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+      const uint32_t rbytes = (uint32_t)(nh * 6 * kRec * sizeof(T));
+      mbar_expect_tx(bar, rbytes + (uint32_t)nl * node_bytes);
+      bulk_g2s(smem_u32(srb(b)), rec + (int64_t)h0 * 6 * kRec, rbytes, bar);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int l = threadIdx.x + j * kBlock;
+      if (l < nl) {
+        snb(b)[l] = nd[j];
+        bulk_g2s(smem_u32(psb(b) + (int64_t)l * per_node), p + (int64_t)(nd[j] & 0x7fffffff) * per_node, node_bytes,
+                 bar);
+      }
+    }
+  };
+  double dot = 0.0;
+  int nd_next[2], nd_after[2];
+  const int t0 = blockIdx.x;
+  {
+    int nd0[2];
+    load_nodes(t0, nd0);
+    load_nodes(t0 + gridDim.x, nd_next);
+    if (t0 < ht.n_tiles) issue(t0, 0, nd0);
+  }
+  for (int k = 0;; ++k) {
+    const int t = t0 + k * gridDim.x;
+    if (t >= ht.n_tiles) break;
+    const int b = k & 1;
+    const int tn = t + gridDim.x;
+    if (tn < ht.n_tiles) issue(tn, b ^ 1, nd_next);
+    load_nodes(tn + gridDim.x, nd_after);
+    const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
+    const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
+    for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) qs[i] = (T)0;
+    const uint32_t bar = smem_u32(mbar + b);
+    if (!mbar_wait(bar, (uint32_t)((k >> 1) & 1))) {
+      atomicExch(&g_tma_timeout, 1);
+      mbar_wait(bar, (uint32_t)((k >> 1) & 1));   // second bounded wait for the copies still in flight
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) {
-      const int l = (i >> rshift) / 3, rem = i - l * per_node;
-      ps[i] = p[(int64_t)(snode[l] & 0x7fffffff) * per_node + rem];
-      qs[i] = (T)0;
-    }
-    __syncthreads();
+    const T* ps = psb(b);
+    const T* sr = srb(b);
+    const int* snode = snb(b);
     T tdot = 0;
     const int items = nh << rshift;
     const int rounds_end = seg ? ((items + blockDim.x - 1) / blockDim.x) * blockDim.x : items;
@@ -522,11 +612,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
 #pragma unroll
       for (int sl = 0; sl < 8; ++sl)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          P[sl][k] = ps[ls[sl] * per_node + (k << rshift) + c];
-          Q[sl][k] = (T)0;
+        for (int kk = 0; kk < 3; ++kk) {
+          P[sl][kk] = ps[ls[sl] * per_node + (kk << rshift) + c];
+          Q[sl][kk] = (T)0;
         }
-      const T* re = srec + hl * 6 * kRec;
+      const T* re = sr + hl * 6 * kRec;
       tet_acc_s<T, kHexTet[0][0], kHexTet[0][1], kHexTet[0][2], kHexTet[0][3]>(re + 0 * kRec, aM, aK, P, Q);
       tet_acc_s<T, kHexTet[1][0], kHexTet[1][1], kHexTet[1][2], kHexTet[1][3]>(re + 1 * kRec, aM, aK, P, Q);
       tet_acc_s<T, kHexTet[2][0], kHexTet[2][1], kHexTet[2][2], kHexTet[2][3]>(re + 2 * kRec, aM, aK, P, Q);
@@ -537,9 +627,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
 #pragma unroll
       for (int sl = 0; sl < 8; ++sl)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          if (DOT) hdot += P[sl][k] * Q[sl][k];
-          atomicAdd(qs + ls[sl] * per_node + (k << rshift) + c, Q[sl][k]);
+        for (int kk = 0; kk < 3; ++kk) {
+          if (DOT) hdot += P[sl][kk] * Q[sl][kk];
+          atomicAdd(qs + ls[sl] * per_node + (kk << rshift) + c, Q[sl][kk]);
         }
       if (seg) {
         double v1[1] = {(double)hdot};
@@ -552,10 +642,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
     __syncthreads();
     for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) {
       const int l = (i >> rshift) / 3, rem = i - l * per_node;
-      const int k = rem >> rshift;
+      const int kk = rem >> rshift;
       const int raw = snode[l];
       const int64_t g = raw & 0x7fffffff;
-      const bool fixed = !dof_free(m.freemask[g], k);
+      const bool fixed = !dof_free(m.freemask[g], kk);
       T* dst = q + g * per_node + rem;
       if (raw < 0) {
         if (!fixed) atomicAdd(dst, qs[i]);
@@ -564,6 +654,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
       }
     }
     __syncthreads();
+    nd_next[0] = nd_after[0];
+    nd_next[1] = nd_after[1];
   }
   if (DOT) {
     if (seg) {
@@ -577,6 +669,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
 
 template <typename T>
 size_t ebe_hex_staged_smem(const HexTiles& ht, const MeshView& m, int rpad) {
+  if ((3 * rpad * sizeof(T)) % 16 != 0 || ht.nloc_max > 2 * kBlock) return ~(size_t)0;   // not applicable
   return staged_layout<T>(ht.nloc_max, rpad, ht.hex_per_tile, m.seg ? m.nseg : 0).total;
 }
 template size_t ebe_hex_staged_smem<float>(const HexTiles&, const MeshView&, int);
@@ -586,10 +679,11 @@ template <typename T>
 cudaError_t launch_ebe_hex_staged(const HexTiles& ht, const MeshView& m, int rpad, const T* p, T* q, double aM,
                                   double aK, const Reducer* red, CgCase* sc, double* ptq_out, const int* gate,
                                   cudaStream_t s) {
+  const size_t smem = ebe_hex_staged_smem<T>(ht, m, rpad);
+  if (smem == ~(size_t)0 || (reinterpret_cast<uintptr_t>(p) & 15) != 0) return cudaErrorInvalidValue;
   cudaError_t err = cudaMemsetAsync(q, 0, sizeof(T) * (size_t)m.N * 3 * rpad, s);
   if (err != cudaSuccess) return err;
   const int rs = log2i(rpad);
-  const size_t smem = ebe_hex_staged_smem<T>(ht, m, rpad);
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -613,6 +707,14 @@ template cudaError_t launch_ebe_hex_staged<double>(const HexTiles&, const MeshVi
                                                    cudaStream_t);
 template cudaError_t launch_ebe_hex_staged<float>(const HexTiles&, const MeshView&, int, const float*, float*, double,
                                                   double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
+
+// Reads (and clears) the flag set when a staged kernel's bounded wait for its copies gave up.
+cudaError_t ebe_tma_timeout(int* flag) {
+  int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(flag, g_tma_timeout, sizeof(int));
+  if (e == cudaSuccess && *flag) e = cudaMemcpyToSymbol(g_tma_timeout, &zero, sizeof(int));
+  return e;
+}
 
 // Split FP64 product for the certification pass: qM = M p and qK = K p in one pass over the elements (the
 // increment's two products feed the recurrences of the right-hand side).  Generic element kernel.
