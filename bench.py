@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--kernel", default=None, choices=["ebe"],
                     help="time one kernel alone (EBE product) instead of the full step")
     ap.add_argument("--kernel-precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--variant", type=int, default=0, help="EBE variant: 0 auto, 1 generic, 2 tiled hex")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="EBE variant: 0 auto, 1 generic, 2 tiled hex, 3 staged tiles, 4 case-major staged tiles")
     ap.add_argument("--hex-per-tile", type=int, default=0)
     ap.add_argument("--uneven", action="store_true",
                     help="batched uneven meshes: --meshes cases on meshes of different sizes fused into one system")
@@ -267,6 +268,8 @@ def run_ours(args):
                                 use_graph=0 if args.no_graph else 1)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
+    if args.variant or args.hex_per_tile:
+        fem.fem_mesh_tune(h, args.variant, args.hex_per_tile)
     bt = fem.fem_batch_create(opts)
     nc = len(srcs)
     for s in srcs:

@@ -144,17 +144,20 @@ fem_status fem_mesh_destroy(fem_mesh* m);
  * Section 3.2, Eq. eqebefem).  ebe_variant: 0 = automatic, 1 = generic element kernel, 2 = tiled hex-patch
  * kernel (available when the elements come in groups of six tets splitting a hexahedron with the Kuhn
  * topology, which fem_mesh_create detects), 3 = the tiled hex kernel with each tile's node values and
- * element records staged in shared memory first.  hex_per_tile: 0 = automatic (largest tile whose
+ * element records staged in shared memory first by bulk asynchronous copies (double-buffered), 4 = as 3
+ * with warps of one case each, so cases whose inner solve has converged are skipped (needs 3 x n_rhs x
+ * element size to be a multiple of 16 bytes; otherwise 3, then 2, then 1 is used).  hex_per_tile: 0 = automatic (largest tile whose
  * shared memory fits), or 64/128/256/512 hexes per tile.  Errors: FEM_ERR_ARG for other values or variants
- * 2/3 on a mesh without hex patches.
+ * 2-4 on a mesh without hex patches.
  */
 fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile);
 
 /*
  * Autotuner: times each EBE implementation that applies to the mesh on the inner solve's product
  * (q = A p with the fused p^T A p, n_rhs cases; FEM_FP32_INNER = FP32 product, FEM_FP64 = FP64 product):
- * the generic element kernel, the tiled hex kernel with 64/128/256/512 hexes per tile and the staged tiled
- * kernel with 64/128/256 hexes per tile, where their shared memory fits.  The fastest is kept for that precision and n_rhs and used whenever
+ * the generic element kernel, the tiled hex kernel with 64/128/256/512 hexes per tile, the staged tiled
+ * kernel with 64/128/256 and the case-major staged kernel with 64/128 hexes per tile, where their shared
+ * memory fits.  The fastest is kept for that precision and n_rhs and used whenever
  * fem_mesh_tune is left at automatic (0, 0).  Outputs (nullable): the chosen variant and tile size, and its
  * time per product in ms.  Runs on `stream` and synchronises it; allocates two temporary vectors.
  */

@@ -380,6 +380,9 @@ struct fem_mesh {
       if (variant == 3) {
         need = elem_bytes == 4 ? ebe_hex_staged_smem<float>(t, view(), rpad) : ebe_hex_staged_smem<double>(t, view(), rpad);
         budget = 110 * 1024;
+      } else if (variant == 4) {   // one block per SM
+        need = elem_bytes == 4 ? ebe_hex_cm_smem<float>(t, view(), rpad) : ebe_hex_cm_smem<double>(t, view(), rpad);
+        budget = 220 * 1024;
       } else {
         need = (size_t)t.nloc_max * (3 * rpad * elem_bytes + 4);
         budget = elem_bytes == 4 ? 100 * 1024 : 200 * 1024;
@@ -409,6 +412,11 @@ static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, do
                                const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s) {
   int v, h;
   m->resolve(sizeof(T), rpad, &v, &h);
+  if (v == 4) {   // case-major staged tiles (converged cases skipped); same requirements as 3, no fused groups
+    const HexTiles* t = (reinterpret_cast<uintptr_t>(p) & 15) == 0 ? m->tiles_for(sizeof(T), rpad, 4, h) : nullptr;
+    if (t) return launch_ebe_hex_cm<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
+    v = 3, h = 0;
+  }
   if (v == 3) {   // staged copies need 16-byte rows (3 x rpad values) and a 16-byte aligned input
     const HexTiles* t = (reinterpret_cast<uintptr_t>(p) & 15) == 0 ? m->tiles_for(sizeof(T), rpad, 3, h) : nullptr;
     if (t) return launch_ebe_hex_staged<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
@@ -1386,6 +1394,7 @@ static fem_status autotune_t(fem_mesh* m, int rpad, cudaStream_t s, int* v_out, 
   if (m->hex) {
     for (int hpt : {64, 128, 256, 512}) cand.push_back({2, hpt});
     for (int hpt : {64, 128, 256}) cand.push_back({3, hpt});
+    for (int hpt : {64, 128}) cand.push_back({4, hpt});
   }
   double best = 1e30;
   int bv = 1, bh = 0;
@@ -1568,7 +1577,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
 fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile) {
   g_err.clear();
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
-  if (ebe_variant < 0 || ebe_variant > 3) return fail(FEM_ERR_ARG, "ebe_variant must be 0, 1, 2 or 3");
+  if (ebe_variant < 0 || ebe_variant > 4) return fail(FEM_ERR_ARG, "ebe_variant must be 0 .. 4");
   if (ebe_variant >= 2 && !m->hex) return fail(FEM_ERR_ARG, "the mesh has no hex patches: tiled kernel unavailable");
   if (hex_per_tile != 0 && hex_per_tile != 64 && hex_per_tile != 128 && hex_per_tile != 256 && hex_per_tile != 512)
     return fail(FEM_ERR_ARG, "hex_per_tile must be 0, 64, 128, 256 or 512");

@@ -244,6 +244,12 @@ cudaError_t launch_ebe_hex_staged(const HexTiles& ht, const MeshView& m, int rpa
                                   cudaStream_t s);
 template <typename T>
 size_t ebe_hex_staged_smem(const HexTiles& ht, const MeshView& m, int rpad);   // ~0 when not applicable
+// Case-major staged variant: warps of 32 hexes of one case; converged cases (sc[c].active == 0) skipped.
+template <typename T>
+cudaError_t launch_ebe_hex_cm(const HexTiles& ht, const MeshView& m, int rpad, const T* p, T* q, double aM, double aK,
+                              const Reducer* red, CgCase* sc, double* ptq_out, const int* gate, cudaStream_t s);
+template <typename T>
+size_t ebe_hex_cm_smem(const HexTiles& ht, const MeshView& m, int rpad);   // ~0 when not applicable
 // Reads and clears the flag a staged kernel sets when a bounded wait for its copies gave up.
 cudaError_t ebe_tma_timeout(int* flag);
 cudaError_t launch_ebe_split(const MeshView& m, int rpad, const double* p, double* qM, double* qK, cudaStream_t s);

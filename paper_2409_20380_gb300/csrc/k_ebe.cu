@@ -667,6 +667,185 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
   }
 }
 
+// ------------------------------------------------------------------------------------------------------
+// Case-major staged variant: the same TMA double-buffered tiles, but each warp applies 32 hexes of ONE case,
+// so a case whose inner solve has converged (sc[c].active == 0) skips its warps entirely (the product of a
+// converged case is not used: its step length is zero).  Node rows in shared memory are padded to PN
+// values (PN = 4 mod 8 for FP32, PN = 2 mod 4 for FP64: 16-byte rows) so that lanes reading different nodes spread
+// over the banks.  One block of 512 threads per SM.  Per-case p^T q sums go through shared memory.
+// ------------------------------------------------------------------------------------------------------
+constexpr int kBlockCM = 512;
+
+template <typename T>
+__host__ __device__ inline int cm_stride(int rpad) {
+  int pn = 3 * rpad;
+  if (sizeof(T) == 4) {
+    while (pn % 8 != 4) ++pn;
+  } else {
+    while (pn % 4 != 2) ++pn;
+  }
+  return pn;
+}
+
+template <typename T>
+__host__ __device__ inline StagedLayout cm_layout(int nloc_max, int rpad, int hex_per_tile, int nseg) {
+  auto up = [](size_t x) { return (x + 127) & ~(size_t)127; };
+  StagedLayout L;
+  const size_t vals = up((size_t)nloc_max * cm_stride<T>(rpad) * sizeof(T));
+  const size_t recs = up(sizeof(T) * (size_t)hex_per_tile * 6 * kRec);
+  const size_t nodes = up(sizeof(int) * (size_t)nloc_max);
+  L.bar = 0;
+  L.qs = 128;
+  L.ps0 = L.qs + vals;
+  L.ps1 = L.ps0 + vals;
+  L.rec0 = L.ps1 + vals;
+  L.rec1 = L.rec0 + recs;
+  L.node0 = L.rec1 + recs;
+  L.node1 = L.node0 + nodes;
+  L.acc = L.node1 + nodes;
+  L.total = L.acc + sizeof(double) * (size_t)nseg;
+  return L;
+}
+
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(kBlockCM, 1) k_ebe_hex_cm(HexTiles ht, MeshView m, int rpad, int rshift,
+                                                            const T* __restrict__ p, T* __restrict__ q, T aM, T aK,
+                                                            Reducer red, CgCase* sc, double* ptq_out, const int* gate) {
+  if (gate && *gate == 0) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const StagedLayout L = cm_layout<T>(ht.nloc_max, rpad, ht.hex_per_tile, 0);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L.bar);
+  T* qs = reinterpret_cast<T*>(smem_raw + L.qs);
+  auto psb = [&](int b) { return reinterpret_cast<T*>(smem_raw + (b ? L.ps1 : L.ps0)); };
+  auto srb = [&](int b) { return reinterpret_cast<T*>(smem_raw + (b ? L.rec1 : L.rec0)); };
+  auto snb = [&](int b) { return reinterpret_cast<int*>(smem_raw + (b ? L.node1 : L.node0)); };
+  const int per_node = 3 * rpad;
+  const int PN = cm_stride<T>(rpad);
+  const uint32_t node_bytes = (uint32_t)(per_node * sizeof(T));
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(mbar), 1);
+    mbar_init(smem_u32(mbar + 1), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // cases whose product is needed: all, unless the solve state says a case has converged
+  unsigned live = 0xffffffffu;
+  if (DOT && sc)
+    for (int c = 0; c < rpad; ++c)
+      if (!sc[c].active) live &= ~(1u << c);
+  const T* __restrict__ rec = rec_of<T>(m);
+  auto load_node = [&](int t) {
+    int nd = 0;
+    if (t < ht.n_tiles) {
+      const int n0 = ht.tile_node_off[t];
+      if ((int)threadIdx.x < ht.tile_node_off[t + 1] - n0) nd = ht.tile_nodes[n0 + threadIdx.x];
+    }
+    return nd;
+  };
+  auto issue = [&](int t, int b, int nd) {
+    const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
+    const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
+    const uint32_t bar = smem_u32(mbar + b);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+      const uint32_t rbytes = (uint32_t)(nh * 6 * kRec * sizeof(T));
+      mbar_expect_tx(bar, rbytes + (uint32_t)nl * node_bytes);
+      bulk_g2s(smem_u32(srb(b)), rec + (int64_t)h0 * 6 * kRec, rbytes, bar);
+    }
+    const int l = threadIdx.x;
+    if (l < nl) {
+      snb(b)[l] = nd;
+      bulk_g2s(smem_u32(psb(b) + (int64_t)l * PN), p + (int64_t)(nd & 0x7fffffff) * per_node, node_bytes, bar);
+    }
+  };
+  __shared__ double sdot[kMaxRpad];
+  if (DOT && threadIdx.x < kMaxRpad) sdot[threadIdx.x] = 0.0;
+  const int t0 = blockIdx.x;
+  int nd_next = load_node(t0 + gridDim.x);
+  issue(t0, 0, load_node(t0));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0;; ++k) {
+    const int t = t0 + k * gridDim.x;
+    if (t >= ht.n_tiles) break;
+    const int b = k & 1;
+    const int tn = t + gridDim.x;
+    if (tn < ht.n_tiles) issue(tn, b ^ 1, nd_next);
+    const int nd_after = load_node(tn + gridDim.x);
+    const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
+    const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
+    for (int i = threadIdx.x; i < nl * PN; i += blockDim.x) qs[i] = (T)0;
+    const uint32_t bar = smem_u32(mbar + b);
+    if (!mbar_wait(bar, (uint32_t)((k >> 1) & 1))) {
+      atomicExch(&g_tma_timeout, 1);
+      mbar_wait(bar, (uint32_t)((k >> 1) & 1));
+    }
+    __syncthreads();
+    const T* ps = psb(b);
+    const T* sr = srb(b);
+    const int* snode = snb(b);
+    // warp-group g applies hexes 32 (g / rpad) .. +31 of case g % rpad
+    const int groups = ((nh + 31) >> 5) << rshift;
+    for (int gw = warp; gw < groups; gw += kBlockCM / 32) {
+      const int c = gw & (rpad - 1);
+      if (!((live >> c) & 1u)) continue;
+      const int hl = ((gw >> rshift) << 5) + lane;
+      T hdot = 0;
+      if (hl < nh) {
+        const uint4 lw = __ldg(ht.hex_local + h0 + hl);
+        int ls[8] = {(int)(lw.x & 0xffff), (int)(lw.x >> 16), (int)(lw.y & 0xffff), (int)(lw.y >> 16),
+                     (int)(lw.z & 0xffff), (int)(lw.z >> 16), (int)(lw.w & 0xffff), (int)(lw.w >> 16)};
+        T P[8][3], Q[8][3];
+#pragma unroll
+        for (int sl = 0; sl < 8; ++sl)
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) {
+            P[sl][kk] = ps[ls[sl] * PN + (kk << rshift) + c];
+            Q[sl][kk] = (T)0;
+          }
+        const T* re = sr + hl * 6 * kRec;
+        tet_acc_s<T, kHexTet[0][0], kHexTet[0][1], kHexTet[0][2], kHexTet[0][3]>(re + 0 * kRec, aM, aK, P, Q);
+        tet_acc_s<T, kHexTet[1][0], kHexTet[1][1], kHexTet[1][2], kHexTet[1][3]>(re + 1 * kRec, aM, aK, P, Q);
+        tet_acc_s<T, kHexTet[2][0], kHexTet[2][1], kHexTet[2][2], kHexTet[2][3]>(re + 2 * kRec, aM, aK, P, Q);
+        tet_acc_s<T, kHexTet[3][0], kHexTet[3][1], kHexTet[3][2], kHexTet[3][3]>(re + 3 * kRec, aM, aK, P, Q);
+        tet_acc_s<T, kHexTet[4][0], kHexTet[4][1], kHexTet[4][2], kHexTet[4][3]>(re + 4 * kRec, aM, aK, P, Q);
+        tet_acc_s<T, kHexTet[5][0], kHexTet[5][1], kHexTet[5][2], kHexTet[5][3]>(re + 5 * kRec, aM, aK, P, Q);
+#pragma unroll
+        for (int sl = 0; sl < 8; ++sl)
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) {
+            if (DOT) hdot += P[sl][kk] * Q[sl][kk];
+            atomicAdd(qs + ls[sl] * PN + (kk << rshift) + c, Q[sl][kk]);
+          }
+      }
+      if (DOT) {   // the warp's lanes share one case: one shared-memory add per warp
+        for (int off = 16; off > 0; off >>= 1) hdot += __shfl_xor_sync(0xffffffffu, hdot, off);
+        if (lane == 0) atomicAdd(sdot + c, (double)hdot);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) {
+      const int l = (i >> rshift) / 3, rem = i - l * per_node;
+      const int kk = rem >> rshift;
+      const int raw = snode[l];
+      const int64_t g = raw & 0x7fffffff;
+      const bool fixed = !dof_free(m.freemask[g], kk);
+      T* dst = q + g * per_node + rem;
+      const T v = qs[l * PN + rem];
+      if (raw < 0) {
+        if (!fixed) atomicAdd(dst, v);
+      } else {
+        *dst = fixed ? (T)0 : v;
+      }
+    }
+    __syncthreads();
+    nd_next = nd_after;
+  }
+  if (DOT) {
+    // block partials are per case: the lanes of the reduction hold case c in lane c
+    if (block_reduce_last_seg<1>(sdot, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
+  }
+}
+
 template <typename T>
 size_t ebe_hex_staged_smem(const HexTiles& ht, const MeshView& m, int rpad) {
   if ((3 * rpad * sizeof(T)) % 16 != 0 || ht.nloc_max > 2 * kBlock) return ~(size_t)0;   // not applicable
@@ -707,6 +886,40 @@ template cudaError_t launch_ebe_hex_staged<double>(const HexTiles&, const MeshVi
                                                    cudaStream_t);
 template cudaError_t launch_ebe_hex_staged<float>(const HexTiles&, const MeshView&, int, const float*, float*, double,
                                                   double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
+
+template <typename T>
+size_t ebe_hex_cm_smem(const HexTiles& ht, const MeshView& m, int rpad) {
+  if ((3 * rpad * sizeof(T)) % 16 != 0 || ht.nloc_max > kBlockCM || m.seg) return ~(size_t)0;   // not applicable
+  return cm_layout<T>(ht.nloc_max, rpad, ht.hex_per_tile, 0).total;
+}
+template size_t ebe_hex_cm_smem<float>(const HexTiles&, const MeshView&, int);
+template size_t ebe_hex_cm_smem<double>(const HexTiles&, const MeshView&, int);
+
+template <typename T>
+cudaError_t launch_ebe_hex_cm(const HexTiles& ht, const MeshView& m, int rpad, const T* p, T* q, double aM, double aK,
+                              const Reducer* red, CgCase* sc, double* ptq_out, const int* gate, cudaStream_t s) {
+  const size_t smem = ebe_hex_cm_smem<T>(ht, m, rpad);
+  if (smem == ~(size_t)0 || (reinterpret_cast<uintptr_t>(p) & 15) != 0) return cudaErrorInvalidValue;
+  cudaError_t err = cudaMemsetAsync(q, 0, sizeof(T) * (size_t)m.N * 3 * rpad, s);
+  if (err != cudaSuccess) return err;
+  const int rs = log2i(rpad);
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  auto kfn = red ? k_ebe_hex_cm<T, true> : k_ebe_hex_cm<T, false>;
+  err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int grid = nsm;
+  if (grid > ht.n_tiles) grid = ht.n_tiles;
+  Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
+  kfn<<<grid, kBlockCM, smem, s>>>(ht, m, rpad, rs, p, q, (T)aM, (T)aK, rd, red ? sc : nullptr,
+                                   red ? ptq_out : nullptr, gate);
+  return cudaGetLastError();
+}
+template cudaError_t launch_ebe_hex_cm<double>(const HexTiles&, const MeshView&, int, const double*, double*, double,
+                                               double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
+template cudaError_t launch_ebe_hex_cm<float>(const HexTiles&, const MeshView&, int, const float*, float*, double,
+                                              double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
 
 // Reads (and clears) the flag set when a staged kernel's bounded wait for its copies gave up.
 cudaError_t ebe_tma_timeout(int* flag) {

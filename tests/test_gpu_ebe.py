@@ -26,7 +26,7 @@ def torch_dev():
 CASES = [((7, 5, 4), 1, 0.0), ((7, 5, 4), 4, 0.2), ((9, 6, 5), 16, 0.1), ((3, 2, 2), 32, 0.0), ((12, 9, 7), 8, 0.15)]
 # (ebe_variant, hex_per_tile): generic element kernel; tiled hex kernel and staged tiled hex kernel with
 # automatic and small tiles (140..756 hexes over 64-hex tiles: several tiles and a ragged last one)
-VARIANTS = [(1, 0), (2, 0), (2, 64), (3, 0), (3, 64)]
+VARIANTS = [(1, 0), (2, 0), (2, 64), (3, 0), (3, 64), (4, 0), (4, 64)]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -167,7 +167,8 @@ def test_autotuned_product_matches_csr(torch_dev, precision, r):
     try:
         prec = fem.FEM_FP32_INNER if precision == "fp32" else fem.FEM_FP64
         v, hpt, ms = fem.fem_mesh_autotune(h, prec, r)
-        assert (v, hpt) in [(1, 0), (2, 64), (2, 128), (2, 256), (2, 512), (3, 64), (3, 128), (3, 256)] and ms > 0
+        assert (v, hpt) in [(1, 0), (2, 64), (2, 128), (2, 256), (2, 512), (3, 64), (3, 128), (3, 256), (4, 64),
+                            (4, 128)] and ms > 0
         dt = torch.float32 if precision == "fp32" else torch.float64
         ps = random_free_vectors(m, r, seed=5 + r)
         p = torch.tensor(from_cases(ps, m.n_nodes, r), device="cuda", dtype=dt)
