@@ -1533,12 +1533,18 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
   if (h_err & 1) return bail(fail(FEM_ERR_ARG, "connectivity or material id out of range"));
   if (h_err & 2) return bail(fail(FEM_ERR_ARG, "element with non-positive volume (conn must be positively oriented)"));
   if (h_err & 4) return bail(fail(FEM_ERR_ARG, "singular node diagonal block (node with no element?)"));
-  if (detect_hex_patches(conn, n_elems)) {
+  // tile node entries carry the node id (bits 0-27), its three free-DOF bits (28-30) and whether another
+  // tile shares the node (bit 31): the kernels' flush needs no separate mask load
+  if (n_nodes < (int64_t(1) << 28) && detect_hex_patches(conn, n_elems)) {
     const int sizes[fem_mesh::kNTile] = {64, 128, 256, 512};
     bool ok = true;
     for (int i = 0; i < fem_mesh::kNTile && ok; ++i) {
       HexTilesHost th;
       if (!build_hex_tiles(conn, n_elems, n_nodes, sizes[i], &th)) continue;
+      for (int& v : th.tile_nodes) {
+        const uint32_t u = (uint32_t)v, node = u & 0x7fffffffu;
+        v = (int)((u & 0x80000000u) | ((uint32_t)(fm[node] & 7u) << 28) | node);
+      }
       int *d_hoff = nullptr, *d_noff = nullptr, *d_nodes = nullptr;
       uint4* d_loc = nullptr;
       ok = dalloc(&d_hoff, th.tile_hex_off.size()) == FEM_OK && dalloc(&d_noff, th.tile_node_off.size()) == FEM_OK &&

@@ -42,7 +42,7 @@ struct HexTiles {                    // device view
   int hex_per_tile = 0;
   const int* tile_hex_off = nullptr;
   const int* tile_node_off = nullptr;
-  const int* tile_nodes = nullptr;
+  const int* tile_nodes = nullptr;   // per entry: node id (bits 0-27), free-DOF bits (28-30), shared (31)
   const uint4* hex_local = nullptr;  // 8 x uint16 per hex
 };
 bool detect_hex_patches(const int32_t* conn, int64_t E);

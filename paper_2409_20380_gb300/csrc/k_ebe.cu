@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex(HexT
       T P[8][3], Q[8][3];
 #pragma unroll
       for (int sl = 0; sl < 8; ++sl) {
-        const int64_t g = snode[ls[sl]] & 0x7fffffff;
+        const int64_t g = snode[ls[sl]] & 0x0fffffff;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           P[sl][k] = p[(g * 3 + k) * rpad + c];
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex(HexT
         }
       if (seg) {
         double v1[1] = {(double)hdot};
-        seg_add<1>(sacc, m.nseg, m.seg[snode[ls[0]] & 0x7fffffff], v1);
+        seg_add<1>(sacc, m.nseg, m.seg[snode[ls[0]] & 0x0fffffff], v1);
       } else {
         tdot += hdot;
       }
@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex(HexT
       const int l = i / per_node, rem = i - l * per_node;
       const int k = rem >> rshift;
       const int raw = snode[l];
-      const int64_t g = raw & 0x7fffffff;
-      const bool fixed = !dof_free(m.freemask[g], k);
+      const int64_t g = raw & 0x0fffffff;
+      const bool fixed = !dof_free((uint8_t)((raw >> 28) & 7), k);
       T* dst = q + g * per_node + rem;
       if (raw < 0) {
         if (!fixed) atomicAdd(dst, qs[i]);
@@ -455,7 +455,7 @@ __device__ __forceinline__ void tet_acc_s(const T* re, T aM, T aK, const T (&P)[
 __device__ int g_tma_timeout = 0;
 
 struct StagedLayout {
-  size_t bar, qs, ps0, ps1, rec0, rec1, node0, node1, acc, total;
+  size_t bar, qs, ps0, ps1, rec0, rec1, node0, node1, loc0, loc1, acc, total;
 };
 template <typename T>
 __host__ __device__ inline StagedLayout staged_layout(int nloc_max, int rpad, int hex_per_tile, int nseg) {
@@ -472,6 +472,7 @@ __host__ __device__ inline StagedLayout staged_layout(int nloc_max, int rpad, in
   L.rec1 = L.rec0 + recs;
   L.node0 = L.rec1 + recs;
   L.node1 = L.node0 + nodes;
+  L.loc0 = L.loc1 = L.node1 + nodes;   // (corner tables are not staged in this variant)
   L.acc = L.node1 + nodes;
   L.total = L.acc + sizeof(double) * (size_t)nseg;
   return L;
@@ -562,7 +563,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
       const int l = threadIdx.x + j * kBlock;
       if (l < nl) {
         snb(b)[l] = nd[j];
-        bulk_g2s(smem_u32(psb(b) + (int64_t)l * per_node), p + (int64_t)(nd[j] & 0x7fffffff) * per_node, node_bytes,
+        bulk_g2s(smem_u32(psb(b) + (int64_t)l * per_node), p + (int64_t)(nd[j] & 0x0fffffff) * per_node, node_bytes,
                  bar);
       }
     }
@@ -598,6 +599,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
     T tdot = 0;
     const int items = nh << rshift;
     const int rounds_end = seg ? ((items + blockDim.x - 1) / blockDim.x) * blockDim.x : items;
+    // the corner table of the thread's next item is loaded one item ahead
+    uint4 lw_next = (int)threadIdx.x < items ? __ldg(ht.hex_local + h0 + (threadIdx.x >> rshift)) : make_uint4(0, 0, 0, 0);
     for (int it = threadIdx.x; it < rounds_end; it += blockDim.x) {
       if (it >= items) {
         double z1[1] = {0.0};
@@ -605,7 +608,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
         continue;
       }
       const int hl = it >> rshift, c = it & (rpad - 1);
-      const uint4 lw = __ldg(ht.hex_local + h0 + hl);
+      const uint4 lw = lw_next;
+      if (it + (int)blockDim.x < items) lw_next = __ldg(ht.hex_local + h0 + ((it + blockDim.x) >> rshift));
       int ls[8] = {(int)(lw.x & 0xffff), (int)(lw.x >> 16), (int)(lw.y & 0xffff), (int)(lw.y >> 16),
                    (int)(lw.z & 0xffff), (int)(lw.z >> 16), (int)(lw.w & 0xffff), (int)(lw.w >> 16)};
       T P[8][3], Q[8][3];
@@ -633,7 +637,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
         }
       if (seg) {
         double v1[1] = {(double)hdot};
-        seg_add<1>(sacc, m.nseg, m.seg[snode[ls[0]] & 0x7fffffff], v1);
+        seg_add<1>(sacc, m.nseg, m.seg[snode[ls[0]] & 0x0fffffff], v1);
       } else {
         tdot += hdot;
       }
@@ -644,8 +648,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
       const int l = (i >> rshift) / 3, rem = i - l * per_node;
       const int kk = rem >> rshift;
       const int raw = snode[l];
-      const int64_t g = raw & 0x7fffffff;
-      const bool fixed = !dof_free(m.freemask[g], kk);
+      const int64_t g = raw & 0x0fffffff;
+      const bool fixed = !dof_free((uint8_t)((raw >> 28) & 7), kk);
       T* dst = q + g * per_node + rem;
       if (raw < 0) {
         if (!fixed) atomicAdd(dst, qs[i]);
@@ -702,7 +706,9 @@ __host__ __device__ inline StagedLayout cm_layout(int nloc_max, int rpad, int he
   L.rec1 = L.rec0 + recs;
   L.node0 = L.rec1 + recs;
   L.node1 = L.node0 + nodes;
-  L.acc = L.node1 + nodes;
+  L.loc0 = L.node1 + nodes;
+  L.loc1 = L.loc0 + up(sizeof(uint4) * (size_t)hex_per_tile);
+  L.acc = L.loc1 + up(sizeof(uint4) * (size_t)hex_per_tile);
   L.total = L.acc + sizeof(double) * (size_t)nseg;
   return L;
 }
@@ -719,6 +725,7 @@ __global__ void __launch_bounds__(kBlockCM, 1) k_ebe_hex_cm(HexTiles ht, MeshVie
   auto psb = [&](int b) { return reinterpret_cast<T*>(smem_raw + (b ? L.ps1 : L.ps0)); };
   auto srb = [&](int b) { return reinterpret_cast<T*>(smem_raw + (b ? L.rec1 : L.rec0)); };
   auto snb = [&](int b) { return reinterpret_cast<int*>(smem_raw + (b ? L.node1 : L.node0)); };
+  auto lcb = [&](int b) { return reinterpret_cast<uint4*>(smem_raw + (b ? L.loc1 : L.loc0)); };
   const int per_node = 3 * rpad;
   const int PN = cm_stride<T>(rpad);
   const uint32_t node_bytes = (uint32_t)(per_node * sizeof(T));
@@ -749,13 +756,15 @@ __global__ void __launch_bounds__(kBlockCM, 1) k_ebe_hex_cm(HexTiles ht, MeshVie
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x == 0) {
       const uint32_t rbytes = (uint32_t)(nh * 6 * kRec * sizeof(T));
-      mbar_expect_tx(bar, rbytes + (uint32_t)nl * node_bytes);
+      const uint32_t lbytes = (uint32_t)(nh * sizeof(uint4));
+      mbar_expect_tx(bar, rbytes + lbytes + (uint32_t)nl * node_bytes);
       bulk_g2s(smem_u32(srb(b)), rec + (int64_t)h0 * 6 * kRec, rbytes, bar);
+      bulk_g2s(smem_u32(lcb(b)), ht.hex_local + h0, lbytes, bar);
     }
     const int l = threadIdx.x;
     if (l < nl) {
       snb(b)[l] = nd;
-      bulk_g2s(smem_u32(psb(b) + (int64_t)l * PN), p + (int64_t)(nd & 0x7fffffff) * per_node, node_bytes, bar);
+      bulk_g2s(smem_u32(psb(b) + (int64_t)l * PN), p + (int64_t)(nd & 0x0fffffff) * per_node, node_bytes, bar);
     }
   };
   __shared__ double sdot[kMaxRpad];
@@ -783,6 +792,7 @@ __global__ void __launch_bounds__(kBlockCM, 1) k_ebe_hex_cm(HexTiles ht, MeshVie
     const T* ps = psb(b);
     const T* sr = srb(b);
     const int* snode = snb(b);
+    const uint4* hexl = lcb(b);
     // warp-group g applies hexes 32 (g / rpad) .. +31 of case g % rpad
     const int groups = ((nh + 31) >> 5) << rshift;
     for (int gw = warp; gw < groups; gw += kBlockCM / 32) {
@@ -791,7 +801,7 @@ __global__ void __launch_bounds__(kBlockCM, 1) k_ebe_hex_cm(HexTiles ht, MeshVie
       const int hl = ((gw >> rshift) << 5) + lane;
       T hdot = 0;
       if (hl < nh) {
-        const uint4 lw = __ldg(ht.hex_local + h0 + hl);
+        const uint4 lw = hexl[hl];
         int ls[8] = {(int)(lw.x & 0xffff), (int)(lw.x >> 16), (int)(lw.y & 0xffff), (int)(lw.y >> 16),
                      (int)(lw.z & 0xffff), (int)(lw.z >> 16), (int)(lw.w & 0xffff), (int)(lw.w >> 16)};
         T P[8][3], Q[8][3];
@@ -827,8 +837,8 @@ __global__ void __launch_bounds__(kBlockCM, 1) k_ebe_hex_cm(HexTiles ht, MeshVie
       const int l = (i >> rshift) / 3, rem = i - l * per_node;
       const int kk = rem >> rshift;
       const int raw = snode[l];
-      const int64_t g = raw & 0x7fffffff;
-      const bool fixed = !dof_free(m.freemask[g], kk);
+      const int64_t g = raw & 0x0fffffff;
+      const bool fixed = !dof_free((uint8_t)((raw >> 28) & 7), kk);
       T* dst = q + g * per_node + rem;
       const T v = qs[l * PN + rem];
       if (raw < 0) {
