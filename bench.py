@@ -168,6 +168,7 @@ def ncu_traffic(kernel_tag, sources):
 
 
 EBE_SOURCES = ["paper_2409_20380_gb300/csrc/k_ebe.cu", "paper_2409_20380_gb300/csrc/fem_internal.cuh"]
+BCSR_SOURCES = ["paper_2409_20380_gb300/csrc/k_bcsr.cu"]
 
 
 def workload(args, rank):
@@ -378,7 +379,7 @@ def run_ours(args):
         inner = {"bound": "alu", "achieved": fl / (avg32 * 1e-3) / 1e12, "peak": alu32, "unit": "TFLOP/s",
                  "frac": fl / (avg32 * 1e-3) / 1e12 / alu32,
                  "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock",
-                 "traffic": ncu_traffic("ebe_hex_f32_medium16", EBE_SOURCES),
+                 "traffic": ncu_traffic("ebe_staged_f32_medium16", EBE_SOURCES) if not args.variant else None,
                  "kernel": "k_ebe_hex<float> (FP32 EBE product A p of the inner PCG, %d cases)" % rpad,
                  "avg_launch_ms": avg32, "launches": prof["ebe32_launches"], "alg_bytes_per_launch": bytes32,
                  "alg_flops_per_launch": fl, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak,
@@ -409,7 +410,8 @@ def run_ours(args):
         achieved = fl / (avg * 1e-3) / 1e12
         gbs = bytes_c / (avg * 1e-3) / 1e9
         roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"],
-                     "traffic": ncu_traffic("ebe_split_f64_medium16", EBE_SOURCES) if args.cert == 0 else None,
+                     "traffic": (ncu_traffic("ebe_split_f64_medium16", EBE_SOURCES) if args.cert == 0 else
+                                 ncu_traffic("bcsr_split_df_medium16", BCSR_SOURCES) if args.cert == 3 else None),
                      "kernel": kname + ", %d cases" % rpad, "avg_launch_ms": avg, "launches": prof["ebe64_launches"],
                      "alg_bytes_per_launch": bytes_c, "alg_flops_per_launch": fl, "hbm_gbs": gbs,
                      "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak,
