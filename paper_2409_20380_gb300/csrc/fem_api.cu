@@ -620,7 +620,8 @@ struct Group {
   int* acc_status = nullptr;      // [ncase] worst status since then
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  cudaStream_t gs[4] = {nullptr, nullptr, nullptr, nullptr};   // capture streams (top level and bodies)
+  cudaStream_t gs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // capture streams (top level, bodies, fork)
+  cudaEvent_t gev[2] = {nullptr, nullptr};                            // fork / join of the captured step
   int* h_pin = nullptr;           // pinned: [0] = 1 (use_ext flag), [1] = step counter to upload
   int ctl_it = -1;                // step counter the device record holds (-1: unknown, upload first)
   bool graph_failed = false;      // capture or instantiation failed: eager steps from now on
@@ -643,6 +644,8 @@ struct Group {
     if (graph) cudaGraphDestroy(graph);
     for (auto& st : gs)
       if (st) cudaStreamDestroy(st);
+    for (auto& ev : gev)
+      if (ev) cudaEventDestroy(ev);
     dfree(ctl); dfree(acc_iters); dfree(acc_relres); dfree(acc_status);
     if (h_pin) cudaFreeHost(h_pin);
     if (h_slots) cudaFreeHost(h_slots);
@@ -1069,16 +1072,21 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   const int ce = std::max(1, o.check_every);
   cudaStream_t s = g->gs[0], s2 = g->gs[1], s3 = g->gs[2], s4 = g->gs[3];
   const long long n_fixed = 6 + (dd ? 6 : 0), n_pass = 4, n_if = 4, n_inner = 3LL * ce + 1;
-  // 1. step record, initial guess
+  // 1. step record; the per-region Gram solves (few warps per SM) run beside the Adams-Bashforth
+  // increment and the right-hand side, which do not depend on them
   GE(launch_step_begin(ctl, dd ? g->n_slots : 0, o.s_max, dt, dd ? 1 : 0, n_fixed, s));
-  GE(launch_ab4_ring(g->n, dt, V, ctl, g->du_ab, s));
-  GE(cudaMemcpyAsync(g->guess, g->du_ab, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
-  if (dd) {
-    GE(launch_pred_solve(pv, nullptr, 0, 0, o.tau, s, ctl));
-    GE(launch_pred_combine(pv, nullptr, 0, g->guess, s, ctl));
-  }
+  cudaStream_t sf = g->gs[4];
+  GE(cudaEventRecord(g->gev[0], s));
+  GE(cudaStreamWaitEvent(sf, g->gev[0], 0));
+  GE(launch_ab4_ring(g->n, dt, V, ctl, g->du_ab, sf));
+  GE(cudaMemcpyAsync(g->guess, g->du_ab, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, sf));
   // 2. right-hand side from the recurrences
-  GE(launch_rhs_incr(mv, rpad, dt, m->tp.a0, m->tp.a1, g->Ma, g->Mv, g->Kv, g->Ku, g->b, g->src, g->ext, 0.0, s, ctl));
+  GE(launch_rhs_incr(mv, rpad, dt, m->tp.a0, m->tp.a1, g->Ma, g->Mv, g->Kv, g->Ku, g->b, g->src, g->ext, 0.0, sf,
+                     ctl));
+  GE(cudaEventRecord(g->gev[1], sf));
+  if (dd) GE(launch_pred_solve(pv, nullptr, 0, 0, o.tau, s, ctl));
+  GE(cudaStreamWaitEvent(s, g->gev[1], 0));
+  if (dd) GE(launch_pred_combine(pv, nullptr, 0, g->guess, s, ctl));
   // 3. residual of the guess
   const float* qy = nullptr;
   if (dd) {
@@ -1205,14 +1213,16 @@ static fem_status group_graph_build(fem_batch* bt, Group* g) {
     CU(cudaMemsetAsync(g->acc_relres, 0, sizeof(double) * g->ncase, bt->s));
     CU(cudaMemsetAsync(g->acc_status, 0, sizeof(int) * g->ncase, bt->s));
     for (auto& st : g->gs) CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (auto& ev : g->gev) CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     CU(cudaStreamSynchronize(bt->s));
   }
   Prof* saved = g->ws->prof;
   g->ws->prof = nullptr;
   cudaError_t e = cudaStreamBeginCapture(g->gs[0], cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) e = capture_step(bt, g);
-  // end every capture still open (an error leaves inner ones open), keep the top-level graph
-  for (int k = 3; k >= 1; --k) {
+  // after an error, end the nested body captures still open (streams 1-3 start their own captures; stream 4
+  // only joins the top-level one, which ends with it)
+  for (int k = 3; e != cudaSuccess && k >= 1; --k) {
     cudaStreamCaptureStatus cs;
     if (cudaStreamIsCapturing(g->gs[k], &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
       cudaGraph_t t = nullptr;

@@ -333,6 +333,48 @@ namespace fem {
 
 __device__ __forceinline__ bool dof_free(uint8_t fm, int k) { return (fm >> k) & 1; }
 
+// Conversions between FP64 and double-float (hi, lo) FP32 pairs by integer bit operations.  GB300 executes
+// double <-> float conversions on its narrow FP64 pipe; these use the integer pipe instead.
+//   d2df: hi = x truncated to 24 significant bits, lo = the remainder truncated to 24 bits, so that
+//         hi + lo = x to 2^-47 relative; |x| < 2^-126 maps to (0, 0); infinities and NaN keep the slow path.
+//   f2d:  the exact FP64 value of a normal FP32 number; FP32 subnormals (|f| < 2^-126) map to 0.
+__device__ __forceinline__ float2 d2df(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0x7ff) return make_float2((float)x, 0.0f);
+  const int ef = e - 1023 + 127;
+  if (ef <= 0) return make_float2(0.0f, 0.0f);
+  if (ef >= 255) return make_float2((float)x, 0.0f);
+  const uint64_t m = b & 0xFFFFFFFFFFFFFull;
+  const float hi = __uint_as_float(sign | ((uint32_t)ef << 23) | (uint32_t)(m >> 29));
+  const uint32_t rem = (uint32_t)(m & 0x1FFFFFFFull);   // lo = rem * 2^(e - 1075)
+  if (rem == 0u) return make_float2(hi, 0.0f);
+  const int lz = __clz(rem);
+  const int el = e - 1075 + (31 - lz) + 127;
+  if (el <= 0) return make_float2(hi, 0.0f);
+  const uint32_t mant = (uint32_t)((((uint64_t)rem << (lz + 1)) & 0xFFFFFFFFull) >> 9);
+  return make_float2(hi, __uint_as_float(sign | ((uint32_t)el << 23) | mant));
+}
+// FP64 -> FP32 by truncation to 24 significant bits (integer pipe); |x| < 2^-126 maps to 0.
+__device__ __forceinline__ float d2f(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const int ef = e - 1023 + 127;
+  if (e == 0x7ff || ef >= 255) return (float)x;
+  if (ef <= 0) return 0.0f;
+  return __uint_as_float(((uint32_t)(b >> 32) & 0x80000000u) | ((uint32_t)ef << 23) |
+                         (uint32_t)((b & 0xFFFFFFFFFFFFFull) >> 29));
+}
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  if (e == 0xffu) return (double)f;
+  return __longlong_as_double((long long)(((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                                          ((uint64_t)(u & 0x7fffffu) << 29)));
+}
+
 // Relative reduction asked of the next inner FP32 solve: just enough for one refinement pass to reach the
 // FP64 tolerance (a tenth of tol / current relative residual), but no finer than `floor` (what FP32 can
 // deliver) and at least a halving.

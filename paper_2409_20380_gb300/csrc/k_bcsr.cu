@@ -52,12 +52,10 @@ __global__ void k_bcsr_assemble(MeshView m, const int32_t* __restrict__ row_ptr,
   }
 }
 
-// FP64 values -> (hi, lo) FP32 pairs with hi + lo = v to 2^-48 relative.
+// FP64 values -> (hi, lo) FP32 pairs with hi + lo = v to 2^-47 relative (integer-pipe split).
 __global__ void k_to_df(int64_t n, const double* __restrict__ v, float2* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double x = v[i];
-    const float hi = (float)x;
-    out[i] = make_float2(hi, (float)(x - (double)hi));
+    out[i] = d2df(v[i]);
   }
 }
 
@@ -108,8 +106,8 @@ __global__ void __launch_bounds__(256) k_bcsr_split_df(int64_t N, int rpad, int 
     for (int i = 0; i < 3; ++i) {
       const int64_t id = (n * 3 + i) * rpad + c;
       const bool fr = dof_free(f, i);
-      qM[id] = fr ? (double)mh[i] + (double)ml[i] : 0.0;
-      qK[id] = fr ? (double)kh[i] + (double)kl[i] : 0.0;
+      qM[id] = fr ? f2d(mh[i]) + f2d(ml[i]) : 0.0;
+      qK[id] = fr ? f2d(kh[i]) + f2d(kl[i]) : 0.0;
     }
   }
 }

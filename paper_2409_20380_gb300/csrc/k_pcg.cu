@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_outer_resid(MeshView m, int rp
     for (int k = 0; k < 3; ++k) {
       const int64_t id = (n * 3 + k) * rpad + c;
       const double v = dof_free(f, k) ? b[id] - q[id] : 0.0;
-      r32[id] = (float)v;
+      r32[id] = d2f(v);
       rr += v * v;
     }
   }
@@ -267,7 +267,7 @@ __global__ void k_refine(int64_t n_items, int ncase, double* __restrict__ x, con
       outer[threadIdx.x].status = inner[threadIdx.x].status;
   }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += (double)d[i];
+    x[i] += f2d(d[i]);
 }
 
 // x = 0 on Dirichlet DOFs and for cases whose right-hand side is zero (||b|| = 0 gives x = 0).

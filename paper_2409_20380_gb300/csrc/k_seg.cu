@@ -221,9 +221,9 @@ __global__ void k_r0_seg(MeshView m, double h, const double* __restrict__ b, con
         const double bv = b[id];
         if (dof_free(f, k)) {
           val = bv - h * (-9.0 * Av4[id] + 37.0 * Av3[id] - 59.0 * Av2[id] + 55.0 * Av1[id]);
-          if (qy) val -= (double)qy[id];
+          if (qy) val -= f2d(qy[id]);
         }
-        r32[id] = (float)val;
+        r32[id] = d2f(val);
         v[0] += bv * bv;
         v[1] += val * val;
       }
@@ -268,7 +268,7 @@ __global__ void k_cert_seg(MeshView m, double cM, double cK, const double* __res
       for (int k = 0; k < 3; ++k) {
         const int64_t id = n * 3 + k;
         const double val = dof_free(f, k) ? b[id] - (cM * qM[id] + cK * qK[id]) : 0.0;
-        r32[id] = (float)val;
+        r32[id] = d2f(val);
         v[0] += val * val;
       }
     }

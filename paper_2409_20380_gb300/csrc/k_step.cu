@@ -9,10 +9,7 @@ namespace fem {
 // same 8 bytes as FP64, read and combined on the FP32 pipe).
 __device__ __forceinline__ void store_snap(double* p, double v) { *p = v; }
 __device__ __forceinline__ void store_snap(float* p, double v) { *p = (float)v; }
-__device__ __forceinline__ void store_snap(float2* p, double v) {
-  const float hi = (float)v;
-  *p = make_float2(hi, (float)(v - (double)hi));
-}
+__device__ __forceinline__ void store_snap(float2* p, double v) { *p = d2df(v); }
 
 
 static int vec_grid(int64_t items) {
@@ -131,7 +128,7 @@ template <> struct PredAcc<float2> {  // double-float: exact products by FMA, ex
     s = t;
     l = __fadd_rn(l, __fadd_rn(err, e));
   }
-  __device__ __forceinline__ double get() const { return (double)s + (double)l; }
+  __device__ __forceinline__ double get() const { return f2d(s) + f2d(l); }
 };
 template <> struct PredAcc<float> {   // compensated FP32 summation of FP32 products
   float s = 0.f, comp = 0.f;
@@ -166,7 +163,7 @@ template <> struct RedVal<float2> {
   __device__ __forceinline__ RedVal shfl_xor(int off) const {
     return RedVal{__shfl_xor_sync(0xffffffffu, h, off), __shfl_xor_sync(0xffffffffu, l, off)};
   }
-  __device__ __forceinline__ double get() const { return (double)h + (double)l; }
+  __device__ __forceinline__ double get() const { return f2d(h) + f2d(l); }
 };
 
 // Region R is split into p.n_chunks node ranges; block (R, k, g) accumulates, for each valid slot j of its
@@ -318,10 +315,7 @@ template <> struct CombAcc<float> {
 template <> struct CombAcc<float2> {
   typedef float2 W;
   float h = 0.f, l = 0.f;
-  __device__ __forceinline__ static W wconv(double w) {
-    const float hi = (float)w;
-    return make_float2(hi, (float)(w - (double)hi));
-  }
+  __device__ __forceinline__ static W wconv(double w) { return d2df(w); }
   __device__ __forceinline__ void add(W w, float2 y) {
     const float p = __fmul_rn(w.x, y.x);
     float e = __fmaf_rn(w.x, y.x, -p);
@@ -340,7 +334,7 @@ template <> struct CombAcc<float2> {
     h = t;
     l = __fadd_rn(__fadd_rn(l, o.l), err);
   }
-  __device__ __forceinline__ double get() const { return (double)h + (double)l; }
+  __device__ __forceinline__ double get() const { return f2d(h) + f2d(l); }
 };
 
 // y_out += Y w over the region's node range: the coefficients [a][case] and slot offsets in shared memory.
@@ -479,7 +473,7 @@ __global__ void k_rhs_incr(MeshView m, int rpad, int rshift, double c_mv, double
 __global__ void k_corr_f32(int64_t n, const double* __restrict__ guess, const double* __restrict__ du_ab,
                            float* __restrict__ y32) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y32[i] = (float)(guess[i] - du_ab[i]);
+    y32[i] = d2f(guess[i] - du_ab[i]);
 }
 
 // Residual of the guess without an FP64 product:  r0 = b - A du_AB - A y  with
@@ -509,9 +503,9 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_r0(MeshView m, int rpad, int r
       const double bv = b[id];
       if (dof_free(f, k)) {
         v = bv - h * (-9.0 * Av4[id] + 37.0 * Av3[id] - 59.0 * Av2[id] + 55.0 * Av1[id]);
-        if (qy) v -= (double)qy[id];
+        if (qy) v -= f2d(qy[id]);
       }
-      r32[id] = (float)v;
+      r32[id] = d2f(v);
       bb += bv * bv;
       rr += v * v;
     }
@@ -560,7 +554,7 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_cert(MeshView m, int rpad, int
     for (int k = 0; k < 3; ++k) {
       const int64_t id = (n * 3 + k) * rpad + c;
       const double v = dof_free(f, k) ? b[id] - (cM * qM[id] + cK * qK[id]) : 0.0;
-      r32[id] = (float)v;
+      r32[id] = d2f(v);
       rr += v * v;
     }
   }

@@ -67,3 +67,37 @@ def test_split_product_rejects_bad_mode(torch_dev):
         assert ei.value.status == fem.FEM_ERR_ARG
     finally:
         fem.fem_mesh_destroy(h)
+
+
+def test_split_product_double_float_wide_range(torch_dev):
+    """Inputs spanning 1e-15 .. 1e10 (the double-float split is done by integer bit operations): the
+    double-float assembled product matches the FP64 one to 1e-12 of the row's sum of absolute terms.  (FP32
+    pairs carry 48 bits down to about 1e-31; values far below that lose relative accuracy.)"""
+    torch = torch_dev
+    m = small_mesh(6, 5, 4, perturb=0.1)
+    tp = wl.TimeParams()
+    sysm, _ = oracle.build_system(m, tp)
+    rng = np.random.default_rng(11)
+    r = 4
+    ps = []
+    for c in range(r):
+        v = rng.standard_normal(3 * m.n_nodes) * 10.0 ** rng.uniform(-15, 10, 3 * m.n_nodes)
+        v[m.fixed_dof == 1] = 0.0
+        ps.append(v)
+    h = fem.fem_mesh_create(m, tp)
+    try:
+        p = torch.tensor(from_cases(ps, m.n_nodes, r), device="cuda")
+        out = {}
+        for mode in (2, 3):
+            qM, qK = torch.empty_like(p), torch.empty_like(p)
+            fem.fem_mesh_split_product(h, mode, p, qM, qK, r)
+            out[mode] = (to_cases(qM.cpu().numpy(), m.n_nodes, r), to_cases(qK.cpu().numpy(), m.n_nodes, r))
+        absK = abs(sysm.K)
+        absM = abs(sysm.M)
+        for c in range(r):
+            scaleK = absK @ np.abs(ps[c]) + 1e-300
+            scaleM = absM @ np.abs(ps[c]) + 1e-300
+            assert np.all(np.abs(out[3][1][c] - out[2][1][c]) <= 1e-12 * scaleK)
+            assert np.all(np.abs(out[3][0][c] - out[2][0][c]) <= 1e-12 * scaleM)
+    finally:
+        fem.fem_mesh_destroy(h)
