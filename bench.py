@@ -60,13 +60,16 @@ def parse():
     ap.add_argument("--cert", type=int, default=3,
                     help="certification product: 0 EBE FP64, 1 EBE double-float, 2 assembled FP64, "
                          "3 assembled double-float")
+    ap.add_argument("--snapshot-format", type=int, default=2,
+                    help="predictor snapshot storage: 0 FP64, 1 FP32, 2 double-float, 3 FP32 + BF16 residual")
     ap.add_argument("--profile-steps", type=int, default=40,
                     help="steps after the timed region timed per kernel class with CUDA events (eager)")
     ap.add_argument("--kernel", default=None, choices=["ebe"],
                     help="time one kernel alone (EBE product) instead of the full step")
     ap.add_argument("--kernel-precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=0,
-                    help="EBE variant: 0 auto, 1 generic, 2 tiled hex, 3 staged tiles, 4 case-major staged tiles")
+                    help="EBE variant: 0 auto, 1 generic, 2 tiled hex, 3 staged tiles, 4 case-major staged tiles, "
+                         "5/6 packed staged tiles (two / one block per SM)")
     ap.add_argument("--hex-per-tile", type=int, default=0)
     ap.add_argument("--uneven", action="store_true",
                     help="batched uneven meshes: --meshes cases on meshes of different sizes fused into one system")
@@ -265,7 +268,7 @@ def run_ours(args):
 
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER if args.precision == "mixed" else fem.FEM_FP64,
                                 predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
-                                s_max=args.s_max, snapshot_format=2, tol=1e-8, cert_df=args.cert,
+                                s_max=args.s_max, snapshot_format=args.snapshot_format, tol=1e-8, cert_df=args.cert,
                                 use_graph=0 if args.no_graph else 1)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
@@ -379,8 +382,9 @@ def run_ours(args):
         inner = {"bound": "alu", "achieved": fl / (avg32 * 1e-3) / 1e12, "peak": alu32, "unit": "TFLOP/s",
                  "frac": fl / (avg32 * 1e-3) / 1e12 / alu32,
                  "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock",
-                 "traffic": ncu_traffic("ebe_staged_f32_medium16", EBE_SOURCES) if not args.variant else None,
-                 "kernel": "k_ebe_hex<float> (FP32 EBE product A p of the inner PCG, %d cases)" % rpad,
+                 "traffic": ncu_traffic("ebe_packed_f32_medium16", EBE_SOURCES) if not args.variant else None,
+                 "kernel": ("k_ebe_hex_staged<float,1,0,1> (FP32 EBE product A p of the inner PCG, TMA-staged "
+                            "hex tiles, two cases per thread; %d cases)" % rpad),
                  "avg_launch_ms": avg32, "launches": prof["ebe32_launches"], "alg_bytes_per_launch": bytes32,
                  "alg_flops_per_launch": fl, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak,
                  "hbm_peak_kind": peak_kind, "ms_per_step": prof["ebe32_ms"] / max(prof["steps"], 1)}
@@ -521,7 +525,7 @@ def run_learned(args):
     fem.fem_mesh_set_regions(h, regions)
     K = args.case_steps
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
-                                tol=1e-8, snapshot_format=2, cert_df=args.cert)
+                                tol=1e-8, snapshot_format=args.snapshot_format, cert_df=args.cert)
 
     def run(srcs, net=None, xs=None, ts=None, window=(250, 500)):
         """Cases in batches of --cases; returns (rows collected, case-steps/s over the window, iterations,
@@ -622,7 +626,7 @@ def run_uneven(args):
     dims = wl.config3_dims(args.meshes)
     handles, n_el, n_nd = [], 0, 0
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
-                                tol=1e-8, snapshot_format=2, fuse_meshes=0 if args.no_fuse else 1, cert_df=args.cert,
+                                tol=1e-8, snapshot_format=args.snapshot_format, fuse_meshes=0 if args.no_fuse else 1, cert_df=args.cert,
                                 use_graph=0 if args.no_graph else 1)
     bt = fem.fem_batch_create(opts)
     for i, d in enumerate(dims):

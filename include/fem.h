@@ -92,7 +92,9 @@ typedef struct {
   double tau;            /* predictor column-drop threshold (relative orthogonalised norm) */
   int snapshot_format;   /* predictor snapshot storage: 0 = FP64; 1 = FP32 (half the memory; the prediction
                             loses the small orthogonal components FP32 rounds away); 2 = double-float pairs
-                            (hi, lo FP32: FP64 size, 48-bit significand, arithmetic on the FP32 pipe) */
+                            (hi, lo FP32: FP64 size, 48-bit significand, arithmetic on the FP32 pipe);
+                            3 = FP32 value and its residual rounded to BF16 (6 bytes, about 32-bit
+                            significand, read as double-float pairs) */
   int check_every;       /* CG iterations between host-side convergence polls (>= 1) */
   int refresh_every;     /* FEM_FP32_INNER steps: every this many steps the products K u, M v, K v, M a and
                             A v^{it-3..it} that fem_step keeps by recurrence are recomputed directly
@@ -145,10 +147,13 @@ fem_status fem_mesh_destroy(fem_mesh* m);
  * kernel (available when the elements come in groups of six tets splitting a hexahedron with the Kuhn
  * topology, which fem_mesh_create detects), 3 = the tiled hex kernel with each tile's node values and
  * element records staged in shared memory first by bulk asynchronous copies (double-buffered), 4 = as 3
- * with warps of one case each, so cases whose inner solve has converged are skipped (needs 3 x n_rhs x
- * element size to be a multiple of 16 bytes; otherwise 3, then 2, then 1 is used).  hex_per_tile: 0 = automatic (largest tile whose
- * shared memory fits), or 64/128/256/512 hexes per tile.  Errors: FEM_ERR_ARG for other values or variants
- * 2-4 on a mesh without hex patches.
+ * with warps of one case each, so cases whose inner solve has converged are skipped, 5 = as 3 with each
+ * thread applying its hex to two cases at once by paired FP32 operations (FP32 products of groups with
+ * n_rhs >= 4; FP64 products and fused groups use 3), registers capped for two blocks per SM, 6 = as 5 with
+ * one block per SM (variants 3-6 need 3 x n_rhs x element size to be a multiple of 16 bytes; otherwise 3,
+ * then 2, then 1 is used).  hex_per_tile: 0 = automatic (largest tile whose shared memory fits), or
+ * 64/128/256/512 hexes per tile.  Errors: FEM_ERR_ARG for other values or variants 2-6 on a mesh without
+ * hex patches.
  */
 fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile);
 
@@ -156,8 +161,8 @@ fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile);
  * Autotuner: times each EBE implementation that applies to the mesh on the inner solve's product
  * (q = A p with the fused p^T A p, n_rhs cases; FEM_FP32_INNER = FP32 product, FEM_FP64 = FP64 product):
  * the generic element kernel, the tiled hex kernel with 64/128/256/512 hexes per tile, the staged tiled
- * kernel with 64/128/256 and the case-major staged kernel with 64/128 hexes per tile, where their shared
- * memory fits.  The fastest is kept for that precision and n_rhs and used whenever
+ * kernel with 64/128/256, the case-major staged kernel with 64/128 and the packed staged kernels with
+ * 64/128/256 hexes per tile, where their shared memory fits.  The fastest is kept for that precision and n_rhs and used whenever
  * fem_mesh_tune is left at automatic (0, 0).  Outputs (nullable): the chosen variant and tile size, and its
  * time per product in ms.  Runs on `stream` and synchronises it; allocates two temporary vectors.
  */

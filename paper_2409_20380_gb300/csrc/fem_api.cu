@@ -51,6 +51,9 @@ static void dfree(T*& p) {
   p = nullptr;
 }
 
+// Bytes of one stored snapshot value per snapshot_format: FP64, FP32, double-float pair, FP32 + BF16.
+static size_t snap_bytes(int fmt) { return fmt == 1 ? 4 : fmt == 3 ? 6 : 8; }
+
 static bool pow2_rhs(int r) { return r == 1 || r == 2 || r == 4 || r == 8 || r == 16 || r == 32; }
 
 static int next_pow2(int r) {
@@ -253,7 +256,7 @@ struct fem_mesh {
   static constexpr int kNTile = 4;
   HexTiles tiles[kNTile];          // hex_per_tile 64, 128, 256, 512
   std::vector<void*> tile_bufs;
-  int ebe_variant = 0;             // 0 auto, 1 generic element kernel, 2 tiled hex kernel
+  int ebe_variant = 0;             // 0 auto, 1 generic, 2 tiled hex, 3 staged, 4 case-major, 5/6 packed staged
   int hex_per_tile = 0;            // 0 auto
   // autotuned choice per (FP32 / FP64 product, log2 of the case count); variant 0 = not tuned
   struct Tuned {
@@ -356,7 +359,7 @@ struct fem_mesh {
   // Tiling for a product on T with rpad cases: the largest tile whose accumulator fits the budget.
   // EBE implementation of a product on elements of elem_bytes with rpad cases: an explicit fem_mesh_tune
   // setting wins, else the autotuned choice for this precision and case count, else the staged tiled hex
-  // kernel when the mesh has hex patches.
+  // kernel (two cases per thread for FP32 products) when the mesh has hex patches.
   void resolve(size_t elem_bytes, int rpad, int* variant, int* hpt) const {
     *variant = ebe_variant, *hpt = hex_per_tile;
     if (*variant == 0 && *hpt == 0) {
@@ -365,7 +368,7 @@ struct fem_mesh {
       const Tuned& t = tuned[elem_bytes == 4 ? 0 : 1][lg];
       if (t.variant) *variant = t.variant, *hpt = t.hpt;
     }
-    if (*variant == 0) *variant = hex ? 3 : 1;       // staged tiles where they apply (else tiled, else generic)
+    if (*variant == 0) *variant = hex ? 5 : 1;       // packed staged tiles where they apply (else 3, 2, 1)
     if (!hex) *variant = 1;
   }
   // Tiling for the resolved variant: the largest tile whose shared memory fits (or the requested size).
@@ -377,9 +380,9 @@ struct fem_mesh {
       if (t.n_tiles == 0) continue;
       if (hpt && t.hex_per_tile != hpt) continue;
       size_t need, budget;
-      if (variant == 3) {
+      if (variant == 3 || variant == 5 || variant == 6) {   // (6: one block per SM)
         need = elem_bytes == 4 ? ebe_hex_staged_smem<float>(t, view(), rpad) : ebe_hex_staged_smem<double>(t, view(), rpad);
-        budget = 110 * 1024;
+        budget = variant == 6 ? 220 * 1024 : 110 * 1024;
       } else if (variant == 4) {   // one block per SM
         need = elem_bytes == 4 ? ebe_hex_cm_smem<float>(t, view(), rpad) : ebe_hex_cm_smem<double>(t, view(), rpad);
         budget = 220 * 1024;
@@ -417,9 +420,10 @@ static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, do
     if (t) return launch_ebe_hex_cm<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
     v = 3, h = 0;
   }
-  if (v == 3) {   // staged copies need 16-byte rows (3 x rpad values) and a 16-byte aligned input
-    const HexTiles* t = (reinterpret_cast<uintptr_t>(p) & 15) == 0 ? m->tiles_for(sizeof(T), rpad, 3, h) : nullptr;
-    if (t) return launch_ebe_hex_staged<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
+  if ((v == 5 || v == 6) && (sizeof(T) != 4 || m->seg || rpad < 4)) v = 3;   // packed pairs: FP32, r >= 4 lanes
+  if (v == 3 || v == 5 || v == 6) {   // staged copies need 16-byte rows (3 x rpad values), 16-byte aligned input
+    const HexTiles* t = (reinterpret_cast<uintptr_t>(p) & 15) == 0 ? m->tiles_for(sizeof(T), rpad, v, h) : nullptr;
+    if (t) return launch_ebe_hex_staged<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s, v == 3 ? 0 : v - 4);
     v = 2, h = 0;
   }
   if (const HexTiles* t = m->tiles_for(sizeof(T), rpad, v, h))
@@ -430,6 +434,10 @@ static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, do
 // ------------------------------------------------------------------------------------------------------
 // PCG drivers.
 // ------------------------------------------------------------------------------------------------------
+// Deferred x updates (launch_dir_defer) apply to the FP32 inner solves of multi-RHS groups; the caller then
+// completes x with launch_refine_pending.
+static bool defer_inner(const MeshView& mv) { return mv.seg == nullptr; }
+
 template <typename T>
 static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T* z, T* p, T* q, CgCase* sc,
                            bool zero_guess, bool true_check, double tol, int maxit, const CgCase* gate,
@@ -439,6 +447,7 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
   const Reducer red = w->red();
   const int ebe_cls = sizeof(T) == 4 ? P_EBE32 : P_EBE64;
   const bool sg = mv.seg != nullptr;
+  const bool defer = sizeof(T) == 4 && !true_check && defer_inner(mv);
   if (sg) {
     CU(launch_norm_b_seg<T>(mv, b, red, sc, gate, tol, s));
   } else {
@@ -468,7 +477,9 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
   for (;;) {
     for (int k = 0; k < check_every; ++k) {
       int p0 = w->pbeg(P_VEC, s);
-      if (sg) {
+      if (defer) {
+        if constexpr (sizeof(T) == 4) CU(launch_dir_defer<float>(mv, rpad, r, p, x, sc, w->n_active, s));
+      } else if (sg) {
         CU(launch_dir_seg<T>(mv, z, p, sc, w->n_active, s));
       } else {
         CU(launch_dir_gated<T>(mv, rpad, z, p, sc, w->n_active, s));
@@ -478,7 +489,9 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
       CU(ebe_product<T>(m, rpad, p, q, m->cM, m->cK, &red, sc, nullptr, w->n_active, s));
       w->pend(p1, s);
       int p2 = w->pbeg(P_VEC, s);
-      if (sg) {
+      if (defer) {
+        if constexpr (sizeof(T) == 4) CU(launch_update_defer<float>(mv, rpad, q, r, red, sc, w->n_active, maxit, s));
+      } else if (sg) {
         CU(launch_update_seg<T>(mv, p, q, x, r, z, red, sc, w->n_active, maxit, s));
       } else {
         CU(launch_update<T>(mv, rpad, p, q, x, r, z, red, sc, w->n_active, tol, maxit, s));
@@ -539,7 +552,11 @@ static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double
     }
     CHK(pcg_core<float>(m, w, w->r32, w->x32, w->rr32, w->z32, w->p32, w->q32, w->sc, true, false, o.inner_tol,
                         o.maxit - used, w->outer, o.check_every, s));
-    CU(launch_refine_counts(mv, rpad, rpad, x, w->x32, w->outer, w->sc, s));
+    if (defer_inner(mv)) {
+      CU(launch_refine_pending(mv, rpad, rpad, x, w->x32, w->p32, w->outer, w->sc, s));
+    } else {
+      CU(launch_refine_counts(mv, rpad, rpad, x, w->x32, w->outer, w->sc, s));
+    }
     w->count();
   }
   w->resolve();
@@ -568,7 +585,7 @@ static fem_status check_opts(const fem_opts* o) {
   if (o->predictor != FEM_PRED_AB4 && o->predictor != FEM_PRED_DD) return fail(FEM_ERR_ARG, "unknown predictor");
   if (o->s_max < 1 || o->s_max > kMaxSlots - 1) return fail(FEM_ERR_ARG, "s_max must be in [1, 32]");
   if (o->cert_df < 0 || o->cert_df > 3) return fail(FEM_ERR_ARG, "cert_df must be 0, 1, 2 or 3");
-  if (o->snapshot_format < 0 || o->snapshot_format > 2) return fail(FEM_ERR_ARG, "snapshot_format must be 0, 1 or 2");
+  if (o->snapshot_format < 0 || o->snapshot_format > 3) return fail(FEM_ERR_ARG, "snapshot_format must be 0 .. 3");
   return FEM_OK;
 }
 
@@ -588,6 +605,7 @@ struct Group {
   double *b = nullptr, *x = nullptr, *du_ab = nullptr, *m_in = nullptr, *k_in = nullptr, *guess = nullptr;
   void* ring = nullptr;
   int n_slots = 0;
+  int64_t snap_stride = 0;   // values per ring slot: n rounded up to a multiple of 8
   int n_regions = 0;            // regions the Gram buffers were sized for
   double* gram = nullptr;
   double* wcoef = nullptr;
@@ -704,14 +722,15 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
   }
   if (bt->opts.predictor == FEM_PRED_DD) {
     g->n_slots = bt->opts.s_max + 1;
-    const size_t esz = bt->opts.snapshot_format == 1 ? 4 : 8;
-    cudaError_t e = cudaMalloc(&g->ring, esz * n * g->n_slots);
+    g->snap_stride = (n + 7) & ~(int64_t)7;
+    const size_t ring_bytes = snap_bytes(bt->opts.snapshot_format) * (size_t)g->snap_stride * g->n_slots;
+    cudaError_t e = cudaMalloc(&g->ring, ring_bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       g->ring = nullptr;
       return fail(FEM_ERR_OOM, "snapshot ring allocation failed");
     }
-    CU(cudaMemsetAsync(g->ring, 0, esz * n * g->n_slots, s));
+    CU(cudaMemsetAsync(g->ring, 0, ring_bytes, s));
     g->n_regions = m->n_regions;
     const int R = std::max(1, m->n_regions);
     CHK(dalloc(&g->gram, (size_t)R * g->rpad * kMaxSlots * kMaxSlots));
@@ -748,7 +767,7 @@ static PredView pred_view(const fem_batch* bt, const Group* g) {
   p.reg_hi = g->mesh->reg_hi;
   p.rpad = g->rpad;
   p.n_slots = g->n_slots;
-  p.slot_stride = g->n;
+  p.slot_stride = g->snap_stride;
   p.ring = g->ring;
   p.fmt = bt->opts.snapshot_format;
   p.gram = g->gram;
@@ -948,7 +967,11 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
       } else {
         CHK(pcg_core<float>(m, w, w->r32, w->x32, w->rr32, w->z32, w->p32, w->q32, w->sc, true, false, o.inner_tol,
                             o.maxit - used, w->outer, o.check_every, s));
-        CU(launch_refine_counts(mv, g->rpad, g->ncase, g->x, w->x32, w->outer, w->sc, s));
+        if (defer_inner(mv)) {
+          CU(launch_refine_pending(mv, g->rpad, g->ncase, g->x, w->x32, w->p32, w->outer, w->sc, s));
+        } else {
+          CU(launch_refine_counts(mv, g->rpad, g->ncase, g->x, w->x32, w->outer, w->sc, s));
+        }
         w->count();
       }
     } else if (pass > 0) {
@@ -973,11 +996,11 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   void* e_push = nullptr;
   const bool dd = o.predictor == FEM_PRED_DD && g->n_regions > 0;
   if (dd) {
-    const size_t esz = o.snapshot_format == 1 ? 4 : 8;
-    e_push = (char*)g->ring + esz * (size_t)g->n * slot_of(g, it);
+    e_push = (char*)g->ring + snap_bytes(o.snapshot_format) * (size_t)g->snap_stride * slot_of(g, it);
   }
   CU(launch_newmark_incr(g->n, dt, m->cM, m->cK, g->x, g->du_ab, g->qM, g->qK, g->u, vslot(it - 1), g->a, vslot(it),
-                         g->Ku, g->Mv, g->Kv, g->Ma, aslot(it), e_push, o.snapshot_format, s));
+                         g->Ku, g->Mv, g->Kv, g->Ma, aslot(it), e_push, o.snapshot_format, s, Ring4{}, Ring4{},
+                         nullptr, g->snap_stride));
   w->count();
   if (dd) {
     uint64_t mask = 0;
@@ -1159,20 +1182,23 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
         if (sg) {
           GE(launch_dir_seg<float>(mv, w->z32, w->p32, w->sc, w->n_active, s4));
         } else {
-          GE(launch_dir_gated<float>(mv, rpad, w->z32, w->p32, w->sc, w->n_active, s4));
+          GE(launch_dir_defer<float>(mv, rpad, w->rr32, w->p32, w->x32, w->sc, w->n_active, s4));
         }
         GE(ebe_product<float>(m, rpad, w->p32, w->q32, m->cM, m->cK, &red, w->sc, nullptr, w->n_active, s4));
         if (sg) {
           GE(launch_update_seg<float>(mv, w->p32, w->q32, w->x32, w->rr32, w->z32, red, w->sc, w->n_active, o.maxit,
                                       s4));
         } else {
-          GE(launch_update<float>(mv, rpad, w->p32, w->q32, w->x32, w->rr32, w->z32, red, w->sc, w->n_active,
-                                  o.inner_tol, o.maxit, s4));
+          GE(launch_update_defer<float>(mv, rpad, w->q32, w->rr32, red, w->sc, w->n_active, o.maxit, s4));
         }
       }
       GE(launch_inner_cond(w->n_active, ctl, h_in, ce, o.maxit + 64 * ce, n_inner, s4));
       GE(cudaStreamEndCapture(s4, &tmp));
-      GE(launch_refine_counts(mv, rpad, g->ncase, g->x, w->x32, w->outer, w->sc, s3));
+      if (sg) {
+        GE(launch_refine_counts(mv, rpad, g->ncase, g->x, w->x32, w->outer, w->sc, s3));
+      } else {
+        GE(launch_refine_pending(mv, rpad, g->ncase, g->x, w->x32, w->p32, w->outer, w->sc, s3));
+      }
     }
     GE(cudaStreamEndCapture(s3, &tmp));
     // FP64 certification: split products of the increment, true residual, per-case stop test
@@ -1190,7 +1216,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   // 5. Newmark update, recurrences, snapshot push, Gram row of the new snapshot, statistics
   GE(launch_newmark_incr(g->n, dt, m->cM, m->cK, g->x, g->du_ab, g->qM, g->qK, g->u, nullptr, g->a, nullptr, g->Ku,
                          g->Mv, g->Kv, g->Ma, nullptr, nullptr, o.snapshot_format, s, V, AV, dd ? g->ring : nullptr,
-                         g->n, ctl));
+                         g->snap_stride, ctl));
   if (dd) GE(launch_pred_dots(pv, 0, 0, s, ctl));
   GE(launch_step_end(w->outer, g->ncase, g->acc_iters, g->acc_relres, g->acc_status, ctl, s));
   return cudaSuccess;
@@ -1341,11 +1367,10 @@ static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
   void* e_push = nullptr;
   const bool dd = bt->opts.predictor == FEM_PRED_DD && g->n_regions > 0;
   if (dd) {
-    const size_t esz = bt->opts.snapshot_format == 1 ? 4 : 8;
-    e_push = (char*)g->ring + esz * (size_t)g->n * slot_of(g, it);
+    e_push = (char*)g->ring + snap_bytes(bt->opts.snapshot_format) * (size_t)g->snap_stride * slot_of(g, it);
   }
   CU(launch_newmark_update(g->n, dt, g->x, g->du_ab, g->u, vslot(it - 1), g->a, vslot(it), e_push,
-                           bt->opts.snapshot_format, s));
+                           bt->opts.snapshot_format, g->snap_stride, s));
   w->count();
   if (dd) {
     uint64_t mask = 0;
@@ -1405,6 +1430,10 @@ static fem_status autotune_t(fem_mesh* m, int rpad, cudaStream_t s, int* v_out, 
     for (int hpt : {64, 128, 256, 512}) cand.push_back({2, hpt});
     for (int hpt : {64, 128, 256}) cand.push_back({3, hpt});
     for (int hpt : {64, 128}) cand.push_back({4, hpt});
+    if (sizeof(T) == 4 && rpad >= 4 && !m->seg) {
+      for (int hpt : {64, 128}) cand.push_back({5, hpt});
+      for (int hpt : {64, 128, 256}) cand.push_back({6, hpt});
+    }
   }
   double best = 1e30;
   int bv = 1, bh = 0;
@@ -1593,7 +1622,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
 fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile) {
   g_err.clear();
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
-  if (ebe_variant < 0 || ebe_variant > 4) return fail(FEM_ERR_ARG, "ebe_variant must be 0 .. 4");
+  if (ebe_variant < 0 || ebe_variant > 6) return fail(FEM_ERR_ARG, "ebe_variant must be 0 .. 6");
   if (ebe_variant >= 2 && !m->hex) return fail(FEM_ERR_ARG, "the mesh has no hex patches: tiled kernel unavailable");
   if (hex_per_tile != 0 && hex_per_tile != 64 && hex_per_tile != 128 && hex_per_tile != 256 && hex_per_tile != 512)
     return fail(FEM_ERR_ARG, "hex_per_tile must be 0, 64, 128, 256 or 512");

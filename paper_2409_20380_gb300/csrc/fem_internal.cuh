@@ -166,6 +166,18 @@ template <typename T>
 cudaError_t launch_update(const MeshView& m, int rpad, const T* p, const T* q, T* x, T* r, T* z,
                           Reducer red, CgCase* sc, int* n_active, double tol, int maxit, cudaStream_t s);
 
+// Deferred-update iteration of the FP32 inner solves (no true-residual test): the direction pass forms
+// z = B^{-1} r and applies the previous x += alpha p; the update pass only advances r.  x is complete
+// after launch_refine_pending, which adds each case's last alpha p.
+template <typename T>
+cudaError_t launch_dir_defer(const MeshView& m, int rpad, const T* r, T* p, T* x, const CgCase* sc,
+                             const int* n_active, cudaStream_t s);
+template <typename T>
+cudaError_t launch_update_defer(const MeshView& m, int rpad, const T* q, T* r, Reducer red, CgCase* sc,
+                                int* n_active, int maxit, cudaStream_t s);
+cudaError_t launch_refine_pending(const MeshView& m, int rpad, int ncase, double* x, const float* d32,
+                                  const float* p32, CgCase* outer, const CgCase* inner, cudaStream_t s);
+
 // Mixed precision helpers.
 cudaError_t launch_outer_resid(const MeshView& m, int rpad, const double* b, const double* q,
                                float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
@@ -212,7 +224,7 @@ cudaError_t launch_ab4_ring(int64_t n, double dt, Ring4 v, const StepCtl* ctl, d
 cudaError_t launch_add(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
 cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const double* du_ab, double* u,
                                   const double* v_prev, double* a, double* v_push, void* e_push, int e_fmt,
-                                  cudaStream_t s);
+                                  int64_t stride, cudaStream_t s);
 
 // FP32-inner steps with products kept by recurrences (see k_step.cu).
 cudaError_t launch_rhs_incr(const MeshView& m, int rpad, double dt, double a0, double a1, const double* Ma,
@@ -238,10 +250,12 @@ cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, 
 // Split FP64 product: qM = M p and qK = K p in one pass (generic element kernel).
 // Staged variant of the tiled hex kernel: each tile's node values and element records are brought into
 // shared memory by bulk asynchronous (TMA) copies, double-buffered against the previous tile's compute.
+// packed (FP32, not fused groups): each thread applies its hex to two cases with paired FP32 operations,
+// 1 = registers capped for two blocks per SM, 2 = one block per SM; 0 = one case per thread.
 template <typename T>
 cudaError_t launch_ebe_hex_staged(const HexTiles& ht, const MeshView& m, int rpad, const T* p, T* q, double aM,
                                   double aK, const Reducer* red, CgCase* sc, double* ptq_out, const int* gate,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int packed = 0);
 template <typename T>
 size_t ebe_hex_staged_smem(const HexTiles& ht, const MeshView& m, int rpad);   // ~0 when not applicable
 // Case-major staged variant: warps of 32 hexes of one case; converged cases (sc[c].active == 0) skipped.
@@ -265,9 +279,9 @@ struct PredView {
   const int32_t* reg_hi;
   int rpad;
   int n_slots;             // ring size (s_max + 1)
-  int64_t slot_stride;     // elements per slot = N * 3 * rpad
-  const void* ring;        // [n_slots][N][3][rpad] of FP64, FP32 or (hi, lo) FP32 pairs
-  int fmt;                 // snapshot storage: 0 FP64, 1 FP32, 2 double-float pairs
+  int64_t slot_stride;     // values per slot: N * 3 * rpad rounded up to a multiple of 8
+  const void* ring;        // [n_slots] slots of [N][3][rpad] values, stored as fmt says
+  int fmt;                 // snapshot storage: 0 FP64, 1 FP32, 2 double-float pairs, 3 FP32 + BF16 residual
   double* gram;            // [R][rpad][kMaxSlots][kMaxSlots]
   double* w;               // [R][rpad][kMaxSlots] coefficients in X order
   int n_chunks;            // node-range chunks per region (blocks per region of the dot/combine kernels)

@@ -444,6 +444,100 @@ __device__ __forceinline__ void tet_acc_s(const T* re, T aM, T aK, const T (&P)[
   }
 }
 
+// Two cases per thread on Blackwell's paired FP32 pipe operations (one instruction, two lanes of values):
+// the cases of a node are adjacent in memory, so a pair loads as one float2 and every operation of the
+// element arithmetic is the same for both; the element records are shared and broadcast to both halves.
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// The tet_acc_s arithmetic for a pair of cases.
+template <int A0, int A1, int A2, int A3>
+__device__ __forceinline__ void tet_acc_p(const float* re, float aM, float aK, const float2 (&P)[8][3],
+                                          float2 (&Q)[8][3]) {
+  float r[12];
+  SVec4<float>::load12(re, r);
+  const float2 lam = bc2(aK * r[9]), mu = bc2(aK * r[10]), ms = bc2(aM * r[11]);
+  float2 G[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float2 d1 = sub2(P[A1][i], P[A0][i]), d2 = sub2(P[A2][i], P[A0][i]), d3 = sub2(P[A3][i], P[A0][i]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) G[i][j] = fma2(d3, bc2(r[6 + j]), fma2(d2, bc2(r[3 + j]), mul2(d1, bc2(r[j]))));
+  }
+  const float2 tr = add2(add2(G[0][0], G[1][1]), G[2][2]);
+  const float2 mu2 = add2(mu, mu);
+  const float2 ltr = mul2(lam, tr);
+  float2 S[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) S[i][i] = fma2(mu2, G[i][i], ltr);
+  S[0][1] = S[1][0] = mul2(mu, add2(G[0][1], G[1][0]));
+  S[0][2] = S[2][0] = mul2(mu, add2(G[0][2], G[2][0]));
+  S[1][2] = S[2][1] = mul2(mu, add2(G[1][2], G[2][1]));
+  float2 F[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      F[b][i] = fma2(S[i][2], bc2(r[3 * b + 2]), fma2(S[i][1], bc2(r[3 * b + 1]), mul2(S[i][0], bc2(r[3 * b]))));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float2 sum = add2(add2(P[A0][k], P[A1][k]), add2(P[A2][k], P[A3][k]));
+    const float2 fs = add2(add2(F[0][k], F[1][k]), F[2][k]);
+    Q[A0][k] = fma2(ms, add2(P[A0][k], sum), sub2(Q[A0][k], fs));
+    Q[A1][k] = fma2(ms, add2(P[A1][k], sum), add2(Q[A1][k], F[0][k]));
+    Q[A2][k] = fma2(ms, add2(P[A2][k], sum), add2(Q[A2][k], F[1][k]));
+    Q[A3][k] = fma2(ms, add2(P[A3][k], sum), add2(Q[A3][k], F[2][k]));
+  }
+}
+
+// One hex for a pair of cases, corner offsets o[] into the staged tile.  The six tets are visited around
+// the cycle of their middle corners (the diagonal corners 0 and 3 are in all six), so each middle corner's
+// values are loaded just before its first tet and its sums leave for the tile accumulator right after its
+// second: fewer values live at once than with all eight corners held through the hex.
+template <bool DOT>
+__device__ __forceinline__ void hex_acc_p(const float* ps, float* qs, const int (&o)[8], int rpad, const float* re,
+                                          float aM, float aK, float2& hd) {
+  float2 P[8][3], Q[8][3];
+  auto ld = [&](int sl) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      P[sl][k] = *reinterpret_cast<const float2*>(ps + o[sl] + k * rpad);
+      Q[sl][k] = make_float2(0.f, 0.f);
+    }
+  };
+  auto fl = [&](int sl) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (DOT) hd = fma2(P[sl][k], Q[sl][k], hd);
+      float* d = qs + o[sl] + k * rpad;
+      atomicAdd(d, Q[sl][k].x);
+      atomicAdd(d + 1, Q[sl][k].y);
+    }
+  };
+  static_assert(kHexTet[0][1] == 1 && kHexTet[0][2] == 2 && kHexTet[1][3] == 4 && kHexTet[4][1] == 7 &&
+                    kHexTet[5][3] == 6 && kHexTet[3][1] == 5,
+                "the visiting order follows the corner table");
+  ld(0), ld(3), ld(1), ld(2);
+  tet_acc_p<kHexTet[0][0], kHexTet[0][1], kHexTet[0][2], kHexTet[0][3]>(re + 0 * kRec, aM, aK, P, Q);
+  ld(4);
+  tet_acc_p<kHexTet[1][0], kHexTet[1][1], kHexTet[1][2], kHexTet[1][3]>(re + 1 * kRec, aM, aK, P, Q);
+  fl(1);
+  ld(7);
+  tet_acc_p<kHexTet[4][0], kHexTet[4][1], kHexTet[4][2], kHexTet[4][3]>(re + 4 * kRec, aM, aK, P, Q);
+  fl(4);
+  ld(6);
+  tet_acc_p<kHexTet[5][0], kHexTet[5][1], kHexTet[5][2], kHexTet[5][3]>(re + 5 * kRec, aM, aK, P, Q);
+  fl(7);
+  ld(5);
+  tet_acc_p<kHexTet[3][0], kHexTet[3][1], kHexTet[3][2], kHexTet[3][3]>(re + 3 * kRec, aM, aK, P, Q);
+  fl(6);
+  tet_acc_p<kHexTet[2][0], kHexTet[2][1], kHexTet[2][2], kHexTet[2][3]>(re + 2 * kRec, aM, aK, P, Q);
+  fl(5), fl(2), fl(0), fl(3);
+}
+
 // ------------------------------------------------------------------------------------------------------
 // TMA-staged tiled hex kernel.  Tile t's element records (one contiguous block) and its nodes' values of
 // p (3 x rpad contiguous values per node) are brought into shared memory by bulk asynchronous copies
@@ -509,8 +603,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-template <typename T, bool DOT, bool SEG>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_staged(
+template <typename T, bool DOT, bool SEG, int PK>
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && PK != 2) ? 2 : 1) k_ebe_hex_staged(
     HexTiles ht, MeshView m, int rpad, int rshift, const T* __restrict__ p, T* __restrict__ q, T aM, T aK, Reducer red,
     CgCase* sc, double* ptq_out, const int* gate) {
   if (gate && *gate == 0) return;
@@ -568,7 +662,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
       }
     }
   };
-  double dot = 0.0;
+  double dot = 0.0, dot1 = 0.0;   // (packed: dot1 is the second case of the thread's pair)
+  constexpr bool pk = PK != 0;
   int nd_next[2], nd_after[2];
   const int t0 = blockIdx.x;
   {
@@ -586,7 +681,12 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
     load_nodes(tn + gridDim.x, nd_after);
     const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
     const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
-    for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) qs[i] = (T)0;
+    if constexpr (pk) {
+      for (int i = threadIdx.x; i < (nl * per_node) >> 2; i += blockDim.x)
+        reinterpret_cast<float4*>(qs)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) qs[i] = (T)0;
+    }
     const uint32_t bar = smem_u32(mbar + b);
     if (!mbar_wait(bar, (uint32_t)((k >> 1) & 1))) {
       atomicExch(&g_tma_timeout, 1);
@@ -596,6 +696,26 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
     const T* ps = psb(b);
     const T* sr = srb(b);
     const int* snode = snb(b);
+    if constexpr (pk) {
+      // items (hex, case pair); a thread's pair is fixed (blockDim.x is a multiple of rpad / 2)
+      const int rs1 = rshift - 1, pm = (rpad >> 1) - 1;
+      const int items = nh << rs1;
+      float2 tdot2 = make_float2(0.f, 0.f);
+      uint4 lw_next = (int)threadIdx.x < items ? __ldg(ht.hex_local + h0 + (threadIdx.x >> rs1)) : make_uint4(0, 0, 0, 0);
+      for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int hl = it >> rs1, c0 = (it & pm) << 1;
+        const uint4 lw = lw_next;
+        if (it + (int)blockDim.x < items) lw_next = __ldg(ht.hex_local + h0 + ((it + blockDim.x) >> rs1));
+        const int o[8] = {(int)(lw.x & 0xffff) * per_node + c0, (int)(lw.x >> 16) * per_node + c0,
+                          (int)(lw.y & 0xffff) * per_node + c0, (int)(lw.y >> 16) * per_node + c0,
+                          (int)(lw.z & 0xffff) * per_node + c0, (int)(lw.z >> 16) * per_node + c0,
+                          (int)(lw.w & 0xffff) * per_node + c0, (int)(lw.w >> 16) * per_node + c0};
+        hex_acc_p<DOT>(reinterpret_cast<const float*>(ps), reinterpret_cast<float*>(qs), o, rpad,
+                       reinterpret_cast<const float*>(sr) + hl * 6 * kRec, (float)aM, (float)aK, tdot2);
+      }
+      dot += (double)tdot2.x;
+      dot1 += (double)tdot2.y;
+    } else {
     T tdot = 0;
     const int items = nh << rshift;
     const int rounds_end = seg ? ((items + blockDim.x - 1) / blockDim.x) * blockDim.x : items;
@@ -643,7 +763,26 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
       }
     }
     dot += (double)tdot;
+    }
     __syncthreads();
+    if constexpr (pk) {
+      // float4 pieces of the tile accumulator (four cases of one component of one node)
+      const int sh4 = rshift - 2;
+      const int f4 = per_node >> 2;
+      for (int i = threadIdx.x; i < nl * f4; i += blockDim.x) {
+        const int l = (i >> sh4) / 3, kk = (i - l * f4) >> sh4;
+        const int raw = snode[l];
+        const int64_t g = raw & 0x0fffffff;
+        const bool fixed = !dof_free((uint8_t)((raw >> 28) & 7), kk);
+        float4* dst = reinterpret_cast<float4*>(q + g * per_node) + (i - l * f4);
+        const float4 v = reinterpret_cast<const float4*>(qs)[i];
+        if (raw < 0) {
+          if (!fixed) atomicAdd(dst, v);
+        } else {
+          *dst = fixed ? make_float4(0.f, 0.f, 0.f, 0.f) : v;
+        }
+      }
+    } else
     for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) {
       const int l = (i >> rshift) / 3, rem = i - l * per_node;
       const int kk = rem >> rshift;
@@ -664,6 +803,18 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe_hex_stag
   if (DOT) {
     if (seg) {
       if (block_reduce_last_seg<1>(sacc, m.nseg, red)) ebe_tail_seg(red, sc, ptq_out, m.nseg);
+    } else if constexpr (pk) {
+      // pair sums over the warp's hexes, then lane c < rpad takes case c (the layout of the block reduction)
+      const int lane = threadIdx.x & 31, half = rpad >> 1;
+      double d0 = dot, d1 = dot1;
+      for (int off = half; off < 32; off <<= 1) {
+        d0 += __shfl_xor_sync(0xffffffffu, d0, off);
+        d1 += __shfl_xor_sync(0xffffffffu, d1, off);
+      }
+      const double a = __shfl_sync(0xffffffffu, d0, (lane >> 1) & (half - 1));
+      const double bb = __shfl_sync(0xffffffffu, d1, (lane >> 1) & (half - 1));
+      double v[1] = {lane < rpad ? ((lane & 1) ? bb : a) : 0.0};
+      if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
     } else {
       double v[1] = {dot};
       if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
@@ -867,7 +1018,7 @@ template size_t ebe_hex_staged_smem<double>(const HexTiles&, const MeshView&, in
 template <typename T>
 cudaError_t launch_ebe_hex_staged(const HexTiles& ht, const MeshView& m, int rpad, const T* p, T* q, double aM,
                                   double aK, const Reducer* red, CgCase* sc, double* ptq_out, const int* gate,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int packed) {
   const size_t smem = ebe_hex_staged_smem<T>(ht, m, rpad);
   if (smem == ~(size_t)0 || (reinterpret_cast<uintptr_t>(p) & 15) != 0) return cudaErrorInvalidValue;
   cudaError_t err = cudaMemsetAsync(q, 0, sizeof(T) * (size_t)m.N * 3 * rpad, s);
@@ -877,8 +1028,15 @@ cudaError_t launch_ebe_hex_staged(const HexTiles& ht, const MeshView& m, int rpa
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 1;
-  auto kfn = red ? (m.seg ? k_ebe_hex_staged<T, true, true> : k_ebe_hex_staged<T, true, false>)
-                 : k_ebe_hex_staged<T, false, false>;
+  // packed pairs: FP32 only, one case per lane of the node row (not fused groups), a 16-byte aligned output
+  // (the tile flush writes float4 pieces); 1: registers capped for two blocks per SM, 2: one block per SM
+  const int pk = (sizeof(T) == 4 && !m.seg && rpad >= 4 && (reinterpret_cast<uintptr_t>(q) & 15) == 0) ? packed : 0;
+  auto kfn = red ? (m.seg ? k_ebe_hex_staged<T, true, true, 0> : k_ebe_hex_staged<T, true, false, 0>)
+                 : k_ebe_hex_staged<T, false, false, 0>;
+  if constexpr (sizeof(T) == 4) {
+    if (pk == 1) kfn = red ? k_ebe_hex_staged<T, true, false, 1> : k_ebe_hex_staged<T, false, false, 1>;
+    if (pk == 2) kfn = red ? k_ebe_hex_staged<T, true, false, 2> : k_ebe_hex_staged<T, false, false, 2>;
+  }
   err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBlock, smem);
   if (err != cudaSuccess) return err;
@@ -893,9 +1051,10 @@ cudaError_t launch_ebe_hex_staged(const HexTiles& ht, const MeshView& m, int rpa
 }
 template cudaError_t launch_ebe_hex_staged<double>(const HexTiles&, const MeshView&, int, const double*, double*,
                                                    double, double, const Reducer*, CgCase*, double*, const int*,
-                                                   cudaStream_t);
+                                                   cudaStream_t, int);
 template cudaError_t launch_ebe_hex_staged<float>(const HexTiles&, const MeshView&, int, const float*, float*, double,
-                                                  double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
+                                                  double, const Reducer*, CgCase*, double*, const int*, cudaStream_t,
+                                                  int);
 
 template <typename T>
 size_t ebe_hex_cm_smem(const HexTiles& ht, const MeshView& m, int rpad) {

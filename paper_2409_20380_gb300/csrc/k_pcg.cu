@@ -220,6 +220,104 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_update(MeshView m, int rpad, i
   }
 }
 
+// Deferred-update form of the iteration (the FP32 inner solves, which do not test the true residual): the
+// direction pass forms z = B^{-1} r itself and applies the previous step's x += alpha p while it reads p,
+// so the update pass reads only q and r and stores only r (z is never stored): 8 vector passes an
+// iteration instead of 10.  A case that has stopped keeps its last alpha until a later direction pass or
+// the final refinement (k_refine_pending) applies it; the product's tail then zeroes it.
+template <typename T>
+__global__ void __launch_bounds__(kVecBlock, 3) k_dir_defer(MeshView m, int rpad, int rshift, const T* __restrict__ r,
+                                                      T* __restrict__ p, T* __restrict__ x, const CgCase* sc,
+                                                      const int* n_active) {
+  if (*n_active == 0) return;
+  // the grid stride is a multiple of rpad: every thread serves one case
+  const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & (rpad - 1));
+  const bool act = sc[c].active != 0;
+  const T alpha = (T)sc[c].alpha;
+  if (!act && alpha == (T)0) return;
+  const T beta = (T)(sc[c].phase ? sc[c].beta : 0.0);
+  const T* __restrict__ bi = binv_of<T>(m);
+  const int64_t total = m.N << rshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i >> rshift;
+    const int64_t id0 = n * 3 * rpad + c;
+    T pv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      pv[k] = p[id0 + k * rpad];
+      if (alpha != (T)0) x[id0 + k * rpad] += alpha * pv[k];
+    }
+    if (act) {
+      const T r0 = r[id0], r1 = r[id0 + rpad], r2 = r[id0 + 2 * rpad];
+      const T* B = bi + n * 6;
+      p[id0] = B[0] * r0 + B[3] * r1 + B[4] * r2 + beta * pv[0];
+      p[id0 + rpad] = B[3] * r0 + B[1] * r1 + B[5] * r2 + beta * pv[1];
+      p[id0 + 2 * rpad] = B[4] * r0 + B[5] * r1 + B[2] * r2 + beta * pv[2];
+    }
+  }
+}
+
+// r -= alpha q on free DOFs; (B^{-1} r, r) and (r, r) reduced; the same per-case tail as k_update.
+template <typename T>
+__global__ void __launch_bounds__(kVecBlock, 3) k_update_defer(MeshView m, int rpad, int rshift,
+                                                         const T* __restrict__ q, T* __restrict__ r, Reducer red,
+                                                         CgCase* sc, int* n_active, int maxit) {
+  if (*n_active == 0) return;
+  const T* __restrict__ bi = binv_of<T>(m);
+  typename Acc<T>::type zr = 0, rr = 0;
+  const int64_t total = m.N << rshift;
+  const T alpha = (T)sc[(blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & (rpad - 1)].alpha;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i >> rshift;
+    const int c = (int)(i & (rpad - 1));
+    const uint8_t f = m.freemask[n];
+    T rv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int64_t id = (n * 3 + k) * rpad + c;
+      T rk = r[id];
+      if (alpha != (T)0 && dof_free(f, k)) {
+        rk -= alpha * q[id];
+        r[id] = rk;
+      }
+      rv[k] = rk;
+    }
+    const T* B = bi + n * 6;
+    const T z0 = B[0] * rv[0] + B[3] * rv[1] + B[4] * rv[2];
+    const T z1 = B[3] * rv[0] + B[1] * rv[1] + B[5] * rv[2];
+    const T z2 = B[4] * rv[0] + B[5] * rv[1] + B[2] * rv[2];
+    zr += z0 * rv[0] + z1 * rv[1] + z2 * rv[2];
+    rr += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+  }
+  double v[2] = {(double)zr, (double)rr};
+  if (block_reduce_last<2>(v, rpad, red)) {
+    if (threadIdx.x < rpad) {
+      const int c = threadIdx.x;
+      CgCase& s = sc[c];
+      if (s.active) {
+        const double zrc = red.out[c], rrc = red.out[rpad + c];
+        s.beta = zrc / s.rho;
+        s.rho = zrc;
+        s.rr = rrc;
+        s.iters += 1;
+        s.phase = 1;
+        s.relres = sqrt(rrc / s.bb);
+        if (!isfinite(zrc) || !isfinite(rrc)) {
+          s.status = FEM_ERR_NONFINITE;
+          s.active = 0;
+        } else if (rrc < s.tol2 * s.bb) {
+          s.active = 0;
+        } else if (s.iters >= maxit) {
+          s.active = 0;
+          s.status = FEM_ERR_NOT_CONVERGED;
+        }
+      }
+    }
+    __syncthreads();
+    count_active(sc, rpad, n_active);
+  }
+}
+
 // ---- mixed precision: FP64 outer residual -> FP32 inner right-hand side; FP64 refinement update ----
 __global__ void __launch_bounds__(kVecBlock, 3) k_outer_resid(MeshView m, int rpad, int rshift, const double* __restrict__ b,
                                                         const double* __restrict__ q, float* __restrict__ r32,
@@ -268,6 +366,21 @@ __global__ void k_refine(int64_t n_items, int ncase, double* __restrict__ x, con
   }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items; i += (int64_t)gridDim.x * blockDim.x)
     x[i] += f2d(d[i]);
+}
+
+// The same after a deferred-update inner solve: x += d + alpha_c p (each case's pending last step).
+__global__ void k_refine_pending(int64_t n_items, int rpad, int ncase, double* __restrict__ x,
+                                 const float* __restrict__ d, const float* __restrict__ p, CgCase* outer,
+                                 const CgCase* inner) {
+  if (blockIdx.x == 0 && threadIdx.x < ncase) {
+    outer[threadIdx.x].iters += inner[threadIdx.x].iters;
+    if (inner[threadIdx.x].status == FEM_ERR_BREAKDOWN || inner[threadIdx.x].status == FEM_ERR_NONFINITE)
+      outer[threadIdx.x].status = inner[threadIdx.x].status;
+  }
+  // the grid stride is a multiple of rpad: every thread serves one case
+  const float a = (float)inner[(blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & (rpad - 1)].alpha;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += f2d(a != 0.0f ? fmaf(a, p[i], d[i]) : d[i]);
 }
 
 // x = 0 on Dirichlet DOFs and for cases whose right-hand side is zero (||b|| = 0 gives x = 0).
@@ -323,6 +436,33 @@ cudaError_t launch_update(const MeshView& m, int rpad, const T* p, const T* q, T
                           CgCase* sc, int* n_active, double tol, int maxit, cudaStream_t s) {
   const int rs = log2i(rpad);
   k_update<T><<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, p, q, x, r, z, red, sc, n_active, tol, maxit);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dir_defer(const MeshView& m, int rpad, const T* r, T* p, T* x, const CgCase* sc,
+                             const int* n_active, cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_dir_defer<T><<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, r, p, x, sc, n_active);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update_defer(const MeshView& m, int rpad, const T* q, T* r, Reducer red, CgCase* sc,
+                                int* n_active, int maxit, cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_update_defer<T><<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, q, r, red, sc, n_active, maxit);
+  return cudaGetLastError();
+}
+template cudaError_t launch_dir_defer<float>(const MeshView&, int, const float*, float*, float*, const CgCase*,
+                                             const int*, cudaStream_t);
+template cudaError_t launch_update_defer<float>(const MeshView&, int, const float*, float*, Reducer, CgCase*, int*,
+                                                int, cudaStream_t);
+
+cudaError_t launch_refine_pending(const MeshView& m, int rpad, int ncase, double* x, const float* d32,
+                                  const float* p32, CgCase* outer, const CgCase* inner, cudaStream_t s) {
+  const int64_t n = m.N * 3 * rpad;
+  k_refine_pending<<<grid_for(n), kBlock, 0, s>>>(n, rpad, ncase, x, d32, p32, outer, inner);
   return cudaGetLastError();
 }
 

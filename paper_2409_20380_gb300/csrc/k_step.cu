@@ -5,11 +5,46 @@
 
 namespace fem {
 
-// Snapshot storage: FP64, FP32, or double-float pairs (hi, lo FP32 with hi + lo = e to 2^-48 relative; the
-// same 8 bytes as FP64, read and combined on the FP32 pipe).
-__device__ __forceinline__ void store_snap(double* p, double v) { *p = v; }
-__device__ __forceinline__ void store_snap(float* p, double v) { *p = (float)v; }
-__device__ __forceinline__ void store_snap(float2* p, double v) { *p = d2df(v); }
+// Snapshot storage: FP64, FP32, double-float pairs (hi, lo FP32 with hi + lo = e to 2^-48 relative; the
+// same 8 bytes as FP64, read and combined on the FP32 pipe), or SnapHL: the FP32 value and its residual
+// rounded to BF16 in two planes of one slot (6 bytes a value, e to about 2^-32 relative, read as a
+// double-float pair).  A slot holds `stride` values (a multiple of 8, so both planes start on 16 bytes);
+// slot j starts snap_bytes<E> * stride * j bytes into the ring.
+struct SnapHL {
+  float h;
+};
+template <typename E> struct SnapVal { typedef E V; };
+template <> struct SnapVal<SnapHL> { typedef float2 V; };
+template <typename E> constexpr int snap_bytes() { return (int)sizeof(E); }
+template <> constexpr int snap_bytes<SnapHL>() { return 6; }
+
+__device__ __forceinline__ uint16_t f2bf_rn(float x) {   // round to nearest even (finite inputs)
+  const uint32_t u = __float_as_uint(x);
+  return (uint16_t)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+__device__ __forceinline__ float bf2f(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+__device__ __forceinline__ void store_snap(double* p, int64_t, int64_t i, double v) { p[i] = v; }
+__device__ __forceinline__ void store_snap(float* p, int64_t, int64_t i, double v) { p[i] = (float)v; }
+__device__ __forceinline__ void store_snap(float2* p, int64_t, int64_t i, double v) { p[i] = d2df(v); }
+__device__ __forceinline__ void store_snap(SnapHL* p, int64_t stride, int64_t i, double v) {
+  const float2 hl = d2df(v);
+  reinterpret_cast<float*>(p)[i] = hl.x;
+  reinterpret_cast<uint16_t*>(reinterpret_cast<float*>(p) + stride)[i] = f2bf_rn(hl.y);
+}
+template <typename E>
+__device__ __forceinline__ typename SnapVal<E>::V load_snap(const E* p, int64_t, int64_t i) { return p[i]; }
+template <>
+__device__ __forceinline__ float2 load_snap<SnapHL>(const SnapHL* p, int64_t stride, int64_t i) {
+  const float* h = reinterpret_cast<const float*>(p);
+  return make_float2(h[i], bf2f(reinterpret_cast<const uint16_t*>(h + stride)[i]));
+}
+template <typename E> __device__ __forceinline__ E* snap_slot(E* ring, int64_t slot, int64_t stride) {
+  return reinterpret_cast<E*>(reinterpret_cast<char*>(ring) + slot * stride * snap_bytes<E>());
+}
+template <typename E> __device__ __forceinline__ const E* snap_slot(const E* ring, int64_t slot, int64_t stride) {
+  return reinterpret_cast<const E*>(reinterpret_cast<const char*>(ring) + slot * stride * snap_bytes<E>());
+}
 
 
 static int vec_grid(int64_t items) {
@@ -92,7 +127,7 @@ __global__ void k_add(int64_t n, const double* __restrict__ a, const double* __r
 template <typename E>
 __global__ void k_newmark(int64_t n, double dt, const double* __restrict__ du, const double* __restrict__ du_ab,
                           double* __restrict__ u, const double* __restrict__ v_prev, double* __restrict__ a,
-                          double* __restrict__ v_push, E* __restrict__ e_push) {
+                          double* __restrict__ v_push, E* __restrict__ e_push, int64_t stride) {
   const double c2 = 2.0 / dt, c4 = 4.0 / dt, c44 = 4.0 / (dt * dt);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double d = du[i];
@@ -100,7 +135,7 @@ __global__ void k_newmark(int64_t n, double dt, const double* __restrict__ du, c
     u[i] += d;
     v_push[i] = c2 * d - vp;
     a[i] = c44 * d - c4 * vp - a[i];
-    if (e_push) store_snap(e_push + i, d - du_ab[i]);
+    if (e_push) store_snap(e_push, stride, i, d - du_ab[i]);
   }
 }
 
@@ -171,9 +206,10 @@ template <> struct RedVal<float2> {
 // dpart[R][k][j][c].  Slot groups keep the accumulators in registers at a useful occupancy.
 constexpr int kDotGrp = 11;
 constexpr int kDotGroups = (kMaxSlots + kDotGrp - 1) / kDotGrp;
-template <typename T>
+template <typename E>
 __global__ void __launch_bounds__(kBlock, 3) k_pred_dots(PredView p, int slot_new, uint64_t valid_mask,
                                                          const StepCtl* ctl) {
+  typedef typename SnapVal<E>::V T;
   if (ctl) slot_new = ctl->slot_new, valid_mask = ctl->mask;
   const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
   const int j0 = blockIdx.y * kDotGrp;
@@ -181,16 +217,17 @@ __global__ void __launch_bounds__(kBlock, 3) k_pred_dots(PredView p, int slot_ne
   const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
   const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
   const int rpad = p.rpad;
-  const T* ring = (const T*)p.ring;
-  const T* xn = ring + (int64_t)slot_new * p.slot_stride;
+  const E* ring = (const E*)p.ring;
+  const int64_t st = p.slot_stride;
+  const E* xn = snap_slot(ring, slot_new, st);
   PredAcc<T> acc[kDotGrp];
   const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
   for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-    const T x = xn[base + i];
+    const T x = load_snap(xn, st, base + i);
 #pragma unroll
     for (int jj = 0; jj < kDotGrp; ++jj) {
       const int j = j0 + jj;
-      if (j < kMaxSlots && ((valid_mask >> j) & 1ull)) acc[jj].add(ring[(int64_t)j * p.slot_stride + base + i], x);
+      if (j < kMaxSlots && ((valid_mask >> j) & 1ull)) acc[jj].add(load_snap(snap_slot(ring, j, st), st, base + i), x);
     }
   }
   __shared__ RedVal<T> sh[kBlock / 32][kDotGrp][32];
@@ -230,8 +267,10 @@ __global__ void k_pred_dots_finish(PredView p, int slot_new, uint64_t valid_mask
 
 // Per (region, case): least-squares coefficients w of the query (newest slot) on the X slots, by a
 // pivot-free Cholesky of the Gram with the column-drop rule  pivot <= tau^2 G_jj  (the squared form of
-// the modified Gram-Schmidt test ||v_j|| <= tau ||x_j||), then forward/back substitution.  One warp: lane i
-// owns row i; rows padded to an odd length of doubles to spread shared-memory banks.
+// the modified Gram-Schmidt test ||v_j|| <= tau ||x_j||), then forward/back substitution.  One warp per
+// system: the trailing updates of the factorisation are spread over the lanes (the FP64 pipe is the limit,
+// so no lane idles through a column), the pivots are kept as reciprocals so the substitutions (lane i owns
+// row i) multiply; rows padded to an odd length of doubles to spread shared-memory banks.
 __global__ void k_pred_solve(PredView p, const int* __restrict__ x_slots, int n, int slot_new, double tau,
                              const StepCtl* ctl) {
   if (ctl) x_slots = ctl->xs, n = ctl->n_pairs, slot_new = ctl->slot_query;
@@ -239,43 +278,52 @@ __global__ void k_pred_solve(PredView p, const int* __restrict__ x_slots, int n,
   const int lane = threadIdx.x;
   constexpr int LD = kMaxSlots;                 // 33 doubles per row
   __shared__ double L[kMaxSlots * LD];
-  __shared__ double dg[kMaxSlots];
+  __shared__ double inv[kMaxSlots];             // 1 / pivot, 0 for a dropped column
+  __shared__ unsigned short tab[kMaxSlots * (kMaxSlots + 1) / 2];
   const double* G = p.gram + ((int64_t)R * p.rpad + c) * kMaxSlots * kMaxSlots;
   const int xi = lane < n ? x_slots[lane] : 0;
   for (int i = 0; i < n; ++i) {
     const int xs_i = __shfl_sync(0xffffffffu, xi, i);
     if (lane < n) L[i * LD + lane] = G[xs_i * kMaxSlots + xi];
   }
+  // lower-triangle entries (i, k), k descending: the trailing block of column j is the prefix of length
+  // (n - 1 - j)(n - j) / 2 (all entries with k > j)
+  if (lane < n) {
+    const int off = (n - 1 - lane) * (n - lane) / 2;
+    for (int i = lane; i < n; ++i) tab[off + i - lane] = (unsigned short)((i << 8) | lane);
+  }
   double rhs = lane < n ? G[xi * kMaxSlots + slot_new] : 0.0;
   const double d0 = lane < n ? G[xi * kMaxSlots + xi] : 0.0;
   __syncwarp();
-  // right-looking Cholesky: column j, then lanes i > j update their rows
+  // right-looking Cholesky: column j scaled by 1 / pivot, then the trailing block updated with its
+  // entries spread over the lanes (each entry still receives its updates in column order)
   for (int j = 0; j < n; ++j) {
     const double djj = L[j * LD + j];
     const double d0j = __shfl_sync(0xffffffffu, d0, j);
     const bool keep = d0j > 0.0 && djj > tau * tau * d0j && isfinite(djj);
-    const double piv = keep ? sqrt(djj) : 0.0;
+    const double ip = keep ? rsqrt(djj) : 0.0;
     __syncwarp();
-    double lij = 0.0;
-    if (lane > j && lane < n) {
-      lij = keep ? L[lane * LD + j] / piv : 0.0;
-      L[lane * LD + j] = lij;
-    }
+    if (lane > j && lane < n) L[lane * LD + j] = keep ? L[lane * LD + j] * ip : 0.0;
     if (lane == j) {
-      L[j * LD + j] = piv;
-      dg[j] = keep ? 1.0 : 0.0;
+      L[j * LD + j] = keep ? djj * ip : 0.0;
+      inv[j] = ip;
     }
     __syncwarp();
-    if (lane > j && lane < n && keep)
-      for (int k2 = j + 1; k2 <= lane; ++k2) L[lane * LD + k2] -= lij * L[k2 * LD + j];
+    if (keep) {
+      const int T = (n - 1 - j) * (n - j) / 2;
+      for (int t = lane; t < T; t += 32) {
+        const int e = tab[t], i = e >> 8, k = e & 255;
+        L[i * LD + k] = fma(-L[i * LD + j], L[k * LD + j], L[i * LD + k]);
+      }
+    }
     __syncwarp();
   }
   // forward substitution L y = rhs (column sweep), dropped columns give 0
   double y = rhs;
   for (int j = 0; j < n; ++j) {
     const double yj_raw = __shfl_sync(0xffffffffu, y, j);
-    const bool keep = dg[j] != 0.0;
-    const double yj = keep ? yj_raw / L[j * LD + j] : 0.0;
+    const double ij = inv[j];
+    const double yj = ij != 0.0 ? yj_raw * ij : 0.0;
     if (lane == j) y = yj;
     if (lane > j && lane < n) y -= L[lane * LD + j] * yj;
   }
@@ -283,8 +331,8 @@ __global__ void k_pred_solve(PredView p, const int* __restrict__ x_slots, int n,
   double w = y;
   for (int j = n - 1; j >= 0; --j) {
     const double wj_raw = __shfl_sync(0xffffffffu, w, j);
-    const bool keep = dg[j] != 0.0;
-    const double wj = keep ? wj_raw / L[j * LD + j] : 0.0;
+    const double ij = inv[j];
+    const double wj = ij != 0.0 ? wj_raw * ij : 0.0;
     if (lane == j) w = wj;
     if (lane < j) w -= L[j * LD + lane] * wj;
   }
@@ -338,24 +386,26 @@ template <> struct CombAcc<float2> {
 };
 
 // y_out += Y w over the region's node range: the coefficients [a][case] and slot offsets in shared memory.
-template <typename T>
+template <typename E>
 __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* __restrict__ y_slots, int n,
                                                          double* __restrict__ y_out, const StepCtl* ctl) {
   if (ctl) y_slots = ctl->ys, n = ctl->n_pairs;
+  typedef typename SnapVal<E>::V T;
   typedef typename CombAcc<T>::W W;
   const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
   const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
   const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
   const int rpad = p.rpad;
-  const T* ring = (const T*)p.ring;
+  const E* ring = (const E*)p.ring;
+  const int64_t st = p.slot_stride;
   __shared__ W sw[kMaxSlots * kMaxRpad];
-  __shared__ int64_t soff[kMaxSlots];
+  __shared__ const E* sptr[kMaxSlots];
   for (int t = threadIdx.x; t < n * rpad; t += blockDim.x) {
     const int a = t / rpad, c = t % rpad;
     sw[t] = CombAcc<T>::wconv(p.w[((int64_t)R * rpad + c) * kMaxSlots + a]);
   }
-  for (int a = threadIdx.x; a < n; a += blockDim.x) soff[a] = (int64_t)y_slots[a] * p.slot_stride;
+  for (int a = threadIdx.x; a < n; a += blockDim.x) sptr[a] = snap_slot(ring, y_slots[a], st);
   __syncthreads();
   const int c = threadIdx.x & (rpad - 1);
   const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
@@ -366,7 +416,7 @@ __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* 
     for (int a0 = 0; a0 < n; a0 += 8) {
       T y[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) y[u] = a0 + u < n ? ring[soff[a0 + u] + gi] : T{};
+      for (int u = 0; u < 8; ++u) y[u] = a0 + u < n ? load_snap(sptr[a0 + u], st, gi) : T{};
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
         if (a0 + u < n) s0.add(sw[(a0 + u) * rpad + c], y[u]);
@@ -380,27 +430,29 @@ __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* 
 
 // Two combinations in one pass over the ring: y_out += Y w (the data-driven guess) and y2 = Y w2 (the
 // learned proposal's correction of it).
-template <typename T>
+template <typename E>
 __global__ void __launch_bounds__(kBlock) k_pred_combine2(PredView p, const int* __restrict__ y_slots, int n,
                                                           double* __restrict__ y_out, const double* __restrict__ w2,
                                                           double* __restrict__ y2) {
+  typedef typename SnapVal<E>::V T;
   typedef typename CombAcc<T>::W W;
   const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
   const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
   const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
   const int rpad = p.rpad;
-  const T* ring = (const T*)p.ring;
+  const E* ring = (const E*)p.ring;
+  const int64_t st = p.slot_stride;
   __shared__ W sw[kMaxSlots * kMaxRpad];
   __shared__ W sw2[kMaxSlots * kMaxRpad];
-  __shared__ int64_t soff[kMaxSlots];
+  __shared__ const E* sptr[kMaxSlots];
   for (int t = threadIdx.x; t < n * rpad; t += blockDim.x) {
     const int a = t / rpad, c = t % rpad;
     const int64_t o = ((int64_t)R * rpad + c) * kMaxSlots + a;
     sw[t] = CombAcc<T>::wconv(p.w[o]);
     sw2[t] = CombAcc<T>::wconv(w2[o]);
   }
-  for (int a = threadIdx.x; a < n; a += blockDim.x) soff[a] = (int64_t)y_slots[a] * p.slot_stride;
+  for (int a = threadIdx.x; a < n; a += blockDim.x) sptr[a] = snap_slot(ring, y_slots[a], st);
   __syncthreads();
   const int c = threadIdx.x & (rpad - 1);
   const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
@@ -408,7 +460,7 @@ __global__ void __launch_bounds__(kBlock) k_pred_combine2(PredView p, const int*
     const int64_t gi = base + i;
     CombAcc<T> s0, t0;
     for (int a = 0; a < n; ++a) {
-      const T y = ring[soff[a] + gi];
+      const T y = load_snap(sptr[a], st, gi);
       s0.add(sw[a * rpad + c], y);
       t0.add(sw2[a * rpad + c], y);
     }
@@ -597,7 +649,7 @@ __global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, const
     v_prev = vr.p[(it + 3) & 3];
     v_push = vr.p[it & 3];
     Av_push = avr.p[it & 3];
-    e_push = ring ? ring + (int64_t)ctl->slot_new * slot_stride : nullptr;
+    e_push = ring ? snap_slot(ring, ctl->slot_new, slot_stride) : nullptr;
   }
   const double c2 = 2.0 / dt, c4 = 4.0 / dt, c44 = 4.0 / (dt * dt);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -612,7 +664,7 @@ __global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, const
     Mv[i] = mv2;
     Kv[i] = kv2;
     Av_push[i] = cM * mv2 + cK * kv2;
-    if (e_push) store_snap(e_push + i, d - du_ab[i]);
+    if (e_push) store_snap(e_push, slot_stride, i, d - du_ab[i]);
   }
 }
 
@@ -671,13 +723,15 @@ cudaError_t launch_add(int64_t n, const double* a, const double* b, double* out,
 
 cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const double* du_ab, double* u,
                                   const double* v_prev, double* a, double* v_push, void* e_push, int e_fmt,
-                                  cudaStream_t s) {
+                                  int64_t stride, cudaStream_t s) {
   if (e_fmt == 1)
-    k_newmark<float><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (float*)e_push);
+    k_newmark<float><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (float*)e_push, stride);
   else if (e_fmt == 2)
-    k_newmark<float2><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (float2*)e_push);
+    k_newmark<float2><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (float2*)e_push, stride);
+  else if (e_fmt == 3)
+    k_newmark<SnapHL><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (SnapHL*)e_push, stride);
   else
-    k_newmark<double><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (double*)e_push);
+    k_newmark<double><<<grid_for(n), kBlock, 0, s>>>(n, dt, du, du_ab, u, v_prev, a, v_push, (double*)e_push, stride);
   return cudaGetLastError();
 }
 
@@ -726,6 +780,10 @@ cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, cons
     k_newmark_incr<float2><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
                                                           Mv, Kv, Ma, Av_push, (float2*)e_push, vr, avr, (float2*)ring,
                                                           slot_stride, ctl);
+  else if (e_fmt == 3)
+    k_newmark_incr<SnapHL><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
+                                                          Mv, Kv, Ma, Av_push, (SnapHL*)e_push, vr, avr, (SnapHL*)ring,
+                                                          slot_stride, ctl);
   else
     k_newmark_incr<double><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
                                                           Mv, Kv, Ma, Av_push, (double*)e_push, vr, avr, (double*)ring,
@@ -741,6 +799,8 @@ cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mas
     k_pred_dots<float><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask, ctl);
   else if (p.fmt == 2)
     k_pred_dots<float2><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask, ctl);
+  else if (p.fmt == 3)
+    k_pred_dots<SnapHL><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask, ctl);
   else
     k_pred_dots<double><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask, ctl);
   cudaError_t e = cudaGetLastError();
@@ -764,6 +824,8 @@ cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pai
     k_pred_combine<float><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
   else if (p.fmt == 2)
     k_pred_combine<float2><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
+  else if (p.fmt == 3)
+    k_pred_combine<SnapHL><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
   else
     k_pred_combine<double><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
   return cudaGetLastError();
@@ -777,6 +839,8 @@ cudaError_t launch_pred_combine2(const PredView& p, const int* y_slots, int n_pa
     k_pred_combine2<float><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, w2, y2);
   else if (p.fmt == 2)
     k_pred_combine2<float2><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, w2, y2);
+  else if (p.fmt == 3)
+    k_pred_combine2<SnapHL><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, w2, y2);
   else
     k_pred_combine2<double><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, w2, y2);
   return cudaGetLastError();

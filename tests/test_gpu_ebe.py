@@ -26,7 +26,7 @@ def torch_dev():
 CASES = [((7, 5, 4), 1, 0.0), ((7, 5, 4), 4, 0.2), ((9, 6, 5), 16, 0.1), ((3, 2, 2), 32, 0.0), ((12, 9, 7), 8, 0.15)]
 # (ebe_variant, hex_per_tile): generic element kernel; tiled hex kernel and staged tiled hex kernel with
 # automatic and small tiles (140..756 hexes over 64-hex tiles: several tiles and a ragged last one)
-VARIANTS = [(1, 0), (2, 0), (2, 64), (3, 0), (3, 64), (4, 0), (4, 64)]
+VARIANTS = [(1, 0), (2, 0), (2, 64), (3, 0), (3, 64), (4, 0), (4, 64), (5, 0), (5, 64), (6, 0), (6, 64)]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
