@@ -296,6 +296,19 @@ fem_status fem_batch_set_loads(fem_batch* b, const double* loads);
  * Device memory if on_device != 0, else host memory (a host copy synchronises the batch stream). */
 fem_status fem_batch_get_field(fem_batch* b, int what, double* dst, int on_device);
 
+/*
+ * Asynchronous form of fem_batch_get_field into host memory (a library service; the paper has none): the
+ * field as it stands after the work queued so far is staged on the device (two staging buffers of the
+ * field's size, allocated on first use and kept with the batch), and its copy to host_dst runs on the
+ * batch's own copy stream, so it overlaps the steps queued next.  host_dst should be page-locked (else
+ * the copy is not asynchronous); it is complete after fem_batch_sync, or after the next-but-one call of
+ * this function (which reuses the staging buffer).  Same layout as fem_batch_get_field.
+ */
+fem_status fem_batch_get_field_async(fem_batch* b, int what, double* host_dst);
+
+/* Waits until the batch stream and every asynchronous field copy have finished. */
+fem_status fem_batch_sync(fem_batch* b);
+
 /* Device-time profile of fem_step, measured with CUDA events on the batch stream. */
 typedef struct {
   int steps;                         /* steps profiled */

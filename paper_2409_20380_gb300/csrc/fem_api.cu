@@ -250,6 +250,9 @@ struct fem_mesh {
   float inv_extent = 1.0f;          // 1 / largest edge of the bounding box
   int32_t* reg_lo = nullptr;
   int32_t* reg_hi = nullptr;
+  // nodes outside every region range: [reg_hi[R], reg_gap[R]) follows region R, [0, reg_lead) precedes all
+  int32_t* reg_gap = nullptr;
+  int reg_lead = 0;
   std::vector<Workspace*> ws;
   // tiled hex-patch EBE (present when the elements come in Kuhn hex patches)
   bool hex = false;
@@ -352,7 +355,7 @@ struct fem_mesh {
   ~fem_mesh() {
     dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(rec_df); dfree(D);
     dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(Kd); dfree(Md);
-    dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi); dfree(seg); dfree(reg_cent);
+    dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi); dfree(reg_gap); dfree(seg); dfree(reg_cent);
     for (auto* w : ws) delete w;
     for (void* b : tile_bufs) cudaFree(b);
   }
@@ -685,8 +688,20 @@ struct fem_batch {
   float* col_t = nullptr;
   int64_t col_cap = 0, col_n = 0;
   bool col_full = false;
+  // asynchronous field reads: two device staging buffers, copied to the host on their own stream
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ready[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
+  double* stage[2] = {nullptr, nullptr};
+  int stage_k = 0;
   ~fem_batch() {
     for (auto* g : groups) delete g;
+    if (cs) cudaStreamSynchronize(cs);
+    for (int k = 0; k < 2; ++k) {
+      if (stage[k]) cudaFree(stage[k]);
+      if (ready[k]) cudaEventDestroy(ready[k]);
+      if (done[k]) cudaEventDestroy(done[k]);
+    }
+    if (cs) cudaStreamDestroy(cs);
   }
 };
 
@@ -1094,7 +1109,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   StepCtl* ctl = g->ctl;
   const int ce = std::max(1, o.check_every);
   cudaStream_t s = g->gs[0], s2 = g->gs[1], s3 = g->gs[2], s4 = g->gs[3];
-  const long long n_fixed = 6 + (dd ? 6 : 0), n_pass = 4, n_if = 4, n_inner = 3LL * ce + 1;
+  const long long n_fixed = 6 + (dd ? 5 : 0), n_pass = 4, n_if = 4, n_inner = 3LL * ce + 1;
   // 1. step record; the per-region Gram solves (few warps per SM) run beside the Adams-Bashforth
   // increment and the right-hand side, which do not depend on them
   GE(launch_step_begin(ctl, dd ? g->n_slots : 0, o.s_max, dt, dd ? 1 : 0, n_fixed, s));
@@ -1102,18 +1117,21 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   GE(cudaEventRecord(g->gev[0], s));
   GE(cudaStreamWaitEvent(sf, g->gev[0], 0));
   GE(launch_ab4_ring(g->n, dt, V, ctl, g->du_ab, sf));
-  GE(cudaMemcpyAsync(g->guess, g->du_ab, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, sf));
   // 2. right-hand side from the recurrences
   GE(launch_rhs_incr(mv, rpad, dt, m->tp.a0, m->tp.a1, g->Ma, g->Mv, g->Kv, g->Ku, g->b, g->src, g->ext, 0.0, sf,
                      ctl));
   GE(cudaEventRecord(g->gev[1], sf));
   if (dd) GE(launch_pred_solve(pv, nullptr, 0, 0, o.tau, s, ctl));
   GE(cudaStreamWaitEvent(s, g->gev[1], 0));
-  if (dd) GE(launch_pred_combine(pv, nullptr, 0, g->guess, s, ctl));
+  // guess = du_AB + Y w, and the correction Y w in FP32 for its residual
+  if (dd) {
+    GE(launch_pred_combine(pv, nullptr, 0, g->guess, s, ctl, g->du_ab, w->z32, m->reg_gap, m->reg_lead));
+  } else {
+    GE(cudaMemcpyAsync(g->guess, g->du_ab, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+  }
   // 3. residual of the guess
   const float* qy = nullptr;
   if (dd) {
-    GE(launch_corr_f32(g->n, g->guess, g->du_ab, w->z32, s));
     GE(ebe_product<float>(m, rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
     qy = w->q32;
   }
@@ -1699,6 +1717,7 @@ fem_status fem_mesh_set_regions(fem_mesh* m, const int32_t* region_of_node) {
   }
   dfree(m->reg_lo);
   dfree(m->reg_hi);
+  dfree(m->reg_gap);
   dfree(m->reg_cent);
   m->n_regions = 0;
   m->h_region.assign(region_of_node, region_of_node + m->N);
@@ -1720,11 +1739,22 @@ fem_status fem_mesh_set_regions(fem_mesh* m, const int32_t* region_of_node) {
     for (int k = 0; k < 3; ++k) cf[3 * (size_t)r + k] = (float)(cs[3 * (size_t)r + k] / cnt[r]);
   const double ext = std::max(bmax[0] - bmin[0], std::max(bmax[1] - bmin[1], bmax[2] - bmin[2]));
   m->inv_extent = ext > 0.0 ? (float)(1.0 / ext) : 1.0f;
+  // node gaps between the ranges (ranges are disjoint): the gap after region r ends at the next range's start
+  std::vector<int32_t> gap(R, (int32_t)m->N);
+  {
+    std::vector<int> order(R);
+    for (int r = 0; r < R; ++r) order[r] = r;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return lo[x] < lo[y]; });
+    for (int i = 0; i + 1 < R; ++i) gap[order[i]] = lo[order[i + 1]];
+    m->reg_lead = R > 0 ? lo[order[0]] : 0;
+  }
   CHK(dalloc(&m->reg_lo, R));
   CHK(dalloc(&m->reg_hi, R));
+  CHK(dalloc(&m->reg_gap, R));
   CHK(dalloc(&m->reg_cent, 3 * (int64_t)R));
   CU(cudaMemcpy(m->reg_lo, lo.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(m->reg_hi, hi.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(m->reg_gap, gap.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(m->reg_cent, cf.data(), sizeof(float) * 3 * R, cudaMemcpyHostToDevice));
   m->n_regions = R;
   return FEM_OK;
@@ -2099,11 +2129,8 @@ fem_status fem_batch_proposal_counts(fem_batch* b, long long* taken, long long* 
   return FEM_OK;
 }
 
-fem_status fem_batch_get_field(fem_batch* b, int what, double* dst, int on_device) {
-  g_err.clear();
-  if (!b || !dst) return fail(FEM_ERR_ARG, "null argument");
-  CHK(batch_start(b));
-  // case c's field starts after the fields of cases 0..c-1 (each [n_nodes of its mesh][3])
+// case c's field starts after the fields of cases 0..c-1 (each [n_nodes of its mesh][3])
+static std::vector<int64_t> field_offsets(const fem_batch* b) {
   std::vector<int64_t> case_off(b->loc.size() + 1, 0);
   for (size_t c = 0; c < b->loc.size(); ++c) {
     const Group* g = b->groups[b->loc[c].first];
@@ -2111,6 +2138,14 @@ fem_status fem_batch_get_field(fem_batch* b, int what, double* dst, int on_devic
     const int64_t nn = g->owned_mesh ? g->node_off[l + 1] - g->node_off[l] : g->mesh->N;
     case_off[c + 1] = case_off[c] + 3 * nn;
   }
+  return case_off;
+}
+
+fem_status fem_batch_get_field(fem_batch* b, int what, double* dst, int on_device) {
+  g_err.clear();
+  if (!b || !dst) return fail(FEM_ERR_ARG, "null argument");
+  CHK(batch_start(b));
+  const std::vector<int64_t> case_off = field_offsets(b);
   for (auto* g : b->groups) {
     const double* src = nullptr;
     switch (what) {
@@ -2137,6 +2172,40 @@ fem_status fem_batch_get_field(fem_batch* b, int what, double* dst, int on_devic
       CU(cudaMemcpyAsync(dst + case_off[g->cases[l]], tmp + l * n3, sizeof(double) * n3, kind, b->s));
   }
   if (!on_device) CU(cudaStreamSynchronize(b->s));
+  return FEM_OK;
+}
+
+fem_status fem_batch_get_field_async(fem_batch* b, int what, double* host_dst) {
+  g_err.clear();
+  if (!b || !host_dst) return fail(FEM_ERR_ARG, "null argument");
+  CHK(batch_start(b));
+  const std::vector<int64_t> case_off = field_offsets(b);
+  const size_t total = (size_t)case_off.back();
+  if (!b->cs) {
+    CU(cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      CU(cudaEventCreateWithFlags(&b->ready[k], cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming));
+      CHK(dalloc(&b->stage[k], total));
+    }
+  }
+  const int k = b->stage_k;
+  b->stage_k ^= 1;
+  // the previous host copy out of stage[k] has finished before the field is staged there again
+  CU(cudaStreamWaitEvent(b->s, b->done[k], 0));
+  CHK(fem_batch_get_field(b, what, b->stage[k], 1));
+  CU(cudaEventRecord(b->ready[k], b->s));
+  CU(cudaStreamWaitEvent(b->cs, b->ready[k], 0));
+  CU(cudaMemcpyAsync(host_dst, b->stage[k], sizeof(double) * total, cudaMemcpyDeviceToHost, b->cs));
+  CU(cudaEventRecord(b->done[k], b->cs));
+  return FEM_OK;
+}
+
+fem_status fem_batch_sync(fem_batch* b) {
+  g_err.clear();
+  if (!b) return fail(FEM_ERR_ARG, "batch is null");
+  if (b->cs) CU(cudaStreamSynchronize(b->cs));
+  CU(cudaStreamSynchronize(b->s));
   return FEM_OK;
 }
 

@@ -496,7 +496,8 @@ __device__ __forceinline__ void tet_acc_p(const float* re, float aM, float aK, c
 // One hex for a pair of cases, corner offsets o[] into the staged tile.  The six tets are visited around
 // the cycle of their middle corners (the diagonal corners 0 and 3 are in all six), so each middle corner's
 // values are loaded just before its first tet and its sums leave for the tile accumulator right after its
-// second: fewer values live at once than with all eight corners held through the hex.
+// second; corner 2, which closes the cycle, leaves after the first tet and is loaded again for the last,
+// so at most four corners are live at once (instead of all eight held through the hex).
 template <bool DOT>
 __device__ __forceinline__ void hex_acc_p(const float* ps, float* qs, const int (&o)[8], int rpad, const float* re,
                                           float aM, float aK, float2& hd) {
@@ -522,6 +523,7 @@ __device__ __forceinline__ void hex_acc_p(const float* ps, float* qs, const int 
                 "the visiting order follows the corner table");
   ld(0), ld(3), ld(1), ld(2);
   tet_acc_p<kHexTet[0][0], kHexTet[0][1], kHexTet[0][2], kHexTet[0][3]>(re + 0 * kRec, aM, aK, P, Q);
+  fl(2);
   ld(4);
   tet_acc_p<kHexTet[1][0], kHexTet[1][1], kHexTet[1][2], kHexTet[1][3]>(re + 1 * kRec, aM, aK, P, Q);
   fl(1);
@@ -534,6 +536,7 @@ __device__ __forceinline__ void hex_acc_p(const float* ps, float* qs, const int 
   ld(5);
   tet_acc_p<kHexTet[3][0], kHexTet[3][1], kHexTet[3][2], kHexTet[3][3]>(re + 3 * kRec, aM, aK, P, Q);
   fl(6);
+  ld(2);
   tet_acc_p<kHexTet[2][0], kHexTet[2][1], kHexTet[2][2], kHexTet[2][3]>(re + 2 * kRec, aM, aK, P, Q);
   fl(5), fl(2), fl(0), fl(3);
 }
@@ -678,7 +681,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && PK != 2) ? 2 : 1) k
     const int b = k & 1;
     const int tn = t + gridDim.x;
     if (tn < ht.n_tiles) issue(tn, b ^ 1, nd_next);
-    load_nodes(tn + gridDim.x, nd_after);
+    if constexpr (!PK) load_nodes(tn + gridDim.x, nd_after);
     const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
     const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
     if constexpr (pk) {
@@ -715,6 +718,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && PK != 2) ? 2 : 1) k
       }
       dot += (double)tdot2.x;
       dot1 += (double)tdot2.y;
+      load_nodes(tn + gridDim.x, nd_after);   // (after the items: fewer registers live through them)
     } else {
     T tdot = 0;
     const int items = nh << rshift;

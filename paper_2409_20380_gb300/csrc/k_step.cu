@@ -351,6 +351,7 @@ template <> struct CombAcc<double> {
   __device__ __forceinline__ void add(W w, double y) { s = fma(w, y, s); }
   __device__ __forceinline__ void merge(const CombAcc& o) { s += o.s; }
   __device__ __forceinline__ double get() const { return s; }
+  __device__ __forceinline__ float getf() const { return d2f(s); }
 };
 template <> struct CombAcc<float> {
   typedef float W;
@@ -359,6 +360,7 @@ template <> struct CombAcc<float> {
   __device__ __forceinline__ void add(W w, float y) { s = fmaf(w, y, s); }
   __device__ __forceinline__ void merge(const CombAcc& o) { s += o.s; }
   __device__ __forceinline__ double get() const { return (double)s; }
+  __device__ __forceinline__ float getf() const { return s; }
 };
 template <> struct CombAcc<float2> {
   typedef float2 W;
@@ -383,12 +385,18 @@ template <> struct CombAcc<float2> {
     l = __fadd_rn(__fadd_rn(l, o.l), err);
   }
   __device__ __forceinline__ double get() const { return f2d(h) + f2d(l); }
+  __device__ __forceinline__ float getf() const { return __fadd_rn(h, l); }
 };
 
 // y_out += Y w over the region's node range: the coefficients [a][case] and slot offsets in shared memory.
+// With y_base: y_out = y_base + Y w and corr32 = Y w in FP32 (the correction the guess's residual needs),
+// and outside every region range y_out = y_base, corr32 = 0: the last chunk of region R also covers the
+// nodes from its range's end to gap_hi[R] (the next range's start), block 0 the nodes before lead_hi.
 template <typename E>
-__global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* __restrict__ y_slots, int n,
-                                                         double* __restrict__ y_out, const StepCtl* ctl) {
+__global__ void __launch_bounds__(kBlock, 5) k_pred_combine(PredView p, const int* __restrict__ y_slots, int n,
+                                                         double* __restrict__ y_out, const double* __restrict__ y_base,
+                                                         float* __restrict__ corr32, const int32_t* __restrict__ gap_hi,
+                                                         int lead_hi, const StepCtl* ctl) {
   if (ctl) y_slots = ctl->ys, n = ctl->n_pairs;
   typedef typename SnapVal<E>::V T;
   typedef typename CombAcc<T>::W W;
@@ -424,7 +432,22 @@ __global__ void __launch_bounds__(kBlock) k_pred_combine(PredView p, const int* 
       }
     }
     s0.merge(s1);
-    y_out[gi] += s0.get();
+    if (y_base) {
+      y_out[gi] = y_base[gi] + s0.get();
+      corr32[gi] = s0.getf();
+    } else {
+      y_out[gi] += s0.get();
+    }
+  }
+  if (y_base) {
+    auto copy = [&](int64_t e0, int64_t e1) {
+      for (int64_t gi = e0 + threadIdx.x; gi < e1; gi += blockDim.x) {
+        y_out[gi] = y_base[gi];
+        corr32[gi] = 0.0f;
+      }
+    };
+    if (k == p.n_chunks - 1) copy(hi * 3 * rpad, (int64_t)gap_hi[R] * 3 * rpad);
+    if (blockIdx.x == 0) copy(0, (int64_t)lead_hi * 3 * rpad);
   }
 }
 
@@ -817,17 +840,21 @@ cudaError_t launch_pred_solve(const PredView& p, const int* x_slots, int n_pairs
 }
 
 cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out, cudaStream_t s,
-                                const StepCtl* ctl) {
-  if (p.n_regions == 0 || (!ctl && n_pairs <= 0)) return cudaSuccess;
+                                const StepCtl* ctl, const double* y_base, float* corr32, const int32_t* gap_hi,
+                                int lead_hi) {
+  if (p.n_regions == 0 || (!ctl && n_pairs <= 0 && !y_base)) return cudaSuccess;
+  if (y_base && (!corr32 || !gap_hi)) return cudaErrorInvalidValue;
   const int grid = p.n_regions * p.n_chunks;
+#define CMB_ARGS p, y_slots, n_pairs, y_out, y_base, corr32, gap_hi, lead_hi, ctl
   if (p.fmt == 1)
-    k_pred_combine<float><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
+    k_pred_combine<float><<<grid, kBlock, 0, s>>>(CMB_ARGS);
   else if (p.fmt == 2)
-    k_pred_combine<float2><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
+    k_pred_combine<float2><<<grid, kBlock, 0, s>>>(CMB_ARGS);
   else if (p.fmt == 3)
-    k_pred_combine<SnapHL><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
+    k_pred_combine<SnapHL><<<grid, kBlock, 0, s>>>(CMB_ARGS);
   else
-    k_pred_combine<double><<<grid, kBlock, 0, s>>>(p, y_slots, n_pairs, y_out, ctl);
+    k_pred_combine<double><<<grid, kBlock, 0, s>>>(CMB_ARGS);
+#undef CMB_ARGS
   return cudaGetLastError();
 }
 

@@ -27,7 +27,8 @@ EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_
            "fem_mesh_set_regions", "fem_ebe_apply",
            "fem_ebe_apply_noalloc",
            "pcg_solve", "fem_batch_create", "fem_batch_destroy", "fem_case_add", "fem_step", "predictor_fit",
-           "predictor_predict", "fem_case_get", "fem_batch_set_loads", "fem_batch_get_field", "fem_batch_profile",
+           "predictor_predict", "fem_case_get", "fem_batch_set_loads", "fem_batch_get_field", "fem_batch_get_field_async",
+           "fem_batch_sync", "fem_batch_profile",
            "fem_case_stats", "fem_batch_steps", "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_get_params",
            "fem_mlp_forward", "fem_mlp_loss_grad", "fem_mlp_train", "fem_batch_set_mlp", "fem_batch_collect",
            "fem_batch_collected", "fem_batch_proposal_counts", "fem_last_error")
@@ -103,6 +104,8 @@ def lib():
         "fem_case_get": (I, [P, I, I, P, I]),
         "fem_batch_set_loads": (I, [P, P]),
         "fem_batch_get_field": (I, [P, I, P, I]),
+        "fem_batch_get_field_async": (I, [P, I, P]),
+        "fem_batch_sync": (I, [P]),
         "fem_batch_profile": (I, [P, I, ctypes.POINTER(fem_profile)]),
         "fem_case_stats": (I, [P, I, ctypes.POINTER(fem_case_stats_t)]),
         "fem_batch_steps": (I, [P, ctypes.POINTER(I)]),
@@ -307,6 +310,18 @@ def fem_batch_get_field(batch, what, out):
         assert out.dtype == np.float64 and out.flags.c_contiguous
         _check(lib().fem_batch_get_field(batch, what, _np_ptr(out), 0))
     return out
+
+
+def fem_batch_get_field_async(batch, what, out):
+    """out: page-locked host torch tensor [n_cases*n_nodes*3] (float64); filled after fem_batch_sync (the copy
+    overlaps the steps queued next)."""
+    assert not out.is_cuda and out.dtype.itemsize == 8 and out.is_contiguous()
+    _check(lib().fem_batch_get_field_async(batch, what, ctypes.c_void_p(out.data_ptr())))
+    return out
+
+
+def fem_batch_sync(batch):
+    _check(lib().fem_batch_sync(batch))
 
 
 def fem_batch_profile(batch, enable=-1):

@@ -112,3 +112,42 @@ def test_graph_step_equals_eager_fused_meshes(torch_dev):
     eager = _run(meshes, srcs, 30, 0, fuse_meshes=1, cert_df=3)
     graph = _run(meshes, srcs, 30, 1, fuse_meshes=1, cert_df=3)
     _same(eager, graph)
+
+
+def test_async_field_reads_match_sync(torch_dev):
+    """fem_batch_get_field_async: each step's field, staged on the device and copied on the copy stream
+    while the next step runs, equals the synchronous read of that step (alternating pinned buffers), and
+    fused groups read the same way."""
+    torch = torch_dev
+    for fuse in (0, 1):
+        meshes = [small_mesh(6, 5, 4, h=1.0 / 64), small_mesh(5, 6, 3, h=1.0 / 64)] if fuse else \
+            [small_mesh(6, 5, 4, h=1.0 / 64)]
+        tp = wl.config2_time_params()
+        opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=8, tol=1e-8,
+                                    fuse_meshes=fuse)
+        hs = []
+        for m in meshes:
+            h = fem.fem_mesh_create(m, tp)
+            fem.fem_mesh_set_regions(h, wl.region_map(m, 64))
+            hs.append(h)
+        bt = fem.fem_batch_create(opts)
+        srcs = [wl.random_source(meshes[k % len(meshes)], wl.rng_for(97, k, 0, 2)) for k in range(3)]
+        try:
+            for k, s in enumerate(srcs):
+                fem.fem_case_add(bt, hs[k % len(hs)], s)
+            n_tot = 3 * sum(meshes[k % len(meshes)].n_nodes for k in range(len(srcs)))
+            bufs = [torch.empty(n_tot, dtype=torch.float64).pin_memory() for _ in range(2)]
+            ref = []
+            for k in range(6):
+                fem.fem_step(bt, 1, len(srcs))
+                sync = np.empty(n_tot)
+                fem.fem_batch_get_field(bt, fem.FEM_FIELD_U, sync)
+                ref.append(sync)
+                fem.fem_batch_get_field_async(bt, fem.FEM_FIELD_U, bufs[k % 2])
+            fem.fem_batch_sync(bt)
+            assert np.array_equal(bufs[0].numpy(), ref[4]) and np.array_equal(bufs[1].numpy(), ref[5])
+            assert np.abs(ref[5]).max() > 0.0
+        finally:
+            fem.fem_batch_destroy(bt)
+            for h in hs:
+                fem.fem_mesh_destroy(h)
