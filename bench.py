@@ -64,7 +64,7 @@ def parse():
                     help="predictor snapshot storage: 0 FP64, 1 FP32, 2 double-float, 3 FP32 + BF16 residual")
     ap.add_argument("--profile-steps", type=int, default=40,
                     help="steps after the timed region timed per kernel class with CUDA events (eager)")
-    ap.add_argument("--kernel", default=None, choices=["ebe"],
+    ap.add_argument("--kernel", default=None, choices=["ebe", "split"],
                     help="time one kernel alone (EBE product) instead of the full step")
     ap.add_argument("--kernel-precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=0,
@@ -671,6 +671,38 @@ def run_uneven(args):
         fem.fem_mesh_destroy(h)
 
 
+def run_split(args):
+    """Times the certification product alone (fem_mesh_split_product, form --cert) on the --dims mesh with
+    --cases cases (CUDA events, inputs resident)."""
+    import torch
+    from paper_2409_20380_gb300 import build, fem
+    from paper_2409_20380_gb300 import workload as wl
+    build.build()
+    fem.lib()
+    torch.cuda.set_device(0)
+    Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
+    mesh = wl.config2_mesh(Hx, Hy, Hz)
+    h = fem.fem_mesh_create(mesh, wl.config2_time_params())
+    r = args.cases
+    g = torch.Generator(device="cuda").manual_seed(0)
+    p = torch.randn(mesh.n_nodes * 3 * r, device="cuda", dtype=torch.float64, generator=g)
+    qM, qK = torch.empty_like(p), torch.empty_like(p)
+    for _ in range(args.warmup):
+        fem.fem_mesh_split_product(h, args.cert, p, qM, qK, r)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fem.fem_mesh_split_product(h, args.cert, p, qM, qK, r)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": "split", "form": args.cert, "dims": args.dims, "cases": r,
+                      "ms_per_launch": e0.elapsed_time(e1) / args.steps,
+                      "note": "includes the input split to double-float pairs (form 3) and the temporary copy"}),
+          flush=True)
+    fem.fem_mesh_destroy(h)
+
+
 def main():
     args = parse()
     if args.uneven:
@@ -681,6 +713,9 @@ def main():
         return
     if args.kernel == "ebe":
         run_kernel(args)
+        return
+    if args.kernel == "split":
+        run_split(args)
         return
     if args.impl == "reference":
         run_reference(args)
