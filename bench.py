@@ -64,7 +64,7 @@ def parse():
                     help="predictor snapshot storage: 0 FP64, 1 FP32, 2 double-float, 3 FP32 + BF16 residual")
     ap.add_argument("--profile-steps", type=int, default=40,
                     help="steps after the timed region timed per kernel class with CUDA events (eager)")
-    ap.add_argument("--kernel", default=None, choices=["ebe", "split"],
+    ap.add_argument("--kernel", default=None, choices=["ebe", "split", "predictor"],
                     help="time one kernel alone (EBE product) instead of the full step")
     ap.add_argument("--kernel-precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=0,
@@ -703,6 +703,48 @@ def run_split(args):
     fem.fem_mesh_destroy(h)
 
 
+def run_predictor_kernels(args):
+    """Times the predictor's ring passes alone on the --dims mesh with --cases cases and s = --s-max, after
+    --spinup steps fill the snapshot ring: predictor_fit (one Gram row per stored snapshot: s+1 launches of
+    the dot kernel) and predictor_predict (Adams-Bashforth, the Gram solves and the combination)."""
+    import torch
+    from paper_2409_20380_gb300 import build, fem
+    from paper_2409_20380_gb300 import workload as wl
+    build.build()
+    fem.lib()
+    torch.cuda.set_device(0)
+    Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
+    mesh = wl.config2_mesh(Hx, Hy, Hz)
+    tp = wl.config2_time_params()
+    h = fem.fem_mesh_create(mesh, tp)
+    fem.fem_mesh_set_regions(h, wl.region_map(mesh, args.region_nodes))
+    opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
+                                snapshot_format=args.snapshot_format, tol=1e-8, cert_df=args.cert)
+    bt = fem.fem_batch_create(opts)
+    nc = args.cases
+    for c in range(nc):
+        fem.fem_case_add(bt, h, wl.random_source(mesh, wl.rng_for(2, 0, c, 0)))
+    fem.fem_step(bt, max(args.spinup, args.s_max + 2), nc)
+    guess = torch.empty(mesh.n_nodes * 3, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        fem.predictor_fit(bt, 0)
+        fem.predictor_predict(bt, 0, guess)
+    torch.cuda.synchronize()
+    out = {"kernel": "predictor", "dims": args.dims, "cases": nc, "s_max": args.s_max,
+           "snapshot_format": args.snapshot_format}
+    for name, fn in (("fit", lambda: fem.predictor_fit(bt, 0)), ("predict", lambda: fem.predictor_predict(bt, 0, guess))):
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fn()
+        torch.cuda.synchronize()
+        out[name + "_ms"] = (time.perf_counter() - t0) * 1e3 / args.steps
+    out["dots_ms_per_row"] = out["fit_ms"] / (args.s_max + 1)
+    out["note"] = "host-timed calls (each synchronises); fit = s+1 dot-kernel launches"
+    print(json.dumps(out), flush=True)
+    fem.fem_batch_destroy(bt)
+    fem.fem_mesh_destroy(h)
+
+
 def main():
     args = parse()
     if args.uneven:
@@ -716,6 +758,9 @@ def main():
         return
     if args.kernel == "split":
         run_split(args)
+        return
+    if args.kernel == "predictor":
+        run_predictor_kernels(args)
         return
     if args.impl == "reference":
         run_reference(args)

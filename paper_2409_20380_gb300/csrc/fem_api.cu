@@ -239,8 +239,7 @@ struct fem_mesh {
   int64_t nnz = 0;
   double* Kb = nullptr;             // [nnz][3][3] stiffness blocks
   double* Mb = nullptr;             // [nnz] consistent-mass entries
-  float2* Kd = nullptr;             // (hi, lo) pairs of Kb
-  float2* Md = nullptr;             // (hi, lo) pairs of Mb
+  float2* KMd = nullptr;            // per block: the 9 (hi, lo) pairs of Kb, then the pair of Mb (80 bytes)
   double* D = nullptr;
   double* binv64 = nullptr;
   float* binv32 = nullptr;
@@ -326,24 +325,23 @@ struct fem_mesh {
     if (st == FEM_OK) st = dalloc(&col, (size_t)total);
     if (st == FEM_OK) st = dalloc(&Kb, 9 * (size_t)total);
     if (st == FEM_OK) st = dalloc(&Mb, (size_t)total);
-    if (st == FEM_OK) st = dalloc(&Kd, 9 * (size_t)total);
-    if (st == FEM_OK) st = dalloc(&Md, (size_t)total);
+    if (st == FEM_OK) st = dalloc(&KMd, 10 * (size_t)total);
     if (st == FEM_OK) st = dalloc(&missing, 1);
     if (st != FEM_OK) {
-      dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(Kd); dfree(Md); dfree(missing);
+      dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(KMd); dfree(missing);
       return st;
     }
     nnz = total;
     int h_missing = 0;
     cudaError_t e = cudaMemcpyAsync(row_ptr, rp.data(), sizeof(int32_t) * (n_nodes + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(col, cl.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_bcsr_assemble(view(), row_ptr, col, nnz, Kb, Mb, Kd, Md, missing, s);
+    if (e == cudaSuccess) e = launch_bcsr_assemble(view(), row_ptr, col, nnz, Kb, Mb, KMd, missing, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_missing, missing, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dfree(missing);
     if (e != cudaSuccess || h_missing) {
       cudaGetLastError();
-      dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(Kd); dfree(Md);
+      dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(KMd);
       row_ptr = nullptr;
       nnz = 0;
       return fail(e != cudaSuccess ? FEM_ERR_CUDA : FEM_ERR_ARG,
@@ -354,7 +352,7 @@ struct fem_mesh {
   MeshView view() const { return MeshView{N, E, conn, rec64, rec32, binv64, binv32, fm, seg, nseg}; }
   ~fem_mesh() {
     dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(rec_df); dfree(D);
-    dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(Kd); dfree(Md);
+    dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(KMd);
     dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi); dfree(reg_gap); dfree(seg); dfree(reg_cent);
     for (auto* w : ws) delete w;
     for (void* b : tile_bufs) cudaFree(b);
@@ -878,7 +876,7 @@ static cudaError_t split_product(const fem_mesh* m, int mode, int rpad, const do
   const MeshView mv = m->view();
   if (mode == 1) return launch_ebe_split_df(mv, m->rec_df, rpad, p, qM, qK, s);
   if (mode == 2 || mode == 3)
-    return launch_bcsr_split(mv, rpad, m->row_ptr, m->col, m->Kb, m->Mb, m->Kd, m->Md, p, mode == 3 ? p_df : nullptr,
+    return launch_bcsr_split(mv, rpad, m->row_ptr, m->col, m->Kb, m->Mb, m->KMd, p, mode == 3 ? p_df : nullptr,
                              qM, qK, s);
   return launch_ebe_split(mv, rpad, p, qM, qK, s);
 }

@@ -124,6 +124,9 @@ void mesh_view_of(const fem_mesh* m, MeshView* view, int* device);
 
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
 int grid_for(int64_t items, int cap = kMaxRedBlocks);
+// Grid of grid-stride kernel `fn` (blocks of `block` threads, no dynamic shared memory): at most one wave of
+// the blocks that fit on the GPU at once, so no partial second wave.
+int grid_resident(const void* fn, int block, int64_t items);
 
 cudaError_t launch_elem_setup(int64_t E, int64_t N, const double* xyz, const int4* conn, const int32_t* mat,
                               int n_mat, const double* lmr, double* rec64, float* rec32, int* err_flag,
@@ -299,15 +302,16 @@ cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pai
                                 float* corr32 = nullptr, const int32_t* gap_hi = nullptr, int lead_hi = 0);
 
 // Assembled operators for the certification product (k_bcsr.cu): K as 3x3 blocks and M as scalars on the
-// node pattern row_ptr/col.  assemble also writes the (hi, lo) FP32-pair copies Kd, Md; *missing = 1 if
-// an element pair had no slot in the pattern.
+// node pattern row_ptr/col.  assemble also writes the (hi, lo) FP32-pair copy KMd (per block the 9 pairs of
+// the K block, then the pair of the M entry: 80 bytes); *missing = 1 if an element pair had no slot in the
+// pattern.
 cudaError_t launch_bcsr_assemble(const MeshView& m, const int32_t* row_ptr, const int32_t* col, int64_t nnz,
-                                 double* Kb, double* Mb, float2* Kd, float2* Md, int* missing, cudaStream_t s);
+                                 double* Kb, double* Mb, float2* KMd, int* missing, cudaStream_t s);
 // qM = M p, qK = K p (r cases, Dirichlet rows zero).  p_df != null: double-float arithmetic (p split into
 // p_df first); else native FP64.
 cudaError_t launch_bcsr_split(const MeshView& m, int rpad, const int32_t* row_ptr, const int32_t* col,
-                              const double* Kb, const double* Mb, const float2* Kd, const float2* Md, const double* p,
-                              float2* p_df, double* qM, double* qK, cudaStream_t s);
+                              const double* Kb, const double* Mb, const float2* KMd, const double* p, float2* p_df,
+                              double* qM, double* qK, cudaStream_t s);
 
 // Graph steps (k_graph.cu): device-side step control and the conditions of the graph's loops.
 cudaError_t launch_step_begin(StepCtl* ctl, int n_slots, int s_max, double dt, int dd, long long n_fixed,

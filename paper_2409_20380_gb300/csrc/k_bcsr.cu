@@ -59,6 +59,16 @@ __global__ void k_to_df(int64_t n, const double* __restrict__ v, float2* __restr
   }
 }
 
+// The 80-byte double-float block records: KMd[10 j + 0..8] = pairs of Kb[9 j + 0..8], KMd[10 j + 9] = Mb[j].
+__global__ void k_to_kmd(int64_t nnz, const double* __restrict__ Kb, const double* __restrict__ Mb,
+                         float2* __restrict__ KMd) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 10 * nnz; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = i / 10;
+    const int r = (int)(i - 10 * j);
+    KMd[i] = d2df(r < 9 ? Kb[9 * j + r] : Mb[j]);
+  }
+}
+
 // acc (sh + sl) += (ah + al)(bh + bl): the product's rounding error by FMA, the sum's by two-sum; the low
 // word is renormalised only at the end (its own FP32 rounding is ~2^-24 of a quantity ~2^-24 smaller).
 __device__ __forceinline__ void df_fma_acc(float& sh, float& sl, float ah, float al, float bh, float bl) {
@@ -73,38 +83,44 @@ __device__ __forceinline__ void df_fma_acc(float& sh, float& sl, float ah, float
   sl = __fadd_rn(sl, __fadd_rn(err, e));
 }
 
-// qM = M p, qK = K p for r cases, one thread per (node row, case); rows of Dirichlet DOFs are zero.
+// qM = M p, qK = K p for r cases, one thread per (node row, case); rows of Dirichlet DOFs are zero.  I is
+// the index type of the vector offsets (32-bit when N * 3 * rpad fits).  A block record is 5 aligned
+// 16-byte loads.
+template <typename I>
 __global__ void __launch_bounds__(256) k_bcsr_split_df(int64_t N, int rpad, int rshift, const int32_t* __restrict__ row_ptr,
-                                                       const int32_t* __restrict__ col, const float2* __restrict__ Kd,
-                                                       const float2* __restrict__ Md, const uint8_t* __restrict__ fm,
-                                                       const float2* __restrict__ p, double* __restrict__ qM,
-                                                       double* __restrict__ qK) {
+                                                       const int32_t* __restrict__ col, const float4* __restrict__ KM,
+                                                       const uint8_t* __restrict__ fm, const float2* __restrict__ p,
+                                                       double* __restrict__ qM, double* __restrict__ qK) {
   const int64_t total = N << rshift;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n = t >> rshift;
+    const I n = (I)(t >> rshift);
     const int c = (int)(t & (rpad - 1));
     float kh[3] = {0.f, 0.f, 0.f}, kl[3] = {0.f, 0.f, 0.f}, mh[3] = {0.f, 0.f, 0.f}, ml[3] = {0.f, 0.f, 0.f};
     const int lo = __ldg(row_ptr + n), hi = __ldg(row_ptr + n + 1);
+    const float2* pc = p + c;
+    const I r3 = (I)(3 * rpad);
     for (int j = lo; j < hi; ++j) {
-      const int64_t cn = __ldg(col + j);
+      const I cn = (I)__ldg(col + j);
       float2 pv[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) pv[k] = __ldg(p + (cn * 3 + k) * rpad + c);
-      const float2 mv = __ldg(Md + j);
+      for (int k = 0; k < 3; ++k) pv[k] = __ldg(pc + cn * r3 + (I)(k * rpad));
+      const float4* rec = KM + (int64_t)j * 5;
+      const float4 q0 = __ldg(rec), q1 = __ldg(rec + 1), q2 = __ldg(rec + 2), q3 = __ldg(rec + 3), q4 = __ldg(rec + 4);
+      const float2 a[10] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                            make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w),
+                            make_float2(q3.x, q3.y), make_float2(q3.z, q3.w), make_float2(q4.x, q4.y),
+                            make_float2(q4.z, q4.w)};
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        df_fma_acc(mh[i], ml[i], mv.x, mv.y, pv[i].x, pv[i].y);
+        df_fma_acc(mh[i], ml[i], a[9].x, a[9].y, pv[i].x, pv[i].y);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const float2 a = __ldg(Kd + (int64_t)j * 9 + i * 3 + k);
-          df_fma_acc(kh[i], kl[i], a.x, a.y, pv[k].x, pv[k].y);
-        }
+        for (int k = 0; k < 3; ++k) df_fma_acc(kh[i], kl[i], a[i * 3 + k].x, a[i * 3 + k].y, pv[k].x, pv[k].y);
       }
     }
     const uint8_t f = fm[n];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const int64_t id = (n * 3 + i) * rpad + c;
+      const int64_t id = ((int64_t)n * 3 + i) * rpad + c;
       const bool fr = dof_free(f, i);
       qM[id] = fr ? f2d(mh[i]) + f2d(ml[i]) : 0.0;
       qK[id] = fr ? f2d(kh[i]) + f2d(kl[i]) : 0.0;
@@ -164,7 +180,7 @@ int grid_of(int64_t items) {
 }  // namespace
 
 cudaError_t launch_bcsr_assemble(const MeshView& m, const int32_t* row_ptr, const int32_t* col, int64_t nnz,
-                                 double* Kb, double* Mb, float2* Kd, float2* Md, int* missing, cudaStream_t s) {
+                                 double* Kb, double* Mb, float2* KMd, int* missing, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(Kb, 0, sizeof(double) * 9 * (size_t)nnz, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(Mb, 0, sizeof(double) * (size_t)nnz, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(missing, 0, sizeof(int), s);
@@ -172,10 +188,7 @@ cudaError_t launch_bcsr_assemble(const MeshView& m, const int32_t* row_ptr, cons
   k_bcsr_assemble<<<grid_of(m.E), 256, 0, s>>>(m, row_ptr, col, Kb, Mb, missing);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_to_df<<<grid_of(9 * nnz), 256, 0, s>>>(9 * nnz, Kb, Kd);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_to_df<<<grid_of(nnz), 256, 0, s>>>(nnz, Mb, Md);
+  k_to_kmd<<<grid_of(10 * nnz), 256, 0, s>>>(nnz, Kb, Mb, KMd);
   return cudaGetLastError();
 }
 
@@ -185,14 +198,18 @@ cudaError_t launch_to_df(int64_t n, const double* v, float2* out, cudaStream_t s
 }
 
 cudaError_t launch_bcsr_split(const MeshView& m, int rpad, const int32_t* row_ptr, const int32_t* col,
-                              const double* Kb, const double* Mb, const float2* Kd, const float2* Md, const double* p,
-                              float2* p_df, double* qM, double* qK, cudaStream_t s) {
+                              const double* Kb, const double* Mb, const float2* KMd, const double* p, float2* p_df,
+                              double* qM, double* qK, cudaStream_t s) {
   const int rs = lg2(rpad);
   const int64_t items = m.N << rs;
   if (p_df) {   // double-float: inputs split once per value, then the product on the FP32 pipe
     cudaError_t e = launch_to_df(m.N * 3 * rpad, p, p_df, s);
     if (e != cudaSuccess) return e;
-    k_bcsr_split_df<<<grid_of(items), 256, 0, s>>>(m.N, rpad, rs, row_ptr, col, Kd, Md, m.freemask, p_df, qM, qK);
+    const float4* km = reinterpret_cast<const float4*>(KMd);
+    if (m.N * 3 * rpad < ((int64_t)1 << 31))
+      k_bcsr_split_df<int32_t><<<grid_of(items), 256, 0, s>>>(m.N, rpad, rs, row_ptr, col, km, m.freemask, p_df, qM, qK);
+    else
+      k_bcsr_split_df<int64_t><<<grid_of(items), 256, 0, s>>>(m.N, rpad, rs, row_ptr, col, km, m.freemask, p_df, qM, qK);
   } else {
     k_bcsr_split_f64<<<grid_of(items), 256, 0, s>>>(m.N, rpad, rs, row_ptr, col, Kb, Mb, m.freemask, p, qM, qK);
   }

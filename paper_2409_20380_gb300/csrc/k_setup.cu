@@ -2,7 +2,37 @@
 // block-Jacobi preconditioner of Algorithm 1.
 #include "fem_internal.cuh"
 
+#include <mutex>
+#include <unordered_map>
+
 namespace fem {
+
+// One full wave of resident blocks for grid-stride kernels: SMs x blocks of `fn` that fit on one SM (the
+// occupancy query is made once per kernel).
+int grid_resident(const void* fn, int block, int64_t items) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  int waves;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(fn);
+    if (it == cache.end()) {
+      int dev = 0, nsm = 152, per_sm = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+      }
+      it = cache.emplace(fn, nsm * per_sm).first;
+    }
+    waves = it->second;
+  }
+  int64_t g = (items + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > waves) g = waves;
+  return (int)g;
+}
 
 int grid_for(int64_t items, int cap) {
   int64_t g = (items + kBlock - 1) / kBlock;

@@ -203,16 +203,18 @@ template <> struct RedVal<float2> {
 
 // Region R is split into p.n_chunks node ranges; block (R, k, g) accumulates, for each valid slot j of its
 // group g of kDotGrp slots, the partial dot of slot j with the newest slot over its range, per case:
-// dpart[R][k][j][c].  Slot groups keep the accumulators in registers at a useful occupancy.
-constexpr int kDotGrp = 11;
+// dpart[R][k][j][c].  Six slots a block (measured on the medium workload: 350 us a Gram row, against 412 us
+// with 11 and 635 us with 17 slots a block: fewer ring streams at once per SM read faster).
+constexpr int kDotGrp = 6;
 constexpr int kDotGroups = (kMaxSlots + kDotGrp - 1) / kDotGrp;
 template <typename E>
 __global__ void __launch_bounds__(kBlock, 3) k_pred_dots(PredView p, int slot_new, uint64_t valid_mask,
                                                          const StepCtl* ctl) {
   typedef typename SnapVal<E>::V T;
   if (ctl) slot_new = ctl->slot_new, valid_mask = ctl->mask;
-  const int R = blockIdx.x / p.n_chunks, k = blockIdx.x % p.n_chunks;
-  const int j0 = blockIdx.y * kDotGrp;
+  const int rk = blockIdx.x / kDotGroups;   // the slot groups of one chunk are neighbours in the launch order,
+  const int R = rk / p.n_chunks, k = rk % p.n_chunks;   // so their reads of the new slot's chunk share L2
+  const int j0 = (blockIdx.x % kDotGroups) * kDotGrp;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
   const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
   const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
@@ -762,7 +764,7 @@ cudaError_t launch_rhs_incr(const MeshView& m, int rpad, double dt, double a0, d
                             const double* Mv, const double* Kv, const double* Ku, double* b, const RickerSrc* src,
                             const double* ext, double t, cudaStream_t s, const StepCtl* ctl) {
   const int rs = log2i(rpad);
-  k_rhs_incr<<<grid_for(m.N << rs), kBlock, 0, s>>>(m, rpad, rs, 4.0 / dt + a0, a1, Ma, Mv, Kv, Ku, b, src, ext, t,
+  k_rhs_incr<<<grid_resident((const void*)k_rhs_incr, kBlock, m.N << rs), kBlock, 0, s>>>(m, rpad, rs, 4.0 / dt + a0, a1, Ma, Mv, Kv, Ku, b, src, ext, t,
                                                    ctl);
   return cudaGetLastError();
 }
@@ -795,20 +797,24 @@ cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, cons
                                 double* v_push, double* Ku, double* Mv, double* Kv, double* Ma, double* Av_push,
                                 void* e_push, int e_fmt, cudaStream_t s, Ring4 vr, Ring4 avr, void* ring,
                                 int64_t slot_stride, const StepCtl* ctl) {
+  const int grid = e_fmt == 1   ? grid_resident((const void*)k_newmark_incr<float>, kBlock, n)
+                   : e_fmt == 2 ? grid_resident((const void*)k_newmark_incr<float2>, kBlock, n)
+                   : e_fmt == 3 ? grid_resident((const void*)k_newmark_incr<SnapHL>, kBlock, n)
+                                : grid_resident((const void*)k_newmark_incr<double>, kBlock, n);
   if (e_fmt == 1)
-    k_newmark_incr<float><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
+    k_newmark_incr<float><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
                                                          Mv, Kv, Ma, Av_push, (float*)e_push, vr, avr, (float*)ring,
                                                          slot_stride, ctl);
   else if (e_fmt == 2)
-    k_newmark_incr<float2><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
+    k_newmark_incr<float2><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
                                                           Mv, Kv, Ma, Av_push, (float2*)e_push, vr, avr, (float2*)ring,
                                                           slot_stride, ctl);
   else if (e_fmt == 3)
-    k_newmark_incr<SnapHL><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
+    k_newmark_incr<SnapHL><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
                                                           Mv, Kv, Ma, Av_push, (SnapHL*)e_push, vr, avr, (SnapHL*)ring,
                                                           slot_stride, ctl);
   else
-    k_newmark_incr<double><<<grid_for(n), kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
+    k_newmark_incr<double><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
                                                           Mv, Kv, Ma, Av_push, (double*)e_push, vr, avr, (double*)ring,
                                                           slot_stride, ctl);
   return cudaGetLastError();
@@ -817,7 +823,7 @@ cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, cons
 cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mask, cudaStream_t s,
                              const StepCtl* ctl) {
   if (p.n_regions == 0) return cudaSuccess;
-  const dim3 grid(p.n_regions * p.n_chunks, kDotGroups);
+  const dim3 grid(p.n_regions * p.n_chunks * kDotGroups);
   if (p.fmt == 1)
     k_pred_dots<float><<<grid, kBlock, 0, s>>>(p, slot_new, valid_mask, ctl);
   else if (p.fmt == 2)
