@@ -267,6 +267,14 @@ fem_status fem_case_add(fem_batch* b, fem_mesh* m, int32_t src_node, const doubl
 fem_status fem_step(fem_batch* b, int n_steps, int* iters_out, double* relres_out);
 
 /*
+ * fem_step without waiting for the GPU (a library service; the paper has none): queues n_steps on the
+ * batch stream and returns (graph steps need no host round trip; steps that cannot run as a graph still
+ * wait inside).  Statistics and status of these steps accumulate: fem_batch_sync returns their worst
+ * status, and the next fem_step's iters_out / relres_out / status include them.
+ */
+fem_status fem_step_async(fem_batch* b, int n_steps);
+
+/*
  * Refreshes the predictor of case `case_id` from its stored snapshots: recomputes the per-region Gram
  * matrices of the stored corrections from scratch (Section 3.2: the orthogonal decomposition of the
  * stored inputs X), replacing the incrementally updated ones.
@@ -306,7 +314,8 @@ fem_status fem_batch_get_field(fem_batch* b, int what, double* dst, int on_devic
  */
 fem_status fem_batch_get_field_async(fem_batch* b, int what, double* host_dst);
 
-/* Waits until the batch stream and every asynchronous field copy have finished. */
+/* Waits until the batch stream and every asynchronous field copy have finished; returns the worst status
+ * of the steps queued by fem_step_async since the last report (FEM_OK, FEM_ERR_NOT_CONVERGED, ...). */
 fem_status fem_batch_sync(fem_batch* b);
 
 /* Device-time profile of fem_step, measured with CUDA events on the batch stream. */

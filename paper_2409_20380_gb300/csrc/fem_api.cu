@@ -691,6 +691,7 @@ struct fem_batch {
   cudaEvent_t ready[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
   double* stage[2] = {nullptr, nullptr};
   int stage_k = 0;
+  fem_status pending = FEM_OK;         // worst status of eagerly run steps queued by fem_step_async
   ~fem_batch() {
     for (auto* g : groups) delete g;
     if (cs) cudaStreamSynchronize(cs);
@@ -1593,6 +1594,11 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
   if (n_nodes < (int64_t(1) << 28) && detect_hex_patches(conn, n_elems)) {
     const int sizes[fem_mesh::kNTile] = {64, 128, 256, 512};
     bool ok = true;
+    double abs_m = 0.0, abs_k = 0.0;   // scale bounds of the packed kernel's fixed-point tile sums
+    {
+      cudaError_t ce = elem_abs_row_bounds(m->view(), &abs_m, &abs_k, s);
+      if (ce != cudaSuccess) return bail(fail(FEM_ERR_CUDA, std::string("row bounds: ") + cudaGetErrorString(ce)));
+    }
     for (int i = 0; i < fem_mesh::kNTile && ok; ++i) {
       HexTilesHost th;
       if (!build_hex_tiles(conn, n_elems, n_nodes, sizes[i], &th)) continue;
@@ -1620,6 +1626,9 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
       t.tile_node_off = d_noff;
       t.tile_nodes = d_nodes;
       t.hex_local = d_loc;
+      // (rounded up to FP32 and given 1% more for the FP32 rounding of the records and products)
+      t.abs_m = (float)(abs_m * 1.01);
+      t.abs_k = (float)(abs_k * 1.01);
     }
     if (!ok) return bail(fail(FEM_ERR_OOM, "tile allocation failed"));
     m->hex = true;
@@ -1953,10 +1962,6 @@ fem_status fem_step(fem_batch* b, int n_steps, int* iters_out, double* relres_ou
   if (!b) return fail(FEM_ERR_ARG, "batch is null");
   if (n_steps < 0) return fail(FEM_ERR_ARG, "n_steps < 0");
   CHK(batch_start(b));
-  for (auto* g : b->groups) {
-    std::fill(g->iters_acc.begin(), g->iters_acc.end(), 0);
-    std::fill(g->relres_max.begin(), g->relres_max.end(), 0.0);
-  }
   fem_status worst = FEM_OK;
   for (int k = 0; k < n_steps; ++k) {
     for (auto* g : b->groups) CHK(group_step(b, g, &worst));
@@ -1969,13 +1974,35 @@ fem_status fem_step(fem_batch* b, int n_steps, int* iters_out, double* relres_ou
     CU(ebe_tma_timeout(&tmo));
     if (tmo) return fail(FEM_ERR_TIMEOUT, "fem_step: an EBE kernel's wait for its tile copies timed out");
   }
+  // the statistics since the last report (this call's steps and any queued by fem_step_async)
   for (size_t c = 0; c < b->loc.size(); ++c) {
     const Group* g = b->groups[b->loc[c].first];
     const int l = b->loc[c].second;
     if (iters_out) iters_out[c] = g->iters_acc[l];
     if (relres_out) relres_out[c] = g->relres_max[l];
   }
+  for (auto* g : b->groups) {
+    std::fill(g->iters_acc.begin(), g->iters_acc.end(), 0);
+    std::fill(g->relres_max.begin(), g->relres_max.end(), 0.0);
+  }
+  if (b->pending != FEM_OK && (worst == FEM_OK || b->pending < worst)) worst = b->pending;
+  b->pending = FEM_OK;
   if (worst != FEM_OK) return fail(worst, "fem_step: a case did not converge or broke down");
+  return FEM_OK;
+}
+
+fem_status fem_step_async(fem_batch* b, int n_steps) {
+  g_err.clear();
+  if (!b) return fail(FEM_ERR_ARG, "batch is null");
+  if (n_steps < 0) return fail(FEM_ERR_ARG, "n_steps < 0");
+  CHK(batch_start(b));
+  fem_status worst = FEM_OK;   // (steps that run eagerly report here; graph steps on the device)
+  for (int k = 0; k < n_steps; ++k) {
+    for (auto* g : b->groups) CHK(group_step(b, g, &worst));
+    b->steps += 1;
+    if (b->prof.on) b->prof.steps += 1;
+  }
+  if (worst != FEM_OK && (b->pending == FEM_OK || worst < b->pending)) b->pending = worst;
   return FEM_OK;
 }
 
@@ -2204,6 +2231,15 @@ fem_status fem_batch_sync(fem_batch* b) {
   if (!b) return fail(FEM_ERR_ARG, "batch is null");
   if (b->cs) CU(cudaStreamSynchronize(b->cs));
   CU(cudaStreamSynchronize(b->s));
+  fem_status worst = b->pending;
+  b->pending = FEM_OK;
+  if (b->started) {
+    for (auto* g : b->groups) CHK(group_graph_stats(b, g, &worst));
+    int tmo = 0;
+    CU(ebe_tma_timeout(&tmo));
+    if (tmo) return fail(FEM_ERR_TIMEOUT, "fem_batch_sync: an EBE kernel's wait for its tile copies timed out");
+  }
+  if (worst != FEM_OK) return fail(worst, "fem_batch_sync: a case did not converge or broke down");
   return FEM_OK;
 }
 

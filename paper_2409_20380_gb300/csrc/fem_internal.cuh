@@ -44,6 +44,9 @@ struct HexTiles {                    // device view
   const int* tile_node_off = nullptr;
   const int* tile_nodes = nullptr;   // per entry: node id (bits 0-27), free-DOF bits (28-30), shared (31)
   const uint4* hex_local = nullptr;  // 8 x uint16 per hex
+  // largest element-wise absolute row sums over the nodes: sum over the elements e of a node i and over j
+  // of |M^e_ij| and |K^e_ij| (bounds on any partial sum of a product's element contributions to a row)
+  float abs_m = 0.0f, abs_k = 0.0f;
 };
 bool detect_hex_patches(const int32_t* conn, int64_t E);
 bool build_hex_tiles(const int32_t* conn, int64_t E, int64_t N, int hex_per_tile, HexTilesHost* out);
@@ -124,6 +127,8 @@ void mesh_view_of(const fem_mesh* m, MeshView* view, int* device);
 
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
 int grid_for(int64_t items, int cap = kMaxRedBlocks);
+// Largest element-wise absolute row sums of M and K over the mesh's nodes (see HexTiles::abs_m).
+cudaError_t elem_abs_row_bounds(const MeshView& m, double* abs_m, double* abs_k, cudaStream_t s);
 // Grid of grid-stride kernel `fn` (blocks of `block` threads, no dynamic shared memory): at most one wave of
 // the blocks that fit on the GPU at once, so no partial second wave.
 int grid_resident(const void* fn, int block, int64_t items);

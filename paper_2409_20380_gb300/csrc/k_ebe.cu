@@ -499,8 +499,8 @@ __device__ __forceinline__ void tet_acc_p(const float* re, float aM, float aK, c
 // second; corner 2, which closes the cycle, leaves after the first tet and is loaded again for the last,
 // so at most four corners are live at once (instead of all eight held through the hex).
 template <bool DOT>
-__device__ __forceinline__ void hex_acc_p(const float* ps, float* qs, const int (&o)[8], int rpad, const float* re,
-                                          float aM, float aK, float2& hd) {
+__device__ __forceinline__ void hex_acc_p(const float* ps, int* qs, const int (&o)[8], int rpad, const float* re,
+                                          float aM, float aK, float2 sinv, float2& hd) {
   float2 P[8][3], Q[8][3];
   auto ld = [&](int sl) {
 #pragma unroll
@@ -509,13 +509,17 @@ __device__ __forceinline__ void hex_acc_p(const float* ps, float* qs, const int 
       Q[sl][k] = make_float2(0.f, 0.f);
     }
   };
+  // corner sums leave in fixed point: Q scaled by the tile's power of two sinv, rounded to integers and
+  // added by native integer shared-memory atomics (a float atomic add on shared memory is a compare-and-
+  // swap loop)
   auto fl = [&](int sl) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       if (DOT) hd = fma2(P[sl][k], Q[sl][k], hd);
-      float* d = qs + o[sl] + k * rpad;
-      atomicAdd(d, Q[sl][k].x);
-      atomicAdd(d + 1, Q[sl][k].y);
+      int* d = qs + o[sl] + k * rpad;
+      const float2 v = mul2(Q[sl][k], sinv);
+      atomicAdd(d, __float2int_rn(v.x));
+      atomicAdd(d + 1, __float2int_rn(v.y));
     }
   };
   static_assert(kHexTet[0][1] == 1 && kHexTet[0][2] == 2 && kHexTet[1][3] == 4 && kHexTet[4][1] == 7 &&
@@ -562,7 +566,7 @@ __host__ __device__ inline StagedLayout staged_layout(int nloc_max, int rpad, in
   const size_t recs = up(sizeof(T) * (size_t)hex_per_tile * 6 * kRec);
   const size_t nodes = up(sizeof(int) * (size_t)nloc_max);
   L.bar = 0;
-  L.qs = 128;
+  L.qs = 512;   // head: 2 mbarriers, then (packed kernel) per-case |p| maxima x2 and scales
   L.ps0 = L.qs + vals;
   L.ps1 = L.ps0 + vals;
   L.rec0 = L.ps1 + vals;
@@ -592,14 +596,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                "l"(gmem_u64(src)), "r"(bytes), "r"(bar)
                : "memory");
 }
-// Bounded wait for phase `parity` of the barrier; false if it did not complete.
+// Bounded wait for phase `parity` of the barrier; false if it did not complete.  Each try may suspend the
+// thread for up to 1 us (instead of spinning on the issue slots the other block of the SM computes with);
+// at most 2^20 tries, about a second.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   for (int i = 0; i < (1 << 20); ++i) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(1000u)
         : "memory");
     if (ok) return true;
   }
@@ -675,6 +681,41 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && PK != 2) ? 2 : 1) k
     load_nodes(t0 + gridDim.x, nd_next);
     if (t0 < ht.n_tiles) issue(t0, 0, nd0);
   }
+  // packed: fixed-point tile sums.  Per tile and case c the scale is 2^(30 - E_c) with 2^E_c >= bound_c =
+  // (|aM| abs_m + |aK| abs_k) max |p_c| over the tile's nodes, which bounds every partial sum of element
+  // contributions to a tile node's row: the integer sums stay below 2^30, and the rounding of the sums is
+  // below 2^-31 bound_c per contribution.  spm[2][32]: the per-case maxima (|p| bit patterns, ordered as
+  // integers), one buffer per tile parity; sfwd[32]: 2^(E_c - 30), the factors back to floating point.
+  int* spm = reinterpret_cast<int*>(smem_raw + 32);
+  float* sfwd = reinterpret_cast<float*>(smem_raw + 288);
+  const float bco = fabsf((float)aM) * ht.abs_m + fabsf((float)aK) * ht.abs_k;
+  if constexpr (pk) {   // the tile accumulator starts zeroed; each flush zeroes what it reads
+    for (int i = threadIdx.x; i < (ht.nloc_max * per_node) >> 2; i += blockDim.x)
+      reinterpret_cast<float4*>(qs)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if ((int)threadIdx.x < 2 * 32) spm[threadIdx.x] = 0;
+  }
+  // packed: the case pairs with an active case (inner iterations; all pairs otherwise), nap of them, laid
+  // on napw >= nap item slots (a power of two, so a thread's slot, and pair, is fixed); a converged pair's
+  // product is not needed (its step length is zero)
+  uint32_t pmask = 0;
+  int nap = 0, napw = 1, lgw = 0, mypair = -1;
+  if constexpr (pk) {
+    const int npair = rpad >> 1;
+    if (DOT && sc) {
+      for (int pr = 0; pr < npair; ++pr)
+        if (sc[2 * pr].active || sc[2 * pr + 1].active) pmask |= 1u << pr;
+    } else {
+      pmask = npair >= 32 ? 0xffffffffu : ((1u << npair) - 1u);
+    }
+    nap = __popc(pmask);
+    while (napw < nap) napw <<= 1, ++lgw;
+    const int slot = threadIdx.x & (napw - 1);
+    if (slot < nap) {   // the slot-th active pair
+      uint32_t m = pmask;
+      for (int q = 0; q < slot; ++q) m &= m - 1;
+      mypair = __ffs(m) - 1;
+    }
+  }
   for (int k = 0;; ++k) {
     const int t = t0 + k * gridDim.x;
     if (t >= ht.n_tiles) break;
@@ -684,10 +725,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && PK != 2) ? 2 : 1) k
     if constexpr (!PK) load_nodes(tn + gridDim.x, nd_after);
     const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
     const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
-    if constexpr (pk) {
-      for (int i = threadIdx.x; i < (nl * per_node) >> 2; i += blockDim.x)
-        reinterpret_cast<float4*>(qs)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
+    if constexpr (!pk) {   // (the packed flush leaves the accumulator zeroed behind it)
       for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) qs[i] = (T)0;
     }
     const uint32_t bar = smem_u32(mbar + b);
@@ -699,22 +737,42 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && PK != 2) ? 2 : 1) k
     const T* ps = psb(b);
     const T* sr = srb(b);
     const int* snode = snb(b);
+    float2 sinv = make_float2(1.f, 1.f);
     if constexpr (pk) {
-      // items (hex, case pair); a thread's pair is fixed (blockDim.x is a multiple of rpad / 2)
-      const int rs1 = rshift - 1, pm = (rpad >> 1) - 1;
-      const int items = nh << rs1;
+      // per-case largest |p| of the staged tile (a thread's values all belong to case threadIdx.x mod rpad)
+      const float* pf = reinterpret_cast<const float*>(ps);
+      float mx = 0.f;
+      for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) mx = fmaxf(mx, fabsf(pf[i]));
+      for (int off = 16; off >= rpad; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      int* spm_b = spm + (b << 5);
+      if ((int)(threadIdx.x & 31) < rpad) atomicMax(spm_b + (threadIdx.x & 31), __float_as_int(mx));
+      if ((int)threadIdx.x < rpad) spm[((b ^ 1) << 5) + threadIdx.x] = 0;   // the next tile's buffer
+      __syncthreads();
+      // E_c: the exponent field of bound_c gives bound_c < 2^(field - 126)
+      auto expo = [&](int c) {
+        const uint32_t f = (__float_as_uint(bco * __int_as_float(spm_b[c])) >> 23) & 0xffu;
+        return f == 0u ? -126 : (int)f - 126;
+      };
+      auto pow2 = [](int e) { return __uint_as_float((uint32_t)min(max(e + 127, 1), 254) << 23); };
+      if (mypair >= 0) sinv = make_float2(pow2(30 - expo(2 * mypair)), pow2(30 - expo(2 * mypair + 1)));
+      if ((int)threadIdx.x < rpad) sfwd[threadIdx.x] = pow2(expo(threadIdx.x) - 30);
+    }
+    if constexpr (pk) {
+      // items (hex, active-pair slot); a thread's slot and pair are fixed (blockDim.x is a multiple of napw)
+      const int items = mypair >= 0 ? nh << lgw : 0;
+      const int c0 = mypair << 1;
       float2 tdot2 = make_float2(0.f, 0.f);
-      uint4 lw_next = (int)threadIdx.x < items ? __ldg(ht.hex_local + h0 + (threadIdx.x >> rs1)) : make_uint4(0, 0, 0, 0);
+      uint4 lw_next = (int)threadIdx.x < items ? __ldg(ht.hex_local + h0 + (threadIdx.x >> lgw)) : make_uint4(0, 0, 0, 0);
       for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int hl = it >> rs1, c0 = (it & pm) << 1;
+        const int hl = it >> lgw;
         const uint4 lw = lw_next;
-        if (it + (int)blockDim.x < items) lw_next = __ldg(ht.hex_local + h0 + ((it + blockDim.x) >> rs1));
+        if (it + (int)blockDim.x < items) lw_next = __ldg(ht.hex_local + h0 + ((it + blockDim.x) >> lgw));
         const int o[8] = {(int)(lw.x & 0xffff) * per_node + c0, (int)(lw.x >> 16) * per_node + c0,
                           (int)(lw.y & 0xffff) * per_node + c0, (int)(lw.y >> 16) * per_node + c0,
                           (int)(lw.z & 0xffff) * per_node + c0, (int)(lw.z >> 16) * per_node + c0,
                           (int)(lw.w & 0xffff) * per_node + c0, (int)(lw.w >> 16) * per_node + c0};
-        hex_acc_p<DOT>(reinterpret_cast<const float*>(ps), reinterpret_cast<float*>(qs), o, rpad,
-                       reinterpret_cast<const float*>(sr) + hl * 6 * kRec, (float)aM, (float)aK, tdot2);
+        hex_acc_p<DOT>(reinterpret_cast<const float*>(ps), reinterpret_cast<int*>(qs), o, rpad,
+                       reinterpret_cast<const float*>(sr) + hl * 6 * kRec, (float)aM, (float)aK, sinv, tdot2);
       }
       dot += (double)tdot2.x;
       dot1 += (double)tdot2.y;
@@ -779,7 +837,11 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && PK != 2) ? 2 : 1) k
         const int64_t g = raw & 0x0fffffff;
         const bool fixed = !dof_free((uint8_t)((raw >> 28) & 7), kk);
         float4* dst = reinterpret_cast<float4*>(q + g * per_node) + (i - l * f4);
-        const float4 v = reinterpret_cast<const float4*>(qs)[i];
+        const int4 vi = reinterpret_cast<const int4*>(qs)[i];
+        const int c4 = (i << 2) & (rpad - 1);   // the four cases of this piece: c4 .. c4 + 3
+        const float4 v = make_float4((float)vi.x * sfwd[c4], (float)vi.y * sfwd[c4 + 1], (float)vi.z * sfwd[c4 + 2],
+                                     (float)vi.w * sfwd[c4 + 3]);
+        reinterpret_cast<int4*>(qs)[i] = make_int4(0, 0, 0, 0);
         if (raw < 0) {
           if (!fixed) atomicAdd(dst, v);
         } else {
@@ -808,16 +870,30 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && PK != 2) ? 2 : 1) k
     if (seg) {
       if (block_reduce_last_seg<1>(sacc, m.nseg, red)) ebe_tail_seg(red, sc, ptq_out, m.nseg);
     } else if constexpr (pk) {
-      // pair sums over the warp's hexes, then lane c < rpad takes case c (the layout of the block reduction)
-      const int lane = threadIdx.x & 31, half = rpad >> 1;
+      // slot sums over the warp's hexes, then over the warps (through the idle record buffer), then thread
+      // c < rpad takes case c (the layout of the block reduction); converged pairs give 0
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
       double d0 = dot, d1 = dot1;
-      for (int off = half; off < 32; off <<= 1) {
+      for (int off = napw; off < 32; off <<= 1) {
         d0 += __shfl_xor_sync(0xffffffffu, d0, off);
         d1 += __shfl_xor_sync(0xffffffffu, d1, off);
       }
-      const double a = __shfl_sync(0xffffffffu, d0, (lane >> 1) & (half - 1));
-      const double bb = __shfl_sync(0xffffffffu, d1, (lane >> 1) & (half - 1));
-      double v[1] = {lane < rpad ? ((lane & 1) ? bb : a) : 0.0};
+      double* spair = reinterpret_cast<double*>(smem_raw + L.rec0);   // [warp][16 slots][2]
+      __syncthreads();
+      if (lane < napw) {
+        spair[(warp * 16 + lane) * 2] = d0;
+        spair[(warp * 16 + lane) * 2 + 1] = d1;
+      }
+      __syncthreads();
+      double vc = 0.0;
+      if ((int)threadIdx.x < rpad) {
+        const int pr = threadIdx.x >> 1;
+        if ((pmask >> pr) & 1u) {
+          const int sl = __popc(pmask & ((1u << pr) - 1u));
+          for (int w = 0; w < nw; ++w) vc += spair[(w * 16 + sl) * 2 + (threadIdx.x & 1)];
+        }
+      }
+      double v[1] = {vc};
       if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
     } else {
       double v[1] = {dot};

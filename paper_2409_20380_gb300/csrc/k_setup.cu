@@ -3,6 +3,8 @@
 #include "fem_internal.cuh"
 
 #include <mutex>
+#include <vector>
+#include <algorithm>
 #include <unordered_map>
 
 namespace fem {
@@ -182,6 +184,60 @@ cudaError_t launch_binv(int64_t N, const double* D, const uint8_t* freemask, dou
                         int* err_flag, cudaStream_t s) {
   k_binv<<<grid_for(N, 152 * 16), kBlock, 0, s>>>(N, D, freemask, binv64, binv32, err_flag);
   return cudaGetLastError();
+}
+
+// Per-node element-wise absolute row sums: for local node a and component i of element e,
+// sum_b sum_k |K^e_ab[i][k]| with K^e_ab = lambdaV g_a g_b^T + muV (g_a . g_b) I + muV g_b g_a^T, and
+// sum_b |M^e_ab| = 5 rho V / 20 (M^e_ab = rho V / 20 (1 + delta_ab) I).
+__global__ void k_abs_rows(MeshView m, double* __restrict__ mrow, double* __restrict__ krow) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m.E; e += (int64_t)gridDim.x * blockDim.x) {
+    const double* r = m.rec64 + e * kRec;
+    double g[4][3];
+    for (int k = 0; k < 3; ++k) {
+      g[1][k] = r[k];
+      g[2][k] = r[3 + k];
+      g[3][k] = r[6 + k];
+      g[0][k] = -(g[1][k] + g[2][k] + g[3][k]);
+    }
+    const double lam = r[9], mu = r[10], ms = r[11];
+    const int4 cn = m.conn[e];
+    const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
+    for (int a = 0; a < 4; ++a)
+      for (int i = 0; i < 3; ++i) {
+        double ks = 0.0;
+        for (int b = 0; b < 4; ++b) {
+          const double gab = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+          for (int k = 0; k < 3; ++k) ks += fabs(lam * g[a][i] * g[b][k] + mu * g[b][i] * g[a][k] + (i == k ? mu * gab : 0.0));
+        }
+        atomicAdd(krow + (int64_t)nd[a] * 3 + i, ks);
+        atomicAdd(mrow + (int64_t)nd[a] * 3 + i, 5.0 * fabs(ms));
+      }
+  }
+}
+
+cudaError_t elem_abs_row_bounds(const MeshView& m, double* abs_m, double* abs_k, cudaStream_t s) {
+  double *mrow = nullptr, *krow = nullptr;
+  const size_t n = (size_t)m.N * 3;
+  cudaError_t e = cudaMalloc(&mrow, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&krow, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mrow, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(krow, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess) {
+    k_abs_rows<<<grid_for(m.E), kBlock, 0, s>>>(m, mrow, krow);
+    e = cudaGetLastError();
+  }
+  std::vector<double> hm(n), hk(n);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), mrow, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hk.data(), krow, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(mrow);
+  cudaFree(krow);
+  if (e != cudaSuccess) return e;
+  double bm = 0.0, bk = 0.0;
+  for (size_t i = 0; i < n; ++i) bm = std::max(bm, hm[i]), bk = std::max(bk, hk[i]);
+  *abs_m = bm;
+  *abs_k = bk;
+  return cudaSuccess;
 }
 
 }  // namespace fem

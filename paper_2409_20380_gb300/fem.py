@@ -28,7 +28,7 @@ EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_
            "fem_ebe_apply_noalloc",
            "pcg_solve", "fem_batch_create", "fem_batch_destroy", "fem_case_add", "fem_step", "predictor_fit",
            "predictor_predict", "fem_case_get", "fem_batch_set_loads", "fem_batch_get_field", "fem_batch_get_field_async",
-           "fem_batch_sync", "fem_batch_profile",
+           "fem_batch_sync", "fem_step_async", "fem_batch_profile",
            "fem_case_stats", "fem_batch_steps", "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_get_params",
            "fem_mlp_forward", "fem_mlp_loss_grad", "fem_mlp_train", "fem_batch_set_mlp", "fem_batch_collect",
            "fem_batch_collected", "fem_batch_proposal_counts", "fem_last_error")
@@ -106,6 +106,7 @@ def lib():
         "fem_batch_get_field": (I, [P, I, P, I]),
         "fem_batch_get_field_async": (I, [P, I, P]),
         "fem_batch_sync": (I, [P]),
+        "fem_step_async": (I, [P, I]),
         "fem_batch_profile": (I, [P, I, ctypes.POINTER(fem_profile)]),
         "fem_case_stats": (I, [P, I, ctypes.POINTER(fem_case_stats_t)]),
         "fem_batch_steps": (I, [P, ctypes.POINTER(I)]),
@@ -320,8 +321,17 @@ def fem_batch_get_field_async(batch, what, out):
     return out
 
 
-def fem_batch_sync(batch):
-    _check(lib().fem_batch_sync(batch))
+def fem_batch_sync(batch, raise_on_error=True):
+    """Waits for the batch (steps and field copies); returns the worst status of fem_step_async's steps."""
+    st = lib().fem_batch_sync(batch)
+    if raise_on_error:
+        _check(st)
+    return st
+
+
+def fem_step_async(batch, n_steps):
+    """Queues n_steps without waiting; fem_batch_sync reports their status."""
+    _check(lib().fem_step_async(batch, n_steps))
 
 
 def fem_batch_profile(batch, enable=-1):

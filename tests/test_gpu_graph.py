@@ -151,3 +151,41 @@ def test_async_field_reads_match_sync(torch_dev):
             fem.fem_batch_destroy(bt)
             for h in hs:
                 fem.fem_mesh_destroy(h)
+
+
+def test_step_async_matches_step(torch_dev):
+    """fem_step_async queues graph steps without host waits; after fem_batch_sync the fields match a run
+    of fem_step within the run-to-run envelope, the statistics of the queued steps reach the next
+    fem_step's outputs, and the status is reported by fem_batch_sync."""
+    m = small_mesh(6, 5, 4, h=1.0 / 64)
+    tp = wl.config2_time_params()
+    srcs = [wl.random_source(m, wl.rng_for(98, 0, c, 2)) for c in range(3)]
+
+    def run(async_steps):
+        h = fem.fem_mesh_create(m, tp)
+        fem.fem_mesh_set_regions(h, wl.region_map(m, 64))
+        bt = fem.fem_batch_create(fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD,
+                                                       s_max=8, tol=1e-8))
+        try:
+            for s in srcs:
+                fem.fem_case_add(bt, h, s)
+            if async_steps:
+                for _ in range(24):
+                    fem.fem_step_async(bt, 1)
+                assert fem.fem_batch_sync(bt) == fem.FEM_OK
+                st, it, rr = fem.fem_step(bt, 1, len(srcs))     # its outputs include the queued steps
+            else:
+                st, it, rr = fem.fem_step(bt, 25, len(srcs))
+            u = np.empty(3 * m.n_nodes * len(srcs))
+            fem.fem_batch_get_field(bt, fem.FEM_FIELD_U, u)
+            assert fem.fem_batch_steps(bt) == 25
+            return st, it, rr, u
+        finally:
+            fem.fem_batch_destroy(bt)
+            fem.fem_mesh_destroy(h)
+
+    a, b = run(True), run(False)
+    assert a[0] == b[0] == fem.FEM_OK
+    assert np.abs(a[1] - b[1]).max() <= 25 and abs(int(a[1].sum()) - int(b[1].sum())) <= 0.02 * b[1].sum() + 2
+    assert np.all(a[2] < 1e-8) and np.all(b[2] < 1e-8)
+    assert np.linalg.norm(a[3] - b[3]) <= 1e-7 * np.linalg.norm(b[3])
