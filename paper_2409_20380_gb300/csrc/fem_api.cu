@@ -2218,7 +2218,15 @@ fem_status fem_batch_get_field_async(fem_batch* b, int what, double* host_dst) {
   b->stage_k ^= 1;
   // the previous host copy out of stage[k] has finished before the field is staged there again
   CU(cudaStreamWaitEvent(b->s, b->done[k], 0));
-  CHK(fem_batch_get_field(b, what, b->stage[k], 1));
+  const Group* g0 = b->groups[0];
+  bool direct = b->groups.size() == 1 && !g0->owned_mesh;   // one multi-case group, cases in lane order
+  for (size_t c = 0; direct && c < b->loc.size(); ++c) direct = b->loc[c].second == (int)c;
+  if (direct && (what == FEM_FIELD_U || what == FEM_FIELD_A || what == FEM_FIELD_DU)) {
+    const double* src = what == FEM_FIELD_U ? g0->u : what == FEM_FIELD_A ? g0->a : g0->x;
+    CU(launch_extract_all(g0->mesh->N, g0->rpad, (int)g0->cases.size(), src, b->stage[k], b->s));
+  } else {
+    CHK(fem_batch_get_field(b, what, b->stage[k], 1));
+  }
   CU(cudaEventRecord(b->ready[k], b->s));
   CU(cudaStreamWaitEvent(b->cs, b->ready[k], 0));
   CU(cudaMemcpyAsync(host_dst, b->stage[k], sizeof(double) * total, cudaMemcpyDeviceToHost, b->cs));

@@ -496,18 +496,20 @@ __device__ __forceinline__ bool block_reduce_last(double (&vals)[NQ], int rpad, 
   if (S * V > (kVecBlock / 32) * NQ * 32) S = (kVecBlock / 32) * NQ * 32 / V;
   if (threadIdx.x < S * V) {
     const int v = threadIdx.x % V, sl = threadIdx.x / V;
-    // four independent chains so the L2 loads overlap; fixed assignment keeps the sum deterministic
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    // eight loads in flight per round so the L2 latency is paid few times; fixed assignment keeps the sum
+    // deterministic
+    double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     int b = sl;
     const int nb = (int)gridDim.x;
-    for (; b + 3 * S < nb; b += 4 * S) {
-      a0 += __ldcg(red.partial + (size_t)b * V + v);
-      a1 += __ldcg(red.partial + (size_t)(b + S) * V + v);
-      a2 += __ldcg(red.partial + (size_t)(b + 2 * S) * V + v);
-      a3 += __ldcg(red.partial + (size_t)(b + 3 * S) * V + v);
+    for (; b + 7 * S < nb; b += 8 * S) {
+      double t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = __ldcg(red.partial + (size_t)(b + u * S) * V + v);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] += t[u];
     }
-    for (; b < nb; b += S) a0 += __ldcg(red.partial + (size_t)b * V + v);
-    flat[sl * V + v] = (a0 + a1) + (a2 + a3);
+    for (int u = 0; b < nb; b += S, ++u) a[u & 7] += __ldcg(red.partial + (size_t)b * V + v);
+    flat[sl * V + v] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   }
   __syncthreads();
   if (threadIdx.x < V) {

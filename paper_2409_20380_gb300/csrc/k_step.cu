@@ -500,12 +500,13 @@ __global__ void k_extract_case(int64_t n3, int rpad, int c, const double* __rest
     dst[i] = src[i * rpad + c];
 }
 
+// dst[c][j] = src[j][c]: a thread reads one node component's row of cases (its neighbours the adjacent
+// rows, so the reads stay in the same cache lines) and writes it out case by case, coalesced per case.
 __global__ void k_extract_all(int64_t n3, int rpad, int n_cases, const double* __restrict__ src,
                               double* __restrict__ dst) {
-  const int64_t total = n3 * n_cases;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = i / n3, j = i - c * n3;
-    dst[i] = src[j * rpad + c];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n3; j += (int64_t)gridDim.x * blockDim.x) {
+    const double* row = src + j * rpad;
+    for (int c = 0; c < n_cases; ++c) dst[c * n3 + j] = row[c];
   }
 }
 
@@ -708,7 +709,7 @@ cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, 
 }
 
 cudaError_t launch_extract_all(int64_t N, int rpad, int n_cases, const double* src, double* dst, cudaStream_t s) {
-  k_extract_all<<<grid_for(N * 3 * n_cases, 152 * 16), kBlock, 0, s>>>(N * 3, rpad, n_cases, src, dst);
+  k_extract_all<<<grid_for(N * 3, 152 * 16), kBlock, 0, s>>>(N * 3, rpad, n_cases, src, dst);
   return cudaGetLastError();
 }
 
