@@ -3,6 +3,8 @@
 // All vectors are [N][3][rpad] FP64 unless stated.
 #include "fem_internal.cuh"
 
+#include <type_traits>
+
 namespace fem {
 
 // Snapshot storage: FP64, FP32, double-float pairs (hi, lo FP32 with hi + lo = e to 2^-48 relative; the
@@ -32,12 +34,49 @@ __device__ __forceinline__ void store_snap(SnapHL* p, int64_t stride, int64_t i,
   reinterpret_cast<float*>(p)[i] = hl.x;
   reinterpret_cast<uint16_t*>(reinterpret_cast<float*>(p) + stride)[i] = f2bf_rn(hl.y);
 }
+// Values i and i + 1 (i even) stored with one vector access per plane.
+__device__ __forceinline__ void store_snap2(double* p, int64_t, int64_t i, double v0, double v1) {
+  *reinterpret_cast<double2*>(p + i) = make_double2(v0, v1);
+}
+__device__ __forceinline__ void store_snap2(float* p, int64_t, int64_t i, double v0, double v1) {
+  *reinterpret_cast<float2*>(p + i) = make_float2((float)v0, (float)v1);
+}
+__device__ __forceinline__ void store_snap2(float2* p, int64_t, int64_t i, double v0, double v1) {
+  const float2 a = d2df(v0), b = d2df(v1);
+  *reinterpret_cast<float4*>(p + i) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void store_snap2(SnapHL* p, int64_t stride, int64_t i, double v0, double v1) {
+  const float2 a = d2df(v0), b = d2df(v1);
+  float* h = reinterpret_cast<float*>(p);
+  *reinterpret_cast<float2*>(h + i) = make_float2(a.x, b.x);
+  *reinterpret_cast<uint32_t*>(reinterpret_cast<uint16_t*>(h + stride) + i) =
+      (uint32_t)f2bf_rn(a.y) | ((uint32_t)f2bf_rn(b.y) << 16);
+}
 template <typename E>
 __device__ __forceinline__ typename SnapVal<E>::V load_snap(const E* p, int64_t, int64_t i) { return p[i]; }
 template <>
 __device__ __forceinline__ float2 load_snap<SnapHL>(const SnapHL* p, int64_t stride, int64_t i) {
   const float* h = reinterpret_cast<const float*>(p);
   return make_float2(h[i], bf2f(reinterpret_cast<const uint16_t*>(h + stride)[i]));
+}
+// Values i and i + 1 of a slot (i even) in one vector access per plane.
+__device__ __forceinline__ void load_snap2(const double* p, int64_t, int64_t i, double& a, double& b) {
+  const double2 t = *reinterpret_cast<const double2*>(p + i);
+  a = t.x, b = t.y;
+}
+__device__ __forceinline__ void load_snap2(const float* p, int64_t, int64_t i, float& a, float& b) {
+  const float2 t = *reinterpret_cast<const float2*>(p + i);
+  a = t.x, b = t.y;
+}
+__device__ __forceinline__ void load_snap2(const float2* p, int64_t, int64_t i, float2& a, float2& b) {
+  const float4 t = *reinterpret_cast<const float4*>(p + i);
+  a = make_float2(t.x, t.y), b = make_float2(t.z, t.w);
+}
+__device__ __forceinline__ void load_snap2(const SnapHL* p, int64_t stride, int64_t i, float2& a, float2& b) {
+  const float* h = reinterpret_cast<const float*>(p);
+  const float2 hh = *reinterpret_cast<const float2*>(h + i);
+  const uint32_t l = *reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint16_t*>(h + stride) + i);
+  a = make_float2(hh.x, bf2f((uint16_t)(l & 0xffffu))), b = make_float2(hh.y, bf2f((uint16_t)(l >> 16)));
 }
 template <typename E> __device__ __forceinline__ E* snap_slot(E* ring, int64_t slot, int64_t stride) {
   return reinterpret_cast<E*>(reinterpret_cast<char*>(ring) + slot * stride * snap_bytes<E>());
@@ -222,24 +261,51 @@ __global__ void __launch_bounds__(kBlock, 3) k_pred_dots(PredView p, int slot_ne
   const E* ring = (const E*)p.ring;
   const int64_t st = p.slot_stride;
   const E* xn = snap_slot(ring, slot_new, st);
-  PredAcc<T> acc[kDotGrp];
   const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
-  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-    const T x = load_snap(xn, st, base + i);
-#pragma unroll
-    for (int jj = 0; jj < kDotGrp; ++jj) {
-      const int j = j0 + jj;
-      if (j < kMaxSlots && ((valid_mask >> j) & 1ull)) acc[jj].add(load_snap(snap_slot(ring, j, st), st, base + i), x);
-    }
-  }
   __shared__ RedVal<T> sh[kBlock / 32][kDotGrp][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* out = p.dpart + ((int64_t)R * p.n_chunks + k) * kMaxSlots * rpad;
+  if (std::is_same<E, SnapHL>::value && rpad >= 2) {
+    // FP32 + BF16 snapshots: two consecutive values a thread (cases c, c + 1), so the two residual words
+    // come in one 32-bit load (one value a thread, 2-byte loads, measured 3x slower); for the 8-byte
+    // formats one value a thread is faster (350 us a Gram row against 578 us)
+    PredAcc<T> acc0[kDotGrp], acc1[kDotGrp];
+    for (int64_t i = 2 * (int64_t)threadIdx.x; i < cnt; i += 2 * (int64_t)blockDim.x) {
+      T x0, x1;
+      load_snap2(xn, st, base + i, x0, x1);
 #pragma unroll
-  for (int jj = 0; jj < kDotGrp; ++jj) {
-    RedVal<T> v = RedVal<T>::from(acc[jj]);
-    for (int off = 16; off >= rpad; off >>= 1) v.add(v.shfl_xor(off));
-    if (lane < rpad) sh[warp][jj][lane] = v;
+      for (int jj = 0; jj < kDotGrp; ++jj) {
+        const int j = j0 + jj;
+        if (j < kMaxSlots && ((valid_mask >> j) & 1ull)) {
+          T y0, y1;
+          load_snap2(snap_slot(ring, j, st), st, base + i, y0, y1);
+          acc0[jj].add(y0, x0);
+          acc1[jj].add(y1, x1);
+        }
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < kDotGrp; ++jj) {   // lanes holding the same case pair are rpad / 2 apart
+      RedVal<T> v0 = RedVal<T>::from(acc0[jj]), v1 = RedVal<T>::from(acc1[jj]);
+      for (int off = 16; off >= (rpad >> 1); off >>= 1) v0.add(v0.shfl_xor(off)), v1.add(v1.shfl_xor(off));
+      if (lane < (rpad >> 1)) sh[warp][jj][2 * lane] = v0, sh[warp][jj][2 * lane + 1] = v1;
+    }
+  } else {
+    PredAcc<T> acc[kDotGrp];
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const T x = load_snap(xn, st, base + i);
+#pragma unroll
+      for (int jj = 0; jj < kDotGrp; ++jj) {
+        const int j = j0 + jj;
+        if (j < kMaxSlots && ((valid_mask >> j) & 1ull)) acc[jj].add(load_snap(snap_slot(ring, j, st), st, base + i), x);
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < kDotGrp; ++jj) {
+      RedVal<T> v = RedVal<T>::from(acc[jj]);
+      for (int off = 16; off >= rpad; off >>= 1) v.add(v.shfl_xor(off));
+      if (lane < rpad) sh[warp][jj][lane] = v;
+    }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < kDotGrp * rpad; t += blockDim.x) {
@@ -419,6 +485,38 @@ __global__ void __launch_bounds__(kBlock, 5) k_pred_combine(PredView p, const in
   __syncthreads();
   const int c = threadIdx.x & (rpad - 1);
   const int64_t base = c_lo * 3 * rpad, cnt = c_hi > c_lo ? (c_hi - c_lo) * 3 * rpad : 0;
+  if (rpad >= 2) {
+    // two consecutive values a thread (cases c0, c0 + 1), four slots' vector loads in flight
+    const int c0 = (2 * threadIdx.x) & (rpad - 1);
+    for (int64_t i = 2 * (int64_t)threadIdx.x; i < cnt; i += 2 * (int64_t)blockDim.x) {
+      const int64_t gi = base + i;
+      CombAcc<T> s0, s1;
+      for (int a0 = 0; a0 < n; a0 += 4) {
+        T y0[4], y1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (a0 + u < n) {
+            load_snap2(sptr[a0 + u], st, gi, y0[u], y1[u]);
+          } else {
+            y0[u] = y1[u] = T{};
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (a0 + u < n) s0.add(sw[(a0 + u) * rpad + c0], y0[u]), s1.add(sw[(a0 + u) * rpad + c0 + 1], y1[u]);
+      }
+      if (y_base) {
+        const double2 yb = *reinterpret_cast<const double2*>(y_base + gi);
+        *reinterpret_cast<double2*>(y_out + gi) = make_double2(yb.x + s0.get(), yb.y + s1.get());
+        *reinterpret_cast<float2*>(corr32 + gi) = make_float2(s0.getf(), s1.getf());
+      } else {
+        double2 yo = *reinterpret_cast<const double2*>(y_out + gi);
+        yo.x += s0.get();
+        yo.y += s1.get();
+        *reinterpret_cast<double2*>(y_out + gi) = yo;
+      }
+    }
+  } else
   for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     const int64_t gi = base + i;
     CombAcc<T> s0, s1;
@@ -678,7 +776,30 @@ __global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, const
     e_push = ring ? snap_slot(ring, ctl->slot_new, slot_stride) : nullptr;
   }
   const double c2 = 2.0 / dt, c4 = 4.0 / dt, c44 = 4.0 / (dt * dt);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  // two consecutive values a thread (vector loads and stores of every vector; n even), then a last odd one
+  const int64_t npair = n >> 1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npair; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = 2 * t;
+    auto ld = [&](const double* x) { return *reinterpret_cast<const double2*>(x + i); };
+    auto st = [&](double* x, double y0, double y1) { *reinterpret_cast<double2*>(x + i) = make_double2(y0, y1); };
+    const double2 d = ld(du), vp = ld(v_prev), m_ = ld(qM), k_ = ld(qK), uu = ld(u), aa = ld(a), ku = ld(Ku);
+    const double2 mv = ld(Mv), kv = ld(Kv), ma = ld(Ma);
+    st(u, uu.x + d.x, uu.y + d.y);
+    st(v_push, c2 * d.x - vp.x, c2 * d.y - vp.y);
+    st(a, c44 * d.x - c4 * vp.x - aa.x, c44 * d.y - c4 * vp.y - aa.y);
+    st(Ku, ku.x + k_.x, ku.y + k_.y);
+    const double mv2x = c2 * m_.x - mv.x, kv2x = c2 * k_.x - kv.x, mv2y = c2 * m_.y - mv.y, kv2y = c2 * k_.y - kv.y;
+    st(Ma, c44 * m_.x - c4 * mv.x - ma.x, c44 * m_.y - c4 * mv.y - ma.y);
+    st(Mv, mv2x, mv2y);
+    st(Kv, kv2x, kv2y);
+    st(Av_push, cM * mv2x + cK * kv2x, cM * mv2y + cK * kv2y);
+    if (e_push) {
+      const double2 ab = ld(du_ab);
+      store_snap2(e_push, slot_stride, i, d.x - ab.x, d.y - ab.y);
+    }
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t i = n - 1;
     const double d = du[i], vp = v_prev[i], m_ = qM[i], k_ = qK[i];
     u[i] += d;
     v_push[i] = c2 * d - vp;
