@@ -1108,7 +1108,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   StepCtl* ctl = g->ctl;
   const int ce = std::max(1, o.check_every);
   cudaStream_t s = g->gs[0], s2 = g->gs[1], s3 = g->gs[2], s4 = g->gs[3];
-  const long long n_fixed = 6 + (dd ? 5 : 0), n_pass = 4, n_if = 4, n_inner = 3LL * ce + 1;
+  const long long n_fixed = 6 + (dd ? 5 : 0), n_pass = 4, n_if = sg ? 4 : 2, n_inner = 3LL * ce + 1;
   // 1. step record; the per-region Gram solves (few warps per SM) run beside the Adams-Bashforth
   // increment and the right-hand side, which do not depend on them
   GE(launch_step_begin(ctl, dd ? g->n_slots : 0, o.s_max, dt, dd ? 1 : 0, n_fixed, s));
@@ -1139,7 +1139,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
                      o.inner_tol, s, AV, ctl));
   } else {
     GE(launch_r0(mv, rpad, dt, g->b, nullptr, nullptr, nullptr, nullptr, qy, w->r32, red, w->outer, w->n_active, o.tol,
-                 o.inner_tol, s, AV, ctl));
+                 o.inner_tol, s, AV, ctl, w->sc));   // (and the inner solve's starting state)
   }
   GE(cudaMemcpyAsync(g->x, g->guess, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
   // 4. refinement passes: WHILE (pass 0, then while a case is above tol)
@@ -1168,18 +1168,10 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
     b_if = pif.conditional.phGraph_out[0];
     GE(cudaStreamBeginCaptureToGraph(s3, b_if, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     {
-      if (sg) {
-        GE(launch_norm_b_seg<float>(mv, w->r32, red, w->sc, w->outer, o.inner_tol, s3));
-      } else {
-        GE(launch_norm_b_gated<float>(mv, rpad, w->r32, red, w->sc, w->outer, o.inner_tol, s3));
-      }
+      // multi-case groups: the residual kernel (r0 or cert) has started the inner solve on r32 in place
+      if (sg) GE(launch_norm_b_seg<float>(mv, w->r32, red, w->sc, w->outer, o.inner_tol, s3));
       GE(cudaMemsetAsync(w->x32, 0, sizeof(float) * (size_t)w->n, s3));
-      if (sg) {
-        GE(launch_resid_seg<float>(mv, w->r32, nullptr, w->x32, w->rr32, w->z32, red, w->sc, w->n_active, s3));
-      } else {
-        GE(launch_resid<float>(mv, rpad, w->r32, nullptr, w->x32, w->rr32, w->z32, 1, red, w->sc, w->n_active,
-                               o.inner_tol, o.maxit, s3));
-      }
+      if (sg) GE(launch_resid_seg<float>(mv, w->r32, nullptr, w->x32, w->rr32, w->z32, red, w->sc, w->n_active, s3));
       cudaGraph_t gi = nullptr;
       GE(cudaStreamGetCaptureInfo(s3, &cs, nullptr, &gi, nullptr, nullptr, nullptr));
       GE(cudaGraphConditionalHandleCreate(&h_in, gi, 0, 0));
@@ -1199,14 +1191,14 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
         if (sg) {
           GE(launch_dir_seg<float>(mv, w->z32, w->p32, w->sc, w->n_active, s4));
         } else {
-          GE(launch_dir_defer<float>(mv, rpad, w->rr32, w->p32, w->x32, w->sc, w->n_active, s4));
+          GE(launch_dir_defer<float>(mv, rpad, w->r32, w->p32, w->x32, w->sc, w->n_active, s4));
         }
         GE(ebe_product<float>(m, rpad, w->p32, w->q32, m->cM, m->cK, &red, w->sc, nullptr, w->n_active, s4));
         if (sg) {
           GE(launch_update_seg<float>(mv, w->p32, w->q32, w->x32, w->rr32, w->z32, red, w->sc, w->n_active, o.maxit,
                                       s4));
         } else {
-          GE(launch_update_defer<float>(mv, rpad, w->q32, w->rr32, red, w->sc, w->n_active, o.maxit, s4));
+          GE(launch_update_defer<float>(mv, rpad, w->q32, w->r32, red, w->sc, w->n_active, o.maxit, s4));
         }
       }
       GE(launch_inner_cond(w->n_active, ctl, h_in, ce, o.maxit + 64 * ce, n_inner, s4));
@@ -1225,7 +1217,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
                          s2));
     } else {
       GE(launch_cert(mv, rpad, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
-                     o.inner_tol, s2));
+                     o.inner_tol, s2, w->sc));
     }
     GE(launch_pass_end(w->n_active, ctl, h_pass, kMaxPass, n_pass, s2));
   }

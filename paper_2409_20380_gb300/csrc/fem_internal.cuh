@@ -239,13 +239,15 @@ cudaError_t launch_rhs_incr(const MeshView& m, int rpad, double dt, double a0, d
                             const double* Mv, const double* Kv, const double* Ku, double* b, const RickerSrc* src,
                             const double* ext, double t, cudaStream_t s, const StepCtl* ctl = nullptr);
 cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab, float* y32, cudaStream_t s);
+// inner != null (r0, cert): also start the inner FP32 solve of the pass on r32 (zero guess, its residual
+// r32 itself): the inner case state as the norm and first-residual passes would leave it.
 cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
                       const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
                       int* n_active, double tol, double inner_max, cudaStream_t s, Ring4 avr = Ring4{},
-                      const StepCtl* ctl = nullptr);
+                      const StepCtl* ctl = nullptr, CgCase* inner = nullptr);
 cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const double* b, const double* qM,
                         const double* qK, float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
-                        double inner_max, cudaStream_t s);
+                        double inner_max, cudaStream_t s, CgCase* inner = nullptr);
 // With ctl: v_prev, v_push, Av_push and the snapshot slot come from the rings (vr, avr, ring of slots of
 // slot_stride elements) at the step read from ctl.
 cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, const double* du, const double* du_ab,

@@ -270,17 +270,20 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_update_defer(MeshView m, int r
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = i >> rshift;
     const int c = (int)(i & (rpad - 1));
+    // r and q loaded together (no load behind the free-DOF test): one memory round trip an item
     const uint8_t f = m.freemask[n];
-    T rv[3];
+    const int64_t id0 = n * 3 * rpad + c;
+    const T r0 = r[id0], r1 = r[id0 + rpad], r2 = r[id0 + 2 * rpad];
+    T rv[3] = {r0, r1, r2};
+    if (alpha != (T)0) {
+      const T q0 = q[id0], q1 = q[id0 + rpad], q2 = q[id0 + 2 * rpad];
+      const T qv[3] = {q0, q1, q2};
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int64_t id = (n * 3 + k) * rpad + c;
-      T rk = r[id];
-      if (alpha != (T)0 && dof_free(f, k)) {
-        rk -= alpha * q[id];
-        r[id] = rk;
-      }
-      rv[k] = rk;
+      for (int k = 0; k < 3; ++k)
+        if (dof_free(f, k)) {
+          rv[k] -= alpha * qv[k];
+          r[id0 + k * rpad] = rv[k];
+        }
     }
     const T* B = bi + n * 6;
     const T z0 = B[0] * rv[0] + B[3] * rv[1] + B[4] * rv[2];

@@ -656,22 +656,52 @@ __global__ void k_corr_f32(int64_t n, const double* __restrict__ guess, const do
 // A du_AB = dt/24 (-9 Av^{it-4} + 37 Av^{it-3} - 59 Av^{it-2} + 55 Av^{it-1}) exact (FP64 recurrences)
 // and A y from the FP32 product of the small data-driven correction (qy, nullable).  Writes r32 and
 // starts the outer (FP64) iteration state.
+// The inner FP32 solve's starting state for a refinement pass whose right-hand side r32 a residual kernel
+// has just written (zero initial guess, so its residual is r32 itself): the work of the separate norm and
+// first-residual passes, from the sums the residual kernel already forms.  ||r32||^2 (rrc, summed in FP64)
+// is both the right-hand side norm and the residual norm; zrc = (B^-1 r32, r32).  A case whose outer
+// solve is inactive gets a zero right-hand side (inactive).
+__device__ __forceinline__ void init_inner(CgCase& s, const CgCase& o, double rrc, double zrc) {
+  s.bb = o.active ? rrc : 0.0;
+  s.pq = s.alpha = s.beta = 0.0;
+  s.iters = 0;
+  s.outer = 0;
+  s.phase = 0;
+  s.tol2 = o.inner_tol * o.inner_tol;
+  s.rho = zrc;
+  s.rr = rrc;
+  s.relres = s.bb > 0.0 ? 1.0 : 0.0;
+  s.relres0 = s.relres;
+  s.status = (isfinite(rrc) && isfinite(zrc)) ? FEM_OK : FEM_ERR_NONFINITE;
+  s.active = (s.status == FEM_OK && s.bb > 0.0) ? 1 : 0;
+}
+
+// (B^-1 r, r) of one node's three values (FP32, B^-1 symmetric [xx yy zz xy xz yz]).
+__device__ __forceinline__ float zr_node(const float* __restrict__ B, float r0, float r1, float r2) {
+  const float z0 = B[0] * r0 + B[3] * r1 + B[4] * r2;
+  const float z1 = B[3] * r0 + B[1] * r1 + B[5] * r2;
+  const float z2 = B[4] * r0 + B[5] * r1 + B[2] * r2;
+  return z0 * r0 + z1 * r1 + z2 * r2;
+}
+
 __global__ void __launch_bounds__(kVecBlock, 3) k_r0(MeshView m, int rpad, int rshift, double h, const double* __restrict__ b,
                                                const double* __restrict__ Av4, const double* __restrict__ Av3,
                                                const double* __restrict__ Av2, const double* __restrict__ Av1,
                                                const float* __restrict__ qy, float* __restrict__ r32, Reducer red,
                                                CgCase* outer, int* n_active, double tol, double inner_max,
-                                               Ring4 avr, const StepCtl* ctl) {
+                                               Ring4 avr, const StepCtl* ctl, CgCase* inner) {
   if (ctl) {   // A v^{it-4} .. A v^{it-1} in ring slots it .. it+3 (mod 4)
     const int it = ctl->it;
     Av4 = avr.p[it & 3], Av3 = avr.p[(it + 1) & 3], Av2 = avr.p[(it + 2) & 3], Av1 = avr.p[(it + 3) & 3];
   }
   double bb = 0.0, rr = 0.0;
+  float zr = 0.f;
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = i >> rshift;
     const int c = (int)(i & (rpad - 1));
     const uint8_t f = m.freemask[n];
+    float rf[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const int64_t id = (n * 3 + k) * rpad + c;
@@ -681,13 +711,15 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_r0(MeshView m, int rpad, int r
         v = bv - h * (-9.0 * Av4[id] + 37.0 * Av3[id] - 59.0 * Av2[id] + 55.0 * Av1[id]);
         if (qy) v -= f2d(qy[id]);
       }
-      r32[id] = d2f(v);
+      rf[k] = d2f(v);
+      r32[id] = rf[k];
       bb += bv * bv;
       rr += v * v;
     }
+    if (inner) zr += zr_node(m.binv32 + n * 6, rf[0], rf[1], rf[2]);
   }
-  double vals[2] = {bb, rr};
-  if (block_reduce_last<2>(vals, rpad, red)) {
+  double vals[3] = {bb, rr, (double)zr};
+  if (block_reduce_last<3>(vals, rpad, red)) {
     if (threadIdx.x < rpad) {
       const int c = threadIdx.x;
       CgCase& s = outer[c];
@@ -704,6 +736,7 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_r0(MeshView m, int rpad, int r
       // estimate only: the certificate is the FP64 residual computed after the solve
       s.active = (s.status == FEM_OK && bbc > 0.0 && rrc >= tol * tol * bbc) ? 1 : 0;
       s.inner_tol = inner_target(tol, s.relres, inner_max);
+      if (inner) init_inner(inner[c], s, rrc, red.out[2 * rpad + c]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -719,23 +752,28 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_r0(MeshView m, int rpad, int r
 __global__ void __launch_bounds__(kVecBlock, 3) k_cert(MeshView m, int rpad, int rshift, double cM, double cK,
                                                  const double* __restrict__ b, const double* __restrict__ qM,
                                                  const double* __restrict__ qK, float* __restrict__ r32, Reducer red,
-                                                 CgCase* outer, int* n_active, double tol, double inner_max) {
+                                                 CgCase* outer, int* n_active, double tol, double inner_max,
+                                                 CgCase* inner) {
   double rr = 0.0;
+  float zr = 0.f;
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = i >> rshift;
     const int c = (int)(i & (rpad - 1));
     const uint8_t f = m.freemask[n];
+    float rf[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const int64_t id = (n * 3 + k) * rpad + c;
       const double v = dof_free(f, k) ? b[id] - (cM * qM[id] + cK * qK[id]) : 0.0;
-      r32[id] = d2f(v);
+      rf[k] = d2f(v);
+      r32[id] = rf[k];
       rr += v * v;
     }
+    if (inner) zr += zr_node(m.binv32 + n * 6, rf[0], rf[1], rf[2]);
   }
-  double vals[1] = {rr};
-  if (block_reduce_last<1>(vals, rpad, red)) {
+  double vals[2] = {rr, (double)zr};
+  if (block_reduce_last<2>(vals, rpad, red)) {
     if (threadIdx.x < rpad) {
       const int c = threadIdx.x;
       CgCase& s = outer[c];
@@ -746,6 +784,7 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_cert(MeshView m, int rpad, int
       if (!isfinite(rrc)) s.status = FEM_ERR_NONFINITE;
       s.active = (s.status == FEM_OK && s.bb > 0.0 && rrc >= tol * tol * s.bb) ? 1 : 0;
       s.inner_tol = inner_target(tol, s.relres, inner_max);
+      if (inner) init_inner(inner[c], s, rrc, red.out[rpad + c]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -898,19 +937,20 @@ cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab,
 
 cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
                       const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
-                      int* n_active, double tol, double inner_max, cudaStream_t s, Ring4 avr, const StepCtl* ctl) {
+                      int* n_active, double tol, double inner_max, cudaStream_t s, Ring4 avr, const StepCtl* ctl,
+                      CgCase* inner) {
   const int rs = log2i(rpad);
   k_r0<<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer,
-                                                n_active, tol, inner_max, avr, ctl);
+                                                n_active, tol, inner_max, avr, ctl, inner);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const double* b, const double* qM,
                         const double* qK, float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
-                        double inner_max, cudaStream_t s) {
+                        double inner_max, cudaStream_t s, CgCase* inner) {
   const int rs = log2i(rpad);
   k_cert<<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, cM, cK, b, qM, qK, r32, red, outer, n_active, tol,
-                                                inner_max);
+                                                inner_max, inner);
   return cudaGetLastError();
 }
 
