@@ -62,6 +62,8 @@ def parse():
                          "3 assembled double-float")
     ap.add_argument("--snapshot-format", type=int, default=2,
                     help="predictor snapshot storage: 0 FP64, 1 FP32, 2 double-float, 3 FP32 + BF16 residual")
+    ap.add_argument("--check-every", type=int, default=8,
+                    help="inner CG iterations per convergence check (graph: launches per WHILE-loop body)")
     ap.add_argument("--profile-steps", type=int, default=40,
                     help="steps after the timed region timed per kernel class with CUDA events (eager)")
     ap.add_argument("--kernel", default=None, choices=["ebe", "split", "predictor"],
@@ -269,7 +271,7 @@ def run_ours(args):
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER if args.precision == "mixed" else fem.FEM_FP64,
                                 predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
                                 s_max=args.s_max, snapshot_format=args.snapshot_format, tol=1e-8, cert_df=args.cert,
-                                use_graph=0 if args.no_graph else 1)
+                                use_graph=0 if args.no_graph else 1, check_every=args.check_every)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
     if args.variant or args.hex_per_tile:

@@ -1122,11 +1122,12 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   GE(cudaEventRecord(g->gev[1], sf));
   if (dd) GE(launch_pred_solve(pv, nullptr, 0, 0, o.tau, s, ctl));
   GE(cudaStreamWaitEvent(s, g->gev[1], 0));
-  // guess = du_AB + Y w, and the correction Y w in FP32 for its residual
+  // guess = x = du_AB + Y w, and the correction Y w in FP32 for its residual
   if (dd) {
-    GE(launch_pred_combine(pv, nullptr, 0, g->guess, s, ctl, g->du_ab, w->z32, m->reg_gap, m->reg_lead));
+    GE(launch_pred_combine(pv, nullptr, 0, g->guess, s, ctl, g->du_ab, w->z32, m->reg_gap, m->reg_lead, g->x));
   } else {
     GE(cudaMemcpyAsync(g->guess, g->du_ab, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
+    GE(cudaMemcpyAsync(g->x, g->du_ab, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
   }
   // 3. residual of the guess
   const float* qy = nullptr;
@@ -1141,7 +1142,6 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
     GE(launch_r0(mv, rpad, dt, g->b, nullptr, nullptr, nullptr, nullptr, qy, w->r32, red, w->outer, w->n_active, o.tol,
                  o.inner_tol, s, AV, ctl, w->sc));   // (and the inner solve's starting state)
   }
-  GE(cudaMemcpyAsync(g->x, g->guess, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
   // 4. refinement passes: WHILE (pass 0, then while a case is above tol)
   cudaGraphConditionalHandle h_pass, h_if, h_in;
   cudaGraph_t b_pass, b_if, b_in, tmp;

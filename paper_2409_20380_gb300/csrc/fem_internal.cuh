@@ -306,7 +306,8 @@ cudaError_t launch_pred_solve(const PredView& p, const int* x_slots, int n_pairs
                               cudaStream_t s, const StepCtl* ctl = nullptr);
 cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out, cudaStream_t s,
                                 const StepCtl* ctl = nullptr, const double* y_base = nullptr,
-                                float* corr32 = nullptr, const int32_t* gap_hi = nullptr, int lead_hi = 0);
+                                float* corr32 = nullptr, const int32_t* gap_hi = nullptr, int lead_hi = 0,
+                                double* y_out2 = nullptr);
 
 // Assembled operators for the certification product (k_bcsr.cu): K as 3x3 blocks and M as scalars on the
 // node pattern row_ptr/col.  assemble also writes the (hi, lo) FP32-pair copy KMd (per block the 9 pairs of

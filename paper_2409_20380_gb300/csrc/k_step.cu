@@ -460,11 +460,12 @@ template <> struct CombAcc<float2> {
 // With y_base: y_out = y_base + Y w and corr32 = Y w in FP32 (the correction the guess's residual needs),
 // and outside every region range y_out = y_base, corr32 = 0: the last chunk of region R also covers the
 // nodes from its range's end to gap_hi[R] (the next range's start), block 0 the nodes before lead_hi.
+// y_out2 (optional, with y_base) receives a second copy of y_out: the solver's starting iterate.
 template <typename E>
 __global__ void __launch_bounds__(kBlock, 5) k_pred_combine(PredView p, const int* __restrict__ y_slots, int n,
                                                          double* __restrict__ y_out, const double* __restrict__ y_base,
                                                          float* __restrict__ corr32, const int32_t* __restrict__ gap_hi,
-                                                         int lead_hi, const StepCtl* ctl) {
+                                                         int lead_hi, const StepCtl* ctl, double* __restrict__ y_out2) {
   if (ctl) y_slots = ctl->ys, n = ctl->n_pairs;
   typedef typename SnapVal<E>::V T;
   typedef typename CombAcc<T>::W W;
@@ -507,7 +508,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_pred_combine(PredView p, const in
       }
       if (y_base) {
         const double2 yb = *reinterpret_cast<const double2*>(y_base + gi);
-        *reinterpret_cast<double2*>(y_out + gi) = make_double2(yb.x + s0.get(), yb.y + s1.get());
+        const double2 yo = make_double2(yb.x + s0.get(), yb.y + s1.get());
+        *reinterpret_cast<double2*>(y_out + gi) = yo;
+        if (y_out2) *reinterpret_cast<double2*>(y_out2 + gi) = yo;
         *reinterpret_cast<float2*>(corr32 + gi) = make_float2(s0.getf(), s1.getf());
       } else {
         double2 yo = *reinterpret_cast<const double2*>(y_out + gi);
@@ -533,7 +536,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_pred_combine(PredView p, const in
     }
     s0.merge(s1);
     if (y_base) {
-      y_out[gi] = y_base[gi] + s0.get();
+      const double yo = y_base[gi] + s0.get();
+      y_out[gi] = yo;
+      if (y_out2) y_out2[gi] = yo;
       corr32[gi] = s0.getf();
     } else {
       y_out[gi] += s0.get();
@@ -542,7 +547,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_pred_combine(PredView p, const in
   if (y_base) {
     auto copy = [&](int64_t e0, int64_t e1) {
       for (int64_t gi = e0 + threadIdx.x; gi < e1; gi += blockDim.x) {
-        y_out[gi] = y_base[gi];
+        const double yb = y_base[gi];
+        y_out[gi] = yb;
+        if (y_out2) y_out2[gi] = yb;
         corr32[gi] = 0.0f;
       }
     };
@@ -1009,11 +1016,11 @@ cudaError_t launch_pred_solve(const PredView& p, const int* x_slots, int n_pairs
 
 cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pairs, double* y_out, cudaStream_t s,
                                 const StepCtl* ctl, const double* y_base, float* corr32, const int32_t* gap_hi,
-                                int lead_hi) {
+                                int lead_hi, double* y_out2) {
   if (p.n_regions == 0 || (!ctl && n_pairs <= 0 && !y_base)) return cudaSuccess;
   if (y_base && (!corr32 || !gap_hi)) return cudaErrorInvalidValue;
   const int grid = p.n_regions * p.n_chunks;
-#define CMB_ARGS p, y_slots, n_pairs, y_out, y_base, corr32, gap_hi, lead_hi, ctl
+#define CMB_ARGS p, y_slots, n_pairs, y_out, y_base, corr32, gap_hi, lead_hi, ctl, y_base ? y_out2 : nullptr
   if (p.fmt == 1)
     k_pred_combine<float><<<grid, kBlock, 0, s>>>(CMB_ARGS);
   else if (p.fmt == 2)
