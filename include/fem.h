@@ -151,8 +151,12 @@ fem_status fem_mesh_destroy(fem_mesh* m);
  * thread applying its hex to two cases at once by paired FP32 operations (FP32 products of groups with
  * n_rhs >= 4; FP64 products and fused groups use 3), registers capped for two blocks per SM, 6 = as 5 with
  * one block per SM (variants 3-6 need 3 x n_rhs x element size to be a multiple of 16 bytes; otherwise 3,
- * then 2, then 1 is used).  hex_per_tile: 0 = automatic (largest tile whose shared memory fits), or
- * 64/128/256/512 hexes per tile.  Errors: FEM_ERR_ARG for other values or variants 2-6 on a mesh without
+ * then 2, then 1 is used), 7 = hex element matrices: each hex's six tets summed once into its symmetric
+ * 24 x 24 matrix aM M_h + aK K_h (FP64 sums stored FP32, 1200 bytes a hex, built on first use, kept with
+ * the mesh) and applied as dense blocks to pairs of hexes by paired FP32 operations, 64-hex tiles (FP32
+ * products with the mesh's own Newmark coefficients and 16-byte aligned vectors, not fused groups;
+ * otherwise 5 is used).  hex_per_tile: 0 = automatic (largest tile whose shared memory fits), or
+ * 64/128/256/512 hexes per tile.  Errors: FEM_ERR_ARG for other values or variants 2-7 on a mesh without
  * hex patches.
  */
 fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile);

@@ -258,7 +258,9 @@ struct fem_mesh {
   static constexpr int kNTile = 4;
   HexTiles tiles[kNTile];          // hex_per_tile 64, 128, 256, 512
   std::vector<void*> tile_bufs;
-  int ebe_variant = 0;             // 0 auto, 1 generic, 2 tiled hex, 3 staged, 4 case-major, 5/6 packed staged
+  int ebe_variant = 0;             // 0 auto, 1 generic, 2 tiled hex, 3 staged, 4 case-major, 5/6 packed staged,
+                                   // 7 hex element matrices
+  float* hexmat = nullptr;         // [ceil(H / 2)][300][2] hex matrices for (cM, cK) (built on first use)
   int hex_per_tile = 0;            // 0 auto
   // autotuned choice per (FP32 / FP64 product, log2 of the case count); variant 0 = not tuned
   struct Tuned {
@@ -350,9 +352,25 @@ struct fem_mesh {
     return FEM_OK;
   }
   MeshView view() const { return MeshView{N, E, conn, rec64, rec32, binv64, binv32, fm, seg, nseg}; }
+  // Hex element matrices for the mesh's own coefficients (cM, cK); built outside stream capture only.
+  fem_status ensure_hexmat(cudaStream_t s) {
+    if (hexmat || !hex) return FEM_OK;
+    const int64_t H = E / 6;
+    float* buf = nullptr;
+    CHK(dalloc(&buf, (size_t)2 * kHexMatVals * (size_t)((H + 1) / 2)));
+    cudaError_t e = launch_hexmat_build(H, rec64, cM, cK, buf, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      dfree(buf);
+      return fail(FEM_ERR_CUDA, std::string("hex matrices: ") + cudaGetErrorString(e));
+    }
+    hexmat = buf;
+    return FEM_OK;
+  }
   ~fem_mesh() {
     dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(rec_df); dfree(D);
-    dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(KMd);
+    dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(KMd); dfree(hexmat);
     dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi); dfree(reg_gap); dfree(seg); dfree(reg_cent);
     for (auto* w : ws) delete w;
     for (void* b : tile_bufs) cudaFree(b);
@@ -381,7 +399,10 @@ struct fem_mesh {
       if (t.n_tiles == 0) continue;
       if (hpt && t.hex_per_tile != hpt) continue;
       size_t need, budget;
-      if (variant == 3 || variant == 5 || variant == 6) {   // (6: one block per SM)
+      if (variant == 7) {
+        need = elem_bytes == 4 ? ebe_hexmat_smem(t, view(), rpad) : ~(size_t)0;
+        budget = 110 * 1024;
+      } else if (variant == 3 || variant == 5 || variant == 6) {   // (6: one block per SM)
         need = elem_bytes == 4 ? ebe_hex_staged_smem<float>(t, view(), rpad) : ebe_hex_staged_smem<double>(t, view(), rpad);
         budget = variant == 6 ? 220 * 1024 : 110 * 1024;
       } else if (variant == 4) {   // one block per SM
@@ -416,6 +437,20 @@ static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, do
                                const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s) {
   int v, h;
   m->resolve(sizeof(T), rpad, &v, &h);
+  if (v == 7) {   // hex element matrices: FP32, the mesh's own coefficients, no fused groups, aligned vectors
+    if constexpr (sizeof(T) == 4) {
+      const HexTiles* t = m->tiles_for(sizeof(T), rpad, 7, h);
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      // (coefficients equal to the mesh's to 1e-12: far below the FP32 matrices' own rounding)
+      auto same = [](double x, double y) { return std::fabs(x - y) <= 1e-12 * std::fabs(y); };
+      if (t && !m->seg && same(aM, m->cM) && same(aK, m->cK) &&
+          ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15) == 0 &&
+          (m->hexmat || (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+                         const_cast<fem_mesh*>(m)->ensure_hexmat(s) == FEM_OK)))
+        return launch_ebe_hexmat(*t, m->view(), m->hexmat, rpad, p, q, aM, aK, red, sc, ptq, gate, s);
+    }
+    v = 5, h = 0;
+  }
   if (v == 4) {   // case-major staged tiles (converged cases skipped); same requirements as 3, no fused groups
     const HexTiles* t = (reinterpret_cast<uintptr_t>(p) & 15) == 0 ? m->tiles_for(sizeof(T), rpad, 4, h) : nullptr;
     if (t) return launch_ebe_hex_cm<T>(*t, m->view(), rpad, p, q, aM, aK, red, sc, ptq, gate, s);
@@ -1251,6 +1286,11 @@ static fem_status group_graph_build(fem_batch* bt, Group* g) {
     for (auto& ev : g->gev) CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     CU(cudaStreamSynchronize(bt->s));
   }
+  {   // operators built on first use are built before the capture (the graph only replays products)
+    int v = 0, h = 0;
+    g->mesh->resolve(sizeof(float), g->rpad, &v, &h);
+    if (v == 7) CHK(g->mesh->ensure_hexmat(bt->s));
+  }
   Prof* saved = g->ws->prof;
   g->ws->prof = nullptr;
   cudaError_t e = cudaStreamBeginCapture(g->gs[0], cudaStreamCaptureModeRelaxed);
@@ -1442,6 +1482,7 @@ static fem_status autotune_t(fem_mesh* m, int rpad, cudaStream_t s, int* v_out, 
     if (sizeof(T) == 4 && rpad >= 4 && !m->seg) {
       for (int hpt : {64, 128}) cand.push_back({5, hpt});
       for (int hpt : {64, 128, 256}) cand.push_back({6, hpt});
+      cand.push_back({7, 64});
     }
   }
   double best = 1e30;
@@ -1639,7 +1680,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
 fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile) {
   g_err.clear();
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
-  if (ebe_variant < 0 || ebe_variant > 6) return fail(FEM_ERR_ARG, "ebe_variant must be 0 .. 6");
+  if (ebe_variant < 0 || ebe_variant > 7) return fail(FEM_ERR_ARG, "ebe_variant must be 0 .. 7");
   if (ebe_variant >= 2 && !m->hex) return fail(FEM_ERR_ARG, "the mesh has no hex patches: tiled kernel unavailable");
   if (hex_per_tile != 0 && hex_per_tile != 64 && hex_per_tile != 128 && hex_per_tile != 256 && hex_per_tile != 512)
     return fail(FEM_ERR_ARG, "hex_per_tile must be 0, 64, 128, 256 or 512");

@@ -22,6 +22,7 @@ constexpr int kMaxRedBlocks = 152 * 8;   // grid cap of reducing kernels (partia
 // Per-element record, 12 values: g1 (3), g2 (3), g3 (3) shape-function gradients of local nodes 1..3
 // (g0 = -g1-g2-g3), lambda*V, mu*V, rho*V/20.
 constexpr int kRec = 12;
+constexpr int kHexMatVals = 300;          // stored values of a hex's symmetric 24 x 24 element matrix
 
 // Hex-patch topology: slots of the four corners of each of the six tets of a hex, slots numbered by first
 // appearance (the Kuhn split along the (0,0,0)-(1,1,1) diagonal gives exactly this table).
@@ -274,6 +275,14 @@ cudaError_t launch_ebe_hex_cm(const HexTiles& ht, const MeshView& m, int rpad, c
                               const Reducer* red, CgCase* sc, double* ptq_out, const int* gate, cudaStream_t s);
 template <typename T>
 size_t ebe_hex_cm_smem(const HexTiles& ht, const MeshView& m, int rpad);   // ~0 when not applicable
+// Hex element matrices (variant 7): build the interleaved symmetric 24 x 24 matrices A_h = aM M_h + aK K_h
+// of the mesh's hexes (n_hex, hex h = elements 6h .. 6h + 5, FP64 records) into out
+// ([ceil(n_hex / 2)][300][2] floats), and the product q = A p with them (FP32, r cases, not fused groups).
+cudaError_t launch_hexmat_build(int64_t n_hex, const double* rec64, double aM, double aK, float* out, cudaStream_t s);
+cudaError_t launch_ebe_hexmat(const HexTiles& ht, const MeshView& m, const float* hm, int rpad, const float* p,
+                              float* q, double aM, double aK, const Reducer* red, CgCase* sc, double* ptq_out,
+                              const int* gate, cudaStream_t s);
+size_t ebe_hexmat_smem(const HexTiles& ht, const MeshView& m, int rpad);   // ~0 when not applicable
 // Reads and clears the flag a staged kernel sets when a bounded wait for its copies gave up.
 cudaError_t ebe_tma_timeout(int* flag);
 cudaError_t launch_ebe_split(const MeshView& m, int rpad, const double* p, double* qM, double* qK, cudaStream_t s);

@@ -1136,6 +1136,360 @@ template cudaError_t launch_ebe_hex_staged<float>(const HexTiles&, const MeshVie
                                                   double, const Reducer*, CgCase*, double*, const int*, cudaStream_t,
                                                   int);
 
+// ------------------------------------------------------------------------------------------------------
+// Hex element matrices (variant 7).  The six Kuhn tets of a hex are summed once into the hex's symmetric
+// 24 x 24 operator A_h = aM M_h + aK K_h (in FP64 from the FP64 records, stored FP32), so a product applies
+// each hex as one dense 24 x 24 block: 576 multiply-adds a case, with no per-tet strain and stress
+// intermediates, at 1200 bytes of matrix a hex instead of 288 of tet records.  Per tet with gradients g_a
+// (g_0 = -(g_1 + g_2 + g_3)), lambda V, mu V and rho V / 20:
+//   K_ab = lambda V g_a g_b^T + mu V ((g_a . g_b) I + g_b g_a^T),   M_ab = rho V / 20 (1 + delta_ab) I.
+// Storage: per hex the upper block triangle by corner rows -- for corner a the diagonal block as
+// (xx, xy, xz, yy, yz, zz), then the blocks (a, b > a) row-major -- 300 values; hexes 2j and 2j + 1 are
+// interleaved value by value, so one float2 holds an entry of both and a thread applies a PAIR OF HEXES to
+// one case with paired FP32 operations on natural pairs (no broadcast operands).
+// ------------------------------------------------------------------------------------------------------
+__host__ __device__ constexpr int hm_row_off(int a) { return 6 * a + 9 * (7 * a - a * (a - 1) / 2); }
+static_assert(hm_row_off(8) == kHexMatVals, "300 values a hex");
+
+__global__ void k_hexmat_build(int64_t H, const double* __restrict__ rec, double aM, double aK,
+                               float* __restrict__ out) {
+  constexpr int T[6][4] = {{0, 1, 2, 3}, {0, 1, 3, 4}, {0, 5, 3, 2}, {0, 5, 6, 3}, {0, 7, 4, 3}, {0, 7, 3, 6}};
+  const int64_t n = H * 36;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n; w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t h = w / 36;
+    int bi = (int)(w - h * 36), a = 0;
+    while (bi >= 8 - a) bi -= 8 - a, ++a;
+    const int b = a + bi;
+    double B[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    for (int t = 0; t < 6; ++t) {
+      int la = -1, lb = -1;
+      for (int k = 0; k < 4; ++k) {
+        if (T[t][k] == a) la = k;
+        if (T[t][k] == b) lb = k;
+      }
+      if (la < 0 || lb < 0) continue;
+      const double* r = rec + (h * 6 + t) * kRec;
+      double ga[3], gb[3];
+      for (int i = 0; i < 3; ++i) {
+        ga[i] = la == 0 ? -(r[i] + r[3 + i] + r[6 + i]) : r[3 * (la - 1) + i];
+        gb[i] = lb == 0 ? -(r[i] + r[3 + i] + r[6 + i]) : r[3 * (lb - 1) + i];
+      }
+      const double lam = aK * r[9], mu = aK * r[10], ms = aM * r[11] * (la == lb ? 2.0 : 1.0);
+      const double gg = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k)
+          B[i][k] += lam * ga[i] * gb[k] + mu * (gb[i] * ga[k] + (i == k ? gg : 0.0)) + (i == k ? ms : 0.0);
+    }
+    float* o = out + (h >> 1) * (2 * kHexMatVals) + (h & 1);
+    if (a == b) {
+      const int e = hm_row_off(a);
+      const double d[6] = {B[0][0], B[0][1], B[0][2], B[1][1], B[1][2], B[2][2]};
+      for (int j = 0; j < 6; ++j) o[2 * (e + j)] = (float)d[j];
+    } else {
+      const int e = hm_row_off(a) + 6 + 9 * (b - a - 1);
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) o[2 * (e + 3 * i + k)] = (float)B[i][k];
+    }
+  }
+}
+
+cudaError_t launch_hexmat_build(int64_t n_hex, const double* rec64, double aM, double aK, float* out,
+                                cudaStream_t s) {
+  const int64_t pairs = (n_hex + 1) / 2;
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * 2 * kHexMatVals * (size_t)pairs, s);   // odd tail
+  if (e != cudaSuccess || n_hex == 0) return e;
+  k_hexmat_build<<<grid_for(n_hex * 36, 152 * 16), kBlock, 0, s>>>(n_hex, rec64, aM, aK, out);
+  return cudaGetLastError();
+}
+
+constexpr int kHmChunk = 32;   // hexes a staged chunk (16 interleaved pairs, 38.4 KB)
+
+struct HexMatLayout {
+  size_t qs, node, m0, m1, total;
+};
+__host__ __device__ inline HexMatLayout hexmat_layout(int nloc_max, int rpad) {
+  auto up = [](size_t x) { return (x + 127) & ~(size_t)127; };
+  HexMatLayout L;
+  L.qs = 512;   // head: 2 mbarriers, per-case |p| maxima and scales
+  L.node = L.qs + up((size_t)nloc_max * 3 * rpad * sizeof(int));
+  L.m0 = L.node + up(sizeof(int) * (size_t)nloc_max);
+  L.m1 = L.m0 + up(sizeof(float) * 2 * kHexMatVals * (kHmChunk / 2));
+  L.total = L.m1 + up(sizeof(float) * 2 * kHexMatVals * (kHmChunk / 2));
+  return L;
+}
+
+// Product q = A p with the hex matrices, r cases, FP32.  Tiles as in the staged kernel (its node list, the
+// fixed-point tile accumulator and flush); the chunks of 32 hexes' matrices come by bulk asynchronous copies,
+// double-buffered (the copy of chunk j + 1 runs while chunk j is applied); p is gathered straight from
+// global memory (it is L2-resident: the search-direction pass has just written it).  Items are (hex pair,
+// active case slot); a thread's case is fixed.  The matrix is applied row by row (corner a's three sums
+// live at a time, then added to the tile accumulator), each stored off-diagonal block serving two rows.
+// Measured slower than the tet form on the medium workload (167 against 105 us): the shared-memory loads
+// of the matrix (one vector load a value pair for two lanes' worth of distinct data) and the gathers
+// leave it latency-bound at 1.9 k instructions an item, 35% issue; applying each stored block to both of
+// its corners from registers instead (one block of 8 warps per SM) measured 197 us.
+template <bool DOT>
+__global__ void __launch_bounds__(kBlock, 2) k_ebe_hexmat(HexTiles ht, const float* __restrict__ hm, int rpad,
+                                                          const float* __restrict__ p, float* __restrict__ q,
+                                                          float aM, float aK, Reducer red, CgCase* sc,
+                                                          double* ptq_out, const int* gate) {
+  if (gate && *gate == 0) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const HexMatLayout L = hexmat_layout(ht.nloc_max, rpad);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);
+  int* spm = reinterpret_cast<int*>(smem_raw + 32);          // [32] per-case largest |p| (bit patterns)
+  float* sfwd = reinterpret_cast<float*>(smem_raw + 160);    // [32] 2^(E_c - 30)
+  int* qs = reinterpret_cast<int*>(smem_raw + L.qs);
+  int* snode = reinterpret_cast<int*>(smem_raw + L.node);
+  auto smb = [&](int b) { return reinterpret_cast<const float4*>(smem_raw + (b ? L.m1 : L.m0)); };
+  const int per_node = 3 * rpad;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&mbar[0]), 1);
+    mbar_init(smem_u32(&mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < (ht.nloc_max * per_node) >> 2; i += blockDim.x)
+    reinterpret_cast<int4*>(qs)[i] = make_int4(0, 0, 0, 0);
+  if ((int)threadIdx.x < 32) spm[threadIdx.x] = 0;
+  // active cases (inner iterations; all otherwise) on napw >= nac slots, a power of two: a thread's slot,
+  // and case, are fixed (blockDim.x is a multiple of napw)
+  uint32_t cmask = rpad >= 32 ? 0xffffffffu : ((1u << rpad) - 1u);
+  if (DOT && sc) {
+    cmask = 0;
+    for (int c = 0; c < rpad; ++c)
+      if (sc[c].active) cmask |= 1u << c;
+  }
+  const int nac = __popc(cmask);
+  int napw = 1, lgw = 0, myc = -1;
+  while (napw < nac) napw <<= 1, ++lgw;
+  {
+    const int slot = threadIdx.x & (napw - 1);
+    if (slot < nac) {
+      uint32_t mm = cmask;
+      for (int k = 0; k < slot; ++k) mm &= mm - 1;
+      myc = __ffs(mm) - 1;
+    }
+  }
+  __syncthreads();
+  const float bco = fabsf(aM) * ht.abs_m + fabsf(aK) * ht.abs_k;
+  // chunk sequence of this block: tiles t0, t0 + grid, ..., each in chunks of kHmChunk hexes
+  const int t0 = blockIdx.x;
+  auto n_chunks = [&](int t) { return (ht.tile_hex_off[t + 1] - ht.tile_hex_off[t] + kHmChunk - 1) / kHmChunk; };
+  auto issue = [&](int t, int ch, int b) {   // chunk ch of tile t into buffer b (its readers are past a barrier)
+    const int hb = ht.tile_hex_off[t] + ch * kHmChunk;
+    const int he = min(hb + kHmChunk, ht.tile_hex_off[t + 1]);
+    const uint32_t bytes = (uint32_t)(sizeof(float) * 2 * kHexMatVals * ((he - hb + 1) >> 1));
+    const uint32_t bar = smem_u32(mbar + b);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, bytes);
+      bulk_g2s(smem_u32(smb(b)), hm + (int64_t)(hb >> 1) * (2 * kHexMatVals), bytes, bar);
+    }
+  };
+  if (t0 < ht.n_tiles) issue(t0, 0, 0);
+  double dsum = 0.0;
+  int j = 0;   // chunk counter (buffer j & 1, phase (j >> 1) & 1)
+  for (int t = t0; t < ht.n_tiles; t += gridDim.x) {
+    const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
+    const int h0 = ht.tile_hex_off[t], h1 = ht.tile_hex_off[t + 1];
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) snode[l] = ht.tile_nodes[n0 + l];
+    __syncthreads();
+    {
+      // per-case largest |p| over the tile's nodes: float4 pieces, a thread's four cases fixed
+      const int f4 = per_node >> 2, cq = rpad >> 2;
+      float4 mx = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = threadIdx.x; i < nl * f4; i += blockDim.x) {
+        const int l = i / f4;
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p + (int64_t)(snode[l] & 0x0fffffff) * per_node) +
+                               (i - l * f4));
+        mx.x = fmaxf(mx.x, fabsf(v.x)), mx.y = fmaxf(mx.y, fabsf(v.y));
+        mx.z = fmaxf(mx.z, fabsf(v.z)), mx.w = fmaxf(mx.w, fabsf(v.w));
+      }
+      for (int off = cq; off < 32; off <<= 1) {
+        mx.x = fmaxf(mx.x, __shfl_xor_sync(0xffffffffu, mx.x, off));
+        mx.y = fmaxf(mx.y, __shfl_xor_sync(0xffffffffu, mx.y, off));
+        mx.z = fmaxf(mx.z, __shfl_xor_sync(0xffffffffu, mx.z, off));
+        mx.w = fmaxf(mx.w, __shfl_xor_sync(0xffffffffu, mx.w, off));
+      }
+      const int lane = threadIdx.x & 31;
+      if (lane < cq) {
+        const int c = 4 * (lane % cq);
+        atomicMax(spm + c, __float_as_int(mx.x));
+        atomicMax(spm + c + 1, __float_as_int(mx.y));
+        atomicMax(spm + c + 2, __float_as_int(mx.z));
+        atomicMax(spm + c + 3, __float_as_int(mx.w));
+      }
+    }
+    __syncthreads();
+    // E_c from the exponent field of bound_c (bound_c < 2^(field - 126)); scale 2^(30 - E_c)
+    auto expo = [&](int c) {
+      const uint32_t f = (__float_as_uint(bco * __int_as_float(spm[c])) >> 23) & 0xffu;
+      return f == 0u ? -126 : (int)f - 126;
+    };
+    auto pow2 = [](int e) { return __uint_as_float((uint32_t)min(max(e + 127, 1), 254) << 23); };
+    const float sv = myc >= 0 ? pow2(30 - expo(myc)) : 1.f;
+    const float2 sinv = make_float2(sv, sv);
+    if ((int)threadIdx.x < rpad) sfwd[threadIdx.x] = pow2(expo(threadIdx.x) - 30);
+    const int nch = n_chunks(t);
+    for (int ch = 0; ch < nch; ++ch, ++j) {
+      const int b = j & 1;
+      // the next chunk: this tile's next, else the first of the block's next tile
+      {
+        int tn = t, cn = ch + 1;
+        if (cn == nch) tn = t + gridDim.x, cn = 0;
+        if (tn < ht.n_tiles) issue(tn, cn, b ^ 1);
+      }
+      const uint32_t bar = smem_u32(mbar + b);
+      if (!mbar_wait(bar, (uint32_t)((j >> 1) & 1))) {
+        atomicExch(&g_tma_timeout, 1);
+        mbar_wait(bar, (uint32_t)((j >> 1) & 1));   // second bounded wait for the copy still in flight
+      }
+      const float4* m4b = smb(b);
+      const int hb = h0 + ch * kHmChunk;
+      const int he = min(hb + kHmChunk, h1);
+      const int npair = (he - hb + 1) >> 1;
+      const int items = myc >= 0 ? npair << lgw : 0;
+      float2 hd = make_float2(0.f, 0.f);
+      for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int pr = it >> lgw;
+        const int hA = hb + 2 * pr;
+        const bool hasB = hA + 1 < he;
+        const uint4 lA = __ldg(ht.hex_local + hA);
+        const uint4 lB = hasB ? __ldg(ht.hex_local + hA + 1) : lA;
+        auto loc = [](const uint4& w, int s) -> int {
+          const uint32_t v = s < 2 ? w.x : s < 4 ? w.y : s < 6 ? w.z : w.w;
+          return (int)((s & 1) ? (v >> 16) : (v & 0xffffu));
+        };
+        float2 P[8][3];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const float* pa = p + (int64_t)(snode[loc(lA, s)] & 0x0fffffff) * per_node + myc;
+          const float* pb = p + (int64_t)(snode[loc(lB, s)] & 0x0fffffff) * per_node + myc;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) P[s][k] = make_float2(__ldg(pa + k * rpad), __ldg(pb + k * rpad));
+        }
+        const float4* m4 = m4b + pr * (kHexMatVals / 2);
+        auto M = [&](int e) -> float2 {
+          const float4 v = m4[e >> 1];
+          return (e & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+        };
+        // row a of A: blocks (a, b >= a) as stored, blocks (b < a, a) transposed (the stored block read
+        // again: the symmetric storage halves the matrix bytes, and only corner a's sums are live)
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          float2 Q[3];
+          {
+            const int e0 = hm_row_off(a);
+            const float2 xx = M(e0), xy = M(e0 + 1), xz = M(e0 + 2), yy = M(e0 + 3), yz = M(e0 + 4), zz = M(e0 + 5);
+            Q[0] = fma2(xz, P[a][2], fma2(xy, P[a][1], mul2(xx, P[a][0])));
+            Q[1] = fma2(yz, P[a][2], fma2(yy, P[a][1], mul2(xy, P[a][0])));
+            Q[2] = fma2(zz, P[a][2], fma2(yz, P[a][1], mul2(xz, P[a][0])));
+          }
+#pragma unroll
+          for (int bb = 0; bb < 8; ++bb) {
+            if (bb == a) continue;
+            const int lo = bb < a ? bb : a, hi = bb < a ? a : bb;
+            const int eb = hm_row_off(lo) + 6 + 9 * (hi - lo - 1);
+            float2 B[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+              for (int k = 0; k < 3; ++k) B[i][k] = bb > a ? M(eb + 3 * i + k) : M(eb + 3 * k + i);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+              Q[i] = fma2(B[i][2], P[bb][2], fma2(B[i][1], P[bb][1], fma2(B[i][0], P[bb][0], Q[i])));
+          }
+          // corner a's sums: fixed point into the tile accumulator
+          int* da = qs + loc(lA, a) * per_node + myc;
+          int* db = qs + loc(lB, a) * per_node + myc;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            if (DOT) hd = fma2(P[a][k], Q[k], hd);
+            const float2 v = mul2(Q[k], sinv);
+            atomicAdd(da + k * rpad, __float2int_rn(v.x));
+            if (hasB) atomicAdd(db + k * rpad, __float2int_rn(v.y));
+          }
+        }
+      }
+      if (DOT) dsum += (double)hd.x + (double)hd.y;
+      __syncthreads();   // buffer b's readers are done; the tile accumulator is complete after the last chunk
+    }
+    // flush: float4 pieces of the tile accumulator (four cases of one component of one node)
+    {
+      const int sh4 = __ffs(rpad) - 3;
+      const int f4 = per_node >> 2;
+      for (int i = threadIdx.x; i < nl * f4; i += blockDim.x) {
+        const int l = (i >> sh4) / 3, kk = (i - l * f4) >> sh4;
+        const int raw = snode[l];
+        const int64_t g = raw & 0x0fffffff;
+        const bool fixed = !dof_free((uint8_t)((raw >> 28) & 7), kk);
+        float4* dst = reinterpret_cast<float4*>(q + g * per_node) + (i - l * f4);
+        const int4 vi = reinterpret_cast<const int4*>(qs)[i];
+        const int c4 = (i << 2) & (rpad - 1);
+        const float4 v = make_float4((float)vi.x * sfwd[c4], (float)vi.y * sfwd[c4 + 1], (float)vi.z * sfwd[c4 + 2],
+                                     (float)vi.w * sfwd[c4 + 3]);
+        reinterpret_cast<int4*>(qs)[i] = make_int4(0, 0, 0, 0);
+        if (raw < 0) {
+          if (!fixed) atomicAdd(dst, v);
+        } else {
+          *dst = fixed ? make_float4(0.f, 0.f, 0.f, 0.f) : v;
+        }
+      }
+      if ((int)threadIdx.x < 32) spm[threadIdx.x] = 0;   // (its readers passed the chunk barriers)
+    }
+    __syncthreads();
+  }
+  if (DOT) {
+    // case totals: lanes of one case slot are napw apart in a warp; warps through shared memory one slot at
+    // a time would cost a barrier each, so each warp's slot sums go to a [warp][slot] table in the (idle)
+    // matrix buffer, then thread c < rpad adds its case's column
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double d = dsum;
+    for (int off = napw; off < 32; off <<= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    double* tab = reinterpret_cast<double*>(smem_raw + L.m0);   // [warp][32 slots]
+    if (lane < napw) tab[warp * 32 + lane] = d;
+    __syncthreads();
+    double vc = 0.0;
+    if ((int)threadIdx.x < rpad && ((cmask >> threadIdx.x) & 1u)) {
+      const int sl = __popc(cmask & ((1u << threadIdx.x) - 1u));
+      for (int w = 0; w < nw; ++w) vc += tab[w * 32 + sl];
+    }
+    double v[1] = {vc};
+    if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
+  }
+}
+
+size_t ebe_hexmat_smem(const HexTiles& ht, const MeshView& m, int rpad) {
+  if (m.seg || rpad < 4 || rpad > 32 || ht.hex_per_tile % kHmChunk != 0) return ~(size_t)0;   // not applicable
+  return hexmat_layout(ht.nloc_max, rpad).total;
+}
+
+cudaError_t launch_ebe_hexmat(const HexTiles& ht, const MeshView& m, const float* hm, int rpad, const float* p,
+                              float* q, double aM, double aK, const Reducer* red, CgCase* sc, double* ptq_out,
+                              const int* gate, cudaStream_t s) {
+  const size_t smem = ebe_hexmat_smem(ht, m, rpad);
+  if (smem == ~(size_t)0 || !hm || (reinterpret_cast<uintptr_t>(p) & 15) != 0 ||
+      (reinterpret_cast<uintptr_t>(q) & 15) != 0)
+    return cudaErrorInvalidValue;
+  cudaError_t err = cudaMemsetAsync(q, 0, sizeof(float) * (size_t)m.N * 3 * rpad, s);
+  if (err != cudaSuccess) return err;
+  int dev = 0, nsm = 152, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  auto kfn = red ? k_ebe_hexmat<true> : k_ebe_hexmat<false>;
+  err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBlock, smem);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  int grid = nsm * per_sm;
+  if (grid > ht.n_tiles) grid = ht.n_tiles;
+  if (grid > kMaxRedBlocks) grid = kMaxRedBlocks;
+  Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
+  kfn<<<grid, kBlock, smem, s>>>(ht, hm, rpad, p, q, (float)aM, (float)aK, rd, red ? sc : nullptr,
+                                 red ? ptq_out : nullptr, gate);
+  return cudaGetLastError();
+}
+
 template <typename T>
 size_t ebe_hex_cm_smem(const HexTiles& ht, const MeshView& m, int rpad) {
   if ((3 * rpad * sizeof(T)) % 16 != 0 || ht.nloc_max > kBlockCM || m.seg) return ~(size_t)0;   // not applicable

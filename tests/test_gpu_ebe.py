@@ -25,8 +25,10 @@ def torch_dev():
 
 CASES = [((7, 5, 4), 1, 0.0), ((7, 5, 4), 4, 0.2), ((9, 6, 5), 16, 0.1), ((3, 2, 2), 32, 0.0), ((12, 9, 7), 8, 0.15)]
 # (ebe_variant, hex_per_tile): generic element kernel; tiled hex kernel and staged tiled hex kernel with
-# automatic and small tiles (140..756 hexes over 64-hex tiles: several tiles and a ragged last one)
-VARIANTS = [(1, 0), (2, 0), (2, 64), (3, 0), (3, 64), (4, 0), (4, 64), (5, 0), (5, 64), (6, 0), (6, 64)]
+# automatic and small tiles (140..756 hexes over 64-hex tiles: several tiles and a ragged last one); 7 (hex
+# element matrices) applies to FP32 products with the mesh's coefficients and falls back to 5 (then 3) else
+VARIANTS = [(1, 0), (2, 0), (2, 64), (3, 0), (3, 64), (4, 0), (4, 64), (5, 0), (5, 64), (6, 0), (6, 64), (7, 0),
+            (7, 64)]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
