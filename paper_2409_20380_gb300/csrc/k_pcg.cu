@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_dir_defer(MeshView m, int rpad
 
 // r -= alpha q on free DOFs; (B^{-1} r, r) and (r, r) reduced; the same per-case tail as k_update.
 template <typename T>
-__global__ void __launch_bounds__(kVecBlock, 3) k_update_defer(MeshView m, int rpad, int rshift,
+__global__ void __launch_bounds__(kVecBlock, 2) k_update_defer(MeshView m, int rpad, int rshift,
                                                          const T* __restrict__ q, T* __restrict__ r, Reducer red,
                                                          CgCase* sc, int* n_active, int maxit) {
   if (*n_active == 0) return;
@@ -267,30 +267,51 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_update_defer(MeshView m, int r
   typename Acc<T>::type zr = 0, rr = 0;
   const int64_t total = m.N << rshift;
   const T alpha = (T)sc[(blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & (rpad - 1)].alpha;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+  // two items an iteration (the grid stride apart: the same case), all their loads -- r, q, the free-DOF
+  // bits and B^-1 -- issued before either is updated: two memory round trips' worth of bytes in flight
+  struct Item {
+    T rv[3], qv[3], B[6];
+    uint8_t f;
+    int64_t id0;
+  };
+  auto load = [&](int64_t i, Item& it) {
     const int64_t n = i >> rshift;
-    const int c = (int)(i & (rpad - 1));
-    // r and q loaded together (no load behind the free-DOF test): one memory round trip an item
-    const uint8_t f = m.freemask[n];
-    const int64_t id0 = n * 3 * rpad + c;
-    const T r0 = r[id0], r1 = r[id0 + rpad], r2 = r[id0 + 2 * rpad];
-    T rv[3] = {r0, r1, r2};
+    it.id0 = n * 3 * rpad + (int)(i & (rpad - 1));
+    it.f = m.freemask[n];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) it.rv[k] = r[it.id0 + k * rpad];
     if (alpha != (T)0) {
-      const T q0 = q[id0], q1 = q[id0 + rpad], q2 = q[id0 + 2 * rpad];
-      const T qv[3] = {q0, q1, q2};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) it.qv[k] = q[it.id0 + k * rpad];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) it.B[k] = bi[n * 6 + k];
+  };
+  auto apply = [&](Item& it) {
+    if (alpha != (T)0) {
 #pragma unroll
       for (int k = 0; k < 3; ++k)
-        if (dof_free(f, k)) {
-          rv[k] -= alpha * qv[k];
-          r[id0 + k * rpad] = rv[k];
+        if (dof_free(it.f, k)) {
+          it.rv[k] -= alpha * it.qv[k];
+          r[it.id0 + k * rpad] = it.rv[k];
         }
     }
-    const T* B = bi + n * 6;
+    const T* B = it.B;
+    const T* rv = it.rv;
     const T z0 = B[0] * rv[0] + B[3] * rv[1] + B[4] * rv[2];
     const T z1 = B[3] * rv[0] + B[1] * rv[1] + B[5] * rv[2];
     const T z2 = B[4] * rv[0] + B[5] * rv[1] + B[2] * rv[2];
     zr += z0 * rv[0] + z1 * rv[1] + z2 * rv[2];
     rr += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+  };
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += 2 * stride) {
+    Item a, b;
+    const bool two = i + stride < total;
+    load(i, a);
+    if (two) load(i + stride, b);
+    apply(a);
+    if (two) apply(b);
   }
   double v[2] = {(double)zr, (double)rr};
   if (block_reduce_last<2>(v, rpad, red)) {
@@ -381,9 +402,24 @@ __global__ void k_refine_pending(int64_t n_items, int rpad, int ncase, double* _
       outer[threadIdx.x].status = inner[threadIdx.x].status;
   }
   // the grid stride is a multiple of rpad: every thread serves one case
-  const float a = (float)inner[(blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & (rpad - 1)].alpha;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += f2d(a != 0.0f ? fmaf(a, p[i], d[i]) : d[i]);
+  // two consecutive values (cases c, c + 1) a thread by vector accesses; the grid stride is a multiple of
+  // rpad / 2 pairs, so a thread's pair of cases is fixed
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int c0 = (int)((2 * t0) & (rpad - 1));
+  const float a0 = (float)inner[c0].alpha, a1 = (float)inner[rpad > 1 ? c0 + 1 : c0].alpha;
+  if (rpad > 1) {
+    for (int64_t t = t0; t < (n_items >> 1); t += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = 2 * t;
+      const float2 dv = *reinterpret_cast<const float2*>(d + i), pv = *reinterpret_cast<const float2*>(p + i);
+      double2 xv = *reinterpret_cast<const double2*>(x + i);
+      xv.x += f2d(a0 != 0.0f ? fmaf(a0, pv.x, dv.x) : dv.x);
+      xv.y += f2d(a1 != 0.0f ? fmaf(a1, pv.y, dv.y) : dv.y);
+      *reinterpret_cast<double2*>(x + i) = xv;
+    }
+  } else {
+    for (int64_t i = t0; i < n_items; i += (int64_t)gridDim.x * blockDim.x)
+      x[i] += f2d(a0 != 0.0f ? fmaf(a0, p[i], d[i]) : d[i]);
+  }
 }
 
 // x = 0 on Dirichlet DOFs and for cases whose right-hand side is zero (||b|| = 0 gives x = 0).
@@ -454,7 +490,7 @@ template <typename T>
 cudaError_t launch_update_defer(const MeshView& m, int rpad, const T* q, T* r, Reducer red, CgCase* sc,
                                 int* n_active, int maxit, cudaStream_t s) {
   const int rs = log2i(rpad);
-  k_update_defer<T><<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, q, r, red, sc, n_active, maxit);
+  k_update_defer<T><<<grid_resident((const void*)k_update_defer<T>, kVecBlock, m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, q, r, red, sc, n_active, maxit);
   return cudaGetLastError();
 }
 template cudaError_t launch_dir_defer<float>(const MeshView&, int, const float*, float*, float*, const CgCase*,

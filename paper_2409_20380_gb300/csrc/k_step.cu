@@ -140,20 +140,33 @@ __global__ void k_rhs_finish(MeshView m, int rpad, int rshift, double* __restric
 }
 
 // du_AB = dt/24 (-9 v^{it-4} + 37 v^{it-3} - 59 v^{it-2} + 55 v^{it-1})   (Section 3.2)
+// Weights times h (four FMAs a value: the FP64 pipe bounds this kernel), two values a thread by 16-byte
+// accesses, then the odd last one.
+__device__ __forceinline__ void ab4_body(int64_t n, double h, const double* __restrict__ v4,
+                                         const double* __restrict__ v3, const double* __restrict__ v2,
+                                         const double* __restrict__ v1, double* __restrict__ out) {
+  const double w4 = -9.0 * h, w3 = 37.0 * h, w2 = -59.0 * h, w1 = 55.0 * h;
+  auto ld = [](const double* x, int64_t i) { return *reinterpret_cast<const double2*>(x + i); };
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (n >> 1); t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = 2 * t;
+    const double2 a4 = ld(v4, i), a3 = ld(v3, i), a2 = ld(v2, i), a1 = ld(v1, i);
+    *reinterpret_cast<double2*>(out + i) = make_double2(fma(w1, a1.x, fma(w2, a2.x, fma(w3, a3.x, w4 * a4.x))),
+                                                        fma(w1, a1.y, fma(w2, a2.y, fma(w3, a3.y, w4 * a4.y))));
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t i = n - 1;
+    out[i] = fma(w1, v1[i], fma(w2, v2[i], fma(w3, v3[i], w4 * v4[i])));
+  }
+}
+
 __global__ void k_ab4(int64_t n, double h, const double* __restrict__ v4, const double* __restrict__ v3,
                       const double* __restrict__ v2, const double* __restrict__ v1, double* __restrict__ out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = h * (-9.0 * v4[i] + 37.0 * v3[i] - 59.0 * v2[i] + 55.0 * v1[i]);
+  ab4_body(n, h, v4, v3, v2, v1, out);
 }
 
 __global__ void k_ab4_ring(int64_t n, double h, Ring4 v, const StepCtl* __restrict__ ctl, double* __restrict__ out) {
   const int it = ctl->it;   // v^{it-4} .. v^{it-1} sit in slots it, it+1, it+2, it+3 (mod 4)
-  const double* __restrict__ v4 = v.p[it & 3];
-  const double* __restrict__ v3 = v.p[(it + 1) & 3];
-  const double* __restrict__ v2 = v.p[(it + 2) & 3];
-  const double* __restrict__ v1 = v.p[(it + 3) & 3];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = h * (-9.0 * v4[i] + 37.0 * v3[i] - 59.0 * v2[i] + 55.0 * v1[i]);
+  ab4_body(n, h, v.p[it & 3], v.p[(it + 1) & 3], v.p[(it + 2) & 3], v.p[(it + 3) & 3], out);
 }
 
 __global__ void k_add(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o) {
@@ -627,23 +640,51 @@ __global__ void k_rhs_incr(MeshView m, int rpad, int rshift, double c_mv, double
     t = ctl->t;
     if (!ctl->use_ext) ext = nullptr;
   }
+  // point load of case cs at node n (zero elsewhere)
+  auto load_of = [&](int64_t n, int cs) -> double3 {
+    if (src[cs].node != n) return make_double3(0.0, 0.0, 0.0);
+    if (ext) return make_double3(ext[cs * 3], ext[cs * 3 + 1], ext[cs * 3 + 2]);
+    const RickerSrc& s = src[cs];
+    const double arg = (M_PI * s.f0 * (t - s.t0)) * (M_PI * s.f0 * (t - s.t0));
+    const double w = s.amp * (1.0 - 2.0 * arg) * exp(-arg);
+    return make_double3(w * s.dir[0], w * s.dir[1], w * s.dir[2]);
+  };
+  if (!m.seg && rpad >= 2) {
+    // two cases (c, c + 1) a thread by 16-byte accesses: 12 vector loads in flight an item
+    const int rs1 = rshift - 1;
+    const int64_t total = m.N << rs1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t n = i >> rs1;
+      const int c = (int)(i & ((rpad >> 1) - 1)) << 1;
+      const uint8_t f = m.freemask[n];
+      double2 ma[3], mv[3], kv[3], ku[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int64_t id = (n * 3 + k) * rpad + c;
+        ma[k] = *reinterpret_cast<const double2*>(Ma + id), mv[k] = *reinterpret_cast<const double2*>(Mv + id);
+        kv[k] = *reinterpret_cast<const double2*>(Kv + id), ku[k] = *reinterpret_cast<const double2*>(Ku + id);
+      }
+      const double3 g0 = load_of(n, c), g1 = load_of(n, c + 1);
+      const double f0[3] = {g0.x, g0.y, g0.z}, f1[3] = {g1.x, g1.y, g1.z};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int64_t id = (n * 3 + k) * rpad + c;
+        *reinterpret_cast<double2*>(b + id) =
+            dof_free(f, k) ? make_double2(f0[k] + ma[k].x + c_mv * mv[k].x + a1 * kv[k].x - ku[k].x,
+                                          f1[k] + ma[k].y + c_mv * mv[k].y + a1 * kv[k].y - ku[k].y)
+                           : make_double2(0.0, 0.0);
+      }
+    }
+    return;
+  }
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = i >> rshift;
     const int c = (int)(i & (rpad - 1));
     const int cs = m.seg ? m.seg[n] : c;            // case of this entry (fused groups: the node's mesh)
     const uint8_t f = m.freemask[n];
-    const RickerSrc s = src[cs];
-    double fv[3] = {0.0, 0.0, 0.0};
-    if (s.node == n) {
-      if (ext) {
-        for (int k = 0; k < 3; ++k) fv[k] = ext[cs * 3 + k];
-      } else {
-        const double arg = (M_PI * s.f0 * (t - s.t0)) * (M_PI * s.f0 * (t - s.t0));
-        const double w = s.amp * (1.0 - 2.0 * arg) * exp(-arg);
-        for (int k = 0; k < 3; ++k) fv[k] = w * s.dir[k];
-      }
-    }
+    const double3 g = load_of(n, cs);
+    const double fv[3] = {g.x, g.y, g.z};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const int64_t id = (n * 3 + k) * rpad + c;
@@ -691,7 +732,7 @@ __device__ __forceinline__ float zr_node(const float* __restrict__ B, float r0, 
   return z0 * r0 + z1 * r1 + z2 * r2;
 }
 
-__global__ void __launch_bounds__(kVecBlock, 3) k_r0(MeshView m, int rpad, int rshift, double h, const double* __restrict__ b,
+__global__ void __launch_bounds__(kVecBlock, 2) k_r0(MeshView m, int rpad, int rshift, double h, const double* __restrict__ b,
                                                const double* __restrict__ Av4, const double* __restrict__ Av3,
                                                const double* __restrict__ Av2, const double* __restrict__ Av1,
                                                const float* __restrict__ qy, float* __restrict__ r32, Reducer red,
@@ -703,6 +744,8 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_r0(MeshView m, int rpad, int r
   }
   double bb = 0.0, rr = 0.0;
   float zr = 0.f;
+  // the Adams-Bashforth weights times -h: four FMAs from b (the FP64 pipe bounds this kernel)
+  const double w4 = 9.0 * h, w3 = -37.0 * h, w2 = 59.0 * h, w1 = -55.0 * h;
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = i >> rshift;
@@ -715,7 +758,7 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_r0(MeshView m, int rpad, int r
       double v = 0.0;
       const double bv = b[id];
       if (dof_free(f, k)) {
-        v = bv - h * (-9.0 * Av4[id] + 37.0 * Av3[id] - 59.0 * Av2[id] + 55.0 * Av1[id]);
+        v = fma(w1, Av1[id], fma(w2, Av2[id], fma(w3, Av3[id], fma(w4, Av4[id], bv))));
         if (qy) v -= f2d(qy[id]);
       }
       rf[k] = d2f(v);
@@ -756,7 +799,7 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_r0(MeshView m, int rpad, int r
 
 // Certified FP64 residual from the split products:  r = b - (cM qM + cK qK);  r32 = float(r) for the next
 // inner solve; cases at or above tol stay active.
-__global__ void __launch_bounds__(kVecBlock, 3) k_cert(MeshView m, int rpad, int rshift, double cM, double cK,
+__global__ void __launch_bounds__(kVecBlock, 2) k_cert(MeshView m, int rpad, int rshift, double cM, double cK,
                                                  const double* __restrict__ b, const double* __restrict__ qM,
                                                  const double* __restrict__ qK, float* __restrict__ r32, Reducer red,
                                                  CgCase* outer, int* n_active, double tol, double inner_max,
@@ -764,20 +807,41 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_cert(MeshView m, int rpad, int
   double rr = 0.0;
   float zr = 0.f;
   const int64_t total = m.N << rshift;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n = i >> rshift;
-    const int c = (int)(i & (rpad - 1));
-    const uint8_t f = m.freemask[n];
+  // two items an iteration (the grid stride apart), the loads of both issued first
+  struct Item {
+    double b[3], m[3], k[3];
+    uint8_t f;
+    int64_t n, id0;
+  };
+  auto load = [&](int64_t i, Item& it) {
+    it.n = i >> rshift;
+    it.id0 = it.n * 3 * rpad + (int)(i & (rpad - 1));
+    it.f = m.freemask[it.n];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int64_t id = it.id0 + k * rpad;
+      it.b[k] = b[id], it.m[k] = qM[id], it.k[k] = qK[id];
+    }
+  };
+  auto apply = [&](const Item& it) {
     float rf[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const int64_t id = (n * 3 + k) * rpad + c;
-      const double v = dof_free(f, k) ? b[id] - (cM * qM[id] + cK * qK[id]) : 0.0;
+      const double v = dof_free(it.f, k) ? fma(-cK, it.k[k], fma(-cM, it.m[k], it.b[k])) : 0.0;
       rf[k] = d2f(v);
-      r32[id] = rf[k];
-      rr += v * v;
+      r32[it.id0 + k * rpad] = rf[k];
+      rr = fma(v, v, rr);
     }
-    if (inner) zr += zr_node(m.binv32 + n * 6, rf[0], rf[1], rf[2]);
+    if (inner) zr += zr_node(m.binv32 + it.n * 6, rf[0], rf[1], rf[2]);
+  };
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += 2 * stride) {
+    Item a, b2;
+    const bool two = i + stride < total;
+    load(i, a);
+    if (two) load(i + stride, b2);
+    apply(a);
+    if (two) apply(b2);
   }
   double vals[2] = {rr, (double)zr};
   if (block_reduce_last<2>(vals, rpad, red)) {
@@ -947,7 +1011,7 @@ cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, c
                       int* n_active, double tol, double inner_max, cudaStream_t s, Ring4 avr, const StepCtl* ctl,
                       CgCase* inner) {
   const int rs = log2i(rpad);
-  k_r0<<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer,
+  k_r0<<<grid_resident((const void*)k_r0, kVecBlock, m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer,
                                                 n_active, tol, inner_max, avr, ctl, inner);
   return cudaGetLastError();
 }
@@ -956,7 +1020,7 @@ cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const
                         const double* qK, float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
                         double inner_max, cudaStream_t s, CgCase* inner) {
   const int rs = log2i(rpad);
-  k_cert<<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, cM, cK, b, qM, qK, r32, red, outer, n_active, tol,
+  k_cert<<<grid_resident((const void*)k_cert, kVecBlock, m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, cM, cK, b, qM, qK, r32, red, outer, n_active, tol,
                                                 inner_max, inner);
   return cudaGetLastError();
 }

@@ -170,7 +170,7 @@ def test_autotuned_product_matches_csr(torch_dev, precision, r):
         prec = fem.FEM_FP32_INNER if precision == "fp32" else fem.FEM_FP64
         v, hpt, ms = fem.fem_mesh_autotune(h, prec, r)
         assert (v, hpt) in [(1, 0), (2, 64), (2, 128), (2, 256), (2, 512), (3, 64), (3, 128), (3, 256), (4, 64),
-                            (4, 128)] and ms > 0
+                            (4, 128), (5, 64), (5, 128), (6, 64), (6, 128), (6, 256), (7, 64)] and ms > 0
         dt = torch.float32 if precision == "fp32" else torch.float64
         ps = random_free_vectors(m, r, seed=5 + r)
         p = torch.tensor(from_cases(ps, m.n_nodes, r), device="cuda", dtype=dt)
