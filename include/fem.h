@@ -155,9 +155,12 @@ fem_status fem_mesh_destroy(fem_mesh* m);
  * 24 x 24 matrix aM M_h + aK K_h (FP64 sums stored FP32, 1200 bytes a hex, built on first use, kept with
  * the mesh) and applied as dense blocks to pairs of hexes by paired FP32 operations, 64-hex tiles (FP32
  * products with the mesh's own Newmark coefficients and 16-byte aligned vectors, not fused groups;
- * otherwise 5 is used).  hex_per_tile: 0 = automatic (largest tile whose shared memory fits), or
- * 64/128/256/512 hexes per tile.  Errors: FEM_ERR_ARG for other values or variants 2-7 on a mesh without
- * hex patches.
+ * otherwise 5 is used), 8 = not element by element: the assembled 3x3-block operators (the CRS-style
+ * product the paper compares the EBE with, Section 3.3; built on first use and shared with the
+ * certification product), FP64 blocks for FP64 products and their FP32 rounding for FP32 ones, any mesh,
+ * not fused groups (those use 5, or 1 without hex patches).  hex_per_tile: 0 = automatic (largest tile
+ * whose shared memory fits), or 64/128/256/512 hexes per tile.  Errors: FEM_ERR_ARG for other values or
+ * variants 2-7 on a mesh without hex patches.
  */
 fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile);
 

@@ -259,7 +259,7 @@ struct fem_mesh {
   HexTiles tiles[kNTile];          // hex_per_tile 64, 128, 256, 512
   std::vector<void*> tile_bufs;
   int ebe_variant = 0;             // 0 auto, 1 generic, 2 tiled hex, 3 staged, 4 case-major, 5/6 packed staged,
-                                   // 7 hex element matrices
+                                   // 7 hex element matrices, 8 assembled 3x3 blocks (CRS-style comparator)
   float* hexmat = nullptr;         // [ceil(H / 2)][300][2] hex matrices for (cM, cK) (built on first use)
   int hex_per_tile = 0;            // 0 auto
   // autotuned choice per (FP32 / FP64 product, log2 of the case count); variant 0 = not tuned
@@ -388,7 +388,7 @@ struct fem_mesh {
       if (t.variant) *variant = t.variant, *hpt = t.hpt;
     }
     if (*variant == 0) *variant = hex ? 5 : 1;       // packed staged tiles where they apply (else 3, 2, 1)
-    if (!hex) *variant = 1;
+    if (!hex && *variant != 8) *variant = 1;
   }
   // Tiling for the resolved variant: the largest tile whose shared memory fits (or the requested size).
   const HexTiles* tiles_for(size_t elem_bytes, int rpad, int variant, int hpt) const {
@@ -437,6 +437,14 @@ static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, do
                                const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s) {
   int v, h;
   m->resolve(sizeof(T), rpad, &v, &h);
+  if (v == 8) {   // assembled 3x3 blocks (built outside stream capture only); not for fused groups
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!m->seg && (m->row_ptr || (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+                                   const_cast<fem_mesh*>(m)->ensure_bcsr(s) == FEM_OK)))
+      return launch_bcsr_apply<T>(m->view(), rpad, m->row_ptr, m->col, m->Kb, m->Mb, m->KMd, p, q, aM, aK, red, sc,
+                                  ptq, gate, s);
+    v = m->hex ? 5 : 1, h = 0;
+  }
   if (v == 7) {   // hex element matrices: FP32, the mesh's own coefficients, no fused groups, aligned vectors
     if constexpr (sizeof(T) == 4) {
       const HexTiles* t = m->tiles_for(sizeof(T), rpad, 7, h);
@@ -1290,6 +1298,7 @@ static fem_status group_graph_build(fem_batch* bt, Group* g) {
     int v = 0, h = 0;
     g->mesh->resolve(sizeof(float), g->rpad, &v, &h);
     if (v == 7) CHK(g->mesh->ensure_hexmat(bt->s));
+    if (v == 8) CHK(g->mesh->ensure_bcsr(bt->s));
   }
   Prof* saved = g->ws->prof;
   g->ws->prof = nullptr;
@@ -1485,13 +1494,14 @@ static fem_status autotune_t(fem_mesh* m, int rpad, cudaStream_t s, int* v_out, 
       cand.push_back({7, 64});
     }
   }
+  if (!m->seg) cand.push_back({8, 0});
   double best = 1e30;
   int bv = 1, bh = 0;
   cudaError_t e = cudaMemsetAsync(p, 0, n * sizeof(T), s);
   for (auto [v, hpt] : cand) {
     if (e != cudaSuccess) break;
     m->ebe_variant = v, m->hex_per_tile = hpt;
-    if (v >= 2) {
+    if (v >= 2 && v <= 7) {
       const HexTiles* t = m->tiles_for(sizeof(T), rpad, v, hpt);
       if (!t || t->hex_per_tile != hpt) continue;   // this tiling does not fit
     }
@@ -1680,8 +1690,9 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
 fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile) {
   g_err.clear();
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
-  if (ebe_variant < 0 || ebe_variant > 7) return fail(FEM_ERR_ARG, "ebe_variant must be 0 .. 7");
-  if (ebe_variant >= 2 && !m->hex) return fail(FEM_ERR_ARG, "the mesh has no hex patches: tiled kernel unavailable");
+  if (ebe_variant < 0 || ebe_variant > 8) return fail(FEM_ERR_ARG, "ebe_variant must be 0 .. 8");
+  if (ebe_variant >= 2 && ebe_variant <= 7 && !m->hex)
+    return fail(FEM_ERR_ARG, "the mesh has no hex patches: tiled kernel unavailable");
   if (hex_per_tile != 0 && hex_per_tile != 64 && hex_per_tile != 128 && hex_per_tile != 256 && hex_per_tile != 512)
     return fail(FEM_ERR_ARG, "hex_per_tile must be 0, 64, 128, 256 or 512");
   m->ebe_variant = ebe_variant;

@@ -326,6 +326,14 @@ cudaError_t launch_bcsr_assemble(const MeshView& m, const int32_t* row_ptr, cons
                                  double* Kb, double* Mb, float2* KMd, int* missing, cudaStream_t s);
 // qM = M p, qK = K p (r cases, Dirichlet rows zero).  p_df != null: double-float arithmetic (p split into
 // p_df first); else native FP64.
+// q = (aM M + aK K) p with the assembled 3x3-block operators (EBE variant 8, the CRS-style comparator):
+// FP64 blocks for FP64 products, the FP32 high words of KMd for FP32 ones; DOT (red != nullptr) fuses p^T q
+// and the CG step length as the EBE products do.  Not for fused groups.
+template <typename T>
+cudaError_t launch_bcsr_apply(const MeshView& m, int rpad, const int32_t* row_ptr, const int32_t* col,
+                              const double* Kb, const double* Mb, const float2* KMd, const T* p, T* q, double aM,
+                              double aK, const Reducer* red, CgCase* sc, double* ptq_out, const int* gate,
+                              cudaStream_t s);
 cudaError_t launch_bcsr_split(const MeshView& m, int rpad, const int32_t* row_ptr, const int32_t* col,
                               const double* Kb, const double* Mb, const float2* KMd, const double* p, float2* p_df,
                               double* qM, double* qK, cudaStream_t s);
@@ -473,6 +481,30 @@ __device__ __forceinline__ bool block_reduce_last_seg(double* acc, int ncase, co
   if (threadIdx.x == 0) *red.counter = 0u;
   __syncthreads();
   return true;
+}
+
+// Last block of a product with the fused p^T q: publish it and set the CG step length alpha.
+__device__ __forceinline__ void ebe_tail(const Reducer& red, CgCase* sc, double* ptq_out, int rpad) {
+  if (threadIdx.x < rpad) {
+    const int c = threadIdx.x;
+    const double pq = red.out[c];
+    if (ptq_out) ptq_out[c] = pq;
+    if (sc) {
+      CgCase& s = sc[c];
+      s.pq = pq;
+      if (s.active) {
+        if (!(pq > 0.0) || !isfinite(pq)) {
+          s.active = 0;
+          s.status = FEM_ERR_BREAKDOWN;
+          s.alpha = 0.0;
+        } else {
+          s.alpha = s.rho / pq;
+        }
+      } else {
+        s.alpha = 0.0;
+      }
+    }
+  }
 }
 
 // Per-case sums over the grid.  Threads hold vals[q] for case c = threadIdx.x % rpad (the grid stride of

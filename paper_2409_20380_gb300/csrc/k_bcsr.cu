@@ -171,6 +171,62 @@ int lg2(int r) {
   return s;
 }
 
+// q = (aM M + aK K) p with the assembled operators (variant 8: the CRS-style product the paper compares the
+// EBE with, Section 3.3), one thread per (node row, case), K p and M p accumulated apart and combined once.
+// FP64 products read the FP64 blocks; FP32 products read the high words of the (hi, lo) block records (the
+// FP32 rounding of the FP64 values).  Dirichlet rows of q are zero; DOT fuses p^T q per case.
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(256) k_bcsr_apply(int64_t N, int rpad, int rshift, const int32_t* __restrict__ row_ptr,
+                                                    const int32_t* __restrict__ col, const double* __restrict__ Kb,
+                                                    const double* __restrict__ Mb, const float4* __restrict__ KM,
+                                                    const uint8_t* __restrict__ fm, const T* __restrict__ p,
+                                                    T* __restrict__ q, T aM, T aK, Reducer red, CgCase* sc,
+                                                    double* ptq_out, const int* gate) {
+  if (gate && *gate == 0) return;
+  double dot = 0.0;
+  const int64_t total = N << rshift;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = t >> rshift;
+    const int c = (int)(t & (rpad - 1));
+    T kp[3] = {0, 0, 0}, mp[3] = {0, 0, 0};
+    const int lo = __ldg(row_ptr + n), hi = __ldg(row_ptr + n + 1);
+    for (int j = lo; j < hi; ++j) {
+      const int64_t cn = __ldg(col + j);
+      T pv[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pv[k] = __ldg(p + (cn * 3 + k) * rpad + c);
+      T K[9], Mv;
+      if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int u = 0; u < 9; ++u) K[u] = __ldg(Kb + j * 9 + u);
+        Mv = __ldg(Mb + j);
+      } else {
+        const float4* rec = KM + j * 5;
+        const float4 q0 = __ldg(rec), q1 = __ldg(rec + 1), q2 = __ldg(rec + 2), q3 = __ldg(rec + 3), q4 = __ldg(rec + 4);
+        K[0] = q0.x, K[1] = q0.z, K[2] = q1.x, K[3] = q1.z, K[4] = q2.x, K[5] = q2.z, K[6] = q3.x, K[7] = q3.z;
+        K[8] = q4.x, Mv = q4.z;
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        mp[i] += Mv * pv[i];
+        kp[i] += K[3 * i] * pv[0] + K[3 * i + 1] * pv[1] + K[3 * i + 2] * pv[2];
+      }
+    }
+    const uint8_t f = fm[n];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int64_t id = (n * 3 + i) * rpad + c;
+      const T v = dof_free(f, i) ? aM * mp[i] + aK * kp[i] : (T)0;
+      q[id] = v;
+      if (DOT) dot += (double)(p[id] * v);
+    }
+  }
+  if (DOT) {
+    double v[1] = {dot};
+    if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
+  }
+}
+
 int grid_of(int64_t items) {
   int64_t g = (items + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
@@ -191,6 +247,32 @@ cudaError_t launch_bcsr_assemble(const MeshView& m, const int32_t* row_ptr, cons
   k_to_kmd<<<grid_of(10 * nnz), 256, 0, s>>>(nnz, Kb, Mb, KMd);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_bcsr_apply(const MeshView& m, int rpad, const int32_t* row_ptr, const int32_t* col,
+                              const double* Kb, const double* Mb, const float2* KMd, const T* p, T* q, double aM,
+                              double aK, const Reducer* red, CgCase* sc, double* ptq_out, const int* gate,
+                              cudaStream_t s) {
+  if (!row_ptr || m.seg) return cudaErrorInvalidValue;
+  const int rs = lg2(rpad);
+  int grid = grid_of(m.N << rs);
+  if (grid > kMaxRedBlocks) grid = kMaxRedBlocks;
+  const float4* km = reinterpret_cast<const float4*>(KMd);
+  Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
+  if (red)
+    k_bcsr_apply<T, true><<<grid, 256, 0, s>>>(m.N, rpad, rs, row_ptr, col, Kb, Mb, km, m.freemask, p, q, (T)aM,
+                                               (T)aK, rd, sc, ptq_out, gate);
+  else
+    k_bcsr_apply<T, false><<<grid, 256, 0, s>>>(m.N, rpad, rs, row_ptr, col, Kb, Mb, km, m.freemask, p, q, (T)aM,
+                                                (T)aK, rd, nullptr, nullptr, gate);
+  return cudaGetLastError();
+}
+template cudaError_t launch_bcsr_apply<double>(const MeshView&, int, const int32_t*, const int32_t*, const double*,
+                                               const double*, const float2*, const double*, double*, double, double,
+                                               const Reducer*, CgCase*, double*, const int*, cudaStream_t);
+template cudaError_t launch_bcsr_apply<float>(const MeshView&, int, const int32_t*, const int32_t*, const double*,
+                                              const double*, const float2*, const float*, float*, double, double,
+                                              const Reducer*, CgCase*, double*, const int*, cudaStream_t);
 
 cudaError_t launch_to_df(int64_t n, const double* v, float2* out, cudaStream_t s) {
   k_to_df<<<grid_of(n), 256, 0, s>>>(n, v, out);

@@ -14,30 +14,6 @@ template <typename T> __device__ __forceinline__ const T* rec_of(const MeshView&
 template <> __device__ __forceinline__ const double* rec_of<double>(const MeshView& m) { return m.rec64; }
 template <> __device__ __forceinline__ const float* rec_of<float>(const MeshView& m) { return m.rec32; }
 
-// Last block of a product with the fused p^T q: publish it and set the CG step length alpha.
-__device__ __forceinline__ void ebe_tail(const Reducer& red, CgCase* sc, double* ptq_out, int rpad) {
-  if (threadIdx.x < rpad) {
-    const int c = threadIdx.x;
-    const double pq = red.out[c];
-    if (ptq_out) ptq_out[c] = pq;
-    if (sc) {
-      CgCase& s = sc[c];
-      s.pq = pq;
-      if (s.active) {
-        if (!(pq > 0.0) || !isfinite(pq)) {
-          s.active = 0;
-          s.status = FEM_ERR_BREAKDOWN;
-          s.alpha = 0.0;
-        } else {
-          s.alpha = s.rho / pq;
-        }
-      } else {
-        s.alpha = 0.0;
-      }
-    }
-  }
-}
-
 // Same for fused groups: cases 0..nc-1, totals in red.out[c].
 __device__ __forceinline__ void ebe_tail_seg(const Reducer& red, CgCase* sc, double* ptq_out, int nc) {
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {

@@ -26,9 +26,10 @@ def torch_dev():
 CASES = [((7, 5, 4), 1, 0.0), ((7, 5, 4), 4, 0.2), ((9, 6, 5), 16, 0.1), ((3, 2, 2), 32, 0.0), ((12, 9, 7), 8, 0.15)]
 # (ebe_variant, hex_per_tile): generic element kernel; tiled hex kernel and staged tiled hex kernel with
 # automatic and small tiles (140..756 hexes over 64-hex tiles: several tiles and a ragged last one); 7 (hex
-# element matrices) applies to FP32 products with the mesh's coefficients and falls back to 5 (then 3) else
+# element matrices) applies to FP32 products with the mesh's coefficients and falls back to 5 (then 3) else;
+# 8 is the assembled 3x3-block (CRS-style) product
 VARIANTS = [(1, 0), (2, 0), (2, 64), (3, 0), (3, 64), (4, 0), (4, 64), (5, 0), (5, 64), (6, 0), (6, 64), (7, 0),
-            (7, 64)]
+            (7, 64), (8, 0)]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -143,14 +144,16 @@ def test_ebe_mesh_without_hex_patches(torch_dev):
             fem.fem_mesh_tune(h, 2, 0)
         ps = random_free_vectors(m, 4, seed=1)
         p = torch.tensor(from_cases(ps, m.n_nodes, 4), device="cuda")
-        q = torch.empty_like(p)
-        fem.fem_ebe_apply(h, p, q, 4, 1.0, 1.0)
-        torch.cuda.synchronize()
-        qs = to_cases(q.cpu().numpy(), m.n_nodes, 4)
-        for c in range(4):
-            ref = (sysm.M + sysm.K) @ ps[c]
-            ref[m.fixed_dof == 1] = 0.0
-            assert np.abs(qs[c] - ref).max() <= 1e-13 * np.abs(ref).max()
+        for variant in (0, 8):      # generic element kernel; assembled blocks (any mesh)
+            fem.fem_mesh_tune(h, variant, 0)
+            q = torch.empty_like(p)
+            fem.fem_ebe_apply(h, p, q, 4, 1.0, 1.0)
+            torch.cuda.synchronize()
+            qs = to_cases(q.cpu().numpy(), m.n_nodes, 4)
+            for c in range(4):
+                ref = (sysm.M + sysm.K) @ ps[c]
+                ref[m.fixed_dof == 1] = 0.0
+                assert np.abs(qs[c] - ref).max() <= 1e-13 * np.abs(ref).max(), variant
     finally:
         fem.fem_mesh_destroy(h)
 
@@ -170,7 +173,7 @@ def test_autotuned_product_matches_csr(torch_dev, precision, r):
         prec = fem.FEM_FP32_INNER if precision == "fp32" else fem.FEM_FP64
         v, hpt, ms = fem.fem_mesh_autotune(h, prec, r)
         assert (v, hpt) in [(1, 0), (2, 64), (2, 128), (2, 256), (2, 512), (3, 64), (3, 128), (3, 256), (4, 64),
-                            (4, 128), (5, 64), (5, 128), (6, 64), (6, 128), (6, 256), (7, 64)] and ms > 0
+                            (4, 128), (5, 64), (5, 128), (6, 64), (6, 128), (6, 256), (7, 64), (8, 0)] and ms > 0
         dt = torch.float32 if precision == "fp32" else torch.float64
         ps = random_free_vectors(m, r, seed=5 + r)
         p = torch.tensor(from_cases(ps, m.n_nodes, r), device="cuda", dtype=dt)
