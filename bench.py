@@ -66,7 +66,7 @@ def parse():
                     help="inner CG iterations per convergence check (graph: launches per WHILE-loop body)")
     ap.add_argument("--profile-steps", type=int, default=40,
                     help="steps after the timed region timed per kernel class with CUDA events (eager)")
-    ap.add_argument("--kernel", default=None, choices=["ebe", "split", "predictor"],
+    ap.add_argument("--kernel", default=None, choices=["ebe", "ebe10", "split", "predictor"],
                     help="time one kernel alone (EBE product) instead of the full step")
     ap.add_argument("--kernel-precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=0,
@@ -529,6 +529,57 @@ def run_kernel(args):
     fem.fem_mesh_destroy(h)
 
 
+# Tet10 product: per Gauss point ~70 flops of shape gradients, 9 x 10 FMAs for the displacement gradient,
+# ~24 for the stress, 30 x 3 FMAs for the nodal forces (454); four points, plus the 30 x 11 FMAs of the
+# consistent mass: ~2.48 kflop per element and case (FMA = 2)
+FLOP_PER_TET10_CASE = 4 * 454 + 660
+
+
+def run_kernel10(args):
+    """Times the tet10 EBE product alone (CUDA events, inputs resident) on the --dims mesh turned into 10-node
+    tets (edge midpoints), --cases cases."""
+    import torch
+    from paper_2409_20380_gb300 import build, fem
+    from paper_2409_20380_gb300 import workload as wl
+    build.build()
+    fem.lib()
+    torch.cuda.set_device(0)
+    Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
+    mesh = wl.tet10_mesh(wl.config2_mesh(Hx, Hy, Hz))
+    tp = wl.config2_time_params()
+    h = fem.fem_mesh10_create(mesh)
+    r = args.cases
+    dt = torch.float32 if args.kernel_precision == "fp32" else torch.float64
+    g = torch.Generator(device="cuda").manual_seed(0)
+    p = torch.randn(mesh.n_nodes * 3 * r, device="cuda", dtype=dt, generator=g)
+    p.view(mesh.n_nodes, 3, r)[torch.from_numpy(mesh.fixed_dof.reshape(-1, 3).astype(bool)).cuda()] = 0
+    q = torch.empty_like(p)
+    ptq = torch.zeros(r, dtype=torch.float64, device="cuda")
+    cM = 4.0 / tp.dt ** 2 + 2.0 * tp.a0 / tp.dt
+    cK = 1.0 + 2.0 * tp.a1 / tp.dt
+    for _ in range(args.warmup):
+        fem.fem_ebe10_apply(h, p, q, r, cM, cK, ptq)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fem.fem_ebe10_apply(h, p, q, r, cM, cK, ptq)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    w = 4 if args.kernel_precision == "fp32" else 8
+    E, N = mesh.n_elems, mesh.n_nodes
+    bytes_launch = E * (40 + 12 * w) + r * N * 3 * 2 * w
+    print(json.dumps({"kernel": "ebe10", "precision": args.kernel_precision, "dims": args.dims, "cases": r,
+                      "n_elems": E, "n_nodes": N, "ms_per_launch": ms,
+                      "alg_gbs": bytes_launch / (ms * 1e-3) / 1e9,
+                      "alg_tflops": FLOP_PER_TET10_CASE * E * r / (ms * 1e-3) / 1e12,
+                      "flop_per_elem_case": FLOP_PER_TET10_CASE,
+                      "note": "one thread per (element, case), global atomics; includes the q zero-fill and "
+                              "the Dirichlet mask pass"}), flush=True)
+    fem.fem_mesh10_destroy(h)
+
+
 def run_learned(args):
     """Learned proposal on the medium mesh: samples from --train-cases cases x --case-steps steps, Adam on
     the GPU, then --eval-cases held-out cases with and without the network (same certified tolerance)."""
@@ -774,6 +825,9 @@ def main():
         return
     if args.learned:
         run_learned(args)
+        return
+    if args.kernel == "ebe10":
+        run_kernel10(args)
         return
     if args.kernel == "ebe":
         run_kernel(args)

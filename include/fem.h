@@ -234,6 +234,33 @@ fem_status fem_ebe_apply_noalloc(fem_mesh* m, int precision, const void* p_dev, 
                                  double alpha_M, double alpha_K, double* ptq_dev, void* stream);
 
 /*
+ * 10-node tetrahedra, the paper's element (Section 3.1): a separate mesh object for the EBE product of
+ * quadratic tets (Section 3.2, Eq. eqebefem with 30 x 30 element operators formed on the fly).
+ * Straight-sided elements; local node order: corners 0-3, then the edge nodes of (0,1), (1,2), (0,2),
+ * (0,3), (1,3), (2,3).  Stiffness by the 4-point Gauss rule (exact for these elements), consistent mass
+ * by exact integration.
+ *   n_nodes, xyz     [n_nodes][3] host double, copied;  n_elems, conn10 [n_elems][10] host int32 (0-based);
+ *   mat_id           [n_elems] host int32 in [0, n_mat);  lam_mu_rho [n_mat][3] host double (lambda, mu, rho);
+ *   fixed_dof        [3 n_nodes] host uint8, 1 = Dirichlet;  stream: CUDA stream (NULL = default).
+ *   out              receives the handle (owned by the caller; release with fem_mesh10_destroy).
+ * Errors: FEM_ERR_ARG (null pointers, empty mesh, node ids out of range, a degenerate or inverted corner
+ * tet, a bad material id), FEM_ERR_CUDA.  The call synchronises the stream.
+ */
+typedef struct fem_mesh10 fem_mesh10;
+fem_status fem_mesh10_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn10,
+                             const int32_t* mat_id, int n_mat, const double* lam_mu_rho, const uint8_t* fixed_dof,
+                             void* stream, fem_mesh10** out);
+fem_status fem_mesh10_destroy(fem_mesh10* m);
+/*
+ * q = sum_e P_e^T ((alpha_M M_e + alpha_K K_e) (P_e p)) on the tet10 mesh, q = 0 on Dirichlet DOFs, for
+ * n_rhs (1, 2, 4, ..., 32) cases; the same layout, precision choice and optional ptq_dev (p^T q per case,
+ * element by element, FP64 reduction) as fem_ebe_apply.  Stream-ordered.  Errors: FEM_ERR_ARG,
+ * FEM_ERR_CUDA.
+ */
+fem_status fem_ebe10_apply(fem_mesh10* m, int precision, const void* p_dev, void* q_dev, int n_rhs,
+                           double alpha_M, double alpha_K, double* ptq_dev, void* stream);
+
+/*
  * Solves A x = b for n_rhs cases (Algorithm 1: 3x3 block-Jacobi PCG with the EBE product), starting from
  * the guess in x_dev.  With opts->precision = FEM_FP32_INNER the solve is an FP64 iterative refinement
  * whose corrections come from an FP32 inner PCG.  Either way each case stops when its FP64 true residual

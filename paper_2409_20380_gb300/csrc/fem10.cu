@@ -1,0 +1,325 @@
+// Element-by-element product for 10-node tetrahedra, the paper's element (Section 3.1; the EBE of
+// Section 3.2 / Eq. eqebefem applied to quadratic tets).  Straight-sided elements: the barycentric
+// gradients g_a are constant on a tet, so the element record is the tet4 one of its corners (g_1..g_3,
+// lambda V, mu V, rho V / 20) and the quadratic shape-function gradients are formed on the fly,
+//   corner a:    grad N_a  = (4 L_a - 1) g_a,       edge (a, b): grad N_ab = 4 (L_a g_b + L_b g_a),
+// at the four points of the degree-2 Gauss rule (exact for the stiffness, whose integrand is quadratic):
+//   (K p)_i = sum_q V/4 sigma(G_q) grad N_i(L_q),  G_q = sum_j p_j (x) grad N_j(L_q),
+//   sigma(G) = lambda tr(G) I + mu (G + G^T).
+// The consistent mass (M p)_i = rho V sum_j m_ij p_j uses the exact integrals m_ij = int N_i N_j dV / V,
+// generated here on the host from int L_0^a L_1^b L_2^c L_3^d dV = 6 V a! b! c! d! / (a + b + c + d + 3)!.
+// Local order: corners 0-3, edges (0,1), (1,2), (0,2), (0,3), (1,3), (2,3).  One thread per (element,
+// case); sums scatter with global atomics (Dirichlet rows masked afterwards).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fem_internal.cuh"
+
+namespace fem {
+
+namespace {
+
+// edge s joins corners edge_a(s) and edge_b(s)
+__host__ __device__ constexpr int edge_a(int s) { return s == 0 ? 0 : s == 1 ? 1 : s == 2 ? 0 : s == 3 ? 0 : s == 4 ? 1 : 2; }
+__host__ __device__ constexpr int edge_b(int s) { return s == 0 ? 1 : s == 1 ? 2 : s == 2 ? 2 : s == 3 ? 3 : s == 4 ? 3 : 3; }
+
+struct Mass10 {
+  float m32[55];    // upper triangle of m_ij, row-major (FP32 products)
+  double m64[55];   // (FP64 products)
+};
+
+// Exact m_ij = int N_i N_j dV / V by expanding N_i N_j into barycentric monomials.
+void mass10_host(double out[10][10]) {
+  // N_i as up to two terms c * L^e (exponents over L_0..L_3)
+  struct Term {
+    double c;
+    int e[4];
+  };
+  std::vector<std::vector<Term>> N(10);
+  for (int a = 0; a < 4; ++a) {
+    Term t2{2.0, {0, 0, 0, 0}}, t1{-1.0, {0, 0, 0, 0}};
+    t2.e[a] = 2;
+    t1.e[a] = 1;
+    N[a] = {t2, t1};
+  }
+  for (int k = 0; k < 6; ++k) {
+    Term t{4.0, {0, 0, 0, 0}};
+    t.e[edge_a(k)] += 1;
+    t.e[edge_b(k)] += 1;
+    N[4 + k] = {t};
+  }
+  auto fact = [](int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+  };
+  for (int i = 0; i < 10; ++i)
+    for (int j = 0; j < 10; ++j) {
+      double s = 0.0;
+      for (const Term& a : N[i])
+        for (const Term& b : N[j]) {
+          int e[4], deg = 0;
+          double num = 6.0;
+          for (int k = 0; k < 4; ++k) {
+            e[k] = a.e[k] + b.e[k];
+            deg += e[k];
+            num *= fact(e[k]);
+          }
+          s += a.c * b.c * num / fact(deg + 3);
+        }
+      out[i][j] = s;
+    }
+}
+
+__host__ __device__ constexpr int tri(int i, int j) { return i <= j ? i * 10 - i * (i - 1) / 2 + (j - i) : tri(j, i); }
+
+template <typename T> __device__ __forceinline__ T mcoef(const Mass10& mc, int i, int j);
+template <> __device__ __forceinline__ float mcoef<float>(const Mass10& mc, int i, int j) { return mc.m32[tri(i, j)]; }
+template <> __device__ __forceinline__ double mcoef<double>(const Mass10& mc, int i, int j) { return mc.m64[tri(i, j)]; }
+
+template <typename T> struct Rec10;
+template <> struct Rec10<float> {
+  static __device__ __forceinline__ const float* get(const float* r32, const double*) { return r32; }
+};
+template <> struct Rec10<double> {
+  static __device__ __forceinline__ const double* get(const float*, const double* r64) { return r64; }
+};
+
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe10(int64_t E, int rpad, int rshift, const int32_t* __restrict__ conn,
+                                                   const float* __restrict__ rec32, const double* __restrict__ rec64,
+                                                   const T* __restrict__ p, T* __restrict__ q, T aM, T aK,
+                                                   Mass10 mc, Reducer red, double* ptq_out) {
+  const T* __restrict__ recs = Rec10<T>::get(rec32, rec64);
+  // barycentric coordinates of the four Gauss points: (A, B, B, B) and its permutations
+  const T GA = (T)0.5854101966249685, GB = (T)0.1381966011250105;
+  double dot = 0.0;
+  const int64_t total = E << rshift;
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < total; it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = it >> rshift;
+    const int c = (int)(it & (rpad - 1));
+    int nd[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) nd[i] = __ldg(conn + e * 10 + i);
+    T P[10][3], Q[10][3];
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        P[i][k] = __ldg(p + ((int64_t)nd[i] * 3 + k) * rpad + c);
+        Q[i][k] = (T)0;
+      }
+    const T* r = recs + e * kRec;
+    T g[4][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      g[1][k] = r[k], g[2][k] = r[3 + k], g[3][k] = r[6 + k];
+      g[0][k] = -(g[1][k] + g[2][k] + g[3][k]);
+    }
+    const T lam = aK * r[9] * (T)0.25, mu = aK * r[10] * (T)0.25, rv = aM * r[11] * (T)20;   // V/4 weights
+#pragma unroll 1
+    for (int qp = 0; qp < 4; ++qp) {   // (not unrolled: one point's gradients live at a time)
+      T L[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) L[a] = a == qp ? GA : GB;
+      T dN[10][3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dN[a][k] = ((T)4 * L[a] - (T)1) * g[a][k];
+#pragma unroll
+      for (int s = 0; s < 6; ++s) {
+        const int a = edge_a(s), b = edge_b(s);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dN[4 + s][k] = (T)4 * (L[a] * g[b][k] + L[b] * g[a][k]);
+      }
+      T G[3][3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          T acc = (T)0;
+#pragma unroll
+          for (int i = 0; i < 10; ++i) acc += P[i][k] * dN[i][j];
+          G[k][j] = acc;
+        }
+      const T ltr = lam * (G[0][0] + G[1][1] + G[2][2]);
+      T S[3][3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) S[k][j] = mu * (G[k][j] + G[j][k]) + (k == j ? ltr : (T)0);
+#pragma unroll
+      for (int i = 0; i < 10; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Q[i][k] += S[k][0] * dN[i][0] + S[k][1] * dN[i][1] + S[k][2] * dN[i][2];
+    }
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        T acc = (T)0;
+#pragma unroll
+        for (int j = 0; j < 10; ++j) acc += mcoef<T>(mc, i, j) * P[j][k];
+        Q[i][k] += rv * acc;
+      }
+    double hd = 0.0;
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (DOT) hd += (double)(P[i][k] * Q[i][k]);
+        atomicAdd(q + ((int64_t)nd[i] * 3 + k) * rpad + c, Q[i][k]);
+      }
+    dot += hd;
+  }
+  if (DOT) {
+    double v[1] = {dot};
+    if (block_reduce_last<1>(v, rpad, red) && threadIdx.x < rpad && ptq_out) ptq_out[threadIdx.x] = red.out[threadIdx.x];
+  }
+}
+
+__global__ void k_corner_conn(int64_t E, const int32_t* __restrict__ conn10, int4* __restrict__ conn4) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
+    conn4[e] = make_int4(conn10[e * 10], conn10[e * 10 + 1], conn10[e * 10 + 2], conn10[e * 10 + 3]);
+}
+
+int lg2i(int r) {
+  int s = 0;
+  while ((1 << s) < r) ++s;
+  return s;
+}
+
+}  // namespace
+}  // namespace fem
+
+using namespace fem;
+
+struct fem_mesh10 {
+  int64_t N = 0, E = 0;
+  int device = 0;
+  int32_t* conn = nullptr;    // [E][10]
+  float* rec32 = nullptr;     // [E][12] records of the corner tets
+  double* rec64 = nullptr;
+  uint8_t* fm = nullptr;      // [N] free-DOF bits
+  double* partial = nullptr;  // reduction scratch
+  unsigned* counter = nullptr;
+  double* out = nullptr;
+  Mass10 mc{};
+  ~fem_mesh10() {
+    cudaFree(conn); cudaFree(rec32); cudaFree(rec64); cudaFree(fm); cudaFree(partial); cudaFree(counter); cudaFree(out);
+  }
+};
+
+extern "C" {
+
+fem_status fem_mesh10_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn10,
+                             const int32_t* mat_id, int n_mat, const double* lam_mu_rho, const uint8_t* fixed_dof,
+                             void* stream, fem_mesh10** out) {
+  if (!out) return set_error(FEM_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!xyz || !conn10 || !mat_id || !lam_mu_rho || !fixed_dof) return set_error(FEM_ERR_ARG, "null input pointer");
+  if (n_nodes < 10 || n_elems < 1 || n_mat < 1) return set_error(FEM_ERR_ARG, "empty mesh");
+  if (n_nodes > INT32_MAX) return set_error(FEM_ERR_ARG, "node ids must fit int32");
+  for (int64_t i = 0; i < n_elems * 10; ++i)
+    if (conn10[i] < 0 || conn10[i] >= n_nodes) return set_error(FEM_ERR_ARG, "connectivity out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  fem_mesh10* m = new fem_mesh10();
+  m->N = n_nodes, m->E = n_elems;
+  cudaGetDevice(&m->device);
+  double* d_xyz = nullptr;
+  int32_t* d_mat = nullptr;
+  double* d_lmr = nullptr;
+  int4* d_c4 = nullptr;
+  int* d_err = nullptr;
+  std::vector<uint8_t> fm(n_nodes);
+  for (int64_t n = 0; n < n_nodes; ++n)
+    fm[n] = (uint8_t)((fixed_dof[3 * n] ? 0 : 1) | (fixed_dof[3 * n + 1] ? 0 : 2) | (fixed_dof[3 * n + 2] ? 0 : 4));
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  al((void**)&m->conn, sizeof(int32_t) * 10 * n_elems);
+  al((void**)&m->rec32, sizeof(float) * kRec * n_elems);
+  al((void**)&m->rec64, sizeof(double) * kRec * n_elems);
+  al((void**)&m->fm, n_nodes);
+  al((void**)&m->partial, sizeof(double) * kMaxRedBlocks * 3 * kMaxCases);
+  al((void**)&m->counter, sizeof(unsigned));
+  al((void**)&m->out, sizeof(double) * 3 * kMaxCases);
+  al((void**)&d_xyz, sizeof(double) * 3 * n_nodes);
+  al((void**)&d_mat, sizeof(int32_t) * n_elems);
+  al((void**)&d_lmr, sizeof(double) * 3 * n_mat);
+  al((void**)&d_c4, sizeof(int4) * n_elems);
+  al((void**)&d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->conn, conn10, sizeof(int32_t) * 10 * n_elems, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->fm, fm.data(), n_nodes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_xyz, xyz, sizeof(double) * 3 * n_nodes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_mat, mat_id, sizeof(int32_t) * n_elems, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_lmr, lam_mu_rho, sizeof(double) * 3 * n_mat, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->counter, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_corner_conn<<<grid_for(n_elems), kBlock, 0, s>>>(n_elems, m->conn, d_c4);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_elem_setup(n_elems, n_nodes, d_xyz, d_c4, d_mat, n_mat, d_lmr, m->rec64, m->rec32, d_err, s);
+  int h_err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_xyz); cudaFree(d_mat); cudaFree(d_lmr); cudaFree(d_c4); cudaFree(d_err);
+  if (e != cudaSuccess || h_err) {
+    cudaGetLastError();
+    delete m;
+    if (e != cudaSuccess) return set_error(FEM_ERR_CUDA, std::string("tet10 mesh: ") + cudaGetErrorString(e));
+    return set_error(FEM_ERR_ARG, h_err & 2 ? "degenerate or inverted corner tet" : "bad material id");
+  }
+  double mm[10][10];
+  mass10_host(mm);
+  for (int i = 0; i < 10; ++i)
+    for (int j = i; j < 10; ++j) {
+      m->mc.m64[tri(i, j)] = mm[i][j];
+      m->mc.m32[tri(i, j)] = (float)mm[i][j];
+    }
+  *out = m;
+  return FEM_OK;
+}
+
+fem_status fem_mesh10_destroy(fem_mesh10* m) {
+  delete m;
+  return FEM_OK;
+}
+
+fem_status fem_ebe10_apply(fem_mesh10* m, int precision, const void* p_dev, void* q_dev, int n_rhs, double alpha_M,
+                           double alpha_K, double* ptq_dev, void* stream) {
+  if (!m || !p_dev || !q_dev) return set_error(FEM_ERR_ARG, "null argument");
+  if (n_rhs < 1 || n_rhs > kMaxRpad || (n_rhs & (n_rhs - 1))) return set_error(FEM_ERR_ARG, "n_rhs must be 1, 2, 4, 8, 16 or 32");
+  if (precision != FEM_FP64 && precision != FEM_FP32_INNER) return set_error(FEM_ERR_ARG, "unknown precision");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int rs = lg2i(n_rhs);
+  const int64_t items = m->E << rs;
+  int grid = grid_for(items, kMaxRedBlocks);
+  const Reducer red{m->partial, m->counter, m->out};
+  const bool dot = ptq_dev != nullptr;
+  const size_t bytes = (precision == FEM_FP64 ? 8 : 4) * (size_t)m->N * 3 * n_rhs;
+  cudaError_t e = cudaMemsetAsync(q_dev, 0, bytes, s);
+  if (e == cudaSuccess) {
+    if (precision == FEM_FP64) {
+      auto fn = dot ? k_ebe10<double, true> : k_ebe10<double, false>;
+      fn<<<grid, kBlock, 0, s>>>(m->E, n_rhs, rs, m->conn, m->rec32, m->rec64, (const double*)p_dev, (double*)q_dev,
+                                 alpha_M, alpha_K, m->mc, red, ptq_dev);
+    } else {
+      auto fn = dot ? k_ebe10<float, true> : k_ebe10<float, false>;
+      fn<<<grid, kBlock, 0, s>>>(m->E, n_rhs, rs, m->conn, m->rec32, m->rec64, (const float*)p_dev, (float*)q_dev,
+                                 (float)alpha_M, (float)alpha_K, m->mc, red, ptq_dev);
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = precision == FEM_FP64 ? launch_mask<double>(m->N, n_rhs, m->fm, (double*)q_dev, s)
+                              : launch_mask<float>(m->N, n_rhs, m->fm, (float*)q_dev, s);
+  if (e != cudaSuccess) return set_error(FEM_ERR_CUDA, std::string("tet10 product: ") + cudaGetErrorString(e));
+  return FEM_OK;
+}
+
+}  // extern "C"

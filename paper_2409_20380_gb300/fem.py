@@ -25,7 +25,7 @@ FEM_FIELD_U, FEM_FIELD_V, FEM_FIELD_A, FEM_FIELD_DU, FEM_FIELD_B, FEM_FIELD_GUES
 EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_tune", "fem_mesh_autotune",
            "fem_mesh_info", "fem_mesh_split_product",
            "fem_mesh_set_regions", "fem_ebe_apply",
-           "fem_ebe_apply_noalloc",
+           "fem_ebe_apply_noalloc", "fem_mesh10_create", "fem_mesh10_destroy", "fem_ebe10_apply",
            "pcg_solve", "fem_batch_create", "fem_batch_destroy", "fem_case_add", "fem_step", "predictor_fit",
            "predictor_predict", "fem_case_get", "fem_batch_set_loads", "fem_batch_get_field", "fem_batch_get_field_async",
            "fem_batch_sync", "fem_step_async", "fem_batch_profile",
@@ -94,6 +94,9 @@ def lib():
         "fem_mesh_set_regions": (I, [P, P]),
         "fem_ebe_apply": (I, [P, I, P, P, I, D, D, P, P]),
         "fem_ebe_apply_noalloc": (I, [P, I, P, P, I, D, D, P, P]),
+        "fem_mesh10_create": (I, [I64, P, I64, P, P, I, P, P, P, ctypes.POINTER(P)]),
+        "fem_mesh10_destroy": (I, [P]),
+        "fem_ebe10_apply": (I, [P, I, P, P, I, D, D, P, P]),
         "pcg_solve": (I, [P, P, P, I, ctypes.POINTER(fem_opts), P, P, P]),
         "fem_batch_create": (I, [ctypes.POINTER(fem_opts), P, ctypes.POINTER(P)]),
         "fem_batch_destroy": (I, [P]),
@@ -230,6 +233,32 @@ def fem_ebe_apply_noalloc(h, p, q, n_rhs, alpha_M, alpha_K, ptq=None, precision=
     dt = torch.float64 if precision == FEM_FP64 else torch.float32
     _check(lib().fem_ebe_apply_noalloc(h, precision, _ptr(p, dt), _ptr(q, dt), n_rhs, float(alpha_M),
                                        float(alpha_K), _ptr(ptq, torch.float64), _stream(stream)))
+
+
+def fem_mesh10_create(mesh10, stream=None):
+    """mesh10: workload.Mesh10 (host arrays, corners then edge midpoints).  Returns an opaque handle."""
+    xyz = np.ascontiguousarray(mesh10.xyz, dtype=np.float64)
+    conn = np.ascontiguousarray(mesh10.conn, dtype=np.int32)
+    mat = np.ascontiguousarray(mesh10.mat_id, dtype=np.int32)
+    lmr = np.ascontiguousarray(mesh10.lam_mu_rho, dtype=np.float64)
+    fixed = np.ascontiguousarray(mesh10.fixed_dof, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    _check(lib().fem_mesh10_create(xyz.shape[0], _np_ptr(xyz), conn.shape[0], _np_ptr(conn), _np_ptr(mat),
+                                   lmr.shape[0], _np_ptr(lmr), _np_ptr(fixed), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def fem_mesh10_destroy(h):
+    _check(lib().fem_mesh10_destroy(h))
+
+
+def fem_ebe10_apply(h, p, q, n_rhs, alpha_M, alpha_K, ptq=None, precision=None, stream=None):
+    import torch
+    if precision is None:
+        precision = FEM_FP64 if p.dtype == torch.float64 else FEM_FP32_INNER
+    dt = torch.float64 if precision == FEM_FP64 else torch.float32
+    _check(lib().fem_ebe10_apply(h, precision, _ptr(p, dt), _ptr(q, dt), n_rhs, float(alpha_M), float(alpha_K),
+                                 _ptr(ptq, torch.float64), _stream(stream)))
 
 
 def pcg_solve(h, b, x, n_rhs, opts, stream=None, raise_on_error=True):

@@ -279,3 +279,51 @@ def config5_sources(mesh: Mesh, n_train: int = 200, n_eval: int = 32):
     train = [random_source(mesh, rng_for(5, 0, c, 2)) for c in range(n_train)]
     held = [random_source(mesh, rng_for(5, 0, 100000 + c, 2)) for c in range(n_eval)]
     return train, held
+
+
+# --------------------------------------------------------------------------------------------------------
+# 10-node tetrahedra (the paper's element, Section 3.1): the tet4 mesh with a node added at the midpoint of
+# every edge.  Local order: corners 0-3, then the edges (0,1), (1,2), (0,2), (0,3), (1,3), (2,3).
+# --------------------------------------------------------------------------------------------------------
+TET10_EDGES = ((0, 1), (1, 2), (0, 2), (0, 3), (1, 3), (2, 3))
+
+
+@dataclasses.dataclass
+class Mesh10:
+    """A straight-sided tet10 mesh: corners of the tet4 mesh plus edge midpoints."""
+    xyz: np.ndarray          # [N10][3] float64 (the tet4 nodes first, then one node per edge)
+    conn: np.ndarray         # [E][10] int32
+    mat_id: np.ndarray       # [E] int32
+    lam_mu_rho: np.ndarray   # [n_mat][3] float64
+    fixed_dof: np.ndarray    # [3 N10] uint8 (an edge node is fixed where both ends are)
+
+    @property
+    def n_nodes(self) -> int:
+        return self.xyz.shape[0]
+
+    @property
+    def n_elems(self) -> int:
+        return self.conn.shape[0]
+
+
+def tet10_mesh(mesh: Mesh) -> Mesh10:
+    """Mid-edge nodes for every distinct edge of the tet4 mesh (numbered after the corner nodes in order of
+    first appearance)."""
+    conn4 = mesh.conn.astype(np.int64)
+    E, N = conn4.shape[0], mesh.n_nodes
+    pairs = np.stack([np.stack([conn4[:, a], conn4[:, b]], axis=1) for a, b in TET10_EDGES], axis=1)   # [E][6][2]
+    lo, hi = pairs.min(axis=2), pairs.max(axis=2)
+    key = (lo * N + hi).reshape(-1)
+    uniq, first, inv = np.unique(key, return_index=True, return_inverse=True)
+    order = np.argsort(first, kind="stable")            # edges numbered by first appearance
+    rank = np.empty_like(order)
+    rank[order] = np.arange(order.size)
+    edge_id = rank[inv].reshape(E, 6)
+    ulo, uhi = (uniq // N)[order], (uniq % N)[order]
+    xyz = np.concatenate([mesh.xyz, 0.5 * (mesh.xyz[ulo] + mesh.xyz[uhi])], axis=0)
+    conn = np.concatenate([conn4, N + edge_id], axis=1).astype(np.int32)
+    f4 = mesh.fixed_dof.reshape(N, 3)
+    fe = f4[ulo] & f4[uhi]
+    fixed = np.concatenate([f4, fe], axis=0).reshape(-1).astype(np.uint8)
+    return Mesh10(np.ascontiguousarray(xyz), np.ascontiguousarray(conn), mesh.mat_id.copy(),
+                  mesh.lam_mu_rho.copy(), np.ascontiguousarray(fixed))

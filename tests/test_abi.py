@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "fem.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:fem_status|void|const char\s*\*)\s*\**\s*([a-z_]+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:fem_status|void|const char\s*\*)\s*\**\s*([a-z_0-9]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 

@@ -1,0 +1,85 @@
+"""Tet10 EBE product on the GPU (the paper's element, Section 3.1; Eq. eqebefem with 30 x 30 element
+operators formed on the fly) against the tet10 oracle's assembled CSR matrices, element by element of the
+output, for 1..32 interleaved cases, FP64 and FP32.
+
+Tolerances: FP64 differs from the CSR product only by summation order (1e-13 of the vector's largest
+entry); FP32 records and arithmetic give ~1e-7 relative per entry, bounded here by 5e-6 (the tet10
+operator's entries span a wider range than the tet4 ones: edge/corner couplings of both signs)."""
+import numpy as np
+import pytest
+
+from oracle import tet10_oracle as t10
+from paper_2409_20380_gb300 import fem
+from paper_2409_20380_gb300 import workload as wl
+from helpers import from_cases, random_free_vectors, small_mesh, to_cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    from paper_2409_20380_gb300 import build
+    build.build()
+    fem.lib()
+    assert torch.cuda.is_available()
+    return torch
+
+
+CASES = [((3, 2, 2), 1, 0.0), ((5, 4, 3), 4, 0.2), ((6, 5, 4), 16, 0.1), ((2, 2, 1), 32, 0.0)]
+
+
+@pytest.mark.parametrize("dims,r,perturb", CASES)
+@pytest.mark.parametrize("coef", ["A", "M", "K"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ebe10_matches_csr(torch_dev, dims, r, perturb, coef, precision):
+    torch = torch_dev
+    m10 = wl.tet10_mesh(small_mesh(*dims, perturb=perturb))
+    K, M = t10.assemble10(m10.xyz, m10.conn, m10.mat_id, m10.lam_mu_rho)
+    tp = wl.TimeParams()
+    cM = 4.0 / tp.dt ** 2 + 2.0 * tp.a0 / tp.dt
+    cK = 1.0 + 2.0 * tp.a1 / tp.dt
+    aM, aK = {"A": (cM, cK), "M": (1.0, 0.0), "K": (0.0, 1.0)}[coef]
+    ref_mat = aM * M + aK * K
+    h = fem.fem_mesh10_create(m10)
+    try:
+        dt = torch.float64 if precision == "fp64" else torch.float32
+        ps = random_free_vectors(m10, r, seed=11 + r)
+        if precision == "fp32":
+            ps = [x.astype(np.float32).astype(np.float64) for x in ps]
+        p = torch.tensor(from_cases(ps, m10.n_nodes, r), device="cuda", dtype=dt)
+        q = torch.full_like(p, 5.0)                      # stale contents must be overwritten
+        ptq = torch.zeros(r, dtype=torch.float64, device="cuda")
+        fem.fem_ebe10_apply(h, p, q, r, aM, aK, ptq)
+        torch.cuda.synchronize()
+        qs = to_cases(q.cpu().double().numpy(), m10.n_nodes, r)
+        fixed = m10.fixed_dof == 1
+        tol = 1e-13 if precision == "fp64" else 5e-6
+        for c in range(r):
+            ref = ref_mat @ ps[c]
+            ref[fixed] = 0.0
+            assert np.all(qs[c][fixed] == 0.0)
+            err = np.abs(qs[c] - ref).max() / np.abs(ref).max()
+            assert err < tol, (c, err)
+            d_ref = ps[c] @ (ref_mat @ ps[c])
+            assert abs(ptq[c].item() - d_ref) <= tol * abs(d_ref)
+    finally:
+        fem.fem_mesh10_destroy(h)
+
+
+def test_ebe10_argument_errors(torch_dev):
+    torch = torch_dev
+    m10 = wl.tet10_mesh(small_mesh(2, 2, 1))
+    bad = wl.Mesh10(m10.xyz, m10.conn.copy(), m10.mat_id, m10.lam_mu_rho, m10.fixed_dof)
+    bad.conn[0, 5] = m10.n_nodes                         # node id out of range
+    with pytest.raises(fem.FemError) as ei:
+        fem.fem_mesh10_create(bad)
+    assert ei.value.status == fem.FEM_ERR_ARG
+    h = fem.fem_mesh10_create(m10)
+    try:
+        p = torch.zeros(m10.n_nodes * 3 * 3, dtype=torch.float64, device="cuda")
+        with pytest.raises(fem.FemError) as ei:
+            fem.fem_ebe10_apply(h, p, p.clone(), 3, 1.0, 1.0)   # n_rhs not a power of two
+        assert ei.value.status == fem.FEM_ERR_ARG
+    finally:
+        fem.fem_mesh10_destroy(h)
