@@ -529,10 +529,10 @@ def run_kernel(args):
     fem.fem_mesh_destroy(h)
 
 
-# Tet10 product: per Gauss point ~70 flops of shape gradients, 9 x 10 FMAs for the displacement gradient,
-# ~24 for the stress, 30 x 3 FMAs for the nodal forces (454); four points, plus the 30 x 11 FMAs of the
-# consistent mass: ~2.48 kflop per element and case (FMA = 2)
-FLOP_PER_TET10_CASE = 4 * 454 + 660
+# Tet10 product as executed: per Gauss point the corner-weighted sums W_a (84 flops), G = sum W_a g_a^T (63),
+# the stress (21), T_a = sigma g_a (60), the nodal forces (78) and the point's coefficients (12): 318; four
+# points, plus the 30 x 11 FMAs of the consistent mass (660): ~1.93 kflop per element and case (FMA = 2)
+FLOP_PER_TET10_CASE = 4 * 318 + 660
 
 
 def run_kernel10(args):

@@ -254,8 +254,9 @@ fem_status fem_mesh10_destroy(fem_mesh10* m);
 /*
  * q = sum_e P_e^T ((alpha_M M_e + alpha_K K_e) (P_e p)) on the tet10 mesh, q = 0 on Dirichlet DOFs, for
  * n_rhs (1, 2, 4, ..., 32) cases; the same layout, precision choice and optional ptq_dev (p^T q per case,
- * element by element, FP64 reduction) as fem_ebe_apply.  Stream-ordered.  Errors: FEM_ERR_ARG,
- * FEM_ERR_CUDA.
+ * element by element, FP64 reduction) as fem_ebe_apply.  Stream-ordered; calls on one mesh share its
+ * reduction scratch, so calls whose kernels could overlap (two streams without ordering) must not share a
+ * mesh.  Errors: FEM_ERR_ARG, FEM_ERR_CUDA.
  */
 fem_status fem_ebe10_apply(fem_mesh10* m, int precision, const void* p_dev, void* q_dev, int n_rhs,
                            double alpha_M, double alpha_K, double* ptq_dev, void* stream);
