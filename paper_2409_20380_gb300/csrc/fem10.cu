@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe10(int64_
     // corners: G = sum_a W_a (x) g_a with W_a = sum_i c_ia p_i, and the forces sum_a c_ia (sigma g_a):
     //   W_a = (4 L_a - 1) p_a + 4 sum_{edges (a, b)} L_b p_ab,
     //   f_a += (4 L_a - 1) T_a,   f_ab += 4 (L_a T_b + L_b T_a),   T_a = sigma g_a.
-#pragma unroll 1
-    for (int qp = 0; qp < 4; ++qp) {   // (not unrolled: one point's values live at a time)
+#pragma unroll
+    for (int qp = 0; qp < 4; ++qp) {   // (unrolled: the points' coefficients are constants)
       T L[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) L[a] = a == qp ? GA : GB;
