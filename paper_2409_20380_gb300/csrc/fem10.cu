@@ -87,7 +87,8 @@ template <> struct Rec10<double> {
   static __device__ __forceinline__ const double* get(const float*, const double* r64) { return r64; }
 };
 
-template <typename T, bool DOT>
+// I: index type of the vector offsets (32-bit when N * 3 * rpad fits: one multiply-add an address)
+template <typename T, bool DOT, typename I>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe10(int64_t E, int rpad, int rshift, const int32_t* __restrict__ conn,
                                                    const float* __restrict__ rec32, const double* __restrict__ rec64,
                                                    const T* __restrict__ p, T* __restrict__ q, T aM, T aK,
@@ -100,15 +101,15 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe10(int64_
   for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < total; it += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = it >> rshift;
     const int c = (int)(it & (rpad - 1));
-    int nd[10];
+    I off[10];   // offset of node i's first value of case c
 #pragma unroll
-    for (int i = 0; i < 10; ++i) nd[i] = __ldg(conn + e * 10 + i);
+    for (int i = 0; i < 10; ++i) off[i] = (I)__ldg(conn + e * 10 + i) * (I)(3 * rpad) + (I)c;
     T P[10][3], Q[10][3];
 #pragma unroll
     for (int i = 0; i < 10; ++i)
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        P[i][k] = __ldg(p + ((int64_t)nd[i] * 3 + k) * rpad + c);
+        P[i][k] = __ldg(p + off[i] + (I)(k * rpad));
         Q[i][k] = (T)0;
       }
     const T* r = recs + e * kRec;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe10(int64_
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         if (DOT) hd += P[i][k] * Q[i][k];
-        atomicAdd(q + ((int64_t)nd[i] * 3 + k) * rpad + c, Q[i][k]);
+        atomicAdd(q + off[i] + (I)(k * rpad), Q[i][k]);
       }
     if (DOT) dot += (double)hd;
   }
@@ -321,12 +322,15 @@ fem_status fem_ebe10_apply(fem_mesh10* m, int precision, const void* p_dev, void
   const size_t bytes = (precision == FEM_FP64 ? 8 : 4) * (size_t)m->N * 3 * n_rhs;
   cudaError_t e = cudaMemsetAsync(q_dev, 0, bytes, s);
   if (e == cudaSuccess) {
+    const bool i32 = m->N * 3 * n_rhs < ((int64_t)1 << 31);
     if (precision == FEM_FP64) {
-      auto fn = dot ? k_ebe10<double, true> : k_ebe10<double, false>;
+      auto fn = dot ? (i32 ? k_ebe10<double, true, int32_t> : k_ebe10<double, true, int64_t>)
+                    : (i32 ? k_ebe10<double, false, int32_t> : k_ebe10<double, false, int64_t>);
       fn<<<grid, kBlock, 0, s>>>(m->E, n_rhs, rs, m->conn, m->rec32, m->rec64, (const double*)p_dev, (double*)q_dev,
                                  alpha_M, alpha_K, m->mc, red, ptq_dev);
     } else {
-      auto fn = dot ? k_ebe10<float, true> : k_ebe10<float, false>;
+      auto fn = dot ? (i32 ? k_ebe10<float, true, int32_t> : k_ebe10<float, true, int64_t>)
+                    : (i32 ? k_ebe10<float, false, int32_t> : k_ebe10<float, false, int64_t>);
       fn<<<grid, kBlock, 0, s>>>(m->E, n_rhs, rs, m->conn, m->rec32, m->rec64, (const float*)p_dev, (float*)q_dev,
                                  (float)alpha_M, (float)alpha_K, m->mc, red, ptq_dev);
     }
