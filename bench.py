@@ -66,7 +66,7 @@ def parse():
                     help="inner CG iterations per convergence check (graph: launches per WHILE-loop body)")
     ap.add_argument("--profile-steps", type=int, default=40,
                     help="steps after the timed region timed per kernel class with CUDA events (eager)")
-    ap.add_argument("--kernel", default=None, choices=["ebe", "ebe10", "split", "predictor"],
+    ap.add_argument("--kernel", default=None, choices=["ebe", "ebe10", "pcg10", "split", "predictor"],
                     help="time one kernel alone (EBE product) instead of the full step")
     ap.add_argument("--kernel-precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=0,
@@ -580,6 +580,46 @@ def run_kernel10(args):
     fem.fem_mesh10_destroy(h)
 
 
+def run_pcg10(args):
+    """Plain FP64 PCG with the tet10 EBE product on the --dims grid as tet10, --cases cases, from a zero guess
+    against a right-hand side M v (v random on the free DOFs): time and iterations of one solve."""
+    import numpy as np
+    import torch
+    from paper_2409_20380_gb300 import build, fem
+    from paper_2409_20380_gb300 import workload as wl
+    build.build()
+    fem.lib()
+    torch.cuda.set_device(0)
+    Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
+    mesh = wl.tet10_mesh(wl.config2_mesh(Hx, Hy, Hz))
+    tp = wl.config2_time_params()
+    h = fem.fem_mesh10_create(mesh)
+    r = args.cases
+    cM = 4.0 / tp.dt ** 2 + 2.0 * tp.a0 / tp.dt
+    cK = 1.0 + 2.0 * tp.a1 / tp.dt
+    g = torch.Generator(device="cuda").manual_seed(1)
+    v = torch.randn(mesh.n_nodes * 3 * r, device="cuda", dtype=torch.float64, generator=g)
+    v.view(mesh.n_nodes, 3, r)[torch.from_numpy(mesh.fixed_dof.reshape(-1, 3).astype(bool)).cuda()] = 0
+    b = torch.empty_like(v)
+    fem.fem_ebe10_apply(h, v, b, r, 1.0, 0.0)          # b = M v: a smooth, mass-weighted load
+    x = torch.zeros_like(b)
+    fem.pcg10_solve(h, b, x, r, cM, cK, tol=1e-8)     # warm-up (allocations, first launches)
+    x.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    iters, relres = fem.pcg10_solve(h, b, x, r, cM, cK, tol=1e-8)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"kernel": "pcg10", "precision": "fp64", "dims": args.dims, "cases": r,
+                      "n_elems": mesh.n_elems, "n_nodes": mesh.n_nodes, "ms_per_solve": ms,
+                      "iters": [int(i) for i in iters], "max_relres": float(np.max(relres)),
+                      "ms_per_iteration": ms / max(1, int(np.max(iters))),
+                      "note": "plain FP64 block-Jacobi PCG, tet10 EBE product, zero guess, tol 1e-8"}), flush=True)
+    fem.fem_mesh10_destroy(h)
+
+
 def run_learned(args):
     """Learned proposal on the medium mesh: samples from --train-cases cases x --case-steps steps, Adam on
     the GPU, then --eval-cases held-out cases with and without the network (same certified tolerance)."""
@@ -828,6 +868,9 @@ def main():
         return
     if args.kernel == "ebe10":
         run_kernel10(args)
+        return
+    if args.kernel == "pcg10":
+        run_pcg10(args)
         return
     if args.kernel == "ebe":
         run_kernel(args)

@@ -92,7 +92,9 @@ template <typename T, bool DOT, typename I>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe10(int64_t E, int rpad, int rshift, const int32_t* __restrict__ conn,
                                                    const float* __restrict__ rec32, const double* __restrict__ rec64,
                                                    const T* __restrict__ p, T* __restrict__ q, T aM, T aK,
-                                                   Mass10 mc, Reducer red, double* ptq_out) {
+                                                   Mass10 mc, Reducer red, double* ptq_out, CgCase* sc,
+                                                   const int* gate) {
+  if (gate && *gate == 0) return;
   const T* __restrict__ recs = Rec10<T>::get(rec32, rec64);
   // barycentric coordinates of the four Gauss points: (A, B, B, B) and its permutations
   const T GA = (T)0.5854101966249685, GB = (T)0.1381966011250105;
@@ -194,7 +196,45 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe10(int64_
   }
   if (DOT) {
     double v[1] = {dot};
-    if (block_reduce_last<1>(v, rpad, red) && threadIdx.x < rpad && ptq_out) ptq_out[threadIdx.x] = red.out[threadIdx.x];
+    if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);   // (and the CG step length)
+  }
+}
+
+// Node diagonal 3x3 blocks of aM M + aK K (xx yy zz xy xz yz), element by element: at the Gauss points
+// K_ii = V/4 sum_q [lambda d d^T + mu (|d|^2 I + d d^T)] with d = grad N_i, and M_ii = rho V m_ii I.
+__global__ void k_diag10(int64_t E, const int32_t* __restrict__ conn, const double* __restrict__ rec, double aM,
+                         double aK, Mass10 mc, double* __restrict__ D) {
+  const double GA = 0.5854101966249685, GB = 0.1381966011250105;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const double* r = rec + e * kRec;
+    double g[4][3];
+    for (int k = 0; k < 3; ++k) {
+      g[1][k] = r[k], g[2][k] = r[3 + k], g[3][k] = r[6 + k];
+      g[0][k] = -(g[1][k] + g[2][k] + g[3][k]);
+    }
+    const double lam = aK * r[9] * 0.25, mu = aK * r[10] * 0.25, rv = aM * r[11] * 20.0;
+    for (int i = 0; i < 10; ++i) {
+      double b[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int qp = 0; qp < 4; ++qp) {
+        double L[4];
+        for (int a = 0; a < 4; ++a) L[a] = a == qp ? GA : GB;
+        double d[3];
+        if (i < 4) {
+          for (int k = 0; k < 3; ++k) d[k] = (4.0 * L[i] - 1.0) * g[i][k];
+        } else {
+          const int a = edge_a(i - 4), bb = edge_b(i - 4);
+          for (int k = 0; k < 3; ++k) d[k] = 4.0 * (L[a] * g[bb][k] + L[bb] * g[a][k]);
+        }
+        const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const double lm = lam + mu;
+        b[0] += lm * d[0] * d[0] + mu * dd, b[1] += lm * d[1] * d[1] + mu * dd, b[2] += lm * d[2] * d[2] + mu * dd;
+        b[3] += lm * d[0] * d[1], b[4] += lm * d[0] * d[2], b[5] += lm * d[1] * d[2];
+      }
+      const double mi = rv * mc.m64[tri(i, i)];
+      b[0] += mi, b[1] += mi, b[2] += mi;
+      double* dn = D + (int64_t)conn[e * 10 + i] * 6;
+      for (int k = 0; k < 6; ++k) atomicAdd(dn + k, b[k]);
+    }
   }
 }
 
@@ -327,12 +367,12 @@ fem_status fem_ebe10_apply(fem_mesh10* m, int precision, const void* p_dev, void
       auto fn = dot ? (i32 ? k_ebe10<double, true, int32_t> : k_ebe10<double, true, int64_t>)
                     : (i32 ? k_ebe10<double, false, int32_t> : k_ebe10<double, false, int64_t>);
       fn<<<grid, kBlock, 0, s>>>(m->E, n_rhs, rs, m->conn, m->rec32, m->rec64, (const double*)p_dev, (double*)q_dev,
-                                 alpha_M, alpha_K, m->mc, red, ptq_dev);
+                                 alpha_M, alpha_K, m->mc, red, ptq_dev, nullptr, nullptr);
     } else {
       auto fn = dot ? (i32 ? k_ebe10<float, true, int32_t> : k_ebe10<float, true, int64_t>)
                     : (i32 ? k_ebe10<float, false, int32_t> : k_ebe10<float, false, int64_t>);
       fn<<<grid, kBlock, 0, s>>>(m->E, n_rhs, rs, m->conn, m->rec32, m->rec64, (const float*)p_dev, (float*)q_dev,
-                                 (float)alpha_M, (float)alpha_K, m->mc, red, ptq_dev);
+                                 (float)alpha_M, (float)alpha_K, m->mc, red, ptq_dev, nullptr, nullptr);
     }
     e = cudaGetLastError();
   }
@@ -340,6 +380,105 @@ fem_status fem_ebe10_apply(fem_mesh10* m, int precision, const void* p_dev, void
     e = precision == FEM_FP64 ? launch_mask<double>(m->N, n_rhs, m->fm, (double*)q_dev, s)
                               : launch_mask<float>(m->N, n_rhs, m->fm, (float*)q_dev, s);
   if (e != cudaSuccess) return set_error(FEM_ERR_CUDA, std::string("tet10 product: ") + cudaGetErrorString(e));
+  return FEM_OK;
+}
+
+// Plain FP64 block-Jacobi PCG (Algorithm 1) on the tet10 system (alpha_M M + alpha_K K) x = b, the
+// product being the tet10 EBE; the same device-side per-case CG kernels as the tet4 solver.
+fem_status pcg10_solve(fem_mesh10* m, const double* b_dev, double* x_dev, int n_rhs, double alpha_M, double alpha_K,
+                       double tol, int maxit, void* stream, int* iters_out, double* relres_out) {
+  if (!m || !b_dev || !x_dev) return set_error(FEM_ERR_ARG, "null argument");
+  if (n_rhs < 1 || n_rhs > kMaxRpad || (n_rhs & (n_rhs - 1))) return set_error(FEM_ERR_ARG, "n_rhs must be 1, 2, 4, 8, 16 or 32");
+  if (!(tol > 0.0) || maxit < 1) return set_error(FEM_ERR_ARG, "tol must be > 0 and maxit >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int rpad = n_rhs, rs = lg2i(n_rhs);
+  const size_t n = (size_t)m->N * 3 * rpad;
+  double *D = nullptr, *b64 = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  float* b32 = nullptr;
+  CgCase* sc = nullptr;
+  int *n_active = nullptr, *err = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+  };
+  al((void**)&D, sizeof(double) * 6 * m->N);
+  al((void**)&b64, sizeof(double) * 6 * m->N);
+  al((void**)&b32, sizeof(float) * 6 * m->N);
+  al((void**)&r, sizeof(double) * n);
+  al((void**)&z, sizeof(double) * n);
+  al((void**)&p, sizeof(double) * n);
+  al((void**)&q, sizeof(double) * n);
+  al((void**)&sc, sizeof(CgCase) * rpad);
+  al((void**)&n_active, sizeof(int));
+  al((void**)&err, sizeof(int));
+  MeshView mv{m->N, m->E, nullptr, m->rec64, m->rec32, b64, b32, m->fm, nullptr, 0};
+  const Reducer red{m->partial, m->counter, m->out};
+  const int grid = grid_for(m->E << rs, kMaxRedBlocks);
+  auto product = [&](const double* in, double* out, bool dot) {
+    if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(double) * n, s);
+    if (e != cudaSuccess) return;
+    if (dot)
+      k_ebe10<double, true, int64_t><<<grid, kBlock, 0, s>>>(m->E, rpad, rs, m->conn, m->rec32, m->rec64, in, out,
+                                                             alpha_M, alpha_K, m->mc, red, nullptr, sc, n_active);
+    else
+      k_ebe10<double, false, int64_t><<<grid, kBlock, 0, s>>>(m->E, rpad, rs, m->conn, m->rec32, m->rec64, in, out,
+                                                              alpha_M, alpha_K, m->mc, red, nullptr, nullptr, nullptr);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_mask<double>(m->N, rpad, m->fm, out, s);
+  };
+  if (e == cudaSuccess) e = cudaMemsetAsync(D, 0, sizeof(double) * 6 * m->N, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_diag10<<<grid_for(m->E, 152 * 16), kBlock, 0, s>>>(m->E, m->conn, m->rec64, alpha_M, alpha_K, m->mc, D);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_binv(m->N, D, m->fm, b64, b32, err, s);
+  if (e == cudaSuccess) e = launch_norm_b_gated<double>(mv, rpad, b_dev, red, sc, nullptr, tol, s);
+  // the guess is zeroed on Dirichlet DOFs (and for b = 0) before its residual is formed
+  if (e == cudaSuccess) e = launch_zero_b0_t<double>(mv, rpad, x_dev, sc, s);
+  product(x_dev, q, false);
+  if (e == cudaSuccess) e = launch_resid<double>(mv, rpad, b_dev, q, x_dev, r, z, 1, red, sc, n_active, tol, maxit, s);
+  int h_active = 1, issued = 0, checks = 0;
+  while (e == cudaSuccess) {
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k) {
+      e = launch_dir_gated<double>(mv, rpad, z, p, sc, n_active, s);
+      product(p, q, true);
+      if (e == cudaSuccess) e = launch_update<double>(mv, rpad, p, q, x_dev, r, z, red, sc, n_active, tol, maxit, s);
+    }
+    issued += 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    if (h_active == 0) {
+      // the recursive residual says converged: confirm with the true one (and resume if it is not)
+      product(x_dev, q, false);
+      if (e == cudaSuccess) e = launch_resid<double>(mv, rpad, b_dev, q, x_dev, r, z, 0, red, sc, n_active, tol, maxit, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess || h_active == 0 || ++checks > 16) break;
+    }
+    if (issued > maxit + 64) break;
+  }
+  std::vector<CgCase> h(rpad);
+  int h_err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), sc, sizeof(CgCase) * rpad, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(D); cudaFree(b64); cudaFree(b32); cudaFree(r); cudaFree(z); cudaFree(p); cudaFree(q); cudaFree(sc);
+  cudaFree(n_active); cudaFree(err);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(FEM_ERR_CUDA, std::string("tet10 solve: ") + cudaGetErrorString(e));
+  }
+  if (h_err) return set_error(FEM_ERR_ARG, "a node's diagonal block is not positive definite");
+  fem_status worst = FEM_OK;
+  for (int c = 0; c < rpad; ++c) {
+    if (iters_out) iters_out[c] = h[c].iters;
+    if (relres_out) relres_out[c] = h[c].relres;
+    if (h[c].status != FEM_OK) worst = (fem_status)h[c].status;
+    else if (h[c].active) worst = FEM_ERR_NOT_CONVERGED;
+  }
+  if (worst != FEM_OK) return set_error(worst, "tet10 solve: a case did not converge");
   return FEM_OK;
 }
 

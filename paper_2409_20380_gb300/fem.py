@@ -25,7 +25,7 @@ FEM_FIELD_U, FEM_FIELD_V, FEM_FIELD_A, FEM_FIELD_DU, FEM_FIELD_B, FEM_FIELD_GUES
 EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_tune", "fem_mesh_autotune",
            "fem_mesh_info", "fem_mesh_split_product",
            "fem_mesh_set_regions", "fem_ebe_apply",
-           "fem_ebe_apply_noalloc", "fem_mesh10_create", "fem_mesh10_destroy", "fem_ebe10_apply",
+           "fem_ebe_apply_noalloc", "fem_mesh10_create", "fem_mesh10_destroy", "fem_ebe10_apply", "pcg10_solve",
            "pcg_solve", "fem_batch_create", "fem_batch_destroy", "fem_case_add", "fem_step", "predictor_fit",
            "predictor_predict", "fem_case_get", "fem_batch_set_loads", "fem_batch_get_field", "fem_batch_get_field_async",
            "fem_batch_sync", "fem_step_async", "fem_batch_profile",
@@ -97,6 +97,7 @@ def lib():
         "fem_mesh10_create": (I, [I64, P, I64, P, P, I, P, P, P, ctypes.POINTER(P)]),
         "fem_mesh10_destroy": (I, [P]),
         "fem_ebe10_apply": (I, [P, I, P, P, I, D, D, P, P]),
+        "pcg10_solve": (I, [P, P, P, I, D, D, D, I, P, P, P]),
         "pcg_solve": (I, [P, P, P, I, ctypes.POINTER(fem_opts), P, P, P]),
         "fem_batch_create": (I, [ctypes.POINTER(fem_opts), P, ctypes.POINTER(P)]),
         "fem_batch_destroy": (I, [P]),
@@ -259,6 +260,17 @@ def fem_ebe10_apply(h, p, q, n_rhs, alpha_M, alpha_K, ptq=None, precision=None, 
     dt = torch.float64 if precision == FEM_FP64 else torch.float32
     _check(lib().fem_ebe10_apply(h, precision, _ptr(p, dt), _ptr(q, dt), n_rhs, float(alpha_M), float(alpha_K),
                                  _ptr(ptq, torch.float64), _stream(stream)))
+
+
+def pcg10_solve(h, b, x, n_rhs, alpha_M, alpha_K, tol=1e-8, maxit=5000, stream=None):
+    """Plain FP64 PCG on the tet10 system; returns (iters [n_rhs], relres [n_rhs])."""
+    import torch
+    iters = np.zeros(n_rhs, dtype=np.int32)
+    relres = np.zeros(n_rhs, dtype=np.float64)
+    _check(lib().pcg10_solve(h, _ptr(b, torch.float64), _ptr(x, torch.float64), n_rhs, float(alpha_M),
+                             float(alpha_K), float(tol), int(maxit), _stream(stream), _np_ptr(iters),
+                             _np_ptr(relres)))
+    return iters, relres
 
 
 def pcg_solve(h, b, x, n_rhs, opts, stream=None, raise_on_error=True):

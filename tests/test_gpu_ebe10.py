@@ -83,3 +83,39 @@ def test_ebe10_argument_errors(torch_dev):
         assert ei.value.status == fem.FEM_ERR_ARG
     finally:
         fem.fem_mesh10_destroy(h)
+
+
+@pytest.mark.parametrize("dims,r", [((3, 3, 2), 1), ((4, 3, 3), 4)])
+def test_pcg10_matches_direct_solve_and_oracle_iterations(torch_dev, dims, r):
+    """The tet10 PCG (Algorithm 1 with 3x3 block Jacobi, FP64) against a sparse direct solve of the oracle's
+    reduced system and against the oracle's literal Algorithm 1 (iteration counts within one)."""
+    import scipy.sparse.linalg as spla
+    import oracle
+    torch = torch_dev
+    m10 = wl.tet10_mesh(small_mesh(*dims, perturb=0.15))
+    K, M = t10.assemble10(m10.xyz, m10.conn, m10.mat_id, m10.lam_mu_rho)
+    tp = wl.TimeParams()
+    cM = 4.0 / tp.dt ** 2 + 2.0 * tp.a0 / tp.dt
+    cK = 1.0 + 2.0 * tp.a1 / tp.dt
+    A = (cM * M + cK * K).tocsr()
+    free = np.nonzero(m10.fixed_dof == 0)[0]
+    A_red = A[free][:, free].tocsr()
+    Binv = oracle.block_jacobi_inverse(A_red, free)
+    bs = random_free_vectors(m10, r, seed=21 + r)
+    h = fem.fem_mesh10_create(m10)
+    try:
+        b = torch.tensor(from_cases(bs, m10.n_nodes, r), device="cuda")
+        x = torch.zeros_like(b)
+        tol = 1e-10
+        iters, relres = fem.pcg10_solve(h, b, x, r, cM, cK, tol=tol)
+        xs = to_cases(x.cpu().numpy(), m10.n_nodes, r)
+        for c in range(r):
+            ref = spla.spsolve(A_red.tocsc(), bs[c][free])
+            assert np.abs(xs[c][free] - ref).max() <= 1e-8 * np.abs(ref).max()
+            assert np.all(xs[c][m10.fixed_dof == 1] == 0.0)
+            true_rel = np.linalg.norm(bs[c][free] - A_red @ xs[c][free]) / np.linalg.norm(bs[c][free])
+            assert true_rel < tol and relres[c] < tol
+            res = oracle.block_jacobi_cg(A_red, Binv, bs[c][free], np.zeros(free.size), eps=tol)
+            assert abs(int(iters[c]) - res.iters) <= 1, (iters[c], res.iters)
+    finally:
+        fem.fem_mesh10_destroy(h)
