@@ -261,9 +261,11 @@ fem_status fem_mesh10_destroy(fem_mesh10* m);
 fem_status fem_ebe10_apply(fem_mesh10* m, int precision, const void* p_dev, void* q_dev, int n_rhs,
                            double alpha_M, double alpha_K, double* ptq_dev, void* stream);
 /*
- * Plain FP64 block-Jacobi PCG (Algorithm 1) on the tet10 system (alpha_M M + alpha_K K) x = b for n_rhs
- * cases, the product being the tet10 EBE: each case iterates until ||b - A x|| / ||b|| < tol, confirmed
- * with the true residual when the recursive one converges.
+ * Block-Jacobi PCG (Algorithm 1) on the tet10 system (alpha_M M + alpha_K K) x = b for n_rhs cases, the
+ * product being the tet10 EBE: each case iterates until ||b - A x|| / ||b|| < tol.  precision FEM_FP64:
+ * plain FP64 PCG, confirmed with the true residual when the recursive one converges; FEM_FP32_INNER: the
+ * FP64 residual r = b - A x (FP64 product), an inner FP32 PCG on A d = r from zero (FP32 product), x += d,
+ * repeated until the FP64 residual meets tol (iterations counted over all inner solves).
  *   b_dev       [n_nodes][3][n_rhs] device double (zero on Dirichlet DOFs);
  *   x_dev       [n_nodes][3][n_rhs] device double, in: initial guess (zeroed on Dirichlet DOFs), out: solution;
  *   iters_out, relres_out  optional host [n_rhs]: iterations and final relative residual per case.
@@ -271,8 +273,9 @@ fem_status fem_ebe10_apply(fem_mesh10* m, int precision, const void* p_dev, void
  * singular diagonal block), FEM_ERR_NOT_CONVERGED (maxit reached), FEM_ERR_BREAKDOWN, FEM_ERR_NONFINITE,
  * FEM_ERR_CUDA.
  */
-fem_status pcg10_solve(fem_mesh10* m, const double* b_dev, double* x_dev, int n_rhs, double alpha_M,
-                       double alpha_K, double tol, int maxit, void* stream, int* iters_out, double* relres_out);
+fem_status pcg10_solve(fem_mesh10* m, int precision, const double* b_dev, double* x_dev, int n_rhs,
+                       double alpha_M, double alpha_K, double tol, int maxit, void* stream, int* iters_out,
+                       double* relres_out);
 
 /*
  * Solves A x = b for n_rhs cases (Algorithm 1: 3x3 block-Jacobi PCG with the EBE product), starting from

@@ -11,6 +11,7 @@
 // generated here on the host from int L_0^a L_1^b L_2^c L_3^d dV = 6 V a! b! c! d! / (a + b + c + d + 3)!.
 // Local order: corners 0-3, edges (0,1), (1,2), (0,2), (0,3), (1,3), (2,3).  One thread per (element,
 // case); sums scatter with global atomics (Dirichlet rows masked afterwards).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -385,9 +386,10 @@ fem_status fem_ebe10_apply(fem_mesh10* m, int precision, const void* p_dev, void
 
 // Plain FP64 block-Jacobi PCG (Algorithm 1) on the tet10 system (alpha_M M + alpha_K K) x = b, the
 // product being the tet10 EBE; the same device-side per-case CG kernels as the tet4 solver.
-fem_status pcg10_solve(fem_mesh10* m, const double* b_dev, double* x_dev, int n_rhs, double alpha_M, double alpha_K,
-                       double tol, int maxit, void* stream, int* iters_out, double* relres_out) {
+fem_status pcg10_solve(fem_mesh10* m, int precision, const double* b_dev, double* x_dev, int n_rhs, double alpha_M,
+                       double alpha_K, double tol, int maxit, void* stream, int* iters_out, double* relres_out) {
   if (!m || !b_dev || !x_dev) return set_error(FEM_ERR_ARG, "null argument");
+  if (precision != FEM_FP64 && precision != FEM_FP32_INNER) return set_error(FEM_ERR_ARG, "unknown precision");
   if (n_rhs < 1 || n_rhs > kMaxRpad || (n_rhs & (n_rhs - 1))) return set_error(FEM_ERR_ARG, "n_rhs must be 1, 2, 4, 8, 16 or 32");
   if (!(tol > 0.0) || maxit < 1) return set_error(FEM_ERR_ARG, "tol must be > 0 and maxit >= 1");
   cudaStream_t s = (cudaStream_t)stream;
@@ -395,8 +397,10 @@ fem_status pcg10_solve(fem_mesh10* m, const double* b_dev, double* x_dev, int n_
   const size_t n = (size_t)m->N * 3 * rpad;
   double *D = nullptr, *b64 = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   float* b32 = nullptr;
-  CgCase* sc = nullptr;
+  CgCase *sc = nullptr, *outer = nullptr;
   int *n_active = nullptr, *err = nullptr;
+  float *r32 = nullptr, *x32 = nullptr, *rr32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  const bool mixed = precision == FEM_FP32_INNER;
   cudaError_t e = cudaSuccess;
   auto al = [&](void** ptr, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
@@ -411,9 +415,22 @@ fem_status pcg10_solve(fem_mesh10* m, const double* b_dev, double* x_dev, int n_
   al((void**)&sc, sizeof(CgCase) * rpad);
   al((void**)&n_active, sizeof(int));
   al((void**)&err, sizeof(int));
+  if (mixed) {
+    al((void**)&outer, sizeof(CgCase) * rpad);
+    for (float** v : {&r32, &x32, &rr32, &z32, &p32, &q32}) al((void**)v, sizeof(float) * n);
+  }
   MeshView mv{m->N, m->E, nullptr, m->rec64, m->rec32, b64, b32, m->fm, nullptr, 0};
   const Reducer red{m->partial, m->counter, m->out};
   const int grid = grid_for(m->E << rs, kMaxRedBlocks);
+  auto product32 = [&](const float* in, float* out) {   // FP32 product with p^T q and the step length
+    if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(float) * n, s);
+    if (e != cudaSuccess) return;
+    k_ebe10<float, true, int64_t><<<grid, kBlock, 0, s>>>(m->E, rpad, rs, m->conn, m->rec32, m->rec64, in, out,
+                                                          (float)alpha_M, (float)alpha_K, m->mc, red, nullptr, sc,
+                                                          n_active);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_mask<float>(m->N, rpad, m->fm, out, s);
+  };
   auto product = [&](const double* in, double* out, bool dot) {
     if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(double) * n, s);
     if (e != cudaSuccess) return;
@@ -433,39 +450,78 @@ fem_status pcg10_solve(fem_mesh10* m, const double* b_dev, double* x_dev, int n_
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = launch_binv(m->N, D, m->fm, b64, b32, err, s);
-  if (e == cudaSuccess) e = launch_norm_b_gated<double>(mv, rpad, b_dev, red, sc, nullptr, tol, s);
-  // the guess is zeroed on Dirichlet DOFs (and for b = 0) before its residual is formed
-  if (e == cudaSuccess) e = launch_zero_b0_t<double>(mv, rpad, x_dev, sc, s);
-  product(x_dev, q, false);
-  if (e == cudaSuccess) e = launch_resid<double>(mv, rpad, b_dev, q, x_dev, r, z, 1, red, sc, n_active, tol, maxit, s);
-  int h_active = 1, issued = 0, checks = 0;
-  while (e == cudaSuccess) {
-    for (int k = 0; k < 8 && e == cudaSuccess; ++k) {
-      e = launch_dir_gated<double>(mv, rpad, z, p, sc, n_active, s);
-      product(p, q, true);
-      if (e == cudaSuccess) e = launch_update<double>(mv, rpad, p, q, x_dev, r, z, red, sc, n_active, tol, maxit, s);
-    }
-    issued += 8;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) break;
-    if (h_active == 0) {
-      // the recursive residual says converged: confirm with the true one (and resume if it is not)
+  if (mixed) {
+    // FP32-inner / FP64-outer refinement (the tet4 solver's form 1): r64 = b - A64 x (FP64 tet10 product),
+    // inner FP32 PCG on A32 d = r64 from zero to the per-case target the outer residual sets, x += d
+    if (e == cudaSuccess) e = launch_norm_b_gated<double>(mv, rpad, b_dev, red, outer, nullptr, tol, s);
+    if (e == cudaSuccess) e = launch_zero_b0_t<double>(mv, rpad, x_dev, outer, s);
+    std::vector<CgCase> ho(rpad);
+    const double inner_tol = 1e-6;
+    for (int outer_it = 0; outer_it <= 40 && e == cudaSuccess; ++outer_it) {
       product(x_dev, q, false);
-      if (e == cudaSuccess) e = launch_resid<double>(mv, rpad, b_dev, q, x_dev, r, z, 0, red, sc, n_active, tol, maxit, s);
+      if (e == cudaSuccess) e = launch_outer_resid(mv, rpad, b_dev, q, r32, red, outer, n_active, tol, inner_tol, s);
+      int h_active = 0;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ho.data(), outer, sizeof(CgCase) * rpad, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess || h_active == 0) break;
+      int used = 0;
+      for (int c = 0; c < rpad; ++c) used = std::max(used, ho[c].iters);
+      if (used >= maxit || outer_it == 40) break;
+      if (e == cudaSuccess) e = launch_norm_b_gated<float>(mv, rpad, r32, red, sc, outer, inner_tol, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(x32, 0, sizeof(float) * n, s);
+      if (e == cudaSuccess)
+        e = launch_resid<float>(mv, rpad, r32, nullptr, x32, rr32, z32, 1, red, sc, n_active, inner_tol, maxit - used, s);
+      for (int issued = 0; e == cudaSuccess && issued <= maxit - used + 64;) {
+        for (int k = 0; k < 8 && e == cudaSuccess; ++k) {
+          e = launch_dir_gated<float>(mv, rpad, z32, p32, sc, n_active, s);
+          product32(p32, q32);
+          if (e == cudaSuccess)
+            e = launch_update<float>(mv, rpad, p32, q32, x32, rr32, z32, red, sc, n_active, inner_tol, maxit - used, s);
+        }
+        issued += 8;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (h_active == 0) break;
+      }
+      if (e == cudaSuccess) e = launch_refine_counts(mv, rpad, rpad, x_dev, x32, outer, sc, s);
+    }
+  } else {
+    if (e == cudaSuccess) e = launch_norm_b_gated<double>(mv, rpad, b_dev, red, sc, nullptr, tol, s);
+    // the guess is zeroed on Dirichlet DOFs (and for b = 0) before its residual is formed
+    if (e == cudaSuccess) e = launch_zero_b0_t<double>(mv, rpad, x_dev, sc, s);
+    product(x_dev, q, false);
+    if (e == cudaSuccess) e = launch_resid<double>(mv, rpad, b_dev, q, x_dev, r, z, 1, red, sc, n_active, tol, maxit, s);
+    int h_active = 1, issued = 0, checks = 0;
+    while (e == cudaSuccess) {
+      for (int k = 0; k < 8 && e == cudaSuccess; ++k) {
+        e = launch_dir_gated<double>(mv, rpad, z, p, sc, n_active, s);
+        product(p, q, true);
+        if (e == cudaSuccess) e = launch_update<double>(mv, rpad, p, q, x_dev, r, z, red, sc, n_active, tol, maxit, s);
+      }
+      issued += 8;
       if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess || h_active == 0 || ++checks > 16) break;
+      if (e != cudaSuccess) break;
+      if (h_active == 0) {
+        // the recursive residual says converged: confirm with the true one (and resume if it is not)
+        product(x_dev, q, false);
+        if (e == cudaSuccess) e = launch_resid<double>(mv, rpad, b_dev, q, x_dev, r, z, 0, red, sc, n_active, tol, maxit, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess || h_active == 0 || ++checks > 16) break;
+      }
+      if (issued > maxit + 64) break;
     }
-    if (issued > maxit + 64) break;
   }
   std::vector<CgCase> h(rpad);
   int h_err = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), sc, sizeof(CgCase) * rpad, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), mixed ? outer : sc, sizeof(CgCase) * rpad, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(D); cudaFree(b64); cudaFree(b32); cudaFree(r); cudaFree(z); cudaFree(p); cudaFree(q); cudaFree(sc);
-  cudaFree(n_active); cudaFree(err);
+  cudaFree(n_active); cudaFree(err); cudaFree(outer);
+  for (float* v : {r32, x32, rr32, z32, p32, q32}) cudaFree(v);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(FEM_ERR_CUDA, std::string("tet10 solve: ") + cudaGetErrorString(e));

@@ -97,7 +97,7 @@ def lib():
         "fem_mesh10_create": (I, [I64, P, I64, P, P, I, P, P, P, ctypes.POINTER(P)]),
         "fem_mesh10_destroy": (I, [P]),
         "fem_ebe10_apply": (I, [P, I, P, P, I, D, D, P, P]),
-        "pcg10_solve": (I, [P, P, P, I, D, D, D, I, P, P, P]),
+        "pcg10_solve": (I, [P, I, P, P, I, D, D, D, I, P, P, P]),
         "pcg_solve": (I, [P, P, P, I, ctypes.POINTER(fem_opts), P, P, P]),
         "fem_batch_create": (I, [ctypes.POINTER(fem_opts), P, ctypes.POINTER(P)]),
         "fem_batch_destroy": (I, [P]),
@@ -262,12 +262,13 @@ def fem_ebe10_apply(h, p, q, n_rhs, alpha_M, alpha_K, ptq=None, precision=None, 
                                  _ptr(ptq, torch.float64), _stream(stream)))
 
 
-def pcg10_solve(h, b, x, n_rhs, alpha_M, alpha_K, tol=1e-8, maxit=5000, stream=None):
-    """Plain FP64 PCG on the tet10 system; returns (iters [n_rhs], relres [n_rhs])."""
+def pcg10_solve(h, b, x, n_rhs, alpha_M, alpha_K, tol=1e-8, maxit=5000, precision=None, stream=None):
+    """PCG on the tet10 system (FEM_FP64 plain, FEM_FP32_INNER refined); returns (iters, relres) [n_rhs]."""
     import torch
+    precision = FEM_FP64 if precision is None else precision
     iters = np.zeros(n_rhs, dtype=np.int32)
     relres = np.zeros(n_rhs, dtype=np.float64)
-    _check(lib().pcg10_solve(h, _ptr(b, torch.float64), _ptr(x, torch.float64), n_rhs, float(alpha_M),
+    _check(lib().pcg10_solve(h, precision, _ptr(b, torch.float64), _ptr(x, torch.float64), n_rhs, float(alpha_M),
                              float(alpha_K), float(tol), int(maxit), _stream(stream), _np_ptr(iters),
                              _np_ptr(relres)))
     return iters, relres
