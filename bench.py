@@ -531,8 +531,9 @@ def run_kernel(args):
 
 # Tet10 product as executed: per Gauss point the corner-weighted sums W_a (84 flops), G = sum W_a g_a^T (63),
 # the stress (21), T_a = sigma g_a (60), the nodal forces (78) and the point's coefficients (12): 318; four
-# points, plus the 30 x 11 FMAs of the consistent mass (660): ~1.93 kflop per element and case (FMA = 2)
-FLOP_PER_TET10_CASE = 4 * 318 + 660
+# points, plus the consistent mass through its corner and edge sums (~100 a component, 300): ~1.57 kflop per
+# element and case (FMA = 2)
+FLOP_PER_TET10_CASE = 4 * 318 + 300
 
 
 def run_kernel10(args):

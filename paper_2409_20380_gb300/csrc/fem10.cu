@@ -7,8 +7,9 @@
 //   (K p)_i = sum_q V/4 sigma(G_q) grad N_i(L_q),  G_q = sum_j p_j (x) grad N_j(L_q),
 //   sigma(G) = lambda tr(G) I + mu (G + G^T),
 // both sums taken through the four corner gradients (about 180 operations a point instead of 450).
-// The consistent mass (M p)_i = rho V sum_j m_ij p_j uses the exact integrals m_ij = int N_i N_j dV / V,
-// generated here on the host from int L_0^a L_1^b L_2^c L_3^d dV = 6 V a! b! c! d! / (a + b + c + d + 3)!.
+// The consistent mass (M p)_i = rho V sum_j m_ij p_j with m_ij = int N_i N_j dV / V: generated on the host
+// from int L_0^a L_1^b L_2^c L_3^d dV = 6 V a! b! c! d! / (a + b + c + d + 3)! for the preconditioner's
+// diagonal, applied in the product through the seven distinct values of 420 m_ij.
 // Local order: corners 0-3, edges (0,1), (1,2), (0,2), (0,3), (1,3), (2,3).  One thread per (element,
 // case); sums scatter with global atomics (Dirichlet rows masked afterwards).
 #include <algorithm>
@@ -25,10 +26,11 @@ namespace {
 // edge s joins corners edge_a(s) and edge_b(s)
 __host__ __device__ constexpr int edge_a(int s) { return s == 0 ? 0 : s == 1 ? 1 : s == 2 ? 0 : s == 3 ? 0 : s == 4 ? 1 : 2; }
 __host__ __device__ constexpr int edge_b(int s) { return s == 0 ? 1 : s == 1 ? 2 : s == 2 ? 2 : s == 3 ? 3 : s == 4 ? 3 : 3; }
+// the edge sharing no corner with edge s
+__host__ __device__ constexpr int edge_opp(int s) { return s == 0 ? 5 : s == 1 ? 3 : s == 2 ? 4 : s == 3 ? 1 : s == 4 ? 2 : 0; }
 
 struct Mass10 {
-  float m32[55];    // upper triangle of m_ij, row-major (FP32 products)
-  double m64[55];   // (FP64 products)
+  double m64[55];   // upper triangle of m_ij, row-major
 };
 
 // Exact m_ij = int N_i N_j dV / V by expanding N_i N_j into barycentric monomials.
@@ -76,9 +78,6 @@ void mass10_host(double out[10][10]) {
 
 __host__ __device__ constexpr int tri(int i, int j) { return i <= j ? i * 10 - i * (i - 1) / 2 + (j - i) : tri(j, i); }
 
-template <typename T> __device__ __forceinline__ T mcoef(const Mass10& mc, int i, int j);
-template <> __device__ __forceinline__ float mcoef<float>(const Mass10& mc, int i, int j) { return mc.m32[tri(i, j)]; }
-template <> __device__ __forceinline__ double mcoef<double>(const Mass10& mc, int i, int j) { return mc.m64[tri(i, j)]; }
 
 template <typename T> struct Rec10;
 template <> struct Rec10<float> {
@@ -93,7 +92,7 @@ template <typename T, bool DOT, typename I>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe10(int64_t E, int rpad, int rshift, const int32_t* __restrict__ conn,
                                                    const float* __restrict__ rec32, const double* __restrict__ rec64,
                                                    const T* __restrict__ p, T* __restrict__ q, T aM, T aK,
-                                                   Mass10 mc, Reducer red, double* ptq_out, CgCase* sc,
+                                                   Reducer red, double* ptq_out, CgCase* sc,
                                                    const int* gate) {
   if (gate && *gate == 0) return;
   const T* __restrict__ recs = Rec10<T>::get(rec32, rec64);
@@ -175,15 +174,31 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_ebe10(int64_
         for (int k = 0; k < 3; ++k) Q[4 + e][k] += la4 * Tg[b][k] + lb4 * Tg[a][k];
       }
     }
+    // consistent mass through its structure: 420 m_ij = 6 / 1 (corner diagonal / other corner), -4 / -6
+    // (corner and an edge through it / the others), 32 / 16 / 8 (edge diagonal / an edge sharing a corner /
+    // the opposite edge), so with the corner and edge sums Sc, Se:
+    //   corner a:      5 p_a + Sc - 6 Se + 2 (sum of a's three edges)
+    //   edge (a, b):  -6 Sc + 2 (p_a + p_b) + 16 Se + 16 p_ab - 8 p_opposite
+    const T rv420 = rv * (T)(1.0 / 420.0);
 #pragma unroll
-    for (int i = 0; i < 10; ++i)
+    for (int k = 0; k < 3; ++k) {
+      const T Sc = (P[0][k] + P[1][k]) + (P[2][k] + P[3][k]);
+      const T Se = (P[4][k] + P[5][k]) + (P[6][k] + P[7][k]) + (P[8][k] + P[9][k]);
+      const T base_c = Sc - (T)6 * Se, base_e = (T)16 * Se - (T)6 * Sc;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        T acc = (T)0;
+      for (int a = 0; a < 4; ++a) {
+        T Ea = (T)0;
 #pragma unroll
-        for (int j = 0; j < 10; ++j) acc += mcoef<T>(mc, i, j) * P[j][k];
-        Q[i][k] += rv * acc;
+        for (int e = 0; e < 6; ++e)
+          if (edge_a(e) == a || edge_b(e) == a) Ea += P[4 + e][k];
+        Q[a][k] += rv420 * ((T)5 * P[a][k] + base_c + (T)2 * Ea);
       }
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        const int a = edge_a(e), b = edge_b(e), o = edge_opp(e);
+        Q[4 + e][k] += rv420 * (base_e + (T)2 * (P[a][k] + P[b][k]) + (T)16 * P[4 + e][k] - (T)8 * P[4 + o][k]);
+      }
+    }
     T hd = (T)0;   // (the element's p^T q in the product's precision, one conversion an element: FP64
                    // conversions and adds run on GB300's narrow FP64 pipe)
 #pragma unroll
@@ -338,7 +353,6 @@ fem_status fem_mesh10_create(int64_t n_nodes, const double* xyz, int64_t n_elems
   for (int i = 0; i < 10; ++i)
     for (int j = i; j < 10; ++j) {
       m->mc.m64[tri(i, j)] = mm[i][j];
-      m->mc.m32[tri(i, j)] = (float)mm[i][j];
     }
   *out = m;
   return FEM_OK;
@@ -368,12 +382,12 @@ fem_status fem_ebe10_apply(fem_mesh10* m, int precision, const void* p_dev, void
       auto fn = dot ? (i32 ? k_ebe10<double, true, int32_t> : k_ebe10<double, true, int64_t>)
                     : (i32 ? k_ebe10<double, false, int32_t> : k_ebe10<double, false, int64_t>);
       fn<<<grid, kBlock, 0, s>>>(m->E, n_rhs, rs, m->conn, m->rec32, m->rec64, (const double*)p_dev, (double*)q_dev,
-                                 alpha_M, alpha_K, m->mc, red, ptq_dev, nullptr, nullptr);
+                                 alpha_M, alpha_K, red, ptq_dev, nullptr, nullptr);
     } else {
       auto fn = dot ? (i32 ? k_ebe10<float, true, int32_t> : k_ebe10<float, true, int64_t>)
                     : (i32 ? k_ebe10<float, false, int32_t> : k_ebe10<float, false, int64_t>);
       fn<<<grid, kBlock, 0, s>>>(m->E, n_rhs, rs, m->conn, m->rec32, m->rec64, (const float*)p_dev, (float*)q_dev,
-                                 (float)alpha_M, (float)alpha_K, m->mc, red, ptq_dev, nullptr, nullptr);
+                                 (float)alpha_M, (float)alpha_K, red, ptq_dev, nullptr, nullptr);
     }
     e = cudaGetLastError();
   }
@@ -426,7 +440,7 @@ fem_status pcg10_solve(fem_mesh10* m, int precision, const double* b_dev, double
     if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(float) * n, s);
     if (e != cudaSuccess) return;
     k_ebe10<float, true, int64_t><<<grid, kBlock, 0, s>>>(m->E, rpad, rs, m->conn, m->rec32, m->rec64, in, out,
-                                                          (float)alpha_M, (float)alpha_K, m->mc, red, nullptr, sc,
+                                                          (float)alpha_M, (float)alpha_K, red, nullptr, sc,
                                                           n_active);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_mask<float>(m->N, rpad, m->fm, out, s);
@@ -436,10 +450,10 @@ fem_status pcg10_solve(fem_mesh10* m, int precision, const double* b_dev, double
     if (e != cudaSuccess) return;
     if (dot)
       k_ebe10<double, true, int64_t><<<grid, kBlock, 0, s>>>(m->E, rpad, rs, m->conn, m->rec32, m->rec64, in, out,
-                                                             alpha_M, alpha_K, m->mc, red, nullptr, sc, n_active);
+                                                             alpha_M, alpha_K, red, nullptr, sc, n_active);
     else
       k_ebe10<double, false, int64_t><<<grid, kBlock, 0, s>>>(m->E, rpad, rs, m->conn, m->rec32, m->rec64, in, out,
-                                                              alpha_M, alpha_K, m->mc, red, nullptr, nullptr, nullptr);
+                                                              alpha_M, alpha_K, red, nullptr, nullptr, nullptr);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_mask<double>(m->N, rpad, m->fm, out, s);
   };
