@@ -1,20 +1,24 @@
 #!/usr/bin/env python
 """Benchmark: time-steps/s over all cases at certified relative residual 1e-8 (one JSON line).
 
-Workload (the medium configuration): a 64x64x32 hex box (h = 1/64) split into 786,432 linear tets
-(139,425 nodes, 418,275 DOF), three seeded log-normal layers, bottom fixed, 16 cases sharing the mesh
+Default workload (--config large): the large single mesh -- a 256x256x128 hex box (h = 1/64, a 4 x 4 x 2
+domain) split into 50,331,648 linear tets (8,520,321 nodes, 25,560,963 DOF), five seeded log-normal layers
+plus a half-ellipsoid low-velocity basin (mu x 0.3) at the surface, bottom fixed, 8 cases sharing the mesh
 (Ricker point sources at seeded interior nodes, f0 ~ U[2, 8]), Newmark dt = 0.004 with Rayleigh damping
 (0.01, 0.001).  The solver is the FP32-inner / FP64-refined block-Jacobi PCG with the EBE product, started
-from the data-driven predictor (s = 32 stored steps, regions of 1024 nodes).  A "step" advances all 16
-cases by one time step: predictor, right-hand side, certified solve, Newmark update.  The simulation is
-first run for --spinup steps (default 250: the paper times steps 250-500), then --warmup untimed steps,
-then --steps timed steps.
+from the data-driven predictor (s = 16 stored steps, regions of 1024 nodes).  --config medium runs the
+64x64x32 box (786,432 tets) with 16 cases and s = 32 instead.
+
+A "step" advances all cases by one time step: predictor, right-hand side, certified solve, Newmark update.
+The simulation is first run for --spinup steps (default 250: the paper times steps 250-500), then --warmup
+untimed steps, then --steps timed steps.
 
 Under torchrun (N > 1) every rank runs its own replica of the workload (different case seeds) on its own
 GPU; value = all ranks' case-steps / the slowest rank's time ("replicas only": cases are independent).
 
 --impl reference times the FP64 CPU oracle (scipy CSR, Algorithm 1, the regional MGS predictor) on the
-host cores; each of its steps is one case-step of the same workload.
+host cores: one process per case on a bounded sub-box of the same recipe (all cores), its case-steps/s
+scaled to the full mesh by the DOF ratio (labelled as extrapolated).
 """
 from __future__ import annotations
 
@@ -39,6 +43,14 @@ FLOP_PER_ELEM_CASE_SPLIT = 157.0
 DP_INSTR_PER_ELEM_CASE_SPLIT = 115.0
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress note on stderr (the JSON result is the only stdout line)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -48,12 +60,22 @@ def parse():
     ap.add_argument("--spinup", type=int, default=250)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--predictor", default="dd", choices=["dd", "ab4"])
-    ap.add_argument("--cases", type=int, default=16)
-    ap.add_argument("--dims", default="64,64,32")
-    ap.add_argument("--s-max", type=int, default=32)
+    ap.add_argument("--config", default="large", choices=["large", "medium"],
+                    help="large: 256x256x128 box, 5 layers + basin, 8 cases, s = 16; medium: 64x64x32 box, "
+                         "3 layers, 16 cases, s = 32")
+    ap.add_argument("--cases", type=int, default=None)
+    ap.add_argument("--dims", default=None)
+    ap.add_argument("--s-max", type=int, default=None)
     ap.add_argument("--region-nodes", type=int, default=1024)
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--comparator-steps", type=int, default=4)
+    ap.add_argument("--comparator-steps", type=int, default=None)
+    ap.add_argument("--comparator-spinup", type=int, default=None)
+    ap.add_argument("--cpu-dims", default=None,
+                    help="hex dims of the oracle's sample (a sub-box of the same recipe; default: 32,32,16 for "
+                         "large, the full mesh for medium)")
+    ap.add_argument("--cpu-spinup", type=int, default=40, help="oracle steps from rest before its timed sample")
+    ap.add_argument("--cpu-steps", type=int, default=20, help="timed oracle steps per case")
+    ap.add_argument("--cpu-procs", type=int, default=0, help="oracle processes (0: min(cores, cases))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of the captured step graph")
@@ -84,7 +106,23 @@ def parse():
     ap.add_argument("--case-steps", type=int, default=500, help="steps per case (learned-proposal mode)")
     ap.add_argument("--updates", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=4096)
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.learned or a.uneven or a.kernel in ("ebe10", "pcg10"):
+        a.config = "medium"          # these modes run on medium-size meshes
+    large = a.config == "large"
+    if a.cases is None:
+        a.cases = 8 if large else 16
+    if a.dims is None:
+        a.dims = "256,256,128" if large else "64,64,32"
+    if a.s_max is None:
+        a.s_max = 16 if large else 32
+    if a.comparator_steps is None:     # (large: the plain FP64 comparators need minutes; run them on request)
+        a.comparator_steps = 0 if large else 4
+    if a.comparator_spinup is None:
+        a.comparator_spinup = 10 if large else 30
+    if a.cpu_dims is None:
+        a.cpu_dims = "32,32,16" if large else a.dims
+    return a
 
 
 def dist_env():
@@ -176,73 +214,145 @@ EBE_SOURCES = ["paper_2409_20380_gb300/csrc/k_ebe.cu", "paper_2409_20380_gb300/c
 BCSR_SOURCES = ["paper_2409_20380_gb300/csrc/k_bcsr.cu"]
 
 
+def make_mesh(config, dims):
+    from paper_2409_20380_gb300 import workload as wl
+    Hx, Hy, Hz = (int(v) for v in dims.split(","))
+    if config == "large":
+        return wl.config4_mesh(Hx, Hy, Hz), wl.config4_time_params()
+    return wl.config2_mesh(Hx, Hy, Hz), wl.config2_time_params()
+
+
+def make_sources(config, mesh, n_cases, first_case=0):
+    from paper_2409_20380_gb300 import workload as wl
+    if config == "large":
+        return wl.config4_sources(mesh, n_cases, first_case=first_case)
+    return wl.config2_sources(mesh, n_cases, first_case=first_case)
+
+
 def workload(args, rank):
     from paper_2409_20380_gb300 import workload as wl
-    Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
-    mesh = wl.config2_mesh(Hx, Hy, Hz)
-    srcs = wl.config2_sources(mesh, args.cases, first_case=rank * args.cases)
-    return mesh, srcs, wl.config2_time_params(), wl.region_map(mesh, args.region_nodes)
+    mesh, tp = make_mesh(args.config, args.dims)
+    srcs = make_sources(args.config, mesh, args.cases, first_case=rank * args.cases)
+    return mesh, srcs, tp, wl.region_map(mesh, args.region_nodes)
 
 
-def cpu_baseline(args, mesh, srcs, tp, regions, n_case_steps=40):
-    """The FP64 oracle, as it stands, on case 0 of the same workload from rest (bounded sample)."""
-    import numpy as np
+def _oracle_case(config, dims, case, predictor, s_max, region_nodes, spinup, steps, barrier, out):
+    """One case of the oracle sample, in its own (spawned) process: the FP64 oracle as it stands on the
+    sample mesh, `spinup` steps from rest, then `steps` timed steps after every process is ready."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    sys.path.insert(0, ROOT)
     import oracle
+    from paper_2409_20380_gb300 import workload as wl
+    mesh, tp = make_mesh(config, dims)
+    src = make_sources(config, mesh, case + 1)[case]
     sysm, A = oracle.build_system(mesh, tp)
     Binv = oracle.block_jacobi_inverse(A, sysm.free)
-    sim = oracle.CaseSimulator(sysm, A, Binv, srcs[0], predictor="dd" if args.predictor == "dd" else "ab4",
-                               s_max=args.s_max, region_of_node=regions)
+    sim = oracle.CaseSimulator(sysm, A, Binv, src, predictor=predictor, s_max=s_max,
+                               region_of_node=wl.region_map(mesh, region_nodes))
+    for _ in range(spinup):
+        sim.step()
+    if barrier is not None:
+        barrier.wait()
     t0 = time.perf_counter()
     its = 0
-    for _ in range(n_case_steps):
+    for _ in range(steps):
         its += sim.step().iters
-    dt = time.perf_counter() - t0
-    return {"value": n_case_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"case 0, steps 1-{n_case_steps} from rest of the same mesh/sources "
-                      f"(scipy CSR FP64 Algorithm 1 + regional MGS, {its} CG iterations, single thread)",
-            "seconds": dt}
+    t1 = time.perf_counter()
+    out.put((case, t0, t1, its))
+
+
+def oracle_sample(args, n_procs, spinup, steps):
+    """Runs the oracle on n_procs cases at once (one spawned process per case, single-threaded each) on the
+    --cpu-dims sample mesh; returns case-steps/s measured there and scaled to the full mesh by the DOF ratio."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    barrier = ctx.Barrier(n_procs) if n_procs > 1 else None
+    pred = "dd" if args.predictor == "dd" else "ab4"
+    procs = [ctx.Process(target=_oracle_case, args=(args.config, args.cpu_dims, c, pred, args.s_max,
+                                                    args.region_nodes, spinup, steps, barrier, out))
+             for c in range(n_procs)]
+    for p in procs:
+        p.start()
+    res = [out.get() for _ in procs]
+    for p in procs:
+        p.join()
+    t0 = min(r[1] for r in res)
+    t1 = max(r[2] for r in res)
+    its = sum(r[3] for r in res)
+    sub = [int(v) for v in args.cpu_dims.split(",")]
+    full = [int(v) for v in args.dims.split(",")]
+    n_sub = 3 * (sub[0] + 1) * (sub[1] + 1) * (sub[2] + 1)
+    n_full = 3 * (full[0] + 1) * (full[1] + 1) * (full[2] + 1)
+    v_sub = n_procs * steps / (t1 - t0)
+    return {"value_sample": v_sub, "value_full": v_sub * n_sub / n_full, "dof_sample": n_sub, "dof_full": n_full,
+            "seconds": t1 - t0, "cg_iters_per_case_step": its / (n_procs * steps), "procs": n_procs}
+
+
+def cpu_baseline(args):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload: --cpu-dims sub-box of the same
+    recipe (the same mesh for medium), steps cpu_spinup+1 .. cpu_spinup+cpu_steps from rest; timed on one
+    core alone and then with one process per case on min(cores, cases) cores."""
+    n_all = args.cpu_procs or max(1, min(os.cpu_count() or 1, args.cases))
+    one = oracle_sample(args, 1, args.cpu_spinup, args.cpu_steps)
+    allc = oracle_sample(args, n_all, args.cpu_spinup, args.cpu_steps) if n_all > 1 else one
+    extrap = args.cpu_dims != args.dims
+    w0, w1 = args.cpu_spinup + 1, args.cpu_spinup + args.cpu_steps
+    sample = (f"oracle (scipy CSR FP64 Algorithm 1 + regional MGS, single-threaded per process) on "
+              f"{'a ' + args.cpu_dims.replace(',', 'x') + ' hex sub-box of the same recipe' if extrap else 'the same mesh'}"
+              f" ({allc['dof_sample']} DOF), cases 0-{n_all - 1} of its sources, steps {w0}-{w1} from rest, "
+              f"{allc['cg_iters_per_case_step']:.2f} CG iterations per case-step; "
+              + (f"case-steps/s scaled to the full mesh by the DOF ratio {allc['dof_sample']}/{allc['dof_full']} "
+                 f"(extrapolated)" if extrap else "measured on the full mesh"))
+    return {"value": allc["value_full"], "unit": UNIT, "cores": n_all, "kind": "oracle", "sample": sample,
+            "extrapolated": extrap, "value_on_sample": allc["value_sample"], "seconds": allc["seconds"],
+            "cg_iters_per_case_step": allc["cg_iters_per_case_step"],
+            "single_core": {"value": one["value_full"], "value_on_sample": one["value_sample"], "cores": 1,
+                            "seconds": one["seconds"], "cg_iters_per_case_step": one["cg_iters_per_case_step"]}}
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    mesh, srcs, tp, regions = workload(args, 0)
-    import oracle
-    sysm, A = oracle.build_system(mesh, tp)
-    Binv = oracle.block_jacobi_inverse(A, sysm.free)
-    sim = oracle.CaseSimulator(sysm, A, Binv, srcs[0], predictor="dd" if args.predictor == "dd" else "ab4",
-                               s_max=args.s_max, region_of_node=regions)
-    for _ in range(args.warmup):
-        sim.step()
-    t0 = time.perf_counter()
-    its = 0
-    for _ in range(args.steps):
-        its += sim.step().iters
-    dt = time.perf_counter() - t0
-    value = args.steps / dt
-    sample = (f"case 0 of the workload, steps {args.warmup + 1}-{args.warmup + args.steps} from rest, one "
-              f"case-step per benchmark step ({its} CG iterations)")
+    n_all = args.cpu_procs or max(1, min(os.cpu_count() or 1, args.cases))
+    r = oracle_sample(args, n_all, args.cpu_spinup + args.warmup, args.steps)
+    value = r["value_full"]
+    extrap = args.cpu_dims != args.dims
+    sample = (f"one process per case ({n_all} cases, one core each) on "
+              f"{'a ' + args.cpu_dims.replace(',', 'x') + ' hex sub-box of the same recipe' if extrap else 'the same mesh'}"
+              f" ({r['dof_sample']} DOF); {args.cpu_spinup} spin-up + {args.warmup} warm-up steps from rest, then "
+              f"{args.steps} timed steps of every case ({r['cg_iters_per_case_step']:.2f} CG iterations per "
+              f"case-step)" + (f"; case-steps/s scaled to the full mesh by the DOF ratio "
+                               f"{r['dof_sample']}/{r['dof_full']} (extrapolated)" if extrap else ""))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["seconds"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(args, mesh),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": config_dict(args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_all, "kind": "oracle", "sample": sample,
+                         "extrapolated": extrap, "value_on_sample": r["value_sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def config_dict(args, mesh):
-    return {"workload": f"medium: {args.dims.replace(',', 'x')} hex box split into {mesh.n_elems} tets "
-                        f"({mesh.n_nodes} nodes), {args.cases} cases on one mesh, "
-                        f"{'FP32-inner/FP64-refined' if args.precision == 'mixed' else 'FP64'} block-Jacobi "
-                        f"EBE-PCG to rel. residual 1e-8, "
-                        f"{'data-driven predictor s=%d' % args.s_max if args.predictor == 'dd' else 'AB4 predictor'}",
-            "mesh_hex": args.dims, "n_elems": mesh.n_elems, "n_nodes": mesh.n_nodes, "cases_per_gpu": args.cases,
-            "precision": args.precision, "predictor": args.predictor, "s_max": args.s_max, "cert_product": args.cert,
-            "region_nodes": args.region_nodes, "tol": 1e-8, "spinup_steps": args.spinup,
-            "l2": "inputs larger than L2: each step streams the 16-case state and the snapshot ring (>1 GB)",
+def config_dict(args, mesh=None):
+    if mesh is None:     # sizes of the Kuhn-split hex box without building it
+        Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
+        mesh = argparse.Namespace(n_elems=6 * Hx * Hy * Hz, n_nodes=(Hx + 1) * (Hy + 1) * (Hz + 1))
+    solver = ("FP32-inner/FP64-refined" if args.precision == "mixed" else "FP64") + " block-Jacobi EBE-PCG to rel. residual 1e-8"
+    pred = "data-driven predictor s=%d" % args.s_max if args.predictor == "dd" else "AB4 predictor"
+    if args.config == "large":
+        name = (f"large: {args.dims.replace(',', 'x')} hex box (h=1/64) split into {mesh.n_elems} tets "
+                f"({mesh.n_nodes} nodes), 5 layers + low-velocity basin, {args.cases} cases on one mesh, {solver}, {pred}")
+    else:
+        name = (f"medium: {args.dims.replace(',', 'x')} hex box split into {mesh.n_elems} tets "
+                f"({mesh.n_nodes} nodes), {args.cases} cases on one mesh, {solver}, {pred}")
+    return {"workload": name, "mesh_hex": args.dims, "n_elems": mesh.n_elems, "n_nodes": mesh.n_nodes,
+            "cases_per_gpu": args.cases, "precision": args.precision, "predictor": args.predictor,
+            "s_max": args.s_max, "cert_product": args.cert, "region_nodes": args.region_nodes, "tol": 1e-8,
+            "spinup_steps": args.spinup,
+            "l2": "inputs larger than L2: each step streams the cases' state and the snapshot ring (>1 GB)",
             "parallelism": "replicas"}
 
 
@@ -260,7 +370,9 @@ def run_ours(args):
     from paper_2409_20380_gb300 import workload as wl
     build.build()
     fem.lib()
+    log("building the workload")
     mesh, srcs, tp, regions = workload(args, rank)
+    log(f"mesh: {mesh.n_elems} tets, {mesh.n_nodes} nodes")
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
 
@@ -280,7 +392,10 @@ def run_ours(args):
     nc = len(srcs)
     for s in srcs:
         fem.fem_case_add(bt, h, s)
+    log("library mesh and batch created")
     fem.fem_step(bt, args.spinup, nc)
+    free_b, total_b = torch.cuda.mem_get_info()
+    log(f"{args.spinup} spin-up steps done; device memory in use {(total_b - free_b) / 1e9:.1f} of {total_b / 1e9:.1f} GB")
     fem.fem_step(bt, args.warmup, nc)
     # ---- timed region: device-resident, CUDA events on the batch stream ----
     sampler = ClockSampler(local)
@@ -297,6 +412,7 @@ def run_ours(args):
     torch.cuda.profiler.stop()
     barrier()
     clocks = sampler.stop()
+    log(f"timed region: {args.steps} steps")
     launches = fem.fem_batch_profile(bt, 0)["kernel_launches"]
     ms = ev0.elapsed_time(ev1)
     # per-kernel-class device times: CUDA events around each launch over the next --profile-steps steps
@@ -349,6 +465,7 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = t.item()
+    log("end-to-end region done")
     e2e = {"value": ws * nc * ne / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nc * 3 * 8,
            "d2h_bytes_per_step": nc * N * 3 * 8, "steps": ne}
     # ---- plain FP64 PCG with Adams-Bashforth on the same state: with the EBE product (the comparator) and
@@ -364,7 +481,7 @@ def run_ours(args):
                 fem.fem_case_add(bt2, h, s)
             # same physics from rest is not the same state; run the comparator on the steps right after a
             # short spin-up so its iteration counts are those of a developed wavefield
-            fem.fem_step(bt2, 30, nc)
+            fem.fem_step(bt2, args.comparator_spinup, nc)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -374,7 +491,7 @@ def run_ours(args):
             runs[name] = (e0.elapsed_time(e1), float(it2.sum()) / (nc * args.comparator_steps))
             fem.fem_batch_destroy(bt2)
         fem.fem_mesh_tune(h, args.variant, args.hex_per_tile)
-        steps_w = "steps 31-%d" % (30 + args.comparator_steps)
+        steps_w = "steps %d-%d" % (args.comparator_spinup + 1, args.comparator_spinup + args.comparator_steps)
         comparator = {"value": nc * args.comparator_steps / (runs["ebe"][0] / 1e3), "unit": UNIT,
                       "what": "plain FP64 EBE-PCG + Adams-Bashforth, same GPU, " + steps_w,
                       "cg_iters_per_case_step": runs["ebe"][1]}
@@ -393,8 +510,9 @@ def run_ours(args):
     hbm_peak, peak_kind, sm_max = peaks()
     E = mesh.n_elems
     rpad = 1 << (nc - 1).bit_length()
-    alu32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # FP32: 152 SMs x 128 lanes x FMA x max clock
-    alu64 = 152 * 2 * 2 * sm_max * 1e6 / 1e12        # FP64: 152 SMs x 2 DFMA/clk x 2 flops x max clock
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    alu32 = n_sm * 128 * 2 * sm_max * 1e6 / 1e12      # FP32: SMs x 128 lanes x FMA x max clock
+    alu64 = n_sm * 2 * 2 * sm_max * 1e6 / 1e12        # FP64: SMs x 2 DFMA/clk x 2 flops x max clock
     inner = None
     if prof["ebe32_launches"] > 0:
         avg32 = prof["ebe32_ms"] / max(1, min(working32, prof["ebe32_launches"]))
@@ -403,8 +521,8 @@ def run_ours(args):
         gbs = bytes32 / (avg32 * 1e-3) / 1e9
         inner = {"bound": "alu", "achieved": fl / (avg32 * 1e-3) / 1e12, "peak": alu32, "unit": "TFLOP/s",
                  "frac": fl / (avg32 * 1e-3) / 1e12 / alu32,
-                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock",
-                 "traffic": ncu_traffic("ebe_packed_f32_medium16", EBE_SOURCES) if not args.variant else None,
+                 "peak_kind": "derived: %d SMs x 128 FP32 lanes x 2 flops x max SM clock" % n_sm,
+                 "traffic": ncu_traffic("ebe_packed_f32_%s%d" % (args.config, rpad), EBE_SOURCES) if not args.variant else None,
                  "kernel": ("k_ebe_hex_staged<float,1,0,1> (FP32 EBE product A p of the inner PCG, TMA-staged "
                             "hex tiles, two cases per thread; %d cases)" % rpad),
                  "avg_launch_ms": avg32, "launches": working32, "launches_issued": prof["ebe32_launches"],
@@ -428,19 +546,19 @@ def run_ours(args):
                 kname = "k_bcsr_split_df (certification product M p, K p: assembled 3x3 blocks, double-float)"
             else:
                 fl = 12 * 2 * nnz * rpad
-                roof = {"bound": "alu", "peak": alu64, "peak_kind": "derived: 152 SMs x 2 DFMA/clk x max SM clock"}
+                roof = {"bound": "alu", "peak": alu64, "peak_kind": "derived: %d SMs x 2 DFMA/clk x max SM clock" % n_sm}
                 kname = "k_bcsr_split_f64 (certification product M p, K p: assembled 3x3 blocks, FP64)"
             roof.update({"nnz_blocks": nnz})
         else:
             fl = FLOP_PER_ELEM_CASE_SPLIT * E * rpad
             bytes_c = E * (16 + 12 * 8) + rpad * N * 3 * (8 + 8 + 8)
-            roof = {"bound": "alu", "peak": alu64, "peak_kind": "derived: 152 SMs x 2 DFMA/clk x max SM clock"}
+            roof = {"bound": "alu", "peak": alu64, "peak_kind": "derived: %d SMs x 2 DFMA/clk x max SM clock" % n_sm}
             kname = "k_ebe_split%s (certification product M p, K p, element by element)" % ("_df" if args.cert == 1 else "")
         achieved = fl / (avg * 1e-3) / 1e12
         gbs = bytes_c / (avg * 1e-3) / 1e9
         roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"],
-                     "traffic": (ncu_traffic("ebe_split_f64_medium16", EBE_SOURCES) if args.cert == 0 else
-                                 ncu_traffic("bcsr_split_df_medium16", BCSR_SOURCES) if args.cert == 3 else None),
+                     "traffic": (ncu_traffic("ebe_split_f64_%s%d" % (args.config, rpad), EBE_SOURCES) if args.cert == 0 else
+                                 ncu_traffic("bcsr_split_df_%s%d" % (args.config, rpad), BCSR_SOURCES) if args.cert == 3 else None),
                      "kernel": kname + ", %d cases" % rpad, "avg_launch_ms": avg, "launches": prof["ebe64_launches"],
                      "alg_bytes_per_launch": bytes_c, "alg_flops_per_launch": fl, "hbm_gbs": gbs,
                      "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak,
@@ -450,9 +568,11 @@ def run_ours(args):
         roof, other = inner, cert
     else:
         roof, other = cert, inner
+    log("comparators done")
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_baseline(args, mesh, srcs, tp, regions)
+        cpu = cpu_baseline(args)
+        log("oracle baseline done")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -493,9 +613,7 @@ def run_kernel(args):
     build.build()
     fem.lib()
     torch.cuda.set_device(0)
-    Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
-    mesh = wl.config2_mesh(Hx, Hy, Hz)
-    tp = wl.config2_time_params()
+    mesh, tp = make_mesh(args.config, args.dims)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_tune(h, args.variant, args.hex_per_tile)
     r = args.cases
@@ -797,9 +915,8 @@ def run_split(args):
     build.build()
     fem.lib()
     torch.cuda.set_device(0)
-    Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
-    mesh = wl.config2_mesh(Hx, Hy, Hz)
-    h = fem.fem_mesh_create(mesh, wl.config2_time_params())
+    mesh, tp = make_mesh(args.config, args.dims)
+    h = fem.fem_mesh_create(mesh, tp)
     r = args.cases
     g = torch.Generator(device="cuda").manual_seed(0)
     p = torch.randn(mesh.n_nodes * 3 * r, device="cuda", dtype=torch.float64, generator=g)
@@ -830,9 +947,7 @@ def run_predictor_kernels(args):
     build.build()
     fem.lib()
     torch.cuda.set_device(0)
-    Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
-    mesh = wl.config2_mesh(Hx, Hy, Hz)
-    tp = wl.config2_time_params()
+    mesh, tp = make_mesh(args.config, args.dims)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, wl.region_map(mesh, args.region_nodes))
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
@@ -840,7 +955,7 @@ def run_predictor_kernels(args):
     bt = fem.fem_batch_create(opts)
     nc = args.cases
     for c in range(nc):
-        fem.fem_case_add(bt, h, wl.random_source(mesh, wl.rng_for(2, 0, c, 0)))
+        fem.fem_case_add(bt, h, wl.random_source(mesh, wl.rng_for(2 if args.config == "medium" else 4, 0, c, 0)))
     fem.fem_step(bt, max(args.spinup, args.s_max + 2), nc)
     guess = torch.empty(mesh.n_nodes * 3, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):

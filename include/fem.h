@@ -111,11 +111,20 @@ typedef struct {
                             inner PCG) and replayed with no host synchronisation between steps; statistics
                             are read once per fem_step call.  Steps with profiling on, a learned proposal or
                             sample collection run eagerly.  0 = eager launches with host-side control */
-  int reserved[2];
+  int wait_budget;       /* bounded device-side waits (the staged EBE kernels' waits for their bulk tile copies):
+                            tries of up to 1 us each before a wait gives up and the call reports
+                            FEM_ERR_TIMEOUT (the kernel then still waits, bounded, for the copies in flight,
+                            so none outlives it; results of a timed-out call are not to be used).  The value
+                            is device-wide: fem_step, fem_step_async and pcg_solve set it before their work,
+                            fem_ebe_apply and fem_mesh_autotune restore the default.  0 = a wait that has not
+                            completed at once reports (a way to exercise the error path); default 1048576
+                            (about a second); must be >= 0 */
+  int reserved;
 } fem_opts;
 
 /* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-6, tau 1e-6,
- * snapshot_format 2, check_every 8, refresh_every 200, cert_df 3, fuse_meshes 0, use_graph 1. */
+ * snapshot_format 2, check_every 8, refresh_every 200, cert_df 3, fuse_meshes 0, use_graph 1,
+ * wait_budget 1048576. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */
@@ -217,8 +226,11 @@ fem_status fem_ebe_apply(fem_mesh* m, int precision, const void* p_dev, void* q_
 
 /*
  * Allocation-free variant of fem_ebe_apply (the paper has no counterpart: this is a library service).
- * Same arguments, results and errors as fem_ebe_apply, but it never allocates device memory (no
- * cudaMalloc/cudaFree, no allocating library routine).  It is meant for callers that cannot allocate:
+ * Same arguments and errors as fem_ebe_apply, but it never allocates device memory (no cudaMalloc/cudaFree,
+ * no allocating library routine).  It always runs the generic element kernel (one thread per element and
+ * case, scatter by global atomics), not the tiled or autotuned kernel fem_ebe_apply may choose, so it can be
+ * slower, and its q and p^T q equal fem_ebe_apply's to rounding (FP32 atomics add in varying order), not bit
+ * for bit.  It is meant for callers that cannot allocate:
  * code whose device memory is owned by another allocator under a fixed budget, and latency-critical loops
  * that cannot take the device-wide synchronisation cudaMalloc/cudaFree may cause.  The scratch of the
  * p^T q reduction is one fixed device array of 311,808 bytes inside the library (per-block partial sums
@@ -338,6 +350,18 @@ fem_status predictor_fit(fem_batch* b, int case_id);
  * x_guess_dev [n_nodes][3] device doubles.  Does not change the batch state.
  */
 fem_status predictor_predict(fem_batch* b, int case_id, double* x_guess_dev);
+
+/*
+ * Coefficients of the data-driven correction of the last completed step of case `case_id` (Section 3.2: per
+ * region R the prediction is y_R = Y_R c_R, c_R the least-squares coefficients of the query e^{it-1} on the
+ * stored inputs X_R after the column-drop rule).  coef_host [n_regions][s_max] host doubles: entry a of a
+ * region multiplies the a-th stored pair, oldest first (x_a = e^{it-1-n+a}, y_a = e^{it-n+a}); a dropped
+ * column has coefficient 0; entries a >= n are 0.  n_pairs_out (nullable): n, the pairs the step used (0: no
+ * correction).  With the learned proposal these are the plain predictor's coefficients.  Errors:
+ * FEM_ERR_ARG; FEM_ERR_STATE for a batch without the data-driven predictor or regions, or fused meshes.
+ * Synchronises the batch stream.
+ */
+fem_status predictor_coefficients(fem_batch* b, int case_id, double* coef_host, int* n_pairs_out);
 
 /* Copies field `what` (FEM_FIELD_*) of case `case_id`, [n_nodes][3] doubles, to `dst` (device memory if
  * on_device != 0, else host memory; a host copy synchronises the batch stream). */

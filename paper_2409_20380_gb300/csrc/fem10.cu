@@ -371,7 +371,7 @@ fem_status fem_ebe10_apply(fem_mesh10* m, int precision, const void* p_dev, void
   cudaStream_t s = (cudaStream_t)stream;
   const int rs = lg2i(n_rhs);
   const int64_t items = m->E << rs;
-  int grid = grid_for(items, kMaxRedBlocks);
+  int grid = grid_for(items, red_grid_cap());
   const Reducer red{m->partial, m->counter, m->out};
   const bool dot = ptq_dev != nullptr;
   const size_t bytes = (precision == FEM_FP64 ? 8 : 4) * (size_t)m->N * 3 * n_rhs;
@@ -435,7 +435,7 @@ fem_status pcg10_solve(fem_mesh10* m, int precision, const double* b_dev, double
   }
   MeshView mv{m->N, m->E, nullptr, m->rec64, m->rec32, b64, b32, m->fm, nullptr, 0};
   const Reducer red{m->partial, m->counter, m->out};
-  const int grid = grid_for(m->E << rs, kMaxRedBlocks);
+  const int grid = grid_for(m->E << rs, red_grid_cap());
   auto product32 = [&](const float* in, float* out) {   // FP32 product with p^T q and the step length
     if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(float) * n, s);
     if (e != cudaSuccess) return;
@@ -460,7 +460,7 @@ fem_status pcg10_solve(fem_mesh10* m, int precision, const double* b_dev, double
   if (e == cudaSuccess) e = cudaMemsetAsync(D, 0, sizeof(double) * 6 * m->N, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
   if (e == cudaSuccess) {
-    k_diag10<<<grid_for(m->E, 152 * 16), kBlock, 0, s>>>(m->E, m->conn, m->rec64, alpha_M, alpha_K, m->mc, D);
+    k_diag10<<<grid_for(m->E, wide_grid_cap()), kBlock, 0, s>>>(m->E, m->conn, m->rec64, alpha_M, alpha_K, m->mc, D);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = launch_binv(m->N, D, m->fm, b64, b32, err, s);

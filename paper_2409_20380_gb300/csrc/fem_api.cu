@@ -630,6 +630,7 @@ static fem_status check_opts(const fem_opts* o) {
   if (o->s_max < 1 || o->s_max > kMaxSlots - 1) return fail(FEM_ERR_ARG, "s_max must be in [1, 32]");
   if (o->cert_df < 0 || o->cert_df > 3) return fail(FEM_ERR_ARG, "cert_df must be 0, 1, 2 or 3");
   if (o->snapshot_format < 0 || o->snapshot_format > 3) return fail(FEM_ERR_ARG, "snapshot_format must be 0 .. 3");
+  if (o->wait_budget < 0) return fail(FEM_ERR_ARG, "wait_budget must be >= 0");
   return FEM_OK;
 }
 
@@ -793,7 +794,7 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
     CHK(dalloc(&g->gram, (size_t)R * g->rpad * kMaxSlots * kMaxSlots));
     CHK(dalloc(&g->wcoef, (size_t)R * g->rpad * kMaxSlots));
     // enough blocks for the dot/combine kernels to fill the GPU: about 8 per SM over all regions
-    g->n_chunks = std::max(1, std::min(64, (8 * 152 + R - 1) / R));
+    g->n_chunks = std::max(1, std::min(64, (8 * sm_count() + R - 1) / R));
     CHK(dalloc(&g->dpart, (size_t)R * g->n_chunks * kMaxSlots * g->rpad));
     CU(cudaMemsetAsync(g->gram, 0, sizeof(double) * (size_t)R * g->rpad * kMaxSlots * kMaxSlots, s));
   }
@@ -1453,6 +1454,7 @@ static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
 
 namespace fem {
 fem_status set_error(fem_status s, const std::string& msg) { return fail(s, msg); }
+void clear_error() { g_err.clear(); }
 void mesh_view_of(const fem_mesh* m, MeshView* view, int* device) {
   *view = m->view();
   *device = m->device;
@@ -1555,6 +1557,7 @@ void fem_opts_default(fem_opts* o) {
   o->cert_df = 3;
   o->fuse_meshes = 0;
   o->use_graph = 1;
+  o->wait_budget = kDefaultWaitBudget;
 }
 
 fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
@@ -1706,6 +1709,7 @@ fem_status fem_mesh_autotune(fem_mesh* m, int precision, int n_rhs, void* stream
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
   if (!pow2_rhs(n_rhs)) return fail(FEM_ERR_ARG, "n_rhs must be 1, 2, 4, 8, 16 or 32");
   cudaStream_t s = (cudaStream_t)stream;
+  CU(ebe_set_wait_budget(kDefaultWaitBudget, s));
   if (precision == FEM_FP64) return autotune_t<double>(m, n_rhs, s, ebe_variant_out, hex_per_tile_out, ms_out);
   if (precision == FEM_FP32_INNER) return autotune_t<float>(m, n_rhs, s, ebe_variant_out, hex_per_tile_out, ms_out);
   return fail(FEM_ERR_ARG, "unknown precision");
@@ -1817,6 +1821,7 @@ fem_status fem_ebe_apply(fem_mesh* m, int precision, const void* p_dev, void* q_
   if (!m || !p_dev || !q_dev) return fail(FEM_ERR_ARG, "null argument");
   if (!pow2_rhs(n_rhs)) return fail(FEM_ERR_ARG, "n_rhs must be 1, 2, 4, 8, 16 or 32");
   cudaStream_t s = (cudaStream_t)stream;
+  CU(ebe_set_wait_budget(kDefaultWaitBudget, s));
   Workspace* w = nullptr;
   CHK(m->workspace(n_rhs, &w));
   const Reducer red = w->red();
@@ -1842,12 +1847,18 @@ fem_status pcg_solve(fem_mesh* m, const double* b_dev, double* x_dev, int n_rhs,
   if (!pow2_rhs(n_rhs)) return fail(FEM_ERR_ARG, "n_rhs must be 1, 2, 4, 8, 16 or 32");
   CHK(check_opts(opts));
   cudaStream_t s = (cudaStream_t)stream;
+  CU(ebe_set_wait_budget(opts->wait_budget, s));
   Workspace* w = nullptr;
   CHK(m->workspace(n_rhs, &w));
   CgCase* res = nullptr;
   CHK(solve_any(m, w, b_dev, x_dev, *opts, s, &res));
   CU(cudaMemcpyAsync(w->h_sc, res, sizeof(CgCase) * n_rhs, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
+  {
+    int tmo = 0;   // a staged EBE kernel whose bounded wait for its copies gave up: results not valid
+    CU(ebe_tma_timeout(&tmo));
+    if (tmo) return fail(FEM_ERR_TIMEOUT, "pcg_solve: an EBE kernel's wait for its tile copies timed out");
+  }
   fem_status worst = FEM_OK;
   for (int c = 0; c < n_rhs; ++c) {
     if (iters_out) iters_out[c] = w->h_sc[c].iters;
@@ -2006,6 +2017,7 @@ fem_status fem_step(fem_batch* b, int n_steps, int* iters_out, double* relres_ou
   if (!b) return fail(FEM_ERR_ARG, "batch is null");
   if (n_steps < 0) return fail(FEM_ERR_ARG, "n_steps < 0");
   CHK(batch_start(b));
+  CU(ebe_set_wait_budget(b->opts.wait_budget, b->s));
   fem_status worst = FEM_OK;
   for (int k = 0; k < n_steps; ++k) {
     for (auto* g : b->groups) CHK(group_step(b, g, &worst));
@@ -2040,6 +2052,7 @@ fem_status fem_step_async(fem_batch* b, int n_steps) {
   if (!b) return fail(FEM_ERR_ARG, "batch is null");
   if (n_steps < 0) return fail(FEM_ERR_ARG, "n_steps < 0");
   CHK(batch_start(b));
+  CU(ebe_set_wait_budget(b->opts.wait_budget, b->s));
   fem_status worst = FEM_OK;   // (steps that run eagerly report here; graph steps on the device)
   for (int k = 0; k < n_steps; ++k) {
     for (auto* g : b->groups) CHK(group_step(b, g, &worst));
@@ -2079,6 +2092,27 @@ fem_status predictor_predict(fem_batch* b, int case_id, double* x_guess_dev) {
     CU(launch_extract_case(g->mesh->N, g->rpad, l, g->ws->q, x_guess_dev, b->s));
   }
   CU(cudaStreamSynchronize(b->s));
+  return FEM_OK;
+}
+
+fem_status predictor_coefficients(fem_batch* b, int case_id, double* coef_host, int* n_pairs_out) {
+  g_err.clear();
+  if (!b || !coef_host || case_id < 0 || case_id >= (int)b->loc.size()) return fail(FEM_ERR_ARG, "bad argument");
+  Group* g = b->groups[b->loc[case_id].first];
+  if (b->opts.predictor != FEM_PRED_DD || !g->wcoef || g->n_regions == 0)
+    return fail(FEM_ERR_STATE, "predictor_coefficients: the batch has no data-driven predictor with regions");
+  if (g->owned_mesh) return fail(FEM_ERR_STATE, "predictor_coefficients: not available for fused meshes");
+  // the pairs of the last completed step's prediction (it = steps): X = e^{it-1-n} .. e^{it-2}
+  const int it = g->steps;
+  const int n_pairs = it >= 1 ? std::max(0, std::min(b->opts.s_max, std::min(it - 1, g->n_slots) - 1)) : 0;
+  const int l = b->loc[case_id].second, R = g->n_regions, s = b->opts.s_max;
+  std::vector<double> all((size_t)R * g->rpad * kMaxSlots);
+  CU(cudaMemcpyAsync(all.data(), g->wcoef, sizeof(double) * all.size(), cudaMemcpyDeviceToHost, b->s));
+  CU(cudaStreamSynchronize(b->s));
+  for (int r = 0; r < R; ++r)
+    for (int a = 0; a < s; ++a)
+      coef_host[(size_t)r * s + a] = a < n_pairs ? all[((size_t)r * g->rpad + l) * kMaxSlots + a] : 0.0;
+  if (n_pairs_out) *n_pairs_out = n_pairs;
   return FEM_OK;
 }
 

@@ -13,11 +13,11 @@ namespace fem {
 
 constexpr int kBlock = 256;              // threads per block of the element kernels
 constexpr int kVecBlock = 512;           // threads per block of the reducing vector kernels
-constexpr int kVecGrid = 152 * 3;        // their grid cap: few blocks keep the final reduction short
 constexpr int kMaxRpad = 32;             // max cases per multi-RHS group (lanes of a node)
 constexpr int kMaxCases = 128;           // max cases of a group (fused groups: one case per mesh)
 constexpr int kMaxSlots = 33;            // predictor ring: s_max + 1 <= 33
-constexpr int kMaxRedBlocks = 152 * 8;   // grid cap of reducing kernels (partials buffer rows)
+constexpr int kDefaultWaitBudget = 1 << 20;   // tries (<= 1 us each) of a reporting device-side wait
+constexpr int kMaxRedBlocks = 1216;     // rows of the per-block partial-sum buffers of reducing kernels
 
 // Per-element record, 12 values: g1 (3), g2 (3), g3 (3) shape-function gradients of local nodes 1..3
 // (g0 = -g1-g2-g3), lambda*V, mu*V, rho*V/20.
@@ -122,12 +122,21 @@ struct RickerSrc {          // per case of a group
 };
 
 // Accessors for translation units other than the C-ABI one: record the thread's error message and
-// return `s`; the device view and device id of a mesh.
+// return `s`; clear it (every entry point does so on entry); the device view and device id of a mesh.
 fem_status set_error(fem_status s, const std::string& msg);
+void clear_error();
 void mesh_view_of(const fem_mesh* m, MeshView* view, int* device);
 
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
-int grid_for(int64_t items, int cap = kMaxRedBlocks);
+// Multiprocessors of the current device (queried once per device) and the grid caps derived from them:
+// reducing vector kernels 3 blocks per SM (few blocks keep the final reduction short), reducing element
+// kernels 8 per SM, grid-stride kernels without reduction 16 per SM; the reducing caps never exceed the
+// partial-sum buffers' kMaxRedBlocks rows.
+int sm_count();
+int vec_grid_cap();
+int red_grid_cap();
+int wide_grid_cap();
+int grid_for(int64_t items, int cap = -1);   // cap < 0: red_grid_cap()
 // Largest element-wise absolute row sums of M and K over the mesh's nodes (see HexTiles::abs_m).
 cudaError_t elem_abs_row_bounds(const MeshView& m, double* abs_m, double* abs_k, cudaStream_t s);
 // Grid of grid-stride kernel `fn` (blocks of `block` threads, no dynamic shared memory): at most one wave of
@@ -285,6 +294,8 @@ cudaError_t launch_ebe_hexmat(const HexTiles& ht, const MeshView& m, const float
 size_t ebe_hexmat_smem(const HexTiles& ht, const MeshView& m, int rpad);   // ~0 when not applicable
 // Reads and clears the flag a staged kernel sets when a bounded wait for its copies gave up.
 cudaError_t ebe_tma_timeout(int* flag);
+// Sets the number of tries (up to 1 us each) of the staged kernels' reporting wait (device-wide; ordered on s).
+cudaError_t ebe_set_wait_budget(int tries, cudaStream_t s);
 cudaError_t launch_ebe_split(const MeshView& m, int rpad, const double* p, double* qM, double* qK, cudaStream_t s);
 // The same product in double-float arithmetic from (hi, lo) FP32 records rec_df [E][12][2].
 cudaError_t launch_ebe_split_df(const MeshView& m, const float* rec_df, int rpad, const double* p, double* qM,

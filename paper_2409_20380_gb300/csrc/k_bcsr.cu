@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(256) k_bcsr_apply(int64_t N, int rpad, int rsh
 
 int grid_of(int64_t items) {
   int64_t g = (items + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
+  if (g > wide_grid_cap()) g = wide_grid_cap();
   return (int)(g < 1 ? 1 : g);
 }
 
@@ -256,7 +256,7 @@ cudaError_t launch_bcsr_apply(const MeshView& m, int rpad, const int32_t* row_pt
   if (!row_ptr || m.seg) return cudaErrorInvalidValue;
   const int rs = lg2(rpad);
   int grid = grid_of(m.N << rs);
-  if (grid > kMaxRedBlocks) grid = kMaxRedBlocks;
+  if (grid > red_grid_cap()) grid = red_grid_cap();
   const float4* km = reinterpret_cast<const float4*>(KMd);
   Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
   if (red)

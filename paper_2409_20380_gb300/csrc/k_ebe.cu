@@ -8,6 +8,9 @@
 // This generic kernel scatters with global atomics; fixed DOFs are left to the consumer to mask.
 #include "fem_internal.cuh"
 
+#include <mutex>
+#include <unordered_map>
+
 namespace fem {
 
 template <typename T> __device__ __forceinline__ const T* rec_of(const MeshView& m);
@@ -120,7 +123,7 @@ cudaError_t launch_ebe_gated(const MeshView& m, int rpad, const T* pm, const T* 
   cudaError_t err = cudaMemsetAsync(q, 0, sizeof(T) * (size_t)m.N * 3 * rpad, s);
   if (err != cudaSuccess) return err;
   const int rs = log2i(rpad);
-  const int grid = grid_for(m.E << rs, red ? kVecGrid : kMaxRedBlocks);
+  const int grid = grid_for(m.E << rs, red ? vec_grid_cap() : red_grid_cap());
   Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
   if (pk) {
     k_ebe_atomic<T, true, false><<<grid, kBlock, 0, s>>>(m, rpad, rs, pm, pk, q, (T)aM, (T)aK, rd, nullptr, nullptr, gate);
@@ -341,9 +344,7 @@ cudaError_t launch_ebe_hex(const HexTiles& ht, const MeshView& m, int rpad, cons
   const int rs = log2i(rpad);
   const size_t smem = ((sizeof(T) * (size_t)ht.nloc_max * 3 * rpad + sizeof(int) * (size_t)ht.nloc_max + 7) & ~(size_t)7) +
                       (m.seg ? sizeof(double) * (size_t)m.nseg : 0);
-  int dev = 0, nsm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nsm = sm_count();
   int per_sm = 1;
   auto kfn = red ? (m.seg ? k_ebe_hex<T, true, true> : k_ebe_hex<T, true, false>) : k_ebe_hex<T, false, false>;
   err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -352,7 +353,7 @@ cudaError_t launch_ebe_hex(const HexTiles& ht, const MeshView& m, int rpad, cons
   if (per_sm < 1) per_sm = 1;
   int grid = nsm * per_sm;
   if (grid > ht.n_tiles) grid = ht.n_tiles;
-  if (grid > kMaxRedBlocks) grid = kMaxRedBlocks;
+  if (grid > red_grid_cap()) grid = red_grid_cap();
   Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
   kfn<<<grid, kBlock, smem, s>>>(ht, m, rpad, rs, p, q, (T)aM, (T)aK, rd, red ? sc : nullptr, red ? ptq_out : nullptr,
                                  gate);
@@ -530,6 +531,9 @@ __device__ __forceinline__ void hex_acc_p(const float* ps, int* qs, const int (&
 // FEM_ERR_TIMEOUT).  Needs 3 x rpad x sizeof(T) to be a multiple of 16 bytes (rpad >= 4 for FP32).
 // ------------------------------------------------------------------------------------------------------
 __device__ int g_tma_timeout = 0;
+// Tries of the reporting wait (fem_opts.wait_budget, set by the host before a solve; device-wide).
+constexpr int kDrainTries = 1 << 20;
+__device__ int g_wait_budget = kDrainTries;
 
 struct StagedLayout {
   size_t bar, qs, ps0, ps1, rec0, rec1, node0, node1, loc0, loc1, acc, total;
@@ -574,9 +578,11 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 // Bounded wait for phase `parity` of the barrier; false if it did not complete.  Each try may suspend the
 // thread for up to 1 us (instead of spinning on the issue slots the other block of the SM computes with);
-// at most 2^20 tries, about a second.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int i = 0; i < (1 << 20); ++i) {
+// at most `tries` tries (2^20: about a second).  The kernels first wait with the budget g_wait_budget and
+// report a wait that gives up; they then wait again with kDrainTries, so that no bulk copy is still in
+// flight when the block moves on to its next tile or exits.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int tries = kDrainTries) {
+  for (int i = 0; i < tries; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -705,7 +711,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && PK != 2) ? 2 : 1) k
       for (int i = threadIdx.x; i < nl * per_node; i += blockDim.x) qs[i] = (T)0;
     }
     const uint32_t bar = smem_u32(mbar + b);
-    if (!mbar_wait(bar, (uint32_t)((k >> 1) & 1))) {
+    if (!mbar_wait(bar, (uint32_t)((k >> 1) & 1), g_wait_budget)) {
       atomicExch(&g_tma_timeout, 1);
       mbar_wait(bar, (uint32_t)((k >> 1) & 1));   // second bounded wait for the copies still in flight
     }
@@ -991,7 +997,7 @@ __global__ void __launch_bounds__(kBlockCM, 1) k_ebe_hex_cm(HexTiles ht, MeshVie
     const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
     for (int i = threadIdx.x; i < nl * PN; i += blockDim.x) qs[i] = (T)0;
     const uint32_t bar = smem_u32(mbar + b);
-    if (!mbar_wait(bar, (uint32_t)((k >> 1) & 1))) {
+    if (!mbar_wait(bar, (uint32_t)((k >> 1) & 1), g_wait_budget)) {
       atomicExch(&g_tma_timeout, 1);
       mbar_wait(bar, (uint32_t)((k >> 1) & 1));
     }
@@ -1080,9 +1086,7 @@ cudaError_t launch_ebe_hex_staged(const HexTiles& ht, const MeshView& m, int rpa
   cudaError_t err = cudaMemsetAsync(q, 0, sizeof(T) * (size_t)m.N * 3 * rpad, s);
   if (err != cudaSuccess) return err;
   const int rs = log2i(rpad);
-  int dev = 0, nsm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nsm = sm_count();
   int per_sm = 1;
   // packed pairs: FP32 only, one case per lane of the node row (not fused groups), a 16-byte aligned output
   // (the tile flush writes float4 pieces); 1: registers capped for two blocks per SM, 2: one block per SM
@@ -1099,7 +1103,7 @@ cudaError_t launch_ebe_hex_staged(const HexTiles& ht, const MeshView& m, int rpa
   if (per_sm < 1) per_sm = 1;
   int grid = nsm * per_sm;
   if (grid > ht.n_tiles) grid = ht.n_tiles;
-  if (grid > kMaxRedBlocks) grid = kMaxRedBlocks;
+  if (grid > red_grid_cap()) grid = red_grid_cap();
   Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
   kfn<<<grid, kBlock, smem, s>>>(ht, m, rpad, rs, p, q, (T)aM, (T)aK, rd, red ? sc : nullptr, red ? ptq_out : nullptr,
                                  gate);
@@ -1174,7 +1178,7 @@ cudaError_t launch_hexmat_build(int64_t n_hex, const double* rec64, double aM, d
   const int64_t pairs = (n_hex + 1) / 2;
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * 2 * kHexMatVals * (size_t)pairs, s);   // odd tail
   if (e != cudaSuccess || n_hex == 0) return e;
-  k_hexmat_build<<<grid_for(n_hex * 36, 152 * 16), kBlock, 0, s>>>(n_hex, rec64, aM, aK, out);
+  k_hexmat_build<<<grid_for(n_hex * 36, wide_grid_cap()), kBlock, 0, s>>>(n_hex, rec64, aM, aK, out);
   return cudaGetLastError();
 }
 
@@ -1316,7 +1320,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_ebe_hexmat(HexTiles ht, const flo
         if (tn < ht.n_tiles) issue(tn, cn, b ^ 1);
       }
       const uint32_t bar = smem_u32(mbar + b);
-      if (!mbar_wait(bar, (uint32_t)((j >> 1) & 1))) {
+      if (!mbar_wait(bar, (uint32_t)((j >> 1) & 1), g_wait_budget)) {
         atomicExch(&g_tma_timeout, 1);
         mbar_wait(bar, (uint32_t)((j >> 1) & 1));   // second bounded wait for the copy still in flight
       }
@@ -1449,9 +1453,8 @@ cudaError_t launch_ebe_hexmat(const HexTiles& ht, const MeshView& m, const float
     return cudaErrorInvalidValue;
   cudaError_t err = cudaMemsetAsync(q, 0, sizeof(float) * (size_t)m.N * 3 * rpad, s);
   if (err != cudaSuccess) return err;
-  int dev = 0, nsm = 152, per_sm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nsm = sm_count();
+  int per_sm = 1;
   auto kfn = red ? k_ebe_hexmat<true> : k_ebe_hexmat<false>;
   err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBlock, smem);
@@ -1459,7 +1462,7 @@ cudaError_t launch_ebe_hexmat(const HexTiles& ht, const MeshView& m, const float
   if (per_sm < 1) per_sm = 1;
   int grid = nsm * per_sm;
   if (grid > ht.n_tiles) grid = ht.n_tiles;
-  if (grid > kMaxRedBlocks) grid = kMaxRedBlocks;
+  if (grid > red_grid_cap()) grid = red_grid_cap();
   Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
   kfn<<<grid, kBlock, smem, s>>>(ht, hm, rpad, p, q, (float)aM, (float)aK, rd, red ? sc : nullptr,
                                  red ? ptq_out : nullptr, gate);
@@ -1482,9 +1485,7 @@ cudaError_t launch_ebe_hex_cm(const HexTiles& ht, const MeshView& m, int rpad, c
   cudaError_t err = cudaMemsetAsync(q, 0, sizeof(T) * (size_t)m.N * 3 * rpad, s);
   if (err != cudaSuccess) return err;
   const int rs = log2i(rpad);
-  int dev = 0, nsm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nsm = sm_count();
   auto kfn = red ? k_ebe_hex_cm<T, true> : k_ebe_hex_cm<T, false>;
   err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -1499,6 +1500,22 @@ template cudaError_t launch_ebe_hex_cm<double>(const HexTiles&, const MeshView&,
                                                double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
 template cudaError_t launch_ebe_hex_cm<float>(const HexTiles&, const MeshView&, int, const float*, float*, double,
                                               double, const Reducer*, CgCase*, double*, const int*, cudaStream_t);
+
+// Tries of the staged kernels' reporting wait for the launches ordered after this on s.
+// (Each device starts with the default; the copy is skipped while the device already holds the value.)
+cudaError_t ebe_set_wait_budget(int tries, cudaStream_t s) {
+  static std::mutex mu;
+  static std::unordered_map<int, int> held;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = held.find(dev);
+  if (it != held.end() ? it->second == tries : tries == kDrainTries) return cudaSuccess;
+  e = cudaMemcpyToSymbolAsync(g_wait_budget, &tries, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) held[dev] = tries;
+  return e;
+}
 
 // Reads (and clears) the flag set when a staged kernel's bounded wait for its copies gave up.
 cudaError_t ebe_tma_timeout(int* flag) {
@@ -1677,7 +1694,7 @@ __global__ void k_split_records(int64_t n, const double* __restrict__ rec64, flo
 }
 
 cudaError_t launch_split_records(int64_t E, const double* rec64, float* rec_df, cudaStream_t s) {
-  k_split_records<<<grid_for(E * kRec, 152 * 16), kBlock, 0, s>>>(E * kRec, rec64, rec_df);
+  k_split_records<<<grid_for(E * kRec, wide_grid_cap()), kBlock, 0, s>>>(E * kRec, rec64, rec_df);
   return cudaGetLastError();
 }
 

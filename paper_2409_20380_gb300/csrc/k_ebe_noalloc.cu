@@ -5,7 +5,10 @@
 // cannot allow that: code whose memory is owned by another allocator under a fixed budget, and
 // latency-critical loops that cannot afford the implicit device synchronisation of cudaMalloc/cudaFree.
 // fem_ebe_apply_noalloc() serves them: its scratch is the file-scope device array below, which exists
-// once per GPU that loads the library and lives until the process exits.
+// once per GPU that loads the library and lives until the process exits.  It always runs the generic
+// element kernel (one thread per element and case, global atomics): the tiled kernels fem_ebe_apply
+// chooses keep per-mesh tile tables and tuning state that are built with allocations.  Its results equal
+// fem_ebe_apply's to rounding (the FP32 atomic scatter order varies), not bit for bit.
 #include <mutex>
 
 #include "fem_internal.cuh"
@@ -45,6 +48,7 @@ using namespace fem;
 
 extern "C" fem_status fem_ebe_apply_noalloc(fem_mesh* m, int precision, const void* p_dev, void* q_dev, int n_rhs,
                                             double alpha_M, double alpha_K, double* ptq_dev, void* stream) {
+  clear_error();
   if (!m || !p_dev || !q_dev) return set_error(FEM_ERR_ARG, "fem_ebe_apply_noalloc: null argument");
   if (!(n_rhs == 1 || n_rhs == 2 || n_rhs == 4 || n_rhs == 8 || n_rhs == 16 || n_rhs == 32))
     return set_error(FEM_ERR_ARG, "fem_ebe_apply_noalloc: n_rhs must be 1, 2, 4, 8, 16 or 32 (the scratch holds "

@@ -244,7 +244,7 @@ __global__ void k_pack(const float* __restrict__ th, bf16* W1, bf16* W2, bf16* W
 
 int grid_of(int64_t n) {
   int64_t g = (n + 255) / 256;
-  return (int)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
+  return (int)(g < 1 ? 1 : (g > wide_grid_cap() ? wide_grid_cap() : g));
 }
 
 }  // namespace
@@ -574,7 +574,7 @@ cudaError_t mlp_choose(const MeshView& m, int rpad, const float* r32, const floa
   while ((1 << rs) < rpad) ++rs;
   int64_t items = m.N << rs;
   int grid = (int)((items + kVecBlock - 1) / kVecBlock);
-  if (grid > kVecGrid) grid = kVecGrid;
+  if (grid > vec_grid_cap()) grid = vec_grid_cap();
   if (grid < 1) grid = 1;
   k_choose<<<grid, kVecBlock, 0, s>>>(m, rpad, rs, r32, qd, red, outer, n_active, tol, inner_max, ncase, choose,
                                       counts);

@@ -16,7 +16,7 @@ template <> __device__ __forceinline__ const float* binv_of<float>(const MeshVie
 static int vec_grid(int64_t items) {
   int64_t g = (items + kVecBlock - 1) / kVecBlock;
   if (g < 1) g = 1;
-  if (g > kVecGrid) g = kVecGrid;
+  if (g > vec_grid_cap()) g = vec_grid_cap();
   return (int)g;
 }
 

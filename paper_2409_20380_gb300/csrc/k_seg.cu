@@ -294,7 +294,7 @@ __global__ void k_cert_seg(MeshView m, double cM, double cK, const double* __res
 static int seg_grid(int64_t items) {
   int64_t g = (items + kVecBlock - 1) / kVecBlock;
   if (g < 1) g = 1;
-  if (g > kVecGrid) g = kVecGrid;
+  if (g > vec_grid_cap()) g = vec_grid_cap();
   return (int)g;
 }
 

@@ -19,9 +19,8 @@ int grid_resident(const void* fn, int block, int64_t items) {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(fn);
     if (it == cache.end()) {
-      int dev = 0, nsm = 152, per_sm = 1;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      int per_sm = 1;
+      const int nsm = sm_count();
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
@@ -36,7 +35,29 @@ int grid_resident(const void* fn, int block, int64_t items) {
   return (int)g;
 }
 
+int sm_count() {
+  static std::mutex mu;
+  static std::unordered_map<int, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it == cache.end()) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    it = cache.emplace(dev, n).first;
+  }
+  return it->second;
+}
+int vec_grid_cap() { return std::min(3 * sm_count(), kMaxRedBlocks); }
+int red_grid_cap() { return std::min(8 * sm_count(), kMaxRedBlocks); }
+int wide_grid_cap() { return 16 * sm_count(); }
+
 int grid_for(int64_t items, int cap) {
+  if (cap < 0) cap = red_grid_cap();
   int64_t g = (items + kBlock - 1) / kBlock;
   if (g < 1) g = 1;
   if (g > cap) g = cap;
@@ -171,18 +192,18 @@ __global__ void k_binv(int64_t N, const double* __restrict__ D, const uint8_t* _
 cudaError_t launch_elem_setup(int64_t E, int64_t N, const double* xyz, const int4* conn, const int32_t* mat,
                               int n_mat, const double* lmr, double* rec64, float* rec32, int* err_flag,
                               cudaStream_t s) {
-  k_elem_setup<<<grid_for(E, 152 * 16), kBlock, 0, s>>>(E, N, xyz, conn, mat, n_mat, lmr, rec64, rec32, err_flag);
+  k_elem_setup<<<grid_for(E, wide_grid_cap()), kBlock, 0, s>>>(E, N, xyz, conn, mat, n_mat, lmr, rec64, rec32, err_flag);
   return cudaGetLastError();
 }
 
 cudaError_t launch_diag_blocks(const MeshView& m, double aM, double aK, double* D, cudaStream_t s) {
-  k_diag_blocks<<<grid_for(m.E, 152 * 16), kBlock, 0, s>>>(m, aM, aK, D);
+  k_diag_blocks<<<grid_for(m.E, wide_grid_cap()), kBlock, 0, s>>>(m, aM, aK, D);
   return cudaGetLastError();
 }
 
 cudaError_t launch_binv(int64_t N, const double* D, const uint8_t* freemask, double* binv64, float* binv32,
                         int* err_flag, cudaStream_t s) {
-  k_binv<<<grid_for(N, 152 * 16), kBlock, 0, s>>>(N, D, freemask, binv64, binv32, err_flag);
+  k_binv<<<grid_for(N, wide_grid_cap()), kBlock, 0, s>>>(N, D, freemask, binv64, binv32, err_flag);
   return cudaGetLastError();
 }
 

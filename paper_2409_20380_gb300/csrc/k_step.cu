@@ -89,7 +89,7 @@ template <typename E> __device__ __forceinline__ const E* snap_slot(const E* rin
 static int vec_grid(int64_t items) {
   int64_t g = (items + kVecBlock - 1) / kVecBlock;
   if (g < 1) g = 1;
-  if (g > kVecGrid) g = kVecGrid;
+  if (g > vec_grid_cap()) g = vec_grid_cap();
   return (int)g;
 }
 
@@ -940,7 +940,7 @@ cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, 
 }
 
 cudaError_t launch_extract_all(int64_t N, int rpad, int n_cases, const double* src, double* dst, cudaStream_t s) {
-  k_extract_all<<<grid_for(N * 3, 152 * 16), kBlock, 0, s>>>(N * 3, rpad, n_cases, src, dst);
+  k_extract_all<<<grid_for(N * 3, wide_grid_cap()), kBlock, 0, s>>>(N * 3, rpad, n_cases, src, dst);
   return cudaGetLastError();
 }
 

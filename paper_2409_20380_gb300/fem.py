@@ -27,7 +27,7 @@ EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_
            "fem_mesh_set_regions", "fem_ebe_apply",
            "fem_ebe_apply_noalloc", "fem_mesh10_create", "fem_mesh10_destroy", "fem_ebe10_apply", "pcg10_solve",
            "pcg_solve", "fem_batch_create", "fem_batch_destroy", "fem_case_add", "fem_step", "predictor_fit",
-           "predictor_predict", "fem_case_get", "fem_batch_set_loads", "fem_batch_get_field", "fem_batch_get_field_async",
+           "predictor_predict", "predictor_coefficients", "fem_case_get", "fem_batch_set_loads", "fem_batch_get_field", "fem_batch_get_field_async",
            "fem_batch_sync", "fem_step_async", "fem_batch_profile",
            "fem_case_stats", "fem_batch_steps", "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_get_params",
            "fem_mlp_forward", "fem_mlp_loss_grad", "fem_mlp_train", "fem_batch_set_mlp", "fem_batch_collect",
@@ -51,7 +51,8 @@ class fem_opts(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("s_max", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("tau", ctypes.c_double), ("snapshot_format", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("refresh_every", ctypes.c_int), ("cert_df", ctypes.c_int), ("fuse_meshes", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("use_graph", ctypes.c_int), ("wait_budget", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class fem_profile(ctypes.Structure):
@@ -105,6 +106,7 @@ def lib():
         "fem_step": (I, [P, I, P, P]),
         "predictor_fit": (I, [P, I]),
         "predictor_predict": (I, [P, I, P]),
+        "predictor_coefficients": (I, [P, I, P, ctypes.POINTER(I)]),
         "fem_case_get": (I, [P, I, I, P, I]),
         "fem_batch_set_loads": (I, [P, P]),
         "fem_batch_get_field": (I, [P, I, P, I]),
@@ -322,6 +324,14 @@ def predictor_fit(batch, case_id):
 def predictor_predict(batch, case_id, x_guess):
     import torch
     _check(lib().predictor_predict(batch, case_id, _ptr(x_guess, torch.float64)))
+
+
+def predictor_coefficients(batch, case_id, n_regions, s_max):
+    """Returns (coefficients [n_regions][s_max], pairs used) of the last step's data-driven correction."""
+    coef = np.zeros((n_regions, s_max), dtype=np.float64)
+    n = ctypes.c_int(0)
+    _check(lib().predictor_coefficients(batch, case_id, _np_ptr(coef), ctypes.byref(n)))
+    return coef, n.value
 
 
 def fem_case_get(batch, case_id, what, n_nodes, out=None):

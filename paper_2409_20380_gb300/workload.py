@@ -237,15 +237,31 @@ def config3_mesh(mesh_id: int, dims) -> Mesh:
 
 
 def config4_mesh(Hx=256, Hy=256, Hz=128, h=1.0 / 64) -> Mesh:
-    """Five seeded layers plus a half-ellipsoid low-velocity basin (mu x 0.3) at the surface."""
+    """Five seeded layers plus a half-ellipsoid low-velocity basin (mu x 0.3) at the surface.
+
+    The full configuration is the 256 x 256 x 128 hex box (4 x 4 x 2, 50,331,648 tets, 8,520,321 nodes).  Smaller
+    dims give the same recipe scaled to the box: layer interfaces at the same depth fractions, the basin's
+    centre at the same fractions of the top face and its semi-axes scaled by the box's extent (by Lx / 4,
+    Ly / 4 and Lz / 2), with the same seeded draws."""
     rng = rng_for(4, 0, 0, 1)
     zt = Hz * h
     tops = [zt * f for f in (0.2, 0.4, 0.6, 0.8)]
     base = [(16.0, 8.0), (12.0, 6.0), (8.0, 4.0), (4.0, 2.0), (2.0, 1.0)]
     Lx, Ly = Hx * h, Hy * h
     basin = (rng.uniform(0.25 * Lx, 0.75 * Lx), rng.uniform(0.25 * Ly, 0.75 * Ly),
-             rng.uniform(0.5, 1.5), rng.uniform(0.5, 1.5), rng.uniform(0.3, 1.0), 0.3)
+             rng.uniform(0.5, 1.5) * Lx / 4.0, rng.uniform(0.5, 1.5) * Ly / 4.0, rng.uniform(0.3, 1.0) * zt / 2.0,
+             0.3)
     return layered_mesh(Hx, Hy, Hz, h, layer_tops=tops, base_lame=base, sigma=0.3, rng=rng, basin=basin)
+
+
+def config4_time_params() -> TimeParams:
+    """The large box has the medium meshes' spacing h = 1/64, so the same dt = 0.004 and damping."""
+    return TimeParams(dt=0.004, a0=0.01, a1=0.001)
+
+
+def config4_sources(mesh: Mesh, n_cases: int = 8, first_case: int = 0):
+    """Ricker point forces at seeded interior nodes, f0 ~ U[2, 8], seeded unit directions."""
+    return [random_source(mesh, rng_for(4, 0, first_case + c, 2)) for c in range(n_cases)]
 
 
 def ricker_load(src: Source, t: float) -> np.ndarray:
