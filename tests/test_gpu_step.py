@@ -66,8 +66,13 @@ def _run_and_check(mesh, tp, sources, opts, n_steps, region_nodes=None, check_pr
                 assert cert < opts.tol, (it, c, cert)
                 assert abs(relres[c] - cert) <= 1e-3 * opts.tol + 1e-6 * cert
                 u_ref, v_ref, a_ref = oracle.newmark_update(S["u"], S["v"], S["a"], du, tp.dt)
-                for got, ref in ((u, u_ref), (v, v_ref), (a, a_ref)):
-                    assert np.abs(got - ref).max() <= 1e-13 * max(np.abs(ref).max(), 1e-300)
+                # a few ulps of the largest term of each update formula (u + du; 2/dt du - v;
+                # 4/dt^2 du - 4/dt v - a)
+                dmax = np.abs(du).max()
+                scales = (max(np.abs(S["u"]).max(), dmax), max(2.0 / tp.dt * dmax, np.abs(S["v"]).max()),
+                          max(4.0 / tp.dt ** 2 * dmax, 4.0 / tp.dt * np.abs(S["v"]).max(), np.abs(S["a"]).max()))
+                for got, ref, sc in ((u, u_ref, scales[0]), (v, v_ref, scales[1]), (a, a_ref, scales[2])):
+                    assert np.abs(got - ref).max() <= 1e-13 * max(np.abs(ref).max(), sc, 1e-300), (it, c)
                 # predictor from the GPU's own history
                 u_ab = oracle.adams_bashforth4(S["u"], S["vh"], tp.dt)
                 du_ab = (u_ab - S["u"])
@@ -122,6 +127,10 @@ def stored_value(v, fmt):
 # Relative rounding of one Gram entry as the GPU accumulates it, per snapshot format: FP64 FMAs; FP32
 # products with compensated FP32 sums; double-float products and sums (formats 2 and 3).
 GRAM_EPS = {0: 2.0 ** -52, 1: 2.0 ** -23, 2: 2.0 ** -46, 3: 2.0 ** -46}
+# Unit of the stored value per format.  The test forms the corrections e = du - du_AB from its own
+# Adams-Bashforth increment, which differs from the GPU's by FP64 rounding; where that difference crosses a
+# rounding boundary of the storage format, the modelled stored value and the GPU's differ by one unit.
+STORE_EPS = {0: 2.0 ** -52, 1: 2.0 ** -24, 2: 2.0 ** -48, 3: 2.0 ** -32}
 
 
 class PredStats:
@@ -181,7 +190,7 @@ def check_prediction(E, reg_dof, n_reg, y_gpu, coef, n_pairs, opts, floor, stats
         # FP32 for FP32 snapshots, double-float or FP64 otherwise)
         comb = np.abs(YR).max() * np.abs(cg).sum()
         err = np.abs(yg - YR @ cg).max()
-        ceps = 4e-6 if opts.snapshot_format == 1 else 1e-12
+        ceps = (4e-6 if opts.snapshot_format == 1 else 1e-12) + 4.0 * STORE_EPS[opts.snapshot_format]
         stats.note("consistency", err / (ceps * comb + floor + 1e-300), where + (R,) if where else R)
         # the oracle: MGS with the drop rule, and each column's orthogonalised norm ratio
         U, P, kept = oracle.mgs_upper(XR, tau)
@@ -212,11 +221,14 @@ def check_prediction(E, reg_dof, n_reg, y_gpu, coef, n_pairs, opts, floor, stats
         else:
             cond_k, smax = 1.0, 0.0
         xn = np.linalg.norm(xR)
-        bound = 30.0 * eps * (min(cond_k, 1e12) * smax * np.linalg.norm(w_ref) + xn) + 1e-14 * xn + floor
+        seps = 4.0 * STORE_EPS[opts.snapshot_format]
+        bound = (30.0 * eps * (min(cond_k, 1e12) * smax * np.linalg.norm(w_ref) + xn) + 1e-14 * xn + floor +
+                 seps * (np.linalg.norm(XR) * np.abs(cg).sum() + xn))
         stats.note("objective", max(res_g - res_ref, 0.0) / bound, where + (R,) if where else R)
         if cond_k <= 1e6 and not amb.any():
             stats.elementwise += 1
-            bnd = 10.0 * eps * cond_k ** 2 * np.abs(YR).max() * np.abs(w_ref).sum() + 1e-13 * np.abs(y_ref).max() + floor
+            bnd = ((10.0 * eps * cond_k ** 2 + seps * cond_k) * np.abs(YR).max() * np.abs(w_ref).sum() +
+                   1e-13 * np.abs(y_ref).max() + floor)
             stats.note("elementwise", np.abs(yg - y_ref).max() / bnd, where + (R,) if where else R)
 
 
