@@ -105,6 +105,11 @@ def parse():
     ap.add_argument("--eval-cases", type=int, default=32)
     ap.add_argument("--case-steps", type=int, default=500, help="steps per case (learned-proposal mode)")
     ap.add_argument("--updates", type=int, default=3000)
+    ap.add_argument("--loss", default="residual", choices=["residual", "coef"],
+                    help="learned proposal: residual-space loss ||Y (c + d) - e||^2 / ||e||^2 per region, or the "
+                         "squared error of the coefficient correction")
+    ap.add_argument("--dt", type=float, default=None, help="time step (default: the configuration's)")
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--batch", type=int, default=4096)
     a = ap.parse_args()
     if a.learned or a.uneven or a.kernel in ("ebe10", "pcg10"):
@@ -763,21 +768,29 @@ def run_learned(args):
     Hx, Hy, Hz = (int(v) for v in args.dims.split(","))
     mesh = wl.config2_mesh(Hx, Hy, Hz)
     tp = wl.config2_time_params()
+    if args.dt:
+        tp.dt = args.dt
     regions = wl.region_map(mesh, args.region_nodes)
     R = int(regions.max()) + 1
     train_src, held_src = wl.config5_sources(mesh, args.train_cases, args.eval_cases)
+    residual = args.loss == "residual"
+    tw = fem.FEM_MLP_RES if residual else 32
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
     K = args.case_steps
+    # both arms step eagerly (the proposal is not captured in the step graph): the same mode for both
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
-                                tol=1e-8, snapshot_format=args.snapshot_format, cert_df=args.cert)
+                                tol=1e-8, snapshot_format=args.snapshot_format, cert_df=args.cert, use_graph=0)
+
+    counts = [0, 0]
 
     def run(srcs, net=None, xs=None, ts=None, window=(250, 500)):
         """Cases in batches of --cases; returns (rows collected, case-steps/s over the window, iterations,
         log initial residuals over the window)."""
         rows, t_win, cs_win, its, logs = 0, 0.0, 0, 0, []
+        counts[:] = [0, 0]
         for g0 in range(0, len(srcs), args.cases):
             grp = srcs[g0:g0 + args.cases]
             bt = fem.fem_batch_create(opts)
@@ -786,7 +799,7 @@ def run_learned(args):
             if net is not None:
                 fem.fem_batch_set_mlp(bt, net)
             if xs is not None:
-                fem.fem_batch_collect(bt, xs[rows:], ts[rows:])
+                (fem.fem_batch_collect_residual if residual else fem.fem_batch_collect)(bt, xs[rows:], ts[rows:])
             nc = len(grp)
             w0, w1 = min(window[0], K), min(window[1], K)
             fem.fem_step(bt, w0, nc)
@@ -806,12 +819,16 @@ def run_learned(args):
                 fem.fem_step(bt, K - w1, nc)
             if xs is not None:
                 rows += fem.fem_batch_collected(bt)[0]
+            if net is not None:
+                tk, rj = fem.fem_batch_proposal_counts(bt)
+                counts[0] += tk
+                counts[1] += rj
             fem.fem_batch_destroy(bt)
         return rows, (cs_win / t_win if t_win > 0 else None), its, logs
 
     cap = len(train_src) * K * R
     xs = torch.empty((cap, 64), device="cuda")
-    ts = torch.empty((cap, 32), device="cuda")
+    ts = torch.empty((cap, tw), device="cuda")
     t0 = time.perf_counter()
     rows, _, _, _ = run(train_src, xs=xs, ts=ts, window=(K, K))
     torch.cuda.synchronize()
@@ -820,22 +837,24 @@ def run_learned(args):
     g = torch.Generator(device="cuda").manual_seed(0)
     order = torch.randint(0, rows, (args.updates, args.batch), device="cuda", generator=g, dtype=torch.int32)
     t0 = time.perf_counter()
-    losses = fem.fem_mlp_train(net, xs[:rows], ts[:rows], order, lr=1e-3)
+    losses = (fem.fem_mlp_train_residual if residual else fem.fem_mlp_train)(net, xs[:rows], ts[:rows], order,
+                                                                              lr=args.lr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    train_var = float((ts[:rows] ** 2).mean())
+    # loss of the zero correction (the plain predictor): mean of ||w||^2, or of the squared targets
+    train_var = float((ts[:rows, -32:] ** 2).sum(dim=1).mean()) if residual else float((ts[:rows] ** 2).mean())
     del xs, ts
     hcap = len(held_src) * K * R
     hx = torch.empty((hcap, 64), device="cuda")
-    ht = torch.empty((hcap, 32), device="cuda")
+    ht = torch.empty((hcap, tw), device="cuda")
     hrows, v_dd, it_dd, log_dd = run(held_src, xs=hx, ts=ht)
     held_loss, n_l = 0.0, 0
     for a in range(0, hrows, 65536):
         b = min(hrows, a + 65536)
-        held_loss += fem.fem_mlp_loss_grad(net, hx[a:b], ht[a:b]) * (b - a)
+        held_loss += (fem.fem_mlp_loss_grad_residual if residual else fem.fem_mlp_loss_grad)(net, hx[a:b], ht[a:b]) * (b - a)
         n_l += b - a
     held_loss /= max(n_l, 1)
-    held_var = float((ht[:hrows] ** 2).mean())
+    held_var = float((ht[:hrows, -32:] ** 2).sum(dim=1).mean()) if residual else float((ht[:hrows] ** 2).mean())
     del hx, ht
     _, v_ml, it_ml, log_ml = run(held_src, net=net)
     print(json.dumps({
@@ -843,13 +862,18 @@ def run_learned(args):
         "unit": UNIT, "value": v_ml, "plain_dd_value": v_dd,
         "config": {"workload": f"medium {args.dims.replace(',', 'x')} mesh, {len(train_src)} training + "
                                f"{len(held_src)} held-out cases x {K} steps, window steps 251-{min(500, K)}, "
-                               f"s={args.s_max}, regions of {args.region_nodes} nodes ({R})",
-                   "updates": args.updates, "batch": args.batch},
+                               f"s={args.s_max}, regions of {args.region_nodes} nodes ({R}), dt={tp.dt}",
+                   "updates": args.updates, "batch": args.batch, "loss": args.loss, "lr": args.lr,
+                   "step_mode": "eager (both arms)"},
         "samples": rows, "sample_gen_s": t_gen, "train_s": t_train,
         "train_loss_first": float(losses[0]), "train_loss_last": float(np.mean(losses[-50:])),
         "train_target_mean_sq": train_var, "heldout_loss": held_loss, "heldout_target_mean_sq": held_var,
         "heldout_r2": 1.0 - held_loss / held_var if held_var > 0 else None,
+        "loss_note": ("residual space: mean over samples of ||W d - w||^2 = relative error of the corrected guess "
+                      "above the least-squares floor; *_target_mean_sq is that of the plain predictor (d = 0)")
+                     if residual else "coefficient space: mean squared error of c* - c",
         "cg_iters_per_case_step": {"plain_dd": it_dd / max(len(log_dd), 1), "learned": it_ml / max(len(log_ml), 1)},
+        "proposal_taken_rejected": list(counts),
         "geo_mean_init_relres": {"plain_dd": math.exp(np.mean(log_dd)), "learned": math.exp(np.mean(log_ml))},
     }), flush=True)
     fem.fem_mlp_destroy(net)

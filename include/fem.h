@@ -443,6 +443,7 @@ fem_status fem_batch_steps(const fem_batch* b, int* steps_out);
 #define FEM_MLP_N_PARAMS 90656
 #define FEM_MLP_IN 64
 #define FEM_MLP_OUT 32
+#define FEM_MLP_RES 560     /* values of one residual-space sample: 528 (upper triangle of W) + 32 (w) */
 typedef struct fem_mlp fem_mlp;
 
 /* Creates a network from host parameters (copied) on the current device; Adam moments start at zero.
@@ -464,6 +465,19 @@ fem_status fem_mlp_loss_grad(fem_mlp* net, const float* x_dev, const float* t_de
 fem_status fem_mlp_train(fem_mlp* net, const float* x_dev, const float* t_dev, int64_t n_samples,
                          const int32_t* order_dev, int n_updates, int batch, double lr, double* loss_out);
 
+/*
+ * The same with the residual-space loss, the error measure the proposal's acceptance decides on: per sample
+ * (region R, case) the relative error ||Y_R (c_R + d) - e_R||^2 / ||e_R||^2 of the corrected coefficients,
+ * d = net(x) in age order.  Y_R's Gram is factored R^T R (in age order, with the predictor's column-drop rule),
+ * so that the error is ||W d - w||^2 plus a part d cannot change, W = R / ||e_R||, w = (R^{-T} Y_R^T e_R - R c_R)
+ * / ||e_R||.  A sample s_dev row holds FEM_MLP_RES floats: the upper triangle of W row by row (W_ij, i <= j),
+ * then w.  Loss = mean over the samples of ||W d - w||^2; otherwise as fem_mlp_loss_grad / fem_mlp_train.
+ */
+fem_status fem_mlp_loss_grad_residual(fem_mlp* net, const float* x_dev, const float* s_dev, int64_t B,
+                                      float* grad_dev, double* loss_out);
+fem_status fem_mlp_train_residual(fem_mlp* net, const float* x_dev, const float* s_dev, int64_t n_samples,
+                                  const int32_t* order_dev, int n_updates, int batch, double lr, double* loss_out);
+
 /* Uses `net` (NULL: none) for the learned proposal in the batch's next steps.  Needs FEM_FP32_INNER, the
  * data-driven predictor, regions and groups of one mesh (no fuse_meshes).  The caller keeps ownership and
  * must not train the network while the batch steps. */
@@ -473,6 +487,10 @@ fem_status fem_batch_set_mlp(fem_batch* b, fem_mlp* net);
  * n_regions x n_cases rows (region-major, then case) while they fit.  Same requirements as
  * fem_batch_set_mlp. */
 fem_status fem_batch_collect(fem_batch* b, float* x_dev, float* t_dev, int64_t capacity);
+/* As fem_batch_collect, but each sample's training data is the residual-space form (W, w) of
+ * fem_mlp_train_residual: s_dev [capacity][FEM_MLP_RES], computed from the stored-snapshot Gram after the
+ * step's correction e^it is pushed.  A region whose e_R is zero gives a zero sample. */
+fem_status fem_batch_collect_residual(fem_batch* b, float* x_dev, float* s_dev, int64_t capacity);
 /* Rows collected so far; *full = 1 if a step's rows no longer fit. */
 fem_status fem_batch_collected(fem_batch* b, int64_t* rows, int* full);
 /* Case-steps in which the learned proposal was taken / rejected (initial residual not smaller). */

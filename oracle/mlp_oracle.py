@@ -29,6 +29,14 @@ Readings (the paper states the data-driven predictor, and the network form is se
       coefficient space says little about the prediction Y_R c.
   L5  loss = mean over samples and the 32 outputs of the squared error; Adam with bias correction
       (lr 1e-3, beta = 0.9 / 0.999, eps = 1e-8).
+  L6  residual-space loss (the quantity the acceptance test decides on): per sample (region R, case) the
+      relative error of the proposed correction, ||Y_R (c_R + d) - e_R||^2 / ||e_R||^2, d the network output
+      in age order.  With Y_R's columns in age order, MGS (drop rule R9) gives P with orthonormal kept columns
+      and R = P^T Y_R (upper triangular); then ||Y_R (c_R + d) - e_R||^2 = ||R (c_R + d) - P^T e_R||^2 +
+      ||(I - P P^T) e_R||^2 (up to the dropped columns' parts outside span(P), below tau of their norms), so
+      the loss is ||W d - w||^2 + const with W = R / ||e_R|| and w = (P^T e_R - R c_R) / ||e_R||.  A sample
+      stores W (upper triangle, row by row) and w; no target clipping is needed, since directions Y_R leaves
+      undetermined carry no weight.  Loss = mean over samples of ||W d - w||^2.
 """
 from __future__ import annotations
 
@@ -108,12 +116,18 @@ def loss(theta, X, T):
 
 def loss_and_grad(theta, X, T):
     """Mean squared error over all B x 32 outputs and its gradient (reverse mode, layer by layer)."""
-    W1, b1, W2, b2, W3, b3 = unpack(theta)
-    out, (X0, Z1, A1, Z2, A2) = forward(theta, X)
+    out, cache = forward(theta, X)
     B = X.shape[0]
     diff = out - T
     L = float(np.mean(diff ** 2))
     d3 = 2.0 * diff / (B * out.shape[1])          # dL/dout
+    return L, backprop(theta, cache, d3)
+
+
+def backprop(theta, cache, d3):
+    """Gradient of a loss with respect to the parameters, given dL/dout = d3 [B][32]."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    X0, Z1, A1, Z2, A2 = cache
     gW3 = d3.T @ A2
     gb3 = d3.sum(axis=0)
     d2 = (d3 @ W3) * gelu_grad(Z2)                 # dL/dZ2
@@ -122,7 +136,80 @@ def loss_and_grad(theta, X, T):
     d1 = (d2 @ W2) * gelu_grad(Z1)                 # dL/dZ1
     gW1 = d1.T @ X0
     gb1 = d1.sum(axis=0)
-    return L, pack([gW1, gb1, gW2, gb2, gW3, gb3])
+    return pack([gW1, gb1, gW2, gb2, gW3, gb3])
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Residual-space loss (L6)
+# ---------------------------------------------------------------------------------------------------------
+N_TRI = N_COEF * (N_COEF + 1) // 2          # packed upper triangle of W
+N_RES = N_TRI + N_COEF                      # one residual-space sample: W then w
+
+
+def pack_residual(W, w):
+    """[W upper triangle row by row (i <= j), w] as one vector of N_RES values."""
+    iu = np.triu_indices(N_COEF)
+    return np.concatenate([W[iu], w])
+
+
+def unpack_residual(S):
+    """Inverse of pack_residual for a [B][N_RES] array: (W [B][32][32], w [B][32])."""
+    S = np.atleast_2d(S)
+    B = S.shape[0]
+    W = np.zeros((B, N_COEF, N_COEF))
+    iu = np.triu_indices(N_COEF)
+    W[:, iu[0], iu[1]] = S[:, :N_TRI]
+    return W, S[:, N_TRI:].copy()
+
+
+def residual_sample(Y, e, c, tau=1e-6):
+    """(W [32][32], w [32]) of one sample (L6).  Y [rows][n]: the stored outputs y_a = e^{it-n+a} (oldest
+    first), e the correction the solve found, c [n] the predictor's coefficients (slot order).  Everything
+    is returned in age order (index k belongs to the pair whose output is e^{it-1-k})."""
+    n = Y.shape[1]
+    W = np.zeros((N_COEF, N_COEF))
+    w = np.zeros(N_COEF)
+    ne = float(np.linalg.norm(e))
+    if n == 0 or ne == 0.0:
+        return W, w
+    Ya = Y[:, ::-1]                      # age order
+    ca = np.asarray(c, dtype=np.float64)[::-1]
+    _, P, _ = mgs_upper(Ya, tau)
+    R = P.T @ Ya
+    W[:n, :n] = R / ne
+    w[:n] = (P.T @ e - R @ ca) / ne
+    return W, w
+
+
+def loss_residual(theta, X, S):
+    """L6 loss: mean over the samples of ||W d - w||^2, d = net(x)."""
+    out, _ = forward(theta, X)
+    W, w = unpack_residual(S)
+    r = np.einsum("bij,bj->bi", W, out) - w
+    return float(np.mean(np.sum(r * r, axis=1)))
+
+
+def loss_and_grad_residual(theta, X, S):
+    """L6 loss and its gradient: dL/dd_b = 2 W_b^T (W_b d_b - w_b) / B, then the same reverse pass."""
+    out, cache = forward(theta, X)
+    W, w = unpack_residual(S)
+    B = X.shape[0]
+    r = np.einsum("bij,bj->bi", W, out) - w
+    L = float(np.mean(np.sum(r * r, axis=1)))
+    d3 = 2.0 * np.einsum("bij,bi->bj", W, r) / B
+    return L, backprop(theta, cache, d3)
+
+
+def train_residual(theta, X, S, batches, lr=1e-3):
+    """Adam on the L6 loss over the given minibatch index arrays; returns (theta, losses before each update)."""
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    losses = []
+    for t, idx in enumerate(batches, start=1):
+        L, g = loss_and_grad_residual(theta, X[idx], S[idx])
+        losses.append(L)
+        theta, m, v = adam_step(theta, g, m, v, t, lr)
+    return theta, losses
 
 
 def adam_step(theta, g, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -202,6 +289,26 @@ def to_age_order(coef_slot_order, n_out=N_COEF):
 
 def from_age_order(coef_age, n):
     return np.array([coef_age[n - 1 - a] for a in range(n)])
+
+
+def step_samples_residual(sim, src_pos, centroids, extent, f0, tau=1e-6):
+    """Residual-space samples (L6) of the step `sim` has just taken: per region (features at prediction time,
+    packed (W, w)).  Returns (X [R][64], S [R][N_RES])."""
+    n = sim.last_npairs
+    R_all = sim.n_regions
+    X = np.zeros((R_all, LAYERS[0]))
+    S = np.zeros((R_all, N_RES))
+    W = sim.last_W
+    if n > 0:
+        Y = np.stack(sim.E_hist[-(n + 1):-1], axis=1)
+        e = sim.E_hist[-1]
+    for R in range(R_all):
+        c = W[R, :n] if n > 0 else np.zeros(0)
+        X[R] = features(src_pos, centroids[R], extent, f0, c)
+        if n > 0:
+            idx = np.nonzero(sim.region_of_dof == R)[0]
+            S[R] = pack_residual(*residual_sample(Y[idx], e[idx], c, tau))
+    return X, S
 
 
 def step_samples(sim, src_pos, centroids, extent, f0, tau=1e-6):

@@ -726,7 +726,8 @@ struct fem_batch {
   bool started = false;
   int steps = 0;
   fem_mlp* mlp = nullptr;              // learned proposal (caller-owned), or none
-  float* col_x = nullptr;              // caller-owned sample buffers [capacity][64] / [capacity][32]
+  float* col_x = nullptr;              // caller-owned sample buffers [capacity][64] / [capacity][32 or FEM_MLP_RES]
+  bool col_res = false;                // residual-space samples (W, w) instead of coefficient targets
   float* col_t = nullptr;
   int64_t col_cap = 0, col_n = 0;
   bool col_full = false;
@@ -1070,13 +1071,19 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     if (bt->col_x && g->featured && g->last_npairs > 0) {
       const int64_t rows = (int64_t)g->n_regions * g->ncase;
       if (bt->col_n + rows <= bt->col_cap) {
-        PredView pt = pred_view(bt, g);
-        pt.w = g->wbest;
-        CU(launch_pred_solve(pt, g->slot_lists + kMaxSlots, g->last_npairs, slot_of(g, it), o.tau, s));
-        CU(mlp_collect(g->n_regions, g->rpad, g->ncase, g->last_npairs, g->F, g->wbest, g->wcoef, bt->col_n,
-                       bt->col_x, bt->col_t, s));
+        if (bt->col_res) {
+          CU(mlp_collect_res(pred_view(bt, g), g->slot_lists + kMaxSlots, g->last_npairs, slot_of(g, it), o.tau,
+                             g->ncase, g->F, bt->col_n, bt->col_x, bt->col_t, s));
+          w->count();
+        } else {
+          PredView pt = pred_view(bt, g);
+          pt.w = g->wbest;
+          CU(launch_pred_solve(pt, g->slot_lists + kMaxSlots, g->last_npairs, slot_of(g, it), o.tau, s));
+          CU(mlp_collect(g->n_regions, g->rpad, g->ncase, g->last_npairs, g->F, g->wbest, g->wcoef, bt->col_n,
+                         bt->col_x, bt->col_t, s));
+          w->count(2);
+        }
         bt->col_n += rows;
-        w->count(2);
       } else {
         bt->col_full = true;
       }
@@ -2189,8 +2196,7 @@ fem_status fem_batch_set_mlp(fem_batch* b, fem_mlp* net) {
   return FEM_OK;
 }
 
-fem_status fem_batch_collect(fem_batch* b, float* x_dev, float* t_dev, int64_t capacity) {
-  g_err.clear();
+static fem_status batch_collect(fem_batch* b, float* x_dev, float* t_dev, int64_t capacity, bool residual) {
   if (!b) return fail(FEM_ERR_ARG, "batch is null");
   if (!x_dev) {
     b->col_x = b->col_t = nullptr;
@@ -2201,10 +2207,21 @@ fem_status fem_batch_collect(fem_batch* b, float* x_dev, float* t_dev, int64_t c
   CHK(learn_ok(b));
   b->col_x = x_dev;
   b->col_t = t_dev;
+  b->col_res = residual;
   b->col_cap = capacity;
   b->col_n = 0;
   b->col_full = false;
   return FEM_OK;
+}
+
+fem_status fem_batch_collect(fem_batch* b, float* x_dev, float* t_dev, int64_t capacity) {
+  g_err.clear();
+  return batch_collect(b, x_dev, t_dev, capacity, false);
+}
+
+fem_status fem_batch_collect_residual(fem_batch* b, float* x_dev, float* s_dev, int64_t capacity) {
+  g_err.clear();
+  return batch_collect(b, x_dev, s_dev, capacity, true);
 }
 
 fem_status fem_batch_collected(fem_batch* b, int64_t* rows, int* full) {

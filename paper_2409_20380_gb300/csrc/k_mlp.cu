@@ -20,6 +20,10 @@ typedef __nv_bfloat16 bf16;
 namespace {
 
 constexpr int kL0 = 64, kL1 = 256, kL2 = 256, kL3 = 32;
+// A residual-space sample: the upper triangle of W (row by row) and w, in age order.
+constexpr int kNTri = kL3 * (kL3 + 1) / 2;
+constexpr int kNRes = kNTri + kL3;
+static_assert(kNRes == FEM_MLP_RES, "residual sample size");
 constexpr int64_t kOffW1 = 0;
 constexpr int64_t kOffB1 = kOffW1 + (int64_t)kL1 * kL0;
 constexpr int64_t kOffW2 = kOffB1 + kL1;
@@ -191,6 +195,43 @@ __global__ void k_loss(const float* __restrict__ out, const float* __restrict__ 
   if ((threadIdx.x & 31) == 0 && sq != 0.0) atomicAdd(loss_acc, sq);
 }
 
+// dL/dout of the residual-space loss, one warp per row: with the row's sample (W upper triangular, w),
+// r = W d - w, loss += ||r||^2, dL/dd = 2 W^T r / B; FP32 and BF16 (row-major and transposed); pad rows zero.
+__global__ void __launch_bounds__(256) k_loss_res(const float* __restrict__ out, const float* __restrict__ smp,
+                                                  const int32_t* __restrict__ idx, int64_t n_src, int64_t B,
+                                                  int64_t Mpad, float* __restrict__ dzf, bf16* __restrict__ dzb,
+                                                  bf16* __restrict__ dzT, double* __restrict__ loss_acc) {
+  __shared__ float sd[8][kL3], sr[8][kL3];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const float scale = 2.0f / (float)B;
+  for (int64_t r = (int64_t)blockIdx.x * 8 + wp; r < Mpad; r += (int64_t)gridDim.x * 8) {
+    const int64_t sr_ = r < B ? (idx ? (int64_t)idx[r] : r) : -1;
+    const bool valid = sr_ >= 0 && sr_ < n_src;
+    float g = 0.0f;
+    if (valid) {
+      const float* S = smp + sr_ * kNRes;
+      sd[wp][lane] = out[r * kL3 + lane];
+      __syncwarp();
+      // r_i = sum_{j >= i} W_ij d_j - w_i  (lane i; row i of the packed triangle starts at 32 i - i (i - 1) / 2)
+      const int off = lane * kL3 - lane * (lane - 1) / 2;
+      float ri = -S[kNTri + lane];
+      for (int j = lane; j < kL3; ++j) ri = fmaf(S[off + j - lane], sd[wp][j], ri);
+      sr[wp][lane] = ri;
+      double sq = (double)ri * ri;
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0) atomicAdd(loss_acc, sq);
+      __syncwarp();
+      // g_j = scale sum_{i <= j} W_ij r_i  (lane j)
+      for (int i = 0; i <= lane; ++i) g = fmaf(S[i * kL3 - i * (i - 1) / 2 + lane - i], sr[wp][i], g);
+      g *= scale;
+      __syncwarp();
+    }
+    dzf[r * kL3 + lane] = g;
+    dzb[r * kL3 + lane] = __float2bfloat16_rn(g);
+    dzT[(int64_t)lane * Mpad + r] = __float2bfloat16_rn(g);
+  }
+}
+
 // Bias gradient: column sums of dz [Mpad][N] (fixed order: deterministic).
 __global__ void k_colsum(const float* __restrict__ dz, int64_t Mpad, int N, float* __restrict__ out) {
   __shared__ float part[8][33];
@@ -357,10 +398,15 @@ cudaError_t forward(fem_mlp* n, const float* x, const int32_t* idx, int64_t n_sr
 
 // Backward of the mean squared error against t (rows gathered through idx) after forward(training):
 // gradient into n->grad, sum of squared errors added to n->loss_acc.
-cudaError_t backward(fem_mlp* n, const float* t, const int32_t* idx, int64_t n_src, int64_t B, cudaStream_t s) {
+cudaError_t backward(fem_mlp* n, const float* t, const int32_t* idx, int64_t n_src, int64_t B, cudaStream_t s,
+                     bool residual = false) {
   const int64_t Mp = ((B + 63) / 64) * 64;
   const int M = (int)Mp;
-  k_loss<<<grid_of(Mp * kL3), 256, 0, s>>>(n->OUT, t, idx, n_src, B, Mp, n->dZ3f, n->dZ3b, n->dZ3T, n->loss_acc);
+  if (residual)
+    k_loss_res<<<(int)std::min<int64_t>((Mp + 7) / 8, 4096), 256, 0, s>>>(n->OUT, t, idx, n_src, B, Mp, n->dZ3f,
+                                                                          n->dZ3b, n->dZ3T, n->loss_acc);
+  else
+    k_loss<<<grid_of(Mp * kL3), 256, 0, s>>>(n->OUT, t, idx, n_src, B, Mp, n->dZ3f, n->dZ3b, n->dZ3T, n->loss_acc);
   CE(cudaGetLastError());
   // dW3 [32][256] = dZ3^T A2, computed as its transpose (256 x 32, contraction over the batch)
   GemmArgs w3 = gargs(kL2, kL3, M, n->A2T, M, n->dZ3T, M);
@@ -541,6 +587,75 @@ __global__ void k_collect(int n_regions, int rpad, int ncase, int n_pairs, const
   }
 }
 
+// Residual-space training samples of one step (one warp per region and real case): the features F of the
+// step's prediction, and (W, w) of the relative residual ||Y (c + d) - e||^2 / ||e||^2 of a correction d to the
+// predictor's coefficients c, from the ring Gram after e = e^it is pushed.  In age order (index k: the pair
+// whose output is e^{it-1-k}) the Gram of Y is factored R^T R by the same right-looking Cholesky with the
+// column-drop rule as the predictor (pivot <= tau^2 G_kk drops column k: its row of R is zero); then
+// z = R^{-T} Y^T e, W = R / ||e||, w = (z - R c) / ||e||.  A sample with ||e|| = 0 or a non-finite value is zero.
+__global__ void __launch_bounds__(32) k_collect_res(PredView p, const int* __restrict__ y_slots, int n, int slot_new,
+                                                    double tau, int ncase, const float* __restrict__ F, int64_t row0,
+                                                    float* __restrict__ x_out, float* __restrict__ s_out) {
+  const int R = blockIdx.x / ncase, c = blockIdx.x % ncase;
+  const int lane = threadIdx.x;
+  constexpr int LD = kMaxSlots;
+  __shared__ double L[kMaxSlots * LD];
+  __shared__ double inv[kMaxSlots];
+  const int64_t src = (int64_t)R * p.rpad + c;
+  const int64_t row = row0 + (int64_t)R * ncase + c;
+  for (int j = lane; j < kL0; j += 32) x_out[row * kL0 + j] = F[src * kL0 + j];
+  const double* G = p.gram + src * kMaxSlots * kMaxSlots;
+  const int yk = lane < n ? y_slots[n - 1 - lane] : 0;
+  for (int i = 0; i < n; ++i) {
+    const int yi = __shfl_sync(0xffffffffu, yk, i);
+    if (lane < n) L[i * LD + lane] = G[yi * kMaxSlots + yk];
+  }
+  const double rhs = lane < n ? G[yk * kMaxSlots + slot_new] : 0.0;
+  const double d0 = lane < n ? G[yk * kMaxSlots + yk] : 0.0;
+  const double E = G[slot_new * kMaxSlots + slot_new];
+  __syncwarp();
+  for (int j = 0; j < n; ++j) {
+    const double djj = L[j * LD + j];
+    const double d0j = __shfl_sync(0xffffffffu, d0, j);
+    const bool keep = d0j > 0.0 && djj > tau * tau * d0j && isfinite(djj);
+    const double ip = keep ? rsqrt(djj) : 0.0;
+    __syncwarp();
+    if (lane > j && lane < n) L[lane * LD + j] = keep ? L[lane * LD + j] * ip : 0.0;
+    if (lane == j) {
+      L[j * LD + j] = keep ? djj * ip : 0.0;
+      inv[j] = ip;
+    }
+    __syncwarp();
+    if (keep && lane > j && lane < n) {   // lane i updates row i of the trailing block: L_ik -= L_ij L_kj
+      const double lij = L[lane * LD + j];
+      for (int k = j + 1; k <= lane; ++k) L[lane * LD + k] = fma(-lij, L[k * LD + j], L[lane * LD + k]);
+    }
+    __syncwarp();
+  }
+  double z = rhs;   // forward substitution R^T z = Y^T e (dropped columns give 0)
+  for (int j = 0; j < n; ++j) {
+    const double zr = __shfl_sync(0xffffffffu, z, j);
+    const double zj = inv[j] != 0.0 ? zr * inv[j] : 0.0;
+    if (lane == j) z = zj;
+    if (lane > j && lane < n) z -= L[lane * LD + j] * zj;
+  }
+  const double ck = lane < n ? p.w[src * kMaxSlots + (n - 1 - lane)] : 0.0;
+  double v = z;     // v_i = z_i - sum_{j >= i} R_ij c_j with R_ij = L_ji
+  for (int j = 0; j < n; ++j) {
+    const double cj = __shfl_sync(0xffffffffu, ck, j);
+    if (lane <= j && lane < n) v -= L[j * LD + lane] * cj;
+  }
+  double sc = (E > 0.0 && isfinite(E)) ? rsqrt(E) : 0.0;
+  if (__any_sync(0xffffffffu, !isfinite(v * sc))) sc = 0.0;
+  float* so = s_out + row * kNRes;
+  for (int i = 0; i < kL3; ++i) {
+    const int off = i * kL3 - i * (i - 1) / 2;
+    for (int j = i + lane; j < kL3; j += 32)
+      so[off + j - i] = (sc != 0.0 && i < n && j < n) ? (float)(L[j * LD + i] * sc) : 0.0f;
+  }
+  so[kNTri + lane] = (sc != 0.0 && lane < n) ? (float)(v * sc) : 0.0f;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------------------
@@ -592,6 +707,12 @@ cudaError_t mlp_collect(int n_regions, int rpad, int ncase, int n_pairs, const f
   const int64_t rows = (int64_t)n_regions * ncase;
   k_collect<<<grid_of(rows * (kL0 + 1)), 256, 0, s>>>(n_regions, rpad, ncase, n_pairs, F, w_best, w_pred, row0,
                                                         x_out, t_out);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_collect_res(const PredView& p, const int* y_slots, int n_pairs, int slot_new, double tau, int ncase,
+                            const float* F, int64_t row0, float* x_out, float* s_out, cudaStream_t s) {
+  k_collect_res<<<p.n_regions * ncase, 32, 0, s>>>(p, y_slots, n_pairs, slot_new, tau, ncase, F, row0, x_out, s_out);
   return cudaGetLastError();
 }
 
@@ -669,23 +790,27 @@ fem_status fem_mlp_forward(fem_mlp* n, const float* x_dev, int64_t B, float* out
   return FEM_OK;
 }
 
-fem_status fem_mlp_loss_grad(fem_mlp* n, const float* x_dev, const float* t_dev, int64_t B, float* grad_dev,
-                             double* loss_out) {
+
+static fem_status mlp_loss_grad_any(fem_mlp* n, const float* x_dev, const float* t_dev, int64_t B, float* grad_dev,
+                                    double* loss_out, bool residual) {
+  clear_error();
   if (!n || !x_dev || !t_dev || B <= 0) return set_error(FEM_ERR_ARG, "fem_mlp_loss_grad: bad argument");
   std::lock_guard<std::mutex> lk(n->mu);
   MCU(cudaMemsetAsync(n->loss_acc, 0, sizeof(double), n->s));
   MCU(forward(n, x_dev, nullptr, B, B, true, n->s));
-  MCU(backward(n, t_dev, nullptr, B, B, n->s));
+  MCU(backward(n, t_dev, nullptr, B, B, n->s, residual));
   if (grad_dev) MCU(cudaMemcpyAsync(grad_dev, n->grad, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, n->s));
   double acc = 0.0;
   MCU(cudaMemcpyAsync(&acc, n->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, n->s));
   MCU(cudaStreamSynchronize(n->s));
-  if (loss_out) *loss_out = acc / ((double)B * kL3);
+  if (loss_out) *loss_out = residual ? acc / (double)B : acc / ((double)B * kL3);
   return FEM_OK;
 }
 
-fem_status fem_mlp_train(fem_mlp* n, const float* x_dev, const float* t_dev, int64_t n_samples,
-                         const int32_t* order_dev, int n_updates, int batch, double lr, double* loss_out) {
+static fem_status mlp_train_any(fem_mlp* n, const float* x_dev, const float* t_dev, int64_t n_samples,
+                                const int32_t* order_dev, int n_updates, int batch, double lr, double* loss_out,
+                                bool residual) {
+  clear_error();
   if (!n || !x_dev || !t_dev || !order_dev || n_samples <= 0 || n_updates < 0 || batch <= 0 || !(lr > 0.0))
     return set_error(FEM_ERR_ARG, "fem_mlp_train: bad argument");
   std::lock_guard<std::mutex> lk(n->mu);
@@ -694,12 +819,12 @@ fem_status fem_mlp_train(fem_mlp* n, const float* x_dev, const float* t_dev, int
     const int32_t* idx = order_dev + (int64_t)u * batch;
     if (loss_out) MCU(cudaMemsetAsync(n->loss_acc, 0, sizeof(double), n->s));
     MCU(forward(n, x_dev, idx, n_samples, batch, true, n->s));
-    MCU(backward(n, t_dev, idx, n_samples, batch, n->s));
+    MCU(backward(n, t_dev, idx, n_samples, batch, n->s, residual));
     if (loss_out) {
       double acc = 0.0;
       MCU(cudaMemcpyAsync(&acc, n->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, n->s));
       MCU(cudaStreamSynchronize(n->s));
-      loss_out[u] = acc / ((double)batch * kL3);
+      loss_out[u] = residual ? acc / (double)batch : acc / ((double)batch * kL3);
     }
     MCU(adam(n, lr, n->s));
   }
@@ -708,6 +833,26 @@ fem_status fem_mlp_train(fem_mlp* n, const float* x_dev, const float* t_dev, int
   MCU(cudaStreamSynchronize(n->s));
   if (bad) return set_error(FEM_ERR_ARG, "fem_mlp_train: a sample index was outside [0, n_samples)");
   return FEM_OK;
+}
+
+fem_status fem_mlp_loss_grad(fem_mlp* n, const float* x_dev, const float* t_dev, int64_t B, float* grad_dev,
+                             double* loss_out) {
+  return mlp_loss_grad_any(n, x_dev, t_dev, B, grad_dev, loss_out, false);
+}
+
+fem_status fem_mlp_loss_grad_residual(fem_mlp* n, const float* x_dev, const float* s_dev, int64_t B, float* grad_dev,
+                                      double* loss_out) {
+  return mlp_loss_grad_any(n, x_dev, s_dev, B, grad_dev, loss_out, true);
+}
+
+fem_status fem_mlp_train(fem_mlp* n, const float* x_dev, const float* t_dev, int64_t n_samples,
+                         const int32_t* order_dev, int n_updates, int batch, double lr, double* loss_out) {
+  return mlp_train_any(n, x_dev, t_dev, n_samples, order_dev, n_updates, batch, lr, loss_out, false);
+}
+
+fem_status fem_mlp_train_residual(fem_mlp* n, const float* x_dev, const float* s_dev, int64_t n_samples,
+                                  const int32_t* order_dev, int n_updates, int batch, double lr, double* loss_out) {
+  return mlp_train_any(n, x_dev, s_dev, n_samples, order_dev, n_updates, batch, lr, loss_out, true);
 }
 
 }  // extern "C"

@@ -31,8 +31,9 @@ EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_
            "fem_batch_sync", "fem_step_async", "fem_batch_profile",
            "fem_case_stats", "fem_batch_steps", "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_get_params",
            "fem_mlp_forward", "fem_mlp_loss_grad", "fem_mlp_train", "fem_batch_set_mlp", "fem_batch_collect",
-           "fem_batch_collected", "fem_batch_proposal_counts", "fem_last_error")
-FEM_MLP_N_PARAMS, FEM_MLP_IN, FEM_MLP_OUT = 90656, 64, 32
+           "fem_batch_collected", "fem_batch_proposal_counts", "fem_last_error", "fem_mlp_loss_grad_residual",
+           "fem_mlp_train_residual", "fem_batch_collect_residual")
+FEM_MLP_N_PARAMS, FEM_MLP_IN, FEM_MLP_OUT, FEM_MLP_RES = 90656, 64, 32, 560
 
 
 class FemError(RuntimeError):
@@ -124,6 +125,9 @@ def lib():
         "fem_mlp_train": (I, [P, P, P, I64, P, I, I, D, P]),
         "fem_batch_set_mlp": (I, [P, P]),
         "fem_batch_collect": (I, [P, P, P, I64]),
+        "fem_batch_collect_residual": (I, [P, P, P, I64]),
+        "fem_mlp_loss_grad_residual": (I, [P, P, P, I64, P, ctypes.POINTER(D)]),
+        "fem_mlp_train_residual": (I, [P, P, P, I64, P, I, I, D, P]),
         "fem_batch_collected": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I)]),
         "fem_batch_proposal_counts": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
         "fem_last_error": (ctypes.c_char_p, []),
@@ -449,6 +453,37 @@ def fem_mlp_train(h, x, t, order, lr=1e-3, with_loss=True):
                                _ptr(order, torch.int32), n_up, batch, lr,
                                _np_ptr(losses) if with_loss else None))
     return losses
+
+
+def fem_mlp_loss_grad_residual(h, x, s, grad=None):
+    """Residual-space loss (s: CUDA tensor [B][FEM_MLP_RES]) and, optionally, its gradient into grad."""
+    import torch
+    loss = ctypes.c_double()
+    _check(lib().fem_mlp_loss_grad_residual(h, _ptr(x, torch.float32), _ptr(s, torch.float32), x.shape[0],
+                                            _ptr(grad, torch.float32), ctypes.byref(loss)))
+    return loss.value
+
+
+def fem_mlp_train_residual(h, x, s, order, lr=1e-3, with_loss=True):
+    """Adam on the residual-space loss; order: int32 CUDA tensor [n_updates][batch].  Returns the losses."""
+    import numpy as np
+    import torch
+    n_up, batch = order.shape
+    losses = np.zeros(n_up) if with_loss else None
+    _check(lib().fem_mlp_train_residual(h, _ptr(x, torch.float32), _ptr(s, torch.float32), x.shape[0],
+                                        _ptr(order, torch.int32), n_up, batch, lr,
+                                        _np_ptr(losses) if with_loss else None))
+    return losses
+
+
+def fem_batch_collect_residual(batch, x, s):
+    """Collect residual-space samples into CUDA tensors x [cap][64], s [cap][FEM_MLP_RES] (x = None stops)."""
+    import torch
+    if x is None:
+        _check(lib().fem_batch_collect_residual(batch, None, None, 0))
+        return
+    assert x.shape[1] == FEM_MLP_IN and s.shape[1] == FEM_MLP_RES and x.shape[0] == s.shape[0]
+    _check(lib().fem_batch_collect_residual(batch, _ptr(x, torch.float32), _ptr(s, torch.float32), x.shape[0]))
 
 
 def fem_batch_set_mlp(batch, net):

@@ -124,6 +124,134 @@ def test_training_follows_oracle(torch_dev):
         fem.fem_mlp_destroy(net)
 
 
+def _random_residual_samples(rng, B):
+    S = np.zeros((B, mo.N_RES))
+    for b in range(B):
+        n = int(rng.integers(1, 33))
+        W = np.zeros((32, 32))
+        W[:n, :n] = np.triu(rng.normal(0, 1, (n, n)))
+        w = np.zeros(32)
+        w[:n] = rng.normal(0, 1, n)
+        S[b] = mo.pack_residual(W, w)
+    return S.astype(np.float32)
+
+
+def test_residual_gradient_matches_oracle(torch_dev):
+    """Residual-space loss ||W d - w||^2 (L6) and its gradient: GPU against the FP64 oracle at the
+    BF16-rounded parameters and inputs."""
+    torch = torch_dev
+    rng = np.random.default_rng(31)
+    th = (wl.mlp_init_weights(6) * 0.7).astype(np.float32)
+    th[16384:16640] = rng.normal(0, 0.1, 256)
+    B = 193
+    X = _inputs(rng, B)
+    S = _random_residual_samples(rng, B)
+    net = fem.fem_mlp_create(th)
+    try:
+        g = torch.empty(fem.FEM_MLP_N_PARAMS, device="cuda", dtype=torch.float32)
+        loss = fem.fem_mlp_loss_grad_residual(net, torch.tensor(X, device="cuda"), torch.tensor(S, device="cuda"), g)
+        L_ref, g_ref = mo.loss_and_grad_residual(rounded_params(th), bf16_round(X), S.astype(np.float64))
+        assert abs(loss - L_ref) <= 1e-2 * L_ref, (loss, L_ref)
+        gg = g.cpu().numpy().astype(np.float64)
+        off = 0
+        for shape in mo.param_shapes():
+            k = int(np.prod(shape))
+            a, b = gg[off:off + k], g_ref[off:off + k]
+            cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+            assert cos > 0.999 and rel < 2e-2, (shape, cos, rel)
+            off += k
+        # training on the residual-space loss follows the oracle's Adam on the same minibatches
+        batches = [rng.choice(B, 64, replace=False) for _ in range(20)]
+        th0 = wl.mlp_init_weights(0)
+        _, losses_ref = mo.train_residual(th0.copy(), X.astype(np.float64), S.astype(np.float64), batches)
+        net2 = fem.fem_mlp_create(th0.astype(np.float32))
+        try:
+            order = torch.tensor(np.stack(batches).astype(np.int32), device="cuda")
+            losses = fem.fem_mlp_train_residual(net2, torch.tensor(X, device="cuda"), torch.tensor(S, device="cuda"),
+                                                order)
+            assert np.all(np.abs(losses - losses_ref) <= 5e-2 * np.asarray(losses_ref)), (losses[-3:], losses_ref[-3:])
+        finally:
+            fem.fem_mlp_destroy(net2)
+    finally:
+        fem.fem_mlp_destroy(net)
+
+
+def test_residual_sample_collection_matches_oracle(torch_dev):
+    """Residual-space samples collected by fem_step against the oracle's (W, w) built by MGS from the GPU's
+    own history and the GPU's own predictor coefficients: for the zero correction and random corrections d
+    the two give the same relative residual ||W d - w||^2 (which equals ||Y (c + d) - e||^2 / ||e||^2 minus the
+    least-squares floor); W and w element by element where Y is well-conditioned."""
+    torch = torch_dev
+    m = small_mesh(6, 5, 4, h=1.0 / 64)
+    tp = wl.config2_time_params()
+    sysm, _ = oracle.build_system(m, tp)
+    N = m.n_nodes
+    regions = wl.region_map(m, 48)
+    R = int(regions.max()) + 1
+    reg_dof = np.repeat(regions, 3)[sysm.free]
+    srcs = [wl.random_source(m, wl.rng_for(91, 0, c, 2)) for c in range(2)]
+    s_max = 6
+    opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=s_max, tol=1e-10)
+    h = fem.fem_mesh_create(m, tp)
+    fem.fem_mesh_set_regions(h, regions)
+    bt = fem.fem_batch_create(opts)
+    n_steps = 16
+    cap = n_steps * R * 2
+    xs = torch.zeros((cap, 64), device="cuda")
+    ss = torch.zeros((cap, fem.FEM_MLP_RES), device="cuda")
+    rng = np.random.default_rng(5)
+    try:
+        for s in srcs:
+            fem.fem_case_add(bt, h, s)
+        fem.fem_batch_collect_residual(bt, xs, ss)
+        st = [dict(u=np.zeros(3 * N), vh=[np.zeros(3 * N)] * 4, E=[]) for _ in srcs]
+        expect = []
+        for it in range(1, n_steps + 1):
+            fem.fem_step(bt, 1, 2)
+            for c in range(2):
+                S_ = st[c]
+                u = fem.fem_case_get(bt, c, fem.FEM_FIELD_U, N)
+                v = fem.fem_case_get(bt, c, fem.FEM_FIELD_V, N)
+                u_ab = oracle.adams_bashforth4(S_["u"], S_["vh"], tp.dt)
+                e_new = (u - u_ab)[sysm.free]
+                coef, n = fem.predictor_coefficients(bt, c, R, s_max)
+                if n > 0:
+                    Y = np.stack(S_["E"][-n:], axis=1)
+                    for r in range(R):
+                        idx = reg_dof == r
+                        W_ref, w_ref = mo.residual_sample(Y[idx], e_new[idx], coef[r, :n])
+                        sy = np.linalg.svd(Y[idx], compute_uv=False)
+                        expect.append((it, r, c, W_ref, w_ref, sy[0] / max(sy[-1], 1e-300)))
+                S_["E"].append(e_new)
+                if len(S_["E"]) > s_max + 1:
+                    S_["E"].pop(0)
+                S_["vh"] = S_["vh"][1:] + [v.copy()]
+                S_["u"] = u
+        rows, full = fem.fem_batch_collected(bt)
+        assert not full and rows == len(expect)
+        gs = ss[:rows].cpu().numpy().astype(np.float64)
+        Wg, wg = mo.unpack_residual(gs)
+        expect.sort(key=lambda e: (e[0], e[1], e[2]))
+        elementwise = 0
+        for k, (it, r, c, W_ref, w_ref, cy) in enumerate(expect):
+            scale = max(np.abs(W_ref).max(), np.abs(w_ref).max(), 1e-300)
+            for trial in range(4):
+                d = np.zeros(32) if trial == 0 else rng.normal(0, 1, 32) / max(np.abs(W_ref).max(), 1e-300)
+                lg = np.sum((Wg[k] @ d - wg[k]) ** 2)
+                lr = np.sum((W_ref @ d - w_ref) ** 2)
+                tol = (1e-5 + 10 * cy ** 2 * 2.0 ** -46) * max(lr, np.sum(w_ref ** 2)) + 1e-12 * scale ** 2
+                assert abs(lg - lr) <= tol, (it, r, c, trial, lg, lr)
+            if cy < 1e3:
+                assert np.abs(Wg[k] - W_ref).max() <= 1e-5 * scale, (it, r, c)
+                assert np.abs(wg[k] - w_ref).max() <= 1e-5 * scale, (it, r, c)
+                elementwise += 1
+        assert elementwise > 0
+    finally:
+        fem.fem_batch_destroy(bt)
+        fem.fem_mesh_destroy(h)
+
+
 def _oracle_reduce(v, free):
     return v[free]
 

@@ -157,3 +157,117 @@ def test_step_samples_small_case():
         cs = c + mo.from_age_order(T[r], n)
         assert np.linalg.norm(Y[idx] @ cs - e[idx]) <= np.linalg.norm(Y[idx] @ c - e[idx]) * (1 + 1e-9) + 1e-300
         assert np.allclose(X[r, :3], (m.xyz[src.node] - cents[r]) / L)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Residual-space loss (L6)
+# ---------------------------------------------------------------------------------------------------------
+
+def _explicit_rel_residual(Y, e, c, d_age):
+    """||Y (c + d) - e||^2 / ||e||^2 with d given in age order, written out directly from the vectors."""
+    n = Y.shape[1]
+    d_slot = np.array([d_age[n - 1 - a] for a in range(n)])
+    return float(np.sum((Y @ (c + d_slot) - e) ** 2) / np.sum(e ** 2))
+
+
+def _lstsq_floor(Y, e):
+    """min_c ||Y c - e||^2 / ||e||^2 by an SVD least-squares solve (independent of MGS)."""
+    c, *_ = np.linalg.lstsq(Y, e, rcond=None)
+    return float(np.sum((Y @ c - e) ** 2) / np.sum(e ** 2))
+
+
+@pytest.mark.parametrize("rank_deficient", [False, True])
+def test_residual_sample_reproduces_the_relative_residual(rank_deficient):
+    """||W d - w||^2 plus the least-squares floor equals the relative residual ||Y (c + d) - e||^2 / ||e||^2
+    of the proposed correction, for any d; also with a column of Y repeated (the drop rule removes it)."""
+    rng = np.random.default_rng(11)
+    n, rows = 7, 60
+    Y = rng.normal(0, 1, (rows, n)) * np.logspace(0, -3, n)
+    if rank_deficient:
+        Y[:, 4] = Y[:, 1]
+    e = Y @ rng.normal(0, 1, n) + 0.05 * rng.normal(0, 1, rows)
+    c = rng.normal(0, 1, n)
+    W, w = mo.residual_sample(Y, e, c)
+    assert np.allclose(W, np.triu(W)) and np.all(np.diag(W)[:n] >= 0.0)
+    assert np.all(W[n:, :] == 0.0) and np.all(W[:, n:] == 0.0) and np.all(w[n:] == 0.0)
+    floor = _lstsq_floor(Y, e)
+    for trial in range(5):
+        d = rng.normal(0, 1, 32) * (0.0 if trial == 0 else 1.0)
+        lhs = float(np.sum((W @ d - w) ** 2)) + floor
+        rhs = _explicit_rel_residual(Y, e, c, d)
+        assert abs(lhs - rhs) <= 1e-10 * rhs, (trial, lhs, rhs)
+    # the least-squares coefficients make the residual-space term vanish
+    cs = mo.best_coefficients(Y, e)
+    d_opt = mo.to_age_order(cs - c)
+    assert np.sum((W @ d_opt - w) ** 2) <= 1e-20 + 1e-12 * np.sum(w ** 2)
+
+
+def test_residual_packing_round_trip():
+    rng = np.random.default_rng(12)
+    W = np.triu(rng.normal(0, 1, (32, 32)))
+    w = rng.normal(0, 1, 32)
+    S = mo.pack_residual(W, w)
+    assert S.shape == (mo.N_RES,) and mo.N_RES == 528 + 32
+    W2, w2 = mo.unpack_residual(S)
+    assert np.array_equal(W2[0], W) and np.array_equal(w2[0], w)
+
+
+def test_residual_loss_gradient_matches_central_differences():
+    rng = np.random.default_rng(13)
+    th = wl.mlp_init_weights(4) * 0.5
+    th[-32:] = rng.normal(0, 0.1, 32)
+    X = rng.normal(0, 1, (16, 64))
+    X[:, 36:] = 0.0
+    S = np.stack([mo.pack_residual(np.triu(rng.normal(0, 1, (32, 32))), rng.normal(0, 1, 32)) for _ in range(16)])
+    L, g = mo.loss_and_grad_residual(th, X, S)
+    assert abs(L - mo.loss_residual(th, X, S)) <= 1e-14 * L
+    idx = np.concatenate([rng.choice(mo.n_params(), 200, replace=False), [0, 16384, 90655, 90655 - 32]])
+    for i in idx:
+        h = 1e-5 * max(1.0, abs(th[i]))
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (mo.loss_residual(tp, X, S) - mo.loss_residual(tm, X, S)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g[i]), 1e-3 * np.abs(g).max()), (i, fd, g[i])
+
+
+def test_residual_loss_identity_weights_is_the_squared_error():
+    """With W = I and w = t the L6 loss is the sum over the 32 outputs of (d - t)^2, i.e. 32 x the MSE."""
+    rng = np.random.default_rng(14)
+    th = wl.mlp_init_weights(5)
+    X = rng.normal(0, 1, (8, 64))
+    T = rng.normal(0, 1, (8, 32))
+    S = np.stack([mo.pack_residual(np.eye(32), t) for t in T])
+    L1, g1 = mo.loss_and_grad_residual(th, X, S)
+    L0, g0 = mo.loss_and_grad(th, X, T)
+    assert abs(L1 - 32.0 * L0) <= 1e-12 * L1
+    assert np.abs(g1 - 32.0 * g0).max() <= 1e-12 * np.abs(g1).max()
+
+
+def test_residual_step_samples_small_case():
+    """Residual-space samples of a developed oracle step: a zero network's loss is the relative error of the
+    predictor's own guess above the least-squares floor, region by region."""
+    m = small_mesh(6, 5, 4)
+    tp = wl.config2_time_params()
+    sysm, A = oracle.build_system(m, tp)
+    Binv = oracle.block_jacobi_inverse(A, sysm.free)
+    reg = wl.region_map(m, 64)
+    src = wl.random_source(m, wl.rng_for(9, 0, 0, 2))
+    sim = oracle.CaseSimulator(sysm, A, Binv, src, predictor="dd", s_max=8, region_of_node=reg)
+    R = sim.n_regions
+    cents = mo.region_centroids(m.xyz, reg, R)
+    L = mo.domain_extent(m.xyz)
+    for _ in range(14):
+        sim.step()
+    X, S = mo.step_samples_residual(sim, m.xyz[src.node], cents, L, src.f0)
+    n = sim.last_npairs
+    assert n == 8 and S.shape == (R, mo.N_RES)
+    Y = np.stack(sim.E_hist[-(n + 1):-1], axis=1)
+    e = sim.E_hist[-1]
+    Wb, wb = mo.unpack_residual(S)
+    for r in range(R):
+        idx = np.nonzero(sim.region_of_dof == r)[0]
+        c = sim.last_W[r, :n]
+        zero = float(np.sum(wb[r] ** 2))
+        rel = _explicit_rel_residual(Y[idx], e[idx], c, np.zeros(32))
+        assert abs(zero + _lstsq_floor(Y[idx], e[idx]) - rel) <= 1e-8 * rel + 1e-14, (r, zero, rel)
