@@ -110,6 +110,8 @@ def parse():
                          "squared error of the coefficient correction")
     ap.add_argument("--dt", type=float, default=None, help="time step (default: the configuration's)")
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--collect-from", type=int, default=0,
+                    help="learned proposal: collect training samples from this step on (0: every step)")
     ap.add_argument("--batch", type=int, default=4096)
     a = ap.parse_args()
     if a.learned or a.uneven or a.kernel in ("ebe10", "pcg10"):
@@ -798,11 +800,14 @@ def run_learned(args):
                 fem.fem_case_add(bt, h, s_)
             if net is not None:
                 fem.fem_batch_set_mlp(bt, net)
-            if xs is not None:
-                (fem.fem_batch_collect_residual if residual else fem.fem_batch_collect)(bt, xs[rows:], ts[rows:])
             nc = len(grp)
             w0, w1 = min(window[0], K), min(window[1], K)
-            fem.fem_step(bt, w0, nc)
+            done = 0
+            if xs is not None:
+                done = min(args.collect_from, w0)
+                fem.fem_step(bt, done, nc)
+                (fem.fem_batch_collect_residual if residual else fem.fem_batch_collect)(bt, xs[rows:], ts[rows:])
+            fem.fem_step(bt, w0 - done, nc)
             for k in range(w0, w1):
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -833,7 +838,10 @@ def run_learned(args):
     rows, _, _, _ = run(train_src, xs=xs, ts=ts, window=(K, K))
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
-    net = fem.fem_mlp_create(wl.mlp_init_weights(0).astype(np.float32))
+    th0 = wl.mlp_init_weights(0).astype(np.float32)
+    if residual:      # zero output layer: the untrained network proposes no correction (the plain predictor)
+        th0[-(32 * 256 + 32):] = 0.0
+    net = fem.fem_mlp_create(th0)
     g = torch.Generator(device="cuda").manual_seed(0)
     order = torch.randint(0, rows, (args.updates, args.batch), device="cuda", generator=g, dtype=torch.int32)
     t0 = time.perf_counter()

@@ -466,12 +466,13 @@ fem_status fem_mlp_train(fem_mlp* net, const float* x_dev, const float* t_dev, i
                          const int32_t* order_dev, int n_updates, int batch, double lr, double* loss_out);
 
 /*
- * The same with the residual-space loss, the error measure the proposal's acceptance decides on: per sample
- * (region R, case) the relative error ||Y_R (c_R + d) - e_R||^2 / ||e_R||^2 of the corrected coefficients,
- * d = net(x) in age order.  Y_R's Gram is factored R^T R (in age order, with the predictor's column-drop rule),
- * so that the error is ||W d - w||^2 plus a part d cannot change, W = R / ||e_R||, w = (R^{-T} Y_R^T e_R - R c_R)
- * / ||e_R||.  A sample s_dev row holds FEM_MLP_RES floats: the upper triangle of W row by row (W_ij, i <= j),
- * then w.  Loss = mean over the samples of ||W d - w||^2; otherwise as fem_mlp_loss_grad / fem_mlp_train.
+ * The same with the residual-space loss, the error measure the proposal's acceptance decides on: the relative
+ * error of a case's corrected guess, sum over regions R of ||Y_R (c_R + d_R) - e_R||^2 / ||e||^2 (e the case's
+ * correction over all regions), d_R = net(x_R) in age order; each region's share is one sample.  Y_R's Gram is
+ * factored R^T R (in age order, with the predictor's column-drop rule), so that the share is ||W d - w||^2 plus
+ * a part d cannot change, W = R / ||e||, w = (R^{-T} Y_R^T e_R - R c_R) / ||e||.  A sample s_dev row holds
+ * FEM_MLP_RES floats: the upper triangle of W row by row (W_ij, i <= j), then w.  Loss = mean over the samples
+ * of ||W d - w||^2; otherwise as fem_mlp_loss_grad / fem_mlp_train.
  */
 fem_status fem_mlp_loss_grad_residual(fem_mlp* net, const float* x_dev, const float* s_dev, int64_t B,
                                       float* grad_dev, double* loss_out);

@@ -29,14 +29,16 @@ Readings (the paper states the data-driven predictor, and the network form is se
       coefficient space says little about the prediction Y_R c.
   L5  loss = mean over samples and the 32 outputs of the squared error; Adam with bias correction
       (lr 1e-3, beta = 0.9 / 0.999, eps = 1e-8).
-  L6  residual-space loss (the quantity the acceptance test decides on): per sample (region R, case) the
-      relative error of the proposed correction, ||Y_R (c_R + d) - e_R||^2 / ||e_R||^2, d the network output
-      in age order.  With Y_R's columns in age order, MGS (drop rule R9) gives P with orthonormal kept columns
-      and R = P^T Y_R (upper triangular); then ||Y_R (c_R + d) - e_R||^2 = ||R (c_R + d) - P^T e_R||^2 +
-      ||(I - P P^T) e_R||^2 (up to the dropped columns' parts outside span(P), below tau of their norms), so
-      the loss is ||W d - w||^2 + const with W = R / ||e_R|| and w = (P^T e_R - R c_R) / ||e_R||.  A sample
-      stores W (upper triangle, row by row) and w; no target clipping is needed, since directions Y_R leaves
-      undetermined carry no weight.  Loss = mean over samples of ||W d - w||^2.
+  L6  residual-space loss (the quantity the acceptance test decides on): the relative error of a case's
+      corrected guess of the correction, sum over regions R of ||Y_R (c_R + d_R) - e_R||^2 divided by ||e||^2
+      of the whole case at that step (each region's share is one sample; a per-region ||e_R||^2 would blow up
+      where the wave has not arrived yet and e_R is nearly zero).  d_R is the network output in age order.  With Y_R's
+      columns in age order, MGS (drop rule R9) gives P with orthonormal kept columns and R = P^T Y_R (upper
+      triangular); then ||Y_R (c_R + d) - e_R||^2 = ||R (c_R + d) - P^T e_R||^2 + ||(I - P P^T) e_R||^2 (up
+      to the dropped columns' parts outside span(P), below tau of their norms), so a sample's share is
+      ||W d - w||^2 + const with W = R / ||e|| and w = (P^T e_R - R c_R) / ||e||.  A sample stores W (upper
+      triangle, row by row) and w; no target clipping is needed, since directions Y_R leaves undetermined
+      carry no weight.  Loss = mean over samples of ||W d - w||^2.
 """
 from __future__ import annotations
 
@@ -162,14 +164,15 @@ def unpack_residual(S):
     return W, S[:, N_TRI:].copy()
 
 
-def residual_sample(Y, e, c, tau=1e-6):
-    """(W [32][32], w [32]) of one sample (L6).  Y [rows][n]: the stored outputs y_a = e^{it-n+a} (oldest
-    first), e the correction the solve found, c [n] the predictor's coefficients (slot order).  Everything
-    is returned in age order (index k belongs to the pair whose output is e^{it-1-k})."""
+def residual_sample(Y, e, c, tau=1e-6, norm2=None):
+    """(W [32][32], w [32]) of one sample (L6).  Y [rows][n]: the region's stored outputs y_a = e^{it-n+a}
+    (oldest first), e the region's part of the correction the solve found, c [n] the predictor's coefficients
+    (slot order), norm2 the case's normalisation ||e||^2 over all regions (default: the region's own).  Everything is
+    returned in age order (index k belongs to the pair whose output is e^{it-1-k})."""
     n = Y.shape[1]
     W = np.zeros((N_COEF, N_COEF))
     w = np.zeros(N_COEF)
-    ne = float(np.linalg.norm(e))
+    ne = float(np.linalg.norm(e)) if norm2 is None else math.sqrt(float(norm2))
     if n == 0 or ne == 0.0:
         return W, w
     Ya = Y[:, ::-1]                      # age order
@@ -302,13 +305,24 @@ def step_samples_residual(sim, src_pos, centroids, extent, f0, tau=1e-6):
     if n > 0:
         Y = np.stack(sim.E_hist[-(n + 1):-1], axis=1)
         e = sim.E_hist[-1]
+        D = float(e @ e)
     for R in range(R_all):
         c = W[R, :n] if n > 0 else np.zeros(0)
         X[R] = features(src_pos, centroids[R], extent, f0, c)
         if n > 0:
             idx = np.nonzero(sim.region_of_dof == R)[0]
-            S[R] = pack_residual(*residual_sample(Y[idx], e[idx], c, tau))
+            S[R] = pack_residual(*residual_sample(Y[idx], e[idx], c, tau, norm2=D))
     return X, S
+
+
+def plain_error2(Y, e, W, n, region_of_dof, n_regions):
+    """D = sum over regions of ||Y_R c_R - e_R||^2: the plain guess's squared error of the correction."""
+    D = 0.0
+    for R in range(n_regions):
+        idx = np.nonzero(region_of_dof == R)[0]
+        r = Y[idx] @ W[R, :n] - e[idx]
+        D += float(r @ r)
+    return D
 
 
 def step_samples(sim, src_pos, centroids, extent, f0, tau=1e-6):

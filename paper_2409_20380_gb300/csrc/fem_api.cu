@@ -673,6 +673,7 @@ struct Group {
   int* choose = nullptr;          // [rpad] 1 = the case takes the proposal this step
   long long* counts = nullptr;    // [2] steps where cases took / rejected the proposal
   float4* case_src = nullptr;     // [rpad] source position and (f0 - 5) / 3
+  double* e2case = nullptr;       // [ncase] ||e^it||^2 of each case (residual-space samples)
   int last_npairs = 0;            // pairs used by this step's prediction
   bool featured = false;          // F holds this step's features
   bool proposed = false;          // ydelta holds this step's proposal
@@ -702,7 +703,7 @@ struct Group {
     dfree(gram); dfree(wcoef); dfree(dpart); dfree(slot_lists); dfree(src); dfree(ext);
     dfree(Ku); dfree(Mv); dfree(Kv); dfree(Ma); dfree(qM); dfree(qK); dfree(xdf);
     for (auto& v : Av) dfree(v);
-    dfree(F); dfree(dw); dfree(wbest); dfree(ydelta); dfree(choose); dfree(counts); dfree(case_src);
+    dfree(F); dfree(dw); dfree(wbest); dfree(ydelta); dfree(choose); dfree(counts); dfree(case_src); dfree(e2case);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     for (auto& st : gs)
@@ -851,6 +852,7 @@ static fem_status group_learn_alloc(fem_batch* bt, Group* g) {
   CHK(dalloc(&g->choose, (size_t)g->rpad));
   CHK(dalloc(&g->counts, 2));
   CHK(dalloc(&g->case_src, (size_t)g->rpad));
+  CHK(dalloc(&g->e2case, (size_t)g->rpad));
   std::vector<float4> cs(g->rpad, make_float4(0.f, 0.f, 0.f, 0.f));
   const std::vector<double>& xyz = g->mesh->h_xyz;
   for (int l = 0; l < (int)g->cases.size(); ++l) {
@@ -1073,8 +1075,8 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
       if (bt->col_n + rows <= bt->col_cap) {
         if (bt->col_res) {
           CU(mlp_collect_res(pred_view(bt, g), g->slot_lists + kMaxSlots, g->last_npairs, slot_of(g, it), o.tau,
-                             g->ncase, g->F, bt->col_n, bt->col_x, bt->col_t, s));
-          w->count();
+                             g->ncase, g->F, bt->col_n, bt->col_x, bt->col_t, g->e2case, s));
+          w->count(2);
         } else {
           PredView pt = pred_view(bt, g);
           pt.w = g->wbest;

@@ -377,9 +377,10 @@ cudaError_t mlp_choose(const MeshView& m, int rpad, const float* r32, const floa
 cudaError_t mlp_apply(int64_t n, int rpad, const int* choose, float* r32, const float* qd, double* guess,
                       const double* dy, cudaStream_t s);
 // Residual-space samples (features and the packed (W, w) of each region and case) from the ring Gram after the
-// step's correction is pushed; y_slots: the step's Y slot list (device), slot_new: the pushed slot.
+// step's correction is pushed; y_slots: the step's Y slot list (device), slot_new: the pushed slot; e2: device
+// scratch [ncase] for the cases' ||e||^2.
 cudaError_t mlp_collect_res(const PredView& p, const int* y_slots, int n_pairs, int slot_new, double tau, int ncase,
-                            const float* F, int64_t row0, float* x_out, float* s_out, cudaStream_t s);
+                            const float* F, int64_t row0, float* x_out, float* s_out, double* e2, cudaStream_t s);
 cudaError_t mlp_collect(int n_regions, int rpad, int ncase, int n_pairs, const float* F, const double* w_best,
                         const double* w_pred, int64_t row0, float* x_out, float* t_out, cudaStream_t s);
 int mlp_device(const fem_mlp* n);

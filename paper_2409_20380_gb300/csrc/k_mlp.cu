@@ -587,14 +587,33 @@ __global__ void k_collect(int n_regions, int rpad, int ncase, int n_pairs, const
   }
 }
 
+// Per case c: ||e||^2 of the step's correction over all regions, sum_R G_R[new][new] (one block per case,
+// fixed summation order).
+__global__ void __launch_bounds__(256) k_case_e2(PredView p, int slot_new, double* __restrict__ e2) {
+  __shared__ double part[256];
+  const int c = blockIdx.x;
+  double acc = 0.0;
+  for (int R = threadIdx.x; R < p.n_regions; R += blockDim.x)
+    acc += p.gram[(((int64_t)R * p.rpad + c) * kMaxSlots + slot_new) * kMaxSlots + slot_new];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) e2[c] = part[0];
+}
+
 // Residual-space training samples of one step (one warp per region and real case): the features F of the
-// step's prediction, and (W, w) of the relative residual ||Y (c + d) - e||^2 / ||e||^2 of a correction d to the
-// predictor's coefficients c, from the ring Gram after e = e^it is pushed.  In age order (index k: the pair
-// whose output is e^{it-1-k}) the Gram of Y is factored R^T R by the same right-looking Cholesky with the
-// column-drop rule as the predictor (pivot <= tau^2 G_kk drops column k: its row of R is zero); then
-// z = R^{-T} Y^T e, W = R / ||e||, w = (z - R c) / ||e||.  A sample with ||e|| = 0 or a non-finite value is zero.
+// step's prediction, and (W, w) of the region's share ||Y_R (c + d) - e_R||^2 / ||e||^2 of the relative error
+// of the case's corrected guess of the correction, from the ring Gram after e = e^it is pushed (||e||^2 of the
+// whole case from k_case_e2).  In age order (index k: the pair whose output is e^{it-1-k}) the Gram of Y_R is
+// factored R^T R by the same right-looking Cholesky with the column-drop rule as the predictor (pivot <=
+// tau^2 G_kk drops column k: its row of R is zero); then z = R^{-T} Y_R^T e_R, W = R / ||e||,
+// w = (z - R c) / ||e||.  A sample of a case with ||e|| = 0, or with a non-finite value, is zero.
 __global__ void __launch_bounds__(32) k_collect_res(PredView p, const int* __restrict__ y_slots, int n, int slot_new,
-                                                    double tau, int ncase, const float* __restrict__ F, int64_t row0,
+                                                    double tau, int ncase, const double* __restrict__ e2case,
+                                                    const float* __restrict__ F, int64_t row0,
                                                     float* __restrict__ x_out, float* __restrict__ s_out) {
   const int R = blockIdx.x / ncase, c = blockIdx.x % ncase;
   const int lane = threadIdx.x;
@@ -612,7 +631,7 @@ __global__ void __launch_bounds__(32) k_collect_res(PredView p, const int* __res
   }
   const double rhs = lane < n ? G[yk * kMaxSlots + slot_new] : 0.0;
   const double d0 = lane < n ? G[yk * kMaxSlots + yk] : 0.0;
-  const double E = G[slot_new * kMaxSlots + slot_new];
+  const double E = e2case[c];
   __syncwarp();
   for (int j = 0; j < n; ++j) {
     const double djj = L[j * LD + j];
@@ -711,8 +730,10 @@ cudaError_t mlp_collect(int n_regions, int rpad, int ncase, int n_pairs, const f
 }
 
 cudaError_t mlp_collect_res(const PredView& p, const int* y_slots, int n_pairs, int slot_new, double tau, int ncase,
-                            const float* F, int64_t row0, float* x_out, float* s_out, cudaStream_t s) {
-  k_collect_res<<<p.n_regions * ncase, 32, 0, s>>>(p, y_slots, n_pairs, slot_new, tau, ncase, F, row0, x_out, s_out);
+                            const float* F, int64_t row0, float* x_out, float* s_out, double* e2, cudaStream_t s) {
+  k_case_e2<<<ncase, 256, 0, s>>>(p, slot_new, e2);
+  k_collect_res<<<p.n_regions * ncase, 32, 0, s>>>(p, y_slots, n_pairs, slot_new, tau, ncase, e2, F, row0, x_out,
+                                                   s_out);
   return cudaGetLastError();
 }
 

@@ -180,8 +180,8 @@ def test_residual_gradient_matches_oracle(torch_dev):
 def test_residual_sample_collection_matches_oracle(torch_dev):
     """Residual-space samples collected by fem_step against the oracle's (W, w) built by MGS from the GPU's
     own history and the GPU's own predictor coefficients: for the zero correction and random corrections d
-    the two give the same relative residual ||W d - w||^2 (which equals ||Y (c + d) - e||^2 / ||e||^2 minus the
-    least-squares floor); W and w element by element where Y is well-conditioned."""
+    the two give the same share ||W d - w||^2 of the case's relative error (||Y_R (c + d) - e_R||^2 / ||e||^2
+    minus the least-squares floor); W and w element by element where Y is well-conditioned."""
     torch = torch_dev
     m = small_mesh(6, 5, 4, h=1.0 / 64)
     tp = wl.config2_time_params()
@@ -218,9 +218,10 @@ def test_residual_sample_collection_matches_oracle(torch_dev):
                 coef, n = fem.predictor_coefficients(bt, c, R, s_max)
                 if n > 0:
                     Y = np.stack(S_["E"][-n:], axis=1)
+                    D = float(e_new @ e_new)
                     for r in range(R):
                         idx = reg_dof == r
-                        W_ref, w_ref = mo.residual_sample(Y[idx], e_new[idx], coef[r, :n])
+                        W_ref, w_ref = mo.residual_sample(Y[idx], e_new[idx], coef[r, :n], norm2=D)
                         sy = np.linalg.svd(Y[idx], compute_uv=False)
                         expect.append((it, r, c, W_ref, w_ref, sy[0] / max(sy[-1], 1e-300)))
                 S_["E"].append(e_new)
@@ -386,9 +387,31 @@ def test_zero_network_reproduces_plain_predictor(torch_dev):
         fem.fem_mlp_destroy(net)
 
 
+def _run_cases_res(mesh, tp, regions, srcs, n_steps, xs, ss, s_max=8):
+    """Plain data-driven steps that collect residual-space samples; returns the rows collected."""
+    opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=s_max, tol=1e-8)
+    h = fem.fem_mesh_create(mesh, tp)
+    fem.fem_mesh_set_regions(h, regions)
+    bt = fem.fem_batch_create(opts)
+    try:
+        for s in srcs:
+            fem.fem_case_add(bt, h, s)
+        fem.fem_batch_collect_residual(bt, xs, ss)
+        st, _, rr = fem.fem_step(bt, n_steps, len(srcs))
+        assert st == fem.FEM_OK and np.all(rr < 1e-8)
+        return fem.fem_batch_collected(bt)[0]
+    finally:
+        fem.fem_batch_destroy(bt)
+        fem.fem_mesh_destroy(h)
+
+
 def test_learned_proposal_gain_on_held_out_cases(torch_dev):
-    """Train on samples the method generates for training cases, evaluate on held-out cases: certified
-    steps, the initial residual never above the plain predictor's, and the gain reported."""
+    """Train on the residual-space loss with samples the method generates for training cases, evaluate on
+    held-out cases.  Stated gain: on the held-out cases' samples the trained network at least halves the
+    relative error of the guessed correction, sum_R ||Y_R (c_R + d_R) - e_R||^2 / ||e||^2 (above the
+    least-squares floors), against the plain predictor (d = 0).  In the time step: every step certified, the
+    proposal taken only where it lowers the initial residual, CG iterations not above the plain predictor's
+    (2% and a few iterations of slack: the two runs' histories differ at the certified-tolerance level)."""
     torch = torch_dev
     m = wl.config2_mesh(16, 16, 8)
     tp = wl.config2_time_params()
@@ -396,27 +419,33 @@ def test_learned_proposal_gain_on_held_out_cases(torch_dev):
     R = int(regions.max()) + 1
     train_src, held_src = wl.config5_sources(m, 16, 8)
     n_steps = 90
-    cap = n_steps * R * 16
-    xs = torch.zeros((cap, 64), device="cuda")
-    ts = torch.zeros((cap, 32), device="cuda")
-    _, _, _, rows = _run_cases(m, tp, regions, train_src, n_steps, collect=(xs, ts))
+    xs = torch.zeros((n_steps * R * 16, 64), device="cuda")
+    ss = torch.zeros((n_steps * R * 16, fem.FEM_MLP_RES), device="cuda")
+    rows = _run_cases_res(m, tp, regions, train_src, n_steps, xs, ss)
     assert rows > 0
-    net = fem.fem_mlp_create(wl.mlp_init_weights(0).astype(np.float32) * 0.1)
+    hx = torch.zeros((n_steps * R * 8, 64), device="cuda")
+    hs = torch.zeros((n_steps * R * 8, fem.FEM_MLP_RES), device="cuda")
+    hrows = _run_cases_res(m, tp, regions, held_src, n_steps, hx, hs)
+    th0 = wl.mlp_init_weights(0).astype(np.float32)
+    th0[-(32 * 256 + 32):] = 0.0                 # zero output layer: starts as the plain predictor
+    net = fem.fem_mlp_create(th0)
     try:
+        base = fem.fem_mlp_loss_grad_residual(net, hx[:hrows], hs[:hrows])
+        assert abs(base - float((hs[:hrows, -32:].double() ** 2).sum(dim=1).mean())) <= 1e-5 * base
         g = torch.Generator(device="cpu").manual_seed(0)
         batch, n_up = 512, 600
         order = torch.stack([torch.randperm(rows, generator=g)[:batch] for _ in range(n_up)]).to(torch.int32).cuda()
-        losses = fem.fem_mlp_train(net, xs[:rows], ts[:rows], order, lr=1e-3)
-        assert np.all(np.isfinite(losses)) and losses[-50:].mean() < losses[:50].mean()
+        losses = fem.fem_mlp_train_residual(net, xs[:rows], ss[:rows], order, lr=1e-3)
+        assert np.all(np.isfinite(losses))
+        held = fem.fem_mlp_loss_grad_residual(net, hx[:hrows], hs[:hrows])
+        print(f"residual-space loss on held-out samples: plain {base:.4e}, learned {held:.4e} "
+              f"(R^2 {1 - held / base:.3f})")
+        assert held <= 0.5 * base, (held, base)
         i_dd, it_dd, _, _ = _run_cases(m, tp, regions, held_src, n_steps)
         i_ml, it_ml, counts, _ = _run_cases(m, tp, regions, held_src, n_steps, net=net)
-        k0 = 20                                  # developed wavefield
-        gain_res = np.exp(np.mean(np.log(i_dd[k0:] + 1e-30)) - np.mean(np.log(i_ml[k0:] + 1e-30)))
-        print(f"learned proposal: taken/rejected {counts}, geometric-mean initial residual gain {gain_res:.3f}, "
-              f"CG iterations {it_dd[k0:].sum():.0f} -> {it_ml[k0:].sum():.0f}")
-        # per step a case keeps the smaller of the two initial residuals; across the two runs the histories
-        # differ at the certified-tolerance level, so the comparison is on the geometric mean
-        assert gain_res >= 0.95
-        assert it_ml[k0:].sum() <= it_dd[k0:].sum() * 1.02 + 8
+        print(f"learned proposal in the step: taken/rejected {counts}, CG iterations {it_dd.sum():.0f} -> "
+              f"{it_ml.sum():.0f}")
+        assert sum(counts) == 8 * (n_steps - 2)
+        assert it_ml.sum() <= it_dd.sum() * 1.02 + 8
     finally:
         fem.fem_mlp_destroy(net)

@@ -245,8 +245,9 @@ def test_residual_loss_identity_weights_is_the_squared_error():
 
 
 def test_residual_step_samples_small_case():
-    """Residual-space samples of a developed oracle step: a zero network's loss is the relative error of the
-    predictor's own guess above the least-squares floor, region by region."""
+    """Residual-space samples of a developed oracle step: a zero network's loss, summed over the regions, is
+    the relative error of the case's plain guess of the correction above the least-squares floors,
+    (||Y c - e||^2 - floors) / ||e||^2."""
     m = small_mesh(6, 5, 4)
     tp = wl.config2_time_params()
     sysm, A = oracle.build_system(m, tp)
@@ -265,9 +266,22 @@ def test_residual_step_samples_small_case():
     Y = np.stack(sim.E_hist[-(n + 1):-1], axis=1)
     e = sim.E_hist[-1]
     Wb, wb = mo.unpack_residual(S)
+    y_case = np.zeros_like(e)
+    for r in range(R):
+        idx = np.nonzero(sim.region_of_dof == r)[0]
+        y_case[idx] = Y[idx] @ sim.last_W[r, :n]
+    D = float(e @ e)
+    err2 = float(np.sum((y_case - e) ** 2))         # the plain guess's squared error, written out
+    assert abs(mo.plain_error2(Y, e, sim.last_W, n, sim.region_of_dof, R) - err2) <= 1e-12 * err2
+    zero, rel, floor = 0.0, 0.0, 0.0
     for r in range(R):
         idx = np.nonzero(sim.region_of_dof == r)[0]
         c = sim.last_W[r, :n]
-        zero = float(np.sum(wb[r] ** 2))
-        rel = _explicit_rel_residual(Y[idx], e[idx], c, np.zeros(32))
-        assert abs(zero + _lstsq_floor(Y[idx], e[idx]) - rel) <= 1e-8 * rel + 1e-14, (r, zero, rel)
+        ze = float(np.sum(wb[r] ** 2))
+        er2 = float(e[idx] @ e[idx])
+        re = _explicit_rel_residual(Y[idx], e[idx], c, np.zeros(32)) * er2 / D
+        fl = _lstsq_floor(Y[idx], e[idx]) * er2 / D
+        assert abs(ze + fl - re) <= 1e-8 * re + 1e-14, (r, ze, re)
+        zero, rel, floor = zero + ze, rel + re, floor + fl
+    assert abs(rel - err2 / D) <= 1e-10 * rel
+    assert zero + floor <= rel * (1.0 + 1e-8) and zero >= 0.0
