@@ -25,6 +25,14 @@ Readings of the paper where it is silent or garbled (each one is listed with its
   R13 ||b|| = 0 gives du = 0 with 0 iterations.
   R14 on exit Algorithm 1's recursive residual is replaced by the true residual; iteration continues
       while that true residual is above the tolerance (up to maxit).
+  R22 absorbing side boundaries (Section 3.1 names them without a form): viscous dashpots of Lysmer and
+      Kuhlemeyer, traction t = -rho (c_p (v.n) n + c_s (v - (v.n) n)) on the boundary faces the caller lists,
+      lumped to the face's corners (a third of the face's area each).  They add the node-block matrix C_b to
+      the damping: C = a0 M + a1 K + C_b.
+  R23 the paper's random inputs (impulses with random amplitudes and uniform spectra, in random directions,
+      at randomly selected surface points): each point receives one force impulse during one time step, a
+      random amplitude times a random unit direction, at a random step (a one-step pulse has a flat spectrum
+      up to the step's Nyquist frequency).
 """
 from __future__ import annotations
 
@@ -130,6 +138,43 @@ def assemble(xyz, conn, mat_id, lam_mu_rho, chunk=200000):
 # --------------------------------------------------------------------------------------------------------
 
 
+def lysmer_dashpots(xyz, conn, mat_id, lam_mu_rho, faces):
+    """R22: the 3N x 3N dashpot matrix C_b (a symmetric 3 x 3 block per node) of the absorbing boundary faces
+    [n][3] (node triples).  Each face must be a face of exactly one element; its outward unit normal n points
+    away from that element's fourth node; with the element's (lambda, mu, rho), c_p = sqrt((lambda + 2 mu) /
+    rho), c_s = sqrt(mu / rho), each of the face's corners gets (area / 3) rho (c_p n n^T + c_s (I - n n^T))."""
+    N = xyz.shape[0]
+    owner = {}
+    for e in range(conn.shape[0]):
+        nd = [int(v) for v in conn[e]]
+        for k in range(4):
+            tri = tuple(sorted(nd[:k] + nd[k + 1:]))
+            owner.setdefault(tri, []).append((e, nd[k]))
+    rows, cols, vals = [], [], []
+    for f in np.asarray(faces):
+        key = tuple(sorted(int(v) for v in f))
+        own = owner.get(key, [])
+        if len(own) != 1:
+            raise ValueError(f"face {key} is not a boundary face of exactly one element")
+        e, opp = own[0]
+        p0, p1, p2 = xyz[key[0]], xyz[key[1]], xyz[key[2]]
+        nrm = np.cross(p1 - p0, p2 - p0)
+        area = 0.5 * np.linalg.norm(nrm)
+        n = nrm / np.linalg.norm(nrm)
+        if n @ (xyz[opp] - p0) > 0.0:
+            n = -n
+        lam, mu, rho = lam_mu_rho[mat_id[e]]
+        cp, cs = math.sqrt((lam + 2.0 * mu) / rho), math.sqrt(mu / rho)
+        blk = area / 3.0 * rho * (cp * np.outer(n, n) + cs * (np.eye(3) - np.outer(n, n)))
+        for node in key:
+            for i in range(3):
+                for j in range(3):
+                    rows.append(3 * node + i)
+                    cols.append(3 * node + j)
+                    vals.append(blk[i, j])
+    return sp.coo_matrix((vals, (rows, cols)), shape=(3 * N, 3 * N)).tocsr()
+
+
 @dataclasses.dataclass
 class System:
     """Assembled operators of one mesh, with Dirichlet DOFs eliminated (reduced system on `free`)."""
@@ -139,10 +184,12 @@ class System:
     dt: float
     a0: float
     a1: float
+    Cb: sp.csr_matrix = None  # R22 dashpots of absorbing boundaries (None: none)
 
     @property
     def C(self):
-        return self.a0 * self.M + self.a1 * self.K                       # R4
+        C = self.a0 * self.M + self.a1 * self.K                          # R4
+        return C + self.Cb if self.Cb is not None else C
 
     @property
     def A_full(self):
@@ -153,11 +200,14 @@ class System:
         return Mat[self.free][:, self.free].tocsr()
 
 
-def build_system(mesh, tp) -> tuple[System, sp.csr_matrix]:
-    """Assemble M, K of a mesh and return (System, reduced A)."""
+def build_system(mesh, tp, absorbing_faces=None) -> tuple[System, sp.csr_matrix]:
+    """Assemble M, K (and the R22 dashpots of the listed boundary faces, if given); return (System, reduced A)."""
     M, K = assemble(mesh.xyz, mesh.conn, mesh.mat_id, mesh.lam_mu_rho)
     free = np.nonzero(mesh.fixed_dof == 0)[0]
-    sysm = System(M=M, K=K, free=free, dt=tp.dt, a0=tp.a0, a1=tp.a1)
+    Cb = None
+    if absorbing_faces is not None:
+        Cb = lysmer_dashpots(mesh.xyz, mesh.conn, mesh.mat_id, mesh.lam_mu_rho, absorbing_faces)
+    sysm = System(M=M, K=K, free=free, dt=tp.dt, a0=tp.a0, a1=tp.a1, Cb=Cb)
     return sysm, sysm.reduce(sysm.A_full)
 
 
@@ -173,6 +223,22 @@ def point_force(n_dof, src, t):
     w = ricker(t, src.f0, src.t0, src.amp)
     f[3 * src.node:3 * src.node + 3] = w * np.asarray(src.direction)
     return f
+
+
+def impulse_force(n_dof, imp, it):
+    """R23: full-length force vector of step `it` of a set of impulses (imp.nodes, imp.steps, imp.forces)."""
+    f = np.zeros(n_dof)
+    for k in np.nonzero(np.asarray(imp.steps) == it)[0]:
+        node = int(imp.nodes[k])
+        f[3 * node:3 * node + 3] += imp.forces[k]
+    return f
+
+
+def case_force(n_dof, src, it, dt):
+    """The load of step `it`: a Ricker point source (R12) at t = it dt, or a set of impulses (R23)."""
+    if hasattr(src, "steps"):
+        return impulse_force(n_dof, src, it)
+    return point_force(n_dof, src, it * dt)
 
 
 def newmark_rhs(sysm: System, f, u, v, a):
@@ -396,7 +462,7 @@ class CaseSimulator:
         self.it += 1
         sysm = self.sysm
         t = self.it * sysm.dt
-        f = point_force(sysm.M.shape[0], self.src, t)
+        f = case_force(sysm.M.shape[0], self.src, self.it, sysm.dt)
         b_full = newmark_rhs(sysm, f, self.u, self.v, self.a)
         b = b_full[sysm.free]
         du_bar, du_ab = self.guess()

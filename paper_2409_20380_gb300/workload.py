@@ -174,6 +174,53 @@ def random_source(mesh: Mesh, rng: np.random.Generator, f0=None, f0_range=(2.0, 
     return Source(node=node, direction=d, f0=float(f0), t0=1.2 / float(f0), amp=1.0)
 
 
+@dataclasses.dataclass
+class Impulses:
+    """Random impulse inputs of one case: at node nodes[k], the force forces[k] during time step steps[k]
+    (steps >= 1), nothing at other steps."""
+    nodes: np.ndarray        # [n] int32
+    steps: np.ndarray        # [n] int32
+    forces: np.ndarray       # [n][3] float64
+
+
+def surface_nodes(mesh: Mesh) -> np.ndarray:
+    """Free nodes of the top face (z = Hz h)."""
+    Hz = mesh.dims[2]
+    q = np.rint(mesh.xyz[:, 2] / mesh.h).astype(np.int64)
+    free = mesh.fixed_dof.reshape(-1, 3).max(axis=1) == 0
+    return np.nonzero((q == Hz) & free)[0]
+
+
+def random_impulses(mesh: Mesh, rng: np.random.Generator, n_points: int, last_step: int) -> Impulses:
+    """Impulses at n_points distinct random surface nodes, each once, at a random step in [1, last_step], with
+    an amplitude ~ N(0, 1) along a random unit direction."""
+    cand = surface_nodes(mesh)
+    nodes = rng.choice(cand, size=min(n_points, cand.size), replace=False).astype(np.int32)
+    n = nodes.size
+    steps = rng.integers(1, last_step + 1, size=n).astype(np.int32)
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    forces = rng.standard_normal(n)[:, None] * d
+    return Impulses(nodes=nodes, steps=steps, forces=forces)
+
+
+def side_faces(mesh: Mesh) -> np.ndarray:
+    """[n][3] int32 node triples of the element faces lying in the four vertical sides of the box (x = 0,
+    x = Lx, y = 0, y = Ly): where the workloads with absorbing sides put them (the bottom is fixed, the top
+    free)."""
+    Hx, Hy, _ = mesh.dims
+    q = np.rint(mesh.xyz / mesh.h).astype(np.int64)
+    out = []
+    for k in range(4):
+        tri = np.delete(mesh.conn, k, axis=1)                       # [E][3] faces opposite corner k
+        qt = q[tri]                                                 # [E][3][3]
+        on = np.zeros(tri.shape[0], dtype=bool)
+        for ax, val in ((0, 0), (0, Hx), (1, 0), (1, Hy)):
+            on |= np.all(qt[:, :, ax] == val, axis=1)
+        out.append(tri[on])
+    return np.ascontiguousarray(np.concatenate(out, axis=0), dtype=np.int32)
+
+
 def region_map(mesh: Mesh, region_nodes: int = 1024) -> np.ndarray:
     """Node -> region id: free nodes in Morton order of their grid position, cut into runs of
     `region_nodes`; nodes whose three DOFs are all fixed get -1 (they carry no unknowns)."""
