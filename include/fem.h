@@ -151,6 +151,21 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
 fem_status fem_mesh_destroy(fem_mesh* m);
 
 /*
+ * Absorbing boundary (the paper applies absorbing boundary conditions to the sides of the domain, Section 3.1;
+ * the form is not given there): viscous dashpots of Lysmer and Kuhlemeyer on the listed boundary faces.  Each
+ * face f of faces [n_faces][3] (host int32 node triples, copied) must be a face of exactly one element; with
+ * its area, the outward unit normal n (away from that element's fourth node) and the element's material,
+ * c_p = sqrt((lambda + 2 mu) / rho), c_s = sqrt(mu / rho), each of its three nodes gets the 3x3 damping block
+ * (area / 3) rho (c_p n n^T + c_s (I - n n^T)).  The blocks form C_b, added to the damping:
+ * C = a0 M + a1 K + C_b, so the system of every later solve and step is A = cM M + cK K + (2/dt) C_b and the
+ * right-hand side gains C_b v (Section 3.1, Eq. GE:DIS); the block-Jacobi preconditioner includes (2/dt) C_b.
+ * The element product entry points (fem_ebe_apply, fem_mesh_split_product) stay without it.  n_faces = 0
+ * removes the dashpots; a new call replaces the previous faces.  Not for meshes of fuse_meshes batches.
+ * Synchronises `stream`.  Errors: FEM_ERR_ARG (a face that is not on exactly one element, bad ids, zero area).
+ */
+fem_status fem_mesh_set_absorbing(fem_mesh* m, int64_t n_faces, const int32_t* faces, void* stream);
+
+/*
  * Selects the EBE product implementation of a mesh (library tuning knob; the paper's EBE is one product,
  * Section 3.2, Eq. eqebefem).  ebe_variant: 0 = automatic, 1 = generic element kernel, 2 = tiled hex-patch
  * kernel (available when the elements come in groups of six tets splitting a hexahedron with the Kuhn
@@ -317,6 +332,17 @@ fem_status fem_batch_destroy(fem_batch* b);
  */
 fem_status fem_case_add(fem_batch* b, fem_mesh* m, int32_t src_node, const double dir[3], double f0,
                         double t0, double amp, int* case_id);
+
+/*
+ * Adds a case on mesh `m` starting at rest, loaded by random impulses (the paper's random inputs: impulse
+ * waveforms of random amplitude and uniform spectrum in random directions at randomly selected surface
+ * points, Section 3.1): impulse k acts during time step steps[k] (>= 1) only, as the force forces[k] [3] at node
+ * nodes[k].  Several impulses may share a node and a step (they add).  Host arrays, copied:
+ * nodes [n], steps [n] int32, forces [n][3] double.  Must be called before the first fem_step; not with
+ * fuse_meshes.  Errors: FEM_ERR_ARG (ids out of range, steps < 1, non-finite forces), FEM_ERR_STATE.
+ */
+fem_status fem_case_add_impulses(fem_batch* b, fem_mesh* m, int64_t n, const int32_t* nodes, const int32_t* steps,
+                                 const double* forces, int* case_id);
 
 /*
  * Advances every case by n_steps time steps.  One step of a case (Section 3.1 and Algorithm 3's

@@ -10,6 +10,9 @@
 
 #include "fem_internal.cuh"
 
+#include <array>
+#include <unordered_map>
+
 using namespace fem;
 
 
@@ -268,11 +271,16 @@ struct fem_mesh {
   } tuned[2][6];
   // host copies of the inputs (used to fuse meshes into one system) and the region map
   std::vector<double> h_xyz, h_lmr;
-  std::vector<int32_t> h_conn, h_mat, h_region;
+  std::vector<int32_t> h_conn, h_mat, h_region, h_ab_faces;
   std::vector<uint8_t> h_fixed;
   // fused meshes: case of each node
   uint8_t* seg = nullptr;
   int nseg = 0;
+  // dashpots of absorbing boundary faces (fem_mesh_set_absorbing)
+  Absorb ab;
+  int32_t* ab_node = nullptr;
+  double* ab_c64 = nullptr;
+  float* ab_c32 = nullptr;
   // Node pattern (host, threads over node ranges) and GPU assembly of the certification operators.
   fem_status ensure_bcsr(cudaStream_t s) {
     if (row_ptr) return FEM_OK;
@@ -372,6 +380,7 @@ struct fem_mesh {
     dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(rec_df); dfree(D);
     dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(KMd); dfree(hexmat);
     dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi); dfree(reg_gap); dfree(seg); dfree(reg_cent);
+    dfree(ab_node); dfree(ab_c64); dfree(ab_c32);
     for (auto* w : ws) delete w;
     for (void* b : tile_bufs) cudaFree(b);
   }
@@ -433,8 +442,8 @@ struct fem_mesh {
 // EBE product q = (aM M + aK K) p on the mesh: the tiled hex kernel when the mesh has hex patches and a
 // tiling fits, else the generic element kernel (q masked on Dirichlet DOFs by the consumers).
 template <typename T>
-static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, double aM, double aK,
-                               const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s) {
+static cudaError_t ebe_elem_product(const fem_mesh* m, int rpad, const T* p, T* q, double aM, double aK,
+                                    const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s) {
   int v, h;
   m->resolve(sizeof(T), rpad, &v, &h);
   if (v == 8) {   // assembled 3x3 blocks (built outside stream capture only); not for fused groups
@@ -475,6 +484,18 @@ static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, do
   return launch_ebe_gated<T>(m->view(), rpad, p, nullptr, q, aM, aK, red, sc, ptq, gate, s);
 }
 
+// A product of the solver: the element-by-element product and, with_ab on a mesh with absorbing faces, the
+// dashpot term cB C_b p of A = cM M + cK K + cB C_b (its p^T q share added to the CG state).
+template <typename T>
+static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, double aM, double aK,
+                               const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s,
+                               bool with_ab = false) {
+  cudaError_t e = ebe_elem_product<T>(m, rpad, p, q, aM, aK, red, sc, ptq, gate, s);
+  if (e == cudaSuccess && with_ab && m->ab.nb > 0)
+    e = launch_dashpot<T>(m->ab, rpad, m->ab.cB, p, q, false, m->fm, red, sc, ptq, gate, s);
+  return e;
+}
+
 // ------------------------------------------------------------------------------------------------------
 // PCG drivers.
 // ------------------------------------------------------------------------------------------------------
@@ -511,7 +532,7 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
     // the guess is zeroed on Dirichlet DOFs (and for b = 0) before its residual is formed
     CU(launch_zero_b0_t<T>(mv, rpad, x, sc, s));
     int pi = w->pbeg(ebe_cls, s);
-    CU(ebe_product<T>(m, rpad, x, q, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
+    CU(ebe_product<T>(m, rpad, x, q, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s, true));
     w->pend(pi, s);
     CU(launch_resid<T>(mv, rpad, b, q, x, r, z, 1, red, sc, w->n_active, tol, maxit, s));
     w->count(3);
@@ -530,7 +551,7 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
       }
       w->pend(p0, s);
       int p1 = w->pbeg(ebe_cls, s);
-      CU(ebe_product<T>(m, rpad, p, q, m->cM, m->cK, &red, sc, nullptr, w->n_active, s));
+      CU(ebe_product<T>(m, rpad, p, q, m->cM, m->cK, &red, sc, nullptr, w->n_active, s, true));
       w->pend(p1, s);
       int p2 = w->pbeg(P_VEC, s);
       if (defer) {
@@ -552,7 +573,7 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
       if (++rechecks > 32) break;
       // Algorithm 1 stops on the recursive residual; confirm with the true one and resume if needed.
       int pi = w->pbeg(ebe_cls, s);
-      CU(ebe_product<T>(m, rpad, x, q, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
+      CU(ebe_product<T>(m, rpad, x, q, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s, true));
       w->pend(pi, s);
       CU(launch_resid<T>(mv, rpad, b, q, x, r, z, 0, red, sc, w->n_active, tol, maxit, s));
       w->count(2);
@@ -578,7 +599,7 @@ static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double
   const int kMaxOuter = 40;
   for (int outer_it = 0; outer_it <= kMaxOuter; ++outer_it) {
     int pi = w->pbeg(P_EBE64, s);
-    CU(ebe_product<double>(m, rpad, x, w->q, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
+    CU(ebe_product<double>(m, rpad, x, w->q, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s, true));
     w->pend(pi, s);
     CU(launch_outer_resid(mv, rpad, b, w->q, w->r32, red, w->outer, w->n_active, o.tol, o.inner_tol, s));
     w->count(2);
@@ -645,6 +666,15 @@ struct Group {
   int rpad = 0;
   std::vector<int> cases;
   std::vector<RickerSrc> hsrc;
+  // random impulse loads per case lane (host, until the batch starts) and their device form
+  struct HostImpulse {
+    int32_t node, step;
+    double f[3];
+  };
+  std::vector<std::vector<HostImpulse>> himp;
+  Impulses imp;
+  int32_t *imp_node = nullptr, *imp_lane = nullptr, *imp_off = nullptr;
+  double* imp_f = nullptr;
   int64_t n = 0;
   double *u = nullptr, *a = nullptr, *vh[4] = {nullptr, nullptr, nullptr, nullptr};
   double *b = nullptr, *x = nullptr, *du_ab = nullptr, *m_in = nullptr, *k_in = nullptr, *guess = nullptr;
@@ -711,6 +741,7 @@ struct Group {
     for (auto& ev : gev)
       if (ev) cudaEventDestroy(ev);
     dfree(ctl); dfree(acc_iters); dfree(acc_relres); dfree(acc_status);
+    dfree(imp_node); dfree(imp_lane); dfree(imp_off); dfree(imp_f);
     if (h_pin) cudaFreeHost(h_pin);
     if (h_slots) cudaFreeHost(h_slots);
     delete ws;
@@ -810,6 +841,39 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
   for (int l = (int)g->cases.size(); l < g->ncase; ++l) g->hsrc[l] = RickerSrc{-1, {0, 0, 0}, 1.0, 0.0, 0.0};
   CHK(dalloc(&g->src, g->ncase));
   CHK(dalloc(&g->ext, 3 * g->ncase));
+  {   // impulse loads: entries sorted by step (counting sort), per step offsets
+    int64_t ni = 0;
+    int last = 0;
+    g->himp.resize(g->ncase);
+    for (const auto& v : g->himp)
+      for (const auto& e : v) ni += 1, last = std::max(last, (int)e.step);
+    if (ni > 0) {
+      if (ni > INT32_MAX / 2) return fail(FEM_ERR_ARG, "too many impulses in one group");
+      std::vector<int32_t> off((size_t)last + 2, 0), nd(ni), ln(ni);
+      std::vector<double> f(3 * ni);
+      for (const auto& v : g->himp)
+        for (const auto& e : v) off[(size_t)e.step + 1] += 1;
+      int mx = 0;
+      for (int k = 1; k <= last + 1; ++k) mx = std::max(mx, off[k]), off[k] += off[k - 1];
+      std::vector<int32_t> pos(off.begin(), off.end());
+      for (int l = 0; l < (int)g->himp.size(); ++l)
+        for (const auto& e : g->himp[l]) {
+          const int32_t k = pos[e.step]++;
+          nd[k] = e.node, ln[k] = l;
+          for (int d = 0; d < 3; ++d) f[3 * (size_t)k + d] = e.f[d];
+        }
+      CHK(dalloc(&g->imp_node, (size_t)ni));
+      CHK(dalloc(&g->imp_lane, (size_t)ni));
+      CHK(dalloc(&g->imp_off, off.size()));
+      CHK(dalloc(&g->imp_f, 3 * (size_t)ni));
+      CU(cudaMemcpyAsync(g->imp_node, nd.data(), sizeof(int32_t) * ni, cudaMemcpyHostToDevice, s));
+      CU(cudaMemcpyAsync(g->imp_lane, ln.data(), sizeof(int32_t) * ni, cudaMemcpyHostToDevice, s));
+      CU(cudaMemcpyAsync(g->imp_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, s));
+      CU(cudaMemcpyAsync(g->imp_f, f.data(), sizeof(double) * 3 * ni, cudaMemcpyHostToDevice, s));
+      CU(cudaStreamSynchronize(s));
+      g->imp = Impulses{(int)ni, last, mx, g->imp_node, g->imp_lane, g->imp_f, g->imp_off};
+    }
+  }
   CU(cudaMemsetAsync(g->ext, 0, sizeof(double) * 3 * g->ncase, s));
   CU(cudaMemcpyAsync(g->src, g->hsrc.data(), sizeof(RickerSrc) * g->ncase, cudaMemcpyHostToDevice, s));
   CHK(ws_create(m->N, g->rpad, &g->ws));
@@ -943,6 +1007,8 @@ static fem_status group_refresh(fem_batch* bt, Group* g) {
     const int sl = ((j % 4) + 4) % 4;
     CU(split_product(m, cm, g->rpad, g->vh[sl], g->xdf, g->qM, g->qK, s));
     CU(launch_axpby(g->n, m->cM, g->qM, m->cK, g->qK, g->Av[sl], s));
+    CU(launch_dashpot<double>(m->ab, g->rpad, m->ab.cB, g->vh[sl], g->Av[sl], false, m->fm, nullptr, nullptr, nullptr,
+                              nullptr, s));
     if (j == it) {
       CU(cudaMemcpyAsync(g->Mv, g->qM, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
       CU(cudaMemcpyAsync(g->Kv, g->qK, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
@@ -977,6 +1043,10 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   ph = w->pbeg(P_RHS, s);
   CU(launch_rhs_incr(mv, g->rpad, dt, m->tp.a0, m->tp.a1, g->Ma, g->Mv, g->Kv, g->Ku, g->b, g->src,
                      g->use_ext ? g->ext : nullptr, it * dt, s));
+  // random impulses of this step, and the dashpots' C_b v of absorbing boundaries
+  CU(launch_impulses(g->imp, g->rpad, it, nullptr, m->fm, g->b, s));
+  CU(launch_dashpot<double>(m->ab, g->rpad, 1.0, vslot(it - 1), g->b, false, m->fm, nullptr, nullptr, nullptr, nullptr,
+                            s));
   g->use_ext = false;
   w->pend(ph, s);
   w->count();
@@ -986,7 +1056,7 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   if (corrected) {
     CU(launch_corr_f32(g->n, g->guess, g->du_ab, w->z32, s));
     int pe = w->pbeg(P_EBE32, s);
-    CU(ebe_product<float>(m, g->rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
+    CU(ebe_product<float>(m, g->rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s, true));
     w->pend(pe, s);
     qy = w->q32;
     w->count(2);
@@ -1002,7 +1072,7 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     // learned proposal: r0' = r0 - A32 (Y dw); a case takes it where its initial residual is smaller
     CU(mlp_to_f32(g->n, g->ydelta, w->z32, s));
     int pe = w->pbeg(P_EBE32, s);
-    CU(ebe_product<float>(m, g->rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
+    CU(ebe_product<float>(m, g->rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s, true));
     w->pend(pe, s);
     CU(mlp_choose(mv, g->rpad, w->r32, w->q32, red, w->outer, w->n_active, o.tol, o.inner_tol, g->ncase, g->choose,
                   g->counts, s));
@@ -1040,6 +1110,9 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     }
     int pe = w->pbeg(P_EBE64, s);
     CU(split_product(m, o.cert_df, g->rpad, g->x, g->xdf, g->qM, g->qK, s));
+    // absorbing boundaries: the certificate's r = b - cM qM - cK qK takes the dashpot term in qK (undone below)
+    CU(launch_dashpot<double>(m->ab, g->rpad, m->ab.cB / m->cK, g->x, g->qK, false, m->fm, nullptr, nullptr, nullptr,
+                              nullptr, s));
     w->pend(pe, s);
     if (mv.seg) {
       CU(launch_cert_seg(mv, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
@@ -1050,6 +1123,8 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     }
     w->count(2);
   }
+  CU(launch_dashpot<double>(m->ab, g->rpad, -m->ab.cB / m->cK, g->x, g->qK, false, m->fm, nullptr, nullptr, nullptr,
+                            nullptr, s));
   w->pend(ph, s);
   CU(cudaMemcpyAsync(w->h_sc, w->outer, sizeof(CgCase) * g->ncase, cudaMemcpyDeviceToHost, s));
   // 5. Newmark update, product recurrences, snapshot push (Section 3.1, Eq. timestep)
@@ -1062,6 +1137,8 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   CU(launch_newmark_incr(g->n, dt, m->cM, m->cK, g->x, g->du_ab, g->qM, g->qK, g->u, vslot(it - 1), g->a, vslot(it),
                          g->Ku, g->Mv, g->Kv, g->Ma, aslot(it), e_push, o.snapshot_format, s, Ring4{}, Ring4{},
                          nullptr, g->snap_stride));
+  CU(launch_dashpot<double>(m->ab, g->rpad, m->ab.cB, vslot(it), aslot(it), false, m->fm, nullptr, nullptr, nullptr,
+                            nullptr, s));
   w->count();
   if (dd) {
     uint64_t mask = 0;
@@ -1161,7 +1238,9 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   StepCtl* ctl = g->ctl;
   const int ce = std::max(1, o.check_every);
   cudaStream_t s = g->gs[0], s2 = g->gs[1], s3 = g->gs[2], s4 = g->gs[3];
-  const long long n_fixed = 6 + (dd ? 5 : 0), n_pass = 4, n_if = sg ? 4 : 2, n_inner = 3LL * ce + 1;
+  const bool ab = m->ab.nb > 0;
+  const long long n_fixed = 6 + (dd ? 5 : 0) + (g->imp.n > 0 ? 1 : 0) + (ab ? 3 + (dd ? 1 : 0) : 0),
+                  n_pass = 4 + (ab ? 1 : 0), n_if = sg ? 4 : 2, n_inner = (ab ? 4LL : 3LL) * ce + 1;
   // 1. step record; the per-region Gram solves (few warps per SM) run beside the Adams-Bashforth
   // increment and the right-hand side, which do not depend on them
   GE(launch_step_begin(ctl, dd ? g->n_slots : 0, o.s_max, dt, dd ? 1 : 0, n_fixed, s));
@@ -1172,6 +1251,10 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   // 2. right-hand side from the recurrences
   GE(launch_rhs_incr(mv, rpad, dt, m->tp.a0, m->tp.a1, g->Ma, g->Mv, g->Kv, g->Ku, g->b, g->src, g->ext, 0.0, sf,
                      ctl));
+  GE(launch_impulses(g->imp, rpad, 0, ctl, m->fm, g->b, sf));
+  if (ab)
+    GE(launch_dashpot<double>(m->ab, rpad, 1.0, nullptr, g->b, false, m->fm, nullptr, nullptr, nullptr, nullptr, sf, V,
+                              -1, Ring4{}, 0, ctl));
   GE(cudaEventRecord(g->gev[1], sf));
   if (dd) GE(launch_pred_solve(pv, nullptr, 0, 0, o.tau, s, ctl));
   GE(cudaStreamWaitEvent(s, g->gev[1], 0));
@@ -1185,7 +1268,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   // 3. residual of the guess
   const float* qy = nullptr;
   if (dd) {
-    GE(ebe_product<float>(m, rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s));
+    GE(ebe_product<float>(m, rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s, true));
     qy = w->q32;
   }
   if (sg) {
@@ -1246,7 +1329,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
         } else {
           GE(launch_dir_defer<float>(mv, rpad, w->r32, w->p32, w->x32, w->sc, w->n_active, s4));
         }
-        GE(ebe_product<float>(m, rpad, w->p32, w->q32, m->cM, m->cK, &red, w->sc, nullptr, w->n_active, s4));
+        GE(ebe_product<float>(m, rpad, w->p32, w->q32, m->cM, m->cK, &red, w->sc, nullptr, w->n_active, s4, true));
         if (sg) {
           GE(launch_update_seg<float>(mv, w->p32, w->q32, w->x32, w->rr32, w->z32, red, w->sc, w->n_active, o.maxit,
                                       s4));
@@ -1265,6 +1348,9 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
     GE(cudaStreamEndCapture(s3, &tmp));
     // FP64 certification: split products of the increment, true residual, per-case stop test
     GE(split_product(m, o.cert_df, rpad, g->x, g->xdf, g->qM, g->qK, s2));
+    if (ab)
+      GE(launch_dashpot<double>(m->ab, rpad, m->ab.cB / m->cK, g->x, g->qK, false, m->fm, nullptr, nullptr, nullptr,
+                                nullptr, s2));
     if (sg) {
       GE(launch_cert_seg(mv, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol, o.inner_tol,
                          s2));
@@ -1275,10 +1361,16 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
     GE(launch_pass_end(w->n_active, ctl, h_pass, kMaxPass, n_pass, s2));
   }
   GE(cudaStreamEndCapture(s2, &tmp));
+  if (ab)   // (the certification's dashpot term leaves qK: the recurrences advance by K du)
+    GE(launch_dashpot<double>(m->ab, rpad, -m->ab.cB / m->cK, g->x, g->qK, false, m->fm, nullptr, nullptr, nullptr,
+                              nullptr, s));
   // 5. Newmark update, recurrences, snapshot push, Gram row of the new snapshot, statistics
   GE(launch_newmark_incr(g->n, dt, m->cM, m->cK, g->x, g->du_ab, g->qM, g->qK, g->u, nullptr, g->a, nullptr, g->Ku,
                          g->Mv, g->Kv, g->Ma, nullptr, nullptr, o.snapshot_format, s, V, AV, dd ? g->ring : nullptr,
                          g->snap_stride, ctl));
+  if (ab)
+    GE(launch_dashpot<double>(m->ab, rpad, m->ab.cB, nullptr, nullptr, false, m->fm, nullptr, nullptr, nullptr, nullptr,
+                              s, V, 0, AV, 0, ctl));
   if (dd) GE(launch_pred_dots(pv, 0, 0, s, ctl));
   GE(launch_step_end(w->outer, g->ncase, g->acc_iters, g->acc_relres, g->acc_status, ctl, s));
   return cudaSuccess;
@@ -1420,6 +1512,9 @@ static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
   CU(launch_ebe<double>(mv, g->rpad, g->m_in, g->k_in, g->b, 1.0, 1.0, nullptr, nullptr, nullptr, s));
   w->pend(pe, s);
   CU(launch_rhs_finish(mv, g->rpad, g->b, g->src, g->use_ext ? g->ext : nullptr, it * dt, s));
+  CU(launch_impulses(g->imp, g->rpad, it, nullptr, m->fm, g->b, s));
+  CU(launch_dashpot<double>(m->ab, g->rpad, 1.0, vslot(it - 1), g->b, false, m->fm, nullptr, nullptr, nullptr, nullptr,
+                            s));
   g->use_ext = false;
   w->pend(ph, s);
   w->count(3);
@@ -1692,6 +1787,103 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
   return FEM_OK;
 }
 
+fem_status fem_mesh_set_absorbing(fem_mesh* m, int64_t n_faces, const int32_t* faces, void* stream) {
+  g_err.clear();
+  if (!m) return fail(FEM_ERR_ARG, "mesh is null");
+  if (n_faces < 0 || (n_faces > 0 && !faces)) return fail(FEM_ERR_ARG, "bad face list");
+  if (m->seg) return fail(FEM_ERR_ARG, "a fused virtual mesh takes no absorbing faces");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = m->N;
+  // node -> elements incidence
+  std::vector<int64_t> ip(N + 1, 0);
+  for (int32_t v : m->h_conn) ip[v + 1] += 1;
+  for (int64_t k = 0; k < N; ++k) ip[k + 1] += ip[k];
+  std::vector<int32_t> inc(m->h_conn.size());
+  {
+    std::vector<int64_t> pos(ip.begin(), ip.end() - 1);
+    for (size_t i = 0; i < m->h_conn.size(); ++i) inc[pos[m->h_conn[i]]++] = (int32_t)(i / 4);
+  }
+  std::unordered_map<int32_t, std::array<double, 6>> blk;
+  for (int64_t f = 0; f < n_faces; ++f) {
+    const int32_t a = faces[3 * f], b = faces[3 * f + 1], c = faces[3 * f + 2];
+    if (a < 0 || a >= N || b < 0 || b >= N || c < 0 || c >= N || a == b || b == c || a == c)
+      return fail(FEM_ERR_ARG, "absorbing face " + std::to_string(f) + ": bad node ids");
+    int owner = -1, opp = -1, count = 0;
+    for (int64_t k = ip[a]; k < ip[a + 1]; ++k) {
+      const int32_t e = inc[k];
+      const int32_t* nd = &m->h_conn[4 * (size_t)e];
+      bool hb = false, hc = false;
+      int other = -1;
+      for (int j = 0; j < 4; ++j) {
+        hb = hb || nd[j] == b;
+        hc = hc || nd[j] == c;
+        if (nd[j] != a && nd[j] != b && nd[j] != c) other = nd[j];
+      }
+      if (hb && hc) owner = e, opp = other, count += 1;
+    }
+    if (count != 1)
+      return fail(FEM_ERR_ARG, "absorbing face " + std::to_string(f) + " is not a face of exactly one element");
+    const double* X = m->h_xyz.data();
+    double e1[3], e2[3], w[3], nrm[3];
+    for (int d = 0; d < 3; ++d) e1[d] = X[3 * b + d] - X[3 * a + d], e2[d] = X[3 * c + d] - X[3 * a + d],
+                                w[d] = X[3 * opp + d] - X[3 * a + d];
+    nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double len = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+    if (!(len > 0.0)) return fail(FEM_ERR_ARG, "absorbing face " + std::to_string(f) + " has zero area");
+    double n[3] = {nrm[0] / len, nrm[1] / len, nrm[2] / len};
+    if (n[0] * w[0] + n[1] * w[1] + n[2] * w[2] > 0.0) n[0] = -n[0], n[1] = -n[1], n[2] = -n[2];   // outward
+    const int mid = m->h_mat[owner];
+    const double lam = m->h_lmr[3 * mid], mu = m->h_lmr[3 * mid + 1], rho = m->h_lmr[3 * mid + 2];
+    const double cp = std::sqrt((lam + 2.0 * mu) / rho), cs = std::sqrt(mu / rho);
+    const double sc = 0.5 * len / 3.0 * rho;   // a third of the face's area, times rho
+    const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int32_t node : {a, b, c}) {
+      auto& B = blk[node];
+      for (int q = 0; q < 6; ++q) {
+        const int i = ij[q][0], j = ij[q][1];
+        B[q] += sc * (cp * n[i] * n[j] + cs * ((i == j ? 1.0 : 0.0) - n[i] * n[j]));
+      }
+    }
+  }
+  std::vector<int32_t> nodes;
+  nodes.reserve(blk.size());
+  for (const auto& kv : blk) nodes.push_back(kv.first);
+  std::sort(nodes.begin(), nodes.end());
+  std::vector<double> c64(6 * nodes.size());
+  std::vector<float> c32(6 * nodes.size());
+  for (size_t k = 0; k < nodes.size(); ++k)
+    for (int q = 0; q < 6; ++q) c64[6 * k + q] = blk[nodes[k]][q], c32[6 * k + q] = (float)c64[6 * k + q];
+  dfree(m->ab_node); dfree(m->ab_c64); dfree(m->ab_c32);
+  m->ab = Absorb{};
+  if (!nodes.empty()) {
+    CHK(dalloc(&m->ab_node, nodes.size()));
+    CHK(dalloc(&m->ab_c64, c64.size()));
+    CHK(dalloc(&m->ab_c32, c32.size()));
+    CU(cudaMemcpyAsync(m->ab_node, nodes.data(), sizeof(int32_t) * nodes.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(m->ab_c64, c64.data(), sizeof(double) * c64.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(m->ab_c32, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice, s));
+    m->ab = Absorb{(int)nodes.size(), m->ab_node, m->ab_c64, m->ab_c32, 2.0 / m->tp.dt};
+  }
+  // block-Jacobi diagonal of A = cM M + cK K + (2/dt) C_b, recomputed from scratch
+  int* d_err = nullptr;
+  CHK(dalloc(&d_err, 1));
+  cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->D, 0, sizeof(double) * 6 * N, s);
+  if (e == cudaSuccess) e = launch_diag_blocks(m->view(), m->cM, m->cK, m->D, s);
+  if (e == cudaSuccess) e = launch_add_node_blocks(m->ab, m->ab.cB, m->D, s);
+  if (e == cudaSuccess) e = launch_binv(N, m->D, m->fm, m->binv64, m->binv32, d_err, s);
+  int h_err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_err);
+  if (e != cudaSuccess) return fail(FEM_ERR_CUDA, std::string("fem_mesh_set_absorbing: ") + cudaGetErrorString(e));
+  if (h_err) return fail(FEM_ERR_ARG, "singular node diagonal block");
+  m->h_ab_faces.assign(faces, faces + 3 * n_faces);
+  return FEM_OK;
+}
+
 fem_status fem_mesh_destroy(fem_mesh* m) {
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
   cudaDeviceSynchronize();
@@ -1899,12 +2091,8 @@ fem_status fem_batch_destroy(fem_batch* b) {
   return FEM_OK;
 }
 
-fem_status fem_case_add(fem_batch* b, fem_mesh* m, int32_t src_node, const double dir[3], double f0, double t0,
-                        double amp, int* case_id) {
-  g_err.clear();
-  if (!b || !m || !dir) return fail(FEM_ERR_ARG, "null argument");
-  if (b->started) return fail(FEM_ERR_STATE, "cases must be added before the first fem_step");
-  if (src_node < 0 || src_node >= m->N) return fail(FEM_ERR_ARG, "source node out of range");
+static fem_status case_add(fem_batch* b, fem_mesh* m, int32_t src_node, const double dir[3], double f0, double t0,
+                           double amp, int* case_id, Group** gout = nullptr) {
   Group* g = nullptr;
   for (auto* gg : b->groups)
     if (gg->mesh == m && gg->cases.size() < (size_t)kMaxRpad) g = gg;
@@ -1916,8 +2104,43 @@ fem_status fem_case_add(fem_batch* b, fem_mesh* m, int32_t src_node, const doubl
   const int id = (int)b->loc.size();
   g->cases.push_back(id);
   g->hsrc.push_back(RickerSrc{src_node, {dir[0], dir[1], dir[2]}, f0, t0, amp});
+  g->himp.resize(g->cases.size());
   b->loc.push_back({(int)(std::find(b->groups.begin(), b->groups.end(), g) - b->groups.begin()),
                     (int)g->cases.size() - 1});
+  if (case_id) *case_id = id;
+  if (gout) *gout = g;
+  return FEM_OK;
+}
+
+fem_status fem_case_add(fem_batch* b, fem_mesh* m, int32_t src_node, const double dir[3], double f0, double t0,
+                        double amp, int* case_id) {
+  g_err.clear();
+  if (!b || !m || !dir) return fail(FEM_ERR_ARG, "null argument");
+  if (b->started) return fail(FEM_ERR_STATE, "cases must be added before the first fem_step");
+  if (src_node < 0 || src_node >= m->N) return fail(FEM_ERR_ARG, "source node out of range");
+  return case_add(b, m, src_node, dir, f0, t0, amp, case_id);
+}
+
+fem_status fem_case_add_impulses(fem_batch* b, fem_mesh* m, int64_t n, const int32_t* nodes, const int32_t* steps,
+                                 const double* forces, int* case_id) {
+  g_err.clear();
+  if (!b || !m || n < 0 || (n > 0 && (!nodes || !steps || !forces))) return fail(FEM_ERR_ARG, "bad argument");
+  if (b->started) return fail(FEM_ERR_STATE, "cases must be added before the first fem_step");
+  for (int64_t k = 0; k < n; ++k) {
+    if (nodes[k] < 0 || nodes[k] >= m->N) return fail(FEM_ERR_ARG, "impulse node out of range");
+    if (steps[k] < 1) return fail(FEM_ERR_ARG, "impulse steps start at 1");
+    for (int d = 0; d < 3; ++d)
+      if (!std::isfinite(forces[3 * k + d])) return fail(FEM_ERR_ARG, "non-finite impulse force");
+  }
+  const double zero[3] = {0.0, 0.0, 0.0};
+  Group* g = nullptr;
+  int id = 0;
+  // no Ricker point force: a zero amplitude (its node 0 receives nothing)
+  CHK(case_add(b, m, 0, zero, 1.0, 0.0, 0.0, &id, &g));
+  auto& v = g->himp[b->loc[id].second];
+  v.reserve((size_t)n);
+  for (int64_t k = 0; k < n; ++k)
+    v.push_back(Group::HostImpulse{nodes[k], steps[k], {forces[3 * k], forces[3 * k + 1], forces[3 * k + 2]}});
   if (case_id) *case_id = id;
   return FEM_OK;
 }
@@ -1942,6 +2165,9 @@ static fem_status fuse_cases(fem_batch* b) {
     const fem_mesh* m = mesh_of[c];
     if (m->tp.dt != tp.dt || m->tp.a0 != tp.a0 || m->tp.a1 != tp.a1)
       return fail(FEM_ERR_ARG, "fused meshes must share dt and damping");
+    if (m->ab.nb > 0) return fail(FEM_ERR_ARG, "fuse_meshes does not support absorbing faces");
+    if (!b->groups[b->loc[c].first]->himp[b->loc[c].second].empty())
+      return fail(FEM_ERR_ARG, "fuse_meshes does not support impulse loads");
     N += m->N;
     E += m->E;
     nmat += (int64_t)m->h_lmr.size() / 3;

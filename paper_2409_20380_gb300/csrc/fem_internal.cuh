@@ -115,6 +115,26 @@ struct MeshView {
   int nseg = 0;
 };
 
+// Dashpots of absorbing boundary faces: per boundary node its symmetric 3x3 block (xx yy zz xy xz yz) of
+// C_b, in FP64 and FP32; cB = 2/dt, the factor with which C_b enters A.
+struct Absorb {
+  int nb = 0;
+  const int32_t* node = nullptr;
+  const double* c64 = nullptr;
+  const float* c32 = nullptr;
+  double cB = 0.0;
+};
+
+// Random impulse loads of a group, sorted by step: entries off[it] .. off[it + 1] - 1 act in step it
+// (1 <= it <= last); per entry the node, the case lane and the force [3].
+struct Impulses {
+  int n = 0, last = 0, max_per_step = 0;
+  const int32_t* node = nullptr;
+  const int32_t* lane = nullptr;
+  const double* f = nullptr;
+  const int32_t* off = nullptr;
+};
+
 struct RickerSrc {          // per case of a group
   int node;                 // -1: no source (padding lane)
   double dir[3];
@@ -292,6 +312,20 @@ cudaError_t launch_ebe_hexmat(const HexTiles& ht, const MeshView& m, const float
                               float* q, double aM, double aK, const Reducer* red, CgCase* sc, double* ptq_out,
                               const int* gate, cudaStream_t s);
 size_t ebe_hexmat_smem(const HexTiles& ht, const MeshView& m, int rpad);   // ~0 when not applicable
+// q (+)= coef C_b p on the boundary nodes (free DOFs; assign: q = coef C_b p there).  red != nullptr: the
+// per-case p . (coef C_b p) is added to ptq_out and to the CG state sc (p^T q and the step length), as the
+// element-by-element product's tail does.  gate: skip when *gate == 0.  With ctl, p and q come from the rings
+// pring / qring (when given) at step ctl->it + poff / + qoff.
+template <typename T>
+cudaError_t launch_dashpot(const Absorb& ab, int rpad, double coef, const T* p, T* q, bool assign,
+                           const uint8_t* fm, const Reducer* red, CgCase* sc, double* ptq_out, const int* gate,
+                           cudaStream_t s, Ring4 pring = Ring4{}, int poff = 0, Ring4 qring = Ring4{}, int qoff = 0,
+                           const StepCtl* ctl = nullptr);
+// D[node] += coef C_b[node] (node 3x3 diagonal blocks of A, before their inversion).
+cudaError_t launch_add_node_blocks(const Absorb& ab, double coef, double* D, cudaStream_t s);
+// b += the impulses of step `it` (or ctl->it) at their nodes and case lanes (free DOFs).
+cudaError_t launch_impulses(const Impulses& im, int rpad, int it, const StepCtl* ctl, const uint8_t* fm, double* b,
+                            cudaStream_t s);
 // Reads and clears the flag a staged kernel sets when a bounded wait for its copies gave up.
 cudaError_t ebe_tma_timeout(int* flag);
 // Sets the number of tries (up to 1 us each) of the staged kernels' reporting wait (device-wide; ordered on s).

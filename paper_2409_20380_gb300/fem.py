@@ -32,7 +32,7 @@ EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_
            "fem_case_stats", "fem_batch_steps", "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_get_params",
            "fem_mlp_forward", "fem_mlp_loss_grad", "fem_mlp_train", "fem_batch_set_mlp", "fem_batch_collect",
            "fem_batch_collected", "fem_batch_proposal_counts", "fem_last_error", "fem_mlp_loss_grad_residual",
-           "fem_mlp_train_residual", "fem_batch_collect_residual")
+           "fem_mlp_train_residual", "fem_batch_collect_residual", "fem_mesh_set_absorbing", "fem_case_add_impulses")
 FEM_MLP_N_PARAMS, FEM_MLP_IN, FEM_MLP_OUT, FEM_MLP_RES = 90656, 64, 32, 560
 
 
@@ -126,6 +126,8 @@ def lib():
         "fem_batch_set_mlp": (I, [P, P]),
         "fem_batch_collect": (I, [P, P, P, I64]),
         "fem_batch_collect_residual": (I, [P, P, P, I64]),
+        "fem_mesh_set_absorbing": (I, [P, I64, P, P]),
+        "fem_case_add_impulses": (I, [P, P, I64, P, P, P, ctypes.POINTER(I)]),
         "fem_mlp_loss_grad_residual": (I, [P, P, P, I64, P, ctypes.POINTER(D)]),
         "fem_mlp_train_residual": (I, [P, P, P, I64, P, I, I, D, P]),
         "fem_batch_collected": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I)]),
@@ -336,6 +338,23 @@ def predictor_coefficients(batch, case_id, n_regions, s_max):
     n = ctypes.c_int(0)
     _check(lib().predictor_coefficients(batch, case_id, _np_ptr(coef), ctypes.byref(n)))
     return coef, n.value
+
+
+def fem_mesh_set_absorbing(h, faces, stream=None):
+    """faces: [n][3] node triples of the absorbing boundary faces (None or empty: remove the dashpots)."""
+    f = np.ascontiguousarray(faces if faces is not None else np.zeros((0, 3)), dtype=np.int32).reshape(-1, 3)
+    _check(lib().fem_mesh_set_absorbing(h, f.shape[0], _np_ptr(f) if f.size else None, _stream(stream)))
+
+
+def fem_case_add_impulses(batch, h, imp):
+    """imp: workload.Impulses (nodes, steps, forces).  Returns the case id."""
+    nodes = np.ascontiguousarray(imp.nodes, dtype=np.int32)
+    steps = np.ascontiguousarray(imp.steps, dtype=np.int32)
+    forces = np.ascontiguousarray(imp.forces, dtype=np.float64).reshape(-1, 3)
+    cid = ctypes.c_int(-1)
+    _check(lib().fem_case_add_impulses(batch, h, nodes.size, _np_ptr(nodes), _np_ptr(steps), _np_ptr(forces),
+                                       ctypes.byref(cid)))
+    return cid.value
 
 
 def fem_case_get(batch, case_id, what, n_nodes, out=None):
