@@ -64,6 +64,13 @@ def parse():
                     help="large: 256x256x128 box, 5 layers + basin, 8 cases, s = 16; medium: 64x64x32 box, "
                          "3 layers, 16 cases, s = 32")
     ap.add_argument("--cases", type=int, default=None)
+    ap.add_argument("--source", default="ricker", choices=["ricker", "impulses"],
+                    help="ricker: one Ricker point force per case; impulses: random impulses at surface points "
+                         "(the paper's random inputs)")
+    ap.add_argument("--impulse-points", type=int, default=None,
+                    help="impulse points per case (default: 7%% of the surface nodes)")
+    ap.add_argument("--impulse-steps", type=int, default=100, help="impulses fall in steps 1 .. this")
+    ap.add_argument("--absorbing", action="store_true", help="absorbing (dashpot) boundaries on the four sides")
     ap.add_argument("--dims", default=None)
     ap.add_argument("--s-max", type=int, default=None)
     ap.add_argument("--region-nodes", type=int, default=1024)
@@ -250,11 +257,24 @@ def make_sources(config, mesh, n_cases, first_case=0):
 def workload(args, rank):
     from paper_2409_20380_gb300 import workload as wl
     mesh, tp = make_mesh(args.config, args.dims)
-    srcs = make_sources(args.config, mesh, args.cases, first_case=rank * args.cases)
+    if args.source == "impulses":
+        npts = args.impulse_points or max(1, int(0.07 * wl.surface_nodes(mesh).size))
+        cfg = 4 if args.config == "large" else 2
+        srcs = [wl.random_impulses(mesh, wl.rng_for(cfg, 0, rank * args.cases + c, 4), npts, args.impulse_steps)
+                for c in range(args.cases)]
+    else:
+        srcs = make_sources(args.config, mesh, args.cases, first_case=rank * args.cases)
     return mesh, srcs, tp, wl.region_map(mesh, args.region_nodes)
 
 
-def _oracle_case(config, dims, case, predictor, s_max, region_nodes, spinup, steps, barrier, out):
+def add_case(fem, bt, h, s):
+    if hasattr(s, "steps"):
+        return fem.fem_case_add_impulses(bt, h, s)
+    return fem.fem_case_add(bt, h, s)
+
+
+def _oracle_case(config, dims, case, predictor, s_max, region_nodes, spinup, steps, barrier, out, source="ricker",
+                 absorbing=False, impulse_steps=100):
     """One case of the oracle sample, in its own (spawned) process: the FP64 oracle as it stands on the
     sample mesh, `spinup` steps from rest, then `steps` timed steps after every process is ready."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
@@ -262,8 +282,12 @@ def _oracle_case(config, dims, case, predictor, s_max, region_nodes, spinup, ste
     import oracle
     from paper_2409_20380_gb300 import workload as wl
     mesh, tp = make_mesh(config, dims)
-    src = make_sources(config, mesh, case + 1)[case]
-    sysm, A = oracle.build_system(mesh, tp)
+    if source == "impulses":
+        npts = max(1, int(0.07 * wl.surface_nodes(mesh).size))
+        src = wl.random_impulses(mesh, wl.rng_for(4 if config == "large" else 2, 0, case, 4), npts, impulse_steps)
+    else:
+        src = make_sources(config, mesh, case + 1)[case]
+    sysm, A = oracle.build_system(mesh, tp, absorbing_faces=wl.side_faces(mesh) if absorbing else None)
     Binv = oracle.block_jacobi_inverse(A, sysm.free)
     sim = oracle.CaseSimulator(sysm, A, Binv, src, predictor=predictor, s_max=s_max,
                                region_of_node=wl.region_map(mesh, region_nodes))
@@ -288,7 +312,8 @@ def oracle_sample(args, n_procs, spinup, steps):
     barrier = ctx.Barrier(n_procs) if n_procs > 1 else None
     pred = "dd" if args.predictor == "dd" else "ab4"
     procs = [ctx.Process(target=_oracle_case, args=(args.config, args.cpu_dims, c, pred, args.s_max,
-                                                    args.region_nodes, spinup, steps, barrier, out))
+                                                    args.region_nodes, spinup, steps, barrier, out, args.source,
+                                                    args.absorbing, args.impulse_steps))
              for c in range(n_procs)]
     for p in procs:
         p.start()
@@ -360,16 +385,19 @@ def config_dict(args, mesh=None):
         mesh = argparse.Namespace(n_elems=6 * Hx * Hy * Hz, n_nodes=(Hx + 1) * (Hy + 1) * (Hz + 1))
     solver = ("FP32-inner/FP64-refined" if args.precision == "mixed" else "FP64") + " block-Jacobi EBE-PCG to rel. residual 1e-8"
     pred = "data-driven predictor s=%d" % args.s_max if args.predictor == "dd" else "AB4 predictor"
+    src = ("random surface impulses" if args.source == "impulses" else "Ricker point sources") + \
+        (", absorbing sides" if args.absorbing else "")
     if args.config == "large":
         name = (f"large: {args.dims.replace(',', 'x')} hex box (h=1/64) split into {mesh.n_elems} tets "
-                f"({mesh.n_nodes} nodes), 5 layers + low-velocity basin, {args.cases} cases on one mesh, {solver}, {pred}")
+                f"({mesh.n_nodes} nodes), 5 layers + low-velocity basin, {args.cases} cases on one mesh ({src}), "
+                f"{solver}, {pred}")
     else:
         name = (f"medium: {args.dims.replace(',', 'x')} hex box split into {mesh.n_elems} tets "
-                f"({mesh.n_nodes} nodes), {args.cases} cases on one mesh, {solver}, {pred}")
+                f"({mesh.n_nodes} nodes), {args.cases} cases on one mesh ({src}), {solver}, {pred}")
     return {"workload": name, "mesh_hex": args.dims, "n_elems": mesh.n_elems, "n_nodes": mesh.n_nodes,
             "cases_per_gpu": args.cases, "precision": args.precision, "predictor": args.predictor,
             "s_max": args.s_max, "cert_product": args.cert, "region_nodes": args.region_nodes, "tol": 1e-8,
-            "spinup_steps": args.spinup,
+            "spinup_steps": args.spinup, "source": args.source, "absorbing_sides": args.absorbing,
             "l2": "inputs larger than L2: each step streams the cases' state and the snapshot ring (>1 GB)",
             "parallelism": "replicas"}
 
@@ -404,12 +432,14 @@ def run_ours(args):
                                 use_graph=0 if args.no_graph else 1, check_every=args.check_every)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
+    if args.absorbing:
+        fem.fem_mesh_set_absorbing(h, wl.side_faces(mesh))
     if args.variant or args.hex_per_tile:
         fem.fem_mesh_tune(h, args.variant, args.hex_per_tile)
     bt = fem.fem_batch_create(opts)
     nc = len(srcs)
     for s in srcs:
-        fem.fem_case_add(bt, h, s)
+        add_case(fem, bt, h, s)
     log("library mesh and batch created")
     fem.fem_step(bt, args.spinup, nc)
     free_b, total_b = torch.cuda.mem_get_info()
@@ -454,17 +484,20 @@ def run_ours(args):
     N = mesh.n_nodes
     step0 = fem.fem_batch_steps(bt)
     ne = args.e2e_steps
-    loads = torch.empty((ne + 2, nc, 3), dtype=torch.float64).pin_memory()
+    ricker = args.source == "ricker"
+    loads = torch.zeros((ne + 2, nc, 3), dtype=torch.float64).pin_memory()
     for k in range(ne + 2):
         tk = (step0 + 1 + k) * tp.dt
         for c, s in enumerate(srcs):
-            loads[k, c] = torch.from_numpy(wl.ricker_load(s, tk))
+            if ricker:
+                loads[k, c] = torch.from_numpy(wl.ricker_load(s, tk))
     # each step's loads come from pinned host memory and its displacement fields go to alternating pinned
     # host buffers; steps are queued without host waits, the copy of step k runs on the batch's copy stream
     # while step k+1 computes, and fem_batch_sync (which also checks every step's status) ends the region
     u_host = [torch.empty(nc * N * 3, dtype=torch.float64).pin_memory() for _ in range(2)]
     for k in range(2):
-        fem.fem_batch_set_loads(bt, loads[k])
+        if ricker:
+            fem.fem_batch_set_loads(bt, loads[k])
         fem.fem_step(bt, 1, nc)
         fem.fem_batch_get_field_async(bt, fem.FEM_FIELD_U, u_host[k % 2])
     fem.fem_batch_sync(bt)
@@ -472,7 +505,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(2, ne + 2):
-        fem.fem_batch_set_loads(bt, loads[k])
+        if ricker:
+            fem.fem_batch_set_loads(bt, loads[k])
         fem.fem_step_async(bt, 1)
         fem.fem_batch_get_field_async(bt, fem.FEM_FIELD_U, u_host[k % 2])
     fem.fem_batch_sync(bt)
@@ -484,7 +518,7 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = t.item()
     log("end-to-end region done")
-    e2e = {"value": ws * nc * ne / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nc * 3 * 8,
+    e2e = {"value": ws * nc * ne / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nc * 3 * 8 if ricker else 0,
            "d2h_bytes_per_step": nc * N * 3 * 8, "steps": ne}
     # ---- plain FP64 PCG with Adams-Bashforth on the same state: with the EBE product (the comparator) and
     # with the assembled 3x3-block product (the CRS-style form the paper compares the EBE with) ----
@@ -496,7 +530,7 @@ def run_ours(args):
             cmp_opts = fem.fem_opts_default(precision=fem.FEM_FP64, predictor=fem.FEM_PRED_AB4, tol=1e-8)
             bt2 = fem.fem_batch_create(cmp_opts)
             for s in srcs:
-                fem.fem_case_add(bt2, h, s)
+                add_case(fem, bt2, h, s)
             # same physics from rest is not the same state; run the comparator on the steps right after a
             # short spin-up so its iteration counts are those of a developed wavefield
             fem.fem_step(bt2, args.comparator_spinup, nc)
