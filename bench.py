@@ -71,6 +71,9 @@ def parse():
                     help="impulse points per case (default: 7%% of the surface nodes)")
     ap.add_argument("--impulse-steps", type=int, default=100, help="impulses fall in steps 1 .. this")
     ap.add_argument("--absorbing", action="store_true", help="absorbing (dashpot) boundaries on the four sides")
+    ap.add_argument("--cpu-predictor", action="store_true",
+                    help="the paper's heterogeneous scheme: data-driven correction on the host CPU, two case sets "
+                         "alternating, s balanced against the solve time")
     ap.add_argument("--dims", default=None)
     ap.add_argument("--s-max", type=int, default=None)
     ap.add_argument("--region-nodes", type=int, default=1024)
@@ -398,6 +401,7 @@ def config_dict(args, mesh=None):
             "cases_per_gpu": args.cases, "precision": args.precision, "predictor": args.predictor,
             "s_max": args.s_max, "cert_product": args.cert, "region_nodes": args.region_nodes, "tol": 1e-8,
             "spinup_steps": args.spinup, "source": args.source, "absorbing_sides": args.absorbing,
+            "cpu_predictor": args.cpu_predictor,
             "l2": "inputs larger than L2: each step streams the cases' state and the snapshot ring (>1 GB)",
             "parallelism": "replicas"}
 
@@ -429,7 +433,8 @@ def run_ours(args):
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER if args.precision == "mixed" else fem.FEM_FP64,
                                 predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
                                 s_max=args.s_max, snapshot_format=args.snapshot_format, tol=1e-8, cert_df=args.cert,
-                                use_graph=0 if args.no_graph else 1, check_every=args.check_every)
+                                use_graph=0 if args.no_graph else 1, check_every=args.check_every,
+                                cpu_predictor=1 if args.cpu_predictor else 0)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
     if args.absorbing:
@@ -622,6 +627,9 @@ def run_ours(args):
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(args)
         log("oracle baseline done")
+    balance = None
+    if args.cpu_predictor:
+        balance = [fem.fem_batch_predictor_balance(bt, c) for c in (0, 1)]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -643,6 +651,7 @@ def run_ours(args):
                                      "ebe64": prof["ebe64_launches"] / max(prof["steps"], 1),
                                      "cg_vec": prof["cg_vec_launches"] / max(prof["steps"], 1),
                                      "all": prof["kernel_launches"] / max(prof["steps"], 1)},
+        "host_predictor_balance": balance,
         "fp64_plain_comparator": comparator,
         "fp64_crs_comparator": crs_comparator,
     }

@@ -119,12 +119,17 @@ typedef struct {
                             fem_ebe_apply and fem_mesh_autotune restore the default.  0 = a wait that has not
                             completed at once reports (a way to exercise the error path); default 1048576
                             (about a second); must be >= 0 */
-  int reserved;
+  int cpu_predictor;     /* 1 = the paper's heterogeneous scheme (Algorithm 3): the data-driven correction is
+                            computed on the host CPU from a pinned host copy of the stored corrections while the
+                            GPU steps the other case set (the cases of a mesh are split into two sets), and s is
+                            adjusted after every step toward equal prediction and solve times (s_max is the
+                            ceiling).  Needs FEM_PRED_DD, regions, snapshot_format 0 or 2, no fuse_meshes and
+                            no learned proposal; steps run eagerly.  0 = the predictor runs on the GPU */
 } fem_opts;
 
 /* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-6, tau 1e-6,
  * snapshot_format 2, check_every 8, refresh_every 200, cert_df 3, fuse_meshes 0, use_graph 1,
- * wait_budget 1048576. */
+ * wait_budget 1048576, cpu_predictor 0. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */
@@ -448,6 +453,15 @@ typedef struct {
 } fem_case_stats_t;
 
 fem_status fem_case_stats(fem_batch* b, int case_id, fem_case_stats_t* out);
+
+/*
+ * With opts.cpu_predictor: the balance of the heterogeneous scheme for the case set of case `case_id`:
+ * s_current the pairs the next prediction uses, predict_ms the last host prediction's wall time, solve_ms the
+ * last GPU step's wall time of the set, predict_total_ms / wait_total_ms the host prediction time and the time
+ * the steps waited for it, summed (nullable outputs).  Errors: FEM_ERR_STATE without the scheme.
+ */
+fem_status fem_batch_predictor_balance(fem_batch* b, int case_id, int* s_current, double* predict_ms,
+                                       double* solve_ms, double* predict_total_ms, double* wait_total_ms);
 
 /* Number of completed steps of the batch. */
 fem_status fem_batch_steps(const fem_batch* b, int* steps_out);

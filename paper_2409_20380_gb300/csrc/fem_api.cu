@@ -2,6 +2,7 @@
 // FP64-refined), and the batched time stepping of many cases (Section 3.1 time loop with the predictor
 // of Section 3.2 and the solver of Algorithm 1; cases on one mesh form one multi-RHS system, Eq. eqmebefem).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -252,6 +253,7 @@ struct fem_mesh {
   float inv_extent = 1.0f;          // 1 / largest edge of the bounding box
   int32_t* reg_lo = nullptr;
   int32_t* reg_hi = nullptr;
+  std::vector<int32_t> h_reg_lo, h_reg_hi;   // host copies (the host predictor)
   // nodes outside every region range: [reg_hi[R], reg_gap[R]) follows region R, [0, reg_lead) precedes all
   int32_t* reg_gap = nullptr;
   int reg_lead = 0;
@@ -652,6 +654,12 @@ static fem_status check_opts(const fem_opts* o) {
   if (o->cert_df < 0 || o->cert_df > 3) return fail(FEM_ERR_ARG, "cert_df must be 0, 1, 2 or 3");
   if (o->snapshot_format < 0 || o->snapshot_format > 3) return fail(FEM_ERR_ARG, "snapshot_format must be 0 .. 3");
   if (o->wait_budget < 0) return fail(FEM_ERR_ARG, "wait_budget must be >= 0");
+  if (o->cpu_predictor) {
+    if (o->predictor != FEM_PRED_DD) return fail(FEM_ERR_ARG, "cpu_predictor needs the data-driven predictor");
+    if (o->snapshot_format != 0 && o->snapshot_format != 2)
+      return fail(FEM_ERR_ARG, "cpu_predictor needs snapshot_format 0 or 2");
+    if (o->fuse_meshes) return fail(FEM_ERR_ARG, "cpu_predictor does not combine with fuse_meshes");
+  }
   return FEM_OK;
 }
 
@@ -675,6 +683,9 @@ struct Group {
   Impulses imp;
   int32_t *imp_node = nullptr, *imp_lane = nullptr, *imp_off = nullptr;
   double* imp_f = nullptr;
+  // the heterogeneous scheme: the host predictor and the device copy of its correction
+  HostPred* hp = nullptr;
+  double* ycpu = nullptr;
   int64_t n = 0;
   double *u = nullptr, *a = nullptr, *vh[4] = {nullptr, nullptr, nullptr, nullptr};
   double *b = nullptr, *x = nullptr, *du_ab = nullptr, *m_in = nullptr, *k_in = nullptr, *guess = nullptr;
@@ -742,6 +753,8 @@ struct Group {
       if (ev) cudaEventDestroy(ev);
     dfree(ctl); dfree(acc_iters); dfree(acc_relres); dfree(acc_status);
     dfree(imp_node); dfree(imp_lane); dfree(imp_off); dfree(imp_f);
+    hostpred_destroy(hp);
+    dfree(ycpu);
     if (h_pin) cudaFreeHost(h_pin);
     if (h_slots) cudaFreeHost(h_slots);
     delete ws;
@@ -830,6 +843,11 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
     g->n_chunks = std::max(1, std::min(64, (8 * sm_count() + R - 1) / R));
     CHK(dalloc(&g->dpart, (size_t)R * g->n_chunks * kMaxSlots * g->rpad));
     CU(cudaMemsetAsync(g->gram, 0, sizeof(double) * (size_t)R * g->rpad * kMaxSlots * kMaxSlots, s));
+    if (bt->opts.cpu_predictor && m->n_regions > 0) {
+      CU(hostpred_create(g->snap_stride, g->rpad, g->n_slots, bt->opts.s_max, bt->opts.snapshot_format,
+                         bt->opts.tau, m->h_reg_lo, m->h_reg_hi, &g->hp));
+      CHK(dalloc(&g->ycpu, n));
+    }
   }
   CHK(dalloc(&g->slot_lists, 2 * kMaxSlots));
   if (cudaMallocHost((void**)&g->h_slots, sizeof(int) * 2 * kMaxSlots) != cudaSuccess) {
@@ -946,6 +964,16 @@ static fem_status group_predict(fem_batch* bt, Group* g, double* out, bool* corr
   CU(cudaMemcpyAsync(out, g->du_ab, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
   if (bt->opts.predictor != FEM_PRED_DD || g->n_regions == 0) return FEM_OK;
   if (g->mesh->n_regions != g->n_regions) return fail(FEM_ERR_STATE, "mesh regions changed after the batch started");
+  if (g->hp) {   // heterogeneous scheme: the correction the host prepared for this step
+    int np = 0;
+    const double* yh = hostpred_take(g->hp, it, &np);
+    if (!yh) return FEM_OK;
+    CU(cudaMemcpyAsync(g->ycpu, yh, sizeof(double) * g->n, cudaMemcpyHostToDevice, s));
+    CU(launch_add(g->n, g->du_ab, g->ycpu, out, s));
+    g->ws->count();
+    if (corrected) *corrected = true;
+    return FEM_OK;
+  }
   const int n_e = std::min(it - 1, g->n_slots);
   const int n_pairs = std::min(bt->opts.s_max, n_e - 1);
   if (n_pairs <= 0) return FEM_OK;
@@ -1022,6 +1050,7 @@ static fem_status group_refresh(fem_batch* bt, Group* g) {
 // recurrences (no FP64 product), inner FP32 PCG, and one FP64 certification product per refinement pass,
 // whose split products M du, K du advance the recurrences.
 static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
+  const auto t_start = std::chrono::steady_clock::now();
   fem_mesh* m = g->mesh;
   const MeshView mv = m->view();
   cudaStream_t s = bt->s;
@@ -1140,7 +1169,11 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   CU(launch_dashpot<double>(m->ab, g->rpad, m->ab.cB, vslot(it), aslot(it), false, m->fm, nullptr, nullptr, nullptr,
                             nullptr, s));
   w->count();
-  if (dd) {
+  if (dd && g->hp) {   // heterogeneous scheme: the new correction to the host, the next prediction there
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    CU(hostpred_push(g->hp, e_push, it, ms, s));
+  } else if (dd) {
     uint64_t mask = 0;
     const int n_e = std::min(it, g->n_slots);
     for (int j = it - n_e + 1; j <= it; ++j) mask |= 1ull << slot_of(g, j);
@@ -1481,7 +1514,7 @@ static fem_status group_graph_stats(fem_batch* bt, Group* g, fem_status* worst) 
 }
 
 static bool graph_eligible(const fem_batch* bt, const Group* g) {
-  return bt->opts.use_graph && bt->opts.precision == FEM_FP32_INNER && !bt->mlp && !bt->col_x &&
+  return bt->opts.use_graph && bt->opts.precision == FEM_FP32_INNER && !bt->mlp && !bt->col_x && !g->hp &&
          !(bt->prof.on && bt->prof.events);
 }
 
@@ -1494,6 +1527,7 @@ static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
   g->ctl_it = -1;
   if (bt->opts.precision == FEM_FP32_INNER) return group_step_mixed(bt, g, worst);
   if (g->owned_mesh) return fail(FEM_ERR_ARG, "fused meshes need the FP32-inner solver");
+  const auto t_start = std::chrono::steady_clock::now();
   fem_mesh* m = g->mesh;
   const MeshView mv = m->view();
   cudaStream_t s = bt->s;
@@ -1535,7 +1569,11 @@ static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
   CU(launch_newmark_update(g->n, dt, g->x, g->du_ab, g->u, vslot(it - 1), g->a, vslot(it), e_push,
                            bt->opts.snapshot_format, g->snap_stride, s));
   w->count();
-  if (dd) {
+  if (dd && g->hp) {
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    CU(hostpred_push(g->hp, e_push, it, ms, s));
+  } else if (dd) {
     uint64_t mask = 0;
     const int n_e = std::min(it, g->n_slots);
     for (int j = it - n_e + 1; j <= it; ++j) mask |= 1ull << slot_of(g, j);
@@ -2010,6 +2048,8 @@ fem_status fem_mesh_set_regions(fem_mesh* m, const int32_t* region_of_node) {
   CHK(dalloc(&m->reg_cent, 3 * (int64_t)R));
   CU(cudaMemcpy(m->reg_lo, lo.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(m->reg_hi, hi.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice));
+  m->h_reg_lo = lo;
+  m->h_reg_hi = hi;
   CU(cudaMemcpy(m->reg_gap, gap.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(m->reg_cent, cf.data(), sizeof(float) * 3 * R, cudaMemcpyHostToDevice));
   m->n_regions = R;
@@ -2094,8 +2134,18 @@ fem_status fem_batch_destroy(fem_batch* b) {
 static fem_status case_add(fem_batch* b, fem_mesh* m, int32_t src_node, const double dir[3], double f0, double t0,
                            double amp, int* case_id, Group** gout = nullptr) {
   Group* g = nullptr;
-  for (auto* gg : b->groups)
-    if (gg->mesh == m && gg->cases.size() < (size_t)kMaxRpad) g = gg;
+  if (b->opts.cpu_predictor) {   // two case sets per mesh, filled alternately (Algorithm 3's ping-pong)
+    std::vector<Group*> sets;
+    for (auto* gg : b->groups)
+      if (gg->mesh == m) sets.push_back(gg);
+    if (sets.size() >= 2) {
+      g = sets[1]->cases.size() < sets[0]->cases.size() ? sets[1] : sets[0];
+      if (g->cases.size() >= (size_t)kMaxRpad) return fail(FEM_ERR_ARG, "cpu_predictor: at most 64 cases per mesh");
+    }
+  } else {
+    for (auto* gg : b->groups)
+      if (gg->mesh == m && gg->cases.size() < (size_t)kMaxRpad) g = gg;
+  }
   if (!g) {
     g = new Group();
     g->mesh = m;
@@ -2342,6 +2392,14 @@ fem_status predictor_coefficients(fem_batch* b, int case_id, double* coef_host, 
   const int n_pairs = it >= 1 ? std::max(0, std::min(b->opts.s_max, std::min(it - 1, g->n_slots) - 1)) : 0;
   const int l = b->loc[case_id].second, R = g->n_regions, s = b->opts.s_max;
   std::vector<double> all((size_t)R * g->rpad * kMaxSlots);
+  if (g->hp) {   // heterogeneous scheme: the host's coefficients and pair count of the last prediction used
+    int np = 0;
+    const double* wh = hostpred_coefficients(g->hp, &np);
+    for (int r = 0; r < R; ++r)
+      for (int a = 0; a < s; ++a) coef_host[(size_t)r * s + a] = a < np ? wh[((size_t)r * g->rpad + l) * kMaxSlots + a] : 0.0;
+    if (n_pairs_out) *n_pairs_out = np;
+    return FEM_OK;
+  }
   CU(cudaMemcpyAsync(all.data(), g->wcoef, sizeof(double) * all.size(), cudaMemcpyDeviceToHost, b->s));
   CU(cudaStreamSynchronize(b->s));
   for (int r = 0; r < R; ++r)
@@ -2405,6 +2463,7 @@ fem_status fem_batch_set_loads(fem_batch* b, const double* loads) {
 }
 
 static fem_status learn_ok(const fem_batch* b) {
+  if (b->opts.cpu_predictor) return fail(FEM_ERR_ARG, "the learned proposal needs the GPU predictor (cpu_predictor 0)");
   if (b->opts.precision != FEM_FP32_INNER) return fail(FEM_ERR_ARG, "the learned proposal needs FEM_FP32_INNER");
   if (b->opts.predictor != FEM_PRED_DD) return fail(FEM_ERR_ARG, "the learned proposal needs the data-driven predictor");
   if (b->opts.fuse_meshes) return fail(FEM_ERR_ARG, "the learned proposal needs groups of one mesh (no fuse_meshes)");
@@ -2619,6 +2678,24 @@ fem_status fem_case_stats(fem_batch* b, int case_id, fem_case_stats_t* out) {
   out->status = c.status;
   out->init_relres = c.relres0;
   out->relres = c.relres;
+  return FEM_OK;
+}
+
+fem_status fem_batch_predictor_balance(fem_batch* b, int case_id, int* s_current, double* predict_ms,
+                                       double* solve_ms, double* predict_total_ms, double* wait_total_ms) {
+  g_err.clear();
+  if (!b || case_id < 0 || case_id >= (int)b->loc.size()) return fail(FEM_ERR_ARG, "bad case id");
+  const Group* g = b->groups[b->loc[case_id].first];
+  if (!g->hp) return fail(FEM_ERR_STATE, "the batch does not use the heterogeneous predictor");
+  int sc = 0;
+  double a = 0, c = 0, d = 0, e = 0;
+  long long n = 0;
+  hostpred_stats(g->hp, &sc, &a, &c, &d, &e, &n);
+  if (s_current) *s_current = sc;
+  if (predict_ms) *predict_ms = a;
+  if (solve_ms) *solve_ms = c;
+  if (predict_total_ms) *predict_total_ms = d;
+  if (wait_total_ms) *wait_total_ms = e;
   return FEM_OK;
 }
 

@@ -326,6 +326,16 @@ cudaError_t launch_add_node_blocks(const Absorb& ab, double coef, double* D, cud
 // b += the impulses of step `it` (or ctl->it) at their nodes and case lanes (free DOFs).
 cudaError_t launch_impulses(const Impulses& im, int rpad, int it, const StepCtl* ctl, const uint8_t* fm, double* b,
                             cudaStream_t s);
+// The heterogeneous predictor (hetero.cu): the data-driven correction of a group computed on the host.
+struct HostPred;
+cudaError_t hostpred_create(int64_t n, int rpad, int n_slots, int s_max, int fmt, double tau,
+                            const std::vector<int32_t>& lo, const std::vector<int32_t>& hi, HostPred** out);
+void hostpred_destroy(HostPred* h);
+cudaError_t hostpred_push(HostPred* h, const void* dev_slot, int it, double solve_ms, cudaStream_t s);
+const double* hostpred_take(HostPred* h, int it, int* n_pairs);
+void hostpred_stats(const HostPred* h, int* s_cur, double* cpu_ms, double* solve_ms, double* cpu_sum,
+                    double* wait_sum, long long* tasks);
+const double* hostpred_coefficients(const HostPred* h, int* n_pairs);
 // Reads and clears the flag a staged kernel sets when a bounded wait for its copies gave up.
 cudaError_t ebe_tma_timeout(int* flag);
 // Sets the number of tries (up to 1 us each) of the staged kernels' reporting wait (device-wide; ordered on s).

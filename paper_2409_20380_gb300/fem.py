@@ -32,7 +32,8 @@ EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_
            "fem_case_stats", "fem_batch_steps", "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_get_params",
            "fem_mlp_forward", "fem_mlp_loss_grad", "fem_mlp_train", "fem_batch_set_mlp", "fem_batch_collect",
            "fem_batch_collected", "fem_batch_proposal_counts", "fem_last_error", "fem_mlp_loss_grad_residual",
-           "fem_mlp_train_residual", "fem_batch_collect_residual", "fem_mesh_set_absorbing", "fem_case_add_impulses")
+           "fem_mlp_train_residual", "fem_batch_collect_residual", "fem_mesh_set_absorbing", "fem_case_add_impulses",
+           "fem_batch_predictor_balance")
 FEM_MLP_N_PARAMS, FEM_MLP_IN, FEM_MLP_OUT, FEM_MLP_RES = 90656, 64, 32, 560
 
 
@@ -53,7 +54,7 @@ class fem_opts(ctypes.Structure):
                 ("tau", ctypes.c_double), ("snapshot_format", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("refresh_every", ctypes.c_int), ("cert_df", ctypes.c_int), ("fuse_meshes", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("wait_budget", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("cpu_predictor", ctypes.c_int)]
 
 
 class fem_profile(ctypes.Structure):
@@ -127,6 +128,8 @@ def lib():
         "fem_batch_collect": (I, [P, P, P, I64]),
         "fem_batch_collect_residual": (I, [P, P, P, I64]),
         "fem_mesh_set_absorbing": (I, [P, I64, P, P]),
+        "fem_batch_predictor_balance": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D),
+                                            ctypes.POINTER(D), ctypes.POINTER(D)]),
         "fem_case_add_impulses": (I, [P, P, I64, P, P, P, ctypes.POINTER(I)]),
         "fem_mlp_loss_grad_residual": (I, [P, P, P, I64, P, ctypes.POINTER(D)]),
         "fem_mlp_train_residual": (I, [P, P, P, I64, P, I, I, D, P]),
@@ -355,6 +358,15 @@ def fem_case_add_impulses(batch, h, imp):
     _check(lib().fem_case_add_impulses(batch, h, nodes.size, _np_ptr(nodes), _np_ptr(steps), _np_ptr(forces),
                                        ctypes.byref(cid)))
     return cid.value
+
+
+def fem_batch_predictor_balance(batch, case_id):
+    """Heterogeneous scheme: dict(s, predict_ms, solve_ms, predict_total_ms, wait_total_ms) of a case's set."""
+    sc = ctypes.c_int()
+    v = [ctypes.c_double() for _ in range(4)]
+    _check(lib().fem_batch_predictor_balance(batch, case_id, ctypes.byref(sc), *[ctypes.byref(x) for x in v]))
+    return dict(s=sc.value, predict_ms=v[0].value, solve_ms=v[1].value, predict_total_ms=v[2].value,
+                wait_total_ms=v[3].value)
 
 
 def fem_case_get(batch, case_id, what, n_nodes, out=None):

@@ -153,7 +153,7 @@ class PredStats:
         assert self.ambiguous <= max(2, 0.02 * self.n), (self.ambiguous, self.n)
 
 
-def check_prediction(E, reg_dof, n_reg, y_gpu, coef, n_pairs, opts, floor, stats, where=None):
+def check_prediction(E, reg_dof, n_reg, y_gpu, coef, n_pairs, opts, floor, stats, where=None, s_used=None):
     """Checks the GPU's regional correction y_gpu (and its coefficients coef [n_reg][s_max]) against the
     oracle's modified Gram-Schmidt on the stored corrections E (oldest first, E[-1] = the query e^{it-1}).
 
@@ -169,7 +169,7 @@ def check_prediction(E, reg_dof, n_reg, y_gpu, coef, n_pairs, opts, floor, stats
     A column whose orthogonalised norm ratio lies within a factor 3 of tau may be kept by one side and
     dropped by the other (the Gram pivot's rounding at the threshold): such a region is counted as ambiguous
     and its objective is bounded by MGS's residual with those columns dropped."""
-    n = min(opts.s_max, len(E) - 1) if E else 0
+    n = min(opts.s_max if s_used is None else s_used, len(E) - 1) if E else 0
     assert n_pairs == max(n, 0), (n_pairs, n, where)
     if n <= 0:
         assert np.abs(y_gpu).max() <= floor, where
