@@ -388,6 +388,9 @@ def config_dict(args, mesh=None):
         mesh = argparse.Namespace(n_elems=6 * Hx * Hy * Hz, n_nodes=(Hx + 1) * (Hy + 1) * (Hz + 1))
     solver = ("FP32-inner/FP64-refined" if args.precision == "mixed" else "FP64") + " block-Jacobi EBE-PCG to rel. residual 1e-8"
     pred = "data-driven predictor s=%d" % args.s_max if args.predictor == "dd" else "AB4 predictor"
+    if args.cpu_predictor:
+        pred = ("data-driven predictor on the host CPU (two case sets alternating, s balanced against the solve "
+                "time, at most %d)" % args.s_max)
     src = ("random surface impulses" if args.source == "impulses" else "Ricker point sources") + \
         (", absorbing sides" if args.absorbing else "")
     if args.config == "large":
