@@ -98,7 +98,7 @@ def parse():
                     help="inner CG iterations per convergence check (graph: launches per WHILE-loop body)")
     ap.add_argument("--profile-steps", type=int, default=40,
                     help="steps after the timed region timed per kernel class with CUDA events (eager)")
-    ap.add_argument("--kernel", default=None, choices=["ebe", "ebe10", "pcg10", "split", "predictor"],
+    ap.add_argument("--kernel", default=None, choices=["ebe", "ebe10", "pcg10", "split", "predictor", "mlp"],
                     help="time one kernel alone (EBE product) instead of the full step")
     ap.add_argument("--kernel-precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=0,
@@ -600,7 +600,9 @@ def run_ours(args):
             if args.cert == 3:     # per block and case: 12 double-float FMAs of 14 FP32 flops each
                 fl = 12 * 14 * nnz * rpad
                 roof = {"bound": "alu", "peak": alu32, "peak_kind": "derived: FP32 lanes x max SM clock"}
-                kname = "k_bcsr_split_df (certification product M p, K p: assembled 3x3 blocks, double-float)"
+                kname = ("k_bcsr_split_df2 (certification product M p, K p: assembled 3x3 blocks, double-float, "
+                         "two cases a thread)" if rpad >= 2 else
+                         "k_bcsr_split_df (certification product M p, K p: assembled 3x3 blocks, double-float)")
             else:
                 fl = 12 * 2 * nnz * rpad
                 roof = {"bound": "alu", "peak": alu64, "peak_kind": "derived: %d SMs x 2 DFMA/clk x max SM clock" % n_sm}
@@ -992,6 +994,54 @@ def run_uneven(args):
         fem.fem_mesh_destroy(h)
 
 
+def run_mlp(args):
+    """Times the learned proposal's network alone (--kernel mlp): Adam updates of batch --batch on the
+    residual-space loss, 100 updates a step, and the forward pass over one step's (region, case) rows of the
+    medium workload (137 regions x 16 cases).  Random samples, inputs resident; CUDA events.  A dense
+    64-256-256-32 network costs 2 x 90112 flops a row forward and 2 x 163840 backward (no input gradient of
+    the first layer)."""
+    import torch
+    from paper_2409_20380_gb300 import build, fem
+    from paper_2409_20380_gb300 import workload as wl
+    build.build()
+    fem.lib()
+    torch.cuda.set_device(0)
+    net = fem.fem_mlp_create(wl.mlp_init_weights(0).astype(np.float32))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    n, upd = 65536, 100
+    xs = torch.randn((n, fem.FEM_MLP_IN), device="cuda", generator=g)
+    ss = 0.1 * torch.randn((n, fem.FEM_MLP_RES), device="cuda", generator=g)
+    order = torch.randint(0, n, (upd, args.batch), device="cuda", generator=g, dtype=torch.int32)
+    for _ in range(args.warmup):
+        fem.fem_mlp_train_residual(net, xs, ss, order, with_loss=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fem.fem_mlp_train_residual(net, xs, ss, order, with_loss=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_upd = e0.elapsed_time(e1) / (args.steps * upd)
+    rows = 137 * 16
+    out = torch.empty((rows, fem.FEM_MLP_OUT), device="cuda")
+    for _ in range(args.warmup):
+        fem.fem_mlp_forward(net, xs[:rows], out)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps * 10):
+        fem.fem_mlp_forward(net, xs[:rows], out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1) / (args.steps * 10)
+    fl_upd = 2.0 * args.batch * (90112 + 163840)
+    print(json.dumps({"kernel": "mlp", "batch": args.batch, "ms_per_update": ms_upd,
+                      "update_tflops": fl_upd / ms_upd / 1e9, "forward_rows": rows, "ms_per_forward": ms_fwd,
+                      "forward_tflops": 2.0 * rows * 90112 / ms_fwd / 1e9,
+                      "note": "update = forward, residual-space loss, backward, Adam (BF16 mma.sync GEMMs)"}),
+          flush=True)
+    fem.fem_mlp_destroy(net)
+
+
 def run_split(args):
     """Times the certification product alone (fem_mesh_split_product, form --cert) on the --dims mesh with
     --cases cases (CUDA events, inputs resident)."""
@@ -1082,6 +1132,9 @@ def main():
         return
     if args.kernel == "split":
         run_split(args)
+        return
+    if args.kernel == "mlp":
+        run_mlp(args)
         return
     if args.kernel == "predictor":
         run_predictor_kernels(args)

@@ -128,6 +128,83 @@ __global__ void __launch_bounds__(256) k_bcsr_split_df(int64_t N, int rpad, int 
   }
 }
 
+// Two cases a thread (rpad >= 2): the same arithmetic as k_bcsr_split_df in paired FP32 instructions (one
+// instruction applies an operation to both cases), so each block record's loads and the loop's address work
+// also serve two cases.  The input comes pair-packed: p2[(node * 3 + k) * rpad / 2 + pair] = (hi of case
+// 2 pair, hi of case 2 pair + 1, lo of case 2 pair, lo of case 2 pair + 1).
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+__device__ __forceinline__ void df2_fma_acc(float2& sh, float2& sl, float2 ah, float2 al, float2 bh, float2 bl) {
+  const float2 p = __fmul2_rn(ah, bh);
+  float2 e = __ffma2_rn(ah, bh, __fmul2_rn(p, make_float2(-1.f, -1.f)));
+  e = __ffma2_rn(ah, bl, e);
+  e = __ffma2_rn(al, bh, e);
+  const float2 s = __fadd2_rn(sh, p);
+  const float2 bb = sub2(s, sh);
+  const float2 err = __fadd2_rn(sub2(sh, sub2(s, bb)), sub2(p, bb));
+  sh = s;
+  sl = __fadd2_rn(sl, __fadd2_rn(err, e));
+}
+
+template <typename I>
+__global__ void __launch_bounds__(256) k_bcsr_split_df2(int64_t N, int rpad, int hshift, const int32_t* __restrict__ row_ptr,
+                                                        const int32_t* __restrict__ col, const float4* __restrict__ KM,
+                                                        const uint8_t* __restrict__ fm, const float4* __restrict__ p2,
+                                                        double* __restrict__ qM, double* __restrict__ qK) {
+  const int hpad = rpad >> 1;
+  const int64_t total = N << hshift;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const I n = (I)(t >> hshift);
+    const int cp = (int)(t & (hpad - 1));
+    const float2 z = make_float2(0.f, 0.f);
+    float2 kh[3] = {z, z, z}, kl[3] = {z, z, z}, mh[3] = {z, z, z}, ml[3] = {z, z, z};
+    const int lo = __ldg(row_ptr + n), hi = __ldg(row_ptr + n + 1);
+    const float4* pc = p2 + cp;
+    const I r3 = (I)(3 * hpad);
+    for (int j = lo; j < hi; ++j) {
+      const I cn = (I)__ldg(col + j);
+      float2 bh[3], bl[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float4 v = __ldg(pc + cn * r3 + (I)(k * hpad));
+        bh[k] = make_float2(v.x, v.y);
+        bl[k] = make_float2(v.z, v.w);
+      }
+      const float4* rec = KM + (int64_t)j * 5;
+      const float4 q0 = __ldg(rec), q1 = __ldg(rec + 1), q2 = __ldg(rec + 2), q3 = __ldg(rec + 3), q4 = __ldg(rec + 4);
+      const float ah[10] = {q0.x, q0.z, q1.x, q1.z, q2.x, q2.z, q3.x, q3.z, q4.x, q4.z};
+      const float al[10] = {q0.y, q0.w, q1.y, q1.w, q2.y, q2.w, q3.y, q3.w, q4.y, q4.w};
+      const float2 mvh = bc2(ah[9]), mvl = bc2(al[9]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        df2_fma_acc(mh[i], ml[i], mvh, mvl, bh[i], bl[i]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) df2_fma_acc(kh[i], kl[i], bc2(ah[i * 3 + k]), bc2(al[i * 3 + k]), bh[k], bl[k]);
+      }
+    }
+    const uint8_t f = fm[n];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int64_t id = ((int64_t)n * 3 + i) * rpad + 2 * cp;
+      const bool fr = dof_free(f, i);
+      *reinterpret_cast<double2*>(qM + id) = fr ? make_double2(f2d(mh[i].x) + f2d(ml[i].x), f2d(mh[i].y) + f2d(ml[i].y))
+                                               : make_double2(0.0, 0.0);
+      *reinterpret_cast<double2*>(qK + id) = fr ? make_double2(f2d(kh[i].x) + f2d(kl[i].x), f2d(kh[i].y) + f2d(kl[i].y))
+                                               : make_double2(0.0, 0.0);
+    }
+  }
+}
+
+// FP64 values of case pairs -> pair-packed double-float inputs of k_bcsr_split_df2.
+__global__ void k_to_df2(int64_t n_pairs, const double2* __restrict__ v, float4* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pairs; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 x = v[i];
+    const float2 a = d2df(x.x), b = d2df(x.y);
+    out[i] = make_float4(a.x, b.x, a.y, b.y);
+  }
+}
+
 // The same product in native FP64.
 __global__ void __launch_bounds__(256) k_bcsr_split_f64(int64_t N, int rpad, int rshift,
                                                         const int32_t* __restrict__ row_ptr,
@@ -284,7 +361,22 @@ cudaError_t launch_bcsr_split(const MeshView& m, int rpad, const int32_t* row_pt
                               double* qM, double* qK, cudaStream_t s) {
   const int rs = lg2(rpad);
   const int64_t items = m.N << rs;
-  if (p_df) {   // double-float: inputs split once per value, then the product on the FP32 pipe
+  const bool al16 = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(qM) |
+                      reinterpret_cast<uintptr_t>(qK) | reinterpret_cast<uintptr_t>(p_df)) & 15u) == 0;
+  if (p_df && rpad >= 2 && al16) {   // double-float, two cases a thread (16-byte accesses of case pairs)
+    const int64_t n_pairs = m.N * 3 * (rpad / 2);
+    k_to_df2<<<grid_of(n_pairs), 256, 0, s>>>(n_pairs, reinterpret_cast<const double2*>(p),
+                                              reinterpret_cast<float4*>(p_df));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const float4* km = reinterpret_cast<const float4*>(KMd);
+    const float4* p2 = reinterpret_cast<const float4*>(p_df);
+    const int64_t items2 = m.N << (rs - 1);
+    if (n_pairs < ((int64_t)1 << 31))
+      k_bcsr_split_df2<int32_t><<<grid_of(items2), 256, 0, s>>>(m.N, rpad, rs - 1, row_ptr, col, km, m.freemask, p2, qM, qK);
+    else
+      k_bcsr_split_df2<int64_t><<<grid_of(items2), 256, 0, s>>>(m.N, rpad, rs - 1, row_ptr, col, km, m.freemask, p2, qM, qK);
+  } else if (p_df) {   // double-float: inputs split once per value, then the product on the FP32 pipe
     cudaError_t e = launch_to_df(m.N * 3 * rpad, p, p_df, s);
     if (e != cudaSuccess) return e;
     const float4* km = reinterpret_cast<const float4*>(KMd);
