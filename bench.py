@@ -105,6 +105,8 @@ def parse():
                     help="EBE variant: 0 auto, 1 generic, 2 tiled hex, 3 staged tiles, 4 case-major staged tiles, "
                          "5/6 packed staged tiles (two / one block per SM)")
     ap.add_argument("--hex-per-tile", type=int, default=0)
+    ap.add_argument("--element", default="tet4", choices=["tet4", "tet10"],
+                    help="tet10: the time-stepping solver on the medium box's tets as 10-node tets (its own line)")
     ap.add_argument("--uneven", action="store_true",
                     help="batched uneven meshes: --meshes cases on meshes of different sizes fused into one system")
     ap.add_argument("--meshes", type=int, default=64)
@@ -124,7 +126,7 @@ def parse():
                     help="learned proposal: collect training samples from this step on (0: every step)")
     ap.add_argument("--batch", type=int, default=4096)
     a = ap.parse_args()
-    if a.learned or a.uneven or a.kernel in ("ebe10", "pcg10"):
+    if a.learned or a.uneven or a.kernel in ("ebe10", "pcg10") or a.element == "tet10":
         a.config = "medium"          # these modes run on medium-size meshes
     large = a.config == "large"
     if a.cases is None:
@@ -994,6 +996,81 @@ def run_uneven(args):
         fem.fem_mesh_destroy(h)
 
 
+def run_step10(args):
+    """The time-stepping solver on 10-node tets (--element tet10): the --dims box of the medium recipe with
+    its tets as quadratic tets (all nodes renumbered in Morton order of their position), --cases cases with
+    the recipe's point sources, FP32-inner / FP64-certified block-Jacobi PCG with the tet10 element kernel,
+    the data-driven predictor (or AB4) on regions of --region-nodes nodes; graph steps after --spinup steps,
+    CUDA events over --steps steps.  The product alone is timed after the steps (FP32, all cases, 10
+    launches)."""
+    import torch
+    from paper_2409_20380_gb300 import build, fem
+    from paper_2409_20380_gb300 import workload as wl
+    build.build()
+    fem.lib()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    mesh, tp = make_mesh("medium", args.dims)
+    m10, new_id = wl.tet10_mesh_ordered(mesh)
+    srcs = make_sources("medium", mesh, args.cases)
+    for s in srcs:
+        s.node = int(new_id[s.node])
+    log(f"tet10 mesh: {m10.n_elems} elements, {m10.n_nodes} nodes")
+    h = fem.fem_mesh_create_tet10(m10, tp)
+    fem.fem_mesh_set_regions(h, wl.region_map10(m10, mesh.h, args.region_nodes))
+    opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER if args.precision == "mixed" else fem.FEM_FP64,
+                                predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
+                                s_max=args.s_max, tol=1e-8, snapshot_format=args.snapshot_format,
+                                cert_df=args.cert, use_graph=0 if args.no_graph else 1)
+    bt = fem.fem_batch_create(opts)
+    nc = len(srcs)
+    for s in srcs:
+        fem.fem_case_add(bt, h, s)
+    fem.fem_step(bt, args.spinup, nc)
+    fem.fem_step(bt, args.warmup, nc)
+    sampler = ClockSampler(0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.start()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    st, iters, relres = fem.fem_step(bt, args.steps, nc)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    fem.fem_batch_destroy(bt)
+    r = nc
+    g = torch.Generator(device="cuda").manual_seed(0)
+    p = torch.randn(m10.n_nodes * 3 * r, device="cuda", generator=g).float()
+    q = torch.empty_like(p)
+    cM = 4.0 / tp.dt ** 2 + 2.0 * tp.a0 / tp.dt
+    cK = 1.0 + 2.0 * tp.a1 / tp.dt
+    for _ in range(3):
+        fem.fem_ebe_apply(h, p, q, r, cM, cK)
+    ev0.record(stream)
+    for _ in range(10):
+        fem.fem_ebe_apply(h, p, q, r, cM, cK)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_prod = ev0.elapsed_time(ev1) / 10
+    print(json.dumps({
+        "metric": "time-steps/s over all cases at rel. residual 1e-8 (10-node tets)", "unit": UNIT,
+        "value": nc * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps, "steps": args.steps,
+        "warmup": args.warmup, "spinup_steps": args.spinup, "n_gpus": 1, "higher_is_better": True,
+        "config": {"workload": f"{args.dims} hex box of the medium recipe as 10-node tets: {m10.n_elems} elements, "
+                               f"{m10.n_nodes} nodes, {nc} cases on one mesh, "
+                               f"{'FP32-inner/FP64-refined' if args.precision == 'mixed' else 'FP64'} block-Jacobi "
+                               f"EBE-PCG, {'data-driven predictor s=%d' % args.s_max if args.predictor == 'dd' else 'AB4'}",
+                   "element": "tet10", "graph": not args.no_graph},
+        "cg_iters_per_case_step": float(iters.sum()) / (nc * args.steps),
+        "max_certified_relres": float(relres.max()), "status": int(st), "clocks": clocks,
+        "tet10_product_ms": ms_prod,
+        "tet10_product_note": "FP32 element kernel, q = A p for all cases, p^T q not fused, incl. zero fill and mask",
+    }), flush=True)
+    fem.fem_mesh_destroy(h)
+
+
 def run_mlp(args):
     """Times the learned proposal's network alone (--kernel mlp): Adam updates of batch --batch on the
     residual-space loss, 100 updates a step, and the forward pass over one step's (region, case) rows of the
@@ -1115,6 +1192,9 @@ def run_predictor_kernels(args):
 
 def main():
     args = parse()
+    if args.element == "tet10":
+        run_step10(args)
+        return
     if args.uneven:
         run_uneven(args)
         return

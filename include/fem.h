@@ -153,6 +153,24 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
                            const int32_t* mat_id, int n_mat, const double* lam_mu_rho,
                            const uint8_t* fixed_dof, const fem_time_params* tp, void* stream,
                            fem_mesh** out);
+/*
+ * The same mesh object for 10-node tetrahedra, the paper's element (Section 3.1), so that the time-stepping
+ * solver (fem_case_add, fem_step: Eq. GE:DIS, Algorithm 1, the predictors of Section 3.2) runs on quadratic
+ * tets.  Straight-sided elements; local node order: corners 0-3, then the edge nodes of (0,1), (1,2), (0,2),
+ * (0,3), (1,3), (2,3).  Arguments as fem_mesh_create's, with conn10 [n_elems][10] host int32 (the corner tet
+ * positively oriented).  The products are the tet10 element-by-element kernel (stiffness by the 4-point Gauss
+ * rule, exact for these elements; consistent mass by exact integration) in FP64 or FP32; the certification
+ * product's assembled 3x3 blocks are assembled from the same operators (cert_df 2, 3), and cert_df 0 and 1
+ * both take the FP64 element kernel.  The block-Jacobi B^{-1} comes from the tet10 node diagonal blocks.  Not
+ * available on such a mesh: absorbing faces, fuse_meshes, fem_mesh_autotune (fem_mesh_tune selects variant 0,
+ * the element kernel, or 8, the assembled blocks).  Predictor regions must be contiguous node ranges, as for
+ * linear tets: number the nodes (corner and edge nodes alike) in an order with locality.
+ * Errors: as fem_mesh_create's (every conn10 entry is range-checked on the host).
+ */
+fem_status fem_mesh_create_tet10(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn10,
+                                 const int32_t* mat_id, int n_mat, const double* lam_mu_rho,
+                                 const uint8_t* fixed_dof, const fem_time_params* tp, void* stream,
+                                 fem_mesh** out);
 fem_status fem_mesh_destroy(fem_mesh* m);
 
 /*
@@ -248,7 +266,8 @@ fem_status fem_ebe_apply(fem_mesh* m, int precision, const void* p_dev, void* q_
  * Allocation-free variant of fem_ebe_apply (the paper has no counterpart: this is a library service).
  * Same arguments and errors as fem_ebe_apply, but it never allocates device memory (no cudaMalloc/cudaFree,
  * no allocating library routine).  It always runs the generic element kernel (one thread per element and
- * case, scatter by global atomics), not the tiled or autotuned kernel fem_ebe_apply may choose, so it can be
+ * case, scatter by global atomics; the tet10 element kernel on a fem_mesh_create_tet10 mesh), not the tiled
+ * or autotuned kernel fem_ebe_apply may choose, so it can be
  * slower, and its q and p^T q equal fem_ebe_apply's to rounding (FP32 atomics add in varying order), not bit
  * for bit.  It is meant for callers that cannot allocate:
  * code whose device memory is owned by another allocator under a fixed budget, and latency-critical loops

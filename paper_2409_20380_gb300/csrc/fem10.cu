@@ -254,6 +254,77 @@ __global__ void k_diag10(int64_t E, const int32_t* __restrict__ conn, const doub
   }
 }
 
+// The assembled operators of a tet10 mesh (the certification product's 3x3-block stiffness and scalar mass on
+// the node pattern): one thread per element adds its 100 node-pair blocks,
+//   K_ij = sum_q V/4 [lambda d_i d_j^T + mu d_j d_i^T + mu (d_i . d_j) I],  d_i = grad N_i at Gauss point q,
+//   M_ij = rho V m_ij,
+// the same operators the product applies (exact Gauss rule for the stiffness, exact mass coefficients).
+__device__ __forceinline__ void grad10(const double (&g)[4][3], const double (&L)[4], int i, double (&d)[3]) {
+  if (i < 4) {
+    for (int k = 0; k < 3; ++k) d[k] = (4.0 * L[i] - 1.0) * g[i][k];
+  } else {
+    const int a = edge_a(i - 4), b = edge_b(i - 4);
+    for (int k = 0; k < 3; ++k) d[k] = 4.0 * (L[a] * g[b][k] + L[b] * g[a][k]);
+  }
+}
+
+__global__ void k_bcsr_assemble10(int64_t E, const int32_t* __restrict__ conn, const double* __restrict__ rec,
+                                  Mass10 mc, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                  double* __restrict__ Kb, double* __restrict__ Mb, int* __restrict__ missing) {
+  const double GA = 0.5854101966249685, GB = 0.1381966011250105;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const double* r = rec + e * kRec;
+    double g[4][3];
+    for (int k = 0; k < 3; ++k) {
+      g[1][k] = r[k], g[2][k] = r[3 + k], g[3][k] = r[6 + k];
+      g[0][k] = -(g[1][k] + g[2][k] + g[3][k]);
+    }
+    const double lam = r[9] * 0.25, mu = r[10] * 0.25, rv = r[11] * 20.0;
+    int nd[10];
+    for (int i = 0; i < 10; ++i) nd[i] = conn[e * 10 + i];
+    for (int i = 0; i < 10; ++i) {
+      const int lo = row_ptr[nd[i]], hi = row_ptr[nd[i] + 1];
+      for (int j = 0; j < 10; ++j) {
+        int jj = -1;
+        for (int t = lo; t < hi; ++t)
+          if (col[t] == nd[j]) {
+            jj = t;
+            break;
+          }
+        if (jj < 0) {
+          atomicExch(missing, 1);
+          continue;
+        }
+        double kb[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int qp = 0; qp < 4; ++qp) {
+          double L[4], di[3], dj[3];
+          for (int a = 0; a < 4; ++a) L[a] = a == qp ? GA : GB;
+          grad10(g, L, i, di);
+          grad10(g, L, j, dj);
+          const double dd = di[0] * dj[0] + di[1] * dj[1] + di[2] * dj[2];
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+              kb[a * 3 + b] += lam * di[a] * dj[b] + mu * dj[a] * di[b] + (a == b ? mu * dd : 0.0);
+        }
+        for (int u = 0; u < 9; ++u) atomicAdd(Kb + (int64_t)jj * 9 + u, kb[u]);
+        atomicAdd(Mb + jj, rv * mc.m64[tri(i, j)]);
+      }
+    }
+  }
+}
+
+Mass10 mass10_table() {
+  static Mass10 mc = [] {
+    Mass10 t{};
+    double mm[10][10];
+    mass10_host(mm);
+    for (int i = 0; i < 10; ++i)
+      for (int j = i; j < 10; ++j) t.m64[tri(i, j)] = mm[i][j];
+    return t;
+  }();
+  return mc;
+}
+
 __global__ void k_corner_conn(int64_t E, const int32_t* __restrict__ conn10, int4* __restrict__ conn4) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
     conn4[e] = make_int4(conn10[e * 10], conn10[e * 10 + 1], conn10[e * 10 + 2], conn10[e * 10 + 3]);
@@ -266,6 +337,63 @@ int lg2i(int r) {
 }
 
 }  // namespace
+
+// The products of the time-stepping solver on a tet10 mesh: q = aM M pm + aK K pk (pk null: the same p for
+// both, with p^T q and the CG step length fused when red is given; gate as the tet4 kernels'), Dirichlet
+// rows of q zeroed.
+template <typename T>
+cudaError_t launch_ebe10_gated(int64_t E, int64_t N, int rpad, const int32_t* conn10, const float* rec32,
+                               const double* rec64, const uint8_t* fm, const T* pm, const T* pk, T* q, double aM,
+                               double aK, const Reducer* red, CgCase* sc, double* ptq, const int* gate,
+                               cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(q, 0, sizeof(T) * (size_t)N * 3 * rpad, s);
+  if (e != cudaSuccess) return e;
+  const int rs = lg2i(rpad);
+  const bool i32 = N * 3 * rpad < ((int64_t)1 << 31);
+  const Reducer none{nullptr, nullptr, nullptr};
+  auto run = [&](const T* p, T a_m, T a_k, bool dot) {
+    const int grid = grid_for(E << rs, dot ? red_grid_cap() : -1);
+    auto fn = dot ? (i32 ? k_ebe10<T, true, int32_t> : k_ebe10<T, true, int64_t>)
+                  : (i32 ? k_ebe10<T, false, int32_t> : k_ebe10<T, false, int64_t>);
+    fn<<<grid, kBlock, 0, s>>>(E, rpad, rs, conn10, rec32, rec64, p, q, a_m, a_k, dot ? *red : none,
+                               dot ? ptq : nullptr, dot ? sc : nullptr, gate);
+    return cudaGetLastError();
+  };
+  if (pk) {
+    e = run(pm, (T)aM, (T)0, false);
+    if (e == cudaSuccess) e = run(pk, (T)0, (T)aK, false);
+  } else {
+    e = run(pm, (T)aM, (T)aK, red != nullptr);
+  }
+  if (e == cudaSuccess) e = launch_mask<T>(N, rpad, fm, q, s);
+  return e;
+}
+template cudaError_t launch_ebe10_gated<float>(int64_t, int64_t, int, const int32_t*, const float*, const double*,
+                                               const uint8_t*, const float*, const float*, float*, double, double,
+                                               const Reducer*, CgCase*, double*, const int*, cudaStream_t);
+template cudaError_t launch_ebe10_gated<double>(int64_t, int64_t, int, const int32_t*, const float*, const double*,
+                                                const uint8_t*, const double*, const double*, double*, double, double,
+                                                const Reducer*, CgCase*, double*, const int*, cudaStream_t);
+
+cudaError_t launch_diag10(int64_t E, const int32_t* conn10, const double* rec64, double aM, double aK, double* D,
+                          cudaStream_t s) {
+  k_diag10<<<grid_for(E), kBlock, 0, s>>>(E, conn10, rec64, aM, aK, mass10_table(), D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bcsr_assemble10(int64_t E, const int32_t* conn10, const double* rec64, const int32_t* row_ptr,
+                                   const int32_t* col, int64_t nnz, double* Kb, double* Mb, float2* KMd, int* missing,
+                                   cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(Kb, 0, sizeof(double) * 9 * (size_t)nnz, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Mb, 0, sizeof(double) * (size_t)nnz, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(missing, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k_bcsr_assemble10<<<grid_for(E), kBlock, 0, s>>>(E, conn10, rec64, mass10_table(), row_ptr, col, Kb, Mb, missing);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_to_kmd(nnz, Kb, Mb, KMd, s);
+}
+
 }  // namespace fem
 
 using namespace fem;

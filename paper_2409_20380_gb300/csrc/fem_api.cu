@@ -227,6 +227,8 @@ static fem_status ws_create(int64_t N, int rpad, Workspace** out) {
 // ------------------------------------------------------------------------------------------------------
 struct fem_mesh {
   int64_t N = 0, E = 0;
+  int npe = 4;                      // nodes per element: 4 (linear tets) or 10 (quadratic tets)
+  int32_t* conn10 = nullptr;        // [E][10] (npe 10): corners, then the edges (0,1) (1,2) (0,2) (0,3) (1,3) (2,3)
   fem_time_params tp{};
   double cM = 0, cK = 0;
   int device = 0;
@@ -293,14 +295,14 @@ struct fem_mesh {
     std::vector<int32_t> inc(h_conn.size());
     {
       std::vector<int64_t> pos(inc_ptr.begin(), inc_ptr.end() - 1);
-      for (size_t i = 0; i < h_conn.size(); ++i) inc[pos[h_conn[i]]++] = (int32_t)(i / 4);
+      for (size_t i = 0; i < h_conn.size(); ++i) inc[pos[h_conn[i]]++] = (int32_t)(i / npe);
     }
     const int nt = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
     std::vector<int32_t> cnt(n_nodes);
     auto neighbours = [&](int64_t n, std::vector<int32_t>& buf) {
       buf.clear();
       for (int64_t k = inc_ptr[n]; k < inc_ptr[n + 1]; ++k)
-        for (int a = 0; a < 4; ++a) buf.push_back(h_conn[4 * (size_t)inc[k] + a]);
+        for (int a = 0; a < npe; ++a) buf.push_back(h_conn[(size_t)npe * inc[k] + a]);
       std::sort(buf.begin(), buf.end());
       buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
       if (buf.empty()) buf.push_back((int32_t)n);     // isolated node: diagonal slot only
@@ -347,7 +349,9 @@ struct fem_mesh {
     int h_missing = 0;
     cudaError_t e = cudaMemcpyAsync(row_ptr, rp.data(), sizeof(int32_t) * (n_nodes + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(col, cl.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_bcsr_assemble(view(), row_ptr, col, nnz, Kb, Mb, KMd, missing, s);
+    if (e == cudaSuccess)
+      e = npe == 10 ? launch_bcsr_assemble10(E, conn10, rec64, row_ptr, col, nnz, Kb, Mb, KMd, missing, s)
+                    : launch_bcsr_assemble(view(), row_ptr, col, nnz, Kb, Mb, KMd, missing, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_missing, missing, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dfree(missing);
@@ -379,7 +383,7 @@ struct fem_mesh {
     return FEM_OK;
   }
   ~fem_mesh() {
-    dfree(xyz); dfree(conn); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(rec_df); dfree(D);
+    dfree(xyz); dfree(conn); dfree(conn10); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(rec_df); dfree(D);
     dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(KMd); dfree(hexmat);
     dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi); dfree(reg_gap); dfree(seg); dfree(reg_cent);
     dfree(ab_node); dfree(ab_c64); dfree(ab_c32);
@@ -448,12 +452,18 @@ static cudaError_t ebe_elem_product(const fem_mesh* m, int rpad, const T* p, T* 
                                     const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s) {
   int v, h;
   m->resolve(sizeof(T), rpad, &v, &h);
+  if (m->npe == 10 && v != 8)   // quadratic tets: the tet10 element kernel (or the assembled blocks, variant 8)
+    return launch_ebe10_gated<T>(m->E, m->N, rpad, m->conn10, m->rec32, m->rec64, m->fm, p, nullptr, q, aM, aK, red,
+                                 sc, ptq, gate, s);
   if (v == 8) {   // assembled 3x3 blocks (built outside stream capture only); not for fused groups
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (!m->seg && (m->row_ptr || (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
                                    const_cast<fem_mesh*>(m)->ensure_bcsr(s) == FEM_OK)))
       return launch_bcsr_apply<T>(m->view(), rpad, m->row_ptr, m->col, m->Kb, m->Mb, m->KMd, p, q, aM, aK, red, sc,
                                   ptq, gate, s);
+    if (m->npe == 10)
+      return launch_ebe10_gated<T>(m->E, m->N, rpad, m->conn10, m->rec32, m->rec64, m->fm, p, nullptr, q, aM, aK,
+                                   red, sc, ptq, gate, s);
     v = m->hex ? 5 : 1, h = 0;
   }
   if (v == 7) {   // hex element matrices: FP32, the mesh's own coefficients, no fused groups, aligned vectors
@@ -1014,6 +1024,13 @@ static fem_status group_predict(fem_batch* bt, Group* g, double* out, bool* corr
 static cudaError_t split_product(const fem_mesh* m, int mode, int rpad, const double* p, float2* p_df, double* qM,
                                  double* qK, cudaStream_t s) {
   const MeshView mv = m->view();
+  if (m->npe == 10 && (mode == 0 || mode == 1)) {   // quadratic tets: the FP64 element kernel, M and K apart
+    cudaError_t e = launch_ebe10_gated<double>(m->E, m->N, rpad, m->conn10, m->rec32, m->rec64, m->fm, p, nullptr, qM,
+                                               1.0, 0.0, nullptr, nullptr, nullptr, nullptr, s);
+    if (e != cudaSuccess) return e;
+    return launch_ebe10_gated<double>(m->E, m->N, rpad, m->conn10, m->rec32, m->rec64, m->fm, p, nullptr, qK, 0.0,
+                                      1.0, nullptr, nullptr, nullptr, nullptr, s);
+  }
   if (mode == 1) return launch_ebe_split_df(mv, m->rec_df, rpad, p, qM, qK, s);
   if (mode == 2 || mode == 3)
     return launch_bcsr_split(mv, rpad, m->row_ptr, m->col, m->Kb, m->Mb, m->KMd, p, mode == 3 ? p_df : nullptr,
@@ -1543,7 +1560,12 @@ static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
   ph = w->pbeg(P_RHS, s);
   CU(launch_rhs_prep(g->n, dt, m->tp.a0, m->tp.a1, g->u, vslot(it - 1), g->a, g->m_in, g->k_in, s));
   int pe = w->pbeg(P_EBE64, s);
-  CU(launch_ebe<double>(mv, g->rpad, g->m_in, g->k_in, g->b, 1.0, 1.0, nullptr, nullptr, nullptr, s));
+  if (m->npe == 10) {
+    CU(launch_ebe10_gated<double>(m->E, m->N, g->rpad, m->conn10, m->rec32, m->rec64, m->fm, g->m_in, g->k_in, g->b,
+                                  1.0, 1.0, nullptr, nullptr, nullptr, nullptr, s));
+  } else {
+    CU(launch_ebe<double>(mv, g->rpad, g->m_in, g->k_in, g->b, 1.0, 1.0, nullptr, nullptr, nullptr, s));
+  }
   w->pend(pe, s);
   CU(launch_rhs_finish(mv, g->rpad, g->b, g->src, g->use_ext ? g->ext : nullptr, it * dt, s));
   CU(launch_impulses(g->imp, g->rpad, it, nullptr, m->fm, g->b, s));
@@ -1597,9 +1619,10 @@ static fem_status group_step(fem_batch* bt, Group* g, fem_status* worst) {
 namespace fem {
 fem_status set_error(fem_status s, const std::string& msg) { return fail(s, msg); }
 void clear_error() { g_err.clear(); }
-void mesh_view_of(const fem_mesh* m, MeshView* view, int* device) {
+void mesh_view_of(const fem_mesh* m, MeshView* view, int* device, const int32_t** conn10) {
   *view = m->view();
   *device = m->device;
+  *conn10 = m->npe == 10 ? m->conn10 : nullptr;
 }
 }  // namespace fem
 
@@ -1702,15 +1725,27 @@ void fem_opts_default(fem_opts* o) {
   o->wait_budget = kDefaultWaitBudget;
 }
 
-fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
-                           const int32_t* mat_id, int n_mat, const double* lam_mu_rho, const uint8_t* fixed_dof,
-                           const fem_time_params* tp, void* stream, fem_mesh** out) {
+// Mesh set-up shared by the linear (npe 4) and quadratic (npe 10) tets: element records of the corner tets,
+// block-Jacobi diagonal of the element type, and (linear tets in hex patches) the hex tiles.
+static fem_status mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn_in, int npe,
+                              const int32_t* mat_id, int n_mat, const double* lam_mu_rho, const uint8_t* fixed_dof,
+                              const fem_time_params* tp, void* stream, fem_mesh** out) {
   g_err.clear();
   if (!out) return fail(FEM_ERR_ARG, "out is null");
   *out = nullptr;
-  if (!xyz || !conn || !mat_id || !lam_mu_rho || !fixed_dof || !tp) return fail(FEM_ERR_ARG, "null input pointer");
-  if (n_nodes < 4 || n_elems < 1 || n_mat < 1) return fail(FEM_ERR_ARG, "empty mesh");
+  if (!xyz || !conn_in || !mat_id || !lam_mu_rho || !fixed_dof || !tp) return fail(FEM_ERR_ARG, "null input pointer");
+  if (n_nodes < npe || n_elems < 1 || n_mat < 1) return fail(FEM_ERR_ARG, "empty mesh");
   if (n_nodes > INT32_MAX) return fail(FEM_ERR_ARG, "node ids must fit int32");
+  std::vector<int32_t> corners;
+  const int32_t* conn = conn_in;
+  if (npe == 10) {   // the corner tets carry the element records; the edge nodes are checked here
+    for (int64_t i = 0; i < 10 * n_elems; ++i)
+      if (conn_in[i] < 0 || conn_in[i] >= n_nodes) return fail(FEM_ERR_ARG, "connectivity out of range");
+    corners.resize(4 * (size_t)n_elems);
+    for (int64_t e = 0; e < n_elems; ++e)
+      for (int a = 0; a < 4; ++a) corners[4 * e + a] = conn_in[10 * e + a];
+    conn = corners.data();
+  }
   if (tp->beta != 0.25 || tp->gamma != 0.5) return fail(FEM_ERR_ARG, "only Newmark beta=1/4, gamma=1/2 is supported");
   if (!(tp->dt > 0.0)) return fail(FEM_ERR_ARG, "dt must be > 0");
   for (int i = 0; i < n_mat; ++i)
@@ -1721,7 +1756,8 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
   fem_mesh* m = new fem_mesh();
   cudaGetDevice(&m->device);
   m->h_xyz.assign(xyz, xyz + 3 * n_nodes);
-  m->h_conn.assign(conn, conn + 4 * n_elems);
+  m->h_conn.assign(conn_in, conn_in + (size_t)npe * n_elems);
+  m->npe = npe;
   m->h_mat.assign(mat_id, mat_id + n_elems);
   m->h_lmr.assign(lam_mu_rho, lam_mu_rho + 3 * n_mat);
   m->h_fixed.assign(fixed_dof, fixed_dof + 3 * n_nodes);
@@ -1763,7 +1799,16 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
   cu(cudaMemsetAsync(d_err, 0, sizeof(int), s));
   cu(cudaMemsetAsync(m->D, 0, sizeof(double) * 6 * n_nodes, s));
   cu(launch_elem_setup(n_elems, n_nodes, m->xyz, m->conn, m->mat, n_mat, m->lmr, m->rec64, m->rec32, d_err, s));
-  cu(launch_diag_blocks(m->view(), m->cM, m->cK, m->D, s));
+  if (npe == 10) {
+    if (dalloc(&m->conn10, 10 * (size_t)n_elems) != FEM_OK) {
+      cudaFree(d_err);
+      return bail(FEM_ERR_OOM);
+    }
+    cu(cudaMemcpyAsync(m->conn10, conn_in, sizeof(int32_t) * 10 * n_elems, cudaMemcpyHostToDevice, s));
+    cu(launch_diag10(n_elems, m->conn10, m->rec64, m->cM, m->cK, m->D, s));
+  } else {
+    cu(launch_diag_blocks(m->view(), m->cM, m->cK, m->D, s));
+  }
   cu(launch_split_records(n_elems, m->rec64, m->rec_df, s));
   cu(launch_binv(n_nodes, m->D, m->fm, m->binv64, m->binv32, d_err, s));
   int h_err = 0;
@@ -1779,7 +1824,7 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
   if (h_err & 4) return bail(fail(FEM_ERR_ARG, "singular node diagonal block (node with no element?)"));
   // tile node entries carry the node id (bits 0-27), its three free-DOF bits (28-30) and whether another
   // tile shares the node (bit 31): the kernels' flush needs no separate mask load
-  if (n_nodes < (int64_t(1) << 28) && detect_hex_patches(conn, n_elems)) {
+  if (npe == 4 && n_nodes < (int64_t(1) << 28) && detect_hex_patches(conn, n_elems)) {
     const int sizes[fem_mesh::kNTile] = {64, 128, 256, 512};
     bool ok = true;
     double abs_m = 0.0, abs_k = 0.0;   // scale bounds of the packed kernel's fixed-point tile sums
@@ -1825,11 +1870,24 @@ fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, 
   return FEM_OK;
 }
 
+fem_status fem_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
+                           const int32_t* mat_id, int n_mat, const double* lam_mu_rho, const uint8_t* fixed_dof,
+                           const fem_time_params* tp, void* stream, fem_mesh** out) {
+  return mesh_create(n_nodes, xyz, n_elems, conn, 4, mat_id, n_mat, lam_mu_rho, fixed_dof, tp, stream, out);
+}
+
+fem_status fem_mesh_create_tet10(int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn10,
+                                 const int32_t* mat_id, int n_mat, const double* lam_mu_rho,
+                                 const uint8_t* fixed_dof, const fem_time_params* tp, void* stream, fem_mesh** out) {
+  return mesh_create(n_nodes, xyz, n_elems, conn10, 10, mat_id, n_mat, lam_mu_rho, fixed_dof, tp, stream, out);
+}
+
 fem_status fem_mesh_set_absorbing(fem_mesh* m, int64_t n_faces, const int32_t* faces, void* stream) {
   g_err.clear();
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
   if (n_faces < 0 || (n_faces > 0 && !faces)) return fail(FEM_ERR_ARG, "bad face list");
   if (m->seg) return fail(FEM_ERR_ARG, "a fused virtual mesh takes no absorbing faces");
+  if (m->npe != 4) return fail(FEM_ERR_ARG, "absorbing faces are supported on linear-tet meshes only");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t N = m->N;
   // node -> elements incidence
@@ -1933,6 +1991,8 @@ fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile) {
   g_err.clear();
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
   if (ebe_variant < 0 || ebe_variant > 8) return fail(FEM_ERR_ARG, "ebe_variant must be 0 .. 8");
+  if (m->npe == 10 && ebe_variant != 0 && ebe_variant != 8)
+    return fail(FEM_ERR_ARG, "a tet10 mesh takes variant 0 (its element kernel) or 8 (assembled blocks)");
   if (ebe_variant >= 2 && ebe_variant <= 7 && !m->hex)
     return fail(FEM_ERR_ARG, "the mesh has no hex patches: tiled kernel unavailable");
   if (hex_per_tile != 0 && hex_per_tile != 64 && hex_per_tile != 128 && hex_per_tile != 256 && hex_per_tile != 512)
@@ -1947,6 +2007,8 @@ fem_status fem_mesh_autotune(fem_mesh* m, int precision, int n_rhs, void* stream
   g_err.clear();
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
   if (!pow2_rhs(n_rhs)) return fail(FEM_ERR_ARG, "n_rhs must be 1, 2, 4, 8, 16 or 32");
+  if (m->npe != 4) return fail(FEM_ERR_ARG, "fem_mesh_autotune: linear-tet meshes only (fem_mesh_tune selects "
+                                           "a tet10 mesh's product)");
   cudaStream_t s = (cudaStream_t)stream;
   CU(ebe_set_wait_budget(kDefaultWaitBudget, s));
   if (precision == FEM_FP64) return autotune_t<double>(m, n_rhs, s, ebe_variant_out, hex_per_tile_out, ms_out);
@@ -2216,6 +2278,7 @@ static fem_status fuse_cases(fem_batch* b) {
     if (m->tp.dt != tp.dt || m->tp.a0 != tp.a0 || m->tp.a1 != tp.a1)
       return fail(FEM_ERR_ARG, "fused meshes must share dt and damping");
     if (m->ab.nb > 0) return fail(FEM_ERR_ARG, "fuse_meshes does not support absorbing faces");
+    if (m->npe != 4) return fail(FEM_ERR_ARG, "fuse_meshes supports linear tets only");
     if (!b->groups[b->loc[c].first]->himp[b->loc[c].second].empty())
       return fail(FEM_ERR_ARG, "fuse_meshes does not support impulse loads");
     N += m->N;

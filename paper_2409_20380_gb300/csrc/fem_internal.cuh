@@ -142,10 +142,11 @@ struct RickerSrc {          // per case of a group
 };
 
 // Accessors for translation units other than the C-ABI one: record the thread's error message and
-// return `s`; clear it (every entry point does so on entry); the device view and device id of a mesh.
+// return `s`; clear it (every entry point does so on entry); the device view and device id of a mesh, and its
+// tet10 connectivity (null for a linear-tet mesh).
 fem_status set_error(fem_status s, const std::string& msg);
 void clear_error();
-void mesh_view_of(const fem_mesh* m, MeshView* view, int* device);
+void mesh_view_of(const fem_mesh* m, MeshView* view, int* device, const int32_t** conn10);
 
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
 // Multiprocessors of the current device (queried once per device) and the grid caps derived from them:
@@ -379,6 +380,21 @@ cudaError_t launch_pred_combine(const PredView& p, const int* y_slots, int n_pai
 // pattern.
 cudaError_t launch_bcsr_assemble(const MeshView& m, const int32_t* row_ptr, const int32_t* col, int64_t nnz,
                                  double* Kb, double* Mb, float2* KMd, int* missing, cudaStream_t s);
+// The 80-byte double-float block records KMd from the FP64 blocks Kb and mass entries Mb.
+cudaError_t launch_to_kmd(int64_t nnz, const double* Kb, const double* Mb, float2* KMd, cudaStream_t s);
+// 10-node tets (fem10.cu): the solver's products q = aM M pm + aK K pk (pk null: one input, p^T q and the CG
+// step length fused when red is given), node diagonal blocks of aM M + aK K added into D, and the assembled
+// operators of the certification product on a tet10 node pattern.
+template <typename T>
+cudaError_t launch_ebe10_gated(int64_t E, int64_t N, int rpad, const int32_t* conn10, const float* rec32,
+                               const double* rec64, const uint8_t* fm, const T* pm, const T* pk, T* q, double aM,
+                               double aK, const Reducer* red, CgCase* sc, double* ptq, const int* gate,
+                               cudaStream_t s);
+cudaError_t launch_diag10(int64_t E, const int32_t* conn10, const double* rec64, double aM, double aK, double* D,
+                          cudaStream_t s);
+cudaError_t launch_bcsr_assemble10(int64_t E, const int32_t* conn10, const double* rec64, const int32_t* row_ptr,
+                                   const int32_t* col, int64_t nnz, double* Kb, double* Mb, float2* KMd, int* missing,
+                                   cudaStream_t s);
 // qM = M p, qK = K p (r cases, Dirichlet rows zero).  p_df != null: double-float arithmetic (p split into
 // p_df first); else native FP64.
 // q = (aM M + aK K) p with the assembled 3x3-block operators (EBE variant 8, the CRS-style comparator):

@@ -351,6 +351,11 @@ template cudaError_t launch_bcsr_apply<float>(const MeshView&, int, const int32_
                                               const double*, const float2*, const float*, float*, double, double,
                                               const Reducer*, CgCase*, double*, const int*, cudaStream_t);
 
+cudaError_t launch_to_kmd(int64_t nnz, const double* Kb, const double* Mb, float2* KMd, cudaStream_t s) {
+  k_to_kmd<<<grid_of(10 * nnz), 256, 0, s>>>(nnz, Kb, Mb, KMd);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_to_df(int64_t n, const double* v, float2* out, cudaStream_t s) {
   k_to_df<<<grid_of(n), 256, 0, s>>>(n, v, out);
   return cudaGetLastError();

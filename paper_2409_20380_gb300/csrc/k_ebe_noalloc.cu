@@ -57,7 +57,8 @@ extern "C" fem_status fem_ebe_apply_noalloc(fem_mesh* m, int precision, const vo
     return set_error(FEM_ERR_ARG, "fem_ebe_apply_noalloc: unknown precision");
   MeshView mv;
   int mesh_dev = 0;
-  mesh_view_of(m, &mv, &mesh_dev);
+  const int32_t* conn10 = nullptr;
+  mesh_view_of(m, &mv, &mesh_dev, &conn10);
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_error(FEM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
@@ -79,7 +80,15 @@ extern "C" fem_status fem_ebe_apply_noalloc(fem_mesh* m, int precision, const vo
     e = cudaMemsetAsync(red.counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return set_error(FEM_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   }
-  if (precision == FEM_FP64) {
+  if (conn10) {   // quadratic tets: their element kernel (the same scratch bound on the reduction's blocks)
+    e = precision == FEM_FP64
+            ? launch_ebe10_gated<double>(mv.E, mv.N, n_rhs, conn10, mv.rec32, mv.rec64, mv.freemask,
+                                         (const double*)p_dev, nullptr, (double*)q_dev, alpha_M, alpha_K,
+                                         ptq_dev ? &red : nullptr, nullptr, ptq_dev, nullptr, s)
+            : launch_ebe10_gated<float>(mv.E, mv.N, n_rhs, conn10, mv.rec32, mv.rec64, mv.freemask,
+                                        (const float*)p_dev, nullptr, (float*)q_dev, alpha_M, alpha_K,
+                                        ptq_dev ? &red : nullptr, nullptr, ptq_dev, nullptr, s);
+  } else if (precision == FEM_FP64) {
     e = launch_ebe<double>(mv, n_rhs, (const double*)p_dev, nullptr, (double*)q_dev, alpha_M, alpha_K,
                            ptq_dev ? &red : nullptr, nullptr, ptq_dev, s);
     if (e == cudaSuccess) e = launch_mask<double>(mv.N, n_rhs, mv.freemask, (double*)q_dev, s);

@@ -22,7 +22,7 @@ FEM_PRED_AB4, FEM_PRED_DD = 0, 1
 FEM_FIELD_U, FEM_FIELD_V, FEM_FIELD_A, FEM_FIELD_DU, FEM_FIELD_B, FEM_FIELD_GUESS = range(6)
 
 # every symbol include/fem.h declares
-EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_tune", "fem_mesh_autotune",
+EXPORTS = ("fem_opts_default", "fem_mesh_create", "fem_mesh_create_tet10", "fem_mesh_destroy", "fem_mesh_tune", "fem_mesh_autotune",
            "fem_mesh_info", "fem_mesh_split_product",
            "fem_mesh_set_regions", "fem_ebe_apply",
            "fem_ebe_apply_noalloc", "fem_mesh10_create", "fem_mesh10_destroy", "fem_ebe10_apply", "pcg10_solve",
@@ -89,6 +89,8 @@ def lib():
     sig = {
         "fem_opts_default": (None, [ctypes.POINTER(fem_opts)]),
         "fem_mesh_create": (I, [I64, P, I64, P, P, I, P, P, ctypes.POINTER(fem_time_params), P, ctypes.POINTER(P)]),
+        "fem_mesh_create_tet10": (I, [I64, P, I64, P, P, I, P, P, ctypes.POINTER(fem_time_params), P,
+                                      ctypes.POINTER(P)]),
         "fem_mesh_destroy": (I, [P]),
         "fem_mesh_tune": (I, [P, I, I]),
         "fem_mesh_split_product": (I, [P, I, P, P, P, I, P]),
@@ -179,8 +181,7 @@ def fem_opts_default(**overrides) -> fem_opts:
     return o
 
 
-def fem_mesh_create(mesh, tp, stream=None):
-    """mesh: workload.Mesh (host arrays); tp: workload.TimeParams.  Returns an opaque handle."""
+def _mesh_create(fn, mesh, tp, stream):
     xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
     conn = np.ascontiguousarray(mesh.conn, dtype=np.int32)
     mat = np.ascontiguousarray(mesh.mat_id, dtype=np.int32)
@@ -188,10 +189,21 @@ def fem_mesh_create(mesh, tp, stream=None):
     fixed = np.ascontiguousarray(mesh.fixed_dof, dtype=np.uint8)
     t = fem_time_params(tp.dt, tp.beta, tp.gamma, tp.a0, tp.a1)
     h = ctypes.c_void_p()
-    _check(lib().fem_mesh_create(xyz.shape[0], _np_ptr(xyz), conn.shape[0], _np_ptr(conn), _np_ptr(mat),
-                                 lmr.shape[0], _np_ptr(lmr), _np_ptr(fixed), ctypes.byref(t), _stream(stream),
-                                 ctypes.byref(h)))
+    _check(fn(xyz.shape[0], _np_ptr(xyz), conn.shape[0], _np_ptr(conn), _np_ptr(mat), lmr.shape[0], _np_ptr(lmr),
+              _np_ptr(fixed), ctypes.byref(t), _stream(stream), ctypes.byref(h)))
     return h
+
+
+def fem_mesh_create(mesh, tp, stream=None):
+    """mesh: workload.Mesh (host arrays); tp: workload.TimeParams.  Returns an opaque handle."""
+    assert mesh.conn.shape[1] == 4, "linear tets: conn [E][4] (fem_mesh_create_tet10 takes quadratic tets)"
+    return _mesh_create(lib().fem_mesh_create, mesh, tp, stream)
+
+
+def fem_mesh_create_tet10(mesh10, tp, stream=None):
+    """mesh10: workload.Mesh10 (conn [E][10]); the same handle type as fem_mesh_create's."""
+    assert mesh10.conn.shape[1] == 10, "quadratic tets: conn [E][10]"
+    return _mesh_create(lib().fem_mesh_create_tet10, mesh10, tp, stream)
 
 
 def fem_mesh_destroy(h):

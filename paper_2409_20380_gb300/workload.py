@@ -390,3 +390,31 @@ def tet10_mesh(mesh: Mesh) -> Mesh10:
     fixed = np.concatenate([f4, fe], axis=0).reshape(-1).astype(np.uint8)
     return Mesh10(np.ascontiguousarray(xyz), np.ascontiguousarray(conn), mesh.mat_id.copy(),
                   mesh.lam_mu_rho.copy(), np.ascontiguousarray(fixed))
+
+
+def tet10_mesh_ordered(mesh: Mesh) -> tuple[Mesh10, np.ndarray]:
+    """tet10_mesh(mesh) with all nodes, corner and edge alike, renumbered in Morton order of their position on
+    the grid of spacing h/2 (a mesher's reordering step; it makes the predictor's regions contiguous node
+    ranges).  Returns the mesh and the new id of each node of `mesh`."""
+    m10 = tet10_mesh(mesh)
+    q = np.rint(2.0 * m10.xyz / mesh.h).astype(np.int64)
+    order = np.argsort(_morton3(q[:, 0], q[:, 1], q[:, 2]), kind="stable")    # old id at each new position
+    new_id = np.empty_like(order)
+    new_id[order] = np.arange(order.size)
+    fixed = m10.fixed_dof.reshape(-1, 3)[order].reshape(-1)
+    out = Mesh10(np.ascontiguousarray(m10.xyz[order]), np.ascontiguousarray(new_id[m10.conn].astype(np.int32)),
+                 m10.mat_id, m10.lam_mu_rho, np.ascontiguousarray(fixed))
+    return out, new_id[:mesh.n_nodes]
+
+
+def region_map10(m10: Mesh10, h: float, region_nodes: int = 1024) -> np.ndarray:
+    """region_map for a tet10 mesh: free nodes in Morton order of their position on the grid of spacing h/2,
+    cut into runs of `region_nodes`; fully fixed nodes get -1."""
+    q = np.rint(2.0 * m10.xyz / h).astype(np.int64)
+    code = _morton3(q[:, 0], q[:, 1], q[:, 2])
+    free_node = m10.fixed_dof.reshape(-1, 3).min(axis=1) == 0
+    order = np.argsort(code, kind="stable")
+    order = order[free_node[order]]
+    reg = np.full(m10.n_nodes, -1, dtype=np.int32)
+    reg[order] = (np.arange(order.size) // region_nodes).astype(np.int32)
+    return reg

@@ -25,15 +25,17 @@ def torch_dev():
     return torch
 
 
-def _run_and_check(mesh, tp, sources, opts, n_steps, region_nodes=None, check_pred=True, b_tol=1e-12):
+def _run_and_check(mesh, tp, sources, opts, n_steps, region_nodes=None, check_pred=True, b_tol=1e-12,
+                   system=None, create=None, regions=None):
     """Steps the batch one step at a time and checks every step against the oracle; returns (iterations per
-    case, predictor check statistics)."""
-    sysm, A = oracle.build_system(mesh, tp)
+    case, predictor check statistics).  system (the oracle's (System, reduced A)), create (the mesh
+    constructor) and regions (a node -> region map) default to the linear-tet ones."""
+    sysm, A = system if system is not None else oracle.build_system(mesh, tp)
     N = mesh.n_nodes
-    h = fem.fem_mesh_create(mesh, tp)
-    regions = None
-    if region_nodes:
+    h = (create or fem.fem_mesh_create)(mesh, tp)
+    if region_nodes and regions is None:
         regions = wl.region_map(mesh, region_nodes)
+    if regions is not None:
         fem.fem_mesh_set_regions(h, regions)
     bt = fem.fem_batch_create(opts)
     nc = len(sources)
