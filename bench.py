@@ -1039,6 +1039,12 @@ def run_step10(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
+    # per-phase and per-kernel-class device times over --profile-steps eager steps after the timed region
+    fem.fem_batch_profile(bt, 1)
+    fem.fem_step(bt, max(1, args.profile_steps), nc)
+    prof = fem.fem_batch_profile(bt, 0)
+    npf = max(prof.get("steps", 1), 1)
+    prof_ms = {k: v / npf for k, v in prof.items() if k.endswith("_ms") or k.endswith("_launches")}
     fem.fem_batch_destroy(bt)
     r = nc
     g = torch.Generator(device="cuda").manual_seed(0)
@@ -1065,7 +1071,7 @@ def run_step10(args):
                    "element": "tet10", "graph": not args.no_graph},
         "cg_iters_per_case_step": float(iters.sum()) / (nc * args.steps),
         "max_certified_relres": float(relres.max()), "status": int(st), "clocks": clocks,
-        "tet10_product_ms": ms_prod,
+        "tet10_product_ms": ms_prod, "profile_ms_per_step": prof_ms,
         "tet10_product_note": "FP32 element kernel, q = A p for all cases, p^T q not fused, incl. zero fill and mask",
     }), flush=True)
     fem.fem_mesh_destroy(h)
@@ -1077,6 +1083,7 @@ def run_mlp(args):
     medium workload (137 regions x 16 cases).  Random samples, inputs resident; CUDA events.  A dense
     64-256-256-32 network costs 2 x 90112 flops a row forward and 2 x 163840 backward (no input gradient of
     the first layer)."""
+    import numpy as np
     import torch
     from paper_2409_20380_gb300 import build, fem
     from paper_2409_20380_gb300 import workload as wl
