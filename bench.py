@@ -94,6 +94,8 @@ def parse():
                          "3 assembled double-float")
     ap.add_argument("--snapshot-format", type=int, default=2,
                     help="predictor snapshot storage: 0 FP64, 1 FP32, 2 double-float, 3 FP32 + BF16 residual")
+    ap.add_argument("--inner-margin", type=float, default=None,
+                    help="FP32-inner solves aim at this fraction of the tolerance (default: the library's)")
     ap.add_argument("--check-every", type=int, default=8,
                     help="inner CG iterations per convergence check (graph: launches per WHILE-loop body)")
     ap.add_argument("--profile-steps", type=int, default=40,
@@ -272,6 +274,11 @@ def workload(args, rank):
     return mesh, srcs, tp, wl.region_map(mesh, args.region_nodes)
 
 
+def margin_kw(args):
+    """fem_opts override of the inner solves' aim, when given on the command line."""
+    return {} if args.inner_margin is None else {"inner_margin": args.inner_margin}
+
+
 def add_case(fem, bt, h, s):
     if hasattr(s, "steps"):
         return fem.fem_case_add_impulses(bt, h, s)
@@ -405,6 +412,7 @@ def config_dict(args, mesh=None):
     return {"workload": name, "mesh_hex": args.dims, "n_elems": mesh.n_elems, "n_nodes": mesh.n_nodes,
             "cases_per_gpu": args.cases, "precision": args.precision, "predictor": args.predictor,
             "s_max": args.s_max, "cert_product": args.cert, "region_nodes": args.region_nodes, "tol": 1e-8,
+            "inner_margin": args.inner_margin if args.inner_margin is not None else 0.1,
             "spinup_steps": args.spinup, "source": args.source, "absorbing_sides": args.absorbing,
             "cpu_predictor": args.cpu_predictor,
             "l2": "inputs larger than L2: each step streams the cases' state and the snapshot ring (>1 GB)",
@@ -439,7 +447,7 @@ def run_ours(args):
                                 predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
                                 s_max=args.s_max, snapshot_format=args.snapshot_format, tol=1e-8, cert_df=args.cert,
                                 use_graph=0 if args.no_graph else 1, check_every=args.check_every,
-                                cpu_predictor=1 if args.cpu_predictor else 0)
+                                cpu_predictor=1 if args.cpu_predictor else 0, **margin_kw(args))
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
     if args.absorbing:
@@ -955,8 +963,8 @@ def run_uneven(args):
     dims = wl.config3_dims(args.meshes)
     handles, n_el, n_nd = [], 0, 0
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
-                                tol=1e-8, snapshot_format=args.snapshot_format, fuse_meshes=0 if args.no_fuse else 1, cert_df=args.cert,
-                                use_graph=0 if args.no_graph else 1)
+                                tol=1e-8, snapshot_format=args.snapshot_format, fuse_meshes=0 if args.no_fuse else 1,
+                                cert_df=args.cert, use_graph=0 if args.no_graph else 1, **margin_kw(args))
     bt = fem.fem_batch_create(opts)
     for i, d in enumerate(dims):
         m = wl.config3_mesh(i, d)
@@ -1022,7 +1030,7 @@ def run_step10(args):
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER if args.precision == "mixed" else fem.FEM_FP64,
                                 predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
                                 s_max=args.s_max, tol=1e-8, snapshot_format=args.snapshot_format,
-                                cert_df=args.cert, use_graph=0 if args.no_graph else 1)
+                                cert_df=args.cert, use_graph=0 if args.no_graph else 1, **margin_kw(args))
     bt = fem.fem_batch_create(opts)
     nc = len(srcs)
     for s in srcs:
@@ -1045,6 +1053,7 @@ def run_step10(args):
     prof = fem.fem_batch_profile(bt, 0)
     npf = max(prof.get("steps", 1), 1)
     prof_ms = {k: v / npf for k, v in prof.items() if k.endswith("_ms") or k.endswith("_launches")}
+    last = [fem.fem_case_stats(bt, c) for c in range(nc)]
     fem.fem_batch_destroy(bt)
     r = nc
     g = torch.Generator(device="cuda").manual_seed(0)
@@ -1072,6 +1081,8 @@ def run_step10(args):
         "cg_iters_per_case_step": float(iters.sum()) / (nc * args.steps),
         "max_certified_relres": float(relres.max()), "status": int(st), "clocks": clocks,
         "tet10_product_ms": ms_prod, "profile_ms_per_step": prof_ms,
+        "last_step": {"iters": [x["iters"] for x in last], "outer": [x["outer"] for x in last],
+                      "init_relres": [x["init_relres"] for x in last]},
         "tet10_product_note": "FP32 element kernel, q = A p for all cases, p^T q not fused, incl. zero fill and mask",
     }), flush=True)
     fem.fem_mesh_destroy(h)

@@ -125,11 +125,16 @@ typedef struct {
                             adjusted after every step toward equal prediction and solve times (s_max is the
                             ceiling).  Needs FEM_PRED_DD, regions, snapshot_format 0 or 2, no fuse_meshes and
                             no learned proposal; steps run eagerly.  0 = the predictor runs on the GPU */
+  double inner_margin;   /* FEM_FP32_INNER: each inner FP32 solve is asked for the reduction that brings the
+                            certified residual to inner_margin x tol (its FP32 recursive residual tracks the FP64
+                            one to ~1e-7 of the pass's right-hand side), within [inner_tol, 0.5]; a case that
+                            still ends at or above tol takes another refinement pass, so every step stays
+                            certified below tol.  In (0, 1); default 0.1 */
 } fem_opts;
 
 /* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-6, tau 1e-6,
  * snapshot_format 2, check_every 8, refresh_every 200, cert_df 3, fuse_meshes 0, use_graph 1,
- * wait_budget 1048576, cpu_predictor 0. */
+ * wait_budget 1048576, cpu_predictor 0, inner_margin 0.1. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */

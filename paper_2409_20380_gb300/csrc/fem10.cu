@@ -601,7 +601,8 @@ fem_status pcg10_solve(fem_mesh10* m, int precision, const double* b_dev, double
     const double inner_tol = 1e-6;
     for (int outer_it = 0; outer_it <= 40 && e == cudaSuccess; ++outer_it) {
       product(x_dev, q, false);
-      if (e == cudaSuccess) e = launch_outer_resid(mv, rpad, b_dev, q, r32, red, outer, n_active, tol, inner_tol, s);
+      if (e == cudaSuccess) e = launch_outer_resid(mv, rpad, b_dev, q, r32, red, outer, n_active, tol, inner_tol,
+                                                              0.1 * tol, s);
       int h_active = 0;
       if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(ho.data(), outer, sizeof(CgCase) * rpad, cudaMemcpyDeviceToHost, s);

@@ -613,7 +613,7 @@ static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double
     int pi = w->pbeg(P_EBE64, s);
     CU(ebe_product<double>(m, rpad, x, w->q, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s, true));
     w->pend(pi, s);
-    CU(launch_outer_resid(mv, rpad, b, w->q, w->r32, red, w->outer, w->n_active, o.tol, o.inner_tol, s));
+    CU(launch_outer_resid(mv, rpad, b, w->q, w->r32, red, w->outer, w->n_active, o.tol, o.inner_tol, o.inner_margin * o.tol, s));
     w->count(2);
     CU(cudaMemcpyAsync(w->h_active, w->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(w->h_sc, w->outer, sizeof(CgCase) * rpad, cudaMemcpyDeviceToHost, s));
@@ -664,6 +664,8 @@ static fem_status check_opts(const fem_opts* o) {
   if (o->cert_df < 0 || o->cert_df > 3) return fail(FEM_ERR_ARG, "cert_df must be 0, 1, 2 or 3");
   if (o->snapshot_format < 0 || o->snapshot_format > 3) return fail(FEM_ERR_ARG, "snapshot_format must be 0 .. 3");
   if (o->wait_budget < 0) return fail(FEM_ERR_ARG, "wait_budget must be >= 0");
+  if (o->precision == FEM_FP32_INNER && !(o->inner_margin > 0.0 && o->inner_margin < 1.0))
+    return fail(FEM_ERR_ARG, "inner_margin must be in (0, 1)");
   if (o->cpu_predictor) {
     if (o->predictor != FEM_PRED_DD) return fail(FEM_ERR_ARG, "cpu_predictor needs the data-driven predictor");
     if (o->snapshot_format != 0 && o->snapshot_format != 2)
@@ -1109,10 +1111,10 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   }
   if (mv.seg) {
     CU(launch_r0_seg(mv, dt, g->b, aslot(it - 4), aslot(it - 3), aslot(it - 2), aslot(it - 1), qy, w->r32, red,
-                     w->outer, w->n_active, o.tol, o.inner_tol, s));
+                     w->outer, w->n_active, o.tol, o.inner_tol, o.inner_margin * o.tol, s));
   } else {
     CU(launch_r0(mv, g->rpad, dt, g->b, aslot(it - 4), aslot(it - 3), aslot(it - 2), aslot(it - 1), qy, w->r32, red,
-                 w->outer, w->n_active, o.tol, o.inner_tol, s));
+                 w->outer, w->n_active, o.tol, o.inner_tol, o.inner_margin * o.tol, s));
   }
   if (g->proposed) {
     // learned proposal: r0' = r0 - A32 (Y dw); a case takes it where its initial residual is smaller
@@ -1120,7 +1122,7 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     int pe = w->pbeg(P_EBE32, s);
     CU(ebe_product<float>(m, g->rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s, true));
     w->pend(pe, s);
-    CU(mlp_choose(mv, g->rpad, w->r32, w->q32, red, w->outer, w->n_active, o.tol, o.inner_tol, g->ncase, g->choose,
+    CU(mlp_choose(mv, g->rpad, w->r32, w->q32, red, w->outer, w->n_active, o.tol, o.inner_tol, o.inner_margin * o.tol, g->ncase, g->choose,
                   g->counts, s));
     CU(mlp_apply(g->n, g->rpad, g->choose, w->r32, w->q32, g->guess, g->ydelta, s));
     w->count(4);
@@ -1162,10 +1164,10 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     w->pend(pe, s);
     if (mv.seg) {
       CU(launch_cert_seg(mv, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
-                         o.inner_tol, s));
+                         o.inner_tol, o.inner_margin * o.tol, s));
     } else {
       CU(launch_cert(mv, g->rpad, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
-                     o.inner_tol, s));
+                     o.inner_tol, o.inner_margin * o.tol, s));
     }
     w->count(2);
   }
@@ -1323,10 +1325,10 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   }
   if (sg) {
     GE(launch_r0_seg(mv, dt, g->b, nullptr, nullptr, nullptr, nullptr, qy, w->r32, red, w->outer, w->n_active, o.tol,
-                     o.inner_tol, s, AV, ctl));
+                     o.inner_tol, o.inner_margin * o.tol, s, AV, ctl));
   } else {
     GE(launch_r0(mv, rpad, dt, g->b, nullptr, nullptr, nullptr, nullptr, qy, w->r32, red, w->outer, w->n_active, o.tol,
-                 o.inner_tol, s, AV, ctl, w->sc));   // (and the inner solve's starting state)
+                 o.inner_tol, o.inner_margin * o.tol, s, AV, ctl, w->sc));   // (and the inner solve's starting state)
   }
   // 4. refinement passes: WHILE (pass 0, then while a case is above tol)
   cudaGraphConditionalHandle h_pass, h_if, h_in;
@@ -1402,11 +1404,11 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
       GE(launch_dashpot<double>(m->ab, rpad, m->ab.cB / m->cK, g->x, g->qK, false, m->fm, nullptr, nullptr, nullptr,
                                 nullptr, s2));
     if (sg) {
-      GE(launch_cert_seg(mv, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol, o.inner_tol,
+      GE(launch_cert_seg(mv, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol, o.inner_tol, o.inner_margin * o.tol,
                          s2));
     } else {
       GE(launch_cert(mv, rpad, m->cM, m->cK, g->b, g->qM, g->qK, w->r32, red, w->outer, w->n_active, o.tol,
-                     o.inner_tol, s2, w->sc));
+                     o.inner_tol, o.inner_margin * o.tol, s2, w->sc));
     }
     GE(launch_pass_end(w->n_active, ctl, h_pass, kMaxPass, n_pass, s2));
   }
@@ -1723,6 +1725,7 @@ void fem_opts_default(fem_opts* o) {
   o->fuse_meshes = 0;
   o->use_graph = 1;
   o->wait_budget = kDefaultWaitBudget;
+  o->inner_margin = 0.1;
 }
 
 // Mesh set-up shared by the linear (npe 4) and quadratic (npe 10) tets: element records of the corner tets,

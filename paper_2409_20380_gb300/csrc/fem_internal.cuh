@@ -220,7 +220,7 @@ cudaError_t launch_refine_pending(const MeshView& m, int rpad, int ncase, double
 // Mixed precision helpers.
 cudaError_t launch_outer_resid(const MeshView& m, int rpad, const double* b, const double* q,
                                float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
-                               double inner_max, cudaStream_t s);
+                               double inner_max, double aim, cudaStream_t s);
 cudaError_t launch_refine_counts(const MeshView& m, int rpad, int ncase, double* x, const float* d32, CgCase* outer,
                                  const CgCase* inner, cudaStream_t s);
 
@@ -238,11 +238,11 @@ cudaError_t launch_update_seg(const MeshView& m, const T* p, const T* q, T* x, T
                               int* n_active, int maxit, cudaStream_t s);
 cudaError_t launch_r0_seg(const MeshView& m, double dt, const double* b, const double* Av4, const double* Av3,
                           const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red,
-                          CgCase* outer, int* n_active, double tol, double inner_floor, cudaStream_t s,
+                          CgCase* outer, int* n_active, double tol, double inner_floor, double aim, cudaStream_t s,
                           Ring4 avr = Ring4{}, const StepCtl* ctl = nullptr);
 cudaError_t launch_cert_seg(const MeshView& m, double cM, double cK, const double* b, const double* qM, const double* qK,
                             float* r32, Reducer red, CgCase* outer, int* n_active, double tol, double inner_floor,
-                            cudaStream_t s);
+                            double aim, cudaStream_t s);
 // x = 0 on Dirichlet DOFs and for cases with ||b|| = 0.
 template <typename T>
 cudaError_t launch_zero_b0_t(const MeshView& m, int rpad, T* x, const CgCase* sc, cudaStream_t s);
@@ -274,11 +274,11 @@ cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab,
 // r32 itself): the inner case state as the norm and first-residual passes would leave it.
 cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
                       const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
-                      int* n_active, double tol, double inner_max, cudaStream_t s, Ring4 avr = Ring4{},
-                      const StepCtl* ctl = nullptr, CgCase* inner = nullptr);
+                      int* n_active, double tol, double inner_max, double aim, cudaStream_t s,
+                      Ring4 avr = Ring4{}, const StepCtl* ctl = nullptr, CgCase* inner = nullptr);
 cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const double* b, const double* qM,
                         const double* qK, float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
-                        double inner_max, cudaStream_t s, CgCase* inner = nullptr);
+                        double inner_max, double aim, cudaStream_t s, CgCase* inner = nullptr);
 // With ctl: v_prev, v_push, Av_push and the snapshot slot come from the rings (vr, avr, ring of slots of
 // slot_stride elements) at the step read from ctl.
 cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, const double* du, const double* du_ab,
@@ -432,8 +432,8 @@ cudaError_t mlp_features(const PredView& p, int n_pairs, const float4* case_src,
 cudaError_t mlp_propose(fem_mlp* net, const float* F, int64_t rows, int n_pairs, double* dw, cudaStream_t s);
 cudaError_t mlp_to_f32(int64_t n, const double* x, float* y, cudaStream_t s);
 cudaError_t mlp_choose(const MeshView& m, int rpad, const float* r32, const float* qd, Reducer red, CgCase* outer,
-                       int* n_active, double tol, double inner_max, int ncase, int* choose, long long* counts,
-                       cudaStream_t s);
+                       int* n_active, double tol, double inner_max, double aim, int ncase, int* choose,
+                       long long* counts, cudaStream_t s);
 cudaError_t mlp_apply(int64_t n, int rpad, const int* choose, float* r32, const float* qd, double* guess,
                       const double* dy, cudaStream_t s);
 // Residual-space samples (features and the packed (W, w) of each region and case) from the ring Gram after the
@@ -495,11 +495,11 @@ __device__ __forceinline__ double f2d(float f) {
                                           ((uint64_t)(u & 0x7fffffu) << 29)));
 }
 
-// Relative reduction asked of the next inner FP32 solve: just enough for one refinement pass to reach the
-// FP64 tolerance (a tenth of tol / current relative residual), but no finer than `floor` (what FP32 can
-// deliver) and at least a halving.
-__device__ __forceinline__ double inner_target(double tol, double relres, double floor) {
-  double t = relres > 0.0 ? 0.1 * tol / relres : floor;
+// Relative reduction asked of the next inner FP32 solve: just enough for one refinement pass to reach `aim`
+// (a margin below the FP64 tolerance: aim / current relative residual), but no finer than `floor` (what FP32
+// can deliver) and at least a halving.
+__device__ __forceinline__ double inner_target(double aim, double relres, double floor) {
+  double t = relres > 0.0 ? aim / relres : floor;
   if (t > 0.5) t = 0.5;
   if (t < floor) t = floor;
   return t;

@@ -500,8 +500,9 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restr
 // where it is smaller than the plain guess's.  The last block updates the case's solver state.
 __global__ void __launch_bounds__(kVecBlock) k_choose(MeshView m, int rpad, int rshift, const float* __restrict__ r32,
                                                       const float* __restrict__ qd, Reducer red, CgCase* outer,
-                                                      int* n_active, double tol, double inner_max, int ncase,
-                                                      int* __restrict__ choose, long long* __restrict__ counts) {
+                                                      int* n_active, double tol, double inner_max, double aim,
+                                                      int ncase, int* __restrict__ choose,
+                                                      long long* __restrict__ counts) {
   double rr = 0.0;
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -529,7 +530,7 @@ __global__ void __launch_bounds__(kVecBlock) k_choose(MeshView m, int rpad, int 
         s.relres = sqrt(rrc / s.bb);
         s.relres0 = s.relres;
         s.active = rrc >= tol * tol * s.bb ? 1 : 0;
-        s.inner_tol = inner_target(tol, s.relres, inner_max);
+        s.inner_tol = inner_target(aim, s.relres, inner_max);
       }
       if (c < ncase && s.bb > 0.0) atomicAdd(reinterpret_cast<unsigned long long*>(counts + (take ? 0 : 1)), 1ull);
     }
@@ -702,16 +703,16 @@ cudaError_t mlp_to_f32(int64_t n, const double* x, float* y, cudaStream_t s) {
 }
 
 cudaError_t mlp_choose(const MeshView& m, int rpad, const float* r32, const float* qd, Reducer red, CgCase* outer,
-                       int* n_active, double tol, double inner_max, int ncase, int* choose, long long* counts,
-                       cudaStream_t s) {
+                       int* n_active, double tol, double inner_max, double aim, int ncase, int* choose,
+                       long long* counts, cudaStream_t s) {
   int rs = 0;
   while ((1 << rs) < rpad) ++rs;
   int64_t items = m.N << rs;
   int grid = (int)((items + kVecBlock - 1) / kVecBlock);
   if (grid > vec_grid_cap()) grid = vec_grid_cap();
   if (grid < 1) grid = 1;
-  k_choose<<<grid, kVecBlock, 0, s>>>(m, rpad, rs, r32, qd, red, outer, n_active, tol, inner_max, ncase, choose,
-                                      counts);
+  k_choose<<<grid, kVecBlock, 0, s>>>(m, rpad, rs, r32, qd, red, outer, n_active, tol, inner_max, aim, ncase,
+                                      choose, counts);
   return cudaGetLastError();
 }
 

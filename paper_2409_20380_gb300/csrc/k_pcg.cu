@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_update_defer(MeshView m, int r
 __global__ void __launch_bounds__(kVecBlock, 3) k_outer_resid(MeshView m, int rpad, int rshift, const double* __restrict__ b,
                                                         const double* __restrict__ q, float* __restrict__ r32,
                                                         Reducer red, CgCase* outer, int* n_active, double tol,
-                                                        double inner_max) {
+                                                        double inner_max, double aim) {
   double rr = 0.0;
   const int64_t total = m.N << rshift;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(kVecBlock, 3) k_outer_resid(MeshView m, int rp
       s.outer += 1;
       if (!isfinite(rrc)) s.status = FEM_ERR_NONFINITE;
       s.active = (s.status == FEM_OK && s.bb > 0.0 && rrc >= tol * tol * s.bb) ? 1 : 0;
-      s.inner_tol = inner_target(tol, s.relres, inner_max);
+      s.inner_tol = inner_target(aim, s.relres, inner_max);
     }
     __syncthreads();
     count_active(outer, rpad, n_active);
@@ -506,10 +506,11 @@ cudaError_t launch_refine_pending(const MeshView& m, int rpad, int ncase, double
 }
 
 cudaError_t launch_outer_resid(const MeshView& m, int rpad, const double* b, const double* q, float* r32,
-                               Reducer red, CgCase* outer, int* n_active, double tol, double inner_max,
+                               Reducer red, CgCase* outer, int* n_active, double tol, double inner_max, double aim,
                                cudaStream_t s) {
   const int rs = log2i(rpad);
-  k_outer_resid<<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, b, q, r32, red, outer, n_active, tol, inner_max);
+  k_outer_resid<<<vec_grid(m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, b, q, r32, red, outer, n_active, tol, inner_max,
+                                                          aim);
   return cudaGetLastError();
 }
 

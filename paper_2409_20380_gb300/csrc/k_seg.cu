@@ -199,7 +199,7 @@ __global__ void k_update_seg(MeshView m, const T* __restrict__ p, const T* __res
 __global__ void k_r0_seg(MeshView m, double h, const double* __restrict__ b, const double* __restrict__ Av4,
                          const double* __restrict__ Av3, const double* __restrict__ Av2, const double* __restrict__ Av1,
                          const float* __restrict__ qy, float* __restrict__ r32, Reducer red, CgCase* outer,
-                         int* n_active, double tol, double inner_floor, Ring4 avr, const StepCtl* ctl) {
+                         int* n_active, double tol, double inner_floor, double aim, Ring4 avr, const StepCtl* ctl) {
   if (ctl) {   // A v^{it-4} .. A v^{it-1} in ring slots it .. it+3 (mod 4)
     const int it = ctl->it;
     Av4 = avr.p[it & 3], Av3 = avr.p[(it + 1) & 3], Av2 = avr.p[(it + 2) & 3], Av1 = avr.p[(it + 3) & 3];
@@ -244,7 +244,7 @@ __global__ void k_r0_seg(MeshView m, double h, const double* __restrict__ b, con
       s.relres0 = s.relres;
       s.status = (isfinite(bbc) && isfinite(rrc)) ? FEM_OK : FEM_ERR_NONFINITE;
       s.active = (s.status == FEM_OK && bbc > 0.0 && rrc >= tol * tol * bbc) ? 1 : 0;
-      s.inner_tol = inner_target(tol, s.relres, inner_floor);
+      s.inner_tol = inner_target(aim, s.relres, inner_floor);
     }
     __syncthreads();
     count_active_seg(outer, nc, n_active);
@@ -253,7 +253,7 @@ __global__ void k_r0_seg(MeshView m, double h, const double* __restrict__ b, con
 
 __global__ void k_cert_seg(MeshView m, double cM, double cK, const double* __restrict__ b,
                            const double* __restrict__ qM, const double* __restrict__ qK, float* __restrict__ r32,
-                           Reducer red, CgCase* outer, int* n_active, double tol, double inner_floor) {
+                           Reducer red, CgCase* outer, int* n_active, double tol, double inner_floor, double aim) {
   extern __shared__ double acc[];
   const int nc = m.nseg;
   zero_acc(acc, nc);
@@ -283,7 +283,7 @@ __global__ void k_cert_seg(MeshView m, double cM, double cK, const double* __res
       s.outer += 1;
       if (!isfinite(rrc)) s.status = FEM_ERR_NONFINITE;
       s.active = (s.status == FEM_OK && s.bb > 0.0 && rrc >= tol * tol * s.bb) ? 1 : 0;
-      s.inner_tol = inner_target(tol, s.relres, inner_floor);
+      s.inner_tol = inner_target(aim, s.relres, inner_floor);
     }
     __syncthreads();
     count_active_seg(outer, nc, n_active);
@@ -324,18 +324,18 @@ cudaError_t launch_update_seg(const MeshView& m, const T* p, const T* q, T* x, T
 }
 cudaError_t launch_r0_seg(const MeshView& m, double dt, const double* b, const double* Av4, const double* Av3,
                           const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red,
-                          CgCase* outer, int* n_active, double tol, double inner_floor, cudaStream_t s, Ring4 avr,
-                          const StepCtl* ctl) {
+                          CgCase* outer, int* n_active, double tol, double inner_floor, double aim, cudaStream_t s,
+                          Ring4 avr, const StepCtl* ctl) {
   k_r0_seg<<<seg_grid(m.N), kVecBlock, sizeof(double) * 2 * m.nseg, s>>>(m, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32,
-                                                                          red, outer, n_active, tol, inner_floor, avr,
-                                                                          ctl);
+                                                                          red, outer, n_active, tol, inner_floor, aim,
+                                                                          avr, ctl);
   return cudaGetLastError();
 }
 cudaError_t launch_cert_seg(const MeshView& m, double cM, double cK, const double* b, const double* qM, const double* qK,
                             float* r32, Reducer red, CgCase* outer, int* n_active, double tol, double inner_floor,
-                            cudaStream_t s) {
+                            double aim, cudaStream_t s) {
   k_cert_seg<<<seg_grid(m.N), kVecBlock, sizeof(double) * m.nseg, s>>>(m, cM, cK, b, qM, qK, r32, red, outer,
-                                                                        n_active, tol, inner_floor);
+                                                                        n_active, tol, inner_floor, aim);
   return cudaGetLastError();
 }
 

@@ -737,7 +737,7 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_r0(MeshView m, int rpad, int r
                                                const double* __restrict__ Av2, const double* __restrict__ Av1,
                                                const float* __restrict__ qy, float* __restrict__ r32, Reducer red,
                                                CgCase* outer, int* n_active, double tol, double inner_max,
-                                               Ring4 avr, const StepCtl* ctl, CgCase* inner) {
+                                               double aim, Ring4 avr, const StepCtl* ctl, CgCase* inner) {
   if (ctl) {   // A v^{it-4} .. A v^{it-1} in ring slots it .. it+3 (mod 4)
     const int it = ctl->it;
     Av4 = avr.p[it & 3], Av3 = avr.p[(it + 1) & 3], Av2 = avr.p[(it + 2) & 3], Av1 = avr.p[(it + 3) & 3];
@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_r0(MeshView m, int rpad, int r
       s.status = (isfinite(bbc) && isfinite(rrc)) ? FEM_OK : FEM_ERR_NONFINITE;
       // estimate only: the certificate is the FP64 residual computed after the solve
       s.active = (s.status == FEM_OK && bbc > 0.0 && rrc >= tol * tol * bbc) ? 1 : 0;
-      s.inner_tol = inner_target(tol, s.relres, inner_max);
+      s.inner_tol = inner_target(aim, s.relres, inner_max);
       if (inner) init_inner(inner[c], s, rrc, red.out[2 * rpad + c]);
     }
     __syncthreads();
@@ -803,7 +803,7 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_cert(MeshView m, int rpad, int
                                                  const double* __restrict__ b, const double* __restrict__ qM,
                                                  const double* __restrict__ qK, float* __restrict__ r32, Reducer red,
                                                  CgCase* outer, int* n_active, double tol, double inner_max,
-                                                 CgCase* inner) {
+                                                 double aim, CgCase* inner) {
   double rr = 0.0;
   float zr = 0.f;
   const int64_t total = m.N << rshift;
@@ -854,7 +854,7 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_cert(MeshView m, int rpad, int
       s.outer += 1;
       if (!isfinite(rrc)) s.status = FEM_ERR_NONFINITE;
       s.active = (s.status == FEM_OK && s.bb > 0.0 && rrc >= tol * tol * s.bb) ? 1 : 0;
-      s.inner_tol = inner_target(tol, s.relres, inner_max);
+      s.inner_tol = inner_target(aim, s.relres, inner_max);
       if (inner) init_inner(inner[c], s, rrc, red.out[rpad + c]);
     }
     __syncthreads();
@@ -1008,20 +1008,20 @@ cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab,
 
 cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
                       const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
-                      int* n_active, double tol, double inner_max, cudaStream_t s, Ring4 avr, const StepCtl* ctl,
-                      CgCase* inner) {
+                      int* n_active, double tol, double inner_max, double aim, cudaStream_t s, Ring4 avr,
+                      const StepCtl* ctl, CgCase* inner) {
   const int rs = log2i(rpad);
   k_r0<<<grid_resident((const void*)k_r0, kVecBlock, m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer,
-                                                n_active, tol, inner_max, avr, ctl, inner);
+                                                n_active, tol, inner_max, aim, avr, ctl, inner);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const double* b, const double* qM,
                         const double* qK, float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
-                        double inner_max, cudaStream_t s, CgCase* inner) {
+                        double inner_max, double aim, cudaStream_t s, CgCase* inner) {
   const int rs = log2i(rpad);
   k_cert<<<grid_resident((const void*)k_cert, kVecBlock, m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, cM, cK, b, qM, qK, r32, red, outer, n_active, tol,
-                                                inner_max, inner);
+                                                inner_max, aim, inner);
   return cudaGetLastError();
 }
 

@@ -54,7 +54,7 @@ class fem_opts(ctypes.Structure):
                 ("tau", ctypes.c_double), ("snapshot_format", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("refresh_every", ctypes.c_int), ("cert_df", ctypes.c_int), ("fuse_meshes", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("wait_budget", ctypes.c_int),
-                ("cpu_predictor", ctypes.c_int)]
+                ("cpu_predictor", ctypes.c_int), ("inner_margin", ctypes.c_double)]
 
 
 class fem_profile(ctypes.Structure):

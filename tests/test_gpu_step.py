@@ -320,6 +320,30 @@ def test_step_benchmark_settings(torch_dev, s_max):
     assert stats.n >= 16 * (s_max + 20) * 3 and stats.elementwise > 0, (stats.n, stats.elementwise)
 
 
+@pytest.mark.parametrize("margin", [0.5, 0.9])
+def test_step_inner_margin(torch_dev, margin):
+    """Inner FP32 solves aimed at a larger fraction of the tolerance (fem_opts.inner_margin): every step is
+    still certified below tol by the oracle's CSR A (a case that ends at or above tol takes another
+    refinement pass), and the CG iterations do not exceed those of the default aim of 0.1 on the same steps."""
+    mesh = wl.config4_mesh(16, 16, 12)
+    tp = wl.config4_time_params()
+    srcs = wl.config4_sources(mesh, 8)
+    its = {}
+    for m in (0.1, margin):
+        opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=16,
+                                    cert_df=3, snapshot_format=2, use_graph=1, inner_margin=m)
+        it, _ = _run_and_check(mesh, tp, srcs, opts, 40, region_nodes=1024, b_tol=1e-11)
+        its[m] = int(it.sum())
+    assert its[margin] <= its[0.1], its
+
+
+def test_inner_margin_out_of_range_rejected(torch_dev):
+    for m in (0.0, 1.0, -0.5):
+        with pytest.raises(fem.FemError) as ei:
+            fem.fem_batch_create(fem.fem_opts_default(precision=fem.FEM_FP32_INNER, inner_margin=m))
+        assert ei.value.status == fem.FEM_ERR_ARG
+
+
 def test_step_matches_independent_oracle_run(torch_dev):
     """GPU and oracle time histories, each solved to 1e-12, agree to 1e-9 after 50 steps."""
     mesh = wl.config1_mesh()
