@@ -135,8 +135,8 @@ def parse():
         a.cases = 8 if large else 16
     if a.dims is None:
         a.dims = "256,256,128" if large else "64,64,32"
-    if a.s_max is None:
-        a.s_max = 16 if large else 32
+    if a.s_max is None:     # (10-node tets: s = 32 overfits on the medium box, one case's guess 7x worse than AB4)
+        a.s_max = 16 if large or a.element == "tet10" else 32
     if a.comparator_steps is None:     # (large: the plain FP64 comparators need minutes; run them on request)
         a.comparator_steps = 0 if large else 4
     if a.comparator_spinup is None:
@@ -412,7 +412,7 @@ def config_dict(args, mesh=None):
     return {"workload": name, "mesh_hex": args.dims, "n_elems": mesh.n_elems, "n_nodes": mesh.n_nodes,
             "cases_per_gpu": args.cases, "precision": args.precision, "predictor": args.predictor,
             "s_max": args.s_max, "cert_product": args.cert, "region_nodes": args.region_nodes, "tol": 1e-8,
-            "inner_margin": args.inner_margin if args.inner_margin is not None else 0.1,
+            "inner_margin": args.inner_margin if args.inner_margin is not None else 0.5,
             "spinup_steps": args.spinup, "source": args.source, "absorbing_sides": args.absorbing,
             "cpu_predictor": args.cpu_predictor,
             "l2": "inputs larger than L2: each step streams the cases' state and the snapshot ring (>1 GB)",
@@ -1026,6 +1026,7 @@ def run_step10(args):
         s.node = int(new_id[s.node])
     log(f"tet10 mesh: {m10.n_elems} elements, {m10.n_nodes} nodes")
     h = fem.fem_mesh_create_tet10(m10, tp)
+    fem.fem_mesh_tune(h, 8 if args.variant == 8 else 0, 0)   # the element kernel, or the assembled blocks
     fem.fem_mesh_set_regions(h, wl.region_map10(m10, mesh.h, args.region_nodes))
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER if args.precision == "mixed" else fem.FEM_FP64,
                                 predictor=fem.FEM_PRED_DD if args.predictor == "dd" else fem.FEM_PRED_AB4,
@@ -1077,7 +1078,8 @@ def run_step10(args):
                                f"{m10.n_nodes} nodes, {nc} cases on one mesh, "
                                f"{'FP32-inner/FP64-refined' if args.precision == 'mixed' else 'FP64'} block-Jacobi "
                                f"EBE-PCG, {'data-driven predictor s=%d' % args.s_max if args.predictor == 'dd' else 'AB4'}",
-                   "element": "tet10", "graph": not args.no_graph},
+                   "element": "tet10", "graph": not args.no_graph,
+                   "product": "assembled 3x3 blocks" if args.variant == 8 else "tet10 element kernel"},
         "cg_iters_per_case_step": float(iters.sum()) / (nc * args.steps),
         "max_certified_relres": float(relres.max()), "status": int(st), "clocks": clocks,
         "tet10_product_ms": ms_prod, "profile_ms_per_step": prof_ms,

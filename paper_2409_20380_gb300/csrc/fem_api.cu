@@ -1725,7 +1725,7 @@ void fem_opts_default(fem_opts* o) {
   o->fuse_meshes = 0;
   o->use_graph = 1;
   o->wait_budget = kDefaultWaitBudget;
-  o->inner_margin = 0.1;
+  o->inner_margin = 0.5;
 }
 
 // Mesh set-up shared by the linear (npe 4) and quadratic (npe 10) tets: element records of the corner tets,

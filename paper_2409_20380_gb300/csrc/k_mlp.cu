@@ -42,6 +42,8 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 // C = A B^T on the tensor cores.  A [M][K] and B [N][K] are BF16 with K contiguous; FP32 accumulation.
 // M % 64 == 0, N % 32 == 0, K % 32 == 0, lda/ldb % 8 == 0 (16-byte rows of the staged tiles).  A CTA of
 // 4 warps computes a 64 x 32 tile; warp w owns rows 16w..16w+15 and all 32 columns (4 m16n8 tiles).
+// With gridDim.z > 1 (split contraction, plain epilogue only) CTA z sums its share of K and adds it into C,
+// which the caller has zeroed.
 // ------------------------------------------------------------------------------------------------------
 enum { EPI_BIAS = 0, EPI_GELU = 1, EPI_GELU_BWD = 2, EPI_PLAIN = 3 };
 
@@ -83,7 +85,8 @@ __global__ void __launch_bounds__(128) k_gemm_tn(GemmArgs g) {
   for (int j = 0; j < 4; ++j)
 #pragma unroll
     for (int e = 0; e < 4; ++e) acc[j][e] = 0.0f;
-  for (int k0 = 0; k0 < g.K; k0 += 32) {
+  const int kper = g.K / (int)gridDim.z, kbeg = (int)blockIdx.z * kper;
+  for (int k0 = kbeg; k0 < kbeg + kper; k0 += 32) {
 #pragma unroll
     for (int v = tid; v < 256; v += 128) {
       const int r = v >> 2, cv = (v & 3) * 8;
@@ -128,7 +131,13 @@ __global__ void __launch_bounds__(128) k_gemm_tn(GemmArgs g) {
         out = r < g.m_valid ? v * gelu_grad_f(g.zin[(int64_t)r * g.ldz + c]) : 0.0f;
         a = out;
       }
-      if (g.C) g.C[(int64_t)r * g.c_rs + (int64_t)c * g.c_cs] = out;
+      if (g.C) {
+        float* dst = g.C + (int64_t)r * g.c_rs + (int64_t)c * g.c_cs;
+        if (gridDim.z > 1)
+          atomicAdd(dst, out);
+        else
+          *dst = out;
+      }
       if (g.act) g.act[(int64_t)r * g.ld_act + c] = __float2bfloat16_rn(a);
       if (g.actT) g.actT[(int64_t)c * g.ld_actT + r] = __float2bfloat16_rn(a);
     }
@@ -137,7 +146,21 @@ __global__ void __launch_bounds__(128) k_gemm_tn(GemmArgs g) {
 template <int EPI>
 cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
   if (g.M % 64 || g.N % 32 || g.K % 32 || g.lda % 8 || g.ldb % 8) return cudaErrorInvalidValue;
-  dim3 grid(g.M / 64, g.N / 32);
+  dim3 grid(g.M / 64, g.N / 32, 1);
+  // A contraction long against the output (the weight gradients: K = the batch) is split so that the grid
+  // covers the SMs twice, each share at least 8 of the 32-wide K steps; C (dense M x N) is zeroed first.
+  if (EPI == EPI_PLAIN && g.C && !g.act && !g.actT &&
+      ((g.c_rs == g.N && g.c_cs == 1) || (g.c_rs == 1 && g.c_cs == g.M))) {
+    const int steps = g.K / 32, tiles = (int)(grid.x * grid.y), want = 2 * sm_count();
+    int ks = 1;
+    for (int d = 2; d <= steps / 8 && tiles * ks < want; ++d)
+      if (steps % d == 0) ks = d;
+    if (ks > 1) {
+      cudaError_t e = cudaMemsetAsync(g.C, 0, sizeof(float) * (size_t)g.M * g.N, s);
+      if (e != cudaSuccess) return e;
+      grid.z = ks;
+    }
+  }
   k_gemm_tn<EPI><<<grid, 128, 0, s>>>(g);
   return cudaGetLastError();
 }

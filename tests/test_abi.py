@@ -36,7 +36,7 @@ def test_defaults_and_errors_without_gpu(libfem):
     o = fem.fem_opts_default()
     assert o.tol == 1e-8 and o.precision == fem.FEM_FP64 and o.s_max == 32
     # the last fields read back their documented defaults (the binding's struct layout matches the header's)
-    assert o.wait_budget == 1048576 and o.cpu_predictor == 0 and o.inner_margin == 0.1
+    assert o.wait_budget == 1048576 and o.cpu_predictor == 0 and o.inner_margin == 0.5
     # argument errors are reported without touching a device
     st = libfem.fem_mesh_destroy(None)
     assert st == fem.FEM_ERR_ARG

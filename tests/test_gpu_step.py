@@ -324,7 +324,7 @@ def test_step_benchmark_settings(torch_dev, s_max):
 def test_step_inner_margin(torch_dev, margin):
     """Inner FP32 solves aimed at a larger fraction of the tolerance (fem_opts.inner_margin): every step is
     still certified below tol by the oracle's CSR A (a case that ends at or above tol takes another
-    refinement pass), and the CG iterations do not exceed those of the default aim of 0.1 on the same steps."""
+    refinement pass), and the CG iterations do not exceed those of an aim of 0.1 on the same steps."""
     mesh = wl.config4_mesh(16, 16, 12)
     tp = wl.config4_time_params()
     srcs = wl.config4_sources(mesh, 8)
