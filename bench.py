@@ -51,7 +51,7 @@ def log(msg):
     print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=150)
@@ -127,7 +127,7 @@ def parse():
     ap.add_argument("--collect-from", type=int, default=0,
                     help="learned proposal: collect training samples from this step on (0: every step)")
     ap.add_argument("--batch", type=int, default=4096)
-    a = ap.parse_args()
+    a = ap.parse_args(argv)
     if a.learned or a.uneven or a.kernel in ("ebe10", "pcg10") or a.element == "tet10":
         a.config = "medium"          # these modes run on medium-size meshes
     large = a.config == "large"
@@ -151,6 +151,26 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def rank_first_case(rank, cases):
+    """Cases are sharded by rank: rank k steps the recipe's cases k * cases .. (k + 1) * cases - 1."""
+    return rank * cases
+
+
+def max_over_ranks(x, ws, device):
+    """The largest value of x over the job's ranks (the slowest rank's time); x itself for one rank."""
+    if ws == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.item()
+
+
+def job_value(ws, cases_per_rank, steps, t_max_ms):
+    """Whole-job case-steps per second: all ranks' case-steps over the slowest rank's time."""
+    return ws * cases_per_rank * steps / (t_max_ms / 1e3)
 
 
 def peaks():
@@ -267,10 +287,11 @@ def workload(args, rank):
     if args.source == "impulses":
         npts = args.impulse_points or max(1, int(0.07 * wl.surface_nodes(mesh).size))
         cfg = 4 if args.config == "large" else 2
-        srcs = [wl.random_impulses(mesh, wl.rng_for(cfg, 0, rank * args.cases + c, 4), npts, args.impulse_steps)
+        first = rank_first_case(rank, args.cases)
+        srcs = [wl.random_impulses(mesh, wl.rng_for(cfg, 0, first + c, 4), npts, args.impulse_steps)
                 for c in range(args.cases)]
     else:
-        srcs = make_sources(args.config, mesh, args.cases, first_case=rank * args.cases)
+        srcs = make_sources(args.config, mesh, args.cases, first_case=rank_first_case(rank, args.cases))
     return mesh, srcs, tp, wl.region_map(mesh, args.region_nodes)
 
 
@@ -492,12 +513,8 @@ def run_ours(args):
         _, it_k, _ = fem.fem_step(bt, 1, nc)
         working32 += int(it_k.max()) + (1 if args.predictor == "dd" else 0)
     prof = fem.fem_batch_profile(bt, 0)
-    t_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = t.item()
-    value = ws * nc * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(ms, ws, "cuda")
+    value = job_value(ws, nc, args.steps, t_max)
     # ---- end to end through the public API: H2D loads, step, D2H displacements ----
     N = mesh.n_nodes
     step0 = fem.fem_batch_steps(bt)
@@ -531,12 +548,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier()
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = t.item()
+    e2e_s = max_over_ranks(e2e_s, ws, "cuda")
     log("end-to-end region done")
-    e2e = {"value": ws * nc * ne / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nc * 3 * 8 if ricker else 0,
+    e2e = {"value": job_value(ws, nc, ne, 1e3 * e2e_s), "unit": UNIT, "h2d_bytes_per_step": nc * 3 * 8 if ricker else 0,
            "d2h_bytes_per_step": nc * N * 3 * 8, "steps": ne}
     # ---- plain FP64 PCG with Adams-Bashforth on the same state: with the EBE product (the comparator) and
     # with the assembled 3x3-block product (the CRS-style form the paper compares the EBE with) ----
