@@ -94,6 +94,8 @@ def parse(argv=None):
                          "3 assembled double-float")
     ap.add_argument("--snapshot-format", type=int, default=2,
                     help="predictor snapshot storage: 0 FP64, 1 FP32, 2 double-float, 3 FP32 + BF16 residual")
+    ap.add_argument("--inner-product", default="fp32", choices=["fp32", "tc"],
+                    help="inner CG products: FP32 element kernels, or FP16 hex element matrices on the tensor cores")
     ap.add_argument("--inner-margin", type=float, default=None,
                     help="FP32-inner solves aim at this fraction of the tolerance (default: the library's)")
     ap.add_argument("--check-every", type=int, default=8,
@@ -296,8 +298,11 @@ def workload(args, rank):
 
 
 def margin_kw(args):
-    """fem_opts override of the inner solves' aim, when given on the command line."""
-    return {} if args.inner_margin is None else {"inner_margin": args.inner_margin}
+    """fem_opts overrides of the inner solves (their aim, their CG product) given on the command line."""
+    kw = {} if args.inner_margin is None else {"inner_margin": args.inner_margin}
+    if args.inner_product == "tc":
+        kw["inner_product"] = 1
+    return kw
 
 
 def add_case(fem, bt, h, s):
@@ -434,6 +439,8 @@ def config_dict(args, mesh=None):
             "cases_per_gpu": args.cases, "precision": args.precision, "predictor": args.predictor,
             "s_max": args.s_max, "cert_product": args.cert, "region_nodes": args.region_nodes, "tol": 1e-8,
             "inner_margin": args.inner_margin if args.inner_margin is not None else 0.5,
+            "inner_product": "FP16 hex element matrices on the tensor cores" if args.inner_product == "tc"
+                             else "FP32 element kernels",
             "spinup_steps": args.spinup, "source": args.source, "absorbing_sides": args.absorbing,
             "cpu_predictor": args.cpu_predictor,
             "l2": "inputs larger than L2: each step streams the cases' state and the snapshot ring (>1 GB)",
@@ -615,6 +622,26 @@ def run_ours(args):
                  "alg_bytes_per_launch": bytes32,
                  "alg_flops_per_launch": fl, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak,
                  "hbm_peak_kind": peak_kind, "ms_per_step": prof["ebe32_ms"] / max(prof["steps"], 1)}
+    if args.inner_product == "tc" and prof.get("ebe16_launches", 0) > 0:
+        # the inner CG products on the tensor cores: per hex a 608-byte FP16 matrix record and its corner
+        # table (16 bytes), p read and q written in FP32; four mma.sync a hex and 8 cases
+        H = E // 6
+        working16 = max(1, working32 - (args.profile_steps if args.predictor == "dd" else 0))
+        avg16 = prof["ebe16_ms"] / max(1, min(working16, prof["ebe16_launches"]))
+        bytes16 = H * (608 + 16) + rpad * N * 3 * (4 + 4)
+        fl16 = H * (rpad // 8) * 2 * (16 * 8 * 16 + 16 * 8 * 8) * 2
+        gbs = bytes16 / (avg16 * 1e-3) / 1e9
+        inner = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                 "peak_kind": peak_kind,
+                 "traffic": ncu_traffic("ebe_tc_f16_%s%d" % (args.config, rpad), EBE_SOURCES),
+                 "kernel": ("k_ebe_hex_tc<true> (inner PCG product A p with FP16 hex element matrices on the tensor "
+                            "cores (mma.sync), FP32 vectors; %d cases)" % rpad),
+                 "avg_launch_ms": avg16, "launches": working16, "launches_issued": prof["ebe16_launches"],
+                 "launch_note": "launches that did work (the slowest case's inner iterations per step)",
+                 "alg_bytes_per_launch": bytes16, "alg_tensor_flops_per_launch": fl16,
+                 "tensor_tflops": fl16 / (avg16 * 1e-3) / 1e12,
+                 "ms_per_step": prof["ebe16_ms"] / max(prof["steps"], 1),
+                 "correction_product_ms_per_step": prof["ebe32_ms"] / max(prof["steps"], 1)}
     cert = None
     if prof["ebe64_launches"] > 0:
         avg = prof["ebe64_ms"] / prof["ebe64_launches"]
@@ -675,8 +702,10 @@ def run_ours(args):
                               ("predict_ms", "rhs_ms", "solve_ms", "update_ms")},
         "kernel_ms_per_step": {"ebe32": prof["ebe32_ms"] / max(prof["steps"], 1),
                                "ebe64": prof["ebe64_ms"] / max(prof["steps"], 1),
-                               "cg_vec": prof["cg_vec_ms"] / max(prof["steps"], 1)},
+                               "cg_vec": prof["cg_vec_ms"] / max(prof["steps"], 1),
+                               "ebe16": prof["ebe16_ms"] / max(prof["steps"], 1)},
         "kernel_launches_per_step": {"ebe32": prof["ebe32_launches"] / max(prof["steps"], 1),
+                                     "ebe16": prof["ebe16_launches"] / max(prof["steps"], 1),
                                      "ebe64": prof["ebe64_launches"] / max(prof["steps"], 1),
                                      "cg_vec": prof["cg_vec_launches"] / max(prof["steps"], 1),
                                      "all": prof["kernel_launches"] / max(prof["steps"], 1)},
@@ -725,6 +754,8 @@ def run_kernel(args):
     w = 4 if args.kernel_precision == "fp32" else 8
     E, N = mesh.n_elems, mesh.n_nodes
     bytes_launch = E * (16 + 12 * w) + r * N * 3 * 2 * w
+    if args.variant == 9 and args.kernel_precision == "fp32":   # FP16 hex records and corner tables
+        bytes_launch = (E // 6) * (608 + 16) + r * N * 3 * 2 * w
     info = fem.fem_mesh_info(h)
     print(json.dumps({"kernel": "ebe", "precision": args.kernel_precision, "dims": args.dims, "cases": r,
                       "variant": args.variant, "hex_per_tile": args.hex_per_tile, "mesh_info": info,

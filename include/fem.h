@@ -57,6 +57,16 @@ enum {
                             dot-product accumulation and refinement update; certified in FP64 */
 };
 
+/* Product of the inner FP32 solve's CG iterations (FEM_FP32_INNER). */
+enum {
+  FEM_INNER_FP32 = 0,    /* the FP32 element-by-element kernels (the default) */
+  FEM_INNER_TC = 1       /* per-hex 24 x 24 element matrices of A in FP16 (the element data in reduced precision),
+                            applied on the tensor cores with FP32 accumulation: ~2.4e-4 relative error in a
+                            product, so each inner solve is asked for at most a 1e-3 reduction and the FP64
+                            refinement passes carry the solve to tol.  Hex-patch meshes, 8, 16 or 32 cases a
+                            group; the predictor's correction and all other products stay FP32/FP64 */
+};
+
 /* Initial-guess predictor used by fem_step. */
 enum {
   FEM_PRED_AB4 = 0,      /* Adams-Bashforth 4 (Section 3.2) */
@@ -131,11 +141,13 @@ typedef struct {
                             still ends at or above tol takes another refinement pass, so every step stays
                             certified below tol.  In (0, 1); default 0.5 (measured: 0.1 cost 3.5% more time on the
                             large workload for the same certificate) */
+  int inner_product;     /* FEM_INNER_FP32 or FEM_INNER_TC (see above); the FP16 hex matrices (608 bytes a hex)
+                            are built on the group's first step.  Default FEM_INNER_FP32 */
 } fem_opts;
 
 /* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-6, tau 1e-6,
  * snapshot_format 2, check_every 8, refresh_every 200, cert_df 3, fuse_meshes 0, use_graph 1,
- * wait_budget 1048576, cpu_predictor 0, inner_margin 0.5. */
+ * wait_budget 1048576, cpu_predictor 0, inner_margin 0.5, inner_product FEM_INNER_FP32. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */
@@ -460,6 +472,8 @@ typedef struct {
   long long cg_vec_launches;         /* CG direction + update kernels */
   double cg_vec_ms;
   double predict_ms, rhs_ms, solve_ms, update_ms;  /* phases of fem_step, summed over steps */
+  long long ebe16_launches;          /* inner CG products with inner_product FEM_INNER_TC (FP16 hex matrices) */
+  double ebe16_ms;
 } fem_profile;
 
 /* enable = 1: reset and start profiling (launch counts and per-class device times from CUDA events around

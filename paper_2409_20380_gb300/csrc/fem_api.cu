@@ -69,7 +69,7 @@ static int next_pow2(int r) {
 // ------------------------------------------------------------------------------------------------------
 // Event-based device-time profiler (CUDA events on the working stream, resolved at sync points).
 // ------------------------------------------------------------------------------------------------------
-enum ProfClass { P_EBE32 = 0, P_EBE64, P_VEC, P_PREDICT, P_RHS, P_SOLVE, P_UPDATE, P_NCLASS };
+enum ProfClass { P_EBE32 = 0, P_EBE64, P_VEC, P_PREDICT, P_RHS, P_SOLVE, P_UPDATE, P_EBE16, P_NCLASS };
 
 struct Prof {
   bool on = false;       // counting launches and steps
@@ -164,6 +164,7 @@ struct Workspace {
   int* h_active = nullptr;   // pinned
   CgCase* h_sc = nullptr;    // pinned
   Prof* prof = nullptr;      // not owned; null = not profiled
+  bool tc = false;           // FP32 CG products of the inner solve on the tensor cores (fem_opts.inner_product)
   void count(int k = 1) {
     if (prof && prof->on) prof->launches += k;
   }
@@ -268,6 +269,7 @@ struct fem_mesh {
   int ebe_variant = 0;             // 0 auto, 1 generic, 2 tiled hex, 3 staged, 4 case-major, 5/6 packed staged,
                                    // 7 hex element matrices, 8 assembled 3x3 blocks (CRS-style comparator)
   float* hexmat = nullptr;         // [ceil(H / 2)][300][2] hex matrices for (cM, cK) (built on first use)
+  unsigned char* hm16 = nullptr;   // [H] 608-byte FP16 hex matrices for (cM, cK) (variant 9; built on first use)
   int hex_per_tile = 0;            // 0 auto
   // autotuned choice per (FP32 / FP64 product, log2 of the case count); variant 0 = not tuned
   struct Tuned {
@@ -382,9 +384,24 @@ struct fem_mesh {
     hexmat = buf;
     return FEM_OK;
   }
+  fem_status ensure_hm16(cudaStream_t s) {
+    if (hm16 || !hex) return FEM_OK;
+    const int64_t H = E / 6;
+    unsigned char* buf = nullptr;
+    CHK(dalloc(&buf, (size_t)kHm16RecBytes * (size_t)H));
+    cudaError_t e = launch_hexmat16_build(H, rec64, cM, cK, buf, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      dfree(buf);
+      return fail(FEM_ERR_CUDA, std::string("FP16 hex matrices: ") + cudaGetErrorString(e));
+    }
+    hm16 = buf;
+    return FEM_OK;
+  }
   ~fem_mesh() {
     dfree(xyz); dfree(conn); dfree(conn10); dfree(mat); dfree(lmr); dfree(rec64); dfree(rec32); dfree(rec_df); dfree(D);
-    dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(KMd); dfree(hexmat);
+    dfree(row_ptr); dfree(col); dfree(Kb); dfree(Mb); dfree(KMd); dfree(hexmat); dfree(hm16);
     dfree(binv64); dfree(binv32); dfree(fm); dfree(reg_lo); dfree(reg_hi); dfree(reg_gap); dfree(seg); dfree(reg_cent);
     dfree(ab_node); dfree(ab_c64); dfree(ab_c32);
     for (auto* w : ws) delete w;
@@ -414,7 +431,10 @@ struct fem_mesh {
       if (t.n_tiles == 0) continue;
       if (hpt && t.hex_per_tile != hpt) continue;
       size_t need, budget;
-      if (variant == 7) {
+      if (variant == 9) {
+        need = elem_bytes == 4 ? ebe_hex_tc_smem(t, rpad) : ~(size_t)0;
+        budget = 220 * 1024;
+      } else if (variant == 7) {
         need = elem_bytes == 4 ? ebe_hexmat_smem(t, view(), rpad) : ~(size_t)0;
         budget = 110 * 1024;
       } else if (variant == 3 || variant == 5 || variant == 6) {   // (6: one block per SM)
@@ -449,9 +469,23 @@ struct fem_mesh {
 // tiling fits, else the generic element kernel (q masked on Dirichlet DOFs by the consumers).
 template <typename T>
 static cudaError_t ebe_elem_product(const fem_mesh* m, int rpad, const T* p, T* q, double aM, double aK,
-                                    const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s) {
+                                    const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s,
+                                    bool tc = false) {
   int v, h;
   m->resolve(sizeof(T), rpad, &v, &h);
+  if (tc || v == 9) {   // FP16 hex matrices on the tensor cores: FP32, the mesh's own coefficients, 8/16/32 cases
+    if constexpr (sizeof(T) == 4) {
+      const HexTiles* t = m->npe == 4 && !m->seg ? m->tiles_for(4, rpad, 9, 64) : nullptr;
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      auto same = [](double x, double y) { return std::fabs(x - y) <= 1e-12 * std::fabs(y); };
+      if (t && (rpad == 8 || rpad == 16 || rpad == 32) && same(aM, m->cM) && same(aK, m->cK) &&
+          ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15) == 0 &&
+          (m->hm16 || (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+                       const_cast<fem_mesh*>(m)->ensure_hm16(s) == FEM_OK)))
+        return launch_ebe_hex_tc(*t, m->view(), m->hm16, rpad, p, q, aM, aK, red, sc, ptq, gate, s);
+    }
+    if (v == 9) v = m->hex ? 5 : 1, h = 0;
+  }
   if (m->npe == 10 && v != 8)   // quadratic tets: the tet10 element kernel (or the assembled blocks, variant 8)
     return launch_ebe10_gated<T>(m->E, m->N, rpad, m->conn10, m->rec32, m->rec64, m->fm, p, nullptr, q, aM, aK, red,
                                  sc, ptq, gate, s);
@@ -501,8 +535,8 @@ static cudaError_t ebe_elem_product(const fem_mesh* m, int rpad, const T* p, T* 
 template <typename T>
 static cudaError_t ebe_product(const fem_mesh* m, int rpad, const T* p, T* q, double aM, double aK,
                                const Reducer* red, CgCase* sc, double* ptq, const int* gate, cudaStream_t s,
-                               bool with_ab = false) {
-  cudaError_t e = ebe_elem_product<T>(m, rpad, p, q, aM, aK, red, sc, ptq, gate, s);
+                               bool with_ab = false, bool tc = false) {
+  cudaError_t e = ebe_elem_product<T>(m, rpad, p, q, aM, aK, red, sc, ptq, gate, s, tc);
   if (e == cudaSuccess && with_ab && m->ab.nb > 0)
     e = launch_dashpot<T>(m->ab, rpad, m->ab.cB, p, q, false, m->fm, red, sc, ptq, gate, s);
   return e;
@@ -562,8 +596,8 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
         CU(launch_dir_gated<T>(mv, rpad, z, p, sc, w->n_active, s));
       }
       w->pend(p0, s);
-      int p1 = w->pbeg(ebe_cls, s);
-      CU(ebe_product<T>(m, rpad, p, q, m->cM, m->cK, &red, sc, nullptr, w->n_active, s, true));
+      int p1 = w->pbeg(sizeof(T) == 4 && w->tc ? P_EBE16 : ebe_cls, s);
+      CU(ebe_product<T>(m, rpad, p, q, m->cM, m->cK, &red, sc, nullptr, w->n_active, s, true, w->tc));
       w->pend(p1, s);
       int p2 = w->pbeg(P_VEC, s);
       if (defer) {
@@ -599,9 +633,19 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
   return FEM_OK;
 }
 
+// The options an FP32-inner solve runs with: with the FP16 tensor-core inner product (relative error ~2.4e-4)
+// one inner solve is not asked for more than a 1e-3 reduction; the refinement passes take it from there.
+static fem_opts inner_opts(const fem_opts& o) {
+  fem_opts r = o;
+  if (o.inner_product == FEM_INNER_TC) r.inner_tol = std::max(o.inner_tol, 1e-3);
+  return r;
+}
+
 // FP32-inner / FP64-outer iterative refinement:  r64 = b - A64 x;  A32 d = r64 (inner PCG);  x += d.
-static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double* x, const fem_opts& o,
+static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double* x, const fem_opts& o_in,
                               cudaStream_t s) {
+  const fem_opts o = inner_opts(o_in);
+  w->tc = o.inner_product == FEM_INNER_TC;
   const MeshView mv = m->view();
   const int rpad = w->rpad;
   const Reducer red = w->red();
@@ -666,6 +710,8 @@ static fem_status check_opts(const fem_opts* o) {
   if (o->wait_budget < 0) return fail(FEM_ERR_ARG, "wait_budget must be >= 0");
   if (o->precision == FEM_FP32_INNER && !(o->inner_margin > 0.0 && o->inner_margin < 1.0))
     return fail(FEM_ERR_ARG, "inner_margin must be in (0, 1)");
+  if (o->inner_product != FEM_INNER_FP32 && o->inner_product != FEM_INNER_TC)
+    return fail(FEM_ERR_ARG, "inner_product must be FEM_INNER_FP32 or FEM_INNER_TC");
   if (o->cpu_predictor) {
     if (o->predictor != FEM_PRED_DD) return fail(FEM_ERR_ARG, "cpu_predictor needs the data-driven predictor");
     if (o->snapshot_format != 0 && o->snapshot_format != 2)
@@ -834,6 +880,7 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
       CU(cudaMemsetAsync(*v, 0, n * 8, s));
     }
     if (bt->opts.cert_df >= 2) CHK(m->ensure_bcsr(s));
+    if (bt->opts.inner_product == FEM_INNER_TC && bt->opts.precision == FEM_FP32_INNER) CHK(m->ensure_hm16(s));
     if (bt->opts.cert_df == 3) CHK(dalloc(&g->xdf, n));
   }
   if (bt->opts.predictor == FEM_PRED_DD) {
@@ -1075,8 +1122,9 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   cudaStream_t s = bt->s;
   const int it = g->steps + 1;
   const double dt = m->tp.dt;
-  const fem_opts& o = bt->opts;
+  const fem_opts o = inner_opts(bt->opts);
   Workspace* w = g->ws;
+  w->tc = o.inner_product == FEM_INNER_TC;
   const Reducer red = w->red();
   auto vslot = [&](int j) { return g->vh[((j % 4) + 4) % 4]; };
   auto aslot = [&](int j) { return g->Av[((j % 4) + 4) % 4]; };
@@ -1279,7 +1327,8 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   const MeshView mv = m->view();
   Workspace* w = g->ws;
   const Reducer red = w->red();
-  const fem_opts& o = bt->opts;
+  const fem_opts o = inner_opts(bt->opts);
+  w->tc = o.inner_product == FEM_INNER_TC;
   const double dt = m->tp.dt;
   const int rpad = g->rpad;
   const bool sg = mv.seg != nullptr;
@@ -1381,7 +1430,8 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
         } else {
           GE(launch_dir_defer<float>(mv, rpad, w->r32, w->p32, w->x32, w->sc, w->n_active, s4));
         }
-        GE(ebe_product<float>(m, rpad, w->p32, w->q32, m->cM, m->cK, &red, w->sc, nullptr, w->n_active, s4, true));
+        GE(ebe_product<float>(m, rpad, w->p32, w->q32, m->cM, m->cK, &red, w->sc, nullptr, w->n_active, s4, true,
+                              w->tc));
         if (sg) {
           GE(launch_update_seg<float>(mv, w->p32, w->q32, w->x32, w->rr32, w->z32, red, w->sc, w->n_active, o.maxit,
                                       s4));
@@ -1726,6 +1776,7 @@ void fem_opts_default(fem_opts* o) {
   o->use_graph = 1;
   o->wait_budget = kDefaultWaitBudget;
   o->inner_margin = 0.5;
+  o->inner_product = FEM_INNER_FP32;
 }
 
 // Mesh set-up shared by the linear (npe 4) and quadratic (npe 10) tets: element records of the corner tets,
@@ -1993,10 +2044,10 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
 fem_status fem_mesh_tune(fem_mesh* m, int ebe_variant, int hex_per_tile) {
   g_err.clear();
   if (!m) return fail(FEM_ERR_ARG, "mesh is null");
-  if (ebe_variant < 0 || ebe_variant > 8) return fail(FEM_ERR_ARG, "ebe_variant must be 0 .. 8");
+  if (ebe_variant < 0 || ebe_variant > 9) return fail(FEM_ERR_ARG, "ebe_variant must be 0 .. 9");
   if (m->npe == 10 && ebe_variant != 0 && ebe_variant != 8)
     return fail(FEM_ERR_ARG, "a tet10 mesh takes variant 0 (its element kernel) or 8 (assembled blocks)");
-  if (ebe_variant >= 2 && ebe_variant <= 7 && !m->hex)
+  if (((ebe_variant >= 2 && ebe_variant <= 7) || ebe_variant == 9) && !m->hex)
     return fail(FEM_ERR_ARG, "the mesh has no hex patches: tiled kernel unavailable");
   if (hex_per_tile != 0 && hex_per_tile != 64 && hex_per_tile != 128 && hex_per_tile != 256 && hex_per_tile != 512)
     return fail(FEM_ERR_ARG, "hex_per_tile must be 0, 64, 128, 256 or 512");
@@ -2727,6 +2778,8 @@ fem_status fem_batch_profile(fem_batch* b, int enable, fem_profile* out) {
     out->rhs_ms = p.ms[P_RHS];
     out->solve_ms = p.ms[P_SOLVE];
     out->update_ms = p.ms[P_UPDATE];
+    out->ebe16_launches = p.n[P_EBE16];
+    out->ebe16_ms = p.ms[P_EBE16];
   }
   return FEM_OK;
 }

@@ -6,6 +6,8 @@
 //   G = sum_b p_b g_b^T,  sigma = lambda tr(G) I + mu (G + G^T),  (K_e p)_a = V sigma g_a,
 //   (M_e p)_a = rho V / 20 (p_a + sum_b p_b).
 // This generic kernel scatters with global atomics; fixed DOFs are left to the consumer to mask.
+#include <cuda_fp16.h>
+
 #include "fem_internal.cuh"
 
 #include <mutex>
@@ -1706,6 +1708,353 @@ cudaError_t launch_ebe_split_df(const MeshView& m, const float* rec_df, int rpad
   if (err != cudaSuccess) return err;
   const int rs = log2i(rpad);
   k_ebe_split_df<<<grid_for(m.E << rs), kBlock, 0, s>>>(m, rec_df, rpad, rs, p, qM, qK);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Hex element matrices in FP16 on the tensor cores (variant 9; the inner FP32 solve's CG products).
+// Per hex the symmetric 24 x 24 operator A_h = aM M_h + aK K_h (the six Kuhn tets summed in FP64, as for
+// variant 7) in component-major DOF order (row x-components of corner slots 0..7, then y, then z), scaled
+// by a power of two so that its largest entry lies in [2^13, 2^14), rounded to FP16, and stored as the
+// packed upper triangle: 300 halves, then the FP32 factor 2^-scale back, then 4 bytes of padding (608-byte
+// records, one bulk copy per tile).  A product stages a tile's records and node rows of p by bulk copies
+// (double-buffered), scales each case's values of p by a power of two into FP16 range per tile, and applies
+// each hex to 8 cases at a time with four mma.sync (m16n8k16 on the x and y columns, m16n8k8 on the z
+// columns, for output rows 0..15 and 16..23): with the component-major order a lane's B operand needs
+// only corner slots 2tq and 2tq + 1 and its outputs are the three components of corner slot gq.  Sums go
+// to the tile accumulator in the packed kernel's fixed point; p^T q is taken at the flush from the tile's
+// sums and its FP32 values of p.  FP16 operands carry ~2.4e-4 of relative error into a product (FP32
+// accumulation): the inner solve's refinement pass removes it, its reduction target is floored at 1e-3.
+// ------------------------------------------------------------------------------------------------------
+constexpr int kHm16Bytes = 608;
+constexpr int kTcBlock = 512;
+
+__host__ __device__ constexpr int tri24(int r, int c) { return r * 24 - r * (r - 1) / 2 + (c - r); }
+static_assert(tri24(23, 23) == 299, "300 packed halves");
+
+// Block (a, b) of the hex operator (corner slots a, b): B[i][k] = A[(i, a), (k, b)].
+__device__ void hex_block(const double* __restrict__ rec, int64_t h, int a, int b, double aM, double aK,
+                          double (&B)[3][3]) {
+  constexpr int T[6][4] = {{0, 1, 2, 3}, {0, 1, 3, 4}, {0, 5, 3, 2}, {0, 5, 6, 3}, {0, 7, 4, 3}, {0, 7, 3, 6}};
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) B[i][k] = 0.0;
+  for (int t = 0; t < 6; ++t) {
+    int la = -1, lb = -1;
+    for (int k = 0; k < 4; ++k) {
+      if (T[t][k] == a) la = k;
+      if (T[t][k] == b) lb = k;
+    }
+    if (la < 0 || lb < 0) continue;
+    const double* r = rec + (h * 6 + t) * kRec;
+    double ga[3], gb[3];
+    for (int i = 0; i < 3; ++i) {
+      ga[i] = la == 0 ? -(r[i] + r[3 + i] + r[6 + i]) : r[3 * (la - 1) + i];
+      gb[i] = lb == 0 ? -(r[i] + r[3 + i] + r[6 + i]) : r[3 * (lb - 1) + i];
+    }
+    const double lam = aK * r[9], mu = aK * r[10], ms = aM * r[11] * (la == lb ? 2.0 : 1.0);
+    const double gg = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k)
+        B[i][k] += lam * ga[i] * gb[k] + mu * (gb[i] * ga[k] + (i == k ? gg : 0.0)) + (i == k ? ms : 0.0);
+  }
+}
+
+// One thread per hex: the largest entry first, then the scaled FP16 entries.
+__global__ void k_hexmat16_build(int64_t H, const double* __restrict__ rec, double aM, double aK,
+                                 unsigned char* __restrict__ out) {
+  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < H; h += (int64_t)gridDim.x * blockDim.x) {
+    double mx = 0.0, B[3][3];
+    for (int a = 0; a < 8; ++a)
+      for (int b = a; b < 8; ++b) {
+        hex_block(rec, h, a, b, aM, aK, B);
+        for (int i = 0; i < 3; ++i)
+          for (int k = 0; k < 3; ++k) mx = fmax(mx, fabs(B[i][k]));
+      }
+    int e = 0;
+    frexp(mx, &e);                                  // mx < 2^e
+    const double sc = mx > 0.0 ? ldexp(1.0, 14 - e) : 1.0;
+    __half* o = reinterpret_cast<__half*>(out + h * kHm16Bytes);
+    for (int a = 0; a < 8; ++a)
+      for (int b = a; b < 8; ++b) {
+        hex_block(rec, h, a, b, aM, aK, B);
+        for (int i = 0; i < 3; ++i)
+          for (int k = (a == b ? i : 0); k < 3; ++k) {
+            int r = 8 * i + a, c = 8 * k + b;
+            if (r > c) {
+              const int t = r;
+              r = c, c = t;
+            }
+            o[tri24(r, c)] = __float2half_rn((float)(B[i][k] * sc));
+          }
+      }
+    *reinterpret_cast<float*>(out + h * kHm16Bytes + 600) = mx > 0.0 ? (float)ldexp(1.0, e - 14) : 1.0f;
+    *reinterpret_cast<float*>(out + h * kHm16Bytes + 604) = 0.0f;
+  }
+}
+
+cudaError_t launch_hexmat16_build(int64_t n_hex, const double* rec64, double aM, double aK, unsigned char* out,
+                                  cudaStream_t s) {
+  if (n_hex == 0) return cudaSuccess;
+  k_hexmat16_build<<<grid_for(n_hex, wide_grid_cap()), kBlock, 0, s>>>(n_hex, rec64, aM, aK, out);
+  return cudaGetLastError();
+}
+
+struct TcLayout {
+  size_t qs, ps0, ps1, hm0, hm1, node0, node1, total;
+};
+__host__ __device__ inline TcLayout tc_layout(int nloc_max, int rpad, int hex_per_tile) {
+  auto up = [](size_t x) { return (x + 127) & ~(size_t)127; };
+  TcLayout L;
+  const size_t vals = up((size_t)nloc_max * 3 * rpad * sizeof(float));
+  const size_t hms = up((size_t)hex_per_tile * kHm16Bytes);
+  const size_t nodes = up(sizeof(int) * (size_t)nloc_max);
+  L.qs = 1024;   // head: 2 mbarriers, per-case |p| maxima x2, back factors, output factors, dot sums
+  L.ps0 = L.qs + vals;
+  L.ps1 = L.ps0 + vals;
+  L.hm0 = L.ps1 + vals;
+  L.hm1 = L.hm0 + hms;
+  L.node0 = L.hm1 + hms;
+  L.node1 = L.node0 + nodes;
+  L.total = L.node1 + nodes;
+  return L;
+}
+
+__device__ __forceinline__ void mma_f16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                              uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_f16_1688(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(b0));
+}
+__device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack_h(unsigned short lo, unsigned short hi) {
+  return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+template <bool DOT>
+__global__ void __launch_bounds__(kTcBlock, 1) k_ebe_hex_tc(HexTiles ht, MeshView m, int rpad, int rshift,
+                                                         const float* __restrict__ p, float* __restrict__ q,
+                                                         const unsigned char* __restrict__ hm, float aM, float aK,
+                                                         Reducer red, CgCase* sc, double* ptq_out, const int* gate) {
+  if (gate && *gate == 0) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const TcLayout L = tc_layout(ht.nloc_max, rpad, ht.hex_per_tile);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);
+  int* spm = reinterpret_cast<int*>(smem_raw + 32);          // [2][32] per-case max |p| bits, per tile parity
+  float* sfwd = reinterpret_cast<float*>(smem_raw + 288);    // [32] fixed point back to FP32
+  float* sfx = reinterpret_cast<float*>(smem_raw + 416);     // [32] MMA output (scaled p) to fixed point
+  float* sps = reinterpret_cast<float*>(smem_raw + 544);     // [32] scale of p into FP16 range
+  double* sdot = reinterpret_cast<double*>(smem_raw + 768);  // [32] p^T q sums of the block
+  int* qs = reinterpret_cast<int*>(smem_raw + L.qs);
+  auto psb = [&](int b) { return reinterpret_cast<float*>(smem_raw + (b ? L.ps1 : L.ps0)); };
+  auto hmb = [&](int b) { return smem_raw + (b ? L.hm1 : L.hm0); };
+  auto snb = [&](int b) { return reinterpret_cast<int*>(smem_raw + (b ? L.node1 : L.node0)); };
+  const int per_node = 3 * rpad;
+  const uint32_t node_bytes = (uint32_t)(per_node * sizeof(float));
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbar[0]), 1);
+    mbar_init(smem_u32(&mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < (ht.nloc_max * per_node) >> 2; i += blockDim.x)
+    reinterpret_cast<int4*>(qs)[i] = make_int4(0, 0, 0, 0);
+  if (tid < 64) spm[tid] = 0;
+  if (tid < 32) sdot[tid] = 0.0;
+  __syncthreads();
+  auto load_node = [&](int t) {   // node id of this thread's tile-local node of tile t (tiles hold <= blockDim nodes)
+    if (t >= ht.n_tiles) return 0;
+    const int n0 = ht.tile_node_off[t];
+    return tid < ht.tile_node_off[t + 1] - n0 ? ht.tile_nodes[n0 + tid] : 0;
+  };
+  auto issue = [&](int t, int b, int nd) {
+    const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
+    const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
+    const uint32_t bar = smem_u32(mbar + b);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) {
+      const uint32_t hbytes = (uint32_t)(nh * kHm16Bytes);
+      mbar_expect_tx(bar, hbytes + (uint32_t)nl * node_bytes);
+      bulk_g2s(smem_u32(hmb(b)), hm + (int64_t)h0 * kHm16Bytes, hbytes, bar);
+    }
+    if (tid < nl) {
+      snb(b)[tid] = nd;
+      bulk_g2s(smem_u32(psb(b) + (int64_t)tid * per_node), p + (int64_t)(nd & 0x0fffffff) * per_node, node_bytes,
+               bar);
+    }
+  };
+  // the lane's fragment coordinates and the packed indices of its 18 A entries (constant over the hexes)
+  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int gq = lane >> 2, tq = lane & 3;
+  auto pidx = [](int r, int c) { return r <= c ? tri24(r, c) : tri24(c, r); };
+  const int k0 = 2 * tq;
+  const int ia[18] = {pidx(gq, k0),          pidx(gq, k0 + 1),          pidx(gq + 8, k0),      pidx(gq + 8, k0 + 1),
+                      pidx(gq, k0 + 8),      pidx(gq, k0 + 9),          pidx(gq + 8, k0 + 8),  pidx(gq + 8, k0 + 9),
+                      pidx(gq, 16 + k0),     pidx(gq, 17 + k0),         pidx(gq + 8, 16 + k0), pidx(gq + 8, 17 + k0),
+                      pidx(16 + gq, k0),     pidx(16 + gq, k0 + 1),     pidx(16 + gq, k0 + 8), pidx(16 + gq, k0 + 9),
+                      pidx(16 + gq, 16 + k0), pidx(16 + gq, 17 + k0)};
+  const float bco = fabsf(aM) * ht.abs_m + fabsf(aK) * ht.abs_k;
+  float4 tdot = make_float4(0.f, 0.f, 0.f, 0.f);
+  double dd[4] = {0.0, 0.0, 0.0, 0.0};
+  const int t0 = blockIdx.x;
+  int nd_next = load_node(t0 + gridDim.x);
+  if (t0 < ht.n_tiles) issue(t0, 0, load_node(t0));
+  for (int k = 0;; ++k) {
+    const int t = t0 + k * gridDim.x;
+    if (t >= ht.n_tiles) break;
+    const int b = k & 1;
+    const int tn = t + gridDim.x;
+    if (tn < ht.n_tiles) issue(tn, b ^ 1, nd_next);
+    const int nd_after = load_node(tn + gridDim.x);
+    const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
+    const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
+    const uint32_t bar = smem_u32(mbar + b);
+    if (!mbar_wait(bar, (uint32_t)((k >> 1) & 1), g_wait_budget)) {
+      atomicExch(&g_tma_timeout, 1);
+      mbar_wait(bar, (uint32_t)((k >> 1) & 1));   // second bounded wait for the copies still in flight
+    }
+    __syncthreads();
+    const float* ps = psb(b);
+    const unsigned char* hs = hmb(b);
+    const int* snode = snb(b);
+    // per-case largest |p| of the staged tile: the fixed-point scale (as the packed kernel) and the scale of
+    // p into FP16 range (its largest value below 2^14)
+    {
+      float mx = 0.f;
+      for (int i = tid; i < nl * per_node; i += blockDim.x) mx = fmaxf(mx, fabsf(ps[i]));
+      for (int off = 16; off >= rpad; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      int* spm_b = spm + (b << 5);
+      if ((tid & 31) < rpad) atomicMax(spm_b + (tid & 31), __float_as_int(mx));
+      if (tid < rpad) spm[((b ^ 1) << 5) + tid] = 0;   // the next tile's buffer
+      __syncthreads();
+      if (tid < rpad) {
+        auto pow2 = [](int e) { return __uint_as_float((uint32_t)min(max(e + 127, 1), 254) << 23); };
+        const uint32_t fb = (__float_as_uint(bco * __int_as_float(spm_b[tid])) >> 23) & 0xffu;
+        const int E = fb == 0u ? -126 : (int)fb - 126;                      // bound < 2^E
+        const uint32_t fp = ((uint32_t)spm_b[tid] >> 23) & 0xffu;
+        const int ep = fp == 0u ? -126 : (int)fp - 126;                      // max |p| < 2^ep
+        sfwd[tid] = pow2(E - 30);
+        sps[tid] = pow2(14 - ep);
+        sfx[tid] = pow2(30 - E - (14 - ep));
+      }
+      __syncthreads();
+    }
+    const int nt_n = rpad >> 3;
+    for (int hl = warp; hl < nh; hl += nwarp) {
+      const uint32_t* lw = reinterpret_cast<const uint32_t*>(ht.hex_local + h0 + hl);
+      const uint32_t wb = __ldg(lw + tq), wo = __ldg(lw + (gq >> 1));
+      const int cb0 = (int)(wb & 0xffffu), cb1 = (int)(wb >> 16);
+      const int co = (int)((wo >> ((gq & 1) << 4)) & 0xffffu);
+      const unsigned short* hh = reinterpret_cast<const unsigned short*>(hs + hl * kHm16Bytes);
+      const float hu = *reinterpret_cast<const float*>(hs + hl * kHm16Bytes + 600);
+      const uint32_t a0 = pack_h(hh[ia[0]], hh[ia[1]]), a1 = pack_h(hh[ia[2]], hh[ia[3]]);
+      const uint32_t a2 = pack_h(hh[ia[4]], hh[ia[5]]), a3 = pack_h(hh[ia[6]], hh[ia[7]]);
+      const uint32_t a4 = pack_h(hh[ia[8]], hh[ia[9]]), a5 = pack_h(hh[ia[10]], hh[ia[11]]);
+      const uint32_t a6 = pack_h(hh[ia[12]], hh[ia[13]]), a7 = pack_h(hh[ia[14]], hh[ia[15]]);
+      const uint32_t a8 = pack_h(hh[ia[16]], hh[ia[17]]);
+      const float* p0 = ps + cb0 * per_node;
+      const float* p1 = ps + cb1 * per_node;
+      int* dst = qs + co * per_node;
+      for (int nt = 0; nt < nt_n; ++nt) {
+        const int cn = (nt << 3) + gq;   // the case of the lane's B operand
+        const float s = sps[cn];
+        const uint32_t b0 = pack_f16(p0[cn] * s, p1[cn] * s);
+        const uint32_t b1 = pack_f16(p0[rpad + cn] * s, p1[rpad + cn] * s);
+        const uint32_t b2 = pack_f16(p0[2 * rpad + cn] * s, p1[2 * rpad + cn] * s);
+        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_f16_16816(d0, a0, a1, a2, a3, b0, b1);
+        mma_f16_1688(d0, a4, a5, b2);
+        mma_f16_16816(d1, a6, 0u, a7, 0u, b0, b1);
+        mma_f16_1688(d1, a8, 0u, b2);
+        // rows gq (x), gq + 8 (y), 16 + gq (z) of corner slot gq; columns: cases c, c + 1
+        const int c = (nt << 3) + 2 * tq;
+        const float f0 = hu * sfx[c], f1 = hu * sfx[c + 1];
+        atomicAdd(dst + c, __float2int_rn(d0[0] * f0));
+        atomicAdd(dst + c + 1, __float2int_rn(d0[1] * f1));
+        atomicAdd(dst + rpad + c, __float2int_rn(d0[2] * f0));
+        atomicAdd(dst + rpad + c + 1, __float2int_rn(d0[3] * f1));
+        atomicAdd(dst + 2 * rpad + c, __float2int_rn(d1[0] * f0));
+        atomicAdd(dst + 2 * rpad + c + 1, __float2int_rn(d1[1] * f1));
+      }
+    }
+    __syncthreads();
+    // flush: float4 pieces (four cases of one component of one node) to the output; p^T q from the tile's
+    // sums and its FP32 values of p (a thread's four cases are fixed: 4 blockDim is a multiple of rpad)
+    {
+      const int sh4 = rshift - 2;
+      const int f4 = per_node >> 2;
+      for (int i = tid; i < nl * f4; i += blockDim.x) {
+        const int l = (i >> sh4) / 3, kk = (i - l * f4) >> sh4;
+        const int raw = snode[l];
+        const int64_t g = raw & 0x0fffffff;
+        const bool fixed = !dof_free((uint8_t)((raw >> 28) & 7), kk);
+        float4* dstg = reinterpret_cast<float4*>(q + g * per_node) + (i - l * f4);
+        const int4 vi = reinterpret_cast<const int4*>(qs)[i];
+        const int c4 = (i << 2) & (rpad - 1);
+        const float4 v = make_float4((float)vi.x * sfwd[c4], (float)vi.y * sfwd[c4 + 1], (float)vi.z * sfwd[c4 + 2],
+                                     (float)vi.w * sfwd[c4 + 3]);
+        reinterpret_cast<int4*>(qs)[i] = make_int4(0, 0, 0, 0);
+        if (DOT && !fixed) {
+          const float4 pv = reinterpret_cast<const float4*>(ps)[i];
+          tdot.x = fmaf(pv.x, v.x, tdot.x), tdot.y = fmaf(pv.y, v.y, tdot.y);
+          tdot.z = fmaf(pv.z, v.z, tdot.z), tdot.w = fmaf(pv.w, v.w, tdot.w);
+        }
+        if (raw < 0) {
+          if (!fixed) atomicAdd(dstg, v);
+        } else {
+          *dstg = fixed ? make_float4(0.f, 0.f, 0.f, 0.f) : v;
+        }
+      }
+    }
+    if (DOT) {
+      dd[0] += (double)tdot.x, dd[1] += (double)tdot.y, dd[2] += (double)tdot.z, dd[3] += (double)tdot.w;
+      tdot = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    nd_next = nd_after;
+  }
+  if (DOT) {
+    const int c4 = (tid << 2) & (rpad - 1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) atomicAdd(sdot + c4 + j, dd[j]);
+    __syncthreads();
+    double v[1] = {tid < rpad ? sdot[tid] : 0.0};
+    if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
+  }
+}
+
+size_t ebe_hex_tc_smem(const HexTiles& ht, int rpad) {
+  if (ht.nloc_max > kTcBlock || ht.hex_per_tile > 64 || rpad < 8 || rpad > 32) return ~(size_t)0;
+  return tc_layout(ht.nloc_max, rpad, ht.hex_per_tile).total;
+}
+
+cudaError_t launch_ebe_hex_tc(const HexTiles& ht, const MeshView& m, const unsigned char* hm16, int rpad,
+                              const float* p, float* q, double aM, double aK, const Reducer* red, CgCase* sc,
+                              double* ptq_out, const int* gate, cudaStream_t s) {
+  const size_t smem = ebe_hex_tc_smem(ht, rpad);
+  if (smem == ~(size_t)0 || ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15) != 0 || m.seg)
+    return cudaErrorInvalidValue;
+  cudaError_t err = cudaMemsetAsync(q, 0, sizeof(float) * (size_t)m.N * 3 * rpad, s);
+  if (err != cudaSuccess) return err;
+  auto kfn = red ? k_ebe_hex_tc<true> : k_ebe_hex_tc<false>;
+  err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int grid = sm_count();
+  if (grid > ht.n_tiles) grid = ht.n_tiles;
+  if (grid > red_grid_cap()) grid = red_grid_cap();
+  Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
+  kfn<<<grid, kTcBlock, smem, s>>>(ht, m, rpad, log2i(rpad), p, q, hm16, (float)aM, (float)aK, rd,
+                                   red ? sc : nullptr, red ? ptq_out : nullptr, gate);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@ FEM_ERR_ARG, FEM_ERR_OOM, FEM_ERR_CUDA = -1, -2, -3
 FEM_ERR_NOT_CONVERGED, FEM_ERR_BREAKDOWN, FEM_ERR_NONFINITE, FEM_ERR_TIMEOUT, FEM_ERR_STATE = -4, -5, -6, -7, -8
 FEM_FP64, FEM_FP32_INNER = 0, 1
 FEM_PRED_AB4, FEM_PRED_DD = 0, 1
+FEM_INNER_FP32, FEM_INNER_TC = 0, 1
 FEM_FIELD_U, FEM_FIELD_V, FEM_FIELD_A, FEM_FIELD_DU, FEM_FIELD_B, FEM_FIELD_GUESS = range(6)
 
 # every symbol include/fem.h declares
@@ -54,7 +55,8 @@ class fem_opts(ctypes.Structure):
                 ("tau", ctypes.c_double), ("snapshot_format", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("refresh_every", ctypes.c_int), ("cert_df", ctypes.c_int), ("fuse_meshes", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("wait_budget", ctypes.c_int),
-                ("cpu_predictor", ctypes.c_int), ("inner_margin", ctypes.c_double)]
+                ("cpu_predictor", ctypes.c_int), ("inner_margin", ctypes.c_double),
+                ("inner_product", ctypes.c_int)]
 
 
 class fem_profile(ctypes.Structure):
@@ -63,7 +65,7 @@ class fem_profile(ctypes.Structure):
                 ("ebe64_launches", ctypes.c_longlong), ("ebe64_ms", ctypes.c_double),
                 ("cg_vec_launches", ctypes.c_longlong), ("cg_vec_ms", ctypes.c_double),
                 ("predict_ms", ctypes.c_double), ("rhs_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
-                ("update_ms", ctypes.c_double)]
+                ("update_ms", ctypes.c_double), ("ebe16_launches", ctypes.c_longlong), ("ebe16_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
