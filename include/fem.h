@@ -63,8 +63,9 @@ enum {
   FEM_INNER_TC = 1       /* per-hex 24 x 24 element matrices of A in FP16 (the element data in reduced precision),
                             applied on the tensor cores with FP32 accumulation: ~2.4e-4 relative error in a
                             product, so each inner solve is asked for at most a 1e-3 reduction and the FP64
-                            refinement passes carry the solve to tol.  Hex-patch meshes, 8, 16 or 32 cases a
-                            group; the predictor's correction and all other products stay FP32/FP64 */
+                            refinement passes carry the solve to tol.  Hex-patch meshes, groups of 5..16 cases
+                            (8 or 16 lanes; other groups keep the FP32 kernels); the predictor's correction and
+                            all other products stay FP32/FP64 */
 };
 
 /* Initial-guess predictor used by fem_step. */

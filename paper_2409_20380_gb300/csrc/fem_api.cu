@@ -473,12 +473,12 @@ static cudaError_t ebe_elem_product(const fem_mesh* m, int rpad, const T* p, T* 
                                     bool tc = false) {
   int v, h;
   m->resolve(sizeof(T), rpad, &v, &h);
-  if (tc || v == 9) {   // FP16 hex matrices on the tensor cores: FP32, the mesh's own coefficients, 8/16/32 cases
+  if (tc || v == 9) {   // FP16 hex matrices on the tensor cores: FP32, the mesh's own coefficients, 8 or 16 cases
     if constexpr (sizeof(T) == 4) {
       const HexTiles* t = m->npe == 4 && !m->seg ? m->tiles_for(4, rpad, 9, 64) : nullptr;
       cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
       auto same = [](double x, double y) { return std::fabs(x - y) <= 1e-12 * std::fabs(y); };
-      if (t && (rpad == 8 || rpad == 16 || rpad == 32) && same(aM, m->cM) && same(aK, m->cK) &&
+      if (t && (rpad == 8 || rpad == 16) && same(aM, m->cM) && same(aK, m->cK) &&
           ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15) == 0 &&
           (m->hm16 || (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
                        const_cast<fem_mesh*>(m)->ensure_hm16(s) == FEM_OK)))

@@ -2034,7 +2034,7 @@ __global__ void __launch_bounds__(kTcBlock, 1) k_ebe_hex_tc(HexTiles ht, MeshVie
 }
 
 size_t ebe_hex_tc_smem(const HexTiles& ht, int rpad) {
-  if (ht.nloc_max > kTcBlock || ht.hex_per_tile > 64 || rpad < 8 || rpad > 32) return ~(size_t)0;
+  if (ht.nloc_max > kTcBlock || ht.hex_per_tile > 64 || (rpad != 8 && rpad != 16)) return ~(size_t)0;
   return tc_layout(ht.nloc_max, rpad, ht.hex_per_tile).total;
 }
 
