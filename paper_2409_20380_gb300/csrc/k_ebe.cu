@@ -1800,7 +1800,7 @@ cudaError_t launch_hexmat16_build(int64_t n_hex, const double* rec64, double aM,
 }
 
 struct TcLayout {
-  size_t qs, ps0, ps1, hm0, hm1, node0, node1, total;
+  size_t qs, ps0, ps1, hm0, hm1, loc0, loc1, node0, node1, total;
 };
 __host__ __device__ inline TcLayout tc_layout(int nloc_max, int rpad, int hex_per_tile) {
   auto up = [](size_t x) { return (x + 127) & ~(size_t)127; };
@@ -1813,7 +1813,9 @@ __host__ __device__ inline TcLayout tc_layout(int nloc_max, int rpad, int hex_pe
   L.ps1 = L.ps0 + vals;
   L.hm0 = L.ps1 + vals;
   L.hm1 = L.hm0 + hms;
-  L.node0 = L.hm1 + hms;
+  L.loc0 = L.hm1 + hms;                       // the tile's corner tables (16 bytes a hex)
+  L.loc1 = L.loc0 + up((size_t)hex_per_tile * 16);
+  L.node0 = L.loc1 + up((size_t)hex_per_tile * 16);
   L.node1 = L.node0 + nodes;
   L.total = L.node1 + nodes;
   return L;
@@ -1858,6 +1860,7 @@ __global__ void __launch_bounds__(kTcBlock, 1) k_ebe_hex_tc(HexTiles ht, MeshVie
   int* qs = reinterpret_cast<int*>(smem_raw + L.qs);
   auto psb = [&](int b) { return reinterpret_cast<float*>(smem_raw + (b ? L.ps1 : L.ps0)); };
   auto hmb = [&](int b) { return smem_raw + (b ? L.hm1 : L.hm0); };
+  auto slb = [&](int b) { return reinterpret_cast<const uint32_t*>(smem_raw + (b ? L.loc1 : L.loc0)); };
   auto snb = [&](int b) { return reinterpret_cast<int*>(smem_raw + (b ? L.node1 : L.node0)); };
   const int per_node = 3 * rpad;
   const uint32_t node_bytes = (uint32_t)(per_node * sizeof(float));
@@ -1883,9 +1886,10 @@ __global__ void __launch_bounds__(kTcBlock, 1) k_ebe_hex_tc(HexTiles ht, MeshVie
     const uint32_t bar = smem_u32(mbar + b);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (tid == 0) {
-      const uint32_t hbytes = (uint32_t)(nh * kHm16Bytes);
-      mbar_expect_tx(bar, hbytes + (uint32_t)nl * node_bytes);
+      const uint32_t hbytes = (uint32_t)(nh * kHm16Bytes), lbytes = (uint32_t)(nh * 16);
+      mbar_expect_tx(bar, hbytes + lbytes + (uint32_t)nl * node_bytes);
       bulk_g2s(smem_u32(hmb(b)), hm + (int64_t)h0 * kHm16Bytes, hbytes, bar);
+      bulk_g2s(smem_u32(slb(b)), ht.hex_local + h0, lbytes, bar);
     }
     if (tid < nl) {
       snb(b)[tid] = nd;
@@ -1926,6 +1930,7 @@ __global__ void __launch_bounds__(kTcBlock, 1) k_ebe_hex_tc(HexTiles ht, MeshVie
     __syncthreads();
     const float* ps = psb(b);
     const unsigned char* hs = hmb(b);
+    const uint32_t* sl = slb(b);
     const int* snode = snb(b);
     // per-case largest |p| of the staged tile: the fixed-point scale (as the packed kernel) and the scale of
     // p into FP16 range (its largest value below 2^14)
@@ -1951,8 +1956,7 @@ __global__ void __launch_bounds__(kTcBlock, 1) k_ebe_hex_tc(HexTiles ht, MeshVie
     }
     const int nt_n = rpad >> 3;
     for (int hl = warp; hl < nh; hl += nwarp) {
-      const uint32_t* lw = reinterpret_cast<const uint32_t*>(ht.hex_local + h0 + hl);
-      const uint32_t wb = __ldg(lw + tq), wo = __ldg(lw + (gq >> 1));
+      const uint32_t wb = sl[4 * hl + tq], wo = sl[4 * hl + (gq >> 1)];
       const int cb0 = (int)(wb & 0xffffu), cb1 = (int)(wb >> 16);
       const int co = (int)((wo >> ((gq & 1) << 4)) & 0xffffu);
       const unsigned short* hh = reinterpret_cast<const unsigned short*>(hs + hl * kHm16Bytes);
