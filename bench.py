@@ -623,12 +623,12 @@ def run_ours(args):
                  "alg_flops_per_launch": fl, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak": hbm_peak,
                  "hbm_peak_kind": peak_kind, "ms_per_step": prof["ebe32_ms"] / max(prof["steps"], 1)}
     if args.inner_product == "tc" and prof.get("ebe16_launches", 0) > 0:
-        # the inner CG products on the tensor cores: per hex a 608-byte FP16 matrix record and its corner
+        # the inner CG products on the tensor cores: per hex a 784-byte FP16 matrix record and its corner
         # table (16 bytes), p read and q written in FP32; four mma.sync a hex and 8 cases
         H = E // 6
         working16 = max(1, working32 - (args.profile_steps if args.predictor == "dd" else 0))
         avg16 = prof["ebe16_ms"] / max(1, min(working16, prof["ebe16_launches"]))
-        bytes16 = H * (608 + 16) + rpad * N * 3 * (4 + 4)
+        bytes16 = H * (784 + 16) + rpad * N * 3 * (4 + 4)
         fl16 = H * (rpad // 8) * 2 * (16 * 8 * 16 + 16 * 8 * 8) * 2
         gbs = bytes16 / (avg16 * 1e-3) / 1e9
         inner = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
@@ -755,7 +755,7 @@ def run_kernel(args):
     E, N = mesh.n_elems, mesh.n_nodes
     bytes_launch = E * (16 + 12 * w) + r * N * 3 * 2 * w
     if args.variant == 9 and args.kernel_precision == "fp32":   # FP16 hex records and corner tables
-        bytes_launch = (E // 6) * (608 + 16) + r * N * 3 * 2 * w
+        bytes_launch = (E // 6) * (784 + 16) + r * N * 3 * 2 * w
     info = fem.fem_mesh_info(h)
     print(json.dumps({"kernel": "ebe", "precision": args.kernel_precision, "dims": args.dims, "cases": r,
                       "variant": args.variant, "hex_per_tile": args.hex_per_tile, "mesh_info": info,

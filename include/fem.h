@@ -142,7 +142,7 @@ typedef struct {
                             still ends at or above tol takes another refinement pass, so every step stays
                             certified below tol.  In (0, 1); default 0.5 (measured: 0.1 cost 3.5% more time on the
                             large workload for the same certificate) */
-  int inner_product;     /* FEM_INNER_FP32 or FEM_INNER_TC (see above); the FP16 hex matrices (608 bytes a hex)
+  int inner_product;     /* FEM_INNER_FP32 or FEM_INNER_TC (see above); the FP16 hex matrices (784 bytes a hex)
                             are built on the group's first step.  Default FEM_INNER_FP32 */
 } fem_opts;
 

@@ -269,7 +269,7 @@ struct fem_mesh {
   int ebe_variant = 0;             // 0 auto, 1 generic, 2 tiled hex, 3 staged, 4 case-major, 5/6 packed staged,
                                    // 7 hex element matrices, 8 assembled 3x3 blocks (CRS-style comparator)
   float* hexmat = nullptr;         // [ceil(H / 2)][300][2] hex matrices for (cM, cK) (built on first use)
-  unsigned char* hm16 = nullptr;   // [H] 608-byte FP16 hex matrices for (cM, cK) (variant 9; built on first use)
+  unsigned char* hm16 = nullptr;   // [H] 784-byte FP16 hex matrices for (cM, cK) (variant 9; built on first use)
   int hex_per_tile = 0;            // 0 auto
   // autotuned choice per (FP32 / FP64 product, log2 of the case count); variant 0 = not tuned
   struct Tuned {

@@ -309,10 +309,10 @@ size_t ebe_hex_cm_smem(const HexTiles& ht, const MeshView& m, int rpad);   // ~0
 // of the mesh's hexes (n_hex, hex h = elements 6h .. 6h + 5, FP64 records) into out
 // ([ceil(n_hex / 2)][300][2] floats), and the product q = A p with them (FP32, r cases, not fused groups).
 cudaError_t launch_hexmat_build(int64_t n_hex, const double* rec64, double aM, double aK, float* out, cudaStream_t s);
-// Variant 9: FP16 hex element matrices (608-byte records, one a hex) for the coefficients (aM, aK), and the
+// Variant 9: FP16 hex element matrices (784-byte records, one a hex) for the coefficients (aM, aK), and the
 // FP32 product q = A p with them on the tensor cores (rpad 8 or 16; p^T q and the CG step length fused
 // when red is given); smem ~0 when a tiling does not fit the kernel.
-constexpr int kHm16RecBytes = 608;
+constexpr int kHm16RecBytes = 784;
 cudaError_t launch_hexmat16_build(int64_t n_hex, const double* rec64, double aM, double aK, unsigned char* out,
                                   cudaStream_t s);
 size_t ebe_hex_tc_smem(const HexTiles& ht, int rpad);

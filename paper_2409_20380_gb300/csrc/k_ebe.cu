@@ -1714,23 +1714,24 @@ cudaError_t launch_ebe_split_df(const MeshView& m, const float* rec_df, int rpad
 // ------------------------------------------------------------------------------------------------------
 // Hex element matrices in FP16 on the tensor cores (variant 9; the inner FP32 solve's CG products).
 // Per hex the symmetric 24 x 24 operator A_h = aM M_h + aK K_h (the six Kuhn tets summed in FP64, as for
-// variant 7) in component-major DOF order (row x-components of corner slots 0..7, then y, then z), scaled
-// by a power of two so that its largest entry lies in [2^13, 2^14), rounded to FP16, and stored as the
-// packed upper triangle: 300 halves, then the FP32 factor 2^-scale back, then 4 bytes of padding (608-byte
-// records, one bulk copy per tile).  A product stages a tile's records and node rows of p by bulk copies
-// (double-buffered), scales each case's values of p by a power of two into FP16 range per tile, and applies
-// each hex to 8 cases at a time with four mma.sync (m16n8k16 on the x and y columns, m16n8k8 on the z
-// columns, for output rows 0..15 and 16..23): with the component-major order a lane's B operand needs
-// only corner slots 2tq and 2tq + 1 and its outputs are the three components of corner slot gq.  Sums go
-// to the tile accumulator in the packed kernel's fixed point; p^T q is taken at the flush from the tile's
-// sums and its FP32 values of p.  FP16 operands carry ~2.4e-4 of relative error into a product (FP32
-// accumulation): the inner solve's refinement pass removes it, its reduction target is floored at 1e-3.
+// variant 7) in component-major DOF order (rows: x-components of corner slots 0..7, then y, then z), scaled
+// by a power of two so that its largest entry lies in [2^13, 2^14), rounded to FP16.  Of its nine 8 x 8
+// component blocks the six upper ones (xx, xy, xz, yy, yz, zz) are stored row-major (128 bytes each), then
+// the FP32 factor 2^-scale back and padding: 784-byte records.  A tile's records, corner tables and node
+// rows of p arrive by bulk copies; the tile's per-case largest |p| sets a power-of-two scale of p into FP16
+// range.  A warp applies a hex to 8 cases with four mma.sync (m16n8k16 over the x and y columns, m16n8k8
+// over the z columns, for output rows 0..15 and 16..23); the A fragments come from four ldmatrix, the
+// lower blocks as transposes (.trans) of the stored upper ones.  With the component-major order a lane's B
+// operand needs only corner slots 2tq and 2tq + 1, and its outputs are the three components of corner slot
+// gq.  Sums go to the tile accumulator in the packed kernel's fixed point; p^T q is taken at the flush from
+// the tile's sums and its FP32 values of p.  FP16 operands carry ~2.4e-4 of relative error into a product
+// (FP32 accumulation): the inner solve's refinement passes remove it (its reduction target is floored at
+// 1e-3).  Two blocks of 256 threads an SM: the node rows are double-buffered, the records single-buffered
+// (the next tile's records are requested once the hexes of this one are done).
 // ------------------------------------------------------------------------------------------------------
-constexpr int kHm16Bytes = 608;
-constexpr int kTcBlock = 512;
-
-__host__ __device__ constexpr int tri24(int r, int c) { return r * 24 - r * (r - 1) / 2 + (c - r); }
-static_assert(tri24(23, 23) == 299, "300 packed halves");
+constexpr int kHm16Bytes = kHm16RecBytes;
+constexpr int kTcBlock = 256;
+static_assert(kHm16Bytes % 16 == 0 && kHm16Bytes >= 6 * 128 + 4, "six 8 x 8 FP16 blocks and the factor");
 
 // Block (a, b) of the hex operator (corner slots a, b): B[i][k] = A[(i, a), (k, b)].
 __device__ void hex_block(const double* __restrict__ rec, int64_t h, int a, int b, double aM, double aK,
@@ -1759,6 +1760,9 @@ __device__ void hex_block(const double* __restrict__ rec, int64_t h, int a, int 
   }
 }
 
+// Stored component blocks (bi <= bj) in record order: xx, xy, xz, yy, yz, zz.
+__host__ __device__ constexpr int cblk(int bi, int bj) { return bi == 0 ? bj : bi == 1 ? 2 + bj : 5; }
+
 // One thread per hex: the largest entry first, then the scaled FP16 entries.
 __global__ void k_hexmat16_build(int64_t H, const double* __restrict__ rec, double aM, double aK,
                                  unsigned char* __restrict__ out) {
@@ -1774,21 +1778,19 @@ __global__ void k_hexmat16_build(int64_t H, const double* __restrict__ rec, doub
     frexp(mx, &e);                                  // mx < 2^e
     const double sc = mx > 0.0 ? ldexp(1.0, 14 - e) : 1.0;
     __half* o = reinterpret_cast<__half*>(out + h * kHm16Bytes);
+    // entry (r, c) of component block (bi, bj) is A[(bi, r), (bj, c)] = B_rc[bi][bj] with B_cr = B_rc^T
     for (int a = 0; a < 8; ++a)
       for (int b = a; b < 8; ++b) {
         hex_block(rec, h, a, b, aM, aK, B);
-        for (int i = 0; i < 3; ++i)
-          for (int k = (a == b ? i : 0); k < 3; ++k) {
-            int r = 8 * i + a, c = 8 * k + b;
-            if (r > c) {
-              const int t = r;
-              r = c, c = t;
-            }
-            o[tri24(r, c)] = __float2half_rn((float)(B[i][k] * sc));
+        for (int bi = 0; bi < 3; ++bi)
+          for (int bj = bi; bj < 3; ++bj) {
+            __half* blk = o + 64 * cblk(bi, bj);
+            blk[8 * a + b] = __float2half_rn((float)(B[bi][bj] * sc));   // (row a, col b)
+            blk[8 * b + a] = __float2half_rn((float)(B[bj][bi] * sc));   // (row b, col a) = B_ba[bi][bj]
           }
       }
-    *reinterpret_cast<float*>(out + h * kHm16Bytes + 600) = mx > 0.0 ? (float)ldexp(1.0, e - 14) : 1.0f;
-    *reinterpret_cast<float*>(out + h * kHm16Bytes + 604) = 0.0f;
+    *reinterpret_cast<float*>(out + h * kHm16Bytes + 768) = mx > 0.0 ? (float)ldexp(1.0, e - 14) : 1.0f;
+    for (int j = 772; j < kHm16Bytes; j += 4) *reinterpret_cast<float*>(out + h * kHm16Bytes + j) = 0.0f;
   }
 }
 
@@ -1800,22 +1802,21 @@ cudaError_t launch_hexmat16_build(int64_t n_hex, const double* rec64, double aM,
 }
 
 struct TcLayout {
-  size_t qs, ps0, ps1, hm0, hm1, loc0, loc1, node0, node1, total;
+  size_t qs, ps0, ps1, hm, loc0, loc1, node0, node1, total;
 };
 __host__ __device__ inline TcLayout tc_layout(int nloc_max, int rpad, int hex_per_tile) {
   auto up = [](size_t x) { return (x + 127) & ~(size_t)127; };
   TcLayout L;
   const size_t vals = up((size_t)nloc_max * 3 * rpad * sizeof(float));
-  const size_t hms = up((size_t)hex_per_tile * kHm16Bytes);
   const size_t nodes = up(sizeof(int) * (size_t)nloc_max);
-  L.qs = 1024;   // head: 2 mbarriers, per-case |p| maxima x2, back factors, output factors, dot sums
+  const size_t locs = up((size_t)hex_per_tile * 16);
+  L.qs = 1024;   // head: 2 mbarriers, per-case |p| maxima x2, back factors, dot sums
   L.ps0 = L.qs + vals;
   L.ps1 = L.ps0 + vals;
-  L.hm0 = L.ps1 + vals;
-  L.hm1 = L.hm0 + hms;
-  L.loc0 = L.hm1 + hms;                       // the tile's corner tables (16 bytes a hex)
-  L.loc1 = L.loc0 + up((size_t)hex_per_tile * 16);
-  L.node0 = L.loc1 + up((size_t)hex_per_tile * 16);
+  L.hm = L.ps1 + vals;
+  L.loc0 = L.hm + up((size_t)hex_per_tile * kHm16Bytes);
+  L.loc1 = L.loc0 + locs;
+  L.node0 = L.loc1 + locs;
   L.node1 = L.node0 + nodes;
   L.total = L.node1 + nodes;
   return L;
@@ -1835,91 +1836,105 @@ __device__ __forceinline__ void mma_f16_1688(float (&d)[4], uint32_t a0, uint32_
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a0), "r"(a1), "r"(b0));
 }
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2t(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x1t(uint32_t addr, uint32_t& r0) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x1.trans.shared.b16 {%0}, [%1];\n" : "=r"(r0) : "r"(addr));
+}
 __device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
   const __half2 h = __floats2half2_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
-__device__ __forceinline__ uint32_t pack_h(unsigned short lo, unsigned short hi) {
-  return (uint32_t)lo | ((uint32_t)hi << 16);
-}
 
-template <bool DOT>
-__global__ void __launch_bounds__(kTcBlock, 1) k_ebe_hex_tc(HexTiles ht, MeshView m, int rpad, int rshift,
-                                                         const float* __restrict__ p, float* __restrict__ q,
-                                                         const unsigned char* __restrict__ hm, float aM, float aK,
-                                                         Reducer red, CgCase* sc, double* ptq_out, const int* gate) {
+template <bool DOT, int R>
+__global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshView m, const float* __restrict__ p,
+                                                         float* __restrict__ q, const unsigned char* __restrict__ hm,
+                                                         float aM, float aK, Reducer red, CgCase* sc,
+                                                         double* ptq_out, const int* gate) {
   if (gate && *gate == 0) return;
+  constexpr int rpad = R, per_node = 3 * R, f4 = per_node / 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const TcLayout L = tc_layout(ht.nloc_max, rpad, ht.hex_per_tile);
+  const TcLayout L = tc_layout(ht.nloc_max, R, ht.hex_per_tile);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);
   int* spm = reinterpret_cast<int*>(smem_raw + 32);          // [2][32] per-case max |p| bits, per tile parity
   float* sfwd = reinterpret_cast<float*>(smem_raw + 288);    // [32] fixed point back to FP32
-  float* sfx = reinterpret_cast<float*>(smem_raw + 416);     // [32] MMA output (scaled p) to fixed point
-  float* sps = reinterpret_cast<float*>(smem_raw + 544);     // [32] scale of p into FP16 range
   double* sdot = reinterpret_cast<double*>(smem_raw + 768);  // [32] p^T q sums of the block
   int* qs = reinterpret_cast<int*>(smem_raw + L.qs);
+  unsigned char* hs = smem_raw + L.hm;
   auto psb = [&](int b) { return reinterpret_cast<float*>(smem_raw + (b ? L.ps1 : L.ps0)); };
-  auto hmb = [&](int b) { return smem_raw + (b ? L.hm1 : L.hm0); };
   auto slb = [&](int b) { return reinterpret_cast<const uint32_t*>(smem_raw + (b ? L.loc1 : L.loc0)); };
   auto snb = [&](int b) { return reinterpret_cast<int*>(smem_raw + (b ? L.node1 : L.node0)); };
-  const int per_node = 3 * rpad;
-  const uint32_t node_bytes = (uint32_t)(per_node * sizeof(float));
+  constexpr uint32_t node_bytes = (uint32_t)(per_node * sizeof(float));
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(smem_u32(&mbar[0]), 1);
     mbar_init(smem_u32(&mbar[1]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = tid; i < (ht.nloc_max * per_node) >> 2; i += blockDim.x)
-    reinterpret_cast<int4*>(qs)[i] = make_int4(0, 0, 0, 0);
+  for (int i = tid; i < ht.nloc_max * f4; i += kTcBlock) reinterpret_cast<int4*>(qs)[i] = make_int4(0, 0, 0, 0);
   if (tid < 64) spm[tid] = 0;
   if (tid < 32) sdot[tid] = 0.0;
   __syncthreads();
-  auto load_node = [&](int t) {   // node id of this thread's tile-local node of tile t (tiles hold <= blockDim nodes)
-    if (t >= ht.n_tiles) return 0;
-    const int n0 = ht.tile_node_off[t];
-    return tid < ht.tile_node_off[t + 1] - n0 ? ht.tile_nodes[n0 + tid] : 0;
-  };
-  auto issue = [&](int t, int b, int nd) {
+  // node rows and corner tables of tile t into buffer b (bytes of the tile's records counted too: they are
+  // requested by request_records once the record buffer is free)
+  auto issue = [&](int t, int b) {
     const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
     const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
     const uint32_t bar = smem_u32(mbar + b);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (tid == 0) {
-      const uint32_t hbytes = (uint32_t)(nh * kHm16Bytes), lbytes = (uint32_t)(nh * 16);
-      mbar_expect_tx(bar, hbytes + lbytes + (uint32_t)nl * node_bytes);
-      bulk_g2s(smem_u32(hmb(b)), hm + (int64_t)h0 * kHm16Bytes, hbytes, bar);
+      const uint32_t lbytes = (uint32_t)(nh * 16);
+      mbar_expect_tx(bar, (uint32_t)(nh * kHm16Bytes) + lbytes + (uint32_t)nl * node_bytes);
       bulk_g2s(smem_u32(slb(b)), ht.hex_local + h0, lbytes, bar);
     }
-    if (tid < nl) {
-      snb(b)[tid] = nd;
-      bulk_g2s(smem_u32(psb(b) + (int64_t)tid * per_node), p + (int64_t)(nd & 0x0fffffff) * per_node, node_bytes,
-               bar);
+    for (int l = tid; l < nl; l += kTcBlock) {
+      const int nd = ht.tile_nodes[n0 + l];
+      snb(b)[l] = nd;
+      bulk_g2s(smem_u32(psb(b) + l * per_node), p + (int64_t)(nd & 0x0fffffff) * per_node, node_bytes, bar);
     }
   };
-  // the lane's fragment coordinates and the packed indices of its 18 A entries (constant over the hexes)
-  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  auto request_records = [&](int t, int b) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) {
+      const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
+      bulk_g2s(smem_u32(hs), hm + (int64_t)h0 * kHm16Bytes, (uint32_t)(nh * kHm16Bytes), smem_u32(mbar + b));
+    }
+  };
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int nwarp = kTcBlock / 32;
   const int gq = lane >> 2, tq = lane & 3;
-  auto pidx = [](int r, int c) { return r <= c ? tri24(r, c) : tri24(c, r); };
-  const int k0 = 2 * tq;
-  const int ia[18] = {pidx(gq, k0),          pidx(gq, k0 + 1),          pidx(gq + 8, k0),      pidx(gq + 8, k0 + 1),
-                      pidx(gq, k0 + 8),      pidx(gq, k0 + 9),          pidx(gq + 8, k0 + 8),  pidx(gq + 8, k0 + 9),
-                      pidx(gq, 16 + k0),     pidx(gq, 17 + k0),         pidx(gq + 8, 16 + k0), pidx(gq + 8, 17 + k0),
-                      pidx(16 + gq, k0),     pidx(16 + gq, k0 + 1),     pidx(16 + gq, k0 + 8), pidx(16 + gq, k0 + 9),
-                      pidx(16 + gq, 16 + k0), pidx(16 + gq, 17 + k0)};
+  // ldmatrix row addresses of the lane (byte offsets in a record): x4 {xx, xy, yy, xz}, x2 {yz, zz},
+  // x2.trans {xy, xz} (giving yx, zx), x1.trans {yz} (giving zy)
+  const int r16 = (lane & 7) * 16;
+  const uint32_t o_x4 = (uint32_t)(128 * ((lane >> 3) == 0 ? 0 : (lane >> 3) == 1 ? 1 : (lane >> 3) == 2 ? 3 : 2) + r16);
+  const uint32_t o_x2 = (uint32_t)(128 * ((lane & 8) ? 5 : 4) + r16);
+  const uint32_t o_t2 = (uint32_t)(128 * ((lane & 8) ? 2 : 1) + r16);
+  const uint32_t o_t1 = (uint32_t)(128 * 4 + r16);
+  const uint32_t hs_u32 = smem_u32(hs);
   const float bco = fabsf(aM) * ht.abs_m + fabsf(aK) * ht.abs_k;
+  auto pow2 = [](int e) { return __uint_as_float((uint32_t)min(max(e + 127, 1), 254) << 23); };
   float4 tdot = make_float4(0.f, 0.f, 0.f, 0.f);
   double dd[4] = {0.0, 0.0, 0.0, 0.0};
   const int t0 = blockIdx.x;
-  int nd_next = load_node(t0 + gridDim.x);
-  if (t0 < ht.n_tiles) issue(t0, 0, load_node(t0));
+  if (t0 < ht.n_tiles) {
+    issue(t0, 0);
+    request_records(t0, 0);
+  }
   for (int k = 0;; ++k) {
     const int t = t0 + k * gridDim.x;
     if (t >= ht.n_tiles) break;
     const int b = k & 1;
     const int tn = t + gridDim.x;
-    if (tn < ht.n_tiles) issue(tn, b ^ 1, nd_next);
-    const int nd_after = load_node(tn + gridDim.x);
+    if (tn < ht.n_tiles) issue(tn, b ^ 1);
     const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
     const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
     const uint32_t bar = smem_u32(mbar + b);
@@ -1927,97 +1942,99 @@ __global__ void __launch_bounds__(kTcBlock, 1) k_ebe_hex_tc(HexTiles ht, MeshVie
       atomicExch(&g_tma_timeout, 1);
       mbar_wait(bar, (uint32_t)((k >> 1) & 1));   // second bounded wait for the copies still in flight
     }
-    __syncthreads();
     const float* ps = psb(b);
-    const unsigned char* hs = hmb(b);
     const uint32_t* sl = slb(b);
     const int* snode = snb(b);
-    // per-case largest |p| of the staged tile: the fixed-point scale (as the packed kernel) and the scale of
-    // p into FP16 range (its largest value below 2^14)
+    // per-case largest |p| of the staged tile (a thread's values all belong to case tid mod R)
     {
       float mx = 0.f;
-      for (int i = tid; i < nl * per_node; i += blockDim.x) mx = fmaxf(mx, fabsf(ps[i]));
-      for (int off = 16; off >= rpad; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-      int* spm_b = spm + (b << 5);
-      if ((tid & 31) < rpad) atomicMax(spm_b + (tid & 31), __float_as_int(mx));
-      if (tid < rpad) spm[((b ^ 1) << 5) + tid] = 0;   // the next tile's buffer
-      __syncthreads();
-      if (tid < rpad) {
-        auto pow2 = [](int e) { return __uint_as_float((uint32_t)min(max(e + 127, 1), 254) << 23); };
-        const uint32_t fb = (__float_as_uint(bco * __int_as_float(spm_b[tid])) >> 23) & 0xffu;
-        const int E = fb == 0u ? -126 : (int)fb - 126;                      // bound < 2^E
-        const uint32_t fp = ((uint32_t)spm_b[tid] >> 23) & 0xffu;
-        const int ep = fp == 0u ? -126 : (int)fp - 126;                      // max |p| < 2^ep
-        sfwd[tid] = pow2(E - 30);
-        sps[tid] = pow2(14 - ep);
-        sfx[tid] = pow2(30 - E - (14 - ep));
-      }
-      __syncthreads();
+      for (int i = tid; i < nl * per_node; i += kTcBlock) mx = fmaxf(mx, fabsf(ps[i]));
+      for (int off = 16; off >= R; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if (lane < R) atomicMax(spm + (b << 5) + lane, __float_as_int(mx));
     }
-    const int nt_n = rpad >> 3;
+    __syncthreads();
+    const int* spm_b = spm + (b << 5);
+    // per case: E (the fixed-point bound 2^E), ep (max |p| < 2^ep); p enters FP16 as p 2^(14 - ep), sums
+    // leave to fixed point by 2^(30 - E - (14 - ep))
+    auto expo_b = [&](int c) {
+      const uint32_t fb = (__float_as_uint(bco * __int_as_float(spm_b[c])) >> 23) & 0xffu;
+      return fb == 0u ? -126 : (int)fb - 126;
+    };
+    auto expo_p = [&](int c) {
+      const uint32_t fp = ((uint32_t)spm_b[c] >> 23) & 0xffu;
+      return fp == 0u ? -126 : (int)fp - 126;
+    };
+    float s_in[R / 8], f_out0[R / 8], f_out1[R / 8];
+#pragma unroll
+    for (int nt = 0; nt < R / 8; ++nt) {
+      const int cn = nt * 8 + gq, c = nt * 8 + 2 * tq;
+      s_in[nt] = pow2(14 - expo_p(cn));
+      f_out0[nt] = pow2(30 - expo_b(c) - 14 + expo_p(c));
+      f_out1[nt] = pow2(30 - expo_b(c + 1) - 14 + expo_p(c + 1));
+    }
+    if (tid < R) {
+      sfwd[tid] = pow2(expo_b(tid) - 30);
+      spm[((b ^ 1) << 5) + tid] = 0;   // the next tile's maxima
+    }
     for (int hl = warp; hl < nh; hl += nwarp) {
       const uint32_t wb = sl[4 * hl + tq], wo = sl[4 * hl + (gq >> 1)];
-      const int cb0 = (int)(wb & 0xffffu), cb1 = (int)(wb >> 16);
-      const int co = (int)((wo >> ((gq & 1) << 4)) & 0xffffu);
-      const unsigned short* hh = reinterpret_cast<const unsigned short*>(hs + hl * kHm16Bytes);
-      const float hu = *reinterpret_cast<const float*>(hs + hl * kHm16Bytes + 600);
-      const uint32_t a0 = pack_h(hh[ia[0]], hh[ia[1]]), a1 = pack_h(hh[ia[2]], hh[ia[3]]);
-      const uint32_t a2 = pack_h(hh[ia[4]], hh[ia[5]]), a3 = pack_h(hh[ia[6]], hh[ia[7]]);
-      const uint32_t a4 = pack_h(hh[ia[8]], hh[ia[9]]), a5 = pack_h(hh[ia[10]], hh[ia[11]]);
-      const uint32_t a6 = pack_h(hh[ia[12]], hh[ia[13]]), a7 = pack_h(hh[ia[14]], hh[ia[15]]);
-      const uint32_t a8 = pack_h(hh[ia[16]], hh[ia[17]]);
-      const float* p0 = ps + cb0 * per_node;
-      const float* p1 = ps + cb1 * per_node;
-      int* dst = qs + co * per_node;
-      for (int nt = 0; nt < nt_n; ++nt) {
-        const int cn = (nt << 3) + gq;   // the case of the lane's B operand
-        const float s = sps[cn];
+      const float* p0 = ps + (int)(wb & 0xffffu) * per_node;
+      const float* p1 = ps + (int)(wb >> 16) * per_node;
+      int* dst = qs + (int)((wo >> ((gq & 1) << 4)) & 0xffffu) * per_node;
+      const uint32_t rb = hs_u32 + (uint32_t)(hl * kHm16Bytes);
+      const float hu = *reinterpret_cast<const float*>(hs + hl * kHm16Bytes + 768);
+      uint32_t xx, xy, yy, xz, yz, zz, yx, zx, zy;
+      ldsm_x4(rb + o_x4, xx, xy, yy, xz);
+      ldsm_x2(rb + o_x2, yz, zz);
+      ldsm_x2t(rb + o_t2, yx, zx);
+      ldsm_x1t(rb + o_t1, zy);
+#pragma unroll
+      for (int nt = 0; nt < R / 8; ++nt) {
+        const int cn = nt * 8 + gq;   // the case of the lane's B operand
+        const float s = s_in[nt];
         const uint32_t b0 = pack_f16(p0[cn] * s, p1[cn] * s);
-        const uint32_t b1 = pack_f16(p0[rpad + cn] * s, p1[rpad + cn] * s);
-        const uint32_t b2 = pack_f16(p0[2 * rpad + cn] * s, p1[2 * rpad + cn] * s);
+        const uint32_t b1 = pack_f16(p0[R + cn] * s, p1[R + cn] * s);
+        const uint32_t b2 = pack_f16(p0[2 * R + cn] * s, p1[2 * R + cn] * s);
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_f16_16816(d0, a0, a1, a2, a3, b0, b1);
-        mma_f16_1688(d0, a4, a5, b2);
-        mma_f16_16816(d1, a6, 0u, a7, 0u, b0, b1);
-        mma_f16_1688(d1, a8, 0u, b2);
+        mma_f16_16816(d0, xx, yx, xy, yy, b0, b1);   // rows x, y; columns x, y
+        mma_f16_1688(d0, xz, yz, b2);                // rows x, y; columns z
+        mma_f16_16816(d1, zx, 0u, zy, 0u, b0, b1);   // rows z; columns x, y
+        mma_f16_1688(d1, zz, 0u, b2);                // rows z; columns z
         // rows gq (x), gq + 8 (y), 16 + gq (z) of corner slot gq; columns: cases c, c + 1
-        const int c = (nt << 3) + 2 * tq;
-        const float f0 = hu * sfx[c], f1 = hu * sfx[c + 1];
-        atomicAdd(dst + c, __float2int_rn(d0[0] * f0));
-        atomicAdd(dst + c + 1, __float2int_rn(d0[1] * f1));
-        atomicAdd(dst + rpad + c, __float2int_rn(d0[2] * f0));
-        atomicAdd(dst + rpad + c + 1, __float2int_rn(d0[3] * f1));
-        atomicAdd(dst + 2 * rpad + c, __float2int_rn(d1[0] * f0));
-        atomicAdd(dst + 2 * rpad + c + 1, __float2int_rn(d1[1] * f1));
+        const int c = nt * 8 + 2 * tq;
+        const float g0 = hu * f_out0[nt], g1 = hu * f_out1[nt];
+        atomicAdd(dst + c, __float2int_rn(d0[0] * g0));
+        atomicAdd(dst + c + 1, __float2int_rn(d0[1] * g1));
+        atomicAdd(dst + R + c, __float2int_rn(d0[2] * g0));
+        atomicAdd(dst + R + c + 1, __float2int_rn(d0[3] * g1));
+        atomicAdd(dst + 2 * R + c, __float2int_rn(d1[0] * g0));
+        atomicAdd(dst + 2 * R + c + 1, __float2int_rn(d1[1] * g1));
       }
     }
     __syncthreads();
+    if (tn < ht.n_tiles) request_records(tn, b ^ 1);   // the record buffer is free: the next tile's records
     // flush: float4 pieces (four cases of one component of one node) to the output; p^T q from the tile's
-    // sums and its FP32 values of p (a thread's four cases are fixed: 4 blockDim is a multiple of rpad)
-    {
-      const int sh4 = rshift - 2;
-      const int f4 = per_node >> 2;
-      for (int i = tid; i < nl * f4; i += blockDim.x) {
-        const int l = (i >> sh4) / 3, kk = (i - l * f4) >> sh4;
-        const int raw = snode[l];
-        const int64_t g = raw & 0x0fffffff;
-        const bool fixed = !dof_free((uint8_t)((raw >> 28) & 7), kk);
-        float4* dstg = reinterpret_cast<float4*>(q + g * per_node) + (i - l * f4);
-        const int4 vi = reinterpret_cast<const int4*>(qs)[i];
-        const int c4 = (i << 2) & (rpad - 1);
-        const float4 v = make_float4((float)vi.x * sfwd[c4], (float)vi.y * sfwd[c4 + 1], (float)vi.z * sfwd[c4 + 2],
-                                     (float)vi.w * sfwd[c4 + 3]);
-        reinterpret_cast<int4*>(qs)[i] = make_int4(0, 0, 0, 0);
-        if (DOT && !fixed) {
-          const float4 pv = reinterpret_cast<const float4*>(ps)[i];
-          tdot.x = fmaf(pv.x, v.x, tdot.x), tdot.y = fmaf(pv.y, v.y, tdot.y);
-          tdot.z = fmaf(pv.z, v.z, tdot.z), tdot.w = fmaf(pv.w, v.w, tdot.w);
-        }
-        if (raw < 0) {
-          if (!fixed) atomicAdd(dstg, v);
-        } else {
-          *dstg = fixed ? make_float4(0.f, 0.f, 0.f, 0.f) : v;
-        }
+    // sums and its FP32 values of p (a thread's four cases are fixed: 4 kTcBlock is a multiple of R)
+    for (int i = tid; i < nl * f4; i += kTcBlock) {
+      const int l = i / f4, kk = (i - l * f4) / (R / 4);
+      const int raw = snode[l];
+      const int64_t g = raw & 0x0fffffff;
+      const bool fixed = !dof_free((uint8_t)((raw >> 28) & 7), kk);
+      float4* dstg = reinterpret_cast<float4*>(q + g * per_node) + (i - l * f4);
+      const int4 vi = reinterpret_cast<const int4*>(qs)[i];
+      const int c4 = (i << 2) & (R - 1);
+      const float4 v = make_float4((float)vi.x * sfwd[c4], (float)vi.y * sfwd[c4 + 1], (float)vi.z * sfwd[c4 + 2],
+                                   (float)vi.w * sfwd[c4 + 3]);
+      reinterpret_cast<int4*>(qs)[i] = make_int4(0, 0, 0, 0);
+      if (DOT && !fixed) {
+        const float4 pv = reinterpret_cast<const float4*>(ps)[i];
+        tdot.x = fmaf(pv.x, v.x, tdot.x), tdot.y = fmaf(pv.y, v.y, tdot.y);
+        tdot.z = fmaf(pv.z, v.z, tdot.z), tdot.w = fmaf(pv.w, v.w, tdot.w);
+      }
+      if (raw < 0) {
+        if (!fixed) atomicAdd(dstg, v);
+      } else {
+        *dstg = fixed ? make_float4(0.f, 0.f, 0.f, 0.f) : v;
       }
     }
     if (DOT) {
@@ -2025,20 +2042,19 @@ __global__ void __launch_bounds__(kTcBlock, 1) k_ebe_hex_tc(HexTiles ht, MeshVie
       tdot = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    nd_next = nd_after;
   }
   if (DOT) {
-    const int c4 = (tid << 2) & (rpad - 1);
+    const int c4 = (tid << 2) & (R - 1);
 #pragma unroll
     for (int j = 0; j < 4; ++j) atomicAdd(sdot + c4 + j, dd[j]);
     __syncthreads();
-    double v[1] = {tid < rpad ? sdot[tid] : 0.0};
-    if (block_reduce_last<1>(v, rpad, red)) ebe_tail(red, sc, ptq_out, rpad);
+    double v[1] = {tid < R ? sdot[tid] : 0.0};
+    if (block_reduce_last<1>(v, R, red)) ebe_tail(red, sc, ptq_out, R);
   }
 }
 
 size_t ebe_hex_tc_smem(const HexTiles& ht, int rpad) {
-  if (ht.nloc_max > kTcBlock || ht.hex_per_tile > 64 || (rpad != 8 && rpad != 16)) return ~(size_t)0;
+  if (ht.hex_per_tile > 64 || (rpad != 8 && rpad != 16)) return ~(size_t)0;
   return tc_layout(ht.nloc_max, rpad, ht.hex_per_tile).total;
 }
 
@@ -2050,15 +2066,19 @@ cudaError_t launch_ebe_hex_tc(const HexTiles& ht, const MeshView& m, const unsig
     return cudaErrorInvalidValue;
   cudaError_t err = cudaMemsetAsync(q, 0, sizeof(float) * (size_t)m.N * 3 * rpad, s);
   if (err != cudaSuccess) return err;
-  auto kfn = red ? k_ebe_hex_tc<true> : k_ebe_hex_tc<false>;
+  auto kfn = rpad == 8 ? (red ? k_ebe_hex_tc<true, 8> : k_ebe_hex_tc<false, 8>)
+                       : (red ? k_ebe_hex_tc<true, 16> : k_ebe_hex_tc<false, 16>);
   err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 1;
+  if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kTcBlock, smem);
   if (err != cudaSuccess) return err;
-  int grid = sm_count();
+  if (per_sm < 1) per_sm = 1;
+  int grid = sm_count() * per_sm;
   if (grid > ht.n_tiles) grid = ht.n_tiles;
   if (grid > red_grid_cap()) grid = red_grid_cap();
   Reducer rd = red ? *red : Reducer{nullptr, nullptr, nullptr};
-  kfn<<<grid, kTcBlock, smem, s>>>(ht, m, rpad, log2i(rpad), p, q, hm16, (float)aM, (float)aK, rd,
-                                   red ? sc : nullptr, red ? ptq_out : nullptr, gate);
+  kfn<<<grid, kTcBlock, smem, s>>>(ht, m, p, q, hm16, (float)aM, (float)aK, rd, red ? sc : nullptr,
+                                   red ? ptq_out : nullptr, gate);
   return cudaGetLastError();
 }
 
