@@ -1976,62 +1976,39 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshVie
       sfwd[tid] = pow2(expo_b(tid) - 30);
       spm[((b ^ 1) << 5) + tid] = 0;   // the next tile's maxima
     }
-    // two hexes a warp at a time (hl and hl + nwarp): both hexes' operands are loaded before either's
-    // products, so their shared-memory latencies overlap
-    struct HexOps {
-      uint32_t xx, xy, yy, xz, yz, zz, yx, zx, zy;
-      const float* p0;
-      const float* p1;
-      int* dst;
-      float hu;
-    };
-    auto load_ops = [&](int hl, HexOps& o) {
+    for (int hl = warp; hl < nh; hl += nwarp) {
       const uint32_t wb = sl[4 * hl + tq], wo = sl[4 * hl + (gq >> 1)];
-      o.p0 = ps + (int)(wb & 0xffffu) * per_node;
-      o.p1 = ps + (int)(wb >> 16) * per_node;
-      o.dst = qs + (int)((wo >> ((gq & 1) << 4)) & 0xffffu) * per_node;
+      const float* p0 = ps + (int)(wb & 0xffffu) * per_node;
+      const float* p1 = ps + (int)(wb >> 16) * per_node;
+      int* dst = qs + (int)((wo >> ((gq & 1) << 4)) & 0xffffu) * per_node;
       const uint32_t rb = hs_u32 + (uint32_t)(hl * kHm16Bytes);
-      o.hu = *reinterpret_cast<const float*>(hs + hl * kHm16Bytes + 768);
-      ldsm_x4(rb + o_x4, o.xx, o.xy, o.yy, o.xz);
-      ldsm_x2(rb + o_x2, o.yz, o.zz);
-      ldsm_x2t(rb + o_t2, o.yx, o.zx);
-      ldsm_x1t(rb + o_t1, o.zy);
-    };
-    auto apply = [&](const HexOps& o, int nt, float (&d0)[4], float (&d1)[4]) {
-      const int cn = nt * 8 + gq;   // the case of the lane's B operand
-      const float s = s_in[nt];
-      const uint32_t b0 = pack_f16(o.p0[cn] * s, o.p1[cn] * s);
-      const uint32_t b1 = pack_f16(o.p0[R + cn] * s, o.p1[R + cn] * s);
-      const uint32_t b2 = pack_f16(o.p0[2 * R + cn] * s, o.p1[2 * R + cn] * s);
-      mma_f16_16816(d0, o.xx, o.yx, o.xy, o.yy, b0, b1);   // rows x, y; columns x, y
-      mma_f16_1688(d0, o.xz, o.yz, b2);                    // rows x, y; columns z
-      mma_f16_16816(d1, o.zx, 0u, o.zy, 0u, b0, b1);       // rows z; columns x, y
-      mma_f16_1688(d1, o.zz, 0u, b2);                      // rows z; columns z
-    };
-    // rows gq (x), gq + 8 (y), 16 + gq (z) of corner slot gq; columns: cases c, c + 1
-    auto scatter = [&](const HexOps& o, int nt, const float (&d0)[4], const float (&d1)[4]) {
-      const int c = nt * 8 + 2 * tq;
-      const float g0 = o.hu * f_out0[nt], g1 = o.hu * f_out1[nt];
-      atomicAdd(o.dst + c, __float2int_rn(d0[0] * g0));
-      atomicAdd(o.dst + c + 1, __float2int_rn(d0[1] * g1));
-      atomicAdd(o.dst + R + c, __float2int_rn(d0[2] * g0));
-      atomicAdd(o.dst + R + c + 1, __float2int_rn(d0[3] * g1));
-      atomicAdd(o.dst + 2 * R + c, __float2int_rn(d1[0] * g0));
-      atomicAdd(o.dst + 2 * R + c + 1, __float2int_rn(d1[1] * g1));
-    };
-    for (int hl = warp; hl < nh; hl += 2 * nwarp) {
-      const bool two = hl + nwarp < nh;
-      HexOps oa, ob;
-      load_ops(hl, oa);
-      if (two) load_ops(hl + nwarp, ob);
+      const float hu = *reinterpret_cast<const float*>(hs + hl * kHm16Bytes + 768);
+      uint32_t xx, xy, yy, xz, yz, zz, yx, zx, zy;
+      ldsm_x4(rb + o_x4, xx, xy, yy, xz);
+      ldsm_x2(rb + o_x2, yz, zz);
+      ldsm_x2t(rb + o_t2, yx, zx);
+      ldsm_x1t(rb + o_t1, zy);
 #pragma unroll
       for (int nt = 0; nt < R / 8; ++nt) {
-        float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
-        float b0[4] = {0.f, 0.f, 0.f, 0.f}, b1[4] = {0.f, 0.f, 0.f, 0.f};
-        apply(oa, nt, a0, a1);
-        if (two) apply(ob, nt, b0, b1);
-        scatter(oa, nt, a0, a1);
-        if (two) scatter(ob, nt, b0, b1);
+        const int cn = nt * 8 + gq;   // the case of the lane's B operand
+        const float s = s_in[nt];
+        const uint32_t b0 = pack_f16(p0[cn] * s, p1[cn] * s);
+        const uint32_t b1 = pack_f16(p0[R + cn] * s, p1[R + cn] * s);
+        const uint32_t b2 = pack_f16(p0[2 * R + cn] * s, p1[2 * R + cn] * s);
+        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_f16_16816(d0, xx, yx, xy, yy, b0, b1);   // rows x, y; columns x, y
+        mma_f16_1688(d0, xz, yz, b2);                // rows x, y; columns z
+        mma_f16_16816(d1, zx, 0u, zy, 0u, b0, b1);   // rows z; columns x, y
+        mma_f16_1688(d1, zz, 0u, b2);                // rows z; columns z
+        // rows gq (x), gq + 8 (y), 16 + gq (z) of corner slot gq; columns: cases c, c + 1
+        const int c = nt * 8 + 2 * tq;
+        const float g0 = hu * f_out0[nt], g1 = hu * f_out1[nt];
+        atomicAdd(dst + c, __float2int_rn(d0[0] * g0));
+        atomicAdd(dst + c + 1, __float2int_rn(d0[1] * g1));
+        atomicAdd(dst + R + c, __float2int_rn(d0[2] * g0));
+        atomicAdd(dst + R + c + 1, __float2int_rn(d0[3] * g1));
+        atomicAdd(dst + 2 * R + c, __float2int_rn(d1[0] * g0));
+        atomicAdd(dst + 2 * R + c + 1, __float2int_rn(d1[1] * g1));
       }
     }
     __syncthreads();
