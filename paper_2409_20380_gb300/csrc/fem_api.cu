@@ -263,8 +263,8 @@ struct fem_mesh {
   std::vector<Workspace*> ws;
   // tiled hex-patch EBE (present when the elements come in Kuhn hex patches)
   bool hex = false;
-  static constexpr int kNTile = 4;
-  HexTiles tiles[kNTile];          // hex_per_tile 64, 128, 256, 512
+  static constexpr int kNTile = 5;
+  HexTiles tiles[kNTile];          // hex_per_tile 32, 64, 128, 256, 512
   std::vector<void*> tile_bufs;
   int ebe_variant = 0;             // 0 auto, 1 generic, 2 tiled hex, 3 staged, 4 case-major, 5/6 packed staged,
                                    // 7 hex element matrices, 8 assembled 3x3 blocks (CRS-style comparator)
@@ -475,7 +475,7 @@ static cudaError_t ebe_elem_product(const fem_mesh* m, int rpad, const T* p, T* 
   m->resolve(sizeof(T), rpad, &v, &h);
   if (tc || v == 9) {   // FP16 hex matrices on the tensor cores: FP32, the mesh's own coefficients, 8 or 16 cases
     if constexpr (sizeof(T) == 4) {
-      const HexTiles* t = m->npe == 4 && !m->seg ? m->tiles_for(4, rpad, 9, 64) : nullptr;
+      const HexTiles* t = m->npe == 4 && !m->seg ? m->tiles_for(4, rpad, 9, 32) : nullptr;
       cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
       auto same = [](double x, double y) { return std::fabs(x - y) <= 1e-12 * std::fabs(y); };
       if (t && (rpad == 8 || rpad == 16) && same(aM, m->cM) && same(aK, m->cK) &&
@@ -1879,7 +1879,7 @@ static fem_status mesh_create(int64_t n_nodes, const double* xyz, int64_t n_elem
   // tile node entries carry the node id (bits 0-27), its three free-DOF bits (28-30) and whether another
   // tile shares the node (bit 31): the kernels' flush needs no separate mask load
   if (npe == 4 && n_nodes < (int64_t(1) << 28) && detect_hex_patches(conn, n_elems)) {
-    const int sizes[fem_mesh::kNTile] = {64, 128, 256, 512};
+    const int sizes[fem_mesh::kNTile] = {32, 64, 128, 256, 512};
     bool ok = true;
     double abs_m = 0.0, abs_k = 0.0;   // scale bounds of the packed kernel's fixed-point tile sums
     {
