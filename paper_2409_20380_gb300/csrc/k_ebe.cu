@@ -1726,8 +1726,8 @@ cudaError_t launch_ebe_split_df(const MeshView& m, const float* rec_df, int rpad
 // gq.  Sums go to the tile accumulator in the packed kernel's fixed point; p^T q is taken at the flush from
 // the tile's sums and its FP32 values of p.  FP16 operands carry ~2.4e-4 of relative error into a product
 // (FP32 accumulation): the inner solve's refinement passes remove it (its reduction target is floored at
-// 1e-3).  Two blocks of 256 threads an SM: the node rows are double-buffered, the records single-buffered
-// (the next tile's records are requested once the hexes of this one are done).
+// 1e-3).  Tiles of 32 hexes, three blocks of 256 threads an SM: the node rows are double-buffered, the
+// records single-buffered (the next tile's records are requested once the hexes of this one are done).
 // ------------------------------------------------------------------------------------------------------
 constexpr int kHm16Bytes = kHm16RecBytes;
 constexpr int kTcBlock = 256;
@@ -1855,20 +1855,8 @@ __device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-__device__ __forceinline__ void mma_f16_16816_z(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                                uint32_t b0, uint32_t b1) {   // d = A B (zero accumulator)
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%10,%10,%10,%10};\n"
-      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(0.f));
-}
-
-// Per tile (buffer b = tile parity): node rows and corner tables arrive on mbar[b] (double-buffered), the
-// records on mbar[2] (single buffer).  Two block barriers a tile: after the hexes (the records of the next
-// tile may then be requested), and after the flush of this tile and the per-case maxima of the next one.
 template <bool DOT, int R>
-__global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshView m, const float* __restrict__ p,
+__global__ void __launch_bounds__(kTcBlock, 3) k_ebe_hex_tc(HexTiles ht, MeshView m, const float* __restrict__ p,
                                                          float* __restrict__ q, const unsigned char* __restrict__ hm,
                                                          float aM, float aK, Reducer red, CgCase* sc,
                                                          double* ptq_out, const int* gate) {
@@ -1876,9 +1864,9 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshVie
   constexpr int rpad = R, per_node = 3 * R, f4 = per_node / 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const TcLayout L = tc_layout(ht.nloc_max, R, ht.hex_per_tile);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);     // [0], [1] node rows, [2] records
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);
   int* spm = reinterpret_cast<int*>(smem_raw + 32);          // [2][32] per-case max |p| bits, per tile parity
-  float* sfwd = reinterpret_cast<float*>(smem_raw + 288);    // [2][32] fixed point back to FP32, per parity
+  float* sfwd = reinterpret_cast<float*>(smem_raw + 288);    // [32] fixed point back to FP32
   double* sdot = reinterpret_cast<double*>(smem_raw + 768);  // [32] p^T q sums of the block
   int* qs = reinterpret_cast<int*>(smem_raw + L.qs);
   unsigned char* hs = smem_raw + L.hm;
@@ -1890,21 +1878,22 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshVie
   if (tid == 0) {
     mbar_init(smem_u32(&mbar[0]), 1);
     mbar_init(smem_u32(&mbar[1]), 1);
-    mbar_init(smem_u32(&mbar[2]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int i = tid; i < ht.nloc_max * f4; i += kTcBlock) reinterpret_cast<int4*>(qs)[i] = make_int4(0, 0, 0, 0);
   if (tid < 64) spm[tid] = 0;
   if (tid < 32) sdot[tid] = 0.0;
   __syncthreads();
-  auto issue = [&](int t, int b) {   // node rows and corner tables of tile t into buffer b
+  // node rows and corner tables of tile t into buffer b (bytes of the tile's records counted too: they are
+  // requested by request_records once the record buffer is free)
+  auto issue = [&](int t, int b) {
     const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
     const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
     const uint32_t bar = smem_u32(mbar + b);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (tid == 0) {
       const uint32_t lbytes = (uint32_t)(nh * 16);
-      mbar_expect_tx(bar, lbytes + (uint32_t)nl * node_bytes);
+      mbar_expect_tx(bar, (uint32_t)(nh * kHm16Bytes) + lbytes + (uint32_t)nl * node_bytes);
       bulk_g2s(smem_u32(slb(b)), ht.hex_local + h0, lbytes, bar);
     }
     for (int l = tid; l < nl; l += kTcBlock) {
@@ -1913,30 +1902,12 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshVie
       bulk_g2s(smem_u32(psb(b) + l * per_node), p + (int64_t)(nd & 0x0fffffff) * per_node, node_bytes, bar);
     }
   };
-  auto request_records = [&](int t) {   // the record buffer is free: tile t's records
+  auto request_records = [&](int t, int b) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (tid == 0) {
       const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
-      const uint32_t bar = smem_u32(mbar + 2), bytes = (uint32_t)(nh * kHm16Bytes);
-      mbar_expect_tx(bar, bytes);
-      bulk_g2s(smem_u32(hs), hm + (int64_t)h0 * kHm16Bytes, bytes, bar);
+      bulk_g2s(smem_u32(hs), hm + (int64_t)h0 * kHm16Bytes, (uint32_t)(nh * kHm16Bytes), smem_u32(mbar + b));
     }
-  };
-  auto wait = [&](int which, uint32_t parity) {
-    const uint32_t bar = smem_u32(mbar + which);
-    if (!mbar_wait(bar, parity, g_wait_budget)) {
-      atomicExch(&g_tma_timeout, 1);
-      mbar_wait(bar, parity);   // second bounded wait for the copies still in flight
-    }
-  };
-  // per-case largest |p| of tile buffer b (a thread's values all belong to case tid mod R) into spm[b]
-  auto scan_max = [&](int t, int b) {
-    const int nl = ht.tile_node_off[t + 1] - ht.tile_node_off[t];
-    const float* ps = psb(b);
-    float mx = 0.f;
-    for (int i = tid; i < nl * per_node; i += kTcBlock) mx = fmaxf(mx, fabsf(ps[i]));
-    for (int off = 16; off >= R; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if ((tid & 31) < R) atomicMax(spm + (b << 5) + (tid & 31), __float_as_int(mx));
   };
   const int lane = tid & 31, warp = tid >> 5;
   constexpr int nwarp = kTcBlock / 32;
@@ -1956,24 +1927,35 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshVie
   const int t0 = blockIdx.x;
   if (t0 < ht.n_tiles) {
     issue(t0, 0);
-    request_records(t0);
-    wait(0, 0u);
-    scan_max(t0, 0);
+    request_records(t0, 0);
   }
-  __syncthreads();
   for (int k = 0;; ++k) {
     const int t = t0 + k * gridDim.x;
     if (t >= ht.n_tiles) break;
     const int b = k & 1;
     const int tn = t + gridDim.x;
+    if (tn < ht.n_tiles) issue(tn, b ^ 1);
     const int n0 = ht.tile_node_off[t], nl = ht.tile_node_off[t + 1] - n0;
     const int h0 = ht.tile_hex_off[t], nh = ht.tile_hex_off[t + 1] - h0;
+    const uint32_t bar = smem_u32(mbar + b);
+    if (!mbar_wait(bar, (uint32_t)((k >> 1) & 1), g_wait_budget)) {
+      atomicExch(&g_tma_timeout, 1);
+      mbar_wait(bar, (uint32_t)((k >> 1) & 1));   // second bounded wait for the copies still in flight
+    }
     const float* ps = psb(b);
     const uint32_t* sl = slb(b);
     const int* snode = snb(b);
-    // scales of this tile from its per-case maxima: p enters FP16 as p 2^(14 - ep) (max |p| < 2^ep), sums
-    // leave to fixed point by 2^(30 - E - (14 - ep)) (the fixed-point bound 2^E as in the packed kernel)
+    // per-case largest |p| of the staged tile (a thread's values all belong to case tid mod R)
+    {
+      float mx = 0.f;
+      for (int i = tid; i < nl * per_node; i += kTcBlock) mx = fmaxf(mx, fabsf(ps[i]));
+      for (int off = 16; off >= R; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if (lane < R) atomicMax(spm + (b << 5) + lane, __float_as_int(mx));
+    }
+    __syncthreads();
     const int* spm_b = spm + (b << 5);
+    // per case: E (the fixed-point bound 2^E), ep (max |p| < 2^ep); p enters FP16 as p 2^(14 - ep), sums
+    // leave to fixed point by 2^(30 - E - (14 - ep))
     auto expo_b = [&](int c) {
       const uint32_t fb = (__float_as_uint(bco * __int_as_float(spm_b[c])) >> 23) & 0xffu;
       return fb == 0u ? -126 : (int)fb - 126;
@@ -1991,11 +1973,9 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshVie
       f_out1[nt] = pow2(30 - expo_b(c + 1) - 14 + expo_p(c + 1));
     }
     if (tid < R) {
-      sfwd[(b << 5) + tid] = pow2(expo_b(tid) - 30);
-      spm[((b ^ 1) << 5) + tid] = 0;   // (read for the previous tile before the last barrier)
+      sfwd[tid] = pow2(expo_b(tid) - 30);
+      spm[((b ^ 1) << 5) + tid] = 0;   // the next tile's maxima
     }
-    if (tn < ht.n_tiles) issue(tn, b ^ 1);
-    wait(2, (uint32_t)(k & 1));
     for (int hl = warp; hl < nh; hl += nwarp) {
       const uint32_t wb = sl[4 * hl + tq], wo = sl[4 * hl + (gq >> 1)];
       const float* p0 = ps + (int)(wb & 0xffffu) * per_node;
@@ -2015,11 +1995,11 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshVie
         const uint32_t b0 = pack_f16(p0[cn] * s, p1[cn] * s);
         const uint32_t b1 = pack_f16(p0[R + cn] * s, p1[R + cn] * s);
         const uint32_t b2 = pack_f16(p0[2 * R + cn] * s, p1[2 * R + cn] * s);
-        float d0[4], d1[4];
-        mma_f16_16816_z(d0, xx, yx, xy, yy, b0, b1);   // rows x, y; columns x, y
-        mma_f16_1688(d0, xz, yz, b2);                  // rows x, y; columns z
-        mma_f16_16816_z(d1, zx, 0u, zy, 0u, b0, b1);   // rows z; columns x, y
-        mma_f16_1688(d1, zz, 0u, b2);                  // rows z; columns z
+        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_f16_16816(d0, xx, yx, xy, yy, b0, b1);   // rows x, y; columns x, y
+        mma_f16_1688(d0, xz, yz, b2);                // rows x, y; columns z
+        mma_f16_16816(d1, zx, 0u, zy, 0u, b0, b1);   // rows z; columns x, y
+        mma_f16_1688(d1, zz, 0u, b2);                // rows z; columns z
         // rows gq (x), gq + 8 (y), 16 + gq (z) of corner slot gq; columns: cases c, c + 1
         const int c = nt * 8 + 2 * tq;
         const float g0 = hu * f_out0[nt], g1 = hu * f_out1[nt];
@@ -2032,10 +2012,9 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshVie
       }
     }
     __syncthreads();
-    if (tn < ht.n_tiles) request_records(tn);
+    if (tn < ht.n_tiles) request_records(tn, b ^ 1);   // the record buffer is free: the next tile's records
     // flush: float4 pieces (four cases of one component of one node) to the output; p^T q from the tile's
     // sums and its FP32 values of p (a thread's four cases are fixed: 4 kTcBlock is a multiple of R)
-    const float* fw = sfwd + (b << 5);
     for (int i = tid; i < nl * f4; i += kTcBlock) {
       const int l = i / f4, kk = (i - l * f4) / (R / 4);
       const int raw = snode[l];
@@ -2044,8 +2023,8 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshVie
       float4* dstg = reinterpret_cast<float4*>(q + g * per_node) + (i - l * f4);
       const int4 vi = reinterpret_cast<const int4*>(qs)[i];
       const int c4 = (i << 2) & (R - 1);
-      const float4 v = make_float4((float)vi.x * fw[c4], (float)vi.y * fw[c4 + 1], (float)vi.z * fw[c4 + 2],
-                                   (float)vi.w * fw[c4 + 3]);
+      const float4 v = make_float4((float)vi.x * sfwd[c4], (float)vi.y * sfwd[c4 + 1], (float)vi.z * sfwd[c4 + 2],
+                                   (float)vi.w * sfwd[c4 + 3]);
       reinterpret_cast<int4*>(qs)[i] = make_int4(0, 0, 0, 0);
       if (DOT && !fixed) {
         const float4 pv = reinterpret_cast<const float4*>(ps)[i];
@@ -2061,10 +2040,6 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_ebe_hex_tc(HexTiles ht, MeshVie
     if (DOT) {
       dd[0] += (double)tdot.x, dd[1] += (double)tdot.y, dd[2] += (double)tdot.z, dd[3] += (double)tdot.w;
       tdot = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    if (tn < ht.n_tiles) {   // the next tile's node rows: its per-case maxima
-      wait(b ^ 1, (uint32_t)(((k + 1) >> 1) & 1));
-      scan_max(tn, b ^ 1);
     }
     __syncthreads();
   }
