@@ -94,8 +94,10 @@ def parse(argv=None):
                          "3 assembled double-float")
     ap.add_argument("--snapshot-format", type=int, default=2,
                     help="predictor snapshot storage: 0 FP64, 1 FP32, 2 double-float, 3 FP32 + BF16 residual")
-    ap.add_argument("--inner-product", default="fp32", choices=["fp32", "tc"],
-                    help="inner CG products: FP32 element kernels, or FP16 hex element matrices on the tensor cores")
+    ap.add_argument("--inner-product", default=None, choices=["fp32", "tc"],
+                    help="inner CG products: FP32 element kernels, or FP16 hex element matrices on the tensor cores "
+                         "(default: tc for the large box's 8 cases, fp32 for the medium box's 16, the faster one "
+                         "for each)")
     ap.add_argument("--inner-margin", type=float, default=None,
                     help="FP32-inner solves aim at this fraction of the tolerance (default: the library's)")
     ap.add_argument("--check-every", type=int, default=8,
@@ -137,6 +139,8 @@ def parse(argv=None):
         a.cases = 8 if large else 16
     if a.dims is None:
         a.dims = "256,256,128" if large else "64,64,32"
+    if a.inner_product is None:
+        a.inner_product = "tc" if large and a.element == "tet4" and a.precision == "mixed" else "fp32"
     if a.s_max is None:     # (10-node tets: s = 32 overfits on the medium box, one case's guess 7x worse than AB4)
         a.s_max = 16 if large or a.element == "tet10" else 32
     if a.comparator_steps is None:     # (large: the plain FP64 comparators need minutes; run them on request)

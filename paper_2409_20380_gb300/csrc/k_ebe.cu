@@ -1726,8 +1726,9 @@ cudaError_t launch_ebe_split_df(const MeshView& m, const float* rec_df, int rpad
 // gq.  Sums go to the tile accumulator in the packed kernel's fixed point; p^T q is taken at the flush from
 // the tile's sums and its FP32 values of p.  FP16 operands carry ~2.4e-4 of relative error into a product
 // (FP32 accumulation): the inner solve's refinement passes remove it (its reduction target is floored at
-// 1e-3).  Tiles of 32 hexes, three blocks of 256 threads an SM: the node rows are double-buffered, the
-// records single-buffered (the next tile's records are requested once the hexes of this one are done).
+// 1e-3).  Blocks of 256 threads (two an SM with 64-hex tiles at 8 cases, three with 32-hex tiles at 16):
+// the node rows are double-buffered, the records single-buffered (the next tile's records are requested
+// once the hexes of this one are done).
 // ------------------------------------------------------------------------------------------------------
 constexpr int kHm16Bytes = kHm16RecBytes;
 constexpr int kTcBlock = 256;
@@ -1856,7 +1857,7 @@ __device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
 }
 
 template <bool DOT, int R>
-__global__ void __launch_bounds__(kTcBlock, 3) k_ebe_hex_tc(HexTiles ht, MeshView m, const float* __restrict__ p,
+__global__ void __launch_bounds__(kTcBlock, R == 8 ? 2 : 3) k_ebe_hex_tc(HexTiles ht, MeshView m, const float* __restrict__ p,
                                                          float* __restrict__ q, const unsigned char* __restrict__ hm,
                                                          float aM, float aK, Reducer red, CgCase* sc,
                                                          double* ptq_out, const int* gate) {
