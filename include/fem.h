@@ -144,11 +144,19 @@ typedef struct {
                             large workload for the same certificate) */
   int inner_product;     /* FEM_INNER_FP32 or FEM_INNER_TC (see above); the FP16 hex matrices (784 bytes a hex)
                             are built on the group's first step.  Default FEM_INNER_FP32 */
+  int pred_guard;        /* FEM_FP32_INNER steps with FEM_PRED_DD: 1 = guess guard: per case, the step starts from
+                            whichever guess has the smaller initial residual, the data-driven one (Adams-Bashforth
+                            plus the regional correction) or the Adams-Bashforth one alone; the residual of the
+                            latter comes from the same pass (the correction's FP32 product is formed anyway), so
+                            the guard costs one more norm in that pass and a fix pass that returns at once unless a
+                            case dropped its correction (fem_case_stats reports which guess a step used and how
+                            often the correction was dropped).  Not applied to steps that take a learned
+                            proposal.  0 = always the data-driven guess.  Default 1 */
 } fem_opts;
 
 /* Fills `o` with defaults: FP64, AB4, tol 1e-8, maxit 5000, s_max 32, inner_tol 1e-6, tau 1e-6,
  * snapshot_format 2, check_every 8, refresh_every 200, cert_df 3, fuse_meshes 0, use_graph 1,
- * wait_budget 1048576, cpu_predictor 0, inner_margin 0.5, inner_product FEM_INNER_FP32. */
+ * wait_budget 1048576, cpu_predictor 0, inner_margin 0.5, inner_product FEM_INNER_FP32, pred_guard 1. */
 void fem_opts_default(fem_opts* o);
 
 typedef struct fem_mesh fem_mesh;    /* opaque: device copies of geometry, element records, preconditioner */
@@ -490,6 +498,10 @@ typedef struct {
   int status;            /* fem_status of the last step's solve */
   double init_relres;    /* ||b - A guess|| / ||b|| of the last step's initial guess (predictor quality) */
   double relres;         /* certified ||b - A du|| / ||b|| of the last step */
+  int guess;             /* the last step's initial guess: 0 Adams-Bashforth, 1 data-driven (Adams-Bashforth plus
+                            the regional correction), 2 Adams-Bashforth because the guess guard dropped the
+                            correction (its residual was larger); -1 in FEM_FP64 (not tracked) */
+  int fallbacks;         /* steps of the case whose correction the guess guard dropped */
 } fem_case_stats_t;
 
 fem_status fem_case_stats(fem_batch* b, int case_id, fem_case_stats_t* out);

@@ -714,6 +714,7 @@ static fem_status check_opts(const fem_opts* o) {
     return fail(FEM_ERR_ARG, "inner_margin must be in (0, 1)");
   if (o->inner_product != FEM_INNER_FP32 && o->inner_product != FEM_INNER_TC)
     return fail(FEM_ERR_ARG, "inner_product must be FEM_INNER_FP32 or FEM_INNER_TC");
+  if (o->pred_guard != 0 && o->pred_guard != 1) return fail(FEM_ERR_ARG, "pred_guard must be 0 or 1");
   if (o->cpu_predictor) {
     if (o->predictor != FEM_PRED_DD) return fail(FEM_ERR_ARG, "cpu_predictor needs the data-driven predictor");
     if (o->snapshot_format != 0 && o->snapshot_format != 2)
@@ -775,6 +776,7 @@ struct Group {
   long long* counts = nullptr;    // [2] steps where cases took / rejected the proposal
   float4* case_src = nullptr;     // [rpad] source position and (f0 - 5) / 3
   double* e2case = nullptr;       // [ncase] ||e^it||^2 of each case (residual-space samples)
+  int* fb = nullptr;              // [ncase] steps whose data-driven correction the guess guard dropped
   int last_npairs = 0;            // pairs used by this step's prediction
   bool featured = false;          // F holds this step's features
   bool proposed = false;          // ydelta holds this step's proposal
@@ -805,6 +807,7 @@ struct Group {
     dfree(Ku); dfree(Mv); dfree(Kv); dfree(Ma); dfree(qM); dfree(qK); dfree(xdf);
     for (auto& v : Av) dfree(v);
     dfree(F); dfree(dw); dfree(wbest); dfree(ydelta); dfree(choose); dfree(counts); dfree(case_src); dfree(e2case);
+    dfree(fb);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     for (auto& st : gs)
@@ -869,7 +872,9 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
   CHK(dalloc(&g->m_in, n));
   CHK(dalloc(&g->k_in, n));
   CHK(dalloc(&g->guess, n));
+  CHK(dalloc(&g->fb, (size_t)kMaxCases));
   cudaStream_t s = bt->s;
+  CU(cudaMemsetAsync(g->fb, 0, sizeof(int) * kMaxCases, s));
   CU(cudaMemsetAsync(g->u, 0, n * 8, s));
   CU(cudaMemsetAsync(g->a, 0, n * 8, s));
   for (auto& v : g->vh) CU(cudaMemsetAsync(v, 0, n * 8, s));
@@ -1159,12 +1164,21 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
     qy = w->q32;
     w->count(2);
   }
+  // the guess guard: a case whose correction leaves a larger residual than the Adams-Bashforth guess drops it
+  // (not with a learned proposal, whose choice below is made against the corrected guess)
+  const bool guard = qy && o.pred_guard && !g->proposed;
   if (mv.seg) {
     CU(launch_r0_seg(mv, dt, g->b, aslot(it - 4), aslot(it - 3), aslot(it - 2), aslot(it - 1), qy, w->r32, red,
-                     w->outer, w->n_active, o.tol, o.inner_tol, o.inner_margin * o.tol, s));
+                     w->outer, w->n_active, o.tol, o.inner_tol, o.inner_margin * o.tol, s, Ring4{}, nullptr, guard,
+                     g->fb));
   } else {
     CU(launch_r0(mv, g->rpad, dt, g->b, aslot(it - 4), aslot(it - 3), aslot(it - 2), aslot(it - 1), qy, w->r32, red,
-                 w->outer, w->n_active, o.tol, o.inner_tol, o.inner_margin * o.tol, s));
+                 w->outer, w->n_active, o.tol, o.inner_tol, o.inner_margin * o.tol, s, Ring4{}, nullptr, nullptr,
+                 guard, g->fb));
+  }
+  if (guard) {
+    CU(launch_guard_fix(mv, g->rpad, w->outer, qy, w->r32, g->du_ab, g->guess, nullptr, s));
+    w->count();
   }
   if (g->proposed) {
     // learned proposal: r0' = r0 - A32 (Y dw); a case takes it where its initial residual is smaller
@@ -1342,7 +1356,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   const int ce = std::max(1, o.check_every);
   cudaStream_t s = g->gs[0], s2 = g->gs[1], s3 = g->gs[2], s4 = g->gs[3];
   const bool ab = m->ab.nb > 0;
-  const long long n_fixed = 6 + (dd ? 5 : 0) + (g->imp.n > 0 ? 1 : 0) + (ab ? 3 + (dd ? 1 : 0) : 0),
+  const long long n_fixed = 6 + (dd ? 5 + (o.pred_guard ? 1 : 0) : 0) + (g->imp.n > 0 ? 1 : 0) + (ab ? 3 + (dd ? 1 : 0) : 0),
                   n_pass = 4 + (ab ? 1 : 0), n_if = sg ? 4 : 2, n_inner = (ab ? 4LL : 3LL) * ce + 1;
   // 1. step record; the per-region Gram solves (few warps per SM) run beside the Adams-Bashforth
   // increment and the right-hand side, which do not depend on them
@@ -1374,13 +1388,15 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
     GE(ebe_product<float>(m, rpad, w->z32, w->q32, m->cM, m->cK, nullptr, nullptr, nullptr, nullptr, s, true));
     qy = w->q32;
   }
+  const bool guard = qy && o.pred_guard;
   if (sg) {
     GE(launch_r0_seg(mv, dt, g->b, nullptr, nullptr, nullptr, nullptr, qy, w->r32, red, w->outer, w->n_active, o.tol,
-                     o.inner_tol, o.inner_margin * o.tol, s, AV, ctl));
+                     o.inner_tol, o.inner_margin * o.tol, s, AV, ctl, guard, g->fb));
   } else {
     GE(launch_r0(mv, rpad, dt, g->b, nullptr, nullptr, nullptr, nullptr, qy, w->r32, red, w->outer, w->n_active, o.tol,
-                 o.inner_tol, o.inner_margin * o.tol, s, AV, ctl, w->sc));   // (and the inner solve's starting state)
+                 o.inner_tol, o.inner_margin * o.tol, s, AV, ctl, w->sc, guard, g->fb));   // (and the inner solve's starting state)
   }
+  if (guard) GE(launch_guard_fix(mv, rpad, w->outer, qy, w->r32, g->du_ab, g->guess, g->x, s));
   // 4. refinement passes: WHILE (pass 0, then while a case is above tol)
   cudaGraphConditionalHandle h_pass, h_if, h_in;
   cudaGraph_t b_pass, b_if, b_in, tmp;
@@ -1779,6 +1795,7 @@ void fem_opts_default(fem_opts* o) {
   o->wait_budget = kDefaultWaitBudget;
   o->inner_margin = 0.5;
   o->inner_product = FEM_INNER_FP32;
+  o->pred_guard = 1;
 }
 
 // Mesh set-up shared by the linear (npe 4) and quadratic (npe 10) tets: element records of the corner tets,
@@ -2799,6 +2816,11 @@ fem_status fem_case_stats(fem_batch* b, int case_id, fem_case_stats_t* out) {
   out->status = c.status;
   out->init_relres = c.relres0;
   out->relres = c.relres;
+  out->guess = b->opts.precision == FEM_FP64 ? -1 : c.guess;
+  if (g->fb) {
+    CU(cudaMemcpyAsync(&out->fallbacks, g->fb + b->loc[case_id].second, sizeof(int), cudaMemcpyDeviceToHost, b->s));
+    CU(cudaStreamSynchronize(b->s));
+  }
   return FEM_OK;
 }
 

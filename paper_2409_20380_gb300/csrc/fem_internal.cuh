@@ -67,7 +67,8 @@ struct CgCase {
   int phase;       // internal: 0 = before first direction
   double relres0;  // relative residual of the initial guess
   int outer;       // FP64 residual evaluations (refinement passes) of the solve
-  int pad_;
+  int guess;       // outer state: the step's initial guess: 0 Adams-Bashforth (no correction), 1 with the
+                   // data-driven correction, 2 correction dropped by the guess guard (larger residual)
   double tol2;     // squared relative tolerance of this case's (inner) solve; set when the solve starts
   double inner_tol;  // outer state: relative reduction the next inner solve is asked for
 };
@@ -239,7 +240,8 @@ cudaError_t launch_update_seg(const MeshView& m, const T* p, const T* q, T* x, T
 cudaError_t launch_r0_seg(const MeshView& m, double dt, const double* b, const double* Av4, const double* Av3,
                           const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red,
                           CgCase* outer, int* n_active, double tol, double inner_floor, double aim, cudaStream_t s,
-                          Ring4 avr = Ring4{}, const StepCtl* ctl = nullptr);
+                          Ring4 avr = Ring4{}, const StepCtl* ctl = nullptr, bool guard = false,
+                          int* fallbacks = nullptr);
 cudaError_t launch_cert_seg(const MeshView& m, double cM, double cK, const double* b, const double* qM, const double* qK,
                             float* r32, Reducer red, CgCase* outer, int* n_active, double tol, double inner_floor,
                             double aim, cudaStream_t s);
@@ -272,10 +274,17 @@ cudaError_t launch_rhs_incr(const MeshView& m, int rpad, double dt, double a0, d
 cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab, float* y32, cudaStream_t s);
 // inner != null (r0, cert): also start the inner FP32 solve of the pass on r32 (zero guess, its residual
 // r32 itself): the inner case state as the norm and first-residual passes would leave it.
+// guard (with qy, the product A y of the data-driven correction y): per case, the guess whose initial
+// residual is smaller, the data-driven one or the Adams-Bashforth one (CgCase::guess; fallbacks[c], nullable,
+// counts the cases' dropped corrections); launch_guard_fix then rewrites r32 and the guess of the cases that
+// dropped theirs.
 cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
                       const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
                       int* n_active, double tol, double inner_max, double aim, cudaStream_t s,
-                      Ring4 avr = Ring4{}, const StepCtl* ctl = nullptr, CgCase* inner = nullptr);
+                      Ring4 avr = Ring4{}, const StepCtl* ctl = nullptr, CgCase* inner = nullptr, bool guard = false,
+                      int* fallbacks = nullptr);
+cudaError_t launch_guard_fix(const MeshView& m, int rpad, const CgCase* outer, const float* qy, float* r32,
+                             const double* du_ab, double* guess, double* x, cudaStream_t s);
 cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const double* b, const double* qM,
                         const double* qK, float* r32, Reducer red, CgCase* outer, int* n_active, double tol,
                         double inner_max, double aim, cudaStream_t s, CgCase* inner = nullptr);

@@ -195,22 +195,27 @@ __global__ void k_update_seg(MeshView m, const T* __restrict__ p, const T* __res
   }
 }
 
-// Residual of the guess from the recurrences (fused form of k_r0).
+// Residual of the guess from the recurrences (fused form of k_r0; ALT: the guess guard's norms of the
+// Adams-Bashforth guess's residual r0 + A y and the per-case choice, as in k_r0).
+template <bool ALT>
 __global__ void k_r0_seg(MeshView m, double h, const double* __restrict__ b, const double* __restrict__ Av4,
                          const double* __restrict__ Av3, const double* __restrict__ Av2, const double* __restrict__ Av1,
                          const float* __restrict__ qy, float* __restrict__ r32, Reducer red, CgCase* outer,
-                         int* n_active, double tol, double inner_floor, double aim, Ring4 avr, const StepCtl* ctl) {
+                         int* n_active, double tol, double inner_floor, double aim, Ring4 avr, const StepCtl* ctl,
+                         int* fallbacks) {
   if (ctl) {   // A v^{it-4} .. A v^{it-1} in ring slots it .. it+3 (mod 4)
     const int it = ctl->it;
     Av4 = avr.p[it & 3], Av3 = avr.p[(it + 1) & 3], Av2 = avr.p[(it + 2) & 3], Av1 = avr.p[(it + 3) & 3];
   }
+  constexpr int NQ = ALT ? 3 : 2;
   extern __shared__ double acc[];
   const int nc = m.nseg;
-  zero_acc(acc, 2 * nc);
+  zero_acc(acc, NQ * nc);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < m.N; base += stride) {
     const int64_t n = base + threadIdx.x;
-    double v[2] = {0.0, 0.0};
+    double v[NQ];
+    for (int q = 0; q < NQ; ++q) v[q] = 0.0;
     int c = 0;
     if (n < m.N) {
       c = m.seg[n];
@@ -218,22 +223,41 @@ __global__ void k_r0_seg(MeshView m, double h, const double* __restrict__ b, con
       for (int k = 0; k < 3; ++k) {
         const int64_t id = n * 3 + k;
         double val = 0.0;
+        float qv = 0.f;
         const double bv = b[id];
         if (dof_free(f, k)) {
           val = bv - h * (-9.0 * Av4[id] + 37.0 * Av3[id] - 59.0 * Av2[id] + 55.0 * Av1[id]);
-          if (qy) val -= f2d(qy[id]);
+          if (qy) {
+            qv = qy[id];
+            val -= f2d(qv);
+          }
         }
-        r32[id] = d2f(val);
+        const float rf = d2f(val);
+        r32[id] = rf;
         v[0] += bv * bv;
         v[1] += val * val;
+        if (ALT) {
+          const float fa = dof_free(f, k) ? rf + qv : 0.f;
+          v[NQ - 1] += (double)fa * (double)fa;
+        }
       }
     }
-    seg_add<2>(acc, nc, c, v);
+    seg_add<NQ>(acc, nc, c, v);
   }
-  if (block_reduce_last_seg<2>(acc, nc, red)) {
+  if (block_reduce_last_seg<NQ>(acc, nc, red)) {
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       CgCase& s = outer[c];
-      const double bbc = red.out[c], rrc = red.out[nc + c];
+      const double bbc = red.out[c];
+      double rrc = red.out[nc + c];
+      s.guess = qy ? 1 : 0;
+      if (ALT) {
+        const double rra = red.out[2 * nc + c];
+        if (bbc > 0.0 && isfinite(rra) && (!isfinite(rrc) || rra < rrc * (1.0 - 1e-6))) {
+          rrc = rra;
+          s.guess = 2;
+          if (fallbacks) fallbacks[c] += 1;
+        }
+      }
       s.rho = s.pq = s.alpha = s.beta = 0.0;
       s.iters = 0;
       s.outer = 0;
@@ -325,10 +349,14 @@ cudaError_t launch_update_seg(const MeshView& m, const T* p, const T* q, T* x, T
 cudaError_t launch_r0_seg(const MeshView& m, double dt, const double* b, const double* Av4, const double* Av3,
                           const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red,
                           CgCase* outer, int* n_active, double tol, double inner_floor, double aim, cudaStream_t s,
-                          Ring4 avr, const StepCtl* ctl) {
-  k_r0_seg<<<seg_grid(m.N), kVecBlock, sizeof(double) * 2 * m.nseg, s>>>(m, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32,
-                                                                          red, outer, n_active, tol, inner_floor, aim,
-                                                                          avr, ctl);
+                          Ring4 avr, const StepCtl* ctl, bool guard, int* fallbacks) {
+  if (guard && qy) {
+    k_r0_seg<true><<<seg_grid(m.N), kVecBlock, sizeof(double) * 3 * m.nseg, s>>>(
+        m, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer, n_active, tol, inner_floor, aim, avr, ctl, fallbacks);
+  } else {
+    k_r0_seg<false><<<seg_grid(m.N), kVecBlock, sizeof(double) * 2 * m.nseg, s>>>(
+        m, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer, n_active, tol, inner_floor, aim, avr, ctl, nullptr);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_cert_seg(const MeshView& m, double cM, double cK, const double* b, const double* qM, const double* qK,

@@ -732,18 +732,26 @@ __device__ __forceinline__ float zr_node(const float* __restrict__ B, float r0, 
   return z0 * r0 + z1 * r1 + z2 * r2;
 }
 
+// ALT (a data-driven correction y whose product qy = A y is given, and the guess guard on): the same pass
+// also forms the norms of the Adams-Bashforth guess's residual r0 + A y, in the FP32 values the guard's fix
+// pass would write (r32 + qy, rounded once).  The last block keeps, per case, the guess with the smaller
+// initial residual: a case whose correction makes the residual larger (an extrapolation that has gone
+// astray at the onset of a wave) drops it (CgCase::guess = 2, fallbacks[c] += 1), and k_guard_fix then
+// rewrites that case's r32 and guess.
+template <bool ALT>
 __global__ void __launch_bounds__(kVecBlock, 2) k_r0(MeshView m, int rpad, int rshift, double h, const double* __restrict__ b,
                                                const double* __restrict__ Av4, const double* __restrict__ Av3,
                                                const double* __restrict__ Av2, const double* __restrict__ Av1,
                                                const float* __restrict__ qy, float* __restrict__ r32, Reducer red,
                                                CgCase* outer, int* n_active, double tol, double inner_max,
-                                               double aim, Ring4 avr, const StepCtl* ctl, CgCase* inner) {
+                                               double aim, Ring4 avr, const StepCtl* ctl, CgCase* inner,
+                                               int* fallbacks) {
   if (ctl) {   // A v^{it-4} .. A v^{it-1} in ring slots it .. it+3 (mod 4)
     const int it = ctl->it;
     Av4 = avr.p[it & 3], Av3 = avr.p[(it + 1) & 3], Av2 = avr.p[(it + 2) & 3], Av1 = avr.p[(it + 3) & 3];
   }
-  double bb = 0.0, rr = 0.0;
-  float zr = 0.f;
+  double bb = 0.0, rr = 0.0, ra = 0.0;
+  float zr = 0.f, za = 0.f;
   // the Adams-Bashforth weights times -h: four FMAs from b (the FP64 pipe bounds this kernel)
   const double w4 = 9.0 * h, w3 = -37.0 * h, w2 = 59.0 * h, w1 = -55.0 * h;
   const int64_t total = m.N << rshift;
@@ -751,29 +759,55 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_r0(MeshView m, int rpad, int r
     const int64_t n = i >> rshift;
     const int c = (int)(i & (rpad - 1));
     const uint8_t f = m.freemask[n];
-    float rf[3];
+    float rf[3], fa[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const int64_t id = (n * 3 + k) * rpad + c;
       double v = 0.0;
+      float qv = 0.f;
       const double bv = b[id];
       if (dof_free(f, k)) {
         v = fma(w1, Av1[id], fma(w2, Av2[id], fma(w3, Av3[id], fma(w4, Av4[id], bv))));
-        if (qy) v -= f2d(qy[id]);
+        if (qy) {
+          qv = qy[id];
+          v -= f2d(qv);
+        }
       }
       rf[k] = d2f(v);
       r32[id] = rf[k];
       bb += bv * bv;
       rr += v * v;
+      if (ALT) {
+        fa[k] = dof_free(f, k) ? rf[k] + qv : 0.f;
+        ra += (double)fa[k] * (double)fa[k];
+      }
     }
-    if (inner) zr += zr_node(m.binv32 + n * 6, rf[0], rf[1], rf[2]);
+    if (inner) {
+      zr += zr_node(m.binv32 + n * 6, rf[0], rf[1], rf[2]);
+      if (ALT) za += zr_node(m.binv32 + n * 6, fa[0], fa[1], fa[2]);
+    }
   }
-  double vals[3] = {bb, rr, (double)zr};
-  if (block_reduce_last<3>(vals, rpad, red)) {
+  constexpr int NQ = ALT ? 5 : 3;
+  double vals[NQ];
+  vals[0] = bb, vals[1] = rr, vals[2] = (double)zr;
+  if (ALT) vals[NQ - 2] = ra, vals[NQ - 1] = (double)za;
+  if (block_reduce_last<NQ>(vals, rpad, red)) {
     if (threadIdx.x < rpad) {
       const int c = threadIdx.x;
       CgCase& s = outer[c];
-      const double bbc = red.out[c], rrc = red.out[rpad + c];
+      const double bbc = red.out[c];
+      double rrc = red.out[rpad + c], zrc = red.out[2 * rpad + c];
+      s.guess = qy ? 1 : 0;
+      if (ALT) {
+        // (a margin keeps a correction that changes the residual by rounding only)
+        const double rra = red.out[3 * rpad + c];
+        if (bbc > 0.0 && isfinite(rra) && (!isfinite(rrc) || rra < rrc * (1.0 - 1e-6))) {
+          rrc = rra;
+          zrc = red.out[4 * rpad + c];
+          s.guess = 2;
+          if (fallbacks) fallbacks[c] += 1;
+        }
+      }
       s.rho = s.pq = s.alpha = s.beta = 0.0;
       s.iters = 0;
       s.outer = 0;
@@ -786,13 +820,58 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_r0(MeshView m, int rpad, int r
       // estimate only: the certificate is the FP64 residual computed after the solve
       s.active = (s.status == FEM_OK && bbc > 0.0 && rrc >= tol * tol * bbc) ? 1 : 0;
       s.inner_tol = inner_target(aim, s.relres, inner_max);
-      if (inner) init_inner(inner[c], s, rrc, red.out[2 * rpad + c]);
+      if (inner) init_inner(inner[c], s, rrc, zrc);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       int na = 0;
       for (int c = 0; c < rpad; ++c) na += outer[c].active;
       *n_active = na;
+    }
+  }
+}
+
+// The guess guard's fix pass: for each case whose correction k_r0 (or k_r0_seg) dropped (CgCase::guess ==
+// 2), r32 += qy on free DOFs (the Adams-Bashforth guess's residual, the values whose norms were formed) and
+// guess = x = du_AB.  Every block returns at once when no case dropped its correction, the usual case.
+__global__ void k_guard_fix(MeshView m, int rpad, int rshift, const CgCase* __restrict__ outer,
+                            const float* __restrict__ qy, float* __restrict__ r32, const double* __restrict__ du_ab,
+                            double* __restrict__ guess, double* __restrict__ x) {
+  __shared__ unsigned char drop[kMaxCases];
+  __shared__ int any;
+  const int nc = m.seg ? m.nseg : rpad;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    drop[c] = outer[c].guess == 2 ? 1 : 0;
+    if (drop[c]) any = 1;
+  }
+  __syncthreads();
+  if (!any) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (m.seg) {   // fused groups: one case a node, [N][3]
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < m.N; n += stride) {
+      if (!drop[m.seg[n]]) continue;
+      const uint8_t f = m.freemask[n];
+      for (int k = 0; k < 3; ++k) {
+        const int64_t id = n * 3 + k;
+        if (dof_free(f, k)) r32[id] = r32[id] + qy[id];
+        guess[id] = du_ab[id];
+        if (x) x[id] = du_ab[id];
+      }
+    }
+    return;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (m.N << rshift); i += stride) {
+    const int c = (int)(i & (rpad - 1));
+    if (!drop[c]) continue;
+    const int64_t n = i >> rshift;
+    const uint8_t f = m.freemask[n];
+    for (int k = 0; k < 3; ++k) {
+      const int64_t id = (n * 3 + k) * rpad + c;
+      if (dof_free(f, k)) r32[id] = r32[id] + qy[id];
+      guess[id] = du_ab[id];
+      if (x) x[id] = du_ab[id];
     }
   }
 }
@@ -1009,10 +1088,24 @@ cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab,
 cudaError_t launch_r0(const MeshView& m, int rpad, double dt, const double* b, const double* Av4, const double* Av3,
                       const double* Av2, const double* Av1, const float* qy, float* r32, Reducer red, CgCase* outer,
                       int* n_active, double tol, double inner_max, double aim, cudaStream_t s, Ring4 avr,
-                      const StepCtl* ctl, CgCase* inner) {
+                      const StepCtl* ctl, CgCase* inner, bool guard, int* fallbacks) {
   const int rs = log2i(rpad);
-  k_r0<<<grid_resident((const void*)k_r0, kVecBlock, m.N << rs), kVecBlock, 0, s>>>(m, rpad, rs, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer,
-                                                n_active, tol, inner_max, aim, avr, ctl, inner);
+  if (guard && qy) {
+    k_r0<true><<<grid_resident((const void*)k_r0<true>, kVecBlock, m.N << rs), kVecBlock, 0, s>>>(
+        m, rpad, rs, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer, n_active, tol, inner_max, aim, avr, ctl,
+        inner, fallbacks);
+  } else {
+    k_r0<false><<<grid_resident((const void*)k_r0<false>, kVecBlock, m.N << rs), kVecBlock, 0, s>>>(
+        m, rpad, rs, dt / 24.0, b, Av4, Av3, Av2, Av1, qy, r32, red, outer, n_active, tol, inner_max, aim, avr, ctl,
+        inner, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_guard_fix(const MeshView& m, int rpad, const CgCase* outer, const float* qy, float* r32,
+                             const double* du_ab, double* guess, double* x, cudaStream_t s) {
+  const int rs = log2i(rpad);
+  k_guard_fix<<<grid_for(m.seg ? m.N : (m.N << rs)), kBlock, 0, s>>>(m, rpad, rs, outer, qy, r32, du_ab, guess, x);
   return cudaGetLastError();
 }
 

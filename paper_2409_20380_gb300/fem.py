@@ -56,7 +56,7 @@ class fem_opts(ctypes.Structure):
                 ("refresh_every", ctypes.c_int), ("cert_df", ctypes.c_int), ("fuse_meshes", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("wait_budget", ctypes.c_int),
                 ("cpu_predictor", ctypes.c_int), ("inner_margin", ctypes.c_double),
-                ("inner_product", ctypes.c_int)]
+                ("inner_product", ctypes.c_int), ("pred_guard", ctypes.c_int)]
 
 
 class fem_profile(ctypes.Structure):
@@ -73,7 +73,8 @@ class fem_profile(ctypes.Structure):
 
 class fem_case_stats_t(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("iters", ctypes.c_int), ("outer", ctypes.c_int), ("status", ctypes.c_int),
-                ("init_relres", ctypes.c_double), ("relres", ctypes.c_double)]
+                ("init_relres", ctypes.c_double), ("relres", ctypes.c_double), ("guess", ctypes.c_int),
+                ("fallbacks", ctypes.c_int)]
 
 
 _lib = None

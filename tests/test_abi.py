@@ -37,7 +37,7 @@ def test_defaults_and_errors_without_gpu(libfem):
     assert o.tol == 1e-8 and o.precision == fem.FEM_FP64 and o.s_max == 32
     # the last fields read back their documented defaults (the binding's struct layout matches the header's)
     assert o.wait_budget == 1048576 and o.cpu_predictor == 0 and o.inner_margin == 0.5
-    assert o.inner_product == fem.FEM_INNER_FP32
+    assert o.inner_product == fem.FEM_INNER_FP32 and o.pred_guard == 1
     # argument errors are reported without touching a device
     st = libfem.fem_mesh_destroy(None)
     assert st == fem.FEM_ERR_ARG

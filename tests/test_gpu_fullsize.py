@@ -22,7 +22,7 @@ import pytest
 import oracle
 from paper_2409_20380_gb300 import build, fem
 from paper_2409_20380_gb300 import workload as wl
-from test_gpu_step import PredStats, check_prediction, stored_value
+from test_gpu_step import PredStats, check_prediction, guarded_correction, stored_value
 
 pytestmark = pytest.mark.gpu
 
@@ -212,6 +212,8 @@ def test_fullsize_steps_sampled(big):
                 y_gpu = (cur["guess"][c] - du_ab)[reg_i]
                 coef, n_pairs = fem.predictor_coefficients(bt, c, n_reg, opts.s_max)
                 floor = 1e-13 * max(np.abs(du_ab).max(), 1e-300)
+                y_gpu, _ = guarded_correction(bt, c, y_gpu, E[c], reg_of_dof, len(sreg), coef[sreg], n_pairs, floor,
+                                              stats, where=(it, c))
                 check_prediction(E[c], reg_of_dof, len(sreg), y_gpu, coef[sreg], n_pairs, opts, floor, stats,
                                  where=(it, c))
                 E[c].append(stored_value(du[reg_i] - du_ab[reg_i], opts.snapshot_format))

@@ -12,7 +12,7 @@ import oracle
 from paper_2409_20380_gb300 import build, fem
 from paper_2409_20380_gb300 import workload as wl
 from helpers import small_mesh
-from test_gpu_step import PredStats, check_prediction, stored_value
+from test_gpu_step import PredStats, check_guard, check_prediction, guarded_correction, stored_value
 
 pytestmark = pytest.mark.gpu
 
@@ -47,6 +47,7 @@ def test_host_predictor_steps(torch_dev, precision, fmt):
         st = {c: dict(u=np.zeros(3 * N), v=np.zeros(3 * N), a=np.zeros(3 * N), vh=[np.zeros(3 * N)] * 4, E=[])
               for c in range(4)}
         stats = PredStats()
+        absA = abs(A)
         total = np.zeros(4)
         for it in range(1, 41):
             stat, iters, relres = fem.fem_step(bt, 1, 4)
@@ -72,6 +73,9 @@ def test_host_predictor_steps(torch_dev, precision, fmt):
                 if n_pairs == 0:
                     assert np.abs(y).max() <= floor or it <= 2
                 else:
+                    y, kind = guarded_correction(bt, c, y, S["E"], reg_dof, n_reg, coef, n_pairs, floor, stats,
+                                                 where=(it, c))
+                    check_guard(kind, A, absA, b_ref[sysm.free], du_ab[sysm.free], y, where=(it, c))
                     check_prediction(S["E"], reg_dof, n_reg, y, coef, n_pairs, opts, floor, stats, where=(it, c),
                                      s_used=n_pairs)
                 S["E"].append(stored_value(du[sysm.free] - du_ab[sysm.free], fmt))

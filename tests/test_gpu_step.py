@@ -46,6 +46,7 @@ def _run_and_check(mesh, tp, sources, opts, n_steps, region_nodes=None, check_pr
               for c in range(nc)}
         total_iters = np.zeros(nc, dtype=np.int64)
         stats = PredStats()
+        absA = None
         reg_dof = np.repeat(regions, 3)[sysm.free] if regions is not None else None
         n_reg = int(regions.max()) + 1 if regions is not None else 0
         for it in range(1, n_steps + 1):
@@ -85,6 +86,12 @@ def _run_and_check(mesh, tp, sources, opts, n_steps, region_nodes=None, check_pr
                         coef, n_pairs = fem.predictor_coefficients(bt, c, n_reg, opts.s_max)
                         y_gpu = (guess - du_ab)[sysm.free]
                         floor = 1e-13 * max(np.abs(du_ab).max(), 1e-300)     # AB4 rounding in y_gpu
+                        y_gpu, kind = guarded_correction(bt, c, y_gpu, S["E"], reg_dof, n_reg, coef, n_pairs,
+                                                         floor, stats, where=(it, c))
+                        if n_pairs > 0 and opts.pred_guard and opts.precision == fem.FEM_FP32_INNER:
+                            if absA is None:
+                                absA = abs(A)
+                            check_guard(kind, A, absA, b_ref[sysm.free], du_ab[sysm.free], y_gpu, where=(it, c))
                         check_prediction(S["E"], reg_dof, n_reg, y_gpu, coef, n_pairs, opts, floor, stats,
                                          where=(it, c))
                 S["E"].append(stored_value(du[sysm.free] - du_ab[sysm.free], opts.snapshot_format))
@@ -92,6 +99,9 @@ def _run_and_check(mesh, tp, sources, opts, n_steps, region_nodes=None, check_pr
                     S["E"].pop(0)
                 S["vh"] = S["vh"][1:] + [v.copy()]
                 S["u"], S["v"], S["a"] = u, v, a
+        if check_pred and opts.predictor == fem.FEM_PRED_DD and regions is not None and \
+                opts.precision == fem.FEM_FP32_INNER:
+            assert sum(fem.fem_case_stats(bt, c)["fallbacks"] for c in range(nc)) == stats.guess.get(2, 0)
         stats.assert_ok()
         return total_iters, stats
     finally:
@@ -136,9 +146,10 @@ STORE_EPS = {0: 2.0 ** -52, 1: 2.0 ** -24, 2: 2.0 ** -48, 3: 2.0 ** -32}
 
 
 class PredStats:
-    """Per (step, case, region) outcomes of check_prediction."""
+    """Per (step, case, region) outcomes of check_prediction (and the guess guard's choices)."""
 
     def __init__(self):
+        self.guess = {}         # case-steps by initial guess kind (fem_case_stats_t.guess)
         self.n = 0              # regions checked
         self.elementwise = 0    # also checked element by element (well-conditioned kept columns)
         self.ambiguous = 0      # a column's drop decision is within rounding of the threshold
@@ -337,6 +348,28 @@ def test_step_inner_margin(torch_dev, margin):
     assert its[margin] <= its[0.1], its
 
 
+@pytest.mark.parametrize("graph", [0, 1])
+def test_step_guess_guard(torch_dev, graph):
+    """The guess guard (fem_opts.pred_guard) with the benchmark's solver settings on a 16 x 16 x 12 box of the
+    large recipe, 8 cases, 40 steps from rest: every step certified by the oracle's CSR A, every choice
+    between the data-driven and the Adams-Bashforth guess checked against the oracle's residuals of both
+    (check_guard), the coefficients of dropped corrections still checked against the oracle's MGS, and the
+    library's count of dropped corrections equal to the steps seen with the Adams-Bashforth guess.  With the
+    guard off no correction is dropped."""
+    mesh = wl.config4_mesh(16, 16, 12)
+    tp = wl.config4_time_params()
+    srcs = wl.config4_sources(mesh, 8)
+    res = {}
+    for guard in (0, 1):
+        opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=16,
+                                    cert_df=3, snapshot_format=2, use_graph=graph, pred_guard=guard)
+        it, stats = _run_and_check(mesh, tp, srcs, opts, 40, region_nodes=1024, b_tol=1e-11)
+        res[guard] = (int(it.sum()), dict(stats.guess))
+    print("guess guard", graph, res)
+    assert res[0][1].get(2, 0) == 0, res
+    assert res[1][1].get(2, 0) > 0, res
+
+
 def test_inner_margin_out_of_range_rejected(torch_dev):
     for m in (0.0, 1.0, -0.5):
         with pytest.raises(fem.FemError) as ei:
@@ -365,3 +398,41 @@ def test_step_matches_independent_oracle_run(torch_dev):
     finally:
         fem.fem_batch_destroy(bt)
         fem.fem_mesh_destroy(h)
+
+
+def guarded_correction(bt, c, y_gpu, E, reg_dof, n_reg, coef, n_pairs, floor, stats, where=None):
+    """The correction the prediction checks apply to, and the step's initial guess kind.  Where the guess
+    guard dropped the case's correction (kind 2) the guess is the Adams-Bashforth one (y_gpu = 0 to its
+    rounding floor) and the checks apply to the correction the coefficients give, Y_R c_R on each region."""
+    kind = fem.fem_case_stats(bt, c)["guess"]
+    stats.guess[kind] = stats.guess.get(kind, 0) + 1
+    if kind != 2:
+        return y_gpu, kind
+    assert np.abs(y_gpu).max() <= floor, where
+    n = n_pairs
+    if n <= 0:
+        return y_gpu, kind
+    Y = np.stack(E[-n:], axis=1)
+    y = np.zeros_like(y_gpu)
+    for R in range(n_reg):
+        idx = np.nonzero(reg_dof == R)[0]
+        y[idx] = Y[idx] @ coef[R, :n]
+    return y, kind
+
+
+def check_guard(kind, A, absA, b, du_ab, y, where=None):
+    """The guard's choice against the oracle's residuals (free DOFs): the Adams-Bashforth guess's
+    r_ab = b - A du_ab and the data-driven one's r_ab - A y.  Kind 2 (correction dropped) needs
+    ||r_ab|| <= ||r_ab - A y||, kind 1 the reverse, each up to the GPU's rounding: FP32 residual values
+    (1e-6 of the norms), the FP32 product of y in FP32 (4e-6 of || |A| |y| ||) and the FP64 recurrence
+    products (1e-10 of ||b||)."""
+    if kind not in (1, 2):
+        return
+    r_ab = b - A @ du_ab
+    n_ab = np.linalg.norm(r_ab)
+    n_dd = np.linalg.norm(r_ab - A @ y)
+    slack = 4e-6 * np.linalg.norm(absA @ np.abs(y)) + 1e-6 * (n_ab + n_dd) + 1e-10 * np.linalg.norm(b)
+    if kind == 2:
+        assert n_ab <= n_dd + slack, (where, n_ab, n_dd, slack)
+    else:
+        assert n_dd <= n_ab + slack, (where, n_ab, n_dd, slack)
