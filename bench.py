@@ -100,6 +100,8 @@ def parse(argv=None):
                          "for each)")
     ap.add_argument("--inner-margin", type=float, default=None,
                     help="FP32-inner solves aim at this fraction of the tolerance (default: the library's)")
+    ap.add_argument("--no-guard", action="store_true",
+                    help="keep every data-driven correction (no guess guard: fem_opts.pred_guard = 0)")
     ap.add_argument("--check-every", type=int, default=8,
                     help="inner CG iterations per convergence check (graph: launches per WHILE-loop body)")
     ap.add_argument("--profile-steps", type=int, default=40,
@@ -302,10 +304,13 @@ def workload(args, rank):
 
 
 def margin_kw(args):
-    """fem_opts overrides of the inner solves (their aim, their CG product) given on the command line."""
+    """fem_opts overrides of the inner solves (their aim, their CG product) and of the guess guard given on
+    the command line."""
     kw = {} if args.inner_margin is None else {"inner_margin": args.inner_margin}
     if args.inner_product == "tc":
         kw["inner_product"] = 1
+    if args.no_guard:
+        kw["pred_guard"] = 0
     return kw
 
 
@@ -443,8 +448,10 @@ def config_dict(args, mesh=None):
             "cases_per_gpu": args.cases, "precision": args.precision, "predictor": args.predictor,
             "s_max": args.s_max, "cert_product": args.cert, "region_nodes": args.region_nodes, "tol": 1e-8,
             "inner_margin": args.inner_margin if args.inner_margin is not None else 0.5,
-            "inner_product": "FP16 hex element matrices on the tensor cores" if args.inner_product == "tc"
+            "inner_product": ("FP16 hex element matrices on the tensor cores in passes whose reduction targets "
+                              "are 1e-3 or coarser, FP32 element kernels otherwise") if args.inner_product == "tc"
                              else "FP32 element kernels",
+            "guess_guard": args.predictor == "dd" and not args.no_guard,
             "spinup_steps": args.spinup, "source": args.source, "absorbing_sides": args.absorbing,
             "cpu_predictor": args.cpu_predictor,
             "l2": "inputs larger than L2: each step streams the cases' state and the snapshot ring (>1 GB)",
@@ -496,6 +503,7 @@ def run_ours(args):
     log(f"{args.spinup} spin-up steps done; device memory in use {(total_b - free_b) / 1e9:.1f} of {total_b / 1e9:.1f} GB")
     fem.fem_step(bt, args.warmup, nc)
     # ---- timed region: device-resident, CUDA events on the batch stream ----
+    dropped0 = sum(fem.fem_case_stats(bt, c)["fallbacks"] for c in range(nc))
     sampler = ClockSampler(local)
     fem.fem_batch_profile(bt, 2)        # count launches only: the step graph stays a graph
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -512,6 +520,7 @@ def run_ours(args):
     clocks = sampler.stop()
     log(f"timed region: {args.steps} steps")
     launches = fem.fem_batch_profile(bt, 0)["kernel_launches"]
+    dropped = sum(fem.fem_case_stats(bt, c)["fallbacks"] for c in range(nc)) - dropped0
     ms = ev0.elapsed_time(ev1)
     # per-kernel-class device times: CUDA events around each launch over the next --profile-steps steps
     # (eager launches of the same kernels; events cannot sit inside the graph's conditional loops)
@@ -702,6 +711,7 @@ def run_ours(args):
                          f"(eager launches of the same kernels)",
         "cg_iters_per_case_step": float(iters.sum()) / (nc * args.steps),
         "max_certified_relres": float(relres.max()), "status": int(st),
+        "guess_guard_dropped": dropped,
         "phase_ms_per_step": {k: prof[k] / max(prof["steps"], 1) for k in
                               ("predict_ms", "rhs_ms", "solve_ms", "update_ms")},
         "kernel_ms_per_step": {"ebe32": prof["ebe32_ms"] / max(prof["steps"], 1),
@@ -889,9 +899,11 @@ def run_learned(args):
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
     K = args.case_steps
-    # both arms step eagerly (the proposal is not captured in the step graph): the same mode for both
+    # both arms step eagerly (the proposal is not captured in the step graph) and without the guess guard
+    # (steps that take a proposal skip it): the same mode for both
     opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=args.s_max,
-                                tol=1e-8, snapshot_format=args.snapshot_format, cert_df=args.cert, use_graph=0)
+                                tol=1e-8, snapshot_format=args.snapshot_format, cert_df=args.cert, use_graph=0,
+                                pred_guard=0)
 
     counts = [0, 0]
 

@@ -635,19 +635,22 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
   return FEM_OK;
 }
 
-// The options an FP32-inner solve runs with: with the FP16 tensor-core inner product (relative error ~2.4e-4)
-// one inner solve is not asked for more than a 1e-3 reduction; the refinement passes take it from there.
-static fem_opts inner_opts(const fem_opts& o) {
-  fem_opts r = o;
-  if (o.inner_product == FEM_INNER_TC) r.inner_tol = std::max(o.inner_tol, 1e-3);
-  return r;
+// Whether a refinement pass runs its inner CG products on the tensor cores (inner_product FEM_INNER_TC): only
+// when every active case's reduction target is at least kTcFloor, what a product with FP16 operands (relative
+// error ~2.4e-4) still delivers in one pass; a pass that asks more of some case takes the FP32 product, so the
+// tensor cores never cost a refinement pass.
+static bool tc_pass(const fem_opts& o, const CgCase* h_sc, int ncase) {
+  if (o.inner_product != FEM_INNER_TC) return false;
+  for (int c = 0; c < ncase; ++c)
+    if (h_sc[c].active && h_sc[c].inner_tol < kTcFloor) return false;
+  return true;
 }
 
 // FP32-inner / FP64-outer iterative refinement:  r64 = b - A64 x;  A32 d = r64 (inner PCG);  x += d.
 static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double* x, const fem_opts& o_in,
                               cudaStream_t s) {
-  const fem_opts o = inner_opts(o_in);
-  w->tc = o.inner_product == FEM_INNER_TC;
+  const fem_opts& o = o_in;
+  w->tc = false;
   const MeshView mv = m->view();
   const int rpad = w->rpad;
   const Reducer red = w->red();
@@ -673,6 +676,7 @@ static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double
       CU(cudaMemcpyAsync(w->outer, w->h_sc, sizeof(CgCase) * rpad, cudaMemcpyHostToDevice, s));
       break;
     }
+    w->tc = tc_pass(o, w->h_sc, rpad);
     CHK(pcg_core<float>(m, w, w->r32, w->x32, w->rr32, w->z32, w->p32, w->q32, w->sc, true, false, o.inner_tol,
                         o.maxit - used, w->outer, o.check_every, s));
     if (defer_inner(mv)) {
@@ -1129,9 +1133,9 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   cudaStream_t s = bt->s;
   const int it = g->steps + 1;
   const double dt = m->tp.dt;
-  const fem_opts o = inner_opts(bt->opts);
+  const fem_opts& o = bt->opts;
   Workspace* w = g->ws;
-  w->tc = o.inner_product == FEM_INNER_TC;
+  w->tc = false;
   const Reducer red = w->red();
   auto vslot = [&](int j) { return g->vh[((j % 4) + 4) % 4]; };
   auto aslot = [&](int j) { return g->Av[((j % 4) + 4) % 4]; };
@@ -1208,6 +1212,7 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
           if (w->h_sc[c].active) w->h_sc[c].status = FEM_ERR_NOT_CONVERGED, w->h_sc[c].active = 0;
         CU(cudaMemcpyAsync(w->outer, w->h_sc, sizeof(CgCase) * g->ncase, cudaMemcpyHostToDevice, s));
       } else {
+        w->tc = tc_pass(o, w->h_sc, g->ncase);
         CHK(pcg_core<float>(m, w, w->r32, w->x32, w->rr32, w->z32, w->p32, w->q32, w->sc, true, false, o.inner_tol,
                             o.maxit - used, w->outer, o.check_every, s));
         if (defer_inner(mv)) {
@@ -1343,11 +1348,14 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   const MeshView mv = m->view();
   Workspace* w = g->ws;
   const Reducer red = w->red();
-  const fem_opts o = inner_opts(bt->opts);
-  w->tc = o.inner_product == FEM_INNER_TC;
+  const fem_opts& o = bt->opts;
+  w->tc = false;
   const double dt = m->tp.dt;
   const int rpad = g->rpad;
   const bool sg = mv.seg != nullptr;
+  // FEM_INNER_TC: each pass's inner loop is captured twice, with the FP16 tensor-core product and with the
+  // FP32 one; a start kernel runs the one the pass's reduction targets allow (tc_pass) and skips the other
+  const bool sel = o.inner_product == FEM_INNER_TC && !sg;
   const bool dd = o.predictor == FEM_PRED_DD && g->n_regions > 0;
   const PredView pv = pred_view(bt, g);
   const Ring4 V{{g->vh[0], g->vh[1], g->vh[2], g->vh[3]}};
@@ -1357,7 +1365,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   cudaStream_t s = g->gs[0], s2 = g->gs[1], s3 = g->gs[2], s4 = g->gs[3];
   const bool ab = m->ab.nb > 0;
   const long long n_fixed = 6 + (dd ? 5 + (o.pred_guard ? 1 : 0) : 0) + (g->imp.n > 0 ? 1 : 0) + (ab ? 3 + (dd ? 1 : 0) : 0),
-                  n_pass = 4 + (ab ? 1 : 0), n_if = sg ? 4 : 2, n_inner = (ab ? 4LL : 3LL) * ce + 1;
+                  n_pass = 4 + (ab ? 1 : 0), n_if = sg ? 4 : (sel ? 3 : 2), n_inner = (ab ? 4LL : 3LL) * ce + 1;
   // 1. step record; the per-region Gram solves (few warps per SM) run beside the Adams-Bashforth
   // increment and the right-hand side, which do not depend on them
   GE(launch_step_begin(ctl, dd ? g->n_slots : 0, o.s_max, dt, dd ? 1 : 0, n_fixed, s));
@@ -1398,8 +1406,8 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   }
   if (guard) GE(launch_guard_fix(mv, rpad, w->outer, qy, w->r32, g->du_ab, g->guess, g->x, s));
   // 4. refinement passes: WHILE (pass 0, then while a case is above tol)
-  cudaGraphConditionalHandle h_pass, h_if, h_in;
-  cudaGraph_t b_pass, b_if, b_in, tmp;
+  cudaGraphConditionalHandle h_pass, h_if;
+  cudaGraph_t b_pass, b_if, tmp;
   GE(cond_node(s, cudaGraphCondTypeWhile, 1, cudaGraphCondAssignDefault, &h_pass, &b_pass));
   GE(cudaStreamBeginCaptureToGraph(s2, b_pass, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   {
@@ -1427,38 +1435,53 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
       if (sg) GE(launch_norm_b_seg<float>(mv, w->r32, red, w->sc, w->outer, o.inner_tol, s3));
       GE(cudaMemsetAsync(w->x32, 0, sizeof(float) * (size_t)w->n, s3));
       if (sg) GE(launch_resid_seg<float>(mv, w->r32, nullptr, w->x32, w->rr32, w->z32, red, w->sc, w->n_active, s3));
-      cudaGraph_t gi = nullptr;
-      GE(cudaStreamGetCaptureInfo(s3, &cs, nullptr, &gi, nullptr, nullptr, nullptr));
-      GE(cudaGraphConditionalHandleCreate(&h_in, gi, 0, 0));
-      GE(launch_inner_start(w->n_active, ctl, h_in, s3));
-      cudaGraphNodeParams pin{};
-      GE(cudaStreamGetCaptureInfo(s3, &cs, nullptr, &gi, &deps, nullptr, &nd));
-      pin.type = cudaGraphNodeTypeConditional;
-      pin.conditional.handle = h_in;
-      pin.conditional.type = cudaGraphCondTypeWhile;
-      pin.conditional.size = 1;
-      cudaGraphNode_t nin;
-      GE(cudaGraphAddNode(&nin, gi, deps, nullptr, nd, &pin));
-      GE(cudaStreamUpdateCaptureDependencies(s3, &nin, nullptr, 1, cudaStreamSetCaptureDependencies));
-      b_in = pin.conditional.phGraph_out[0];
-      GE(cudaStreamBeginCaptureToGraph(s4, b_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      for (int k = 0; k < ce; ++k) {
-        if (sg) {
-          GE(launch_dir_seg<float>(mv, w->z32, w->p32, w->sc, w->n_active, s4));
+      // the inner PCG: WHILE a case iterates, chunks of ce iterations (want: -1 the loop always starts;
+      // 1 / 0 it starts only if the pass does / does not take the tensor-core product)
+      auto inner_loop = [&](bool tc_loop, int want) -> cudaError_t {
+        cudaGraphConditionalHandle h_in;
+        cudaGraph_t gi = nullptr, b_in = nullptr;
+        GE(cudaStreamGetCaptureInfo(s3, &cs, nullptr, &gi, nullptr, nullptr, nullptr));
+        GE(cudaGraphConditionalHandleCreate(&h_in, gi, 0, 0));
+        if (want < 0) {
+          GE(launch_inner_start(w->n_active, ctl, h_in, s3));
         } else {
-          GE(launch_dir_defer<float>(mv, rpad, w->r32, w->p32, w->x32, w->sc, w->n_active, s4));
+          GE(launch_inner_start_sel(w->n_active, ctl, h_in, w->outer, g->ncase, kTcFloor, want, s3));
         }
-        GE(ebe_product<float>(m, rpad, w->p32, w->q32, m->cM, m->cK, &red, w->sc, nullptr, w->n_active, s4, true,
-                              w->tc));
-        if (sg) {
-          GE(launch_update_seg<float>(mv, w->p32, w->q32, w->x32, w->rr32, w->z32, red, w->sc, w->n_active, o.maxit,
-                                      s4));
-        } else {
-          GE(launch_update_defer<float>(mv, rpad, w->q32, w->r32, red, w->sc, w->n_active, o.maxit, s4));
+        cudaGraphNodeParams pin{};
+        GE(cudaStreamGetCaptureInfo(s3, &cs, nullptr, &gi, &deps, nullptr, &nd));
+        pin.type = cudaGraphNodeTypeConditional;
+        pin.conditional.handle = h_in;
+        pin.conditional.type = cudaGraphCondTypeWhile;
+        pin.conditional.size = 1;
+        cudaGraphNode_t nin;
+        GE(cudaGraphAddNode(&nin, gi, deps, nullptr, nd, &pin));
+        GE(cudaStreamUpdateCaptureDependencies(s3, &nin, nullptr, 1, cudaStreamSetCaptureDependencies));
+        b_in = pin.conditional.phGraph_out[0];
+        GE(cudaStreamBeginCaptureToGraph(s4, b_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        for (int k = 0; k < ce; ++k) {
+          if (sg) {
+            GE(launch_dir_seg<float>(mv, w->z32, w->p32, w->sc, w->n_active, s4));
+          } else {
+            GE(launch_dir_defer<float>(mv, rpad, w->r32, w->p32, w->x32, w->sc, w->n_active, s4));
+          }
+          GE(ebe_product<float>(m, rpad, w->p32, w->q32, m->cM, m->cK, &red, w->sc, nullptr, w->n_active, s4, true,
+                                tc_loop));
+          if (sg) {
+            GE(launch_update_seg<float>(mv, w->p32, w->q32, w->x32, w->rr32, w->z32, red, w->sc, w->n_active,
+                                        o.maxit, s4));
+          } else {
+            GE(launch_update_defer<float>(mv, rpad, w->q32, w->r32, red, w->sc, w->n_active, o.maxit, s4));
+          }
         }
+        GE(launch_inner_cond(w->n_active, ctl, h_in, ce, o.maxit + 64 * ce, n_inner, s4));
+        return cudaStreamEndCapture(s4, &tmp);
+      };
+      if (sel) {
+        GE(inner_loop(true, 1));
+        GE(inner_loop(false, 0));
+      } else {
+        GE(inner_loop(false, -1));
       }
-      GE(launch_inner_cond(w->n_active, ctl, h_in, ce, o.maxit + 64 * ce, n_inner, s4));
-      GE(cudaStreamEndCapture(s4, &tmp));
       if (sg) {
         GE(launch_refine_counts(mv, rpad, g->ncase, g->x, w->x32, w->outer, w->sc, s3));
       } else {

@@ -17,6 +17,9 @@ constexpr int kMaxRpad = 32;             // max cases per multi-RHS group (lanes
 constexpr int kMaxCases = 128;           // max cases of a group (fused groups: one case per mesh)
 constexpr int kMaxSlots = 33;            // predictor ring: s_max + 1 <= 33
 constexpr int kDefaultWaitBudget = 1 << 20;   // tries (<= 1 us each) of a reporting device-side wait
+// Smallest per-pass reduction target of an inner solve whose CG products take FP16 operands on the tensor
+// cores (relative error ~2.4e-4 a product); a pass that asks a case for more runs FP32 products.
+constexpr double kTcFloor = 1e-3;
 constexpr int kMaxRedBlocks = 1216;     // rows of the per-block partial-sum buffers of reducing kernels
 
 // Per-element record, 12 values: g1 (3), g2 (3), g3 (3) shape-function gradients of local nodes 1..3
@@ -435,6 +438,8 @@ cudaError_t launch_set_cond(cudaGraphConditionalHandle h, unsigned value, cudaSt
 cudaError_t launch_pass_begin(CgCase* outer, int ncase, int* n_active, int maxit, int max_pass, StepCtl* ctl,
                               cudaGraphConditionalHandle h_if, long long n_if, cudaStream_t s);
 cudaError_t launch_inner_start(const int* n_active, StepCtl* ctl, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_inner_start_sel(const int* n_active, StepCtl* ctl, cudaGraphConditionalHandle h,
+                                   const CgCase* outer, int ncase, double floor, int want_tc, cudaStream_t s);
 cudaError_t launch_inner_cond(const int* n_active, StepCtl* ctl, cudaGraphConditionalHandle h, int chunk, int limit,
                               long long n_body, cudaStream_t s);
 cudaError_t launch_pass_end(const int* n_active, StepCtl* ctl, cudaGraphConditionalHandle h, int max_pass,

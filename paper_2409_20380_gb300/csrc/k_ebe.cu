@@ -1725,8 +1725,8 @@ cudaError_t launch_ebe_split_df(const MeshView& m, const float* rec_df, int rpad
 // operand needs only corner slots 2tq and 2tq + 1, and its outputs are the three components of corner slot
 // gq.  Sums go to the tile accumulator in the packed kernel's fixed point; p^T q is taken at the flush from
 // the tile's sums and its FP32 values of p.  FP16 operands carry ~2.4e-4 of relative error into a product
-// (FP32 accumulation): the inner solve's refinement passes remove it (its reduction target is floored at
-// 1e-3).  Blocks of 256 threads (two an SM with 64-hex tiles at 8 cases, three with 32-hex tiles at 16):
+// (FP32 accumulation): a refinement pass takes this product only when its reduction targets are 1e-3 or
+// coarser, and the FP64 certification removes the rest.  Blocks of 256 threads (two an SM with 64-hex tiles at 8 cases, three with 32-hex tiles at 16):
 // the node rows are double-buffered, the records single-buffered (the next tile's records are requested
 // once the hexes of this one are done).
 // ------------------------------------------------------------------------------------------------------

@@ -69,6 +69,19 @@ __global__ void k_inner_start(const int* n_active, StepCtl* ctl, cudaGraphCondit
   cudaGraphSetConditional(h, *n_active > 0 ? 1u : 0u);
 }
 
+// Start of one of a pass's two inner loops (FP16 tensor-core products, want_tc 1; FP32 products, 0): the pass
+// takes the tensor-core product only if every active case's reduction target is at least `floor`; the loop
+// of the other product is skipped.
+__global__ void k_inner_start_sel(const int* n_active, StepCtl* ctl, cudaGraphConditionalHandle h,
+                                  const CgCase* outer, int ncase, double floor, int want_tc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  bool tc = true;
+  for (int c = 0; c < ncase; ++c)
+    if (outer[c].active && outer[c].inner_tol < floor) tc = false;
+  ctl->issued = 0;
+  cudaGraphSetConditional(h, (*n_active > 0 && tc == (want_tc != 0)) ? 1u : 0u);
+}
+
 // After a chunk of inner iterations: continue while a case iterates, up to the issue limit.
 __global__ void k_inner_cond(const int* n_active, StepCtl* ctl, cudaGraphConditionalHandle h, int chunk, int limit,
                              long long n_body) {
@@ -119,6 +132,12 @@ cudaError_t launch_pass_begin(CgCase* outer, int ncase, int* n_active, int maxit
 
 cudaError_t launch_inner_start(const int* n_active, StepCtl* ctl, cudaGraphConditionalHandle h, cudaStream_t s) {
   k_inner_start<<<1, 32, 0, s>>>(n_active, ctl, h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inner_start_sel(const int* n_active, StepCtl* ctl, cudaGraphConditionalHandle h,
+                                   const CgCase* outer, int ncase, double floor, int want_tc, cudaStream_t s) {
+  k_inner_start_sel<<<1, 32, 0, s>>>(n_active, ctl, h, outer, ncase, floor, want_tc);
   return cudaGetLastError();
 }
 

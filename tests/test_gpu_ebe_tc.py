@@ -130,3 +130,31 @@ def test_tc_inner_product_option_checked(torch_dev):
     with pytest.raises(fem.FemError) as ei:
         fem.fem_batch_create(fem.fem_opts_default(precision=fem.FEM_FP32_INNER, inner_product=2))
     assert ei.value.status == fem.FEM_ERR_ARG
+
+
+def test_tc_pass_selection(torch_dev):
+    """A refinement pass takes the FP16 products only when every active case asks its inner solve for a
+    reduction of 1e-3 or less: from rest (the predictor not yet trained, initial residuals near 1) passes run
+    the FP32 products, later ones the FP16 products (eager steps, where the profile tells the two apart; the
+    predictor's correction product is the one FP32 product a step otherwise has)."""
+    mesh = wl.config4_mesh(16, 16, 12)
+    tp = wl.config4_time_params()
+    srcs = wl.config4_sources(mesh, 8)
+    opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=16,
+                                cert_df=3, snapshot_format=2, use_graph=0, inner_product=fem.FEM_INNER_TC)
+    h = fem.fem_mesh_create(mesh, tp)
+    fem.fem_mesh_set_regions(h, wl.region_map(mesh, 1024))
+    bt = fem.fem_batch_create(opts)
+    try:
+        for s in srcs:
+            fem.fem_case_add(bt, h, s)
+        fem.fem_batch_profile(bt, 1)
+        n = 60
+        st, it, rel = fem.fem_step(bt, n, len(srcs))
+        prof = fem.fem_batch_profile(bt, 0)
+        assert np.all(rel < opts.tol)
+        assert prof["ebe16_launches"] > 0, prof
+        assert prof["ebe32_launches"] > n, prof
+    finally:
+        fem.fem_batch_destroy(bt)
+        fem.fem_mesh_destroy(h)

@@ -340,7 +340,10 @@ def test_sample_collection_matches_oracle(torch_dev):
 
 
 def _run_cases(mesh, tp, regions, srcs, n_steps, net=None, s_max=8, collect=None):
-    opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=s_max, tol=1e-8)
+    # (steps that take a learned proposal run without the guess guard; the plain arm does too, so the two
+    # arms differ by the network alone)
+    opts = fem.fem_opts_default(precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=s_max, tol=1e-8,
+                                pred_guard=0)
     h = fem.fem_mesh_create(mesh, tp)
     fem.fem_mesh_set_regions(h, regions)
     bt = fem.fem_batch_create(opts)
