@@ -238,7 +238,7 @@ __global__ void k_r0_seg(MeshView m, double h, const double* __restrict__ b, con
         v[1] += val * val;
         if (ALT) {
           const float fa = dof_free(f, k) ? rf + qv : 0.f;
-          v[NQ - 1] += (double)fa * (double)fa;
+          v[NQ - 1] += (double)(fa * fa);
         }
       }
     }

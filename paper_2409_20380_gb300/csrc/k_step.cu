@@ -267,6 +267,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_pred_dots(PredView p, int slot_ne
   const int rk = blockIdx.x / kDotGroups;   // the slot groups of one chunk are neighbours in the launch order,
   const int R = rk / p.n_chunks, k = rk % p.n_chunks;   // so their reads of the new slot's chunk share L2
   const int j0 = (blockIdx.x % kDotGroups) * kDotGrp;
+  // a group with no stored slot (the ring holds s + 1 <= kMaxSlots slots) has nothing to add
+  if (((valid_mask >> j0) & ((1ull << kDotGrp) - 1ull)) == 0ull) return;
   const int64_t lo = p.reg_lo[R], hi = p.reg_hi[R];
   const int64_t len = (hi - lo + p.n_chunks - 1) / p.n_chunks;
   const int64_t c_lo = lo + k * len, c_hi = c_lo + len < hi ? c_lo + len : hi;
@@ -776,12 +778,12 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_r0(MeshView m, int rpad, int r
       rf[k] = d2f(v);
       r32[id] = rf[k];
       bb += bv * bv;
-      rr += v * v;
-      if (ALT) {
-        fa[k] = dof_free(f, k) ? rf[k] + qv : 0.f;
-        ra += (double)fa[k] * (double)fa[k];
-      }
+      if (ALT) fa[k] = dof_free(f, k) ? rf[k] + qv : 0.f;
     }
+    // the residual norms from the FP32 values, a node's three squares summed in FP32 (relative error ~1e-7;
+    // the FP64 pipe, which bounds this kernel, takes one add a node instead of an FMA a value)
+    rr += (double)fmaf(rf[2], rf[2], fmaf(rf[1], rf[1], rf[0] * rf[0]));
+    if (ALT) ra += (double)fmaf(fa[2], fa[2], fmaf(fa[1], fa[1], fa[0] * fa[0]));
     if (inner) {
       zr += zr_node(m.binv32 + n * 6, rf[0], rf[1], rf[2]);
       if (ALT) za += zr_node(m.binv32 + n * 6, fa[0], fa[1], fa[2]);
