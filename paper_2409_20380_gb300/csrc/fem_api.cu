@@ -767,7 +767,8 @@ struct Group {
   RickerSrc* src = nullptr;
   double* ext = nullptr;        // device [ncase][3]: external loads for the next step
   // FP32-inner steps: products kept by recurrences (K u, M v, K v, M a, ring of A v) and split products
-  double *Ku = nullptr, *Mv = nullptr, *Kv = nullptr, *Ma = nullptr, *Av[4] = {nullptr, nullptr, nullptr, nullptr};
+  // (Pb = M a + (4/dt + a0) M v + a1 K v - K u: the right-hand side without the loads)
+  double *Ku = nullptr, *Mv = nullptr, *Kv = nullptr, *Pb = nullptr, *Av[4] = {nullptr, nullptr, nullptr, nullptr};
   double *qM = nullptr, *qK = nullptr;
   float2* xdf = nullptr;          // (hi, lo) split of the product input for the double-float assembled product
   bool use_ext = false;
@@ -808,7 +809,7 @@ struct Group {
     dfree(b); dfree(x); dfree(du_ab); dfree(m_in); dfree(k_in); dfree(guess);
     if (ring) cudaFree(ring);
     dfree(gram); dfree(wcoef); dfree(dpart); dfree(slot_lists); dfree(src); dfree(ext);
-    dfree(Ku); dfree(Mv); dfree(Kv); dfree(Ma); dfree(qM); dfree(qK); dfree(xdf);
+    dfree(Ku); dfree(Mv); dfree(Kv); dfree(Pb); dfree(qM); dfree(qK); dfree(xdf);
     for (auto& v : Av) dfree(v);
     dfree(F); dfree(dw); dfree(wbest); dfree(ydelta); dfree(choose); dfree(counts); dfree(case_src); dfree(e2case);
     dfree(fb);
@@ -886,7 +887,7 @@ static fem_status group_alloc(fem_batch* bt, Group* g) {
   CU(cudaMemsetAsync(g->guess, 0, n * 8, s));
   CU(cudaMemsetAsync(g->b, 0, n * 8, s));
   if (bt->opts.precision == FEM_FP32_INNER) {
-    for (double** v : {&g->Ku, &g->Mv, &g->Kv, &g->Ma, &g->Av[0], &g->Av[1], &g->Av[2], &g->Av[3], &g->qM, &g->qK}) {
+    for (double** v : {&g->Ku, &g->Mv, &g->Kv, &g->Pb, &g->Av[0], &g->Av[1], &g->Av[2], &g->Av[3], &g->qM, &g->qK}) {
       CHK(dalloc(v, n));
       CU(cudaMemsetAsync(*v, 0, n * 8, s));
     }
@@ -1107,7 +1108,7 @@ static fem_status group_refresh(fem_batch* bt, Group* g) {
   const int cm = bt->opts.cert_df;
   CU(split_product(m, cm, g->rpad, g->u, g->xdf, g->qM, g->qK, s));
   CU(cudaMemcpyAsync(g->Ku, g->qK, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
-  CU(split_product(m, cm, g->rpad, g->a, g->xdf, g->Ma, g->qK, s));
+  CU(split_product(m, cm, g->rpad, g->a, g->xdf, g->Pb, g->qK, s));   // (M a into Pb, completed below)
   for (int j = it - 3; j <= it; ++j) {
     const int sl = ((j % 4) + 4) % 4;
     CU(split_product(m, cm, g->rpad, g->vh[sl], g->xdf, g->qM, g->qK, s));
@@ -1119,7 +1120,8 @@ static fem_status group_refresh(fem_batch* bt, Group* g) {
       CU(cudaMemcpyAsync(g->Kv, g->qK, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, s));
     }
   }
-  g->ws->count(12);
+  CU(launch_pb_form(g->n, m->tp.dt, m->tp.a0, m->tp.a1, g->Pb, g->Mv, g->Kv, g->Ku, s));
+  g->ws->count(13);
   return FEM_OK;
 }
 
@@ -1148,7 +1150,7 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   w->pend(ph, s);
   // 2. right-hand side (Section 3.1, Eq. GE:DIS) from the recurrences
   ph = w->pbeg(P_RHS, s);
-  CU(launch_rhs_incr(mv, g->rpad, dt, m->tp.a0, m->tp.a1, g->Ma, g->Mv, g->Kv, g->Ku, g->b, g->src,
+  CU(launch_rhs_incr(mv, g->rpad, g->Pb, g->b, g->src,
                      g->use_ext ? g->ext : nullptr, it * dt, s));
   // random impulses of this step, and the dashpots' C_b v of absorbing boundaries
   CU(launch_impulses(g->imp, g->rpad, it, nullptr, m->fm, g->b, s));
@@ -1251,8 +1253,9 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
   if (dd) {
     e_push = (char*)g->ring + snap_bytes(o.snapshot_format) * (size_t)g->snap_stride * slot_of(g, it);
   }
-  CU(launch_newmark_incr(g->n, dt, m->cM, m->cK, g->x, g->du_ab, g->qM, g->qK, g->u, vslot(it - 1), g->a, vslot(it),
-                         g->Ku, g->Mv, g->Kv, g->Ma, aslot(it), e_push, o.snapshot_format, s, Ring4{}, Ring4{},
+  CU(launch_newmark_incr(g->n, dt, m->cM, m->cK, m->tp.a0, m->tp.a1, g->x, g->du_ab, g->qM, g->qK, g->u,
+                         vslot(it - 1), g->a, vslot(it), g->Ku, g->Mv, g->Kv, g->Pb, aslot(it), e_push,
+                         o.snapshot_format, s, Ring4{}, Ring4{},
                          nullptr, g->snap_stride));
   CU(launch_dashpot<double>(m->ab, g->rpad, m->ab.cB, vslot(it), aslot(it), false, m->fm, nullptr, nullptr, nullptr,
                             nullptr, s));
@@ -1374,7 +1377,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   GE(cudaStreamWaitEvent(sf, g->gev[0], 0));
   GE(launch_ab4_ring(g->n, dt, V, ctl, g->du_ab, sf));
   // 2. right-hand side from the recurrences
-  GE(launch_rhs_incr(mv, rpad, dt, m->tp.a0, m->tp.a1, g->Ma, g->Mv, g->Kv, g->Ku, g->b, g->src, g->ext, 0.0, sf,
+  GE(launch_rhs_incr(mv, rpad, g->Pb, g->b, g->src, g->ext, 0.0, sf,
                      ctl));
   GE(launch_impulses(g->imp, rpad, 0, ctl, m->fm, g->b, sf));
   if (ab)
@@ -1508,8 +1511,9 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
     GE(launch_dashpot<double>(m->ab, rpad, -m->ab.cB / m->cK, g->x, g->qK, false, m->fm, nullptr, nullptr, nullptr,
                               nullptr, s));
   // 5. Newmark update, recurrences, snapshot push, Gram row of the new snapshot, statistics
-  GE(launch_newmark_incr(g->n, dt, m->cM, m->cK, g->x, g->du_ab, g->qM, g->qK, g->u, nullptr, g->a, nullptr, g->Ku,
-                         g->Mv, g->Kv, g->Ma, nullptr, nullptr, o.snapshot_format, s, V, AV, dd ? g->ring : nullptr,
+  GE(launch_newmark_incr(g->n, dt, m->cM, m->cK, m->tp.a0, m->tp.a1, g->x, g->du_ab, g->qM, g->qK, g->u, nullptr,
+                         g->a, nullptr, g->Ku, g->Mv, g->Kv, g->Pb, nullptr, nullptr, o.snapshot_format, s, V, AV,
+                         dd ? g->ring : nullptr,
                          g->snap_stride, ctl));
   if (ab)
     GE(launch_dashpot<double>(m->ab, rpad, m->ab.cB, nullptr, nullptr, false, m->fm, nullptr, nullptr, nullptr, nullptr,

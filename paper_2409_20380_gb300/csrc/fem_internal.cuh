@@ -271,9 +271,12 @@ cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const 
                                   int64_t stride, cudaStream_t s);
 
 // FP32-inner steps with products kept by recurrences (see k_step.cu).
-cudaError_t launch_rhs_incr(const MeshView& m, int rpad, double dt, double a0, double a1, const double* Ma,
-                            const double* Mv, const double* Kv, const double* Ku, double* b, const RickerSrc* src,
+// b = f + Pb on free DOFs, Pb = M a + (4/dt + a0) M v + a1 K v - K u kept by launch_newmark_incr
+cudaError_t launch_rhs_incr(const MeshView& m, int rpad, const double* Pb, double* b, const RickerSrc* src,
                             const double* ext, double t, cudaStream_t s, const StepCtl* ctl = nullptr);
+// Pb <- Pb + (4/dt + a0) Mv + a1 Kv - Ku (Pb holding M a): the refresh's direct form of Pb
+cudaError_t launch_pb_form(int64_t n, double dt, double a0, double a1, double* Pb, const double* Mv, const double* Kv,
+                           const double* Ku, cudaStream_t s);
 cudaError_t launch_corr_f32(int64_t n, const double* guess, const double* du_ab, float* y32, cudaStream_t s);
 // inner != null (r0, cert): also start the inner FP32 solve of the pass on r32 (zero guess, its residual
 // r32 itself): the inner case state as the norm and first-residual passes would leave it.
@@ -293,11 +296,12 @@ cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const
                         double inner_max, double aim, cudaStream_t s, CgCase* inner = nullptr);
 // With ctl: v_prev, v_push, Av_push and the snapshot slot come from the rings (vr, avr, ring of slots of
 // slot_stride elements) at the step read from ctl.
-cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, const double* du, const double* du_ab,
-                                const double* qM, const double* qK, double* u, const double* v_prev, double* a,
-                                double* v_push, double* Ku, double* Mv, double* Kv, double* Ma, double* Av_push,
-                                void* e_push, int e_fmt, cudaStream_t s, Ring4 vr = Ring4{}, Ring4 avr = Ring4{},
-                                void* ring = nullptr, int64_t slot_stride = 0, const StepCtl* ctl = nullptr);
+cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, double a0, double a1, const double* du,
+                                const double* du_ab, const double* qM, const double* qK, double* u,
+                                const double* v_prev, double* a, double* v_push, double* Ku, double* Mv, double* Kv,
+                                double* Pb, double* Av_push, void* e_push, int e_fmt, cudaStream_t s,
+                                Ring4 vr = Ring4{}, Ring4 avr = Ring4{}, void* ring = nullptr,
+                                int64_t slot_stride = 0, const StepCtl* ctl = nullptr);
 cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, const double* y, double* out,
                          cudaStream_t s);
 // Split FP64 product: qM = M p and qK = K p in one pass (generic element kernel).

@@ -631,13 +631,13 @@ __global__ void k_extract_all(int64_t n3, int rpad, int n_cases, const double* _
 }
 
 // ---- products kept by linear recurrences (FP32-inner steps) ----
-// With Ku, Mv, Kv, Ma maintained exactly (FP64) from the split products M du, K du of each certified
-// increment, the Newmark right-hand side needs no EBE pass:
-//   b = f + M a + (4/dt + a0) M v + a1 K v - K u.
-__global__ void k_rhs_incr(MeshView m, int rpad, int rshift, double c_mv, double a1, const double* __restrict__ Ma,
-                           const double* __restrict__ Mv, const double* __restrict__ Kv,
-                           const double* __restrict__ Ku, double* __restrict__ b, const RickerSrc* __restrict__ src,
-                           const double* __restrict__ ext, double t, const StepCtl* ctl) {
+// With K u, M v, K v maintained exactly (FP64) from the split products M du, K du of each certified
+// increment, and with them the load-free part of the Newmark right-hand side
+//   Pb = M a + (4/dt + a0) M v + a1 K v - K u,
+// the right-hand side needs no EBE pass and reads one vector:  b = f + Pb.
+__global__ void k_rhs_incr(MeshView m, int rpad, int rshift, const double* __restrict__ Pb, double* __restrict__ b,
+                           const RickerSrc* __restrict__ src, const double* __restrict__ ext, double t,
+                           const StepCtl* ctl) {
   if (ctl) {
     t = ctl->t;
     if (!ctl->use_ext) ext = nullptr;
@@ -652,29 +652,23 @@ __global__ void k_rhs_incr(MeshView m, int rpad, int rshift, double c_mv, double
     return make_double3(w * s.dir[0], w * s.dir[1], w * s.dir[2]);
   };
   if (!m.seg && rpad >= 2) {
-    // two cases (c, c + 1) a thread by 16-byte accesses: 12 vector loads in flight an item
+    // two cases (c, c + 1) a thread by 16-byte accesses
     const int rs1 = rshift - 1;
     const int64_t total = m.N << rs1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
       const int64_t n = i >> rs1;
       const int c = (int)(i & ((rpad >> 1) - 1)) << 1;
       const uint8_t f = m.freemask[n];
-      double2 ma[3], mv[3], kv[3], ku[3];
+      double2 pb[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int64_t id = (n * 3 + k) * rpad + c;
-        ma[k] = *reinterpret_cast<const double2*>(Ma + id), mv[k] = *reinterpret_cast<const double2*>(Mv + id);
-        kv[k] = *reinterpret_cast<const double2*>(Kv + id), ku[k] = *reinterpret_cast<const double2*>(Ku + id);
-      }
+      for (int k = 0; k < 3; ++k) pb[k] = *reinterpret_cast<const double2*>(Pb + (n * 3 + k) * rpad + c);
       const double3 g0 = load_of(n, c), g1 = load_of(n, c + 1);
       const double f0[3] = {g0.x, g0.y, g0.z}, f1[3] = {g1.x, g1.y, g1.z};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const int64_t id = (n * 3 + k) * rpad + c;
         *reinterpret_cast<double2*>(b + id) =
-            dof_free(f, k) ? make_double2(f0[k] + ma[k].x + c_mv * mv[k].x + a1 * kv[k].x - ku[k].x,
-                                          f1[k] + ma[k].y + c_mv * mv[k].y + a1 * kv[k].y - ku[k].y)
-                           : make_double2(0.0, 0.0);
+            dof_free(f, k) ? make_double2(f0[k] + pb[k].x, f1[k] + pb[k].y) : make_double2(0.0, 0.0);
       }
     }
     return;
@@ -690,9 +684,16 @@ __global__ void k_rhs_incr(MeshView m, int rpad, int rshift, double c_mv, double
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const int64_t id = (n * 3 + k) * rpad + c;
-      b[id] = dof_free(f, k) ? fv[k] + Ma[id] + c_mv * Mv[id] + a1 * Kv[id] - Ku[id] : 0.0;
+      b[id] = dof_free(f, k) ? fv[k] + Pb[id] : 0.0;
     }
   }
+}
+
+// Pb = Ma + c1 Mv + a1 Kv - Ku from directly computed products (the periodic refresh), in place of Ma.
+__global__ void k_pb_form(int64_t n, double c1, double a1, double* __restrict__ Pb, const double* __restrict__ Mv,
+                          const double* __restrict__ Kv, const double* __restrict__ Ku) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    Pb[i] = Pb[i] + c1 * Mv[i] + a1 * Kv[i] - Ku[i];
 }
 
 // y32 = float(guess - du_ab): the data-driven part of the guess, for its FP32 product.
@@ -949,14 +950,15 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_cert(MeshView m, int rpad, int
 
 // Newmark update with the product recurrences (du, its products qM = M du, qK = K du):
 //   u += du;  v' = 2/dt du - v;  a' = 4/dt^2 du - 4/dt v - a;
-//   Ku += qK;  Mv' = 2/dt qM - Mv;  Kv' = 2/dt qK - Kv;  Ma' = 4/dt^2 qM - 4/dt Mv - Ma;
-//   Av' = cM Mv' + cK Kv' (pushed to the 4-deep ring);  e = du - du_AB (snapshot).
+//   Ku += qK;  Mv' = 2/dt qM - Mv;  Kv' = 2/dt qK - Kv;  (Ma' = 4/dt^2 qM - 4/dt Mv - Ma, not stored: it
+//   enters Pb' below);  Av' = cM Mv' + cK Kv' (pushed to the 4-deep ring);  e = du - du_AB (snapshot).
 template <typename E>
-__global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, const double* __restrict__ du,
+__global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, double c1, double a1,
+                               const double* __restrict__ du,
                                const double* __restrict__ du_ab, const double* __restrict__ qM,
                                const double* __restrict__ qK, double* __restrict__ u, const double* __restrict__ v_prev,
                                double* __restrict__ a, double* __restrict__ v_push, double* __restrict__ Ku,
-                               double* __restrict__ Mv, double* __restrict__ Kv, double* __restrict__ Ma,
+                               double* __restrict__ Mv, double* __restrict__ Kv, double* __restrict__ Pb,
                                double* __restrict__ Av_push, E* __restrict__ e_push, Ring4 vr, Ring4 avr,
                                E* __restrict__ ring, int64_t slot_stride, const StepCtl* ctl) {
   if (ctl) {
@@ -967,6 +969,9 @@ __global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, const
     e_push = ring ? snap_slot(ring, ctl->slot_new, slot_stride) : nullptr;
   }
   const double c2 = 2.0 / dt, c4 = 4.0 / dt, c44 = 4.0 / (dt * dt);
+  // Pb' = Ma' + c1 Mv' + a1 Kv' - Ku' with the recurrences above substituted:
+  //   Pb' = (4/dt^2 + 2 c1/dt) qM + (2 a1/dt - 1) qK - Pb - 4/dt Mv - 2 Ku   (Mv, Ku before the update)
+  const double al = c44 + c1 * c2, be = a1 * c2 - 1.0;
   // two consecutive values a thread (vector loads and stores of every vector; n even), then a last odd one
   const int64_t npair = n >> 1;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npair; t += (int64_t)gridDim.x * blockDim.x) {
@@ -974,13 +979,14 @@ __global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, const
     auto ld = [&](const double* x) { return *reinterpret_cast<const double2*>(x + i); };
     auto st = [&](double* x, double y0, double y1) { *reinterpret_cast<double2*>(x + i) = make_double2(y0, y1); };
     const double2 d = ld(du), vp = ld(v_prev), m_ = ld(qM), k_ = ld(qK), uu = ld(u), aa = ld(a), ku = ld(Ku);
-    const double2 mv = ld(Mv), kv = ld(Kv), ma = ld(Ma);
+    const double2 mv = ld(Mv), kv = ld(Kv), pb = ld(Pb);
     st(u, uu.x + d.x, uu.y + d.y);
     st(v_push, c2 * d.x - vp.x, c2 * d.y - vp.y);
     st(a, c44 * d.x - c4 * vp.x - aa.x, c44 * d.y - c4 * vp.y - aa.y);
     st(Ku, ku.x + k_.x, ku.y + k_.y);
     const double mv2x = c2 * m_.x - mv.x, kv2x = c2 * k_.x - kv.x, mv2y = c2 * m_.y - mv.y, kv2y = c2 * k_.y - kv.y;
-    st(Ma, c44 * m_.x - c4 * mv.x - ma.x, c44 * m_.y - c4 * mv.y - ma.y);
+    st(Pb, al * m_.x + be * k_.x - (pb.x + c4 * mv.x + 2.0 * ku.x),
+       al * m_.y + be * k_.y - (pb.y + c4 * mv.y + 2.0 * ku.y));
     st(Mv, mv2x, mv2y);
     st(Kv, kv2x, kv2y);
     st(Av_push, cM * mv2x + cK * kv2x, cM * mv2y + cK * kv2y);
@@ -995,10 +1001,11 @@ __global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, const
     u[i] += d;
     v_push[i] = c2 * d - vp;
     a[i] = c44 * d - c4 * vp - a[i];
-    Ku[i] += k_;
+    const double ku = Ku[i];
+    Ku[i] = ku + k_;
     const double mv = Mv[i], kv = Kv[i];
     const double mv2 = c2 * m_ - mv, kv2 = c2 * k_ - kv;
-    Ma[i] = c44 * m_ - c4 * mv - Ma[i];
+    Pb[i] = al * m_ + be * k_ - (Pb[i] + c4 * mv + 2.0 * ku);
     Mv[i] = mv2;
     Kv[i] = kv2;
     Av_push[i] = cM * mv2 + cK * kv2;
@@ -1073,12 +1080,17 @@ cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_rhs_incr(const MeshView& m, int rpad, double dt, double a0, double a1, const double* Ma,
-                            const double* Mv, const double* Kv, const double* Ku, double* b, const RickerSrc* src,
+cudaError_t launch_rhs_incr(const MeshView& m, int rpad, const double* Pb, double* b, const RickerSrc* src,
                             const double* ext, double t, cudaStream_t s, const StepCtl* ctl) {
   const int rs = log2i(rpad);
-  k_rhs_incr<<<grid_resident((const void*)k_rhs_incr, kBlock, m.N << rs), kBlock, 0, s>>>(m, rpad, rs, 4.0 / dt + a0, a1, Ma, Mv, Kv, Ku, b, src, ext, t,
-                                                   ctl);
+  k_rhs_incr<<<grid_resident((const void*)k_rhs_incr, kBlock, m.N << rs), kBlock, 0, s>>>(m, rpad, rs, Pb, b, src, ext,
+                                                                                          t, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pb_form(int64_t n, double dt, double a0, double a1, double* Pb, const double* Mv, const double* Kv,
+                           const double* Ku, cudaStream_t s) {
+  k_pb_form<<<grid_for(n), kBlock, 0, s>>>(n, 4.0 / dt + a0, a1, Pb, Mv, Kv, Ku);
   return cudaGetLastError();
 }
 
@@ -1120,30 +1132,31 @@ cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, const double* du, const double* du_ab,
-                                const double* qM, const double* qK, double* u, const double* v_prev, double* a,
-                                double* v_push, double* Ku, double* Mv, double* Kv, double* Ma, double* Av_push,
-                                void* e_push, int e_fmt, cudaStream_t s, Ring4 vr, Ring4 avr, void* ring,
-                                int64_t slot_stride, const StepCtl* ctl) {
+cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, double a0, double a1, const double* du,
+                                const double* du_ab, const double* qM, const double* qK, double* u,
+                                const double* v_prev, double* a, double* v_push, double* Ku, double* Mv, double* Kv,
+                                double* Pb, double* Av_push, void* e_push, int e_fmt, cudaStream_t s, Ring4 vr,
+                                Ring4 avr, void* ring, int64_t slot_stride, const StepCtl* ctl) {
+  const double c1 = 4.0 / dt + a0;
   const int grid = e_fmt == 1   ? grid_resident((const void*)k_newmark_incr<float>, kBlock, n)
                    : e_fmt == 2 ? grid_resident((const void*)k_newmark_incr<float2>, kBlock, n)
                    : e_fmt == 3 ? grid_resident((const void*)k_newmark_incr<SnapHL>, kBlock, n)
                                 : grid_resident((const void*)k_newmark_incr<double>, kBlock, n);
   if (e_fmt == 1)
-    k_newmark_incr<float><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
-                                                         Mv, Kv, Ma, Av_push, (float*)e_push, vr, avr, (float*)ring,
+    k_newmark_incr<float><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a,
+                                                         v_push, Ku, Mv, Kv, Pb, Av_push, (float*)e_push, vr, avr, (float*)ring,
                                                          slot_stride, ctl);
   else if (e_fmt == 2)
-    k_newmark_incr<float2><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
-                                                          Mv, Kv, Ma, Av_push, (float2*)e_push, vr, avr, (float2*)ring,
+    k_newmark_incr<float2><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a,
+                                                          v_push, Ku, Mv, Kv, Pb, Av_push, (float2*)e_push, vr, avr, (float2*)ring,
                                                           slot_stride, ctl);
   else if (e_fmt == 3)
-    k_newmark_incr<SnapHL><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
-                                                          Mv, Kv, Ma, Av_push, (SnapHL*)e_push, vr, avr, (SnapHL*)ring,
+    k_newmark_incr<SnapHL><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a,
+                                                          v_push, Ku, Mv, Kv, Pb, Av_push, (SnapHL*)e_push, vr, avr, (SnapHL*)ring,
                                                           slot_stride, ctl);
   else
-    k_newmark_incr<double><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku,
-                                                          Mv, Kv, Ma, Av_push, (double*)e_push, vr, avr, (double*)ring,
+    k_newmark_incr<double><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a,
+                                                          v_push, Ku, Mv, Kv, Pb, Av_push, (double*)e_push, vr, avr, (double*)ring,
                                                           slot_stride, ctl);
   return cudaGetLastError();
 }
