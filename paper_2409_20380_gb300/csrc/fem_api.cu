@@ -639,8 +639,9 @@ static fem_status pcg_core(fem_mesh* m, Workspace* w, const T* b, T* x, T* r, T*
 // when every active case's reduction target is at least kTcFloor, what a product with FP16 operands (relative
 // error ~2.4e-4) still delivers in one pass; a pass that asks more of some case takes the FP32 product, so the
 // tensor cores never cost a refinement pass.
-static bool tc_pass(const fem_opts& o, const CgCase* h_sc, int ncase) {
-  if (o.inner_product != FEM_INNER_TC) return false;
+static bool tc_pass(const fem_opts& o, const fem_mesh* m, int rpad, const CgCase* h_sc, int ncase) {
+  // (the tensor-core product exists for linear-tet hex-patch meshes, one multi-RHS group of 8 or 16 lanes)
+  if (o.inner_product != FEM_INNER_TC || m->npe != 4 || m->seg || (rpad != 8 && rpad != 16)) return false;
   for (int c = 0; c < ncase; ++c)
     if (h_sc[c].active && h_sc[c].inner_tol < kTcFloor) return false;
   return true;
@@ -676,7 +677,7 @@ static fem_status solve_mixed(fem_mesh* m, Workspace* w, const double* b, double
       CU(cudaMemcpyAsync(w->outer, w->h_sc, sizeof(CgCase) * rpad, cudaMemcpyHostToDevice, s));
       break;
     }
-    w->tc = tc_pass(o, w->h_sc, rpad);
+    w->tc = tc_pass(o, m, rpad, w->h_sc, rpad);
     CHK(pcg_core<float>(m, w, w->r32, w->x32, w->rr32, w->z32, w->p32, w->q32, w->sc, true, false, o.inner_tol,
                         o.maxit - used, w->outer, o.check_every, s));
     if (defer_inner(mv)) {
@@ -1214,7 +1215,7 @@ static fem_status group_step_mixed(fem_batch* bt, Group* g, fem_status* worst) {
           if (w->h_sc[c].active) w->h_sc[c].status = FEM_ERR_NOT_CONVERGED, w->h_sc[c].active = 0;
         CU(cudaMemcpyAsync(w->outer, w->h_sc, sizeof(CgCase) * g->ncase, cudaMemcpyHostToDevice, s));
       } else {
-        w->tc = tc_pass(o, w->h_sc, g->ncase);
+        w->tc = tc_pass(o, m, g->rpad, w->h_sc, g->ncase);
         CHK(pcg_core<float>(m, w, w->r32, w->x32, w->rr32, w->z32, w->p32, w->q32, w->sc, true, false, o.inner_tol,
                             o.maxit - used, w->outer, o.check_every, s));
         if (defer_inner(mv)) {
