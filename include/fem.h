@@ -62,9 +62,9 @@ enum {
   FEM_INNER_FP32 = 0,    /* the FP32 element-by-element kernels (the default) */
   FEM_INNER_TC = 1       /* per-hex 24 x 24 element matrices of A in FP16 (the element data in reduced precision),
                             applied on the tensor cores with FP32 accumulation: ~2.4e-4 relative error in a
-                            product, so a refinement pass takes these products only when every active case asks
-                            its inner solve for a reduction of 1e-3 or less (a good initial guess); other passes
-                            take the FP32 kernels.  Hex-patch meshes, groups of 5..16 cases
+                            product, so a refinement pass takes these products only when every active case's
+                            reduction target is 1e-3 or coarser (its inner solve shrinks the residual by at most
+                            a factor of 1000: a good initial guess); other passes take the FP32 kernels.  Hex-patch meshes, groups of 5..16 cases
                             (8 or 16 lanes; other groups keep the FP32 kernels); the predictor's correction and
                             all other products stay FP32/FP64 */
 };
