@@ -370,6 +370,13 @@ def test_step_guess_guard(torch_dev, graph):
     assert res[1][1].get(2, 0) > 0, res
 
 
+def test_pred_guard_option_checked(torch_dev):
+    for g in (-1, 2):
+        with pytest.raises(fem.FemError) as ei:
+            fem.fem_batch_create(fem.fem_opts_default(precision=fem.FEM_FP32_INNER, pred_guard=g))
+        assert ei.value.status == fem.FEM_ERR_ARG
+
+
 def test_inner_margin_out_of_range_rejected(torch_dev):
     for m in (0.0, 1.0, -0.5):
         with pytest.raises(fem.FemError) as ei:
