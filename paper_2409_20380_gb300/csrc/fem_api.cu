@@ -794,7 +794,7 @@ struct Group {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t gs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // capture streams (top level, bodies, fork)
-  cudaEvent_t gev[2] = {nullptr, nullptr};                            // fork / join of the captured step
+  cudaEvent_t gev[4] = {nullptr, nullptr, nullptr, nullptr};          // forks / joins of the captured step
   int* h_pin = nullptr;           // pinned: [0] = 1 (use_ext flag), [1] = step counter to upload
   int ctl_it = -1;                // step counter the device record holds (-1: unknown, upload first)
   bool graph_failed = false;      // capture or instantiation failed: eager steps from now on
@@ -1368,7 +1368,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   const int ce = std::max(1, o.check_every);
   cudaStream_t s = g->gs[0], s2 = g->gs[1], s3 = g->gs[2], s4 = g->gs[3];
   const bool ab = m->ab.nb > 0;
-  const long long n_fixed = 6 + (dd ? 5 + (o.pred_guard ? 1 : 0) : 0) + (g->imp.n > 0 ? 1 : 0) + (ab ? 3 + (dd ? 1 : 0) : 0),
+  const long long n_fixed = 6 + (dd ? 6 + (o.pred_guard ? 1 : 0) : 0) + (g->imp.n > 0 ? 1 : 0) + (ab ? 3 + (dd ? 1 : 0) : 0),
                   n_pass = 4 + (ab ? 1 : 0), n_if = sg ? 4 : (sel ? 3 : 2), n_inner = (ab ? 4LL : 3LL) * ce + 1;
   // 1. step record; the per-region Gram solves (few warps per SM) run beside the Adams-Bashforth
   // increment and the right-hand side, which do not depend on them
@@ -1511,15 +1511,28 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   if (ab)   // (the certification's dashpot term leaves qK: the recurrences advance by K du)
     GE(launch_dashpot<double>(m->ab, rpad, -m->ab.cB / m->cK, g->x, g->qK, false, m->fm, nullptr, nullptr, nullptr,
                               nullptr, s));
-  // 5. Newmark update, recurrences, snapshot push, Gram row of the new snapshot, statistics
-  GE(launch_newmark_incr(g->n, dt, m->cM, m->cK, m->tp.a0, m->tp.a1, g->x, g->du_ab, g->qM, g->qK, g->u, nullptr,
-                         g->a, nullptr, g->Ku, g->Mv, g->Kv, g->Pb, nullptr, nullptr, o.snapshot_format, s, V, AV,
-                         dd ? g->ring : nullptr,
-                         g->snap_stride, ctl));
+  // 5. Newmark update, recurrences, snapshot push, Gram row of the new snapshot, statistics.  With the
+  // data-driven predictor the update runs in two parts: the velocity side first (the Gram row reads its
+  // snapshot), then the state side on the fork stream beside the Gram row.
+  const int n_part = dd ? 1 : 0;
+  GE(launch_newmark_incr_part(g->n, dt, m->cM, m->cK, m->tp.a0, m->tp.a1, g->x, g->du_ab, g->qM, g->qK, g->u, nullptr,
+                              g->a, nullptr, g->Ku, g->Mv, g->Kv, g->Pb, nullptr, nullptr, o.snapshot_format, s, V,
+                              AV, dd ? g->ring : nullptr, g->snap_stride, ctl, n_part));
+  if (dd) {
+    GE(cudaEventRecord(g->gev[2], s));
+    GE(cudaStreamWaitEvent(sf, g->gev[2], 0));
+    GE(launch_newmark_incr_part(g->n, dt, m->cM, m->cK, m->tp.a0, m->tp.a1, g->x, g->du_ab, g->qM, g->qK, g->u,
+                                nullptr, g->a, nullptr, g->Ku, g->Mv, g->Kv, g->Pb, nullptr, nullptr,
+                                o.snapshot_format, sf, V, AV, nullptr, g->snap_stride, ctl, 2));
+    GE(cudaEventRecord(g->gev[3], sf));
+  }
   if (ab)
     GE(launch_dashpot<double>(m->ab, rpad, m->ab.cB, nullptr, nullptr, false, m->fm, nullptr, nullptr, nullptr, nullptr,
                               s, V, 0, AV, 0, ctl));
-  if (dd) GE(launch_pred_dots(pv, 0, 0, s, ctl));
+  if (dd) {
+    GE(launch_pred_dots(pv, 0, 0, s, ctl));
+    GE(cudaStreamWaitEvent(s, g->gev[3], 0));
+  }
   GE(launch_step_end(w->outer, g->ncase, g->acc_iters, g->acc_relres, g->acc_status, ctl, s));
   return cudaSuccess;
 }

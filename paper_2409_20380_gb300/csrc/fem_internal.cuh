@@ -302,6 +302,14 @@ cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, doub
                                 double* Pb, double* Av_push, void* e_push, int e_fmt, cudaStream_t s,
                                 Ring4 vr = Ring4{}, Ring4 avr = Ring4{}, void* ring = nullptr,
                                 int64_t slot_stride = 0, const StepCtl* ctl = nullptr);
+// The same update in two parts: 1 the velocity side (v, M v, K v, A v, the snapshot), 2 the state side (u, a,
+// K u, Pb), launched after part 1 (it reads the updated M v); 0 both, as launch_newmark_incr.
+cudaError_t launch_newmark_incr_part(int64_t n, double dt, double cM, double cK, double a0, double a1,
+                                     const double* du, const double* du_ab, const double* qM, const double* qK,
+                                     double* u, const double* v_prev, double* a, double* v_push, double* Ku,
+                                     double* Mv, double* Kv, double* Pb, double* Av_push, void* e_push, int e_fmt,
+                                     cudaStream_t s, Ring4 vr, Ring4 avr, void* ring, int64_t slot_stride,
+                                     const StepCtl* ctl, int part);
 cudaError_t launch_axpby(int64_t n, double alpha, const double* x, double beta, const double* y, double* out,
                          cudaStream_t s);
 // Split FP64 product: qM = M p and qK = K p in one pass (generic element kernel).

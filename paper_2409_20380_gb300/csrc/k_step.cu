@@ -952,7 +952,11 @@ __global__ void __launch_bounds__(kVecBlock, 2) k_cert(MeshView m, int rpad, int
 //   u += du;  v' = 2/dt du - v;  a' = 4/dt^2 du - 4/dt v - a;
 //   Ku += qK;  Mv' = 2/dt qM - Mv;  Kv' = 2/dt qK - Kv;  (Ma' = 4/dt^2 qM - 4/dt Mv - Ma, not stored: it
 //   enters Pb' below);  Av' = cM Mv' + cK Kv' (pushed to the 4-deep ring);  e = du - du_AB (snapshot).
-template <typename E>
+// P selects the part: 0 all of it; 1 the velocity side (v, M v, K v, A v, the snapshot: what the Gram row and
+// the next step's Adams-Bashforth and guess residual read); 2 the state side (u, a, K u, Pb: what the next
+// right-hand side reads), run after part 1 so that it may overlap the Gram row.  Part 2 finds M v already
+// updated and uses  -4/dt Mv = 4/dt Mv' - (8/dt^2) qM  in the Pb recurrence.
+template <typename E, int P>
 __global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, double c1, double a1,
                                const double* __restrict__ du,
                                const double* __restrict__ du_ab, const double* __restrict__ qM,
@@ -968,48 +972,65 @@ __global__ void k_newmark_incr(int64_t n, double dt, double cM, double cK, doubl
     Av_push = avr.p[it & 3];
     e_push = ring ? snap_slot(ring, ctl->slot_new, slot_stride) : nullptr;
   }
+  constexpr bool VEL = P != 2, STATE = P != 1;
   const double c2 = 2.0 / dt, c4 = 4.0 / dt, c44 = 4.0 / (dt * dt);
   // Pb' = Ma' + c1 Mv' + a1 Kv' - Ku' with the recurrences above substituted:
   //   Pb' = (4/dt^2 + 2 c1/dt) qM + (2 a1/dt - 1) qK - Pb - 4/dt Mv - 2 Ku   (Mv, Ku before the update)
-  const double al = c44 + c1 * c2, be = a1 * c2 - 1.0;
+  // (part 2: al2 qM + be qK - Pb + 4/dt Mv' - 2 Ku, al2 = al - 8/dt^2)
+  const double al = c44 + c1 * c2, be = a1 * c2 - 1.0, al2 = al - c4 * c2;
   // two consecutive values a thread (vector loads and stores of every vector; n even), then a last odd one
   const int64_t npair = n >> 1;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npair; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = 2 * t;
     auto ld = [&](const double* x) { return *reinterpret_cast<const double2*>(x + i); };
     auto st = [&](double* x, double y0, double y1) { *reinterpret_cast<double2*>(x + i) = make_double2(y0, y1); };
-    const double2 d = ld(du), vp = ld(v_prev), m_ = ld(qM), k_ = ld(qK), uu = ld(u), aa = ld(a), ku = ld(Ku);
-    const double2 mv = ld(Mv), kv = ld(Kv), pb = ld(Pb);
-    st(u, uu.x + d.x, uu.y + d.y);
-    st(v_push, c2 * d.x - vp.x, c2 * d.y - vp.y);
-    st(a, c44 * d.x - c4 * vp.x - aa.x, c44 * d.y - c4 * vp.y - aa.y);
-    st(Ku, ku.x + k_.x, ku.y + k_.y);
-    const double mv2x = c2 * m_.x - mv.x, kv2x = c2 * k_.x - kv.x, mv2y = c2 * m_.y - mv.y, kv2y = c2 * k_.y - kv.y;
-    st(Pb, al * m_.x + be * k_.x - (pb.x + c4 * mv.x + 2.0 * ku.x),
-       al * m_.y + be * k_.y - (pb.y + c4 * mv.y + 2.0 * ku.y));
-    st(Mv, mv2x, mv2y);
-    st(Kv, kv2x, kv2y);
-    st(Av_push, cM * mv2x + cK * kv2x, cM * mv2y + cK * kv2y);
-    if (e_push) {
-      const double2 ab = ld(du_ab);
-      store_snap2(e_push, slot_stride, i, d.x - ab.x, d.y - ab.y);
+    const double2 d = ld(du), vp = ld(v_prev), m_ = ld(qM), k_ = ld(qK), mv = ld(Mv);
+    if (STATE) {
+      const double2 uu = ld(u), aa = ld(a), ku = ld(Ku), pb = ld(Pb);
+      st(u, uu.x + d.x, uu.y + d.y);
+      st(a, c44 * d.x - c4 * vp.x - aa.x, c44 * d.y - c4 * vp.y - aa.y);
+      st(Ku, ku.x + k_.x, ku.y + k_.y);
+      if (P == 0) {
+        st(Pb, al * m_.x + be * k_.x - (pb.x + c4 * mv.x + 2.0 * ku.x),
+           al * m_.y + be * k_.y - (pb.y + c4 * mv.y + 2.0 * ku.y));
+      } else {
+        st(Pb, al2 * m_.x + be * k_.x - (pb.x - c4 * mv.x + 2.0 * ku.x),
+           al2 * m_.y + be * k_.y - (pb.y - c4 * mv.y + 2.0 * ku.y));
+      }
+    }
+    if (VEL) {
+      const double2 kv = ld(Kv);
+      st(v_push, c2 * d.x - vp.x, c2 * d.y - vp.y);
+      const double mv2x = c2 * m_.x - mv.x, kv2x = c2 * k_.x - kv.x, mv2y = c2 * m_.y - mv.y, kv2y = c2 * k_.y - kv.y;
+      st(Mv, mv2x, mv2y);
+      st(Kv, kv2x, kv2y);
+      st(Av_push, cM * mv2x + cK * kv2x, cM * mv2y + cK * kv2y);
+      if (e_push) {
+        const double2 ab = ld(du_ab);
+        store_snap2(e_push, slot_stride, i, d.x - ab.x, d.y - ab.y);
+      }
     }
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const int64_t i = n - 1;
-    const double d = du[i], vp = v_prev[i], m_ = qM[i], k_ = qK[i];
-    u[i] += d;
-    v_push[i] = c2 * d - vp;
-    a[i] = c44 * d - c4 * vp - a[i];
-    const double ku = Ku[i];
-    Ku[i] = ku + k_;
-    const double mv = Mv[i], kv = Kv[i];
-    const double mv2 = c2 * m_ - mv, kv2 = c2 * k_ - kv;
-    Pb[i] = al * m_ + be * k_ - (Pb[i] + c4 * mv + 2.0 * ku);
-    Mv[i] = mv2;
-    Kv[i] = kv2;
-    Av_push[i] = cM * mv2 + cK * kv2;
-    if (e_push) store_snap(e_push, slot_stride, i, d - du_ab[i]);
+    const double d = du[i], vp = v_prev[i], m_ = qM[i], k_ = qK[i], mv = Mv[i];
+    if (STATE) {
+      u[i] += d;
+      a[i] = c44 * d - c4 * vp - a[i];
+      const double ku = Ku[i];
+      Ku[i] = ku + k_;
+      Pb[i] = P == 0 ? al * m_ + be * k_ - (Pb[i] + c4 * mv + 2.0 * ku)
+                     : al2 * m_ + be * k_ - (Pb[i] - c4 * mv + 2.0 * ku);
+    }
+    if (VEL) {
+      v_push[i] = c2 * d - vp;
+      const double kv = Kv[i];
+      const double mv2 = c2 * m_ - mv, kv2 = c2 * k_ - kv;
+      Mv[i] = mv2;
+      Kv[i] = kv2;
+      Av_push[i] = cM * mv2 + cK * kv2;
+      if (e_push) store_snap(e_push, slot_stride, i, d - du_ab[i]);
+    }
   }
 }
 
@@ -1132,33 +1153,62 @@ cudaError_t launch_cert(const MeshView& m, int rpad, double cM, double cK, const
   return cudaGetLastError();
 }
 
+template <typename E, int P>
+static void newmark_incr_t(int64_t n, double dt, double cM, double cK, double c1, double a1, const double* du,
+                           const double* du_ab, const double* qM, const double* qK, double* u, const double* v_prev,
+                           double* a, double* v_push, double* Ku, double* Mv, double* Kv, double* Pb, double* Av_push,
+                           void* e_push, cudaStream_t s, Ring4 vr, Ring4 avr, void* ring, int64_t slot_stride,
+                           const StepCtl* ctl) {
+  const int grid = grid_resident((const void*)k_newmark_incr<E, P>, kBlock, n);
+  k_newmark_incr<E, P><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku, Mv,
+                                               Kv, Pb, Av_push, (E*)e_push, vr, avr, (E*)ring, slot_stride, ctl);
+}
+
+template <int P>
+static void newmark_incr_p(int64_t n, double dt, double cM, double cK, double c1, double a1, const double* du,
+                           const double* du_ab, const double* qM, const double* qK, double* u, const double* v_prev,
+                           double* a, double* v_push, double* Ku, double* Mv, double* Kv, double* Pb, double* Av_push,
+                           void* e_push, int e_fmt, cudaStream_t s, Ring4 vr, Ring4 avr, void* ring,
+                           int64_t slot_stride, const StepCtl* ctl) {
+#define NM_ARGS n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku, Mv, Kv, Pb, Av_push, e_push, s, vr, \
+                avr, ring, slot_stride, ctl
+  if (e_fmt == 1)
+    newmark_incr_t<float, P>(NM_ARGS);
+  else if (e_fmt == 2)
+    newmark_incr_t<float2, P>(NM_ARGS);
+  else if (e_fmt == 3)
+    newmark_incr_t<SnapHL, P>(NM_ARGS);
+  else
+    newmark_incr_t<double, P>(NM_ARGS);
+#undef NM_ARGS
+}
+
+cudaError_t launch_newmark_incr_part(int64_t n, double dt, double cM, double cK, double a0, double a1,
+                                     const double* du, const double* du_ab, const double* qM, const double* qK,
+                                     double* u, const double* v_prev, double* a, double* v_push, double* Ku,
+                                     double* Mv, double* Kv, double* Pb, double* Av_push, void* e_push, int e_fmt,
+                                     cudaStream_t s, Ring4 vr, Ring4 avr, void* ring, int64_t slot_stride,
+                                     const StepCtl* ctl, int part) {
+  const double c1 = 4.0 / dt + a0;
+  if (part == 1)
+    newmark_incr_p<1>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku, Mv, Kv, Pb, Av_push, e_push,
+                      e_fmt, s, vr, avr, ring, slot_stride, ctl);
+  else if (part == 2)
+    newmark_incr_p<2>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku, Mv, Kv, Pb, Av_push, e_push,
+                      e_fmt, s, vr, avr, ring, slot_stride, ctl);
+  else
+    newmark_incr_p<0>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku, Mv, Kv, Pb, Av_push, e_push,
+                      e_fmt, s, vr, avr, ring, slot_stride, ctl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_newmark_incr(int64_t n, double dt, double cM, double cK, double a0, double a1, const double* du,
                                 const double* du_ab, const double* qM, const double* qK, double* u,
                                 const double* v_prev, double* a, double* v_push, double* Ku, double* Mv, double* Kv,
                                 double* Pb, double* Av_push, void* e_push, int e_fmt, cudaStream_t s, Ring4 vr,
                                 Ring4 avr, void* ring, int64_t slot_stride, const StepCtl* ctl) {
-  const double c1 = 4.0 / dt + a0;
-  const int grid = e_fmt == 1   ? grid_resident((const void*)k_newmark_incr<float>, kBlock, n)
-                   : e_fmt == 2 ? grid_resident((const void*)k_newmark_incr<float2>, kBlock, n)
-                   : e_fmt == 3 ? grid_resident((const void*)k_newmark_incr<SnapHL>, kBlock, n)
-                                : grid_resident((const void*)k_newmark_incr<double>, kBlock, n);
-  if (e_fmt == 1)
-    k_newmark_incr<float><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a,
-                                                         v_push, Ku, Mv, Kv, Pb, Av_push, (float*)e_push, vr, avr, (float*)ring,
-                                                         slot_stride, ctl);
-  else if (e_fmt == 2)
-    k_newmark_incr<float2><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a,
-                                                          v_push, Ku, Mv, Kv, Pb, Av_push, (float2*)e_push, vr, avr, (float2*)ring,
-                                                          slot_stride, ctl);
-  else if (e_fmt == 3)
-    k_newmark_incr<SnapHL><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a,
-                                                          v_push, Ku, Mv, Kv, Pb, Av_push, (SnapHL*)e_push, vr, avr, (SnapHL*)ring,
-                                                          slot_stride, ctl);
-  else
-    k_newmark_incr<double><<<grid, kBlock, 0, s>>>(n, dt, cM, cK, c1, a1, du, du_ab, qM, qK, u, v_prev, a,
-                                                          v_push, Ku, Mv, Kv, Pb, Av_push, (double*)e_push, vr, avr, (double*)ring,
-                                                          slot_stride, ctl);
-  return cudaGetLastError();
+  return launch_newmark_incr_part(n, dt, cM, cK, a0, a1, du, du_ab, qM, qK, u, v_prev, a, v_push, Ku, Mv, Kv, Pb,
+                                  Av_push, e_push, e_fmt, s, vr, avr, ring, slot_stride, ctl, 0);
 }
 
 cudaError_t launch_pred_dots(const PredView& p, int slot_new, uint64_t valid_mask, cudaStream_t s,
