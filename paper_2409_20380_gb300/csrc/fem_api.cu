@@ -794,7 +794,8 @@ struct Group {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t gs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // capture streams (top level, bodies, fork)
-  cudaEvent_t gev[4] = {nullptr, nullptr, nullptr, nullptr};          // forks / joins of the captured step
+  cudaEvent_t gev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr}; // forks / joins of the captured step
+  int ab_ready = -1;              // step whose du_AB the last graph launch formed at its tail
   int* h_pin = nullptr;           // pinned: [0] = 1 (use_ext flag), [1] = step counter to upload
   int ctl_it = -1;                // step counter the device record holds (-1: unknown, upload first)
   bool graph_failed = false;      // capture or instantiation failed: eager steps from now on
@@ -1376,7 +1377,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   cudaStream_t sf = g->gs[4];
   GE(cudaEventRecord(g->gev[0], s));
   GE(cudaStreamWaitEvent(sf, g->gev[0], 0));
-  GE(launch_ab4_ring(g->n, dt, V, ctl, g->du_ab, sf));
+  // (du_AB of this step was formed at the tail of the previous step's graph, or just before this launch)
   // 2. right-hand side from the recurrences
   GE(launch_rhs_incr(mv, rpad, g->Pb, g->b, g->src, g->ext, 0.0, sf,
                      ctl));
@@ -1518,8 +1519,13 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   GE(launch_newmark_incr_part(g->n, dt, m->cM, m->cK, m->tp.a0, m->tp.a1, g->x, g->du_ab, g->qM, g->qK, g->u, nullptr,
                               g->a, nullptr, g->Ku, g->Mv, g->Kv, g->Pb, nullptr, nullptr, o.snapshot_format, s, V,
                               AV, dd ? g->ring : nullptr, g->snap_stride, ctl, n_part));
+  // ... and the next step's Adams-Bashforth increment (it reads the velocity ring, now holding v^it; this
+  // step's du_AB has been read) on a third stream
+  GE(cudaEventRecord(g->gev[2], s));
+  GE(cudaStreamWaitEvent(s4, g->gev[2], 0));
+  GE(launch_ab4_ring(g->n, dt, V, ctl, g->du_ab, s4, 1));
+  GE(cudaEventRecord(g->gev[4], s4));
   if (dd) {
-    GE(cudaEventRecord(g->gev[2], s));
     GE(cudaStreamWaitEvent(sf, g->gev[2], 0));
     GE(launch_newmark_incr_part(g->n, dt, m->cM, m->cK, m->tp.a0, m->tp.a1, g->x, g->du_ab, g->qM, g->qK, g->u,
                                 nullptr, g->a, nullptr, g->Ku, g->Mv, g->Kv, g->Pb, nullptr, nullptr,
@@ -1533,6 +1539,7 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
     GE(launch_pred_dots(pv, 0, 0, s, ctl));
     GE(cudaStreamWaitEvent(s, g->gev[3], 0));
   }
+  GE(cudaStreamWaitEvent(s, g->gev[4], 0));
   GE(launch_step_end(w->outer, g->ncase, g->acc_iters, g->acc_relres, g->acc_status, ctl, s));
   return cudaSuccess;
 }
@@ -1606,9 +1613,15 @@ static fem_status group_step_graph(fem_batch* bt, Group* g) {
   }
   if (g->use_ext) CU(cudaMemcpyAsync(&g->ctl->use_ext, &g->h_pin[0], sizeof(int), cudaMemcpyHostToDevice, s));
   g->use_ext = false;
+  if (g->ab_ready != it) {   // the first graph step, or after eager steps: this step's du_AB before the graph
+    const Ring4 V{{g->vh[0], g->vh[1], g->vh[2], g->vh[3]}};
+    CU(launch_ab4_ring(g->n, g->mesh->tp.dt, V, g->ctl, g->du_ab, s, 1));
+    g->ws->count();
+  }
   CU(cudaGraphLaunch(g->gexec, s));
   g->steps = it;
   g->ctl_it = it;
+  g->ab_ready = it + 1;
   g->graph_steps += 1;
   return FEM_OK;
 }

@@ -264,7 +264,9 @@ cudaError_t launch_extract_all(int64_t N, int rpad, int n_cases, const double* s
 cudaError_t launch_ab4(int64_t n, double dt, const double* v4, const double* v3, const double* v2,
                        const double* v1, double* du_ab, cudaStream_t s);
 // The same from the velocity ring with the step read from ctl (v^j in v.p[j mod 4]).
-cudaError_t launch_ab4_ring(int64_t n, double dt, Ring4 v, const StepCtl* ctl, double* du_ab, cudaStream_t s);
+// (ahead 1: the increment of the step after the one ctl holds)
+cudaError_t launch_ab4_ring(int64_t n, double dt, Ring4 v, const StepCtl* ctl, double* du_ab, cudaStream_t s,
+                            int ahead = 0);
 cudaError_t launch_add(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
 cudaError_t launch_newmark_update(int64_t n, double dt, const double* du, const double* du_ab, double* u,
                                   const double* v_prev, double* a, double* v_push, void* e_push, int e_fmt,

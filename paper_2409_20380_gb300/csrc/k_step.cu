@@ -164,8 +164,10 @@ __global__ void k_ab4(int64_t n, double h, const double* __restrict__ v4, const 
   ab4_body(n, h, v4, v3, v2, v1, out);
 }
 
-__global__ void k_ab4_ring(int64_t n, double h, Ring4 v, const StepCtl* __restrict__ ctl, double* __restrict__ out) {
-  const int it = ctl->it;   // v^{it-4} .. v^{it-1} sit in slots it, it+1, it+2, it+3 (mod 4)
+// (ahead 1: for the step after the one the record holds, from the tail of the step graph or before it)
+__global__ void k_ab4_ring(int64_t n, double h, Ring4 v, const StepCtl* __restrict__ ctl, double* __restrict__ out,
+                           int ahead) {
+  const int it = ctl->it + ahead;   // v^{it-4} .. v^{it-1} sit in slots it, it+1, it+2, it+3 (mod 4)
   ab4_body(n, h, v.p[it & 3], v.p[(it + 1) & 3], v.p[(it + 2) & 3], v.p[(it + 3) & 3], out);
 }
 
@@ -1077,8 +1079,9 @@ cudaError_t launch_ab4(int64_t n, double dt, const double* v4, const double* v3,
   return cudaGetLastError();
 }
 
-cudaError_t launch_ab4_ring(int64_t n, double dt, Ring4 v, const StepCtl* ctl, double* du_ab, cudaStream_t s) {
-  k_ab4_ring<<<grid_for(n), kBlock, 0, s>>>(n, dt / 24.0, v, ctl, du_ab);
+cudaError_t launch_ab4_ring(int64_t n, double dt, Ring4 v, const StepCtl* ctl, double* du_ab, cudaStream_t s,
+                            int ahead) {
+  k_ab4_ring<<<grid_for(n), kBlock, 0, s>>>(n, dt / 24.0, v, ctl, du_ab, ahead);
   return cudaGetLastError();
 }
 
