@@ -1371,8 +1371,8 @@ static cudaError_t capture_step(fem_batch* bt, Group* g) {
   const bool ab = m->ab.nb > 0;
   const long long n_fixed = 6 + (dd ? 6 + (o.pred_guard ? 1 : 0) : 0) + (g->imp.n > 0 ? 1 : 0) + (ab ? 3 + (dd ? 1 : 0) : 0),
                   n_pass = 4 + (ab ? 1 : 0), n_if = sg ? 4 : (sel ? 3 : 2), n_inner = (ab ? 4LL : 3LL) * ce + 1;
-  // 1. step record; the per-region Gram solves (few warps per SM) run beside the Adams-Bashforth
-  // increment and the right-hand side, which do not depend on them
+  // 1. step record; the per-region Gram solves (few warps per SM) run beside the right-hand side, which
+  // does not depend on them
   GE(launch_step_begin(ctl, dd ? g->n_slots : 0, o.s_max, dt, dd ? 1 : 0, n_fixed, s));
   cudaStream_t sf = g->gs[4];
   GE(cudaEventRecord(g->gev[0], s));
