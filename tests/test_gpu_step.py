@@ -26,10 +26,11 @@ def torch_dev():
 
 
 def _run_and_check(mesh, tp, sources, opts, n_steps, region_nodes=None, check_pred=True, b_tol=1e-12,
-                   system=None, create=None, regions=None):
+                   system=None, create=None, regions=None, eager_steps=()):
     """Steps the batch one step at a time and checks every step against the oracle; returns (iterations per
     case, predictor check statistics).  system (the oracle's (System, reduced A)), create (the mesh
-    constructor) and regions (a node -> region map) default to the linear-tet ones."""
+    constructor) and regions (a node -> region map) default to the linear-tet ones.  Steps listed in
+    eager_steps run eagerly (profiling on) inside a graph-step run."""
     sysm, A = system if system is not None else oracle.build_system(mesh, tp)
     N = mesh.n_nodes
     h = (create or fem.fem_mesh_create)(mesh, tp)
@@ -50,7 +51,11 @@ def _run_and_check(mesh, tp, sources, opts, n_steps, region_nodes=None, check_pr
         reg_dof = np.repeat(regions, 3)[sysm.free] if regions is not None else None
         n_reg = int(regions.max()) + 1 if regions is not None else 0
         for it in range(1, n_steps + 1):
+            if it in eager_steps:
+                fem.fem_batch_profile(bt, 1)
             stat, iters, relres = fem.fem_step(bt, 1, nc)
+            if it in eager_steps:
+                fem.fem_batch_profile(bt, 0)
             total_iters += iters
             for c in range(nc):
                 S = st[c]
@@ -368,6 +373,19 @@ def test_step_guess_guard(torch_dev, graph):
     print("guess guard", graph, res)
     assert res[0][1].get(2, 0) == 0, res
     assert res[1][1].get(2, 0) > 0, res
+
+
+def test_graph_steps_around_eager_steps(torch_dev):
+    """Graph steps form the next step's Adams-Bashforth increment at their tail; a graph step after eager
+    steps forms its own before the launch.  Graph steps interleaved with eager ones (profiling on) on the
+    benchmark's settings: every step certified, every guess checked against the oracle's Adams-Bashforth
+    increment and regional correction."""
+    mesh = wl.config4_mesh(16, 16, 12)
+    tp = wl.config4_time_params()
+    srcs = wl.config4_sources(mesh, 8)
+    opts = fem.fem_opts_default(tol=1e-8, precision=fem.FEM_FP32_INNER, predictor=fem.FEM_PRED_DD, s_max=16,
+                                cert_df=3, snapshot_format=2, use_graph=1)
+    _run_and_check(mesh, tp, srcs, opts, 30, region_nodes=1024, b_tol=1e-11, eager_steps={1, 9, 10, 17, 25})
 
 
 def test_pred_guard_option_checked(torch_dev):
